@@ -1,0 +1,681 @@
+/*
+ * magnus_oracle.c -- TEST INFRASTRUCTURE, not the product.
+ *
+ * A plain, slow, obviously-correct FP64 CPU restatement of the method of
+ * Auer, Einkemmer, Kandolf, Ostermann, "Magnus integrators on multicore CPUs and
+ * GPUs" (arXiv:1709.06483).  Only tests/, __graft_entry__.smoke() and the
+ * CPU-baseline leg of bench.py may load it; the CUDA library never does, and the
+ * two share no code.  Every function cites the passage of the paper it follows.
+ *
+ * Notation.  The paper writes i psi' = H(t) psi (Sec. 1, Eq. (1)) and
+ * Y' = A(t) Y (Sec. 2, Eq. (2)), so A = -iH.  A stored problem is
+ * H(t) = sum_k f_k(t) H_k (the split H_1 + h(t) H_2 of Sec. 4).  One exponential
+ * is written exp(-iK) with a Hermitian generator K that already contains the
+ * step size.
+ *
+ * Readings of the paper (where it is silent or defers to its ref. [ckor15]):
+ *  - Leja points on [-2,2], xi_0 = 2, each next point maximises prod |x - xi_k|;
+ *    ties go to the larger x.
+ *  - K is shifted and scaled, X = (K - cI)/gamma with [c-2gamma, c+2gamma] the
+ *    spectral enclosure, and exp(-iK) = e^{-ic} exp(-i gamma X) is split into
+ *    s = ceil(gamma/rho_max) equal substeps.
+ *  - Early termination: stop at the first j with
+ *    |d_j|*||w_j|| + |d_{j-1}|*||w_{j-1}|| <= tol_abs + tol_rel*||p_j|| (2-norms).
+ *  - The spectral enclosure of each stored term is its Gershgorin interval; the
+ *    enclosure of a combination sum_k beta_k H_k is the Minkowski sum of the
+ *    scaled intervals (Weyl); the M4 commutator adds [-r, r] with
+ *    r = kappa * sum_{k<l} |coef_kl| * 2 * hw_k * hw_l (hw = half-width).
+ */
+#include "magnus_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define MAX_TERMS 8
+
+/* ------------------------------------------------------------------------- */
+/* Leja points (Sec. 3: interpolation nodes xi_0..xi_m, "Leja points").       */
+/* ------------------------------------------------------------------------- */
+
+/* log prod_k |x - xi_k| */
+static double leja_logprod(double x, const double *xi, int n) {
+  double s = 0.0;
+  for (int k = 0; k < n; k++) s += log(fabs(x - xi[k]));
+  return s;
+}
+
+/* derivative of the log-product: sum_k 1/(x - xi_k) */
+static double leja_dlog(double x, const double *xi, int n) {
+  double s = 0.0;
+  for (int k = 0; k < n; k++) s += 1.0 / (x - xi[k]);
+  return s;
+}
+
+/*
+ * xi_0 = 2 and xi_j = argmax_{x in [-2,2]} prod_{k<j} |x - xi_k|.
+ * Once both endpoints are nodes, the maximum lies strictly inside one gap
+ * between consecutive nodes; there the log-product is strictly concave, so its
+ * unique maximiser is the zero of its derivative, found by bisection to the
+ * last bit.  The winning gap is the one with the largest log-product; values
+ * within 1e-10 of the best count as a tie, resolved towards the larger x.
+ */
+int orc_leja_points(int m, double *xi) {
+  if (m < 0 || !xi) return ORC_EINVAL;
+  xi[0] = 2.0;
+  if (m == 0) return ORC_OK;
+  xi[1] = -2.0; /* the maximiser of |x - 2| on [-2,2] */
+  double *s = (double *)malloc(sizeof(double) * (size_t)(m + 1));
+  double *cx = (double *)malloc(sizeof(double) * (size_t)(m + 1));
+  double *cl = (double *)malloc(sizeof(double) * (size_t)(m + 1));
+  if (!s || !cx || !cl) { free(s); free(cx); free(cl); return ORC_ENOMEM; }
+  for (int j = 2; j <= m; j++) {
+    /* sorted copy of the current nodes (insertion sort) */
+    for (int k = 0; k < j; k++) s[k] = xi[k];
+    for (int a = 1; a < j; a++) {
+      double v = s[a];
+      int b = a - 1;
+      while (b >= 0 && s[b] > v) { s[b + 1] = s[b]; b--; }
+      s[b + 1] = v;
+    }
+    double best = -INFINITY;
+    for (int g = 0; g + 1 < j; g++) {
+      double lo = s[g], hi = s[g + 1];
+      double mid = 0.5 * (lo + hi);
+      for (;;) {
+        mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        double slope = leja_dlog(mid, xi, j);
+        if (slope == 0.0) break;
+        if (slope > 0.0) lo = mid; else hi = mid;
+      }
+      cx[g] = mid;
+      cl[g] = leja_logprod(mid, xi, j);
+      if (cl[g] > best) best = cl[g];
+    }
+    double pick = -INFINITY;
+    for (int g = 0; g + 1 < j; g++)
+      if (cl[g] >= best - 1e-10 && cx[g] > pick) pick = cx[g];
+    xi[j] = pick;
+  }
+  free(s); free(cx); free(cl);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Divided differences d_i = exp[xi_0,...,xi_i] (Sec. 3).                      */
+/* ------------------------------------------------------------------------- */
+
+/* C = A*B for lower-triangular n x n matrices (row-major). */
+static void lt_matmul(int n, const double complex *A, const double complex *B, double complex *C) {
+  for (int i = 0; i < n; i++)
+    for (int j = 0; j < n; j++) {
+      double complex acc = 0.0;
+      if (j <= i)
+        for (int k = j; k <= i; k++) acc += A[i * n + k] * B[k * n + j];
+      C[i * n + j] = acc;
+    }
+}
+
+static double mat_norm1(int n, const double complex *A) {
+  double best = 0.0;
+  for (int j = 0; j < n; j++) {
+    double s = 0.0;
+    for (int i = 0; i < n; i++) s += cabs(A[i * n + j]);
+    if (s > best) best = s;
+  }
+  return best;
+}
+
+/*
+ * Opitz: for the lower bidiagonal Z with diagonal xi_0..xi_m and ones below it,
+ * the first column of g(Z) lists the divided differences g[xi_0..xi_j].  Here
+ * g(x) = exp(-i rho x), and g(Z) = exp(-i rho Z) is evaluated by a Taylor series
+ * of the scaled matrix (1-norm <= 1/2) followed by repeated squaring.
+ */
+int orc_divided_differences(int m, const double *xi, double rho, double complex *d) {
+  if (m < 0 || !xi || !d) return ORC_EINVAL;
+  const int n = m + 1;
+  size_t bytes = sizeof(double complex) * (size_t)n * (size_t)n;
+  double complex *A = (double complex *)malloc(bytes);
+  double complex *T = (double complex *)malloc(bytes);
+  double complex *P = (double complex *)malloc(bytes);
+  double complex *Q = (double complex *)malloc(bytes);
+  if (!A || !T || !P || !Q) { free(A); free(T); free(P); free(Q); return ORC_ENOMEM; }
+  memset(A, 0, bytes);
+  for (int j = 0; j < n; j++) {
+    A[j * n + j] = -I * rho * xi[j];
+    if (j > 0) A[j * n + j - 1] = -I * rho;
+  }
+  int q = 0;
+  double nrm = mat_norm1(n, A);
+  while (nrm > 0.5) { nrm *= 0.5; q++; }
+  double scale = ldexp(1.0, -q);
+  for (int e = 0; e < n * n; e++) A[e] *= scale;
+  /* T = sum_k A^k / k!, P holds the current term */
+  memset(T, 0, bytes);
+  memset(P, 0, bytes);
+  for (int j = 0; j < n; j++) { T[j * n + j] = 1.0; P[j * n + j] = 1.0; }
+  for (int k = 1; k <= 60; k++) {
+    lt_matmul(n, P, A, Q);
+    for (int e = 0; e < n * n; e++) { P[e] = Q[e] / (double)k; T[e] += P[e]; }
+    if (mat_norm1(n, P) <= 1e-20 * mat_norm1(n, T)) break;
+  }
+  for (int r = 0; r < q; r++) {
+    lt_matmul(n, T, T, Q);
+    memcpy(T, Q, bytes);
+  }
+  for (int j = 0; j < n; j++) d[j] = T[j * n + 0];
+  free(A); free(T); free(P); free(Q);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Spin-chain Hamiltonians (Sec. 4, Pauli matrices and Kronecker embedding).  */
+/* ------------------------------------------------------------------------- */
+/*
+ * sigma_j^alpha = I x ... x sigma^alpha x ... x I with spin 1 the leftmost
+ * factor, so for n spins the basis index is x = sum_j b_j 2^(n-j): spin j sits
+ * at bit (n-j).  On a basis state, with z_j = 1 - 2 b_j:
+ *   sigma^z_j |x> = z_j |x>,  sigma^x_j |x> = |x ^ bit_j>,
+ *   sigma^y_j |x> = i z_j |x ^ bit_j>      (sigma^y = [[0,-i],[i,0]]).
+ * Hence sigma^x_i sigma^x_j + sigma^y_i sigma^y_j maps |x> to
+ * (1 - z_i z_j) |x ^ bit_i ^ bit_j>: 2 for anti-parallel spins, 0 otherwise,
+ * and every such matrix is real symmetric.
+ */
+static inline int64_t spin_bit(int nspins, int j /* 1-based */) { return (int64_t)1 << (nspins - j); }
+static inline double spin_z(int64_t x, int nspins, int j) { return (x & spin_bit(nspins, j)) ? -1.0 : 1.0; }
+
+int64_t orc_xxz_nnz(int nspins, const double *J, double delta) {
+  (void)J; (void)delta;
+  int64_t D = (int64_t)1 << nspins;
+  return D + (int64_t)(nspins - 1) * (D / 2);
+}
+
+/*
+ * Open XXZ chain: H_s = sum_{i=1}^{n-1} J_i (sx_i sx_{i+1} + sy_i sy_{i+1} + delta sz_i sz_{i+1})
+ *                       + sum_{i=1}^{n} h_i sz_i.
+ * J[i-1] = J_i, hz[i-1] = h_i.  Row x stores the diagonal (always) and one entry
+ * per anti-parallel bond; columns ascending.
+ */
+int orc_build_xxz_csr(int nspins, const double *J, const double *hz, double delta,
+                      int64_t *rowptr, int32_t *col, double complex *val) {
+  if (nspins < 2 || nspins > 30) return ORC_EINVAL;
+  int64_t D = (int64_t)1 << nspins;
+  int64_t pos = 0;
+  int64_t ccol[64];
+  double complex cval[64];
+  for (int64_t x = 0; x < D; x++) {
+    rowptr[x] = pos;
+    int cnt = 0;
+    double diag = 0.0;
+    for (int i = 1; i <= nspins - 1; i++) diag += delta * J[i - 1] * spin_z(x, nspins, i) * spin_z(x, nspins, i + 1);
+    for (int i = 1; i <= nspins; i++) diag += hz[i - 1] * spin_z(x, nspins, i);
+    ccol[cnt] = x; cval[cnt] = diag; cnt++;
+    for (int i = 1; i <= nspins - 1; i++) {
+      double zz = spin_z(x, nspins, i) * spin_z(x, nspins, i + 1);
+      if (zz < 0.0) {
+        ccol[cnt] = x ^ spin_bit(nspins, i) ^ spin_bit(nspins, i + 1);
+        cval[cnt] = J[i - 1] * (1.0 - zz);
+        cnt++;
+      }
+    }
+    for (int a = 1; a < cnt; a++) { /* insertion sort by column */
+      int64_t c = ccol[a]; double complex v = cval[a]; int b = a - 1;
+      while (b >= 0 && ccol[b] > c) { ccol[b + 1] = ccol[b]; cval[b + 1] = cval[b]; b--; }
+      ccol[b + 1] = c; cval[b + 1] = v;
+    }
+    for (int a = 0; a < cnt; a++) { col[pos] = (int32_t)ccol[a]; val[pos] = cval[a]; pos++; }
+  }
+  rowptr[D] = pos;
+  return ORC_OK;
+}
+
+/* Transverse field sum_{i=1}^{n} sx_i: row x has a 1 at every column x ^ bit_i. */
+int orc_build_field_x_csr(int nspins, int64_t *rowptr, int32_t *col, double complex *val) {
+  if (nspins < 1 || nspins > 30) return ORC_EINVAL;
+  int64_t D = (int64_t)1 << nspins;
+  int64_t pos = 0;
+  int64_t ccol[64];
+  for (int64_t x = 0; x < D; x++) {
+    rowptr[x] = pos;
+    int cnt = 0;
+    for (int i = 1; i <= nspins; i++) ccol[cnt++] = x ^ spin_bit(nspins, i);
+    for (int a = 1; a < cnt; a++) {
+      int64_t c = ccol[a]; int b = a - 1;
+      while (b >= 0 && ccol[b] > c) { ccol[b + 1] = ccol[b]; b--; }
+      ccol[b + 1] = c;
+    }
+    for (int a = 0; a < cnt; a++) { col[pos] = (int32_t)ccol[a]; val[pos] = 1.0; pos++; }
+  }
+  rowptr[D] = pos;
+  return ORC_OK;
+}
+
+/*
+ * Long-range chain, every pair i<j once:
+ * H_s = sum_{i<j} J_ij (sx_i sx_j + sy_i sy_j + delta sz_i sz_j) + sum_i h_i sz_i,
+ * J_ij = 1/|i-j|^alpha.  Dense, row-major D x D.
+ */
+int orc_build_longrange_dense(int nspins, double alpha, const double *hz, double delta, double complex *H) {
+  if (nspins < 2 || nspins > 15) return ORC_EINVAL;
+  int64_t D = (int64_t)1 << nspins;
+  memset(H, 0, sizeof(double complex) * (size_t)D * (size_t)D);
+  for (int64_t x = 0; x < D; x++) {
+    double diag = 0.0;
+    for (int i = 1; i <= nspins; i++) diag += hz[i - 1] * spin_z(x, nspins, i);
+    for (int i = 1; i <= nspins; i++)
+      for (int j = i + 1; j <= nspins; j++) {
+        double Jij = 1.0 / pow((double)(j - i), alpha);
+        double zz = spin_z(x, nspins, i) * spin_z(x, nspins, j);
+        diag += delta * Jij * zz;
+        if (zz < 0.0) {
+          int64_t y = x ^ spin_bit(nspins, i) ^ spin_bit(nspins, j);
+          H[x * D + y] += Jij * (1.0 - zz);
+        }
+      }
+    H[x * D + x] += diag;
+  }
+  return ORC_OK;
+}
+
+int orc_build_field_x_dense(int nspins, double complex *H) {
+  if (nspins < 1 || nspins > 15) return ORC_EINVAL;
+  int64_t D = (int64_t)1 << nspins;
+  memset(H, 0, sizeof(double complex) * (size_t)D * (size_t)D);
+  for (int64_t x = 0; x < D; x++)
+    for (int i = 1; i <= nspins; i++) H[x * D + (x ^ spin_bit(nspins, i))] = 1.0;
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Problem: H(t) = sum_k f_k(t) H_k (Sec. 4, split H = H_1 + h(t) H_2).       */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+  int kind;
+  const int64_t *rowptr;
+  const int32_t *col;
+  const double complex *val;
+  double a, b; /* Gershgorin enclosure of the spectrum */
+  int set;
+} orc_term;
+
+typedef struct {
+  double a0;
+  int nmodes;
+  double *ac, *as, *om;
+} orc_coeff;
+
+struct orc_problem {
+  int64_t dim;
+  int nterms;
+  orc_term term[MAX_TERMS];
+  orc_coeff coeff[MAX_TERMS];
+  double tol_rel, tol_abs, rho_max;
+  int m_max;
+  double xi[1024];
+};
+
+orc_problem *orc_problem_new(int64_t dim, int nterms) {
+  if (dim < 1 || nterms < 1 || nterms > MAX_TERMS) return NULL;
+  orc_problem *p = (orc_problem *)calloc(1, sizeof(orc_problem));
+  if (!p) return NULL;
+  p->dim = dim;
+  p->nterms = nterms;
+  p->tol_rel = 1e-10; /* Sec. 4: relative and absolute tolerance 1e-10 */
+  p->tol_abs = 1e-10;
+  p->m_max = 100;
+  p->rho_max = 4.0;
+  orc_leja_points(p->m_max, p->xi);
+  return p;
+}
+
+void orc_problem_free(orc_problem *p) {
+  if (!p) return;
+  for (int k = 0; k < MAX_TERMS; k++) { free(p->coeff[k].ac); free(p->coeff[k].as); free(p->coeff[k].om); }
+  free(p);
+}
+
+/* Gershgorin: spec(H) within [min_i (H_ii - R_i), max_i (H_ii + R_i)], R_i = sum_{j != i} |H_ij|. */
+static void gershgorin(orc_term *t, int64_t D) {
+  double lo = INFINITY, hi = -INFINITY;
+  for (int64_t i = 0; i < D; i++) {
+    double c = 0.0, R = 0.0;
+    if (t->kind == ORC_TERM_CSR) {
+      for (int64_t e = t->rowptr[i]; e < t->rowptr[i + 1]; e++) {
+        if (t->col[e] == i) c += creal(t->val[e]);
+        else R += cabs(t->val[e]);
+      }
+    } else {
+      for (int64_t j = 0; j < D; j++) {
+        if (j == i) c += creal(t->val[i * D + j]);
+        else R += cabs(t->val[i * D + j]);
+      }
+    }
+    if (c - R < lo) lo = c - R;
+    if (c + R > hi) hi = c + R;
+  }
+  t->a = lo;
+  t->b = hi;
+}
+
+int orc_set_csr(orc_problem *p, int k, const int64_t *rowptr, const int32_t *col, const double complex *val) {
+  if (!p || k < 0 || k >= p->nterms || !rowptr || !col || !val) return ORC_EINVAL;
+  orc_term *t = &p->term[k];
+  t->kind = ORC_TERM_CSR; t->rowptr = rowptr; t->col = col; t->val = val; t->set = 1;
+  gershgorin(t, p->dim);
+  return ORC_OK;
+}
+
+int orc_set_dense(orc_problem *p, int k, const double complex *H) {
+  if (!p || k < 0 || k >= p->nterms || !H) return ORC_EINVAL;
+  orc_term *t = &p->term[k];
+  t->kind = ORC_TERM_DENSE; t->rowptr = NULL; t->col = NULL; t->val = H; t->set = 1;
+  gershgorin(t, p->dim);
+  return ORC_OK;
+}
+
+int orc_set_coeff(orc_problem *p, int k, double a0, int nmodes, const double *ac, const double *as,
+                  const double *om) {
+  if (!p || k < 0 || k >= p->nterms || nmodes < 0) return ORC_EINVAL;
+  orc_coeff *c = &p->coeff[k];
+  free(c->ac); free(c->as); free(c->om);
+  c->ac = c->as = c->om = NULL;
+  c->a0 = a0;
+  c->nmodes = nmodes;
+  if (nmodes > 0) {
+    c->ac = (double *)malloc(sizeof(double) * (size_t)nmodes);
+    c->as = (double *)malloc(sizeof(double) * (size_t)nmodes);
+    c->om = (double *)malloc(sizeof(double) * (size_t)nmodes);
+    if (!c->ac || !c->as || !c->om) return ORC_ENOMEM;
+    for (int m = 0; m < nmodes; m++) {
+      c->ac[m] = ac ? ac[m] : 0.0;
+      c->as[m] = as ? as[m] : 0.0;
+      c->om[m] = om[m];
+    }
+  }
+  return ORC_OK;
+}
+
+int orc_set_leja(orc_problem *p, double tol_rel, double tol_abs, int m_max, double rho_max) {
+  if (!p || m_max < 1 || m_max > 1000 || !(rho_max > 0.0)) return ORC_EINVAL;
+  p->tol_rel = tol_rel; p->tol_abs = tol_abs; p->m_max = m_max; p->rho_max = rho_max;
+  return orc_leja_points(m_max, p->xi);
+}
+
+int orc_term_interval(const orc_problem *p, int k, double *a, double *b) {
+  if (!p || k < 0 || k >= p->nterms || !p->term[k].set) return ORC_EINVAL;
+  *a = p->term[k].a; *b = p->term[k].b;
+  return ORC_OK;
+}
+
+/* f_k(t) = a0 + sum_m (ac_m cos(om_m t) + as_m sin(om_m t)) */
+double orc_coeff_eval(const orc_problem *p, int k, double t) {
+  const orc_coeff *c = &p->coeff[k];
+  double f = c->a0;
+  for (int m = 0; m < c->nmodes; m++) f += c->ac[m] * cos(c->om[m] * t) + c->as[m] * sin(c->om[m] * t);
+  return f;
+}
+
+/* y = H_k x */
+int orc_apply_term(const orc_problem *p, int k, const double complex *x, double complex *y) {
+  if (!p || k < 0 || k >= p->nterms || !p->term[k].set) return ORC_EINVAL;
+  const orc_term *t = &p->term[k];
+  const int64_t D = p->dim;
+  for (int64_t i = 0; i < D; i++) {
+    double complex acc = 0.0;
+    if (t->kind == ORC_TERM_CSR) {
+      for (int64_t e = t->rowptr[i]; e < t->rowptr[i + 1]; e++) acc += t->val[e] * x[t->col[e]];
+    } else {
+      for (int64_t j = 0; j < D; j++) acc += t->val[i * D + j] * x[j];
+    }
+    y[i] = acc;
+  }
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Generators K (one exponential exp(-iK)).                                   */
+/* ------------------------------------------------------------------------- */
+
+enum { GEN_LINEAR = 0, GEN_M4 = 1 };
+
+typedef struct {
+  const orc_problem *p;
+  int mode;
+  double beta[MAX_TERMS]; /* GEN_LINEAR: K = sum_k beta_k H_k                                */
+  double f1[MAX_TERMS];   /* GEN_M4: f_k(t_n + c_1 h)                                        */
+  double f2[MAX_TERMS];   /*         f_k(t_n + c_2 h)                                        */
+  double h;               /*         step size                                               */
+  double complex *u1, *u2, *t1, *t2; /* scratch of length dim                               */
+  orc_stats *st;
+} orc_gen;
+
+/* y = sum_k coef_k H_k x */
+static void apply_combo(const orc_gen *g, const double *coef, const double complex *x, double complex *y,
+                        double complex *tmp) {
+  const int64_t D = g->p->dim;
+  for (int64_t i = 0; i < D; i++) y[i] = 0.0;
+  for (int k = 0; k < g->p->nterms; k++) {
+    orc_apply_term(g->p, k, x, tmp);
+    if (g->st) g->st->n_termapply++;
+    for (int64_t i = 0; i < D; i++) y[i] += coef[k] * tmp[i];
+  }
+}
+
+/*
+ * y = K x.
+ * GEN_LINEAR: K = sum_k beta_k H_k.
+ * GEN_M4 (Sec. 2, Method M4, with A = -iH):
+ *   Omega = h/2 (A_1 + A_2) + (sqrt(3) h^2 / 12) [A_2, A_1]
+ *         = -i [ h/2 (H_1 + H_2) - i (sqrt(3) h^2/12) [H_2, H_1] ] = -i K,
+ * with the commutator applied to a vector as H_2(H_1 x) - H_1(H_2 x).
+ */
+static void gen_apply(orc_gen *g, const double complex *x, double complex *y) {
+  const int64_t D = g->p->dim;
+  if (g->mode == GEN_LINEAR) {
+    apply_combo(g, g->beta, x, y, g->t1);
+    return;
+  }
+  const double kappa = sqrt(3.0) * g->h * g->h / 12.0;
+  apply_combo(g, g->f1, x, g->u1, g->t1);    /* u1 = H_1 x        */
+  apply_combo(g, g->f2, x, g->u2, g->t1);    /* u2 = H_2 x        */
+  apply_combo(g, g->f2, g->u1, y, g->t1);    /* y  = H_2 (H_1 x)  */
+  apply_combo(g, g->f1, g->u2, g->t2, g->t1);/* t2 = H_1 (H_2 x)  */
+  for (int64_t i = 0; i < D; i++)
+    y[i] = 0.5 * g->h * (g->u1[i] + g->u2[i]) - I * kappa * (y[i] - g->t2[i]);
+}
+
+/* Spectral enclosure [a,b] of K (see the readings at the top). */
+static void gen_interval(const orc_gen *g, double *a, double *b) {
+  const orc_problem *p = g->p;
+  double lo = 0.0, hi = 0.0;
+  double lin[MAX_TERMS];
+  for (int k = 0; k < p->nterms; k++)
+    lin[k] = (g->mode == GEN_LINEAR) ? g->beta[k] : 0.5 * g->h * (g->f1[k] + g->f2[k]);
+  for (int k = 0; k < p->nterms; k++) {
+    double x1 = lin[k] * p->term[k].a, x2 = lin[k] * p->term[k].b;
+    lo += (x1 < x2) ? x1 : x2;
+    hi += (x1 < x2) ? x2 : x1;
+  }
+  if (g->mode == GEN_M4) {
+    const double kappa = sqrt(3.0) * g->h * g->h / 12.0;
+    double r = 0.0;
+    for (int k = 0; k < p->nterms; k++)
+      for (int l = k + 1; l < p->nterms; l++) {
+        double coef = g->f2[k] * g->f1[l] - g->f2[l] * g->f1[k];
+        double hwk = 0.5 * (p->term[k].b - p->term[k].a);
+        double hwl = 0.5 * (p->term[l].b - p->term[l].a);
+        r += fabs(coef) * 2.0 * hwk * hwl;
+      }
+    lo -= kappa * r;
+    hi += kappa * r;
+  }
+  *a = lo;
+  *b = hi;
+}
+
+static double vnorm(const double complex *x, int64_t D) {
+  double s = 0.0;
+  for (int64_t i = 0; i < D; i++) s += creal(x[i]) * creal(x[i]) + cimag(x[i]) * cimag(x[i]);
+  return sqrt(s);
+}
+
+/*
+ * v <- exp(-iK) v by Newton-form Leja interpolation (Sec. 3):
+ *   p_m(A) v = sum_i d_i prod_{j<i} (A - xi_j I) v, built by the short recurrence
+ *   w = v, p = d_0 v;  for i = 1..m: w = A w - xi_{i-1} w;  p = p + d_i w,
+ * applied here to A = X = (K - cI)/gamma and g(x) = exp(-i (gamma/s) x), s times,
+ * each substep multiplied by e^{-ic/s}.
+ */
+static int leja_core(orc_gen *g, double complex *v) {
+  const orc_problem *p = g->p;
+  const int64_t D = p->dim;
+  double a, b;
+  gen_interval(g, &a, &b);
+  const double c = 0.5 * (a + b);
+  const double gamma = 0.25 * (b - a);
+  if (g->st) g->st->n_exp++;
+  if (!(gamma > 0.0)) { /* K is (enclosed by) a scalar: exp(-iK) v = e^{-ic} v */
+    double complex ph = cexp(-I * c);
+    for (int64_t i = 0; i < D; i++) v[i] *= ph;
+    return ORC_OK;
+  }
+  int s = (int)ceil(gamma / p->rho_max);
+  if (s < 1) s = 1;
+  const double rho = gamma / s;
+  double complex *d = (double complex *)malloc(sizeof(double complex) * (size_t)(p->m_max + 1));
+  double complex *w = (double complex *)malloc(sizeof(double complex) * (size_t)D);
+  double complex *Kw = (double complex *)malloc(sizeof(double complex) * (size_t)D);
+  double complex *pp = (double complex *)malloc(sizeof(double complex) * (size_t)D);
+  if (!d || !w || !Kw || !pp) { free(d); free(w); free(Kw); free(pp); return ORC_ENOMEM; }
+  orc_divided_differences(p->m_max, p->xi, rho, d);
+  const double complex phase = cexp(-I * c / s);
+  int rc = ORC_OK;
+  for (int sub = 0; sub < s && rc == ORC_OK; sub++) {
+    for (int64_t i = 0; i < D; i++) { w[i] = v[i]; pp[i] = d[0] * v[i]; }
+    double e_prev = cabs(d[0]) * vnorm(w, D);
+    int conv = 0, m = 0;
+    for (int j = 1; j <= p->m_max; j++) {
+      gen_apply(g, w, Kw);
+      if (g->st) g->st->n_matvec++;
+      for (int64_t i = 0; i < D; i++) w[i] = (Kw[i] - c * w[i]) / gamma - p->xi[j - 1] * w[i];
+      for (int64_t i = 0; i < D; i++) pp[i] += d[j] * w[i];
+      double e = cabs(d[j]) * vnorm(w, D);
+      double pn = vnorm(pp, D);
+      if (!isfinite(pn) || !isfinite(e)) { rc = ORC_ENONFINITE; m = j; break; }
+      if (e + e_prev <= p->tol_abs + p->tol_rel * pn) { conv = 1; m = j; break; }
+      e_prev = e;
+    }
+    if (rc == ORC_OK && !conv) { rc = ORC_ENOCONV; m = p->m_max; }
+    if (g->st) {
+      g->st->n_substeps++;
+      if (m > g->st->max_m) g->st->max_m = m;
+      if (g->st->m_log && g->st->n_substeps <= g->st->m_log_cap) g->st->m_log[g->st->n_substeps - 1] = m;
+    }
+    for (int64_t i = 0; i < D; i++) v[i] = phase * pp[i];
+  }
+  free(d); free(w); free(Kw); free(pp);
+  return rc;
+}
+
+static int gen_alloc(orc_gen *g, const orc_problem *p, orc_stats *st) {
+  memset(g, 0, sizeof(*g));
+  g->p = p;
+  g->st = st;
+  size_t bytes = sizeof(double complex) * (size_t)p->dim;
+  g->u1 = (double complex *)malloc(bytes);
+  g->u2 = (double complex *)malloc(bytes);
+  g->t1 = (double complex *)malloc(bytes);
+  g->t2 = (double complex *)malloc(bytes);
+  if (!g->u1 || !g->u2 || !g->t1 || !g->t2) return ORC_ENOMEM;
+  return ORC_OK;
+}
+
+static void gen_free(orc_gen *g) { free(g->u1); free(g->u2); free(g->t1); free(g->t2); }
+
+static int check_problem(const orc_problem *p) {
+  if (!p) return ORC_EINVAL;
+  for (int k = 0; k < p->nterms; k++) if (!p->term[k].set) return ORC_EINVAL;
+  return ORC_OK;
+}
+
+int orc_expv(const orc_problem *p, const double *beta, double complex *v, orc_stats *st) {
+  int rc = check_problem(p);
+  if (rc) return rc;
+  orc_gen g;
+  rc = gen_alloc(&g, p, st);
+  if (rc == ORC_OK) {
+    g.mode = GEN_LINEAR;
+    for (int k = 0; k < p->nterms; k++) g.beta[k] = beta[k];
+    rc = leja_core(&g, v);
+  }
+  gen_free(&g);
+  return rc;
+}
+
+/* one exponential exp(-i h sum_k (sum_j alpha_j f_k(t_n + c_j h)) H_k) */
+static int cf_exponential(orc_gen *g, const double *alpha, const double *c, int J, double tn, double h,
+                          double complex *psi) {
+  g->mode = GEN_LINEAR;
+  for (int k = 0; k < g->p->nterms; k++) {
+    double s = 0.0;
+    for (int j = 0; j < J; j++) s += alpha[j] * orc_coeff_eval(g->p, k, tn + c[j] * h);
+    g->beta[k] = h * s;
+  }
+  return leja_core(g, psi);
+}
+
+/*
+ * Time stepping, Y_{n+1} = exp(Omega_n) Y_n (Sec. 2, Eq. (9)) with t_n = t0 + n h:
+ *  M2    (Method M2):    Omega = h A(t_n + h/2).
+ *  M4    (Method M4):    one exponential with the commutator (gen_apply).
+ *  CF4   (Method Cf4):   exp(h(a1 A_1 + a2 A_2)) exp(h(a2 A_1 + a1 A_2)) Y_n,
+ *                        c_{1,2} = 1/2 -+ sqrt(3)/6, a_{1,2} = (3 -+ 2 sqrt(3))/12;
+ *                        the right factor acts first.
+ *  CF4_3 (Method Cf4:3): three exponentials with the 3x3 alpha table and
+ *                        c = 1/2 - sqrt(15)/10, 1/2, 1/2 + sqrt(15)/10; the
+ *                        rightmost (third row) acts first.
+ */
+int orc_propagate(const orc_problem *p, double complex *psi, double t0, double h, int64_t nsteps,
+                  int variant, orc_stats *st) {
+  int rc = check_problem(p);
+  if (rc) return rc;
+  if (nsteps < 0) return ORC_EINVAL;
+  orc_gen g;
+  rc = gen_alloc(&g, p, st);
+  const double r3 = sqrt(3.0), r15 = sqrt(15.0);
+  const double c4[2] = {0.5 - r3 / 6.0, 0.5 + r3 / 6.0};
+  const double a1 = (3.0 - 2.0 * r3) / 12.0, a2 = (3.0 + 2.0 * r3) / 12.0;
+  const double c6[3] = {0.5 - r15 / 10.0, 0.5, 0.5 + r15 / 10.0};
+  const double al3[3][3] = {
+      {37.0 / 240.0 - 10.0 * r15 / 261.0, -1.0 / 30.0, 37.0 / 240.0 + 10.0 * r15 / 261.0},
+      {-11.0 / 360.0, 23.0 / 45.0, -11.0 / 360.0},
+      {37.0 / 240.0 + 10.0 * r15 / 261.0, -1.0 / 30.0, 37.0 / 240.0 - 10.0 * r15 / 261.0}};
+  for (int64_t n = 0; n < nsteps && rc == ORC_OK; n++) {
+    const double tn = t0 + (double)n * h;
+    if (variant == ORC_CF4) {
+      const double right[2] = {a2, a1}, left[2] = {a1, a2};
+      rc = cf_exponential(&g, right, c4, 2, tn, h, psi);
+      if (rc == ORC_OK) rc = cf_exponential(&g, left, c4, 2, tn, h, psi);
+    } else if (variant == ORC_M4) {
+      g.mode = GEN_M4;
+      g.h = h;
+      for (int k = 0; k < p->nterms; k++) {
+        g.f1[k] = orc_coeff_eval(p, k, tn + c4[0] * h);
+        g.f2[k] = orc_coeff_eval(p, k, tn + c4[1] * h);
+      }
+      rc = leja_core(&g, psi);
+    } else if (variant == ORC_CF4_3) {
+      for (int r = 2; r >= 0 && rc == ORC_OK; r--) rc = cf_exponential(&g, al3[r], c6, 3, tn, h, psi);
+    } else if (variant == ORC_M2) {
+      const double one = 1.0, half = 0.5;
+      rc = cf_exponential(&g, &one, &half, 1, tn, h, psi);
+    } else {
+      rc = ORC_EINVAL;
+    }
+  }
+  gen_free(&g);
+  return rc;
+}

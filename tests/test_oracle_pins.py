@@ -1,0 +1,351 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Each test ties one oracle function to something other than itself: closed
+forms, a brute-force search, high-precision arithmetic (mpmath), numpy's
+Kronecker products and eigendecompositions, scipy's integrators, and the errors
+printed in the paper's order plot (Sec. 2, Fig. 1).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import magnus_inputs as mi
+
+# ---------------------------------------------------------------------------
+# Pauli matrices and the Kronecker embedding of Sec. 4 (spin 1 leftmost).
+# ---------------------------------------------------------------------------
+SX = np.array([[0, 1], [1, 0]], dtype=complex)
+SY = np.array([[0, -1j], [1j, 0]], dtype=complex)
+SZ = np.array([[1, 0], [0, -1]], dtype=complex)
+
+
+def embed(op, j, n):
+    """sigma_j^alpha = I x ... x op x ... x I, op at position j (1-based)."""
+    out = np.array([[1.0 + 0j]])
+    for i in range(1, n + 1):
+        out = np.kron(out, op if i == j else np.eye(2))
+    return out
+
+
+def kron_xxz(n, J, hz, delta):
+    D = 1 << n
+    H = np.zeros((D, D), dtype=complex)
+    for i in range(1, n):
+        H += J[i - 1] * (embed(SX, i, n) @ embed(SX, i + 1, n) + embed(SY, i, n) @ embed(SY, i + 1, n)
+                         + delta * embed(SZ, i, n) @ embed(SZ, i + 1, n))
+    for i in range(1, n + 1):
+        H += hz[i - 1] * embed(SZ, i, n)
+    return H
+
+
+def kron_field_x(n):
+    return sum(embed(SX, i, n) for i in range(1, n + 1))
+
+
+def kron_longrange(n, hz, alpha, delta):
+    D = 1 << n
+    H = np.zeros((D, D), dtype=complex)
+    for i in range(1, n + 1):
+        for j in range(i + 1, n + 1):
+            Jij = 1.0 / abs(i - j) ** alpha
+            H += Jij * (embed(SX, i, n) @ embed(SX, j, n) + embed(SY, i, n) @ embed(SY, j, n)
+                        + delta * embed(SZ, i, n) @ embed(SZ, j, n))
+        H += hz[i - 1] * embed(SZ, i, n)
+    return H
+
+
+def eig_expm_apply(K, v):
+    lam, U = np.linalg.eigh(K)
+    return U @ (np.exp(-1j * lam) * (U.conj().T @ v))
+
+
+# ---------------------------------------------------------------------------
+# Leja points (Sec. 3)
+# ---------------------------------------------------------------------------
+def test_leja_first_points_closed_form():
+    xi = oracle.leja_points(4)
+    # 2 by choice; -2 maximises |x-2|; 0 maximises |x^2-4|; |x(x^2-4)| peaks at +-2/sqrt(3), tie -> larger x
+    assert xi[0] == 2.0 and xi[1] == -2.0 and xi[2] == 0.0
+    assert abs(xi[3] - 2.0 / np.sqrt(3.0)) < 1e-15
+
+
+def test_leja_points_are_global_maximisers_brute_force():
+    m = 40
+    xi = oracle.leja_points(m)
+    grid = np.linspace(-2.0, 2.0, 400001)
+    for j in range(1, m + 1):
+        lg = np.sum(np.log(np.abs(grid[:, None] - xi[None, :j]) + 1e-300), axis=1)
+        best = lg.max()
+        mine = np.sum(np.log(np.abs(xi[j] - xi[:j])))
+        # the oracle's point attains the brute-force maximum (up to the grid resolution)
+        assert mine >= best - 1e-8, (j, mine, best)
+    assert np.all(np.abs(xi) <= 2.0)
+    assert np.unique(xi).size == xi.size
+
+
+# ---------------------------------------------------------------------------
+# Divided differences d_i = exp[xi_0..xi_i] (Sec. 3)
+# ---------------------------------------------------------------------------
+def test_divided_differences_vs_mpmath():
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 80
+    xi = oracle.leja_points(30)
+    for rho in (0.05, 0.7, 2.5, 4.0):
+        d = oracle.divided_differences(xi, rho)
+        X = [mp.mpf(float(x)) for x in xi]
+        table = [mp.exp(-1j * mp.mpf(rho) * x) for x in X]
+        ref = [table[0]]
+        for k in range(1, len(X)):  # naive recursion, safe at 80 digits
+            table = [(table[i + 1] - table[i]) / (X[i + k] - X[i]) for i in range(len(table) - 1)]
+            ref.append(table[0])
+        ref = np.array([complex(r) for r in ref])
+        assert np.max(np.abs(d - ref)) < 5e-15, rho
+
+
+def _newton_eval(xi, d, x):
+    out = np.zeros_like(x, dtype=complex)
+    basis = np.ones_like(x, dtype=complex)
+    for j in range(d.size):
+        out += d[j] * basis
+        basis *= (x - xi[j])
+    return out
+
+
+def test_divided_differences_interpolate_and_approximate():
+    m = 60
+    xi = oracle.leja_points(m)
+    for rho in (0.3, 2.0, 4.0):
+        d = oracle.divided_differences(xi, rho)
+        # interpolation identity at the nodes (low degree)
+        k = 12
+        pk = _newton_eval(xi[:k + 1], d[:k + 1], xi[:k + 1])
+        assert np.max(np.abs(pk - np.exp(-1j * rho * xi[:k + 1]))) < 1e-12
+        # the full polynomial approximates exp(-i rho x) on [-2,2]
+        x = np.linspace(-2, 2, 10001)
+        assert np.max(np.abs(_newton_eval(xi, d, x) - np.exp(-1j * rho * x))) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# Hamiltonian builders (Sec. 4, Pauli matrices and Kronecker embedding)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [2, 3, 5, 6])
+def test_xxz_and_field_csr_match_kronecker(n):
+    rng = np.random.default_rng(7 + n)
+    J = rng.uniform(0.5, 1.5, n - 1)
+    hz = rng.uniform(-1, 1, n)
+    Hs = oracle.xxz_csr(n, J, hz, 0.5)
+    assert Hs.nnz == (1 << n) * (3 * n + 1) // 2 - (1 << n) * n  # D + (n-1) D/2
+    assert np.max(np.abs(Hs.todense() - kron_xxz(n, J, hz, 0.5))) < 1e-14
+    Hd = oracle.field_x_csr(n)
+    assert np.max(np.abs(Hd.todense() - kron_field_x(n))) == 0.0
+    for H in (Hs, Hd):  # columns sorted within each row
+        for r in range(H.dim):
+            c = H.col[H.rowptr[r]:H.rowptr[r + 1]]
+            assert np.all(np.diff(c) > 0)
+
+
+@pytest.mark.parametrize("n", [2, 4, 6])
+def test_longrange_dense_matches_kronecker(n):
+    hz = np.linspace(-0.9, 0.8, n)
+    H = oracle.longrange_dense(n, hz, alpha=1.5, delta=0.5)
+    assert np.max(np.abs(H - kron_longrange(n, hz, 1.5, 0.5))) < 1e-13
+    assert np.max(np.abs(oracle.field_x_dense(n) - kron_field_x(n))) == 0.0
+
+
+def test_apply_term_and_gershgorin():
+    n = 7
+    c = mi.xxz_chain(11, n, 0.01, 1)
+    Hs = oracle.xxz_csr(n, c.J, c.hz, 0.5)
+    Hd = oracle.field_x_csr(n)
+    P = oracle.Problem([Hs, Hd], [oracle.Coeff.const(), oracle.Coeff(0, [1.0], [], [5.0])])
+    x = c.psi0
+    for k, H in enumerate((Hs, Hd)):
+        Hdn = H.todense()
+        assert np.max(np.abs(P.apply_term(k, x) - Hdn @ x)) < 1e-13
+        a, b = P.interval(k)
+        lam = np.linalg.eigvalsh(Hdn)
+        assert a <= lam.min() + 1e-12 and lam.max() <= b + 1e-12
+    # Gershgorin of sum_i sx_i is exact: its spectrum is {-n, ..., n}
+    assert P.interval(1) == (-float(n), float(n))
+    # coefficient evaluation f(t) = cos(5t)
+    assert abs(P.coeff(1, 0.3) - np.cos(1.5)) < 1e-16 and P.coeff(0, 0.3) == 1.0
+
+
+# ---------------------------------------------------------------------------
+# Action of the exponential (Sec. 3) against eigendecomposition and scipy
+# ---------------------------------------------------------------------------
+def _chain_problem(n, workload=1, tol=1e-10, dense=False, **kw):
+    c = mi.xxz_chain(workload, n, 0.01, 1)
+    Hs = oracle.xxz_csr(n, c.J, c.hz, 0.5)
+    Hd = oracle.field_x_csr(n)
+    if dense:
+        Hs, Hd = Hs.todense(), Hd.todense()
+    P = oracle.Problem([Hs, Hd], [oracle.Coeff.const(), oracle.Coeff(0, [1.0], [], [5.0])], tol=tol, **kw)
+    return c, P, Hs, Hd
+
+
+@pytest.mark.parametrize("beta", [(0.005, 0.003), (0.05, -0.02), (0.6, 0.4), (3.0, -1.5)])
+def test_expv_matches_eigh_dim1024(beta):
+    c, P, Hs, Hd = _chain_problem(10, tol=1e-12)
+    K = beta[0] * Hs.todense() + beta[1] * Hd.todense()
+    ref = eig_expm_apply(K, c.psi0)
+    st = oracle.Stats(64)
+    out = P.expv(np.array(beta), c.psi0, st)
+    assert np.linalg.norm(out - ref) / np.linalg.norm(ref) < 1e-10
+    if beta[0] >= 3.0:
+        assert st.n_substeps > 1  # rho above rho_max splits the polynomial into substeps
+
+
+def test_expv_matches_scipy_expm_multiply():
+    sla = pytest.importorskip("scipy.sparse.linalg")
+    sp = pytest.importorskip("scipy.sparse")
+    n = 12
+    c, P, Hs, Hd = _chain_problem(n, workload=12, tol=1e-12)
+    beta = np.array([0.02, 0.011])
+    K = sp.csr_matrix((Hs.val, Hs.col, Hs.rowptr)) * beta[0] + sp.csr_matrix((Hd.val, Hd.col, Hd.rowptr)) * beta[1]
+    ref = sla.expm_multiply(-1j * K, c.psi0)
+    out = P.expv(beta, c.psi0)
+    assert np.linalg.norm(out - ref) / np.linalg.norm(ref) < 1e-10
+
+
+def test_expv_degenerate_cases():
+    c, P, Hs, Hd = _chain_problem(6)
+    out = P.expv(np.zeros(2), c.psi0)  # K = 0
+    assert np.array_equal(out, c.psi0)
+    D = 64
+    Id = oracle.CSR(np.arange(D + 1), np.arange(D), np.ones(D))  # K = beta * I: a pure phase
+    Q = oracle.Problem([Id], [oracle.Coeff.const()])
+    out = Q.expv(np.array([0.7]), c.psi0)
+    assert np.max(np.abs(out - np.exp(-0.7j) * c.psi0)) < 1e-15
+
+
+def test_expv_reports_no_convergence():
+    c, P, Hs, Hd = _chain_problem(6, m_max=3)
+    with pytest.raises(oracle.OracleError) as e:
+        P.expv(np.array([2.0, 1.0]), c.psi0)
+    assert e.value.code == oracle.ENOCONV
+
+
+def test_csr_and_dense_storage_agree():
+    c, P, Hs, Hd = _chain_problem(8)
+    _, Pd, _, _ = _chain_problem(8, dense=True)
+    a = P.propagate(c.psi0, 0.0, 0.01, 5, "CF4")
+    b = Pd.propagate(c.psi0, 0.0, 0.01, 5, "CF4")
+    assert np.linalg.norm(a - b) < 1e-13
+
+
+# ---------------------------------------------------------------------------
+# Magnus integrators (Sec. 2)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("variant", ["M4", "CF4", "CF4_3", "M2"])
+def test_time_independent_is_exact(variant):
+    """f == 0: every method reduces to exp(-i t H_s) (M4's commutator vanishes)."""
+    n = 8
+    c = mi.xxz_chain(13, n, 0.01, 1)
+    Hs = oracle.xxz_csr(n, c.J, c.hz, 0.5)
+    Hd = oracle.field_x_csr(n)
+    P = oracle.Problem([Hs, Hd], [oracle.Coeff.const(), oracle.Coeff(0.0)], tol=1e-12)
+    out = P.propagate(c.psi0, 0.0, 0.01, 100, variant)
+    ref = eig_expm_apply(Hs.todense() * 1.0, c.psi0)
+    assert np.linalg.norm(out - ref) < 100 * 1e-12
+
+
+@pytest.mark.parametrize("variant", ["M4", "CF4", "CF4_3"])
+def test_commuting_terms_give_gauss_quadrature(variant):
+    """Diagonal H_s, H_d commute: the discrete solution is exp(-i(E_s T + E_d Q)) psi0 with
+    Q the composite Gauss rule of int f (2 nodes for M4/Cf4, 3 nodes for Cf4:3)."""
+    n = 6
+    D = 1 << n
+    rng = np.random.default_rng(3)
+    Es, Ed = rng.uniform(-3, 3, D), rng.uniform(-1, 1, D)
+    Hs = oracle.CSR(np.arange(D + 1), np.arange(D), Es)
+    Hd = oracle.CSR(np.arange(D + 1), np.arange(D), Ed)
+    f = oracle.Coeff(0.0, [1.0], [], [5.0])
+    P = oracle.Problem([Hs, Hd], [oracle.Coeff.const(), f], tol=1e-13)
+    psi0 = mi.random_state(rng, D)
+    h, N = 0.05, 20
+    out = P.propagate(psi0, 0.0, h, N, variant)
+    if variant == "CF4_3":
+        nodes, w = np.polynomial.legendre.leggauss(3)
+    else:
+        nodes, w = np.polynomial.legendre.leggauss(2)
+    Q = sum(h * 0.5 * np.sum(w * np.cos(5 * (n_ * h + h * (nodes + 1) / 2))) for n_ in range(N))
+    T = h * N
+    exact_int = np.sin(5 * T) / 5
+    ref = np.exp(-1j * (Es * T + Ed * Q)) * psi0
+    assert np.linalg.norm(out - ref) < 1e-11
+    # the column sums of the Cf4:3 table are the 3-point Gauss weights (5/18, 8/18, 5/18), so the
+    # discrete solution differs from the exact one only by the quadrature error of int f
+    assert abs(Q - exact_int) < 1e-5
+
+
+def test_norm_conservation():
+    n = 8
+    c = mi.xxz_chain(14, n, 0.01, 100)
+    Hs = oracle.xxz_csr(n, c.J, c.hz, 0.5)
+    Hd = oracle.field_x_csr(n)
+    P = oracle.Problem([Hs, Hd], [oracle.Coeff.const(), oracle.Coeff(0, [1.0], [], [5.0])], tol=1e-13)
+    for variant in ("CF4", "M4"):
+        out = P.propagate(c.psi0, 0.0, 0.01, 100, variant)
+        assert abs(np.linalg.norm(out) - 1.0) < 1e-12, variant
+
+
+def _dop853_reference(Hs, Hd, fcoef, psi0, T):
+    integ = pytest.importorskip("scipy.integrate")
+    Hs_d, Hd_d = Hs.todense(), Hd.todense()
+
+    def rhs(t, y):
+        return -1j * (Hs_d @ y + fcoef(t) * (Hd_d @ y))
+
+    sol = integ.solve_ivp(rhs, (0.0, T), psi0.astype(complex), method="DOP853", rtol=1e-13, atol=1e-15)
+    return sol.y[:, -1]
+
+
+def test_order_four_against_independent_integrator():
+    n = 6
+    c = mi.xxz_chain(15, n, 0.01, 1)
+    Hs = oracle.xxz_csr(n, c.J, c.hz, 0.5)
+    Hd = oracle.field_x_csr(n)
+    f = oracle.Coeff(0, [1.0], [], [5.0])
+    P = oracle.Problem([Hs, Hd], [oracle.Coeff.const(), f], tol=1e-14, tol_abs=1e-14)
+    ref = _dop853_reference(Hs, Hd, f, c.psi0, 1.0)
+    for variant in ("M4", "CF4"):
+        errs = []
+        for N in (8, 16, 32):
+            out = P.propagate(c.psi0, 0.0, 1.0 / N, N, variant)
+            errs.append(np.linalg.norm(out - ref))
+        ratios = [errs[i] / errs[i + 1] for i in range(len(errs) - 1)]
+        assert errs[-1] > 1e-10, errs  # still far above the reference's own error
+        for r in ratios:
+            assert 14.0 < r < 18.5, (variant, errs, ratios)
+
+
+def test_paper_example1_error_ratios():
+    """Example 1 of Sec. 4 at n=10 (Fig. 1): M4 errors shrink ~16x per halving, Cf4 is ~4x more
+    accurate than M4.  The paper's psi0 is not reproducible (random entries), so the check is soft:
+    ratios from the printed plot data, within a factor of 2 for the Cf4/M4 ratio."""
+    gold = np.loadtxt(__file__.replace("test_oracle_pins.py", "golden/fig1_order_example1.txt"))
+    paper_ratio = gold[3, 2] / gold[3, 1]  # tau = 1/16
+    n = 10
+    D = 1 << n
+    # H = -sum_i sum_{j != i} sz_i sz_j / |i-j| - sin(t) sum_i sx_i  (both orders of each pair)
+    x = np.arange(D)
+    z = 1 - 2 * ((x[:, None] >> (n - np.arange(1, n + 1))[None, :]) & 1)
+    diag = np.zeros(D)
+    for i in range(n):
+        for j in range(n):
+            if i != j:
+                diag -= z[:, i] * z[:, j] / abs(i - j)
+    H1 = oracle.CSR(np.arange(D + 1), np.arange(D), diag)
+    Fx = oracle.field_x_csr(n)
+    H2 = oracle.CSR(Fx.rowptr, Fx.col, -Fx.val)
+    f = oracle.Coeff(0, [], [1.0], [1.0])
+    P = oracle.Problem([H1, H2], [oracle.Coeff.const(), f], tol=1e-14, tol_abs=1e-14)
+    psi0 = mi.random_state(np.random.default_rng(16), D)
+    ref = _dop853_reference(H1, H2, f, psi0, 1.0)
+    err = {}
+    for variant in ("M4", "CF4"):
+        err[variant] = [np.linalg.norm(P.propagate(psi0, 0.0, 1.0 / N, N, variant) - ref) for N in (8, 16)]
+    assert 12.0 < err["M4"][0] / err["M4"][1] < 20.0
+    ratio = err["CF4"][1] / err["M4"][1]
+    assert paper_ratio / 2 < ratio < paper_ratio * 2, (ratio, paper_ratio)
