@@ -1,0 +1,218 @@
+/*
+ * magnus.h -- C ABI of the GB300 (sm_103a) Magnus + Leja library.
+ *
+ * Computes the solution of the Schroedinger equation i psi' = H(t) psi with a
+ * time-dependent Hamiltonian H(t) = sum_k f_k(t) H_k (arXiv:1709.06483, Sec. 1,
+ * Eq. (1), and the split H = H_1 + h(t) H_2 of Sec. 4) by fourth-order Magnus
+ * integrators (Sec. 2: Method M4 with its commutator applied matrix-free as
+ * H_2(H_1 psi) - H_1(H_2 psi), and the commutator-free Method Cf4; also Cf4:3 and
+ * the exponential midpoint rule M2), whose exponentials exp(-i K) psi are applied
+ * by Newton-form Leja interpolation (Sec. 3) entirely on one GPU.
+ *
+ * Conventions (all entry points):
+ *  - Every function returns a magnus_status; none aborts, none throws.
+ *  - "device" pointers are CUDA global-memory pointers on the plan's device;
+ *    "host" pointers are ordinary CPU memory.
+ *  - Complex numbers are interleaved (re, im) FP64 pairs (CUDA double2 layout,
+ *    16-byte aligned), passed as void* so this header needs no CUDA include.
+ *  - A state vector psi of a plan with nvec vectors is stored [nvec][dim].
+ *  - Work is issued on the plan's stream.  magnus_propagate and leja_expv
+ *    synchronise that stream before they return, so that their status is final.
+ *  - The plan BORROWS the term matrices (CSR arrays, dense matrices): they must
+ *    stay valid and unchanged while the plan exists.  Coefficient arrays and the
+ *    spin-chain parameters are copied at creation.  The plan owns its scratch.
+ */
+#ifndef MAGNUS_H
+#define MAGNUS_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MAGNUS_API __attribute__((visibility("default")))
+#else
+#define MAGNUS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MAGNUS_OK = 0,
+  MAGNUS_EINVAL = 1,     /* invalid argument; nothing was launched                       */
+  MAGNUS_ENOMEM = 2,     /* device allocation failed                                     */
+  MAGNUS_ECUDA = 3,      /* a CUDA call failed (see magnus_last_error)                   */
+  MAGNUS_ENOCONV = 4,    /* a Leja polynomial reached m_max without meeting the tolerance */
+  MAGNUS_ENONFINITE = 5, /* a norm became NaN or Inf                                     */
+  MAGNUS_ETIMEOUT = 6    /* a device-side wait gave up (bounded spin)                     */
+} magnus_status;
+
+typedef enum {
+  MAGNUS_M4 = 1,   /* Sec. 2, Method M4 (commutator applied matrix-free)        */
+  MAGNUS_CF4 = 2,  /* Sec. 2, Method Cf4 (two exponentials)                     */
+  MAGNUS_CF4_3 = 3,/* Sec. 2, Method Cf4:3 (three exponentials)                 */
+  MAGNUS_M2 = 4    /* Sec. 2, Method M2 (exponential midpoint rule)             */
+} magnus_variant;
+
+typedef enum {
+  MAGNUS_TERM_CSR = 0,     /* complex128 CSR, row-major, int64 row pointers, int32 columns (Sec. 3, CSR) */
+  MAGNUS_TERM_DENSE = 1,   /* complex128 dense dim x dim, row-major                                      */
+  MAGNUS_TERM_XXZ = 2,     /* matrix-free open XXZ chain (Sec. 4, Pauli/Kronecker embedding)              */
+  MAGNUS_TERM_FIELD_X = 3  /* matrix-free transverse field sum_i sigma^x_i                                */
+} magnus_term_kind;
+
+typedef enum {
+  MAGNUS_FP64 = 0,       /* plain FP64 matvecs                                                     */
+  MAGNUS_FP32_SPLIT = 1, /* reserved: FP32 hi/lo split matvecs, FP64 accumulation                  */
+  MAGNUS_TF32_SPLIT = 2  /* reserved: tensor-core split matvecs                                    */
+} magnus_precision;
+
+/*
+ * One stored term H_k.  Spin index convention (MAGNUS_TERM_XXZ / FIELD_X and
+ * the builders below): for n spins, spin j (1-based) is bit (n - j) of the basis
+ * index, i.e. spin 1 is the leftmost Kronecker factor (Sec. 4).
+ *   CSR:     rowptr[dim+1] (device, int64), col[nnz] (device, int32), val[nnz] (device, complex128).
+ *            Rows may list their columns in any order, without duplicates.
+ *   DENSE:   val[dim*dim] (device, complex128, row-major).
+ *   XXZ:     sum_{i=1}^{n-1} J_i (sx_i sx_{i+1} + sy_i sy_{i+1} + delta sz_i sz_{i+1}) + sum_i hz_i sz_i,
+ *            J[n-1], hz[n] on the HOST (copied); dim must be 2^nspins.
+ *   FIELD_X: sum_{i=1}^{n} sx_i; dim must be 2^nspins.
+ * Every term must be Hermitian (the spectral enclosure assumes it).
+ */
+typedef struct {
+  int32_t kind;
+  int32_t nspins;
+  int64_t nnz;
+  const int64_t *rowptr;
+  const int32_t *col;
+  const void *val;
+  const double *J;
+  const double *hz;
+  double delta;
+} magnus_term;
+
+/* f_k(t) = a0 + sum_{m<nmodes} (ac[m] cos(om[m] t) + as[m] sin(om[m] t)); host arrays, copied. */
+typedef struct {
+  double a0;
+  int32_t nmodes;
+  int32_t _pad;
+  const double *ac;
+  const double *as;
+  const double *om;
+} magnus_coeff;
+
+/*
+ * Options; pass NULL for the defaults in brackets.
+ *   tol_rel, tol_abs [1e-10, 1e-10]: Leja early termination (Sec. 4: relative and absolute tolerance 1e-10)
+ *   rho_max [4.0]: largest scaled step gamma/s per Leja polynomial (substepping)
+ *   m_max [100]:  largest Leja degree per substep (at most 255)
+ *   nvec [1]:     number of state vectors propagated together
+ *   ctas [0]:     CTAs of the persistent kernel (0 = automatic)
+ *   precision [MAGNUS_FP64]
+ */
+typedef struct {
+  double tol_rel;
+  double tol_abs;
+  double rho_max;
+  int32_t m_max;
+  int32_t nvec;
+  int32_t ctas;
+  int32_t precision;
+} magnus_options;
+
+typedef struct {
+  int64_t n_exp;        /* exponentials applied                               */
+  int64_t n_substeps;   /* Leja polynomials evaluated                         */
+  int64_t n_matvec;     /* Leja iterations (one application of K each)       */
+  int64_t n_termapply;  /* applications of a single stored term H_k          */
+  int32_t max_m;        /* largest Leja degree used                           */
+  int32_t status;       /* magnus_status of the call                          */
+  int32_t *m_log;       /* optional HOST array: degree of every substep       */
+  int64_t m_log_cap;    /* its capacity (entries)                             */
+} magnus_stats;
+
+typedef struct magnus_plan_s *magnus_plan_t;
+
+/*
+ * Create a plan for dim x dim terms H_0..H_{nterms-1} (nterms <= 4) with
+ * coefficient functions coeffs[k], on the current CUDA device and the given
+ * stream (a cudaStream_t; NULL = the legacy default stream).  Computes on the
+ * device, once: the Leja points on [-2,2] (Sec. 3) and the Gershgorin enclosure
+ * [a_k, b_k] of every term's spectrum (Sec. 3, the spectrum estimate the Leja
+ * parameters need).  Errors: EINVAL (bad sizes, null pointers, dim not 2^nspins
+ * for matrix-free terms), ENOMEM, ECUDA.  *plan is NULL on error.
+ */
+MAGNUS_API magnus_status magnus_plan_create(magnus_plan_t *plan, int64_t dim, int32_t nterms, const magnus_term *terms,
+                                 const magnus_coeff *coeffs, const magnus_options *opt, void *stream);
+
+/* Release the plan and its scratch (after synchronising its stream).  NULL is accepted. */
+MAGNUS_API magnus_status magnus_plan_destroy(magnus_plan_t plan);
+
+/* Human-readable description of the last error of this plan ("" if none); plan may be NULL. */
+MAGNUS_API const char *magnus_last_error(magnus_plan_t plan);
+
+/* Static name of a status code. */
+MAGNUS_API const char *magnus_status_string(magnus_status s);
+
+/*
+ * out = exp(-i sum_k beta[k] H_k) v for every one of the plan's nvec vectors
+ * (Sec. 3, Newton-form Leja interpolation with early termination).
+ * beta: host, nterms reals (the step size is part of beta).
+ * v, out: device complex128 [nvec][dim]; may be the same buffer.
+ * Errors: EINVAL, ENOCONV, ENONFINITE, ETIMEOUT, ECUDA.
+ */
+MAGNUS_API magnus_status leja_expv(magnus_plan_t plan, const double *beta, const void *v, void *out, magnus_stats *stats);
+
+/*
+ * psi <- Y_{n0+nsteps}: nsteps Magnus steps of size h from t0 (Sec. 2, Eq. (9):
+ * Y_{n+1} = exp(Omega_n) Y_n, with t_n = t0 + n h).  psi: device complex128
+ * [nvec][dim], in/out.  variant: magnus_variant.  The whole propagation runs in
+ * one persistent launch; the only host synchronisation is at the end.
+ * Errors: EINVAL, ENOCONV, ENONFINITE, ETIMEOUT, ECUDA.  On error psi holds the
+ * state after the last completed exponential.
+ */
+MAGNUS_API magnus_status magnus_propagate(magnus_plan_t plan, void *psi, double t0, double h, int64_t nsteps,
+                               int32_t variant, magnus_stats *stats);
+
+/* Gershgorin enclosure [*a, *b] of term k (computed at plan creation). */
+MAGNUS_API magnus_status magnus_term_interval(magnus_plan_t plan, int32_t k, double *a, double *b);
+
+/* Copy the plan's m_max+1 Leja points (device-computed) to host xi[]. */
+MAGNUS_API magnus_status magnus_leja_points(magnus_plan_t plan, double *xi, int32_t count);
+
+/*
+ * Divided differences d_j = g[xi_0..xi_j], j = 0..count-1, of g(x) = exp(-i rho x)
+ * at the plan's Leja points (Sec. 3), computed on the device; d: host complex128[count].
+ */
+MAGNUS_API magnus_status magnus_divided_differences(magnus_plan_t plan, double rho, void *d, int32_t count);
+
+/* ---- Hamiltonian builders (device kernels; all pointers device unless noted) ---- */
+
+/* Number of stored entries of the XXZ CSR built below: 2^n + (n-1) 2^(n-1). */
+MAGNUS_API int64_t magnus_xxz_nnz(int32_t nspins);
+
+/*
+ * Open XXZ chain (as MAGNUS_TERM_XXZ) as CSR: per row the diagonal and one entry per
+ * anti-parallel bond (value 2 J_i), columns ascending.  J, hz: HOST.  rowptr[2^n+1],
+ * col[nnz], val[nnz] device.  stream: cudaStream_t or NULL.
+ */
+MAGNUS_API magnus_status magnus_build_xxz_csr(int32_t nspins, const double *J, const double *hz, double delta,
+                                   int64_t *rowptr, int32_t *col, void *val, void *stream);
+
+/* sum_i sigma^x_i as CSR: N entries of value 1 per row, columns ascending; nnz = n 2^n. */
+MAGNUS_API magnus_status magnus_build_field_x_csr(int32_t nspins, int64_t *rowptr, int32_t *col, void *val, void *stream);
+
+/*
+ * Long-range chain, dense: sum_{i<j} (sx_i sx_j + sy_i sy_j + delta sz_i sz_j)/|i-j|^alpha + sum_i hz_i sz_i.
+ * hz: HOST.  H: device complex128 [2^n][2^n].
+ */
+MAGNUS_API magnus_status magnus_build_longrange_dense(int32_t nspins, double alpha, const double *hz, double delta, void *H,
+                                           void *stream);
+
+/* sum_i sigma^x_i, dense. */
+MAGNUS_API magnus_status magnus_build_field_x_dense(int32_t nspins, void *H, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MAGNUS_H */

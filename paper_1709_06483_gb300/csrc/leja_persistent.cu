@@ -1,0 +1,333 @@
+// The hot path: one persistent, cooperative launch runs a whole Magnus propagation
+// (arXiv:1709.06483, Sec. 2, Y_{n+1} = exp(Omega_n) Y_n) with every exponential applied by the
+// Newton-form Leja recurrence of Sec. 3:
+//     w = v, p = d_0 v;   for j = 1..m:  w <- X w - xi_{j-1} w,  p <- p + d_j w,
+// X = (K - cI)/gamma, stopped early once |d_j| ||w_j|| + |d_{j-1}| ||w_{j-1}|| <= tol_abs + tol_rel ||p||.
+// The paper runs this loop on the CPU and only the vector operations on the GPU (Sec. 3); here
+// the loop control stays on the device: each Leja iteration is one fused pass (matvec of every
+// term + shift + Newton update of p + partial norms), followed by one grid barrier after which
+// every block reads the same per-block partial sums in the same order and so takes the same
+// stop decision.  M4 (Sec. 2, Method M4) applies its commutator matrix-free,
+// [H_2, H_1] w = sum_{k<l} coef_kl (H_k (H_l w) - H_l (H_k w)), with one extra barrier between
+// the two term applications.
+#include <math.h>
+
+#include "magnus_internal.cuh"
+
+namespace mg {
+
+namespace {
+
+constexpr int kBlock = 256;
+constexpr int kMaxVec = 64;
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ long long globaltimer_ns() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid-wide barrier with a bounded wait.  Returns false (in every thread of the block) if the
+// wait gave up or another block reported an error; the caller then leaves the kernel.
+__device__ bool grid_barrier(GridBar *bar, unsigned nblocks, long long limit_ns) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned g = ld_acquire_gpu(&bar->gen);
+    __threadfence();
+    const unsigned prev = atomicAdd(&bar->count, 1u);
+    if (prev == nblocks - 1) {
+      atomicExch(&bar->count, 0u);
+      __threadfence();
+      atomicAdd(&bar->gen, 1u);
+    } else {
+      const long long t0 = globaltimer_ns();
+      for (unsigned spin = 0;; spin++) {
+        if (ld_acquire_gpu(&bar->gen) != g) break;
+        if (*(volatile int *)&bar->error) { ok = 0; break; }
+        if ((spin & 31u) == 31u && (globaltimer_ns() - t0 > limit_ns || spin > (1u << 28))) {
+          atomicExch(&bar->error, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(20);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+// ------------------------------------------------------------- one row of H_k x
+// CSR row: sum_e val[e] x[col[e]]; real-valued matrices skip the imaginary products.
+__device__ __forceinline__ double2 csr_row(const Term &t, const double2 *__restrict__ x, int64_t r) {
+  double2 acc = make_double2(0.0, 0.0);
+  const int64_t e0 = __ldg(t.rowptr + r), e1 = __ldg(t.rowptr + r + 1);
+  if (t.real_valued) {
+    for (int64_t e = e0; e < e1; e++) {
+      const double a = __ldg(&t.val[e].x);
+      acc = rfma(a, x[__ldg(t.col + e)], acc);
+    }
+  } else {
+    for (int64_t e = e0; e < e1; e++) acc = cfma(__ldg(t.val + e), x[__ldg(t.col + e)], acc);
+  }
+  return acc;
+}
+
+// Open XXZ chain (Sec. 4 embedding, spin s at bit n-s): diagonal sum delta J_s z_s z_{s+1} + h_s z_s,
+// and 2 J_s to the state with spins s, s+1 swapped when they are anti-parallel.
+__device__ __forceinline__ double2 xxz_row(const Term &t, const double2 *__restrict__ x, int64_t r) {
+  const int n = t.nspins;
+  double diag = 0.0;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int s = 1; s <= n; s++) {
+    const double zs = ((r >> (n - s)) & 1) ? -1.0 : 1.0;
+    diag = fma(t.hz[s - 1], zs, diag);
+    if (s < n) {
+      const bool anti = ((r >> (n - s)) ^ (r >> (n - s - 1))) & 1;
+      diag = fma(t.delta * t.J[s - 1], anti ? -1.0 : 1.0, diag);
+      if (anti) acc = rfma(2.0 * t.J[s - 1], x[r ^ ((int64_t)3 << (n - s - 1))], acc);
+    }
+  }
+  return rfma(diag, x[r], acc);
+}
+
+// sum_i sigma^x_i: the sum over all single-spin flips.
+__device__ __forceinline__ double2 fieldx_row(const Term &t, const double2 *__restrict__ x, int64_t r) {
+  double2 acc = make_double2(0.0, 0.0);
+  for (int b = 0; b < t.nspins; b++) {
+    const double2 v = x[r ^ ((int64_t)1 << b)];
+    acc.x += v.x;
+    acc.y += v.y;
+  }
+  return acc;
+}
+
+__device__ __forceinline__ double2 term_row(const Term &t, const double2 *__restrict__ x, int64_t r) {
+  switch (t.kind) {
+    case MAGNUS_TERM_CSR: return csr_row(t, x, r);
+    case MAGNUS_TERM_XXZ: return xxz_row(t, x, r);
+    case MAGNUS_TERM_FIELD_X: return fieldx_row(t, x, r);
+    default: return make_double2(0.0, 0.0);
+  }
+}
+
+// --------------------------------------------------------------------- kernel
+__global__ void __launch_bounds__(kBlock) k_magnus_persistent(PersistArgs a) {
+  __shared__ Term sT[kMaxTerms];
+  __shared__ ExpRec sR;
+  __shared__ double s_vn[kMaxVec], s_ep[kMaxVec], s_pn[kMaxVec];
+  __shared__ int s_act[kMaxVec], s_m[kMaxVec];
+  __shared__ double s_red[2][kBlock / 32];
+  __shared__ int s_flag;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned G = gridDim.x;
+  const int b = blockIdx.x;
+  const int vec = b / a.gv, chunk = b % a.gv;
+  const int64_t D = a.dim;
+  const int64_t rows_per = (D + a.gv - 1) / a.gv;
+  const int64_t lo = min(D, (int64_t)chunk * rows_per), hi = min(D, lo + rows_per);
+  const int64_t base = (int64_t)vec * D;
+  const int nt = a.nterms, nv = a.nvec;
+
+  for (int i = tid; i < nt * (int)sizeof(Term) / 4; i += blockDim.x)
+    reinterpret_cast<int *>(sT)[i] = reinterpret_cast<const int *>(a.terms)[i];
+  __syncthreads();
+
+  unsigned it = 0;  // slot counter of the partial sums: consecutive reductions alternate slots
+  auto block_reduce_store = [&](double x0, double x1) {
+    x0 = warp_sum(x0);
+    x1 = warp_sum(x1);
+    if (lane == 0) { s_red[0][warp] = x0; s_red[1][warp] = x1; }
+    __syncthreads();
+    if (tid == 0) {
+      double y0 = 0.0, y1 = 0.0;
+      for (int w = 0; w < kBlock / 32; w++) { y0 += s_red[0][w]; y1 += s_red[1][w]; }
+      double *slot = a.partials + (size_t)(it & 1u) * G * 2;
+      slot[2 * b] = y0;
+      slot[2 * b + 1] = y1;
+    }
+  };
+  // totals of vector v from the current slot, identical in every block (fixed order)
+  auto vector_totals = [&](int v, double &t0, double &t1) {
+    const double *slot = a.partials + (size_t)(it & 1u) * G * 2;
+    double y0 = 0.0, y1 = 0.0;
+    for (int q = lane; q < a.gv; q += 32) {
+      y0 += slot[2 * (v * a.gv + q)];
+      y1 += slot[2 * (v * a.gv + q) + 1];
+    }
+    t0 = warp_sum(y0);
+    t1 = warp_sum(y1);
+  };
+  auto fail = [&](int status) {
+    if (tid == 0) atomicCAS(&a.counters->status, 0, status);
+  };
+
+  // ||psi|| of every vector
+  {
+    double s = 0.0;
+    for (int64_t r = lo + tid; r < hi; r += blockDim.x) s += cabs2(a.psi[base + r]);
+    block_reduce_store(s, 0.0);
+    if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { fail(MAGNUS_ETIMEOUT); return; }
+    if (warp == 0)
+      for (int v = 0; v < nv; v++) {
+        double t0, t1;
+        vector_totals(v, t0, t1);
+        if (lane == 0) s_vn[v] = sqrt(t0);
+      }
+    __syncthreads();
+    it++;
+  }
+
+  double2 *cur = a.psi, *nxt = a.alt;
+  long long sub_counter = 0;
+  for (int64_t e = 0; e < a.nexp; e++) {
+    __syncthreads();
+    if (tid == 0) sR = a.recs[e];
+    __syncthreads();
+    const ExpRec &R = sR;
+    const double2 *d = a.dd + e * (int64_t)(a.m_max + 1);
+    if (!(R.gamma > 0.0)) {  // scalar generator: a phase
+      const double2 ph = d[0];
+      for (int64_t r = lo + tid; r < hi; r += blockDim.x) nxt[base + r] = cmul(ph, cur[base + r]);
+      if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { fail(MAGNUS_ETIMEOUT); return; }
+      double2 *tmp = cur; cur = nxt; nxt = tmp;
+      if (b == 0 && tid == 0) a.counters->n_exp++;
+      continue;
+    }
+    const double2 d0 = d[0];
+    for (int sub = 0; sub < R.s; sub++) {
+      if (tid < nv) {
+        s_act[tid] = 1;
+        s_ep[tid] = sqrt(cabs2(d0)) * s_vn[tid];
+        s_m[tid] = 0;
+      }
+      __syncthreads();
+      bool done = false;
+      int j;
+      for (j = 1; j <= a.m_max; j++) {
+        const double2 *src = (j == 1) ? cur : (((j - 2) & 1) ? a.w1 : a.w0);
+        double2 *dst = ((j - 1) & 1) ? a.w1 : a.w0;
+        const double shift = R.cg + a.xi[j - 1];
+        const double2 dj = d[j];
+        const bool mine = s_act[vec] != 0;
+        if (R.mode == MODE_M4) {
+          // phase 1: u_k = H_k w for this block's rows
+          if (mine)
+            for (int64_t r = lo + tid; r < hi; r += blockDim.x)
+              for (int k = 0; k < nt; k++) a.u[((size_t)k * nv) * D + base + r] = term_row(sT[k], src + base, r);
+          if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { fail(MAGNUS_ETIMEOUT); return; }
+        }
+        double sw = 0.0, sp = 0.0;
+        if (mine) {
+          for (int64_t r = lo + tid; r < hi; r += blockDim.x) {
+            double2 y = make_double2(0.0, 0.0);
+            if (R.mode == MODE_M4) {
+              double2 z = make_double2(0.0, 0.0);
+              int pi = 0;
+              for (int k = 0; k < nt; k++) {
+                y = rfma(R.bg[k], a.u[((size_t)k * nv) * D + base + r], y);
+                for (int l = k + 1; l < nt; l++, pi++) {
+                  const double2 hkul = term_row(sT[k], a.u + ((size_t)l * nv) * D + base, r);
+                  const double2 hluk = term_row(sT[l], a.u + ((size_t)k * nv) * D + base, r);
+                  z = rfma(R.kg[pi], make_double2(hkul.x - hluk.x, hkul.y - hluk.y), z);
+                }
+              }
+              y.x += z.y;  // -i z
+              y.y -= z.x;
+            } else {
+              for (int k = 0; k < nt; k++) y = rfma(R.bg[k], term_row(sT[k], src + base, r), y);
+            }
+            const double2 wr = src[base + r];
+            y = rfma(-shift, wr, y);
+            dst[base + r] = y;
+            double2 pr = (j == 1) ? cmul(d0, wr) : nxt[base + r];
+            pr = cfma(dj, y, pr);
+            nxt[base + r] = pr;
+            sw += cabs2(y);
+            sp += cabs2(pr);
+          }
+        }
+        block_reduce_store(sw, sp);
+        if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { fail(MAGNUS_ETIMEOUT); return; }
+        if (warp == 0) {
+          int any = 0, bad = 0;
+          const double adj = sqrt(cabs2(dj));
+          for (int v = 0; v < nv; v++) {
+            if (!s_act[v]) continue;  // uniform across the warp
+            double tw, tp;
+            vector_totals(v, tw, tp);
+            if (lane == 0) {
+              const double ej = adj * sqrt(tw), pn = sqrt(tp);
+              if (!isfinite(ej) || !isfinite(pn)) bad = 1;
+              if (ej + s_ep[v] <= a.tol_abs + a.tol_rel * pn) {
+                s_act[v] = 0;
+                s_m[v] = j;
+                s_pn[v] = pn;
+              } else {
+                s_ep[v] = ej;
+                any = 1;
+              }
+            }
+          }
+          if (lane == 0) s_flag = bad ? 2 : (any ? 0 : 1);
+        }
+        __syncthreads();
+        it++;
+        if (s_flag == 2) { fail(MAGNUS_ENONFINITE); return; }
+        if (s_flag == 1) { done = true; break; }
+      }
+      if (!done) { fail(MAGNUS_ENOCONV); return; }
+      if (tid < nv) s_vn[tid] = s_pn[tid];
+      if (b == 0 && tid == 0) {
+        Counters *c = a.counters;
+        for (int v = 0; v < nv; v++) {
+          const int m = s_m[v];
+          c->n_matvec += m;
+          c->n_termapply += (long long)m * nt * (R.mode == MODE_M4 ? 2 : 1);
+          if (m > c->max_m) c->max_m = m;
+          if (a.mlog && sub_counter * nv + v < a.mlog_cap) a.mlog[sub_counter * nv + v] = m;
+        }
+        c->n_substeps += nv;
+      }
+      __syncthreads();
+      sub_counter++;
+      double2 *tmp = cur; cur = nxt; nxt = tmp;
+    }
+    if (b == 0 && tid == 0) a.counters->n_exp++;
+  }
+  if (cur != a.psi)
+    for (int64_t r = lo + tid; r < hi; r += blockDim.x) a.psi[base + r] = cur[base + r];
+}
+
+}  // namespace
+
+int persistent_block_size() { return kBlock; }
+
+cudaError_t persistent_max_blocks_per_sm(int *n) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_magnus_persistent, kBlock, 0);
+}
+
+cudaError_t launch_persistent(const PersistArgs &a, int grid, int block, cudaStream_t st) {
+  PersistArgs copy = a;
+  void *args[] = {&copy};
+  return cudaLaunchCooperativeKernel((const void *)k_magnus_persistent, dim3(grid), dim3(block), args, 0, st);
+}
+
+}  // namespace mg

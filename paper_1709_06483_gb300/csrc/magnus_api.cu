@@ -1,0 +1,469 @@
+// Host implementation of the C ABI declared in include/magnus.h.  Argument checking, device
+// allocation, and launching the kernels of setup_kernels.cu and leja_persistent.cu; no part of
+// the method's arithmetic runs on the host.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "magnus_internal.cuh"
+
+using namespace mg;
+
+struct magnus_plan_s {
+  int device = 0;
+  int num_sms = 0;
+  int max_blocks_per_sm = 0;
+  cudaStream_t stream = nullptr;
+  int64_t dim = 0;
+  int nterms = 0;
+  magnus_options opt{};
+  Term terms_host[kMaxTerms]{};
+  double term_ab_host[2 * kMaxTerms]{};
+  // device
+  Term *terms = nullptr;
+  Coeff *coeffs = nullptr;
+  double *term_ab = nullptr;
+  double *xi = nullptr;
+  double *cand = nullptr;
+  unsigned *counter = nullptr;
+  GridBar *bar = nullptr;
+  Counters *counters = nullptr;
+  double *partials = nullptr;
+  int partials_cap = 0;
+  double2 *alt = nullptr, *w0 = nullptr, *w1 = nullptr, *u = nullptr;
+  ExpRec *recs = nullptr;
+  double2 *dd = nullptr;
+  int64_t recs_cap = 0;
+  int *mlog = nullptr;
+  int64_t mlog_cap = 0;
+  std::string err;
+};
+
+namespace {
+
+std::string g_global_err;
+
+magnus_status set_err(magnus_plan_t p, magnus_status s, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
+magnus_status set_err(magnus_plan_t p, magnus_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (p) p->err = buf; else g_global_err = buf;
+  return s;
+}
+
+#define CUDA_TRY(plan, expr)                                                                        \
+  do {                                                                                              \
+    cudaError_t e_ = (expr);                                                                        \
+    if (e_ != cudaSuccess) {                                                                        \
+      return set_err(plan, e_ == cudaErrorMemoryAllocation ? MAGNUS_ENOMEM : MAGNUS_ECUDA, "%s: %s", \
+                     #expr, cudaGetErrorString(e_));                                                \
+    }                                                                                               \
+  } while (0)
+
+template <class T>
+cudaError_t dalloc(T **p, size_t count) {
+  return cudaMalloc((void **)p, sizeof(T) * (count ? count : 1));
+}
+
+void free_plan(magnus_plan_t p) {
+  if (!p) return;
+  void *bufs[] = {p->terms, p->coeffs, p->term_ab, p->xi, p->cand, p->counter, p->bar, p->counters, p->partials,
+                  p->alt, p->w0, p->w1, p->u, p->recs, p->dd, p->mlog};
+  for (void *b : bufs)
+    if (b) cudaFree(b);
+  delete p;
+}
+
+bool is_pow2_dim(int64_t dim, int nspins) {
+  return nspins >= 1 && nspins <= kMaxSpins && dim == ((int64_t)1 << nspins);
+}
+
+magnus_status ensure_exp_capacity(magnus_plan_t p, int64_t nexp) {
+  if (nexp <= p->recs_cap) return MAGNUS_OK;
+  if (p->recs) cudaFree(p->recs);
+  if (p->dd) cudaFree(p->dd);
+  p->recs = nullptr;
+  p->dd = nullptr;
+  p->recs_cap = 0;
+  CUDA_TRY(p, dalloc(&p->recs, (size_t)nexp));
+  CUDA_TRY(p, dalloc(&p->dd, (size_t)nexp * (p->opt.m_max + 1)));
+  p->recs_cap = nexp;
+  return MAGNUS_OK;
+}
+
+magnus_status ensure_mlog(magnus_plan_t p, int64_t cap) {
+  if (cap <= p->mlog_cap) return MAGNUS_OK;
+  if (p->mlog) cudaFree(p->mlog);
+  p->mlog = nullptr;
+  p->mlog_cap = 0;
+  CUDA_TRY(p, dalloc(&p->mlog, (size_t)cap));
+  p->mlog_cap = cap;
+  return MAGNUS_OK;
+}
+
+// grid: nvec * gv blocks, all co-resident (cooperative launch)
+void choose_grid(magnus_plan_t p, int *grid, int *gv) {
+  const int maxg = p->num_sms * std::max(1, p->max_blocks_per_sm);
+  const int nv = p->opt.nvec;
+  int per_vec = std::max(1, maxg / nv);
+  if (p->opt.ctas > 0) per_vec = std::max(1, std::min(per_vec, p->opt.ctas / nv));
+  // at least 32 rows per block: smaller slices only add barrier traffic
+  int64_t by_rows = std::max<int64_t>(1, (p->dim + 31) / 32);
+  if (p->opt.ctas <= 0) per_vec = (int)std::min<int64_t>(per_vec, by_rows);
+  *gv = per_vec;
+  *grid = per_vec * nv;
+}
+
+magnus_status run_persistent(magnus_plan_t p, void *psi, int64_t nexp, magnus_stats *stats) {
+  int grid, gv;
+  choose_grid(p, &grid, &gv);
+  if (grid > p->partials_cap) {
+    if (p->partials) cudaFree(p->partials);
+    p->partials = nullptr;
+    p->partials_cap = 0;
+    CUDA_TRY(p, dalloc(&p->partials, (size_t)4 * grid));
+    p->partials_cap = grid;
+  }
+  int64_t want_log = (stats && stats->m_log && stats->m_log_cap > 0) ? stats->m_log_cap : 0;
+  if (want_log) {
+    magnus_status s = ensure_mlog(p, want_log);
+    if (s != MAGNUS_OK) return s;
+  }
+  CUDA_TRY(p, cudaMemsetAsync(p->bar, 0, sizeof(GridBar), p->stream));
+  CUDA_TRY(p, cudaMemsetAsync(p->counters, 0, sizeof(Counters), p->stream));
+  PersistArgs a{};
+  a.dim = p->dim;
+  a.nvec = p->opt.nvec;
+  a.nterms = p->nterms;
+  a.gv = gv;
+  a.m_max = p->opt.m_max;
+  a.nexp = nexp;
+  a.tol_rel = p->opt.tol_rel;
+  a.tol_abs = p->opt.tol_abs;
+  a.terms = p->terms;
+  a.recs = p->recs;
+  a.dd = p->dd;
+  a.xi = p->xi;
+  a.psi = (double2 *)psi;
+  a.alt = p->alt;
+  a.w0 = p->w0;
+  a.w1 = p->w1;
+  a.u = p->u;
+  a.partials = p->partials;
+  a.bar = p->bar;
+  a.counters = p->counters;
+  a.mlog = want_log ? p->mlog : nullptr;
+  a.mlog_cap = want_log;
+  a.spin_limit_ns = 4000000000LL;  // 4 s: far above any legitimate wait at a barrier
+  CUDA_TRY(p, launch_persistent(a, grid, persistent_block_size(), p->stream));
+  Counters c{};
+  CUDA_TRY(p, cudaMemcpyAsync(&c, p->counters, sizeof c, cudaMemcpyDeviceToHost, p->stream));
+  if (want_log) {
+    std::vector<int> tmp((size_t)want_log, 0);
+    CUDA_TRY(p, cudaMemcpyAsync(tmp.data(), p->mlog, sizeof(int) * want_log, cudaMemcpyDeviceToHost, p->stream));
+    CUDA_TRY(p, cudaStreamSynchronize(p->stream));
+    memcpy(stats->m_log, tmp.data(), sizeof(int) * want_log);
+  } else {
+    CUDA_TRY(p, cudaStreamSynchronize(p->stream));
+  }
+  if (stats) {
+    stats->n_exp = c.n_exp;
+    stats->n_substeps = c.n_substeps;
+    stats->n_matvec = c.n_matvec;
+    stats->n_termapply = c.n_termapply;
+    stats->max_m = c.max_m;
+    stats->status = c.status;
+  }
+  if (c.status != MAGNUS_OK) {
+    const char *what = c.status == MAGNUS_ENOCONV      ? "Leja interpolation did not converge within m_max"
+                       : c.status == MAGNUS_ENONFINITE ? "non-finite norm in the Leja iteration"
+                       : c.status == MAGNUS_ETIMEOUT   ? "grid barrier wait timed out"
+                                                       : "device error";
+    return set_err(p, (magnus_status)c.status, "%s", what);
+  }
+  return MAGNUS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *magnus_status_string(magnus_status s) {
+  switch (s) {
+    case MAGNUS_OK: return "MAGNUS_OK";
+    case MAGNUS_EINVAL: return "MAGNUS_EINVAL";
+    case MAGNUS_ENOMEM: return "MAGNUS_ENOMEM";
+    case MAGNUS_ECUDA: return "MAGNUS_ECUDA";
+    case MAGNUS_ENOCONV: return "MAGNUS_ENOCONV";
+    case MAGNUS_ENONFINITE: return "MAGNUS_ENONFINITE";
+    case MAGNUS_ETIMEOUT: return "MAGNUS_ETIMEOUT";
+  }
+  return "MAGNUS_UNKNOWN";
+}
+
+const char *magnus_last_error(magnus_plan_t plan) { return plan ? plan->err.c_str() : g_global_err.c_str(); }
+
+magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms, const magnus_term *terms,
+                                 const magnus_coeff *coeffs, const magnus_options *opt, void *stream) {
+  if (!out) return set_err(nullptr, MAGNUS_EINVAL, "plan pointer is null");
+  *out = nullptr;
+  if (dim < 1 || dim > ((int64_t)1 << 31)) return set_err(nullptr, MAGNUS_EINVAL, "dim %lld out of range", (long long)dim);
+  if (nterms < 1 || nterms > kMaxTerms) return set_err(nullptr, MAGNUS_EINVAL, "nterms must be 1..%d", kMaxTerms);
+  if (!terms || !coeffs) return set_err(nullptr, MAGNUS_EINVAL, "terms/coeffs are null");
+  magnus_options o{1e-10, 1e-10, 4.0, 100, 1, 0, MAGNUS_FP64};
+  if (opt) o = *opt;
+  if (!(o.tol_rel >= 0.0) || !(o.tol_abs >= 0.0) || !(o.tol_rel + o.tol_abs > 0.0))
+    return set_err(nullptr, MAGNUS_EINVAL, "tolerances must be >= 0 and not both 0");
+  if (!(o.rho_max > 0.0)) return set_err(nullptr, MAGNUS_EINVAL, "rho_max must be > 0");
+  if (o.m_max < 2 || o.m_max > kMmaxLimit) return set_err(nullptr, MAGNUS_EINVAL, "m_max must be 2..%d", kMmaxLimit);
+  if (o.nvec < 1 || o.nvec > 64) return set_err(nullptr, MAGNUS_EINVAL, "nvec must be 1..64");
+  if (o.precision != MAGNUS_FP64) return set_err(nullptr, MAGNUS_EINVAL, "only MAGNUS_FP64 is available");
+  for (int k = 0; k < nterms; k++) {
+    const magnus_term &t = terms[k];
+    const magnus_coeff &c = coeffs[k];
+    if (c.nmodes < 0 || c.nmodes > kMaxModes || (c.nmodes > 0 && !c.om))
+      return set_err(nullptr, MAGNUS_EINVAL, "coefficient %d: nmodes must be 0..%d with om given", k, kMaxModes);
+    switch (t.kind) {
+      case MAGNUS_TERM_CSR:
+        if (!t.rowptr || !t.col || !t.val || t.nnz < 0)
+          return set_err(nullptr, MAGNUS_EINVAL, "term %d: CSR arrays missing", k);
+        break;
+      case MAGNUS_TERM_DENSE:
+        return set_err(nullptr, MAGNUS_EINVAL, "term %d: dense terms are not available in this build", k);
+      case MAGNUS_TERM_XXZ:
+        if (!is_pow2_dim(dim, t.nspins) || t.nspins < 2 || !t.J || !t.hz)
+          return set_err(nullptr, MAGNUS_EINVAL, "term %d: XXZ needs dim = 2^nspins, nspins >= 2, J and hz", k);
+        break;
+      case MAGNUS_TERM_FIELD_X:
+        if (!is_pow2_dim(dim, t.nspins)) return set_err(nullptr, MAGNUS_EINVAL, "term %d: FIELD_X needs dim = 2^nspins", k);
+        break;
+      default: return set_err(nullptr, MAGNUS_EINVAL, "term %d: unknown kind %d", k, t.kind);
+    }
+  }
+
+  magnus_plan_t p = new magnus_plan_s();
+  p->stream = (cudaStream_t)stream;
+  p->dim = dim;
+  p->nterms = nterms;
+  p->opt = o;
+  auto fail = [&](magnus_status s) {
+    g_global_err = p->err;
+    free_plan(p);
+    return s;
+  };
+#define PLAN_TRY(expr)                                            \
+  do {                                                            \
+    cudaError_t e_ = (expr);                                      \
+    if (e_ != cudaSuccess) {                                      \
+      set_err(p, e_ == cudaErrorMemoryAllocation ? MAGNUS_ENOMEM : MAGNUS_ECUDA, "%s: %s", #expr, \
+              cudaGetErrorString(e_));                            \
+      return fail(e_ == cudaErrorMemoryAllocation ? MAGNUS_ENOMEM : MAGNUS_ECUDA); \
+    }                                                             \
+  } while (0)
+
+  PLAN_TRY(cudaGetDevice(&p->device));
+  PLAN_TRY(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device));
+  PLAN_TRY(persistent_max_blocks_per_sm(&p->max_blocks_per_sm));
+
+  std::vector<Coeff> ch(nterms);
+  for (int k = 0; k < nterms; k++) {
+    const magnus_term &t = terms[k];
+    Term &T = p->terms_host[k];
+    memset(&T, 0, sizeof T);
+    T.kind = t.kind;
+    T.nspins = t.nspins;
+    T.nnz = t.nnz;
+    T.rowptr = t.rowptr;
+    T.col = t.col;
+    T.val = (const double2 *)t.val;
+    T.delta = t.delta;
+    if (t.kind == MAGNUS_TERM_XXZ) {
+      for (int i = 0; i < t.nspins - 1; i++) T.J[i] = t.J[i];
+      for (int i = 0; i < t.nspins; i++) T.hz[i] = t.hz[i];
+    }
+    Coeff &C = ch[k];
+    memset(&C, 0, sizeof C);
+    C.a0 = coeffs[k].a0;
+    C.nmodes = coeffs[k].nmodes;
+    for (int m = 0; m < C.nmodes; m++) {
+      C.ac[m] = coeffs[k].ac ? coeffs[k].ac[m] : 0.0;
+      C.as[m] = coeffs[k].as ? coeffs[k].as[m] : 0.0;
+      C.om[m] = coeffs[k].om[m];
+    }
+  }
+  const size_t nd = (size_t)dim * o.nvec;
+  PLAN_TRY(dalloc(&p->terms, nterms));
+  PLAN_TRY(dalloc(&p->coeffs, nterms));
+  PLAN_TRY(dalloc(&p->term_ab, 2 * nterms));
+  PLAN_TRY(dalloc(&p->xi, o.m_max + 1));
+  PLAN_TRY(dalloc(&p->cand, 2 * (o.m_max + 1)));
+  PLAN_TRY(dalloc(&p->counter, 1));
+  PLAN_TRY(dalloc(&p->bar, 1));
+  PLAN_TRY(dalloc(&p->counters, 1));
+  PLAN_TRY(dalloc(&p->alt, nd));
+  PLAN_TRY(dalloc(&p->w0, nd));
+  PLAN_TRY(dalloc(&p->w1, nd));
+  PLAN_TRY(dalloc(&p->u, nd * nterms));
+  PLAN_TRY(cudaMemcpyAsync(p->coeffs, ch.data(), sizeof(Coeff) * nterms, cudaMemcpyHostToDevice, p->stream));
+
+  // real-valued CSR values: only the real parts need multiplying
+  int *flag = nullptr;
+  PLAN_TRY(dalloc(&flag, kMaxTerms));
+  PLAN_TRY(cudaMemsetAsync(flag, 0, sizeof(int) * kMaxTerms, p->stream));
+  for (int k = 0; k < nterms; k++)
+    if (p->terms_host[k].kind == MAGNUS_TERM_CSR && p->terms_host[k].nnz > 0)
+      PLAN_TRY(launch_imag_check(p->terms_host[k].val, p->terms_host[k].nnz, flag + k, p->stream));
+  int fh[kMaxTerms] = {0, 0, 0, 0};
+  PLAN_TRY(cudaMemcpyAsync(fh, flag, sizeof fh, cudaMemcpyDeviceToHost, p->stream));
+  PLAN_TRY(cudaStreamSynchronize(p->stream));
+  cudaFree(flag);
+  for (int k = 0; k < nterms; k++) p->terms_host[k].real_valued = (p->terms_host[k].kind == MAGNUS_TERM_CSR) && !fh[k];
+  PLAN_TRY(cudaMemcpyAsync(p->terms, p->terms_host, sizeof(Term) * nterms, cudaMemcpyHostToDevice, p->stream));
+
+  // Gershgorin enclosures (one pass over every term) and the Leja points
+  const int gblk = std::max(1, std::min(p->num_sms * 4, (int)((dim + 255) / 256)));
+  double *gscratch = nullptr;
+  PLAN_TRY(dalloc(&gscratch, 2 * gblk));
+  for (int k = 0; k < nterms; k++)
+    PLAN_TRY(launch_gershgorin(p->terms + k, p->terms_host[k], dim, gscratch, gblk, p->term_ab + 2 * k, p->stream));
+  PLAN_TRY(launch_leja_points(p->xi, o.m_max, p->cand, p->counter, p->stream));
+  PLAN_TRY(cudaMemcpyAsync(p->term_ab_host, p->term_ab, sizeof(double) * 2 * nterms, cudaMemcpyDeviceToHost, p->stream));
+  PLAN_TRY(cudaStreamSynchronize(p->stream));
+  cudaFree(gscratch);
+  for (int k = 0; k < nterms; k++)
+    if (!(p->term_ab_host[2 * k] <= p->term_ab_host[2 * k + 1])) {
+      set_err(p, MAGNUS_EINVAL, "term %d: spectral enclosure is not finite (NaN/Inf in the matrix?)", k);
+      return fail(MAGNUS_EINVAL);
+    }
+#undef PLAN_TRY
+  *out = p;
+  return MAGNUS_OK;
+}
+
+magnus_status magnus_plan_destroy(magnus_plan_t plan) {
+  if (!plan) return MAGNUS_OK;
+  cudaStreamSynchronize(plan->stream);
+  free_plan(plan);
+  return MAGNUS_OK;
+}
+
+magnus_status magnus_propagate(magnus_plan_t p, void *psi, double t0, double h, int64_t nsteps, int32_t variant,
+                               magnus_stats *stats) {
+  if (!p) return set_err(nullptr, MAGNUS_EINVAL, "plan is null");
+  p->err.clear();
+  if (!psi) return set_err(p, MAGNUS_EINVAL, "psi is null");
+  if (((uintptr_t)psi) % 16) return set_err(p, MAGNUS_EINVAL, "psi must be 16-byte aligned");
+  if (nsteps < 0) return set_err(p, MAGNUS_EINVAL, "nsteps < 0");
+  const int per = exps_per_step(variant);
+  if (per == 0) return set_err(p, MAGNUS_EINVAL, "unknown variant %d", variant);
+  if (!(h == h) || !(t0 == t0)) return set_err(p, MAGNUS_EINVAL, "t0/h is NaN");
+  if (stats) {
+    int32_t *log = stats->m_log;
+    int64_t cap = stats->m_log_cap;
+    memset(stats, 0, sizeof *stats);
+    stats->m_log = log;
+    stats->m_log_cap = cap;
+  }
+  if (nsteps == 0) return MAGNUS_OK;
+  const int64_t nexp = nsteps * per;
+  magnus_status s = ensure_exp_capacity(p, nexp);
+  if (s != MAGNUS_OK) return s;
+  CUDA_TRY(p, launch_exp_setup(variant, t0, h, nsteps, p->nterms, p->coeffs, p->term_ab, p->xi, p->opt.m_max,
+                               p->opt.rho_max, p->recs, p->dd, nexp, p->stream));
+  return run_persistent(p, psi, nexp, stats);
+}
+
+magnus_status leja_expv(magnus_plan_t p, const double *beta, const void *v, void *out, magnus_stats *stats) {
+  if (!p) return set_err(nullptr, MAGNUS_EINVAL, "plan is null");
+  p->err.clear();
+  if (!beta || !v || !out) return set_err(p, MAGNUS_EINVAL, "null argument");
+  if (((uintptr_t)v) % 16 || ((uintptr_t)out) % 16) return set_err(p, MAGNUS_EINVAL, "vectors must be 16-byte aligned");
+  for (int k = 0; k < p->nterms; k++)
+    if (!(beta[k] == beta[k]) || beta[k] - beta[k] != 0.0) return set_err(p, MAGNUS_EINVAL, "beta[%d] not finite", k);
+  if (stats) {
+    int32_t *log = stats->m_log;
+    int64_t cap = stats->m_log_cap;
+    memset(stats, 0, sizeof *stats);
+    stats->m_log = log;
+    stats->m_log_cap = cap;
+  }
+  magnus_status s = ensure_exp_capacity(p, 1);
+  if (s != MAGNUS_OK) return s;
+  if (out != v)
+    CUDA_TRY(p, cudaMemcpyAsync(out, v, sizeof(double2) * (size_t)p->dim * p->opt.nvec, cudaMemcpyDeviceToDevice,
+                                p->stream));
+  CUDA_TRY(p, launch_exp_setup_beta(beta, p->nterms, p->term_ab, p->xi, p->opt.m_max, p->opt.rho_max, p->recs, p->dd,
+                                    p->stream));
+  return run_persistent(p, out, 1, stats);
+}
+
+magnus_status magnus_term_interval(magnus_plan_t p, int32_t k, double *a, double *b) {
+  if (!p || !a || !b || k < 0 || k >= p->nterms) return set_err(p, MAGNUS_EINVAL, "bad argument");
+  *a = p->term_ab_host[2 * k];
+  *b = p->term_ab_host[2 * k + 1];
+  return MAGNUS_OK;
+}
+
+magnus_status magnus_leja_points(magnus_plan_t p, double *xi, int32_t count) {
+  if (!p || !xi || count < 1 || count > p->opt.m_max + 1) return set_err(p, MAGNUS_EINVAL, "bad argument");
+  CUDA_TRY(p, cudaMemcpyAsync(xi, p->xi, sizeof(double) * count, cudaMemcpyDeviceToHost, p->stream));
+  CUDA_TRY(p, cudaStreamSynchronize(p->stream));
+  return MAGNUS_OK;
+}
+
+magnus_status magnus_divided_differences(magnus_plan_t p, double rho, void *d, int32_t count) {
+  if (!p || !d || count < 1 || count > p->opt.m_max + 1 || !(rho >= 0.0))
+    return set_err(p, MAGNUS_EINVAL, "bad argument");
+  double2 *dev = nullptr;
+  CUDA_TRY(p, dalloc(&dev, (size_t)count));
+  cudaError_t e = launch_divided_differences(p->xi, count - 1, rho, dev, p->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d, dev, sizeof(double2) * count, cudaMemcpyDeviceToHost, p->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+  cudaFree(dev);
+  if (e != cudaSuccess) return set_err(p, MAGNUS_ECUDA, "divided differences: %s", cudaGetErrorString(e));
+  return MAGNUS_OK;
+}
+
+int64_t magnus_xxz_nnz(int32_t nspins) {
+  if (nspins < 2 || nspins > kMaxSpins) return -1;
+  const int64_t D = (int64_t)1 << nspins;
+  return D + (int64_t)(nspins - 1) * (D / 2);
+}
+
+magnus_status magnus_build_xxz_csr(int32_t nspins, const double *J, const double *hz, double delta, int64_t *rowptr,
+                                   int32_t *col, void *val, void *stream) {
+  if (nspins < 2 || nspins > kMaxSpins || !J || !hz || !rowptr || !col || !val)
+    return set_err(nullptr, MAGNUS_EINVAL, "build_xxz_csr: bad argument");
+  CUDA_TRY(nullptr, launch_build_xxz_csr(nspins, J, hz, delta, rowptr, col, (double2 *)val, (cudaStream_t)stream));
+  return MAGNUS_OK;
+}
+
+magnus_status magnus_build_field_x_csr(int32_t nspins, int64_t *rowptr, int32_t *col, void *val, void *stream) {
+  if (nspins < 1 || nspins > kMaxSpins || !rowptr || !col || !val)
+    return set_err(nullptr, MAGNUS_EINVAL, "build_field_x_csr: bad argument");
+  CUDA_TRY(nullptr, launch_build_field_x_csr(nspins, rowptr, col, (double2 *)val, (cudaStream_t)stream));
+  return MAGNUS_OK;
+}
+
+magnus_status magnus_build_longrange_dense(int32_t nspins, double alpha, const double *hz, double delta, void *H,
+                                           void *stream) {
+  if (nspins < 2 || nspins > 15 || !hz || !H) return set_err(nullptr, MAGNUS_EINVAL, "build_longrange_dense: bad argument");
+  CUDA_TRY(nullptr, launch_build_longrange_dense(nspins, alpha, hz, delta, (double2 *)H, (cudaStream_t)stream));
+  return MAGNUS_OK;
+}
+
+magnus_status magnus_build_field_x_dense(int32_t nspins, void *H, void *stream) {
+  if (nspins < 1 || nspins > 15 || !H) return set_err(nullptr, MAGNUS_EINVAL, "build_field_x_dense: bad argument");
+  CUDA_TRY(nullptr, launch_build_field_x_dense(nspins, (double2 *)H, (cudaStream_t)stream));
+  return MAGNUS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,145 @@
+// Internal declarations of the GB300 Magnus + Leja library (arXiv:1709.06483).
+// Device-side records, small complex helpers and the launch wrappers the host
+// API (magnus_api.cu) calls.  Nothing here is part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "magnus.h"
+
+namespace mg {
+
+constexpr int kMaxTerms = 4;
+constexpr int kMaxPairs = kMaxTerms * (kMaxTerms - 1) / 2;
+constexpr int kMaxModes = 64;
+constexpr int kMaxSpins = 30;
+constexpr int kMmaxLimit = 255;
+
+// One stored term H_k as the kernels see it.
+struct Term {
+  int kind;          // magnus_term_kind
+  int nspins;        // matrix-free terms
+  int real_valued;   // CSR / DENSE: every imaginary part is zero (then only the real parts are multiplied)
+  int _pad;
+  int64_t nnz;
+  const int64_t *rowptr;
+  const int32_t *col;
+  const double2 *val;
+  double J[kMaxSpins];   // XXZ bond couplings J_1..J_{n-1}
+  double hz[kMaxSpins];  // XXZ longitudinal fields h_1..h_n
+  double delta;          // XXZ zz anisotropy
+};
+
+// Drive coefficient f_k(t) = a0 + sum_m (ac_m cos(om_m t) + as_m sin(om_m t)).
+struct Coeff {
+  double a0;
+  int nmodes;
+  int _pad;
+  double ac[kMaxModes], as[kMaxModes], om[kMaxModes];
+};
+
+// Everything one exponential exp(-iK) needs inside the persistent kernel.  K is shifted and
+// scaled to X = (K - cI)/gamma with spectrum in [-2,2]; the stored weights already carry 1/gamma.
+enum { MODE_LINEAR = 0, MODE_M4 = 1 };
+struct ExpRec {
+  double bg[kMaxTerms];  // beta_k / gamma      (linear part: K = sum_k beta_k H_k + ...)
+  double kg[kMaxPairs];  // M4: kappa * coef_kl / gamma, pairs (k<l) in row-major order
+  double cg;             // c / gamma
+  double gamma;          // quarter width of the spectral enclosure (0: K is a scalar)
+  double c;              // centre of the enclosure
+  double a, b;           // the enclosure itself (diagnostics)
+  int s;                 // substeps
+  int mode;              // MODE_LINEAR or MODE_M4
+};
+
+// Sense-reversing grid barrier state (one per plan, zero-initialised).
+struct GridBar {
+  unsigned int count;
+  unsigned int gen;
+  int error;      // set by the first block whose wait timed out
+  int _pad;
+};
+
+struct Counters {
+  long long n_exp, n_substeps, n_matvec, n_termapply;
+  int max_m;
+  int status;
+};
+
+// ---------------------------------------------------------------- complex helpers
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+// acc + a*b
+__host__ __device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 acc) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+  return acc;
+}
+// acc + s*b, s real
+__host__ __device__ __forceinline__ double2 rfma(double s, double2 b, double2 acc) {
+  acc.x = fma(s, b.x, acc.x);
+  acc.y = fma(s, b.y, acc.y);
+  return acc;
+}
+__host__ __device__ __forceinline__ double cabs2(double2 a) { return fma(a.x, a.x, a.y * a.y); }
+
+// ---------------------------------------------------------------- launch wrappers
+// Leja points xi[0..m] on [-2,2] (Sec. 3); scratch: 2*(m+1) doubles + 1 unsigned.
+cudaError_t launch_leja_points(double *xi, int m, double *cand, unsigned *counter, cudaStream_t st);
+// Divided differences of exp(-i rho x) at xi[0..m] (Sec. 3) into d[0..m] (device).
+cudaError_t launch_divided_differences(const double *xi, int m, double rho, double2 *d, cudaStream_t st);
+// Gershgorin enclosure of one term; out[0] = a, out[1] = b (device); scratch: 2*nblk doubles.
+cudaError_t launch_gershgorin(const Term *t_dev, const Term &t_host, int64_t dim, double *scratch, int nblk,
+                              double *out, cudaStream_t st);
+// Real-valuedness check of a CSR / dense term: flag (device int) set to 1 if any imaginary part != 0.
+cudaError_t launch_imag_check(const double2 *val, int64_t n, int *flag, cudaStream_t st);
+// Per-exponential records + divided-difference tables for a whole propagation.
+cudaError_t launch_exp_setup(int variant, double t0, double h, int64_t nsteps, int nterms, const Coeff *coeffs,
+                             const double *term_ab, const double *xi, int m_max, double rho_max, ExpRec *recs,
+                             double2 *dd, int64_t nexp, cudaStream_t st);
+// Records for a single exponential exp(-i sum_k beta_k H_k) (beta on the host).
+cudaError_t launch_exp_setup_beta(const double *beta_host, int nterms, const double *term_ab, const double *xi,
+                                  int m_max, double rho_max, ExpRec *recs, double2 *dd, cudaStream_t st);
+
+int exps_per_step(int variant);
+
+// The persistent propagation kernel (Sec. 3 Leja loop inside Sec. 2 stepping).
+struct PersistArgs {
+  int64_t dim;
+  int nvec, nterms, gv;    // gv: blocks per vector
+  int m_max;
+  int64_t nexp;
+  double tol_rel, tol_abs;
+  const Term *terms;       // device [nterms]
+  const ExpRec *recs;      // device [nexp]
+  const double2 *dd;       // device [nexp][m_max+1]
+  const double *xi;        // device [m_max+1]
+  double2 *psi;            // user buffer (in/out), [nvec][dim]
+  double2 *alt;            // second state buffer
+  double2 *w0, *w1;        // Leja ping-pong vectors
+  double2 *u;              // M4: [nterms][nvec][dim]
+  double *partials;        // [2][grid][2]
+  GridBar *bar;
+  Counters *counters;
+  int *mlog;               // [capacity] degrees of the substeps (may be null)
+  long long mlog_cap;
+  long long spin_limit_ns; // bounded waits
+  int any_m4;
+};
+cudaError_t launch_persistent(const PersistArgs &a, int grid, int block, cudaStream_t st);
+int persistent_block_size();
+cudaError_t persistent_max_blocks_per_sm(int *n);
+
+// Builders.
+cudaError_t launch_build_xxz_csr(int nspins, const double *J, const double *hz, double delta, int64_t *rowptr,
+                                 int32_t *col, double2 *val, cudaStream_t st);
+cudaError_t launch_build_field_x_csr(int nspins, int64_t *rowptr, int32_t *col, double2 *val, cudaStream_t st);
+cudaError_t launch_build_longrange_dense(int nspins, double alpha, const double *hz, double delta, double2 *H,
+                                         cudaStream_t st);
+cudaError_t launch_build_field_x_dense(int nspins, double2 *H, cudaStream_t st);
+
+}  // namespace mg

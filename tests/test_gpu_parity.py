@@ -1,0 +1,236 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle on identical seeded inputs.
+
+Tolerance: relative 2-norm error <= 1e-10 on the state, the Leja-degree sequence equal
+(both sides take the same stop decisions in FP64).  Builders and index work are bit-exact.
+"""
+import numpy as np
+import pytest
+
+import magnus_inputs as mi
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def mg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1709_06483_gb300 as m
+    m.load()
+    return m
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def cuda(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def chain_terms(mg, c, kind):
+    n = c.nspins
+    if kind == "csr":
+        return [mg.build_xxz_csr(n, c.J, c.hz, c.delta), mg.build_field_x_csr(n)]
+    if kind == "mfree":
+        return [mg.XXZTerm(n, c.J, c.hz, c.delta), mg.FieldXTerm(n)]
+    raise ValueError(kind)
+
+
+def drives_gpu(mg, c):
+    return [mg.Drive.const(), mg.Drive(c.drive_a0, c.drive_ac, c.drive_as, c.drive_om)]
+
+
+def oracle_problem(c, tol=1e-10, **kw):
+    Hs = oracle.xxz_csr(c.nspins, c.J, c.hz, c.delta)
+    Hd = oracle.field_x_csr(c.nspins)
+    f = oracle.Coeff(c.drive_a0, c.drive_ac, c.drive_as, c.drive_om)
+    return oracle.Problem([Hs, Hd], [oracle.Coeff.const(), f], tol=tol, **kw)
+
+
+# ----------------------------------------------------------------- tables
+def test_leja_points_match_oracle(mg):
+    c = mi.xxz_chain(1, 6, 0.01, 1)
+    plan = mg.Plan(c.dim, chain_terms(mg, c, "mfree"), drives_gpu(mg, c), m_max=100)
+    xi = plan.leja_points(101)
+    ref = oracle.leja_points(100)
+    assert np.max(np.abs(xi - ref)) < 1e-14
+    assert xi[0] == 2.0 and xi[1] == -2.0 and xi[2] == 0.0
+
+
+@pytest.mark.parametrize("rho", [0.0, 0.05, 0.9, 2.5, 4.0])
+def test_divided_differences_match_oracle(mg, rho):
+    c = mi.xxz_chain(1, 6, 0.01, 1)
+    plan = mg.Plan(c.dim, chain_terms(mg, c, "mfree"), drives_gpu(mg, c), m_max=100)
+    d = plan.divided_differences(rho, 101)
+    ref = oracle.divided_differences(oracle.leja_points(100), rho)
+    assert np.max(np.abs(d - ref)) < 2e-15
+
+
+# ----------------------------------------------------------------- builders, intervals
+@pytest.mark.parametrize("n", [3, 8, 11])
+def test_csr_builders_bit_exact(mg, n):
+    c = mi.xxz_chain(30 + n, n, 0.01, 1)
+    g = mg.build_xxz_csr(n, c.J, c.hz, c.delta)
+    o = oracle.xxz_csr(n, c.J, c.hz, c.delta)
+    assert np.array_equal(g.rowptr.cpu().numpy(), o.rowptr)
+    assert np.array_equal(g.col.cpu().numpy(), o.col)
+    assert np.max(np.abs(g.val.cpu().numpy() - o.val)) < 1e-14
+    gf, of = mg.build_field_x_csr(n), oracle.field_x_csr(n)
+    assert np.array_equal(gf.rowptr.cpu().numpy(), of.rowptr)
+    assert np.array_equal(gf.col.cpu().numpy(), of.col)
+    assert np.array_equal(gf.val.cpu().numpy(), of.val)
+
+
+@pytest.mark.parametrize("n", [4, 7])
+def test_dense_builders(mg, n):
+    hz = np.linspace(-0.7, 0.9, n)
+    g = mg.build_longrange_dense(n, hz, 1.5, 0.5).cpu().numpy()
+    assert np.max(np.abs(g - oracle.longrange_dense(n, hz, 1.5, 0.5))) < 1e-13
+    assert np.array_equal(mg.build_field_x_dense(n).cpu().numpy(), oracle.field_x_dense(n))
+
+
+@pytest.mark.parametrize("kind", ["csr", "mfree"])
+def test_gershgorin_intervals(mg, kind):
+    c = mi.xxz_chain(1, 10, 0.01, 1)
+    plan = mg.Plan(c.dim, chain_terms(mg, c, kind), drives_gpu(mg, c))
+    P = oracle_problem(c)
+    for k in range(2):
+        a, b = plan.interval(k)
+        ra, rb = P.interval(k)
+        assert abs(a - ra) <= 1e-13 * abs(ra) and abs(b - rb) <= 1e-13 * abs(rb)
+
+
+# ----------------------------------------------------------------- expv
+@pytest.mark.parametrize("kind", ["csr", "mfree"])
+@pytest.mark.parametrize("beta", [(0.005, 0.003), (0.05, -0.02), (3.0, -1.5), (0.0, 0.0)])
+def test_expv_parity(mg, kind, beta):
+    c = mi.xxz_chain(1, 10, 0.01, 1)
+    plan = mg.Plan(c.dim, chain_terms(mg, c, kind), drives_gpu(mg, c))
+    out, st = plan.expv(np.array(beta), cuda(c.psi0), log_cap=64)
+    P = oracle_problem(c)
+    ost = oracle.Stats(64)
+    ref = P.expv(np.array(beta), c.psi0, ost)
+    if beta == (0.0, 0.0):
+        assert np.array_equal(out.cpu().numpy(), c.psi0)
+        return
+    assert rel(out.cpu().numpy(), ref) < REL_TOL
+    assert np.array_equal(st["m_log"], ost.m_log)
+
+
+# ----------------------------------------------------------------- propagation, workload 1
+@pytest.mark.parametrize("kind", ["csr", "mfree"])
+@pytest.mark.parametrize("variant", ["CF4", "M4"])
+def test_propagate_workload1(mg, kind, variant):
+    c = mi.workload1()
+    plan = mg.Plan(c.dim, chain_terms(mg, c, kind), drives_gpu(mg, c))
+    psi = cuda(c.psi0)
+    st = plan.propagate(psi, c.t0, c.h, c.nsteps, variant, log_cap=512)
+    ost = oracle.Stats(512)
+    ref = oracle_problem(c).propagate(c.psi0, c.t0, c.h, c.nsteps, variant, ost)
+    assert st["n_exp"] == ost.n_exp and st["n_substeps"] == ost.n_substeps
+    assert np.array_equal(st["m_log"], ost.m_log)
+    assert rel(psi.cpu().numpy(), ref) < REL_TOL
+
+
+@pytest.mark.parametrize("variant", ["CF4_3", "M2"])
+def test_propagate_other_methods(mg, variant):
+    c = mi.xxz_chain(21, 9, 0.02, 30)
+    plan = mg.Plan(c.dim, chain_terms(mg, c, "csr"), drives_gpu(mg, c))
+    psi = cuda(c.psi0)
+    plan.propagate(psi, 0.1, c.h, c.nsteps, variant)
+    ref = oracle_problem(c).propagate(c.psi0, 0.1, c.h, c.nsteps, variant)
+    assert rel(psi.cpu().numpy(), ref) < REL_TOL
+
+
+@pytest.mark.parametrize("ctas", [1, 3, 7, 64])
+def test_ragged_block_partitions(mg, ctas):
+    """Many tiles and a ragged tail: 2^11 rows over ctas blocks of 256 threads."""
+    c = mi.xxz_chain(22, 11, 0.01, 10)
+    for kind in ("csr", "mfree"):
+        plan = mg.Plan(c.dim, chain_terms(mg, c, kind), drives_gpu(mg, c), ctas=ctas)
+        psi = cuda(c.psi0)
+        plan.propagate(psi, 0.0, c.h, c.nsteps, "M4")
+        ref = oracle_problem(c).propagate(c.psi0, 0.0, c.h, c.nsteps, "M4")
+        assert rel(psi.cpu().numpy(), ref) < REL_TOL
+
+
+def test_multiple_vectors(mg):
+    c = mi.xxz_chain(23, 8, 0.01, 20, nvec=5)
+    plan = mg.Plan(c.dim, chain_terms(mg, c, "csr"), drives_gpu(mg, c), nvec=5)
+    psi = cuda(c.psi0)
+    st = plan.propagate(psi, 0.0, c.h, c.nsteps, "CF4", log_cap=4096)
+    P = oracle_problem(c)
+    out = psi.cpu().numpy()
+    for v in range(5):
+        ost = oracle.Stats(4096)
+        ref = P.propagate(c.psi0[v], 0.0, c.h, c.nsteps, "CF4", ost)
+        assert rel(out[v], ref) < REL_TOL
+        assert np.array_equal(st["m_log"].reshape(-1, 5)[:, v], ost.m_log)
+
+
+def test_smallest_chain_and_zero_steps(mg):
+    c = mi.xxz_chain(24, 2, 0.05, 10)
+    plan = mg.Plan(c.dim, chain_terms(mg, c, "csr"), drives_gpu(mg, c))
+    psi = cuda(c.psi0)
+    st = plan.propagate(psi, 0.0, c.h, 0, "CF4")
+    assert st["n_exp"] == 0 and np.array_equal(psi.cpu().numpy(), c.psi0)
+    plan.propagate(psi, 0.0, c.h, c.nsteps, "CF4")
+    ref = oracle_problem(c).propagate(c.psi0, 0.0, c.h, c.nsteps, "CF4")
+    assert rel(psi.cpu().numpy(), ref) < REL_TOL
+
+
+def test_norm_conservation_tight_tolerance(mg):
+    c = mi.xxz_chain(25, 12, 0.01, 100)
+    plan = mg.Plan(c.dim, chain_terms(mg, c, "mfree"), drives_gpu(mg, c), tol=1e-13)
+    psi = cuda(c.psi0)
+    plan.propagate(psi, 0.0, c.h, c.nsteps, "CF4")
+    assert abs(np.linalg.norm(psi.cpu().numpy()) - 1.0) < 1e-12
+
+
+def test_errors_are_reported(mg):
+    c = mi.xxz_chain(26, 8, 0.01, 1)
+    plan = mg.Plan(c.dim, chain_terms(mg, c, "csr"), drives_gpu(mg, c), m_max=3)
+    with pytest.raises(mg.MagnusError) as e:
+        plan.expv(np.array([2.0, 1.0]), cuda(c.psi0))
+    assert e.value.code == mg.ENOCONV
+    with pytest.raises(mg.MagnusError) as e:
+        plan.propagate(cuda(c.psi0), 0.0, 0.01, 1, 99)
+    assert e.value.code == mg.EINVAL
+    with pytest.raises(mg.MagnusError) as e:
+        mg.Plan(1000, [mg.FieldXTerm(10)], [mg.Drive.const()])  # dim is not 2^nspins
+    assert e.value.code == mg.EINVAL
+    # the plan is still usable after an error
+    plan2 = mg.Plan(c.dim, chain_terms(mg, c, "csr"), drives_gpu(mg, c))
+    psi = cuda(c.psi0)
+    plan2.propagate(psi, 0.0, 0.01, 2, "CF4")
+    ref = oracle_problem(c).propagate(c.psi0, 0.0, 0.01, 2, "CF4")
+    assert rel(psi.cpu().numpy(), ref) < REL_TOL
+
+
+# ----------------------------------------------------------------- workload 2 at full size
+@pytest.fixture(scope="module")
+def wl2():
+    c = mi.workload2()
+    return c, oracle_problem(c), {}
+
+
+@pytest.mark.parametrize("kind", ["csr", "mfree"])
+@pytest.mark.parametrize("variant", ["CF4", "M4"])
+def test_workload2_full_size_first_steps(mg, wl2, kind, variant):
+    """20 spins (dim 2^20) in the bench's launch configuration: the first 2 steps against the oracle,
+    every entry compared."""
+    c, P, cache = wl2
+    plan = mg.Plan(c.dim, chain_terms(mg, c, kind), drives_gpu(mg, c))
+    psi = cuda(c.psi0)
+    st = plan.propagate(psi, 0.0, c.h, 2, variant, log_cap=16)
+    if variant not in cache:
+        ost = oracle.Stats(16)
+        cache[variant] = (P.propagate(c.psi0, 0.0, c.h, 2, variant, ost), ost.m_log)
+    ref, mlog = cache[variant]
+    assert np.array_equal(st["m_log"], mlog)
+    assert rel(psi.cpu().numpy(), ref) < REL_TOL
