@@ -129,6 +129,9 @@ typedef struct {
   int32_t status;       /* magnus_status of the call                          */
   int32_t *m_log;       /* optional HOST array: degree of every substep       */
   int64_t m_log_cap;    /* its capacity (entries)                             */
+  double kernel_ms;     /* device time of the persistent Leja kernel (CUDA events on the plan's stream) */
+  int32_t grid;         /* CTAs of that launch                                */
+  int32_t block;        /* threads per CTA                                    */
 } magnus_stats;
 
 typedef struct magnus_plan_s *magnus_plan_t;
@@ -211,6 +214,31 @@ MAGNUS_API magnus_status magnus_build_longrange_dense(int32_t nspins, double alp
 
 /* sum_i sigma^x_i, dense. */
 MAGNUS_API magnus_status magnus_build_field_x_dense(int32_t nspins, void *H, void *stream);
+
+/* ---- allocation-free entry point ---- */
+
+/*
+ * out = exp(-i (beta[0] H_xxz + beta[1] sum_i sigma^x_i)) v for the matrix-free open XXZ chain
+ * (H_xxz as MAGNUS_TERM_XXZ: J[nspins-1], hz[nspins] on the HOST, anisotropy delta), Leja
+ * tolerance tol (relative and absolute), without a plan and without allocating memory.
+ * The paper has no counterpart: this exists for callers that cannot call cudaMalloc -- code whose
+ * device memory is entirely owned by another allocator or pool, or latency-sensitive loops that
+ * must not pay the implicit synchronisation of cudaMalloc/cudaFree.
+ *  - Scratch: one fixed device array of about 3.2 MB inside the library, held by every GPU that
+ *    loads the library until the process exits.  Maximum size: nspins <= 16 (dim <= 65536);
+ *    larger chains return MAGNUS_EINVAL ("nspins must be 2..16").
+ *  - The first call on a device (with that device current) sets the device up: it resolves the
+ *    array's device address and computes the Leja points into it, synchronising `stream`.  Make
+ *    that first call before any stream capture.
+ *  - Every call shares the one array and overwrites it; calls whose GPU work overlaps (other
+ *    streams or threads on the same device) race and give wrong results.  Serialise them.
+ *  - v, out: device complex128 [2^nspins], 16-byte aligned, may alias.  stream: cudaStream_t or
+ *    NULL.  The call synchronises the stream before it returns.
+ *  - Calls no cudaMalloc, cudaFree or other allocating routine.  Error text: magnus_last_error(NULL).
+ */
+MAGNUS_API magnus_status magnus_expv_xxz_static(int32_t nspins, const double *J, const double *hz, double delta,
+                                                const double *beta, const void *v, void *out, double tol,
+                                                void *stream);
 
 #ifdef __cplusplus
 }

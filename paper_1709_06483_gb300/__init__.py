@@ -28,7 +28,7 @@ EXPORTS = (
     "magnus_plan_create", "magnus_plan_destroy", "magnus_last_error", "magnus_status_string", "leja_expv",
     "magnus_propagate", "magnus_term_interval", "magnus_leja_points", "magnus_divided_differences",
     "magnus_xxz_nnz", "magnus_build_xxz_csr", "magnus_build_field_x_csr", "magnus_build_longrange_dense",
-    "magnus_build_field_x_dense",
+    "magnus_build_field_x_dense", "magnus_expv_xxz_static",
 )
 
 
@@ -57,7 +57,8 @@ class Options(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("n_exp", C.c_int64), ("n_substeps", C.c_int64), ("n_matvec", C.c_int64),
                 ("n_termapply", C.c_int64), ("max_m", C.c_int32), ("status", C.c_int32),
-                ("m_log", C.POINTER(C.c_int32)), ("m_log_cap", C.c_int64)]
+                ("m_log", C.POINTER(C.c_int32)), ("m_log_cap", C.c_int64), ("kernel_ms", C.c_double),
+                ("grid", C.c_int32), ("block", C.c_int32)]
 
 
 _lib = None
@@ -82,6 +83,7 @@ def _declare(L):
         "magnus_build_field_x_csr": (I32, [I32, P, P, P, P]),
         "magnus_build_longrange_dense": (I32, [I32, D, C.POINTER(D), D, P, P]),
         "magnus_build_field_x_dense": (I32, [I32, P, P]),
+        "magnus_expv_xxz_static": (I32, [I32, C.POINTER(D), C.POINTER(D), D, C.POINTER(D), P, P, D, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -285,7 +287,8 @@ class Plan:
 
 
 def _as_dict(st: Stats, log):
-    out = {k: getattr(st, k) for k in ("n_exp", "n_substeps", "n_matvec", "n_termapply", "max_m", "status")}
+    out = {k: getattr(st, k) for k in ("n_exp", "n_substeps", "n_matvec", "n_termapply", "max_m", "status",
+                                       "kernel_ms", "grid", "block")}
     if log is not None:
         out["m_log"] = log[: min(st.n_substeps, log.size)].copy()
     return out
@@ -338,3 +341,20 @@ def build_field_x_dense(nspins, device="cuda", stream=None):
     H = torch.empty((D, D), dtype=torch.complex128, device=device)
     _check(load().magnus_build_field_x_dense(nspins, C.c_void_p(_dptr(H)), _stream_ptr(stream)))
     return H
+
+
+# ------------------------------------------------------------------ allocation-free entry point
+def expv_xxz_static(nspins, J, hz, delta, beta, v, out=None, tol=1e-10, stream=None):
+    """out = exp(-i (beta_0 H_xxz + beta_1 sum_i sx_i)) v without a plan and without any device allocation
+    inside the library (fixed ~3.2 MB scratch, nspins <= 16).  For callers that cannot call cudaMalloc.
+    The first call on a device does a one-time set-up; calls that overlap on the GPU race."""
+    import torch
+    if out is None:
+        out = torch.empty_like(v)
+    J, hz, b = _f64(J), _f64(hz), _f64(beta)
+    assert b.size == 2
+    P = C.POINTER(C.c_double)
+    _check(load().magnus_expv_xxz_static(int(nspins), J.ctypes.data_as(P), hz.ctypes.data_as(P), float(delta),
+                                         b.ctypes.data_as(P), C.c_void_p(_dptr(v)), C.c_void_p(_dptr(out)),
+                                         float(tol), _stream_ptr(stream)))
+    return out

@@ -41,6 +41,7 @@ struct magnus_plan_s {
   int64_t recs_cap = 0;
   int *mlog = nullptr;
   int64_t mlog_cap = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::string err;
 };
 
@@ -79,6 +80,8 @@ void free_plan(magnus_plan_t p) {
                   p->alt, p->w0, p->w1, p->u, p->recs, p->dd, p->mlog};
   for (void *b : bufs)
     if (b) cudaFree(b);
+  if (p->ev0) cudaEventDestroy(p->ev0);
+  if (p->ev1) cudaEventDestroy(p->ev1);
   delete p;
 }
 
@@ -163,7 +166,9 @@ magnus_status run_persistent(magnus_plan_t p, void *psi, int64_t nexp, magnus_st
   a.mlog = want_log ? p->mlog : nullptr;
   a.mlog_cap = want_log;
   a.spin_limit_ns = 4000000000LL;  // 4 s: far above any legitimate wait at a barrier
+  CUDA_TRY(p, cudaEventRecord(p->ev0, p->stream));
   CUDA_TRY(p, launch_persistent(a, grid, persistent_block_size(), p->stream));
+  CUDA_TRY(p, cudaEventRecord(p->ev1, p->stream));
   Counters c{};
   CUDA_TRY(p, cudaMemcpyAsync(&c, p->counters, sizeof c, cudaMemcpyDeviceToHost, p->stream));
   if (want_log) {
@@ -181,6 +186,11 @@ magnus_status run_persistent(magnus_plan_t p, void *psi, int64_t nexp, magnus_st
     stats->n_termapply = c.n_termapply;
     stats->max_m = c.max_m;
     stats->status = c.status;
+    float ms = 0.f;
+    CUDA_TRY(p, cudaEventElapsedTime(&ms, p->ev0, p->ev1));
+    stats->kernel_ms = ms;
+    stats->grid = grid;
+    stats->block = persistent_block_size();
   }
   if (c.status != MAGNUS_OK) {
     const char *what = c.status == MAGNUS_ENOCONV      ? "Leja interpolation did not converge within m_max"
@@ -193,6 +203,11 @@ magnus_status run_persistent(magnus_plan_t p, void *psi, int64_t nexp, magnus_st
 }
 
 }  // namespace
+
+namespace mg {
+// Error text of the entry points that take no plan (read back with magnus_last_error(NULL)).
+void noalloc_set_error(const char *msg) { g_global_err = msg; }
+}  // namespace mg
 
 extern "C" {
 
@@ -272,6 +287,8 @@ magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms
   PLAN_TRY(cudaGetDevice(&p->device));
   PLAN_TRY(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device));
   PLAN_TRY(persistent_max_blocks_per_sm(&p->max_blocks_per_sm));
+  PLAN_TRY(cudaEventCreate(&p->ev0));
+  PLAN_TRY(cudaEventCreate(&p->ev1));
 
   std::vector<Coeff> ch(nterms);
   for (int k = 0; k < nterms; k++) {
