@@ -63,28 +63,34 @@ def drives(mg, c):
 
 
 def algorithmic_per_iteration(c, storage, variant, nnz_total):
-    """Bytes and FP64 flops one Leja iteration needs (real-valued Hamiltonian, complex state).
+    """Bytes and FP64 work one Leja iteration needs (real-valued Hamiltonian, complex state).
 
-    CSR: per stored entry 16 B value + 4 B column, per row 8 B row pointer (two terms: 2 x), plus
-    16 B read of w_{j-1}, 16 B write of w_j, 16+16 B read+write of p per row.  Matrix-free: only the
-    vector traffic.  Flops: 4 per stored entry (real x complex multiply-add), 26 per row for the
-    combination, shift, Newton update and the two squared norms.
-    M4 applies every term twice and keeps two extra vectors (u_k written once, read in the second
-    pass)."""
+    Bytes, CSR: per stored entry 16 B value + 4 B column, per row 8 B row pointer per term, plus per
+    row 16 B read of w_{j-1}, 16 B write of w_j and 16 + 16 B read and write of p; matrix-free: the
+    vector traffic only.  M4 applies every term twice and writes and reads back u_k (2 x 32 B/row).
+
+    FP64 work is counted in FMA-equivalent flops: every FP64 instruction the method needs (add,
+    multiply or fused multiply-add) counts 2, because on GB300 each occupies one slot of the FP64
+    pipe (2 per clock per SM, peak 152 x 2 x 2 x 2070 MHz = 1.259 TFLOP/s).  Per row: CSR needs 2
+    instructions per stored entry; the matrix-free XXZ row needs 4 for the diagonal, 2 per active
+    bond ((n-1)/2 on average) and 2 n for the field sum plus 2 to weight it; both need 4 for the
+    weighted combination (CSR) or none extra (matrix-free), 2 for the shift, 4 for the Newton update
+    of p and 4 for the two squared norms."""
     D = c.dim
     passes = 2 if variant == "M4" else 1
     vec_bytes = 64 * D
     if variant == "M4":
-        vec_bytes += 2 * 16 * D * 2  # u_s, u_d written and read back
+        vec_bytes += 2 * 16 * D * 2
     if storage == "csr":
         mat = 20 * nnz_total + 2 * 8 * (D + 1)
-        flops = passes * 4 * nnz_total + 26 * D
+        inst = passes * 2 * nnz_total + (4 + 2 + 4 + 4) * D
     else:
         n = c.nspins
         mat = 0
-        # per row: (n-1)/2 active bond flips (4 flops) + diagonal (~4n) + n field adds (2 flops each)
-        flops = passes * D * (2 * (n - 1) + 4 * n + 2 * n) + 26 * D
-    return passes * mat + vec_bytes, flops
+        inst = passes * D * (4 + (n - 1) + 2 * n + 2) + (2 + 4 + 4) * D
+    if variant == "M4":
+        inst += 8 * D  # commutator difference and its weight
+    return passes * mat + vec_bytes, 2 * inst
 
 
 class ClockSampler:
@@ -216,7 +222,7 @@ def run_ours(args):
                  "algorithmic_bytes_per_iteration": bytes_it, "algorithmic_flops_per_iteration": flops_it,
                  "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 4),
                  "fp64_tflops": round(tflops, 4), "fp64_frac": round(tflops / FP64_PEAK_TFLOPS, 4),
-                 "peak_source": "hbm: MEASURED_PEAKS.json copy; fp64: 152 SMs x 2 FMA/clk x 2 flops x 2070 MHz"})
+                 "peak_source": "hbm: MEASURED_PEAKS.json copy; fp64: 152 SMs x 2 FP64 instructions/clk x 2 flops x 2070 MHz (FMA-equivalent flops)"})
 
     # end-to-end through the public API with host buffers: H2D of psi, one step, D2H of psi
     host_in = torch.from_numpy(c.psi0).pin_memory()

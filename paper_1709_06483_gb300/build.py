@@ -41,8 +41,13 @@ def _stale(out: str, deps: list[str]) -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
+    """Compile csrc/*.cu for sm_103a and link libmagnus_gb300.so.  MAGNUS_NVCC_EXTRA (space-separated)
+    appends tuning defines, e.g. -DMG_PERSIST_MIN_BLOCKS=3."""
     os.makedirs(BUILD, exist_ok=True)
+    extra = list(extra or []) + os.environ.get("MAGNUS_NVCC_EXTRA", "").split()
     headers = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
+    if extra:
+        force = True
     srcs = sources()
     objs = []
     jobs = []
@@ -50,7 +55,7 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
         o = os.path.join(BUILD, os.path.basename(s) + ".o")
         objs.append(o)
         if force or _stale(o, [s] + headers):
-            cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *(extra or []), "-c", s, "-o", o]
+            cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *extra, "-c", s, "-o", o]
             jobs.append(cmd)
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 4))) as ex:
         for cmd, res in zip(jobs, ex.map(lambda c: subprocess.run(c, capture_output=True, text=True), jobs)):

@@ -10,6 +10,15 @@
 // stop decision.  M4 (Sec. 2, Method M4) applies its commutator matrix-free,
 // [H_2, H_1] w = sum_{k<l} coef_kl (H_k (H_l w) - H_l (H_k w)), with one extra barrier between
 // the two term applications.
+//
+// On GB300 the FP64 pipe (2 FMA/clk/SM) is the tighter limit for these matvecs, so the kernel is
+// specialised at compile time per operator family to keep the FP64 instruction count per row
+// minimal and many independent loads in flight:
+//   FAM_CSR     every term CSR (real-valued values multiply only the real parts);
+//   FAM_MF      matrix-free XXZ chain + transverse field, diagonal from two small tables;
+//   FAM_GENERIC any mix of CSR and matrix-free terms.
+// Vectors written by other blocks between barriers are read with ordinary (coherent, L1-cached)
+// loads; only the immutable matrices use the read-only path.
 #include <math.h>
 
 #include "magnus_internal.cuh"
@@ -19,6 +28,10 @@ namespace mg {
 namespace {
 
 constexpr int kBlock = 256;
+#ifndef MG_PERSIST_MIN_BLOCKS
+#define MG_PERSIST_MIN_BLOCKS 3
+#endif
+constexpr int kMinBlocks = MG_PERSIST_MIN_BLOCKS;  // resident CTAs per SM the register budget targets
 constexpr int kMaxVec = 64;
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -32,6 +45,8 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
+// Coherent load of a vector entry that other blocks may have written before the last barrier.
+__device__ __forceinline__ double2 ldv(const double2 *p) { return __ldca(p); }
 
 // Grid-wide barrier with a bounded wait.  Returns false (in every thread of the block) if the
 // wait gave up or another block reported an error; the caller then leaves the kernel.
@@ -73,25 +88,63 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// ------------------------------------------------------------- one row of H_k x
-// CSR row: sum_e val[e] x[col[e]]; real-valued matrices skip the imaginary products.
-__device__ __forceinline__ double2 csr_row(const Term &t, const double2 *__restrict__ x, int64_t r) {
+// ------------------------------------------------------------- rows of H_k x
+// CSR row: sum_e val[e] x[col[e]].  Entries go in rounds of eight (real values) or four (complex)
+// so that the column/value loads and the gathers of a whole round are in flight together.
+__device__ __forceinline__ double2 csr_row(const Term &t, const double2 *x, int64_t r) {
   double2 acc = make_double2(0.0, 0.0);
-  const int64_t e0 = __ldg(t.rowptr + r), e1 = __ldg(t.rowptr + r + 1);
+  int64_t e = __ldg(t.rowptr + r);
+  const int64_t e1 = __ldg(t.rowptr + r + 1);
   if (t.real_valued) {
-    for (int64_t e = e0; e < e1; e++) {
-      const double a = __ldg(&t.val[e].x);
-      acc = rfma(a, x[__ldg(t.col + e)], acc);
+    for (; e + 8 <= e1; e += 8) {
+      int c[8];
+      double a[8];
+      double2 xv[8];
+#pragma unroll
+      for (int q = 0; q < 8; q++) c[q] = __ldg(t.col + e + q);
+#pragma unroll
+      for (int q = 0; q < 8; q++) a[q] = __ldg(&t.val[e + q].x);
+#pragma unroll
+      for (int q = 0; q < 8; q++) xv[q] = ldv(x + c[q]);
+#pragma unroll
+      for (int q = 0; q < 8; q++) acc = rfma(a[q], xv[q], acc);
     }
+    if (e + 4 <= e1) {
+      int c[4];
+      double a[4];
+      double2 xv[4];
+#pragma unroll
+      for (int q = 0; q < 4; q++) c[q] = __ldg(t.col + e + q);
+#pragma unroll
+      for (int q = 0; q < 4; q++) a[q] = __ldg(&t.val[e + q].x);
+#pragma unroll
+      for (int q = 0; q < 4; q++) xv[q] = ldv(x + c[q]);
+#pragma unroll
+      for (int q = 0; q < 4; q++) acc = rfma(a[q], xv[q], acc);
+      e += 4;
+    }
+    for (; e < e1; e++) acc = rfma(__ldg(&t.val[e].x), ldv(x + __ldg(t.col + e)), acc);
   } else {
-    for (int64_t e = e0; e < e1; e++) acc = cfma(__ldg(t.val + e), x[__ldg(t.col + e)], acc);
+    for (; e + 4 <= e1; e += 4) {
+      int c[4];
+      double2 a[4], xv[4];
+#pragma unroll
+      for (int q = 0; q < 4; q++) c[q] = __ldg(t.col + e + q);
+#pragma unroll
+      for (int q = 0; q < 4; q++) a[q] = __ldg(t.val + e + q);
+#pragma unroll
+      for (int q = 0; q < 4; q++) xv[q] = ldv(x + c[q]);
+#pragma unroll
+      for (int q = 0; q < 4; q++) acc = cfma(a[q], xv[q], acc);
+    }
+    for (; e < e1; e++) acc = cfma(__ldg(t.val + e), ldv(x + __ldg(t.col + e)), acc);
   }
   return acc;
 }
 
 // Open XXZ chain (Sec. 4 embedding, spin s at bit n-s): diagonal sum delta J_s z_s z_{s+1} + h_s z_s,
 // and 2 J_s to the state with spins s, s+1 swapped when they are anti-parallel.
-__device__ __forceinline__ double2 xxz_row(const Term &t, const double2 *__restrict__ x, int64_t r) {
+__device__ __forceinline__ double2 xxz_row(const Term &t, const double2 *x, int64_t r) {
   const int n = t.nspins;
   double diag = 0.0;
   double2 acc = make_double2(0.0, 0.0);
@@ -101,36 +154,112 @@ __device__ __forceinline__ double2 xxz_row(const Term &t, const double2 *__restr
     if (s < n) {
       const bool anti = ((r >> (n - s)) ^ (r >> (n - s - 1))) & 1;
       diag = fma(t.delta * t.J[s - 1], anti ? -1.0 : 1.0, diag);
-      if (anti) acc = rfma(2.0 * t.J[s - 1], x[r ^ ((int64_t)3 << (n - s - 1))], acc);
+      if (anti) acc = rfma(2.0 * t.J[s - 1], ldv(x + (r ^ ((int64_t)3 << (n - s - 1)))), acc);
     }
   }
-  return rfma(diag, x[r], acc);
+  return rfma(diag, ldv(x + r), acc);
 }
 
-// sum_i sigma^x_i: the sum over all single-spin flips.
-__device__ __forceinline__ double2 fieldx_row(const Term &t, const double2 *__restrict__ x, int64_t r) {
+// sum_i sigma^x_i: the sum over all single-spin flips (all loads issued before the adds).
+__device__ __forceinline__ double2 fieldx_row(int n, const double2 *x, int64_t r) {
   double2 acc = make_double2(0.0, 0.0);
-  for (int b = 0; b < t.nspins; b++) {
-    const double2 v = x[r ^ ((int64_t)1 << b)];
+  int b = 0;
+  for (; b + 4 <= n; b += 4) {
+    const double2 v0 = ldv(x + (r ^ ((int64_t)1 << b))), v1 = ldv(x + (r ^ ((int64_t)2 << b))),
+                  v2 = ldv(x + (r ^ ((int64_t)4 << b))), v3 = ldv(x + (r ^ ((int64_t)8 << b)));
+    acc.x += (v0.x + v1.x) + (v2.x + v3.x);
+    acc.y += (v0.y + v1.y) + (v2.y + v3.y);
+  }
+  for (; b < n; b++) {
+    const double2 v = ldv(x + (r ^ ((int64_t)1 << b)));
     acc.x += v.x;
     acc.y += v.y;
   }
   return acc;
 }
 
-__device__ __forceinline__ double2 term_row(const Term &t, const double2 *__restrict__ x, int64_t r) {
+__device__ __forceinline__ double2 term_row_generic(const Term &t, const double2 *x, int64_t r) {
   switch (t.kind) {
     case MAGNUS_TERM_CSR: return csr_row(t, x, r);
     case MAGNUS_TERM_XXZ: return xxz_row(t, x, r);
-    case MAGNUS_TERM_FIELD_X: return fieldx_row(t, x, r);
+    case MAGNUS_TERM_FIELD_X: return fieldx_row(t.nspins, x, r);
     default: return make_double2(0.0, 0.0);
   }
 }
 
+// Per-block operator context: terms in shared memory plus, for FAM_MF, the diagonal tables and
+// the bond couplings pre-scaled by the current exponential's weight.
+struct Ctx {
+  const Term *T;
+  int nt;
+  int n, lbits;
+  int64_t lomask;
+  const double *dlo, *dhi;
+  const double *jb;   // shared: 2 J_bond * bg[0] per bond, bond at bits (p, p-1) stored at p-1
+  const double *j2;   // shared: 2 J_bond (unscaled), same indexing
+};
+
+// H_xxz row with the diagonal from the two tables (FAM_MF).  coefj: per-bond coefficients.
+// Every bond's partner entry is loaded whether or not the bond is active (all loads in flight at
+// once); only the multiply-add depends on the spins.
+constexpr int kMaxBonds = kMaxSpins - 1;
+__device__ __forceinline__ double2 mf_xxz_row(const Ctx &c, const double *coefj, double dscale, double dshift,
+                                              const double2 *x, int64_t r, double2 &xr) {
+  xr = ldv(x + r);
+  const double dg = __ldg(c.dhi + (r >> c.lbits)) + __ldg(c.dlo + (r & c.lomask));
+  const double cr = fma(dscale, dg, -dshift);
+  double2 acc;
+  acc.x = cr * xr.x;
+  acc.y = cr * xr.y;
+  const int nb = c.n - 1;
+  for (int p0 = 0; p0 < nb; p0 += 4) {
+    double2 v[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) v[q] = ldv(x + (r ^ ((int64_t)3 << min(p0 + q, nb - 1))));
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int p = p0 + q + 1;  // bond at bits (p, p-1)
+      if (p <= nb && (((r >> p) ^ (r >> (p - 1))) & 1)) acc = rfma(coefj[p - 1], v[q], acc);
+    }
+  }
+  return acc;
+}
+
+template <int FAM>
+struct Op {
+  // (H_k x)[r]
+  __device__ static __forceinline__ double2 term(const Ctx &c, int k, const double2 *x, int64_t r) {
+    if (FAM == FAM_CSR) return csr_row(c.T[k], x, r);
+    if (FAM == FAM_MF) {
+      if (k == 0) {
+        double2 xr;
+        return mf_xxz_row(c, c.j2, 1.0, 0.0, x, r, xr);
+      }
+      return fieldx_row(c.n, x, r);
+    }
+    return term_row_generic(c.T[k], x, r);
+  }
+  // sum_k bg_k (H_k x)[r] - shift x[r]; also returns x[r]
+  __device__ static __forceinline__ double2 combo(const Ctx &c, const ExpRec &R, double shift, const double2 *x,
+                                                  int64_t r, double2 &xr) {
+    if (FAM == FAM_MF) {
+      double2 y = mf_xxz_row(c, c.jb, R.bg[0], shift, x, r, xr);
+      const double2 f = fieldx_row(c.n, x, r);
+      return rfma(R.bg[1], f, y);
+    }
+    double2 y = make_double2(0.0, 0.0);
+    for (int k = 0; k < c.nt; k++) y = rfma(R.bg[k], term(c, k, x, r), y);
+    xr = ldv(x + r);
+    return rfma(-shift, xr, y);
+  }
+};
+
 // --------------------------------------------------------------------- kernel
-__global__ void __launch_bounds__(kBlock) k_magnus_persistent(PersistArgs a) {
+template <int FAM>
+__global__ void __launch_bounds__(kBlock, kMinBlocks) k_magnus_persistent(PersistArgs a) {
   __shared__ Term sT[kMaxTerms];
   __shared__ ExpRec sR;
+  __shared__ double s_jb[kMaxSpins], s_j2[kMaxSpins];
   __shared__ double s_vn[kMaxVec], s_ep[kMaxVec], s_pn[kMaxVec];
   __shared__ int s_act[kMaxVec], s_m[kMaxVec];
   __shared__ double s_red[2][kBlock / 32];
@@ -141,7 +270,8 @@ __global__ void __launch_bounds__(kBlock) k_magnus_persistent(PersistArgs a) {
   const int b = blockIdx.x;
   const int vec = b / a.gv, chunk = b % a.gv;
   const int64_t D = a.dim;
-  const int64_t rows_per = (D + a.gv - 1) / a.gv;
+  // rows per block rounded up to whole warps, so that each warp owns 32 consecutive rows
+  const int64_t rows_per = (((D + a.gv - 1) / a.gv) + 31) & ~(int64_t)31;
   const int64_t lo = min(D, (int64_t)chunk * rows_per), hi = min(D, lo + rows_per);
   const int64_t base = (int64_t)vec * D;
   const int nt = a.nterms, nv = a.nvec;
@@ -149,6 +279,20 @@ __global__ void __launch_bounds__(kBlock) k_magnus_persistent(PersistArgs a) {
   for (int i = tid; i < nt * (int)sizeof(Term) / 4; i += blockDim.x)
     reinterpret_cast<int *>(sT)[i] = reinterpret_cast<const int *>(a.terms)[i];
   __syncthreads();
+  Ctx cx;
+  cx.T = sT;
+  cx.nt = nt;
+  cx.n = sT[0].nspins;
+  cx.lbits = a.lbits;
+  cx.lomask = ((int64_t)1 << (a.lbits + 1)) - 1;
+  cx.dlo = a.dlo;
+  cx.dhi = a.dhi;
+  cx.jb = s_jb;
+  cx.j2 = s_j2;
+  if (FAM == FAM_MF) {
+    // bond at bits (p, p-1) couples spins s = n-p and s+1 with J[s-1] = J[n-p-1]
+    for (int p = 1 + tid; p < cx.n; p += blockDim.x) s_j2[p - 1] = 2.0 * sT[0].J[cx.n - p - 1];
+  }
 
   unsigned it = 0;  // slot counter of the partial sums: consecutive reductions alternate slots
   auto block_reduce_store = [&](double x0, double x1) {
@@ -202,6 +346,8 @@ __global__ void __launch_bounds__(kBlock) k_magnus_persistent(PersistArgs a) {
     if (tid == 0) sR = a.recs[e];
     __syncthreads();
     const ExpRec &R = sR;
+    if (FAM == FAM_MF)
+      for (int p = 1 + tid; p < cx.n; p += blockDim.x) s_jb[p - 1] = s_j2[p - 1] * R.bg[0];
     const double2 *d = a.dd + e * (int64_t)(a.m_max + 1);
     if (!(R.gamma > 0.0)) {  // scalar generator: a phase
       const double2 ph = d[0];
@@ -231,31 +377,32 @@ __global__ void __launch_bounds__(kBlock) k_magnus_persistent(PersistArgs a) {
           // phase 1: u_k = H_k w for this block's rows
           if (mine)
             for (int64_t r = lo + tid; r < hi; r += blockDim.x)
-              for (int k = 0; k < nt; k++) a.u[((size_t)k * nv) * D + base + r] = term_row(sT[k], src + base, r);
+              for (int k = 0; k < nt; k++) a.u[((size_t)k * nv) * D + base + r] = Op<FAM>::term(cx, k, src + base, r);
           if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { fail(MAGNUS_ETIMEOUT); return; }
         }
         double sw = 0.0, sp = 0.0;
         if (mine) {
           for (int64_t r = lo + tid; r < hi; r += blockDim.x) {
-            double2 y = make_double2(0.0, 0.0);
+            double2 y, wr;
             if (R.mode == MODE_M4) {
+              y = make_double2(0.0, 0.0);
               double2 z = make_double2(0.0, 0.0);
               int pi = 0;
               for (int k = 0; k < nt; k++) {
                 y = rfma(R.bg[k], a.u[((size_t)k * nv) * D + base + r], y);
                 for (int l = k + 1; l < nt; l++, pi++) {
-                  const double2 hkul = term_row(sT[k], a.u + ((size_t)l * nv) * D + base, r);
-                  const double2 hluk = term_row(sT[l], a.u + ((size_t)k * nv) * D + base, r);
+                  const double2 hkul = Op<FAM>::term(cx, k, a.u + ((size_t)l * nv) * D + base, r);
+                  const double2 hluk = Op<FAM>::term(cx, l, a.u + ((size_t)k * nv) * D + base, r);
                   z = rfma(R.kg[pi], make_double2(hkul.x - hluk.x, hkul.y - hluk.y), z);
                 }
               }
               y.x += z.y;  // -i z
               y.y -= z.x;
+              wr = ldv(src + base + r);
+              y = rfma(-shift, wr, y);
             } else {
-              for (int k = 0; k < nt; k++) y = rfma(R.bg[k], term_row(sT[k], src + base, r), y);
+              y = Op<FAM>::combo(cx, R, shift, src + base, r, wr);
             }
-            const double2 wr = src[base + r];
-            y = rfma(-shift, wr, y);
             dst[base + r] = y;
             double2 pr = (j == 1) ? cmul(d0, wr) : nxt[base + r];
             pr = cfma(dj, y, pr);
@@ -316,18 +463,35 @@ __global__ void __launch_bounds__(kBlock) k_magnus_persistent(PersistArgs a) {
     for (int64_t r = lo + tid; r < hi; r += blockDim.x) a.psi[base + r] = cur[base + r];
 }
 
+const void *kernel_for(int fam) {
+  switch (fam) {
+    case FAM_CSR: return (const void *)k_magnus_persistent<FAM_CSR>;
+    case FAM_MF: return (const void *)k_magnus_persistent<FAM_MF>;
+    default: return (const void *)k_magnus_persistent<FAM_GENERIC>;
+  }
+}
+
 }  // namespace
 
 int persistent_block_size() { return kBlock; }
 
+// Smallest occupancy over the families: the grid of any plan fits on the device at once.
 cudaError_t persistent_max_blocks_per_sm(int *n) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_magnus_persistent, kBlock, 0);
+  int best = 1 << 30;
+  for (int fam = 0; fam < 3; fam++) {
+    int k = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, kernel_for(fam), kBlock, 0);
+    if (e != cudaSuccess) return e;
+    best = k < best ? k : best;
+  }
+  *n = best;
+  return cudaSuccess;
 }
 
 cudaError_t launch_persistent(const PersistArgs &a, int grid, int block, cudaStream_t st) {
   PersistArgs copy = a;
   void *args[] = {&copy};
-  return cudaLaunchCooperativeKernel((const void *)k_magnus_persistent, dim3(grid), dim3(block), args, 0, st);
+  return cudaLaunchCooperativeKernel(kernel_for(a.fam), dim3(grid), dim3(block), args, 0, st);
 }
 
 }  // namespace mg

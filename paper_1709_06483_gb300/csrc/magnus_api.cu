@@ -41,6 +41,9 @@ struct magnus_plan_s {
   int64_t recs_cap = 0;
   int *mlog = nullptr;
   int64_t mlog_cap = 0;
+  int fam = FAM_GENERIC;
+  int lbits = 0;
+  double *dlo = nullptr, *dhi = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::string err;
 };
@@ -77,7 +80,7 @@ cudaError_t dalloc(T **p, size_t count) {
 void free_plan(magnus_plan_t p) {
   if (!p) return;
   void *bufs[] = {p->terms, p->coeffs, p->term_ab, p->xi, p->cand, p->counter, p->bar, p->counters, p->partials,
-                  p->alt, p->w0, p->w1, p->u, p->recs, p->dd, p->mlog};
+                  p->alt, p->w0, p->w1, p->u, p->recs, p->dd, p->mlog, p->dlo, p->dhi};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (p->ev0) cudaEventDestroy(p->ev0);
@@ -166,6 +169,10 @@ magnus_status run_persistent(magnus_plan_t p, void *psi, int64_t nexp, magnus_st
   a.mlog = want_log ? p->mlog : nullptr;
   a.mlog_cap = want_log;
   a.spin_limit_ns = 4000000000LL;  // 4 s: far above any legitimate wait at a barrier
+  a.fam = p->fam;
+  a.lbits = p->lbits;
+  a.dlo = p->dlo;
+  a.dhi = p->dhi;
   CUDA_TRY(p, cudaEventRecord(p->ev0, p->stream));
   CUDA_TRY(p, launch_persistent(a, grid, persistent_block_size(), p->stream));
   CUDA_TRY(p, cudaEventRecord(p->ev1, p->stream));
@@ -344,6 +351,23 @@ magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms
   cudaFree(flag);
   for (int k = 0; k < nterms; k++) p->terms_host[k].real_valued = (p->terms_host[k].kind == MAGNUS_TERM_CSR) && !fh[k];
   PLAN_TRY(cudaMemcpyAsync(p->terms, p->terms_host, sizeof(Term) * nterms, cudaMemcpyHostToDevice, p->stream));
+
+  // operator family of the persistent kernel
+  {
+    bool all_csr = true;
+    for (int k = 0; k < nterms; k++) all_csr &= (p->terms_host[k].kind == MAGNUS_TERM_CSR);
+    const bool mf = nterms == 2 && p->terms_host[0].kind == MAGNUS_TERM_XXZ &&
+                    p->terms_host[1].kind == MAGNUS_TERM_FIELD_X && p->terms_host[0].nspins == p->terms_host[1].nspins;
+    if (all_csr) p->fam = FAM_CSR;
+    if (mf) {
+      const int n = p->terms_host[0].nspins;
+      p->fam = FAM_MF;
+      p->lbits = std::max(1, n / 2);
+      PLAN_TRY(dalloc(&p->dlo, (size_t)1 << (p->lbits + 1)));
+      PLAN_TRY(dalloc(&p->dhi, (size_t)1 << (n - p->lbits)));
+      PLAN_TRY(launch_xxz_diag_tables(p->terms, n, p->lbits, p->dlo, p->dhi, p->stream));
+    }
+  }
 
   // Gershgorin enclosures (one pass over every term) and the Leja points
   const int gblk = std::max(1, std::min(p->num_sms * 4, (int)((dim + 255) / 256)));

@@ -128,11 +128,18 @@ struct PersistArgs {
   int *mlog;               // [capacity] degrees of the substeps (may be null)
   long long mlog_cap;
   long long spin_limit_ns; // bounded waits
-  int any_m4;
+  int fam;                 // operator family: FAM_GENERIC, FAM_CSR (every term CSR), FAM_MF (XXZ + field)
+  int lbits;               // FAM_MF: split of the basis index for the diagonal tables
+  const double *dlo;       // FAM_MF: diagonal of H_xxz from the low lbits+1 bits   [2^(lbits+1)]
+  const double *dhi;       // FAM_MF: diagonal of H_xxz from bits lbits..n-1         [2^(n-lbits)]
 };
+enum { FAM_GENERIC = 0, FAM_CSR = 1, FAM_MF = 2 };
 cudaError_t launch_persistent(const PersistArgs &a, int grid, int block, cudaStream_t st);
 int persistent_block_size();
 cudaError_t persistent_max_blocks_per_sm(int *n);
+
+// Diagonal tables of a matrix-free XXZ term (FAM_MF), split at bit lbits.
+cudaError_t launch_xxz_diag_tables(const Term *t_dev, int nspins, int lbits, double *dlo, double *dhi, cudaStream_t st);
 
 // Builders.
 cudaError_t launch_build_xxz_csr(int nspins, const double *J, const double *hz, double delta, int64_t *rowptr,

@@ -490,6 +490,33 @@ __global__ void k_build_field_x_dense(int n, double2 *H) {
     for (int b = 0; b < n; b++) H[x * D + (x ^ ((int64_t)1 << b))] = make_double2(1.0, 0.0);
 }
 
+// Diagonal of the open XXZ chain split at bit L: diag(x) = dhi[x >> L] + dlo[x & (2^(L+1) - 1)].
+// Bit p holds spin n-p; the bond between bits p and p-1 has coupling J[n-p-1].  dlo holds the fields
+// at bits 0..L-1 and the bonds (p, p-1) for p = 1..L; dhi the fields at bits L..n-1 and the bonds
+// for p = L+1..n-1, so that every term of the diagonal is counted exactly once.
+__global__ void k_xxz_diag_tables(const Term *tp, int n, int L, double *dlo, double *dhi) {
+  const Term &t = *tp;
+  const int64_t nlo = (int64_t)1 << (L + 1), nhi = (int64_t)1 << (n - L);
+  const int64_t total = nlo > nhi ? nlo : nhi;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < nlo) {
+      double s = 0.0;
+      for (int p = 0; p < L; p++) s += t.hz[n - p - 1] * (((i >> p) & 1) ? -1.0 : 1.0);
+      for (int p = 1; p <= L; p++)
+        s += t.delta * t.J[n - p - 1] * ((((i >> p) ^ (i >> (p - 1))) & 1) ? -1.0 : 1.0);
+      dlo[i] = s;
+    }
+    if (i < nhi) {
+      const int64_t x = i << L;
+      double s = 0.0;
+      for (int p = L; p < n; p++) s += t.hz[n - p - 1] * (((x >> p) & 1) ? -1.0 : 1.0);
+      for (int p = L + 1; p < n; p++)
+        s += t.delta * t.J[n - p - 1] * ((((x >> p) ^ (x >> (p - 1))) & 1) ? -1.0 : 1.0);
+      dhi[i] = s;
+    }
+  }
+}
+
 int grid_for(int64_t n, int block) {
   int64_t g = (n + block - 1) / block;
   if (g > 152 * 32) g = 152 * 32;
@@ -547,6 +574,13 @@ cudaError_t launch_exp_setup_beta(const double *beta_host, int nterms, const dou
   BetaArg b{};
   for (int k = 0; k < nterms && k < kMaxTerms; k++) b.b[k] = beta_host[k];
   k_exp_setup_beta<<<1, 32, 0, st>>>(b, nterms, term_ab, xi, m_max, rho_max, recs, dd);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_xxz_diag_tables(const Term *t_dev, int nspins, int lbits, double *dlo, double *dhi,
+                                   cudaStream_t st) {
+  int64_t n = (int64_t)1 << (lbits + 1 > nspins - lbits ? lbits + 1 : nspins - lbits);
+  k_xxz_diag_tables<<<grid_for(n, 256), 256, 0, st>>>(t_dev, nspins, lbits, dlo, dhi);
   return cudaGetLastError();
 }
 
