@@ -154,6 +154,20 @@ class CSRTerm:
         return t
 
 
+class DenseTerm:
+    """Complex128 dense term on the device, row-major dim x dim."""
+
+    def __init__(self, H):
+        import torch
+        self.val = H.to(torch.complex128).contiguous()
+
+    def ctype(self):
+        t = Term()
+        t.kind, t.nnz = TERM_DENSE, self.val.numel()
+        t.val = _dptr(self.val)
+        return t
+
+
 class XXZTerm:
     """Matrix-free open XXZ chain sum J_i (sx sx + sy sy + delta sz sz)_{i,i+1} + sum h_i sz_i."""
 

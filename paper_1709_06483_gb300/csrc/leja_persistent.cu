@@ -22,6 +22,7 @@
 #include <math.h>
 
 #include "magnus_internal.cuh"
+#include "persist_common.cuh"
 
 namespace mg {
 
@@ -33,60 +34,6 @@ constexpr int kBlock = 256;
 #endif
 constexpr int kMinBlocks = MG_PERSIST_MIN_BLOCKS;  // resident CTAs per SM the register budget targets
 constexpr int kMaxVec = 64;
-constexpr unsigned kFull = 0xffffffffu;
-
-__device__ __forceinline__ long long globaltimer_ns() {
-  long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-// Coherent load of a vector entry that other blocks may have written before the last barrier.
-__device__ __forceinline__ double2 ldv(const double2 *p) { return __ldca(p); }
-
-// Grid-wide barrier with a bounded wait.  Returns false (in every thread of the block) if the
-// wait gave up or another block reported an error; the caller then leaves the kernel.
-__device__ bool grid_barrier(GridBar *bar, unsigned nblocks, long long limit_ns) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    const unsigned g = ld_acquire_gpu(&bar->gen);
-    __threadfence();
-    const unsigned prev = atomicAdd(&bar->count, 1u);
-    if (prev == nblocks - 1) {
-      atomicExch(&bar->count, 0u);
-      __threadfence();
-      atomicAdd(&bar->gen, 1u);
-    } else {
-      const long long t0 = globaltimer_ns();
-      for (unsigned spin = 0;; spin++) {
-        if (ld_acquire_gpu(&bar->gen) != g) break;
-        if (*(volatile int *)&bar->error) { ok = 0; break; }
-        if ((spin & 31u) == 31u && (globaltimer_ns() - t0 > limit_ns || spin > (1u << 28))) {
-          atomicExch(&bar->error, 1);
-          ok = 0;
-          break;
-        }
-        __nanosleep(20);
-      }
-    }
-    __threadfence();
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-  return v;
-}
 
 // ------------------------------------------------------------- rows of H_k x
 // CSR row: sum_e val[e] x[col[e]].  Entries go in rounds of eight (real values) or four (complex)

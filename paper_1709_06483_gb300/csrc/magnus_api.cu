@@ -34,7 +34,7 @@ struct magnus_plan_s {
   GridBar *bar = nullptr;
   Counters *counters = nullptr;
   double *partials = nullptr;
-  int partials_cap = 0;
+  int64_t partials_cap = 0;
   double2 *alt = nullptr, *w0 = nullptr, *w1 = nullptr, *u = nullptr;
   ExpRec *recs = nullptr;
   double2 *dd = nullptr;
@@ -42,6 +42,8 @@ struct magnus_plan_s {
   int *mlog = nullptr;
   int64_t mlog_cap = 0;
   int fam = FAM_GENERIC;
+  int dense_blocks_per_sm = 0;
+  bool dense_real = true;
   int lbits = 0;
   double *dlo = nullptr, *dhi = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -130,13 +132,26 @@ void choose_grid(magnus_plan_t p, int *grid, int *gv) {
 
 magnus_status run_persistent(magnus_plan_t p, void *psi, int64_t nexp, magnus_stats *stats) {
   int grid, gv;
-  choose_grid(p, &grid, &gv);
-  if (grid > p->partials_cap) {
+  size_t need;
+  if (p->fam == FAM_DENSE) {
+    const bool tiled = p->opt.nvec > 1;
+    const int64_t units = (p->dim + dense_rows_per_unit(tiled) - 1) / dense_rows_per_unit(tiled);
+    const int64_t maxg = (int64_t)p->num_sms * std::max(1, p->dense_blocks_per_sm);
+    // the warp-per-row kernel handles 8 rows per block pass; give each block at least 8 rows
+    const int64_t want = tiled ? units : (units + 7) / 8;
+    grid = (int)std::max<int64_t>(1, std::min<int64_t>(p->opt.ctas > 0 ? p->opt.ctas : maxg, std::min(maxg, want)));
+    gv = grid;
+    need = (size_t)4 * grid * p->opt.nvec + (size_t)4 * p->opt.nvec;
+  } else {
+    choose_grid(p, &grid, &gv);
+    need = (size_t)4 * grid;
+  }
+  if ((int64_t)need > p->partials_cap) {
     if (p->partials) cudaFree(p->partials);
     p->partials = nullptr;
     p->partials_cap = 0;
-    CUDA_TRY(p, dalloc(&p->partials, (size_t)4 * grid));
-    p->partials_cap = grid;
+    CUDA_TRY(p, dalloc(&p->partials, need));
+    p->partials_cap = (int64_t)need;
   }
   int64_t want_log = (stats && stats->m_log && stats->m_log_cap > 0) ? stats->m_log_cap : 0;
   if (want_log) {
@@ -174,7 +189,10 @@ magnus_status run_persistent(magnus_plan_t p, void *psi, int64_t nexp, magnus_st
   a.dlo = p->dlo;
   a.dhi = p->dhi;
   CUDA_TRY(p, cudaEventRecord(p->ev0, p->stream));
-  CUDA_TRY(p, launch_persistent(a, grid, persistent_block_size(), p->stream));
+  if (p->fam == FAM_DENSE)
+    CUDA_TRY(p, launch_dense_persistent(a, p->dense_real, grid, p->stream));
+  else
+    CUDA_TRY(p, launch_persistent(a, grid, persistent_block_size(), p->stream));
   CUDA_TRY(p, cudaEventRecord(p->ev1, p->stream));
   Counters c{};
   CUDA_TRY(p, cudaMemcpyAsync(&c, p->counters, sizeof c, cudaMemcpyDeviceToHost, p->stream));
@@ -197,7 +215,7 @@ magnus_status run_persistent(magnus_plan_t p, void *psi, int64_t nexp, magnus_st
     CUDA_TRY(p, cudaEventElapsedTime(&ms, p->ev0, p->ev1));
     stats->kernel_ms = ms;
     stats->grid = grid;
-    stats->block = persistent_block_size();
+    stats->block = p->fam == FAM_DENSE ? dense_block_size() : persistent_block_size();
   }
   if (c.status != MAGNUS_OK) {
     const char *what = c.status == MAGNUS_ENOCONV      ? "Leja interpolation did not converge within m_max"
@@ -259,7 +277,9 @@ magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms
           return set_err(nullptr, MAGNUS_EINVAL, "term %d: CSR arrays missing", k);
         break;
       case MAGNUS_TERM_DENSE:
-        return set_err(nullptr, MAGNUS_EINVAL, "term %d: dense terms are not available in this build", k);
+        if (!t.val) return set_err(nullptr, MAGNUS_EINVAL, "term %d: dense matrix missing", k);
+        if (dim > 65536) return set_err(nullptr, MAGNUS_EINVAL, "term %d: dense terms need dim <= 65536", k);
+        break;
       case MAGNUS_TERM_XXZ:
         if (!is_pow2_dim(dim, t.nspins) || t.nspins < 2 || !t.J || !t.hz)
           return set_err(nullptr, MAGNUS_EINVAL, "term %d: XXZ needs dim = 2^nspins, nspins >= 2, J and hz", k);
@@ -342,14 +362,21 @@ magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms
   int *flag = nullptr;
   PLAN_TRY(dalloc(&flag, kMaxTerms));
   PLAN_TRY(cudaMemsetAsync(flag, 0, sizeof(int) * kMaxTerms, p->stream));
-  for (int k = 0; k < nterms; k++)
+  for (int k = 0; k < nterms; k++) {
     if (p->terms_host[k].kind == MAGNUS_TERM_CSR && p->terms_host[k].nnz > 0)
       PLAN_TRY(launch_imag_check(p->terms_host[k].val, p->terms_host[k].nnz, flag + k, p->stream));
+    if (p->terms_host[k].kind == MAGNUS_TERM_DENSE)
+      PLAN_TRY(launch_imag_check(p->terms_host[k].val, dim * dim, flag + k, p->stream));
+  }
   int fh[kMaxTerms] = {0, 0, 0, 0};
   PLAN_TRY(cudaMemcpyAsync(fh, flag, sizeof fh, cudaMemcpyDeviceToHost, p->stream));
   PLAN_TRY(cudaStreamSynchronize(p->stream));
   cudaFree(flag);
-  for (int k = 0; k < nterms; k++) p->terms_host[k].real_valued = (p->terms_host[k].kind == MAGNUS_TERM_CSR) && !fh[k];
+  for (int k = 0; k < nterms; k++)
+    p->terms_host[k].real_valued =
+        (p->terms_host[k].kind == MAGNUS_TERM_CSR || p->terms_host[k].kind == MAGNUS_TERM_DENSE) && !fh[k];
+  for (int k = 0; k < nterms; k++)
+    if (p->terms_host[k].kind == MAGNUS_TERM_DENSE && !p->terms_host[k].real_valued) p->dense_real = false;
   PLAN_TRY(cudaMemcpyAsync(p->terms, p->terms_host, sizeof(Term) * nterms, cudaMemcpyHostToDevice, p->stream));
 
   // operator family of the persistent kernel
@@ -359,6 +386,19 @@ magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms
     const bool mf = nterms == 2 && p->terms_host[0].kind == MAGNUS_TERM_XXZ &&
                     p->terms_host[1].kind == MAGNUS_TERM_FIELD_X && p->terms_host[0].nspins == p->terms_host[1].nspins;
     if (all_csr) p->fam = FAM_CSR;
+    bool any_dense = false, dense_ok = true;
+    for (int k = 0; k < nterms; k++) {
+      any_dense |= p->terms_host[k].kind == MAGNUS_TERM_DENSE;
+      dense_ok &= p->terms_host[k].kind == MAGNUS_TERM_DENSE || p->terms_host[k].kind == MAGNUS_TERM_FIELD_X;
+    }
+    if (any_dense && !dense_ok) {
+      set_err(p, MAGNUS_EINVAL, "dense terms can only be combined with MAGNUS_TERM_FIELD_X terms");
+      return fail(MAGNUS_EINVAL);
+    }
+    if (any_dense) {
+      p->fam = FAM_DENSE;
+      PLAN_TRY(dense_max_blocks_per_sm(&p->dense_blocks_per_sm));
+    }
     if (mf) {
       const int n = p->terms_host[0].nspins;
       p->fam = FAM_MF;

@@ -133,10 +133,17 @@ struct PersistArgs {
   const double *dlo;       // FAM_MF: diagonal of H_xxz from the low lbits+1 bits   [2^(lbits+1)]
   const double *dhi;       // FAM_MF: diagonal of H_xxz from bits lbits..n-1         [2^(n-lbits)]
 };
-enum { FAM_GENERIC = 0, FAM_CSR = 1, FAM_MF = 2 };
+enum { FAM_GENERIC = 0, FAM_CSR = 1, FAM_MF = 2, FAM_DENSE = 3 };
 cudaError_t launch_persistent(const PersistArgs &a, int grid, int block, cudaStream_t st);
 int persistent_block_size();
 cudaError_t persistent_max_blocks_per_sm(int *n);
+
+// Dense family (dense terms, optionally with a matrix-free field term): rows of all vectors per block.
+int dense_block_size();
+int dense_rows_per_unit(bool tiled);
+cudaError_t dense_max_blocks_per_sm(int *n);
+// partials must hold 4 * grid * nvec + 4 * nvec doubles
+cudaError_t launch_dense_persistent(const PersistArgs &a, bool real_valued, int grid, cudaStream_t st);
 
 // Diagonal tables of a matrix-free XXZ term (FAM_MF), split at bit lbits.
 cudaError_t launch_xxz_diag_tables(const Term *t_dev, int nspins, int lbits, double *dlo, double *dhi, cudaStream_t st);

@@ -1,0 +1,113 @@
+"""Dense terms on the GPU (long-range chain stored as a dense complex128 matrix) against the oracle.
+
+Tolerance: relative 2-norm error <= 1e-10 per state vector and identical Leja degrees.
+"""
+import numpy as np
+import pytest
+
+import magnus_inputs as mi
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def mg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1709_06483_gb300 as m
+    m.load()
+    return m
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def cuda(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def drive_pair(mg, c):
+    return [mg.Drive.const(), mg.Drive(c.drive_a0, c.drive_ac, c.drive_as, c.drive_om)]
+
+
+def oracle_dense(c, Hs, Hd, tol=1e-10):
+    f = oracle.Coeff(c.drive_a0, c.drive_ac, c.drive_as, c.drive_om)
+    return oracle.Problem([Hs, Hd], [oracle.Coeff.const(), f], tol=tol)
+
+
+@pytest.mark.parametrize("nvec", [1, 5])
+@pytest.mark.parametrize("variant", ["CF4", "M4"])
+@pytest.mark.parametrize("field", ["dense", "mfree"])
+def test_longrange_dense_parity(mg, nvec, variant, field):
+    c = mi.workload3(nvec=nvec, nspins=7, h=0.02, nsteps=15)
+    Hs = mg.build_longrange_dense(c.nspins, c.hz, 1.5, c.delta)
+    Hd = mg.build_field_x_dense(c.nspins) if field == "dense" else mg.FieldXTerm(c.nspins)
+    terms = [mg.DenseTerm(Hs), mg.DenseTerm(Hd) if field == "dense" else Hd]
+    plan = mg.Plan(c.dim, terms, drive_pair(mg, c), nvec=nvec)
+    psi = cuda(c.psi0)
+    st = plan.propagate(psi, 0.0, c.h, c.nsteps, variant, log_cap=4096)
+    P = oracle_dense(c, oracle.longrange_dense(c.nspins, c.hz, 1.5, c.delta), oracle.field_x_dense(c.nspins))
+    out = psi.cpu().numpy().reshape(nvec, -1)
+    for v in range(nvec):
+        ost = oracle.Stats(4096)
+        ref = P.propagate(c.psi0.reshape(nvec, -1)[v], 0.0, c.h, c.nsteps, variant, ost)
+        assert rel(out[v], ref) < REL_TOL, (v, rel(out[v], ref))
+        assert np.array_equal(st["m_log"].reshape(-1, nvec)[:, v], ost.m_log)
+
+
+@pytest.mark.parametrize("dim,nvec", [(100, 1), (100, 3), (37, 2), (16, 1)])
+def test_complex_hermitian_ragged(mg, dim, nvec):
+    """General complex Hermitian H (imaginary parts present), dims that leave ragged tiles."""
+    rng = np.random.default_rng(dim + nvec)
+    A = rng.standard_normal((dim, dim)) + 1j * rng.standard_normal((dim, dim))
+    H1 = (A + A.conj().T) / 4
+    B = rng.standard_normal((dim, dim)) + 1j * rng.standard_normal((dim, dim))
+    H2 = (B + B.conj().T) / 8
+    psi0 = mi.random_state(rng, dim, nvec)
+    plan = mg.Plan(dim, [mg.DenseTerm(cuda(H1)), mg.DenseTerm(cuda(H2))],
+                   [mg.Drive.const(), mg.Drive(0.0, [1.0], [], [3.0])], nvec=nvec)
+    for variant in ("CF4", "M4"):
+        psi = cuda(psi0)
+        plan.propagate(psi, 0.0, 0.05, 8, variant)
+        P = oracle.Problem([H1, H2], [oracle.Coeff.const(), oracle.Coeff(0.0, [1.0], [], [3.0])])
+        out = psi.cpu().numpy().reshape(nvec, -1)
+        for v in range(nvec):
+            ref = P.propagate(psi0.reshape(nvec, -1)[v], 0.0, 0.05, 8, variant)
+            assert rel(out[v], ref) < REL_TOL
+
+
+def test_dense_expv_matches_eigh(mg):
+    c = mi.workload3(nvec=2, nspins=8)
+    Hs = mg.build_longrange_dense(c.nspins, c.hz)
+    Hd = mg.build_field_x_dense(c.nspins)
+    plan = mg.Plan(c.dim, [mg.DenseTerm(Hs), mg.DenseTerm(Hd)], drive_pair(mg, c), nvec=2, tol=1e-12)
+    beta = np.array([0.05, 0.02])
+    out, _ = plan.expv(beta, cuda(c.psi0))
+    K = beta[0] * oracle.longrange_dense(c.nspins, c.hz) + beta[1] * oracle.field_x_dense(c.nspins)
+    lam, U = np.linalg.eigh(K)
+    for v in range(2):
+        ref = U @ (np.exp(-1j * lam) * (U.conj().T @ c.psi0[v]))
+        assert rel(out.cpu().numpy()[v], ref) < 1e-11
+
+
+def test_workload3_full_size_sampled(mg):
+    """13 spins (dim 8192), 64 states, dense H_s and dense sum sx: one Cf4 step of all 64 states in
+    the bench's configuration; states 0 and 63 compared with the oracle entry by entry."""
+    c = mi.workload3()
+    Hs = mg.build_longrange_dense(c.nspins, c.hz, 1.5, c.delta)
+    Hd = mg.build_field_x_dense(c.nspins)
+    plan = mg.Plan(c.dim, [mg.DenseTerm(Hs), mg.DenseTerm(Hd)], drive_pair(mg, c), nvec=64)
+    psi = cuda(c.psi0)
+    st = plan.propagate(psi, 0.0, c.h, 1, "CF4", log_cap=1024)
+    out = psi.cpu().numpy()
+    P = oracle_dense(c, oracle.longrange_dense(c.nspins, c.hz, 1.5, c.delta), oracle.field_x_dense(c.nspins))
+    for v in (0, 63):
+        ost = oracle.Stats(64)
+        ref = P.propagate(c.psi0[v], 0.0, c.h, 1, "CF4", ost)
+        assert rel(out[v], ref) < REL_TOL
+        assert np.array_equal(st["m_log"].reshape(-1, 64)[:, v], ost.m_log)
