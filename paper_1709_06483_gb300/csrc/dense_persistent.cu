@@ -33,6 +33,81 @@ struct DenseSmem {
   double hi[kTM][kTK + kPad];           // imaginary parts (complex terms)
   double2 w[kVecMax][kTK + kPad];
 };
+struct SplitSmem {
+  float2 h[kTM][kTK + kPad];            // (hi, lo) of H
+  float4 w[kVecMax][kTK + kPad];        // (re_hi, re_lo, im_hi, im_lo) of the vectors
+};
+union TileSmem {
+  DenseSmem d;
+  SplitSmem f;
+};
+
+// Split-precision multiply-add on the FP32 pipe: sh + sl += (ah + al) (bh + bl).  The leading
+// product is exact (TwoProd by FMA), the two cross products are added to its error term, the
+// running sum sh is updated by an exact TwoSum, and every rounding error goes to sl.  Explicit
+// _rn intrinsics keep the compiler from contracting or reassociating these steps.
+__device__ __forceinline__ void df_fma(float ah, float al, float bh, float bl, float &sh, float &sl) {
+  const float p = __fmul_rn(ah, bh);
+  float e = __fmaf_rn(ah, bh, -p);
+  e = __fmaf_rn(ah, bl, e);
+  e = __fmaf_rn(al, bh, e);
+  const float s = __fadd_rn(sh, p);
+  const float z = __fsub_rn(s, sh);
+  const float t = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, z)), __fsub_rn(p, z));
+  sh = s;
+  sl = __fadd_rn(sl, __fadd_rn(t, e));
+}
+
+__device__ __forceinline__ float4 split4(double2 v) {
+  const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
+  return make_float4(rh, __double2float_rn(v.x - (double)rh), ih, __double2float_rn(v.y - (double)ih));
+}
+
+// acc[i][q] += coef * sum_j H[r0 + 2 ty + i][j] W[tx + 16 q][j], split precision (see df_fma).
+__device__ __forceinline__ void gemm_tile_split(SplitSmem &S, const float2 *H2, double coef, const float4 *W4,
+                                                int64_t D, int nv, int64_t r0, int64_t rend, double2 (&acc)[2][4]) {
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  float sh[2][4][2], sl[2][4][2];
+#pragma unroll
+  for (int i = 0; i < 2; i++)
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+#pragma unroll
+      for (int c = 0; c < 2; c++) sh[i][q][c] = sl[i][q][c] = 0.f;
+  for (int64_t k0 = 0; k0 < D; k0 += kTK) {
+    __syncthreads();
+    for (int i = tid; i < kTM * kTK; i += kDBlock) {
+      const int rr = i / kTK, kk = i % kTK;
+      const int64_t row = r0 + rr, col = k0 + kk;
+      S.h[rr][kk] = (row < rend && col < D) ? __ldg(H2 + row * D + col) : make_float2(0.f, 0.f);
+    }
+    for (int i = tid; i < kVecMax * kTK; i += kDBlock) {
+      const int vv = i / kTK, kk = i % kTK;
+      const int64_t col = k0 + kk;
+      S.w[vv][kk] = (vv < nv && col < D) ? __ldca(W4 + (int64_t)vv * D + col) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+#pragma unroll 2
+    for (int kk = 0; kk < kTK; kk++) {
+      const float2 h0 = S.h[2 * ty][kk], h1 = S.h[2 * ty + 1][kk];
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        const float4 w = S.w[tx + 16 * q][kk];
+        df_fma(h0.x, h0.y, w.x, w.y, sh[0][q][0], sl[0][q][0]);
+        df_fma(h0.x, h0.y, w.z, w.w, sh[0][q][1], sl[0][q][1]);
+        df_fma(h1.x, h1.y, w.x, w.y, sh[1][q][0], sl[1][q][0]);
+        df_fma(h1.x, h1.y, w.z, w.w, sh[1][q][1], sl[1][q][1]);
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 2; i++)
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      acc[i][q].x = fma(coef, (double)sh[i][q][0] + (double)sl[i][q][0], acc[i][q].x);
+      acc[i][q].y = fma(coef, (double)sh[i][q][1] + (double)sl[i][q][1], acc[i][q].y);
+    }
+}
 
 // acc[i][q] += sum_j coef * H[r0 + 2 ty + i][j] * W[tx + 16 q][j] over all columns j.
 template <bool REAL>
@@ -111,7 +186,7 @@ __device__ __forceinline__ double2 fieldx_at(int n, const double2 *x, int64_t r)
 }
 
 // ------------------------------------------------------------------ kernel
-template <bool REAL, bool TILED>
+template <bool REAL, bool TILED, bool SPLIT>
 __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) {
   __shared__ Term sT[kMaxTerms];
   __shared__ ExpRec sR;
@@ -119,7 +194,8 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
   __shared__ int s_act[kVecMax], s_m[kVecMax];
   __shared__ double s_part[kDBlock / 32][kVecMax][2];
   __shared__ int s_flag;
-  __shared__ DenseSmem S;
+  __shared__ TileSmem TS;
+  DenseSmem &S = TS.d;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ty = tid >> 4, tx = tid & 15;
@@ -197,7 +273,8 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
 
   // y[i][q] = sum_k coef_k (H_k src)[row][vec] (+ field), for this thread's outputs
   // tiled: rows r0 + 2 ty + i, vectors tx + 16 q.  warp path: row r, vector 0 (lane 0 holds it).
-  auto apply_terms = [&](const double *coef, const double2 *const *srcs, int64_t r0, double2 (&y)[2][4]) {
+  auto apply_terms = [&](const double *coef, const double2 *const *srcs, const float4 *const *shs, int64_t r0,
+                         double2 (&y)[2][4]) {
     if (TILED) {
 #pragma unroll
       for (int i = 0; i < 2; i++)
@@ -206,7 +283,10 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
       for (int k = 0; k < nt; k++) {
         if (coef[k] == 0.0) continue;
         if (sT[k].kind == MAGNUS_TERM_DENSE) {
-          gemm_tile<REAL>(S, sT[k].val, coef[k], srcs[k], D, nv, r0, hi, y);
+          if (SPLIT)
+            gemm_tile_split(TS.f, a.hsplit[k], coef[k], shs[k], D, nv, r0, hi, y);
+          else
+            gemm_tile<REAL>(S, sT[k].val, coef[k], srcs[k], D, nv, r0, hi, y);
         } else if (sT[k].kind == MAGNUS_TERM_FIELD_X) {
 #pragma unroll
           for (int i = 0; i < 2; i++) {
@@ -284,14 +364,23 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
         s_ep[tid] = sqrt(cabs2(d0)) * s_vn[tid];
         s_m[tid] = 0;
       }
+      if (SPLIT) {  // split copy of the substep's input vector, read by every block
+        for (int v = 0; v < nv; v++)
+          for (int64_t r = lo + tid; r < hi; r += blockDim.x)
+            a.sh_cur[(int64_t)v * D + r] = split4(cur[(int64_t)v * D + r]);
+        if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { fail(MAGNUS_ETIMEOUT); return; }
+      }
       __syncthreads();
       bool done = false;
       for (int j = 1; j <= a.m_max; j++) {
         const double2 *src = (j == 1) ? cur : (((j - 2) & 1) ? a.w1 : a.w0);
         double2 *dst = ((j - 1) & 1) ? a.w1 : a.w0;
+        const float4 *src_sh = (j == 1) ? a.sh_cur : (((j - 2) & 1) ? a.sh_w1 : a.sh_w0);
+        float4 *dst_sh = ((j - 1) & 1) ? a.sh_w1 : a.sh_w0;
         const double shift = R.cg + a.xi[j - 1];
         const double2 dj = d[j];
         const double2 *srcs[kMaxTerms] = {src, src, src, src};
+        const float4 *shs[kMaxTerms] = {src_sh, src_sh, src_sh, src_sh};
         if (R.mode == MODE_M4) {
           // phase 1: u_k = H_k src for every vector, this block's rows
           double one[kMaxTerms];
@@ -301,20 +390,23 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
             if (TILED) {
               for (int64_t r0 = lo; r0 < hi; r0 += kTM) {
                 double2 y[2][4];
-                apply_terms(one, srcs, r0, y);
+                apply_terms(one, srcs, shs, r0, y);
                 for (int i = 0; i < 2; i++) {
                   const int64_t r = r0 + 2 * ty + i;
                   if (r >= hi) continue;
                   for (int q = 0; q < 4; q++) {
                     const int v = tx + 16 * q;
-                    if (v < nv) uk[(int64_t)v * D + r] = y[i][q];
+                    if (v < nv) {
+                      uk[(int64_t)v * D + r] = y[i][q];
+                      if (SPLIT) a.sh_u[(size_t)k * nv * D + (int64_t)v * D + r] = split4(y[i][q]);
+                    }
                   }
                 }
               }
             } else {
               for (int64_t r = lo + warp; r < hi; r += kDBlock / 32) {
                 double2 y[2][4];
-                apply_terms(one, srcs, r, y);
+                apply_terms(one, srcs, shs, r, y);
                 if (lane == 0) uk[r] = y[0][0];
               }
             }
@@ -328,6 +420,7 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
           const double2 wr = ldv(src + idx);
           y = rfma(-shift, wr, y);
           dst[idx] = y;
+          if (SPLIT) dst_sh[idx] = split4(y);
           double2 pr = (j == 1) ? cmul(d0, wr) : nxt[idx];
           pr = cfma(dj, y, pr);
           nxt[idx] = pr;
@@ -344,13 +437,16 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
               ck[k] = R.kg[pi];
               cl[l] = -R.kg[pi];
               const double2 *sk[kMaxTerms], *sl[kMaxTerms];
+              const float4 *hk[kMaxTerms], *hl[kMaxTerms];
               for (int q = 0; q < kMaxTerms; q++) {
                 sk[q] = a.u + (size_t)l * nv * D;  // H_k applied to u_l
                 sl[q] = a.u + (size_t)k * nv * D;  // H_l applied to u_k
+                hk[q] = a.sh_u + (size_t)l * nv * D;
+                hl[q] = a.sh_u + (size_t)k * nv * D;
               }
               double2 z1[2][4], z2[2][4];
-              apply_terms(ck, sk, r0, z1);
-              apply_terms(cl, sl, r0, z2);
+              apply_terms(ck, sk, hk, r0, z1);
+              apply_terms(cl, sl, hl, r0, z2);
               for (int i = 0; i < 2; i++)
                 for (int q = 0; q < 4; q++) {
                   const double zx = z1[i][q].x + z2[i][q].x, zy = z1[i][q].y + z2[i][q].y;
@@ -376,7 +472,7 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
                 }
               }
             } else {
-              apply_terms(R.bg, srcs, r0, y);
+              apply_terms(R.bg, srcs, shs, r0, y);
             }
             for (int i = 0; i < 2; i++) {
               const int64_t r = r0 + 2 * ty + i;
@@ -395,7 +491,7 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
               commutator(r, y);
               for (int k = 0; k < nt; k++) y[0][0] = rfma(R.bg[k], a.u[(size_t)k * D + r], y[0][0]);
             } else {
-              apply_terms(R.bg, srcs, r, y);
+              apply_terms(R.bg, srcs, shs, r, y);
             }
             if (lane == 0 && s_act[0]) finish(r, 0, y[0][0], 0);
           }
@@ -451,9 +547,11 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
       for (int64_t r = lo + tid; r < hi; r += blockDim.x) a.psi[(int64_t)v * D + r] = cur[(int64_t)v * D + r];
 }
 
-const void *dense_kernel(bool real, bool tiled) {
-  if (real) return tiled ? (const void *)k_dense_persistent<true, true> : (const void *)k_dense_persistent<true, false>;
-  return tiled ? (const void *)k_dense_persistent<false, true> : (const void *)k_dense_persistent<false, false>;
+const void *dense_kernel(bool real, bool tiled, bool split) {
+  if (split) return (const void *)k_dense_persistent<true, true, true>;
+  if (real)
+    return tiled ? (const void *)k_dense_persistent<true, true, false> : (const void *)k_dense_persistent<true, false, false>;
+  return tiled ? (const void *)k_dense_persistent<false, true, false> : (const void *)k_dense_persistent<false, false, false>;
 }
 
 }  // namespace
@@ -461,12 +559,27 @@ const void *dense_kernel(bool real, bool tiled) {
 int dense_block_size() { return kDBlock; }
 int dense_rows_per_unit(bool tiled) { return tiled ? kTM : 1; }
 
+namespace {
+__global__ void k_split_dense(const double2 *H, float2 *out, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = H[i].x;
+    const float hi = __double2float_rn(x);
+    out[i] = make_float2(hi, __double2float_rn(x - (double)hi));
+  }
+}
+}  // namespace
+
+cudaError_t launch_split_dense(const double2 *H, float2 *out, int64_t n, cudaStream_t st) {
+  k_split_dense<<<152 * 8, 256, 0, st>>>(H, out, n);
+  return cudaGetLastError();
+}
+
 cudaError_t dense_max_blocks_per_sm(int *n) {
   int best = 1 << 30;
   for (int r = 0; r < 2; r++)
-    for (int t = 0; t < 2; t++) {
+    for (int t = 0; t < 3; t++) {
       int k = 0;
-      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, dense_kernel(r, t), kDBlock, 0);
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, dense_kernel(r, t > 0, t == 2), kDBlock, 0);
       if (e != cudaSuccess) return e;
       best = k < best ? k : best;
     }
@@ -477,7 +590,8 @@ cudaError_t dense_max_blocks_per_sm(int *n) {
 cudaError_t launch_dense_persistent(const PersistArgs &a, bool real_valued, int grid, cudaStream_t st) {
   PersistArgs copy = a;
   void *args[] = {&copy};
-  return cudaLaunchCooperativeKernel(dense_kernel(real_valued, a.nvec > 1), dim3(grid), dim3(kDBlock), args, 0, st);
+  return cudaLaunchCooperativeKernel(dense_kernel(real_valued, a.nvec > 1 || a.split, a.split != 0), dim3(grid),
+                                     dim3(kDBlock), args, 0, st);
 }
 
 }  // namespace mg

@@ -44,6 +44,8 @@ struct magnus_plan_s {
   int fam = FAM_GENERIC;
   int dense_blocks_per_sm = 0;
   bool dense_real = true;
+  float2 *hsplit[kMaxTerms] = {nullptr, nullptr, nullptr, nullptr};
+  float4 *sh_cur = nullptr, *sh_w0 = nullptr, *sh_w1 = nullptr, *sh_u = nullptr;
   int lbits = 0;
   double *dlo = nullptr, *dhi = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -82,7 +84,8 @@ cudaError_t dalloc(T **p, size_t count) {
 void free_plan(magnus_plan_t p) {
   if (!p) return;
   void *bufs[] = {p->terms, p->coeffs, p->term_ab, p->xi, p->cand, p->counter, p->bar, p->counters, p->partials,
-                  p->alt, p->w0, p->w1, p->u, p->recs, p->dd, p->mlog, p->dlo, p->dhi};
+                  p->alt, p->w0, p->w1, p->u, p->recs, p->dd, p->mlog, p->dlo, p->dhi,
+                  p->hsplit[0], p->hsplit[1], p->hsplit[2], p->hsplit[3], p->sh_cur, p->sh_w0, p->sh_w1, p->sh_u};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (p->ev0) cudaEventDestroy(p->ev0);
@@ -134,7 +137,7 @@ magnus_status run_persistent(magnus_plan_t p, void *psi, int64_t nexp, magnus_st
   int grid, gv;
   size_t need;
   if (p->fam == FAM_DENSE) {
-    const bool tiled = p->opt.nvec > 1;
+    const bool tiled = p->opt.nvec > 1 || p->opt.precision == MAGNUS_FP32_SPLIT;
     const int64_t units = (p->dim + dense_rows_per_unit(tiled) - 1) / dense_rows_per_unit(tiled);
     const int64_t maxg = (int64_t)p->num_sms * std::max(1, p->dense_blocks_per_sm);
     // the warp-per-row kernel handles 8 rows per block pass; give each block at least 8 rows
@@ -188,6 +191,12 @@ magnus_status run_persistent(magnus_plan_t p, void *psi, int64_t nexp, magnus_st
   a.lbits = p->lbits;
   a.dlo = p->dlo;
   a.dhi = p->dhi;
+  a.split = p->opt.precision == MAGNUS_FP32_SPLIT;
+  for (int k = 0; k < kMaxTerms; k++) a.hsplit[k] = p->hsplit[k];
+  a.sh_cur = p->sh_cur;
+  a.sh_w0 = p->sh_w0;
+  a.sh_w1 = p->sh_w1;
+  a.sh_u = p->sh_u;
   CUDA_TRY(p, cudaEventRecord(p->ev0, p->stream));
   if (p->fam == FAM_DENSE)
     CUDA_TRY(p, launch_dense_persistent(a, p->dense_real, grid, p->stream));
@@ -265,7 +274,8 @@ magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms
   if (!(o.rho_max > 0.0)) return set_err(nullptr, MAGNUS_EINVAL, "rho_max must be > 0");
   if (o.m_max < 2 || o.m_max > kMmaxLimit) return set_err(nullptr, MAGNUS_EINVAL, "m_max must be 2..%d", kMmaxLimit);
   if (o.nvec < 1 || o.nvec > 64) return set_err(nullptr, MAGNUS_EINVAL, "nvec must be 1..64");
-  if (o.precision != MAGNUS_FP64) return set_err(nullptr, MAGNUS_EINVAL, "only MAGNUS_FP64 is available");
+  if (o.precision != MAGNUS_FP64 && o.precision != MAGNUS_FP32_SPLIT)
+    return set_err(nullptr, MAGNUS_EINVAL, "precision must be MAGNUS_FP64 or MAGNUS_FP32_SPLIT");
   for (int k = 0; k < nterms; k++) {
     const magnus_term &t = terms[k];
     const magnus_coeff &c = coeffs[k];
@@ -398,6 +408,21 @@ magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms
     if (any_dense) {
       p->fam = FAM_DENSE;
       PLAN_TRY(dense_max_blocks_per_sm(&p->dense_blocks_per_sm));
+    }
+    if (o.precision == MAGNUS_FP32_SPLIT) {
+      if (p->fam != FAM_DENSE || !p->dense_real) {
+        set_err(p, MAGNUS_EINVAL, "MAGNUS_FP32_SPLIT needs real-valued dense terms");
+        return fail(MAGNUS_EINVAL);
+      }
+      for (int k = 0; k < nterms; k++)
+        if (p->terms_host[k].kind == MAGNUS_TERM_DENSE) {
+          PLAN_TRY(dalloc(&p->hsplit[k], (size_t)dim * dim));
+          PLAN_TRY(launch_split_dense(p->terms_host[k].val, p->hsplit[k], dim * dim, p->stream));
+        }
+      PLAN_TRY(dalloc(&p->sh_cur, nd));
+      PLAN_TRY(dalloc(&p->sh_w0, nd));
+      PLAN_TRY(dalloc(&p->sh_w1, nd));
+      PLAN_TRY(dalloc(&p->sh_u, nd * nterms));
     }
     if (mf) {
       const int n = p->terms_host[0].nspins;

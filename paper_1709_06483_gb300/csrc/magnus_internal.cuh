@@ -132,6 +132,11 @@ struct PersistArgs {
   int lbits;               // FAM_MF: split of the basis index for the diagonal tables
   const double *dlo;       // FAM_MF: diagonal of H_xxz from the low lbits+1 bits   [2^(lbits+1)]
   const double *dhi;       // FAM_MF: diagonal of H_xxz from bits lbits..n-1         [2^(n-lbits)]
+  // FAM_DENSE with MAGNUS_FP32_SPLIT: dense terms as FP32 (hi, lo) pairs of their real parts, and
+  // (re_hi, re_lo, im_hi, im_lo) shadows of every vector set a dense matvec reads
+  int split;
+  const float2 *hsplit[kMaxTerms];
+  float4 *sh_cur, *sh_w0, *sh_w1, *sh_u;
 };
 enum { FAM_GENERIC = 0, FAM_CSR = 1, FAM_MF = 2, FAM_DENSE = 3 };
 cudaError_t launch_persistent(const PersistArgs &a, int grid, int block, cudaStream_t st);
@@ -144,6 +149,9 @@ int dense_rows_per_unit(bool tiled);
 cudaError_t dense_max_blocks_per_sm(int *n);
 // partials must hold 4 * grid * nvec + 4 * nvec doubles
 cudaError_t launch_dense_persistent(const PersistArgs &a, bool real_valued, int grid, cudaStream_t st);
+
+// H (complex128, real parts used) -> FP32 (hi, lo) pairs, n entries.
+cudaError_t launch_split_dense(const double2 *H, float2 *out, int64_t n, cudaStream_t st);
 
 // Diagonal tables of a matrix-free XXZ term (FAM_MF), split at bit lbits.
 cudaError_t launch_xxz_diag_tables(const Term *t_dev, int nspins, int lbits, double *dlo, double *dhi, cudaStream_t st);

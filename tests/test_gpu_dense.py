@@ -111,3 +111,27 @@ def test_workload3_full_size_sampled(mg):
         ref = P.propagate(c.psi0[v], 0.0, c.h, 1, "CF4", ost)
         assert rel(out[v], ref) < REL_TOL
         assert np.array_equal(st["m_log"].reshape(-1, 64)[:, v], ost.m_log)
+
+
+@pytest.mark.parametrize("variant", ["CF4", "M4"])
+def test_fp32_split_precision(mg, variant):
+    """MAGNUS_FP32_SPLIT: dense matvecs on the FP32 pipe with error-free products and sums.
+    Stated accuracy: state error <= 1e-9 relative to the FP64 oracle (target of the mode: 1e-8)."""
+    c = mi.workload3(nvec=6, nspins=8, h=0.02, nsteps=10)
+    Hs = mg.build_longrange_dense(c.nspins, c.hz, 1.5, c.delta)
+    Hd = mg.build_field_x_dense(c.nspins)
+    plan = mg.Plan(c.dim, [mg.DenseTerm(Hs), mg.DenseTerm(Hd)], drive_pair(mg, c), nvec=6, precision=mg.FP32_SPLIT)
+    psi = cuda(c.psi0)
+    plan.propagate(psi, 0.0, c.h, c.nsteps, variant)
+    P = oracle_dense(c, oracle.longrange_dense(c.nspins, c.hz, 1.5, c.delta), oracle.field_x_dense(c.nspins))
+    out = psi.cpu().numpy()
+    errs = [rel(out[v], P.propagate(c.psi0[v], 0.0, c.h, c.nsteps, variant)) for v in range(6)]
+    assert max(errs) < 1e-9, errs
+
+
+def test_fp32_split_rejects_complex_terms(mg):
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((32, 32)) + 1j * rng.standard_normal((32, 32))
+    with pytest.raises(mg.MagnusError) as e:
+        mg.Plan(32, [mg.DenseTerm(cuda(A + A.conj().T))], [mg.Drive.const()], nvec=2, precision=mg.FP32_SPLIT)
+    assert e.value.code == mg.EINVAL
