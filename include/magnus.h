@@ -215,6 +215,58 @@ MAGNUS_API magnus_status magnus_build_longrange_dense(int32_t nspins, double alp
 /* sum_i sigma^x_i, dense. */
 MAGNUS_API magnus_status magnus_build_field_x_dense(int32_t nspins, void *H, void *stream);
 
+/* ---- batches of independent problems ---- */
+
+/* One problem of a batch: a state of dimension dim under terms[nterms] with coeffs[nterms] (as in
+ * magnus_plan_create; CSR, XXZ or FIELD_X terms; the CSR arrays are borrowed). */
+typedef struct {
+  int64_t dim;
+  int32_t nterms;
+  int32_t _pad;
+  const magnus_term *terms;
+  const magnus_coeff *coeffs;
+} magnus_batch_item;
+
+typedef struct {
+  int64_t n_exp, n_substeps, n_matvec, n_termapply; /* summed over all problems                  */
+  int32_t max_m;
+  int32_t status;
+  int32_t *m_log;               /* optional HOST [count][m_log_cap_per_item]: Leja degree per substep */
+  int64_t m_log_cap_per_item;
+  double graph_ms;              /* device time of the replayed graph (setup + persistent kernel)    */
+  int32_t block;                /* CTA size the autotuner chose                                     */
+  int32_t _pad;
+} magnus_batch_stats;
+
+typedef struct magnus_batch_s *magnus_batch_t;
+
+/*
+ * A batch of count independent problems (arXiv:1709.06483 Sec. 2 stepping with Sec. 3 Leja
+ * interpolation applied to each) that magnus_batch_propagate advances together in ONE persistent
+ * launch: every CTA takes whole problems from a work queue, largest first, and synchronises only
+ * within itself.  Computes, once, the Gershgorin enclosure of every term and the Leja points.
+ * opt: as for plans, with nvec = 1 (one state per problem) and precision MAGNUS_FP64; ctas > 0
+ * caps the CTAs, ctas < 0 forces the CTA size -ctas (128, 256, 512 or 1024) instead of the autotuner.
+ * The batch uses its own CUDA stream (the stream argument is ignored).  Errors: EINVAL, ENOMEM, ECUDA.
+ */
+MAGNUS_API magnus_status magnus_batch_create(magnus_batch_t *batch, int32_t count, const magnus_batch_item *items,
+                                             const magnus_options *opt, void *stream);
+
+/*
+ * psi[i] (device complex128 [dim_i], in/out; psi is a HOST array of count device pointers) <- nsteps
+ * Magnus steps of size h from t0 for every problem.  The first call times the candidate CTA sizes on
+ * copies of the states (2 steps each) and keeps the fastest; the setup launches and the persistent
+ * kernel are captured into a CUDA graph once per (t0, h, nsteps, variant) and replayed.  Synchronous.
+ * Errors: EINVAL, ENOCONV, ENONFINITE, ECUDA (the first error of any problem).
+ */
+MAGNUS_API magnus_status magnus_batch_propagate(magnus_batch_t batch, void *const *psi, double t0, double h,
+                                                int64_t nsteps, int32_t variant, magnus_batch_stats *stats);
+
+MAGNUS_API magnus_status magnus_batch_destroy(magnus_batch_t batch);
+
+/* Last error of this batch ("" if none); NULL gives the last error of magnus_batch_create. */
+MAGNUS_API const char *magnus_batch_last_error(magnus_batch_t batch);
+
 /* ---- allocation-free entry point ---- */
 
 /*

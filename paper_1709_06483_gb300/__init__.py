@@ -28,7 +28,8 @@ EXPORTS = (
     "magnus_plan_create", "magnus_plan_destroy", "magnus_last_error", "magnus_status_string", "leja_expv",
     "magnus_propagate", "magnus_term_interval", "magnus_leja_points", "magnus_divided_differences",
     "magnus_xxz_nnz", "magnus_build_xxz_csr", "magnus_build_field_x_csr", "magnus_build_longrange_dense",
-    "magnus_build_field_x_dense", "magnus_expv_xxz_static",
+    "magnus_build_field_x_dense", "magnus_expv_xxz_static", "magnus_batch_create", "magnus_batch_propagate",
+    "magnus_batch_destroy", "magnus_batch_last_error",
 )
 
 
@@ -61,6 +62,18 @@ class Stats(C.Structure):
                 ("grid", C.c_int32), ("block", C.c_int32)]
 
 
+class BatchItem(C.Structure):
+    _fields_ = [("dim", C.c_int64), ("nterms", C.c_int32), ("_pad", C.c_int32), ("terms", C.POINTER(Term)),
+                ("coeffs", C.POINTER(Coeff))]
+
+
+class BatchStats(C.Structure):
+    _fields_ = [("n_exp", C.c_int64), ("n_substeps", C.c_int64), ("n_matvec", C.c_int64),
+                ("n_termapply", C.c_int64), ("max_m", C.c_int32), ("status", C.c_int32),
+                ("m_log", C.POINTER(C.c_int32)), ("m_log_cap_per_item", C.c_int64), ("graph_ms", C.c_double),
+                ("block", C.c_int32), ("_pad", C.c_int32)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -84,6 +97,10 @@ def _declare(L):
         "magnus_build_longrange_dense": (I32, [I32, D, C.POINTER(D), D, P, P]),
         "magnus_build_field_x_dense": (I32, [I32, P, P]),
         "magnus_expv_xxz_static": (I32, [I32, C.POINTER(D), C.POINTER(D), D, C.POINTER(D), P, P, D, P]),
+        "magnus_batch_create": (I32, [C.POINTER(C.c_void_p), I32, C.POINTER(BatchItem), C.POINTER(Options), P]),
+        "magnus_batch_propagate": (I32, [P, C.POINTER(C.c_void_p), D, D, I64, I32, C.POINTER(BatchStats)]),
+        "magnus_batch_destroy": (I32, [P]),
+        "magnus_batch_last_error": (C.c_char_p, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -306,6 +323,64 @@ def _as_dict(st: Stats, log):
     if log is not None:
         out["m_log"] = log[: min(st.n_substeps, log.size)].copy()
     return out
+
+
+# ------------------------------------------------------------------ batches
+class Batch:
+    """Many independent problems (dim_i, terms_i, drives_i) advanced together in one persistent launch
+    under a replayed CUDA graph, with an autotuned CTA size."""
+
+    def __init__(self, problems, tol=1e-10, tol_abs=None, rho_max=4.0, m_max=100, ctas=0):
+        L = load()
+        self._keep = []
+        arr = (BatchItem * len(problems))()
+        for i, (dim, terms, drives) in enumerate(problems):
+            t = (Term * len(terms))(*[x.ctype() for x in terms])
+            c = (Coeff * len(drives))(*[x.ctype() for x in drives])
+            self._keep += [terms, drives, t, c]
+            arr[i].dim, arr[i].nterms = int(dim), len(terms)
+            arr[i].terms, arr[i].coeffs = t, c
+        self.count = len(problems)
+        self.dims = [int(p[0]) for p in problems]
+        opt = Options(float(tol), float(tol if tol_abs is None else tol_abs), float(rho_max), int(m_max), 1,
+                      int(ctas), FP64)
+        h = C.c_void_p()
+        code = L.magnus_batch_create(C.byref(h), self.count, arr, C.byref(opt), None)
+        if code != OK:
+            raise MagnusError(code, L.magnus_batch_last_error(None).decode(errors="replace"))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().magnus_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def propagate(self, psis, t0, h, nsteps, variant="CF4", log_cap=0):
+        """psis: list of CUDA complex128 tensors (in place)."""
+        assert len(psis) == self.count
+        ptrs = (C.c_void_p * self.count)(*[_dptr(p) for p in psis])
+        st = BatchStats()
+        log = None
+        if log_cap:
+            log = np.zeros((self.count, log_cap), dtype=np.int32)
+            st.m_log = log.ctypes.data_as(C.POINTER(C.c_int32))
+            st.m_log_cap_per_item = log_cap
+        code = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+        L = load()
+        rc = L.magnus_batch_propagate(self._h, ptrs, float(t0), float(h), int(nsteps), code, C.byref(st))
+        if rc != OK:
+            raise MagnusError(rc, L.magnus_batch_last_error(self._h).decode(errors="replace"))
+        out = {k: getattr(st, k) for k in ("n_exp", "n_substeps", "n_matvec", "n_termapply", "max_m", "status",
+                                           "graph_ms", "block")}
+        if log is not None:
+            out["m_log"] = log
+        return out
 
 
 # ------------------------------------------------------------------ builders

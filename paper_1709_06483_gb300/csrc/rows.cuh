@@ -1,0 +1,179 @@
+// Rows of the operators: (H_k x)[r] for CSR, matrix-free XXZ and transverse-field terms, and the
+// compile-time operator families of the persistent kernels.  Shared by the single-problem kernel
+// (leja_persistent.cu) and the batched kernel (batched.cu).
+#pragma once
+
+#include "magnus_internal.cuh"
+#include "persist_common.cuh"
+
+namespace mg {
+namespace rows {
+
+// ------------------------------------------------------------- rows of H_k x
+// CSR row: sum_e val[e] x[col[e]].  Entries go in rounds of eight (real values) or four (complex)
+// so that the column/value loads and the gathers of a whole round are in flight together.
+static __device__ __forceinline__ double2 csr_row(const Term &t, const double2 *x, int64_t r) {
+  double2 acc = make_double2(0.0, 0.0);
+  int64_t e = __ldg(t.rowptr + r);
+  const int64_t e1 = __ldg(t.rowptr + r + 1);
+  if (t.real_valued) {
+    for (; e + 8 <= e1; e += 8) {
+      int c[8];
+      double a[8];
+      double2 xv[8];
+#pragma unroll
+      for (int q = 0; q < 8; q++) c[q] = __ldg(t.col + e + q);
+#pragma unroll
+      for (int q = 0; q < 8; q++) a[q] = __ldg(&t.val[e + q].x);
+#pragma unroll
+      for (int q = 0; q < 8; q++) xv[q] = ldv(x + c[q]);
+#pragma unroll
+      for (int q = 0; q < 8; q++) acc = rfma(a[q], xv[q], acc);
+    }
+    if (e + 4 <= e1) {
+      int c[4];
+      double a[4];
+      double2 xv[4];
+#pragma unroll
+      for (int q = 0; q < 4; q++) c[q] = __ldg(t.col + e + q);
+#pragma unroll
+      for (int q = 0; q < 4; q++) a[q] = __ldg(&t.val[e + q].x);
+#pragma unroll
+      for (int q = 0; q < 4; q++) xv[q] = ldv(x + c[q]);
+#pragma unroll
+      for (int q = 0; q < 4; q++) acc = rfma(a[q], xv[q], acc);
+      e += 4;
+    }
+    for (; e < e1; e++) acc = rfma(__ldg(&t.val[e].x), ldv(x + __ldg(t.col + e)), acc);
+  } else {
+    for (; e + 4 <= e1; e += 4) {
+      int c[4];
+      double2 a[4], xv[4];
+#pragma unroll
+      for (int q = 0; q < 4; q++) c[q] = __ldg(t.col + e + q);
+#pragma unroll
+      for (int q = 0; q < 4; q++) a[q] = __ldg(t.val + e + q);
+#pragma unroll
+      for (int q = 0; q < 4; q++) xv[q] = ldv(x + c[q]);
+#pragma unroll
+      for (int q = 0; q < 4; q++) acc = cfma(a[q], xv[q], acc);
+    }
+    for (; e < e1; e++) acc = cfma(__ldg(t.val + e), ldv(x + __ldg(t.col + e)), acc);
+  }
+  return acc;
+}
+
+// Open XXZ chain (Sec. 4 embedding, spin s at bit n-s): diagonal sum delta J_s z_s z_{s+1} + h_s z_s,
+// and 2 J_s to the state with spins s, s+1 swapped when they are anti-parallel.
+static __device__ __forceinline__ double2 xxz_row(const Term &t, const double2 *x, int64_t r) {
+  const int n = t.nspins;
+  double diag = 0.0;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int s = 1; s <= n; s++) {
+    const double zs = ((r >> (n - s)) & 1) ? -1.0 : 1.0;
+    diag = fma(t.hz[s - 1], zs, diag);
+    if (s < n) {
+      const bool anti = ((r >> (n - s)) ^ (r >> (n - s - 1))) & 1;
+      diag = fma(t.delta * t.J[s - 1], anti ? -1.0 : 1.0, diag);
+      if (anti) acc = rfma(2.0 * t.J[s - 1], ldv(x + (r ^ ((int64_t)3 << (n - s - 1)))), acc);
+    }
+  }
+  return rfma(diag, ldv(x + r), acc);
+}
+
+// sum_i sigma^x_i: the sum over all single-spin flips (all loads issued before the adds).
+static __device__ __forceinline__ double2 fieldx_row(int n, const double2 *x, int64_t r) {
+  double2 acc = make_double2(0.0, 0.0);
+  int b = 0;
+  for (; b + 4 <= n; b += 4) {
+    const double2 v0 = ldv(x + (r ^ ((int64_t)1 << b))), v1 = ldv(x + (r ^ ((int64_t)2 << b))),
+                  v2 = ldv(x + (r ^ ((int64_t)4 << b))), v3 = ldv(x + (r ^ ((int64_t)8 << b)));
+    acc.x += (v0.x + v1.x) + (v2.x + v3.x);
+    acc.y += (v0.y + v1.y) + (v2.y + v3.y);
+  }
+  for (; b < n; b++) {
+    const double2 v = ldv(x + (r ^ ((int64_t)1 << b)));
+    acc.x += v.x;
+    acc.y += v.y;
+  }
+  return acc;
+}
+
+static __device__ __forceinline__ double2 term_row_generic(const Term &t, const double2 *x, int64_t r) {
+  switch (t.kind) {
+    case MAGNUS_TERM_CSR: return csr_row(t, x, r);
+    case MAGNUS_TERM_XXZ: return xxz_row(t, x, r);
+    case MAGNUS_TERM_FIELD_X: return fieldx_row(t.nspins, x, r);
+    default: return make_double2(0.0, 0.0);
+  }
+}
+
+// Per-block operator context: terms in shared memory plus, for FAM_MF, the diagonal tables and
+// the bond couplings pre-scaled by the current exponential's weight.
+struct Ctx {
+  const Term *T;
+  int nt;
+  int n, lbits;
+  int64_t lomask;
+  const double *dlo, *dhi;
+  const double *jb;   // shared: 2 J_bond * bg[0] per bond, bond at bits (p, p-1) stored at p-1
+  const double *j2;   // shared: 2 J_bond (unscaled), same indexing
+};
+
+// H_xxz row with the diagonal from the two tables (FAM_MF).  coefj: per-bond coefficients.
+// Every bond's partner entry is loaded whether or not the bond is active (all loads in flight at
+// once); only the multiply-add depends on the spins.
+[[maybe_unused]] constexpr int kMaxBonds = kMaxSpins - 1;
+static __device__ __forceinline__ double2 mf_xxz_row(const Ctx &c, const double *coefj, double dscale, double dshift,
+                                              const double2 *x, int64_t r, double2 &xr) {
+  xr = ldv(x + r);
+  const double dg = __ldg(c.dhi + (r >> c.lbits)) + __ldg(c.dlo + (r & c.lomask));
+  const double cr = fma(dscale, dg, -dshift);
+  double2 acc;
+  acc.x = cr * xr.x;
+  acc.y = cr * xr.y;
+  const int nb = c.n - 1;
+  for (int p0 = 0; p0 < nb; p0 += 4) {
+    double2 v[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) v[q] = ldv(x + (r ^ ((int64_t)3 << min(p0 + q, nb - 1))));
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int p = p0 + q + 1;  // bond at bits (p, p-1)
+      if (p <= nb && (((r >> p) ^ (r >> (p - 1))) & 1)) acc = rfma(coefj[p - 1], v[q], acc);
+    }
+  }
+  return acc;
+}
+
+template <int FAM>
+struct Op {
+  // (H_k x)[r]
+  __device__ static __forceinline__ double2 term(const Ctx &c, int k, const double2 *x, int64_t r) {
+    if (FAM == FAM_CSR) return csr_row(c.T[k], x, r);
+    if (FAM == FAM_MF) {
+      if (k == 0) {
+        double2 xr;
+        return mf_xxz_row(c, c.j2, 1.0, 0.0, x, r, xr);
+      }
+      return fieldx_row(c.n, x, r);
+    }
+    return term_row_generic(c.T[k], x, r);
+  }
+  // sum_k bg_k (H_k x)[r] - shift x[r]; also returns x[r]
+  __device__ static __forceinline__ double2 combo(const Ctx &c, const ExpRec &R, double shift, const double2 *x,
+                                                  int64_t r, double2 &xr) {
+    if (FAM == FAM_MF) {
+      double2 y = mf_xxz_row(c, c.jb, R.bg[0], shift, x, r, xr);
+      const double2 f = fieldx_row(c.n, x, r);
+      return rfma(R.bg[1], f, y);
+    }
+    double2 y = make_double2(0.0, 0.0);
+    for (int k = 0; k < c.nt; k++) y = rfma(R.bg[k], term(c, k, x, r), y);
+    xr = ldv(x + r);
+    return rfma(-shift, xr, y);
+  }
+};
+
+}  // namespace rows
+}  // namespace mg
