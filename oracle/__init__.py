@@ -77,6 +77,8 @@ def lib():
                 "orc_apply_term": (I32, [P, I32, P, P]),
                 "orc_expv": (I32, [P, P, P, C.POINTER(_Stats)]),
                 "orc_propagate": (I32, [P, P, D, D, I64, I32, C.POINTER(_Stats)]),
+                "orc_frechet_expv": (I32, [P, P, I32, P, P, P, C.POINTER(_Stats)]),
+                "orc_adjoint_grad": (I32, [P, P, P, D, D, I64, I32, I32, C.POINTER(D), P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -264,3 +266,23 @@ class Problem:
         _check(lib().orc_propagate(self._h, _ptr(out), float(t0), float(h), int(nsteps), code,
                                    C.byref(st) if st else None), "propagate")
         return out
+
+    def frechet_expv(self, beta, kd, v):
+        """(L(Omega, -i H_kd) v, exp(Omega) v) for Omega = -i sum_k beta_k H_k (augmented block matrix)."""
+        beta = np.ascontiguousarray(beta, dtype=np.float64)
+        v = np.ascontiguousarray(v, dtype=np.complex128)
+        a, b = np.zeros_like(v), np.zeros_like(v)
+        _check(lib().orc_frechet_expv(self._h, _ptr(beta), int(kd), _ptr(v), _ptr(a), _ptr(b), None), "frechet_expv")
+        return a, b
+
+    def adjoint_grad(self, psi0, phi, t0, h, nsteps, variant="CF4", kd=1):
+        """F = |<phi|psi(T)>|^2 and dF/d(a0, ac_m, as_m) of term kd's drive."""
+        psi0 = np.ascontiguousarray(psi0, dtype=np.complex128)
+        phi = np.ascontiguousarray(phi, dtype=np.complex128)
+        ng = 1 + 2 * self.coeffs[kd].om.size
+        grad = np.zeros(ng)
+        F = C.c_double()
+        code = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+        _check(lib().orc_adjoint_grad(self._h, _ptr(psi0), _ptr(phi), float(t0), float(h), int(nsteps), code, int(kd),
+                                      C.byref(F), _ptr(grad)), "adjoint_grad")
+        return F.value, grad

@@ -679,3 +679,203 @@ int orc_propagate(const orc_problem *p, double complex *psi, double t0, double h
   gen_free(&g);
   return rc;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Adjoint: gradient of a state-transfer fidelity with respect to the drive.  */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * [a; b] <- exp(Omega_aug) [a; b] for Omega_aug = -i [[K, H_kd], [0, K]], K = sum_k beta_k H_k,
+ * by the Newton-form Leja recurrence of Sec. 3 on stacked vectors.  The block matrix has the
+ * spectrum of K, so it uses K's enclosure, shift, scale, substeps and divided differences; the
+ * early-termination test uses 2-norms of the stacked vectors.
+ */
+static int frechet_core(const orc_problem *p, const double *beta, int kd, double complex *a, double complex *b,
+                        orc_stats *st) {
+  const int64_t D = p->dim;
+  orc_gen g;
+  int rc = gen_alloc(&g, p, st);
+  if (rc) { gen_free(&g); return rc; }
+  g.mode = GEN_LINEAR;
+  for (int k = 0; k < p->nterms; k++) g.beta[k] = beta[k];
+  double lo, hi;
+  gen_interval(&g, &lo, &hi);
+  const double c = 0.5 * (lo + hi), gamma = 0.25 * (hi - lo);
+  if (!(gamma > 0.0)) { /* scalar K: exp(-i[[c, H],[0, c]]) = e^{-ic} [[1, -iH],[0, 1]] */
+    double complex ph = cexp(-I * c);
+    orc_apply_term(p, kd, b, g.u1);
+    for (int64_t i = 0; i < D; i++) { a[i] = ph * (a[i] - I * g.u1[i]); b[i] = ph * b[i]; }
+    gen_free(&g);
+    return ORC_OK;
+  }
+  int s = (int)ceil(gamma / p->rho_max);
+  if (s < 1) s = 1;
+  double complex *d = (double complex *)malloc(sizeof(double complex) * (size_t)(p->m_max + 1));
+  double complex *wa = (double complex *)malloc(sizeof(double complex) * (size_t)D);
+  double complex *wb = (double complex *)malloc(sizeof(double complex) * (size_t)D);
+  double complex *ka = (double complex *)malloc(sizeof(double complex) * (size_t)D);
+  double complex *kb = (double complex *)malloc(sizeof(double complex) * (size_t)D);
+  double complex *pa = (double complex *)malloc(sizeof(double complex) * (size_t)D);
+  double complex *pb = (double complex *)malloc(sizeof(double complex) * (size_t)D);
+  if (!d || !wa || !wb || !ka || !kb || !pa || !pb) rc = ORC_ENOMEM;
+  if (rc == ORC_OK) orc_divided_differences(p->m_max, p->xi, gamma / s, d);
+  const double complex phase = cexp(-I * c / s);
+  for (int sub = 0; sub < s && rc == ORC_OK; sub++) {
+    for (int64_t i = 0; i < D; i++) { wa[i] = a[i]; wb[i] = b[i]; pa[i] = d[0] * a[i]; pb[i] = d[0] * b[i]; }
+    double e_prev = cabs(d[0]) * sqrt(creal(vnorm(wa, D) * vnorm(wa, D) + vnorm(wb, D) * vnorm(wb, D)));
+    int conv = 0, m = 0;
+    for (int j = 1; j <= p->m_max; j++) {
+      /* K_aug [wa; wb] = [K wa + H_kd wb; K wb] */
+      gen_apply(&g, wa, ka);
+      gen_apply(&g, wb, kb);
+      orc_apply_term(p, kd, wb, g.u1);
+      if (st) st->n_matvec++;
+      for (int64_t i = 0; i < D; i++) {
+        double complex na = (ka[i] + g.u1[i] - c * wa[i]) / gamma - p->xi[j - 1] * wa[i];
+        double complex nb = (kb[i] - c * wb[i]) / gamma - p->xi[j - 1] * wb[i];
+        wa[i] = na;
+        wb[i] = nb;
+        pa[i] += d[j] * wa[i];
+        pb[i] += d[j] * wb[i];
+      }
+      double nw2 = vnorm(wa, D) * vnorm(wa, D) + vnorm(wb, D) * vnorm(wb, D);
+      double np2 = vnorm(pa, D) * vnorm(pa, D) + vnorm(pb, D) * vnorm(pb, D);
+      double e = cabs(d[j]) * sqrt(nw2), pn = sqrt(np2);
+      if (!isfinite(e) || !isfinite(pn)) { rc = ORC_ENONFINITE; break; }
+      if (e + e_prev <= p->tol_abs + p->tol_rel * pn) { conv = 1; m = j; break; }
+      e_prev = e;
+    }
+    if (rc == ORC_OK && !conv) rc = ORC_ENOCONV;
+    if (st) {
+      st->n_substeps++;
+      if (m > st->max_m) st->max_m = m;
+    }
+    for (int64_t i = 0; i < D; i++) { a[i] = phase * pa[i]; b[i] = phase * pb[i]; }
+  }
+  if (st) st->n_exp++;
+  free(d); free(wa); free(wb); free(ka); free(kb); free(pa); free(pb);
+  gen_free(&g);
+  return rc;
+}
+
+int orc_frechet_expv(const orc_problem *p, const double *beta, int kd, const double complex *v, double complex *a,
+                     double complex *b, orc_stats *st) {
+  int rc = check_problem(p);
+  if (rc) return rc;
+  if (kd < 0 || kd >= p->nterms) return ORC_EINVAL;
+  for (int64_t i = 0; i < p->dim; i++) { a[i] = 0.0; b[i] = v[i]; }
+  return frechet_core(p, beta, kd, a, b, st);
+}
+
+/*
+ * Commutator-free schedule of the exponentials of one step: for stage q (in application order)
+ * the weights w[q][j] of A(t_n + c_j h); J nodes c[j].
+ */
+static int cf_schedule(int variant, int *nstage, int *J, double w[3][3], double c[3]) {
+  const double r3 = sqrt(3.0), r15 = sqrt(15.0);
+  if (variant == ORC_CF4) {
+    const double a1 = (3.0 - 2.0 * r3) / 12.0, a2 = (3.0 + 2.0 * r3) / 12.0;
+    *nstage = 2; *J = 2;
+    c[0] = 0.5 - r3 / 6.0; c[1] = 0.5 + r3 / 6.0;
+    w[0][0] = a2; w[0][1] = a1;   /* right factor, applied first */
+    w[1][0] = a1; w[1][1] = a2;
+    return ORC_OK;
+  }
+  if (variant == ORC_CF4_3) {
+    const double al[3][3] = {
+        {37.0 / 240.0 - 10.0 * r15 / 261.0, -1.0 / 30.0, 37.0 / 240.0 + 10.0 * r15 / 261.0},
+        {-11.0 / 360.0, 23.0 / 45.0, -11.0 / 360.0},
+        {37.0 / 240.0 + 10.0 * r15 / 261.0, -1.0 / 30.0, 37.0 / 240.0 - 10.0 * r15 / 261.0}};
+    *nstage = 3; *J = 3;
+    c[0] = 0.5 - r15 / 10.0; c[1] = 0.5; c[2] = 0.5 + r15 / 10.0;
+    for (int q = 0; q < 3; q++)
+      for (int j = 0; j < 3; j++) w[q][j] = al[2 - q][j];
+    return ORC_OK;
+  }
+  if (variant == ORC_M2) {
+    *nstage = 1; *J = 1;
+    c[0] = 0.5;
+    w[0][0] = 1.0;
+    return ORC_OK;
+  }
+  return ORC_EINVAL;
+}
+
+/*
+ * F = |z|^2, z = <phi, psi_T> = phi^H U_M ... U_1 psi0 with U_e = exp(-i K_e) the exponentials in
+ * application order.  dz/dc = sum_e (d beta_{kd,e} / dc) <lambda_e, L(Omega_e, -i H_kd) v_e> with
+ * v_e the state before exponential e and lambda_e = U_{e+1}^H ... U_M^H phi the costate after it
+ * (propagated backward with exp(+i K) = exp(-i (-K))), and dF/dc = 2 Re(conj(z) dz/dc).
+ * All forward states are kept (no checkpointing: this is the plain reference).
+ */
+int orc_adjoint_grad(const orc_problem *p, const double complex *psi0, const double complex *phi, double t0,
+                     double h, int64_t nsteps, int variant, int kd, double *F, double *grad) {
+  int rc = check_problem(p);
+  if (rc) return rc;
+  int nstage, J;
+  double w[3][3], c[3];
+  if (cf_schedule(variant, &nstage, &J, w, c) != ORC_OK || kd < 0 || kd >= p->nterms || nsteps < 0) return ORC_EINVAL;
+  const int64_t D = p->dim, nexp = nsteps * nstage;
+  const int nm = p->coeff[kd].nmodes, ng = 1 + 2 * nm;
+  double complex *states = (double complex *)malloc(sizeof(double complex) * (size_t)(nexp + 1) * (size_t)D);
+  double *betas = (double *)malloc(sizeof(double) * (size_t)(nexp > 0 ? nexp : 1) * MAX_TERMS);
+  double *dbeta = (double *)malloc(sizeof(double) * (size_t)(nexp > 0 ? nexp : 1) * (size_t)ng);
+  double complex *lam = (double complex *)malloc(sizeof(double complex) * (size_t)D);
+  double complex *fa = (double complex *)malloc(sizeof(double complex) * (size_t)D);
+  double complex *fb = (double complex *)malloc(sizeof(double complex) * (size_t)D);
+  double complex *dz = (double complex *)calloc((size_t)ng, sizeof(double complex));
+  if (!states || !betas || !dbeta || !lam || !fa || !fb || !dz) rc = ORC_ENOMEM;
+  /* weights of every exponential and their derivatives with respect to the coefficients of term kd */
+  for (int64_t n = 0; n < nsteps && rc == ORC_OK; n++) {
+    const double tn = t0 + (double)n * h;
+    for (int q = 0; q < nstage; q++) {
+      const int64_t e = n * nstage + q;
+      for (int k = 0; k < p->nterms; k++) {
+        double sacc = 0.0;
+        for (int j = 0; j < J; j++) sacc += w[q][j] * orc_coeff_eval(p, k, tn + c[j] * h);
+        betas[e * MAX_TERMS + k] = h * sacc;
+      }
+      const orc_coeff *cf = &p->coeff[kd];
+      double s0 = 0.0;
+      for (int j = 0; j < J; j++) s0 += w[q][j];
+      dbeta[e * ng] = h * s0;
+      for (int m = 0; m < nm; m++) {
+        double sc = 0.0, ss = 0.0;
+        for (int j = 0; j < J; j++) {
+          sc += w[q][j] * cos(cf->om[m] * (tn + c[j] * h));
+          ss += w[q][j] * sin(cf->om[m] * (tn + c[j] * h));
+        }
+        dbeta[e * ng + 1 + m] = h * sc;
+        dbeta[e * ng + 1 + nm + m] = h * ss;
+      }
+    }
+  }
+  /* forward, keeping every state */
+  if (rc == ORC_OK) memcpy(states, psi0, sizeof(double complex) * (size_t)D);
+  for (int64_t e = 0; e < nexp && rc == ORC_OK; e++) {
+    memcpy(states + (e + 1) * D, states + e * D, sizeof(double complex) * (size_t)D);
+    rc = orc_expv(p, betas + e * MAX_TERMS, states + (e + 1) * D, NULL);
+  }
+  double complex z = 0.0;
+  if (rc == ORC_OK) {
+    for (int64_t i = 0; i < D; i++) z += conj(phi[i]) * states[nexp * D + i];
+    memcpy(lam, phi, sizeof(double complex) * (size_t)D);
+  }
+  /* backward */
+  double negb[MAX_TERMS];
+  for (int64_t e = nexp - 1; e >= 0 && rc == ORC_OK; e--) {
+    rc = orc_frechet_expv(p, betas + e * MAX_TERMS, kd, states + e * D, fa, fb, NULL);
+    if (rc) break;
+    double complex Ge = 0.0;
+    for (int64_t i = 0; i < D; i++) Ge += conj(lam[i]) * fa[i];
+    for (int q = 0; q < ng; q++) dz[q] += dbeta[e * ng + q] * Ge;
+    for (int k = 0; k < p->nterms; k++) negb[k] = -betas[e * MAX_TERMS + k];
+    rc = orc_expv(p, negb, lam, NULL);
+  }
+  if (rc == ORC_OK) {
+    *F = creal(z) * creal(z) + cimag(z) * cimag(z);
+    for (int q = 0; q < ng; q++) grad[q] = 2.0 * creal(conj(z) * dz[q]);
+  }
+  free(states); free(betas); free(dbeta); free(lam); free(fa); free(fb); free(dz);
+  return rc;
+}

@@ -74,6 +74,22 @@ int orc_expv(const orc_problem *p, const double *beta, double complex *v, orc_st
 int orc_propagate(const orc_problem *p, double complex *psi, double t0, double h, int64_t nsteps,
                   int variant, orc_stats *st);
 
+/*
+ * Frechet derivative of the exponential by the augmented block matrix:
+ * [a; b] = exp(Omega_aug) [0; v] with Omega_aug = [[Omega, E], [0, Omega]], Omega = -i sum_k beta_k H_k,
+ * E = -i H_kd.  Then a = L(Omega, E) v and b = exp(Omega) v.
+ */
+int orc_frechet_expv(const orc_problem *p, const double *beta, int kd, const double complex *v, double complex *a,
+                     double complex *b, orc_stats *st);
+
+/*
+ * Gradient of F = |<phi|psi(T)>|^2, psi(T) = nsteps commutator-free steps (ORC_CF4, ORC_CF4_3 or
+ * ORC_M2) from psi0, with respect to the drive coefficients of term kd:
+ * grad[0] = dF/da0, grad[1+m] = dF/dac_m, grad[1+nmodes+m] = dF/das_m.  *F receives F.
+ */
+int orc_adjoint_grad(const orc_problem *p, const double complex *psi0, const double complex *phi, double t0,
+                     double h, int64_t nsteps, int variant, int kd, double *F, double *grad);
+
 #ifdef __cplusplus
 }
 #endif
