@@ -177,6 +177,21 @@ MAGNUS_API magnus_status leja_expv(magnus_plan_t plan, const double *beta, const
 MAGNUS_API magnus_status magnus_propagate(magnus_plan_t plan, void *psi, double t0, double h, int64_t nsteps,
                                int32_t variant, magnus_stats *stats);
 
+/*
+ * Adjoint gradient (no counterpart computed in the paper; built on its Sec. 2 stepping and Sec. 3
+ * Leja interpolation).  With psi(T) = nsteps commutator-free steps (MAGNUS_CF4, MAGNUS_CF4_3 or
+ * MAGNUS_M2) from psi0 at t0, F = |<phi|psi(T)>|^2 (written to *F) and its gradient with respect to
+ * the drive coefficients of term kd: grad[0] = dF/da0, grad[1+m] = dF/dac[m], grad[1+nmodes+m] =
+ * dF/das[m] (HOST array of 1 + 2 nmodes doubles).  Each exponential is differentiated through the
+ * augmented block matrix [[Omega, -i H_kd], [0, Omega]] with the same Leja kernels, the costate is
+ * propagated with exp(+iK), and psi is checkpointed every ckpt_every steps and recomputed segment by
+ * segment.  psi0, phi: device complex128 [dim].  Plans with nvec = 1 and CSR / matrix-free terms.
+ * Errors: EINVAL, ENOMEM, ENOCONV, ENONFINITE, ETIMEOUT, ECUDA.
+ */
+MAGNUS_API magnus_status magnus_adjoint_grad(magnus_plan_t plan, const void *psi0, const void *phi, double t0, double h,
+                                             int64_t nsteps, int32_t variant, int32_t kd, int32_t ckpt_every, double *F,
+                                             double *grad, magnus_stats *stats);
+
 /* Gershgorin enclosure [*a, *b] of term k (computed at plan creation). */
 MAGNUS_API magnus_status magnus_term_interval(magnus_plan_t plan, int32_t k, double *a, double *b);
 

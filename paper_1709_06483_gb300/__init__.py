@@ -29,7 +29,7 @@ EXPORTS = (
     "magnus_propagate", "magnus_term_interval", "magnus_leja_points", "magnus_divided_differences",
     "magnus_xxz_nnz", "magnus_build_xxz_csr", "magnus_build_field_x_csr", "magnus_build_longrange_dense",
     "magnus_build_field_x_dense", "magnus_expv_xxz_static", "magnus_batch_create", "magnus_batch_propagate",
-    "magnus_batch_destroy", "magnus_batch_last_error",
+    "magnus_batch_destroy", "magnus_batch_last_error", "magnus_adjoint_grad",
 )
 
 
@@ -101,6 +101,7 @@ def _declare(L):
         "magnus_batch_propagate": (I32, [P, C.POINTER(C.c_void_p), D, D, I64, I32, C.POINTER(BatchStats)]),
         "magnus_batch_destroy": (I32, [P]),
         "magnus_batch_last_error": (C.c_char_p, [P]),
+        "magnus_adjoint_grad": (I32, [P, P, P, D, D, I64, I32, I32, I32, C.POINTER(D), C.POINTER(D), C.POINTER(Stats)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -300,6 +301,20 @@ class Plan:
         _check(load().leja_expv(self._h, b.ctypes.data_as(C.POINTER(C.c_double)), C.c_void_p(_dptr(v)),
                                 C.c_void_p(_dptr(out)), C.byref(st)), self._h)
         return out, _as_dict(st, log)
+
+    def adjoint_grad(self, psi0, phi, t0, h, nsteps, variant="CF4", kd=1, ckpt_every=16):
+        """F = |<phi|psi(T)>|^2 and dF/d(a0, ac_m, as_m) of term kd's drive (adjoint, checkpointed)."""
+        self._check_state(psi0)
+        self._check_state(phi)
+        nm = self._drives[kd].om.size
+        grad = np.zeros(1 + 2 * nm)
+        F = C.c_double()
+        st = Stats()
+        code = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+        _check(load().magnus_adjoint_grad(self._h, C.c_void_p(_dptr(psi0)), C.c_void_p(_dptr(phi)), float(t0),
+                                          float(h), int(nsteps), code, int(kd), int(ckpt_every), C.byref(F),
+                                          grad.ctypes.data_as(C.POINTER(C.c_double)), C.byref(st)), self._h)
+        return F.value, grad, _as_dict(st, None)
 
     def interval(self, k):
         a, b = C.c_double(), C.c_double()

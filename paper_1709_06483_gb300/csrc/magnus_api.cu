@@ -538,6 +538,177 @@ magnus_status magnus_divided_differences(magnus_plan_t p, double rho, void *d, i
   return MAGNUS_OK;
 }
 
+magnus_status magnus_adjoint_grad(magnus_plan_t p, const void *psi0, const void *phi, double t0, double h,
+                                  int64_t nsteps, int32_t variant, int32_t kd, int32_t ckpt_every, double *F,
+                                  double *grad, magnus_stats *stats) {
+  if (!p) return set_err(nullptr, MAGNUS_EINVAL, "plan is null");
+  p->err.clear();
+  if (!psi0 || !phi || !F || !grad) return set_err(p, MAGNUS_EINVAL, "null argument");
+  if (((uintptr_t)psi0) % 16 || ((uintptr_t)phi) % 16) return set_err(p, MAGNUS_EINVAL, "vectors must be 16-byte aligned");
+  if (variant != MAGNUS_CF4 && variant != MAGNUS_CF4_3 && variant != MAGNUS_M2)
+    return set_err(p, MAGNUS_EINVAL, "the adjoint needs a commutator-free variant (CF4, CF4_3 or M2)");
+  if (p->opt.nvec != 1) return set_err(p, MAGNUS_EINVAL, "the adjoint takes plans with nvec = 1");
+  if (p->fam == FAM_DENSE) return set_err(p, MAGNUS_EINVAL, "the adjoint takes CSR or matrix-free terms");
+  if (kd < 0 || kd >= p->nterms) return set_err(p, MAGNUS_EINVAL, "kd out of range");
+  if (ckpt_every < 1 || nsteps < 1) return set_err(p, MAGNUS_EINVAL, "need nsteps >= 1 and ckpt_every >= 1");
+  if (stats) memset(stats, 0, sizeof *stats);
+  const int per = exps_per_step(variant);
+  const int64_t D = p->dim, nexp = nsteps * per, seg_exps = (int64_t)ckpt_every * per;
+  const int64_t nseg = (nexp + seg_exps - 1) / seg_exps;
+  const int m1 = p->opt.m_max + 1;
+  magnus_status s = ensure_exp_capacity(p, nexp);
+  if (s != MAGNUS_OK) return s;
+  // workspace (freed at the end of the call)
+  std::vector<void *> tmp;
+  auto grab = [&](void **ptr, size_t bytes) -> cudaError_t {
+    cudaError_t e = cudaMalloc(ptr, bytes ? bytes : 16);
+    if (e == cudaSuccess) tmp.push_back(*ptr);
+    return e;
+  };
+  struct Free {
+    std::vector<void *> &t;
+    ~Free() { for (void *q : t) cudaFree(q); }
+  } freer{tmp};
+  ExpRec *nrecs = nullptr;
+  double2 *ndd = nullptr, *ckpt = nullptr, *seg = nullptr, *lam = nullptr, *aug = nullptr, *G = nullptr, *z = nullptr,
+          *a_out = nullptr;
+  double *gradd = nullptr, *apart = nullptr;
+  Coeff *cdev = nullptr;
+  int nm = 0;
+  {
+    Coeff ch{};
+    CUDA_TRY(p, cudaMemcpy(&ch, p->coeffs + kd, sizeof(Coeff), cudaMemcpyDeviceToHost));
+    nm = ch.nmodes;
+  }
+  const int ngrad = 1 + 2 * nm;
+  int aug_per_sm = 0;
+  CUDA_TRY(p, aug_max_blocks_per_sm(&aug_per_sm));
+  const int agrid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)p->num_sms * std::max(1, aug_per_sm), (D + 31) / 32));
+  CUDA_TRY(p, grab((void **)&nrecs, sizeof(ExpRec) * nexp));
+  CUDA_TRY(p, grab((void **)&ndd, sizeof(double2) * nexp * m1));
+  CUDA_TRY(p, grab((void **)&ckpt, sizeof(double2) * nseg * D));
+  CUDA_TRY(p, grab((void **)&seg, sizeof(double2) * seg_exps * D));
+  CUDA_TRY(p, grab((void **)&lam, sizeof(double2) * D));
+  CUDA_TRY(p, grab((void **)&aug, sizeof(double2) * 8 * D));
+  CUDA_TRY(p, grab((void **)&a_out, sizeof(double2) * D));
+  CUDA_TRY(p, grab((void **)&G, sizeof(double2) * nexp));
+  CUDA_TRY(p, grab((void **)&z, sizeof(double2)));
+  CUDA_TRY(p, grab((void **)&gradd, sizeof(double) * ngrad));
+  CUDA_TRY(p, grab((void **)&apart, sizeof(double) * 4 * agrid));
+  cdev = p->coeffs + kd;
+
+  int grid, gv;
+  choose_grid(p, &grid, &gv);
+  if ((int64_t)4 * grid > p->partials_cap) {
+    if (p->partials) cudaFree(p->partials);
+    p->partials = nullptr;
+    p->partials_cap = 0;
+    CUDA_TRY(p, dalloc(&p->partials, (size_t)4 * grid));
+    p->partials_cap = (int64_t)4 * grid;
+  }
+  cudaStream_t st = p->stream;
+  CUDA_TRY(p, launch_exp_setup(variant, t0, h, nsteps, p->nterms, p->coeffs, p->term_ab, p->xi, p->opt.m_max,
+                               p->opt.rho_max, p->recs, p->dd, nexp, st));
+  CUDA_TRY(p, launch_negate_records(p->recs, p->dd, nrecs, ndd, nexp, p->opt.m_max, st));
+  CUDA_TRY(p, cudaMemsetAsync(p->bar, 0, sizeof(GridBar), st));
+  CUDA_TRY(p, cudaMemsetAsync(p->counters, 0, sizeof(Counters), st));
+  PersistArgs a{};
+  a.dim = D;
+  a.nvec = 1;
+  a.nterms = p->nterms;
+  a.gv = gv;
+  a.m_max = p->opt.m_max;
+  a.tol_rel = p->opt.tol_rel;
+  a.tol_abs = p->opt.tol_abs;
+  a.terms = p->terms;
+  a.xi = p->xi;
+  a.alt = p->alt;
+  a.w0 = p->w0;
+  a.w1 = p->w1;
+  a.u = p->u;
+  a.partials = p->partials;
+  a.bar = p->bar;
+  a.counters = p->counters;
+  a.spin_limit_ns = 4000000000LL;
+  a.fam = p->fam;
+  a.lbits = p->lbits;
+  a.dlo = p->dlo;
+  a.dhi = p->dhi;
+  auto persist = [&](double2 *x, const ExpRec *R, const double2 *DD, int64_t cnt) -> cudaError_t {
+    PersistArgs q = a;
+    q.recs = R;
+    q.dd = DD;
+    q.nexp = cnt;
+    q.psi = x;
+    return launch_persistent(q, grid, persistent_block_size(), st);
+  };
+  AugArgs g{};
+  g.dim = D;
+  g.nterms = p->nterms;
+  g.kd = kd;
+  g.m_max = p->opt.m_max;
+  g.fam = p->fam;
+  g.lbits = p->lbits;
+  g.tol_rel = p->opt.tol_rel;
+  g.tol_abs = p->opt.tol_abs;
+  g.terms = p->terms;
+  g.xi = p->xi;
+  g.out_a = a_out;
+  g.acur = aug; g.bcur = aug + D; g.anxt = aug + 2 * D; g.bnxt = aug + 3 * D;
+  g.wa0 = aug + 4 * D; g.wb0 = aug + 5 * D; g.wa1 = aug + 6 * D; g.wb1 = aug + 7 * D;
+  g.partials = apart;
+  g.bar = p->bar;
+  g.counters = p->counters;
+  g.spin_limit_ns = 4000000000LL;
+  g.dlo = p->dlo;
+  g.dhi = p->dhi;
+
+  // forward with a checkpoint at the start of every segment; the final state ends in p->alt's partner
+  double2 *psiw = lam;  // lam doubles as the forward work vector until the backward pass starts
+  CUDA_TRY(p, cudaMemcpyAsync(psiw, psi0, sizeof(double2) * D, cudaMemcpyDeviceToDevice, st));
+  for (int64_t sgi = 0; sgi < nseg; sgi++) {
+    const int64_t e0 = sgi * seg_exps, cnt = std::min(seg_exps, nexp - e0);
+    CUDA_TRY(p, cudaMemcpyAsync(ckpt + sgi * D, psiw, sizeof(double2) * D, cudaMemcpyDeviceToDevice, st));
+    CUDA_TRY(p, persist(psiw, p->recs + e0, p->dd + e0 * m1, cnt));
+  }
+  CUDA_TRY(p, launch_dot((const double2 *)phi, psiw, D, z, st));
+  CUDA_TRY(p, cudaMemcpyAsync(lam, phi, sizeof(double2) * D, cudaMemcpyDeviceToDevice, st));
+  // backward, segment by segment
+  for (int64_t sgi = nseg - 1; sgi >= 0; sgi--) {
+    const int64_t e0 = sgi * seg_exps, cnt = std::min(seg_exps, nexp - e0);
+    CUDA_TRY(p, cudaMemcpyAsync(seg, ckpt + sgi * D, sizeof(double2) * D, cudaMemcpyDeviceToDevice, st));
+    for (int64_t i = 1; i < cnt; i++) {
+      CUDA_TRY(p, cudaMemcpyAsync(seg + i * D, seg + (i - 1) * D, sizeof(double2) * D, cudaMemcpyDeviceToDevice, st));
+      CUDA_TRY(p, persist(seg + i * D, p->recs + e0 + i - 1, p->dd + (e0 + i - 1) * m1, 1));
+    }
+    for (int64_t i = cnt - 1; i >= 0; i--) {
+      const int64_t e = e0 + i;
+      g.rec = p->recs + e;
+      g.dd = p->dd + e * m1;
+      g.v = seg + i * D;
+      CUDA_TRY(p, launch_aug_persistent(g, agrid, st));
+      CUDA_TRY(p, launch_dot(lam, a_out, D, G + e, st));
+      CUDA_TRY(p, persist(lam, nrecs + e, ndd + e * m1, 1));
+    }
+  }
+  CUDA_TRY(p, launch_adjoint_contract(G, z, cdev, variant, t0, h, nsteps, gradd, ngrad, st));
+  double2 zh{};
+  Counters c{};
+  CUDA_TRY(p, cudaMemcpyAsync(&zh, z, sizeof zh, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(p, cudaMemcpyAsync(grad, gradd, sizeof(double) * ngrad, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(p, cudaMemcpyAsync(&c, p->counters, sizeof c, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(p, cudaStreamSynchronize(st));
+  *F = zh.x * zh.x + zh.y * zh.y;
+  if (stats) {
+    stats->n_matvec = c.n_matvec;
+    stats->max_m = c.max_m;
+    stats->status = c.status;
+    stats->n_exp = nexp;
+  }
+  if (c.status != MAGNUS_OK) return set_err(p, (magnus_status)c.status, "adjoint: device status %d", c.status);
+  return MAGNUS_OK;
+}
+
 int64_t magnus_xxz_nnz(int32_t nspins) {
   if (nspins < 2 || nspins > kMaxSpins) return -1;
   const int64_t D = (int64_t)1 << nspins;

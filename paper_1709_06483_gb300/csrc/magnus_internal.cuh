@@ -153,6 +153,33 @@ cudaError_t launch_dense_persistent(const PersistArgs &a, bool real_valued, int 
 // H (complex128, real parts used) -> FP32 (hi, lo) pairs, n entries.
 cudaError_t launch_split_dense(const double2 *H, float2 *out, int64_t n, cudaStream_t st);
 
+// Adjoint: the augmented-block Leja kernel for one exponential and its helpers (adjoint.cu).
+struct AugArgs {
+  int64_t dim;
+  int nterms, kd, m_max, fam, lbits;
+  double tol_rel, tol_abs;
+  const Term *terms;
+  const ExpRec *rec;       // the exponential's record
+  const double2 *dd;       // its divided differences [m_max+1]
+  const double *xi;
+  const double2 *v;        // input state
+  double2 *out_a;          // L(Omega, -i H_kd) v
+  double2 *acur, *bcur, *anxt, *bnxt, *wa0, *wb0, *wa1, *wb1;
+  double *partials;        // [2][grid][2]
+  GridBar *bar;
+  Counters *counters;
+  long long spin_limit_ns;
+  const double *dlo, *dhi;
+};
+int aug_block_size();
+cudaError_t aug_max_blocks_per_sm(int *n);
+cudaError_t launch_aug_persistent(const AugArgs &a, int grid, cudaStream_t st);
+cudaError_t launch_negate_records(const ExpRec *in, const double2 *din, ExpRec *out, double2 *dout, int64_t nexp,
+                                  int m_max, cudaStream_t st);
+cudaError_t launch_dot(const double2 *x, const double2 *y, int64_t n, double2 *out, cudaStream_t st);
+cudaError_t launch_adjoint_contract(const double2 *G, const double2 *z, const Coeff *coeff, int variant, double t0,
+                                    double h, int64_t nsteps, double *grad, int ng, cudaStream_t st);
+
 // Diagonal tables of a matrix-free XXZ term (FAM_MF), split at bit lbits.
 cudaError_t launch_xxz_diag_tables(const Term *t_dev, int nspins, int lbits, double *dlo, double *dhi, cudaStream_t st);
 
