@@ -44,6 +44,22 @@ def measured_peaks():
         return {}
 
 
+def max_over_ranks(value, device="cpu"):
+    """Maximum of a per-rank float over all ranks of the default process group (identity alone)."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(units_per_rank, ms_max, world):
+    """Whole-job throughput of independent replicas: all ranks' units / the slowest rank's time."""
+    return world * units_per_rank / (ms_max / 1e3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -193,12 +209,8 @@ def run_ours(args):
         st = plan.propagate(psi, c.t0, c.h, args.steps, variant)
         end.record(stream)
         barrier()
-    ms = start.elapsed_time(end)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * args.steps / (ms / 1e3)
+    ms = max_over_ranks(start.elapsed_time(end), "cuda")
+    value = replica_rate(args.steps, ms, world)
 
     # roofline of the persistent Leja kernel, from its own CUDA-event duration
     nmv = st["n_matvec"]
@@ -281,13 +293,13 @@ def run_dense13(args):
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     mg.load()
-    c = mi.workload3()
+    c = mi.workload3(nvec=args.states, nspins=args.spins)
     Hs = mg.build_longrange_dense(c.nspins, c.hz, 1.5, c.delta)
     Hd = mg.build_field_x_dense(c.nspins)
     stream = torch.cuda.current_stream()
     res = {}
     for prec in ("fp64", "fp32_split"):
-        plan = mg.Plan(c.dim, [mg.DenseTerm(Hs), mg.DenseTerm(Hd)], drives(mg, c), nvec=64,
+        plan = mg.Plan(c.dim, [mg.DenseTerm(Hs), mg.DenseTerm(Hd)], drives(mg, c), nvec=args.states,
                        precision=mg.FP64 if prec == "fp64" else mg.FP32_SPLIT)
         psi0 = torch.from_numpy(c.psi0).cuda()
         psi = psi0.clone()
@@ -304,7 +316,7 @@ def run_dense13(args):
         ms = s0.elapsed_time(s1)
         res[prec] = {"ms": ms, "st": st, "psi": psi.clone(), "clk": clk.summary()}
         plan.close()
-    D, nv = c.dim, 64
+    D, nv = c.dim, args.states
     out = {}
     for prec, r in res.items():
         nmv = r["st"]["n_matvec"] / nv  # Leja iterations (all vectors advance together)
@@ -325,7 +337,8 @@ def run_dense13(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["fp32_split"]["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32-split(f64-equivalent)",
         "data": "synthetic",
-        "config": {"workload": "longrange_chain_13spins_dense_64states_cf4", "spins": 13, "dim": D, "states": nv,
+        "config": {"workload": f"longrange_chain_{c.nspins}spins_dense_{nv}states_cf4", "spins": c.nspins, "dim": D,
+                   "states": nv,
                    "h": c.h, "variant": args.variant, "l2": "inputs larger than L2: 2 x 1.07 GB dense terms"},
         "fp64_path": f64, "fp32_split_path": out["fp32_split"],
         "speedup_vs_fp64": round(out["fp32_split"]["steps_per_s"] / f64["steps_per_s"], 3),
@@ -526,6 +539,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--spins", type=int, default=13, help="dense13 only: chain length (profiling smaller cases)")
+    ap.add_argument("--states", type=int, default=64, help="dense13 only: states sharing H")
     ap.add_argument("--workload", choices=["xxz20", "dense13", "batch512", "adjoint16"], default="xxz20",
                     help="xxz20: the headline 20-spin chain; dense13: 13-spin dense chain, 64 states, FP64 vs split")
     args = ap.parse_args()

@@ -109,6 +109,10 @@ typedef struct {
  *   nvec [1]:     number of state vectors propagated together
  *   ctas [0]:     CTAs of the persistent kernel (0 = automatic)
  *   precision [MAGNUS_FP64]
+ *   barrier_timeout_s [0 = 4 s]: limit of every device-side wait at a grid barrier; a wait that runs
+ *                     out makes the call return MAGNUS_ETIMEOUT and leaves the context usable
+ *   test_skip_arrival [0]: testing only -- if nonzero, CTA 0 of the sparse/matrix-free propagation
+ *                     kernel leaves before its first grid barrier, so the other CTAs' waits run out
  */
 typedef struct {
   double tol_rel;
@@ -118,6 +122,9 @@ typedef struct {
   int32_t nvec;
   int32_t ctas;
   int32_t precision;
+  double barrier_timeout_s;
+  int32_t test_skip_arrival;
+  int32_t _pad;
 } magnus_options;
 
 typedef struct {

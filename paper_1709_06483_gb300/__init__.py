@@ -52,7 +52,8 @@ class Coeff(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("tol_rel", C.c_double), ("tol_abs", C.c_double), ("rho_max", C.c_double), ("m_max", C.c_int32),
-                ("nvec", C.c_int32), ("ctas", C.c_int32), ("precision", C.c_int32)]
+                ("nvec", C.c_int32), ("ctas", C.c_int32), ("precision", C.c_int32), ("barrier_timeout_s", C.c_double),
+                ("test_skip_arrival", C.c_int32), ("_pad", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -239,7 +240,7 @@ class Plan:
     """A Magnus/Leja plan: dim, terms H_k with drives f_k, Leja tolerance, vectors per call."""
 
     def __init__(self, dim, terms, drives, tol=1e-10, tol_abs=None, rho_max=4.0, m_max=100, nvec=1, ctas=0,
-                 precision=FP64, stream=None):
+                 precision=FP64, stream=None, barrier_timeout_s=0.0, test_skip_arrival=0):
         import torch
         L = load()
         assert len(terms) == len(drives)
@@ -249,7 +250,7 @@ class Plan:
         tarr = (Term * len(terms))(*[t.ctype() for t in terms])
         carr = (Coeff * len(drives))(*[d.ctype() for d in drives])
         opt = Options(float(tol), float(tol if tol_abs is None else tol_abs), float(rho_max), int(m_max), int(nvec),
-                      int(ctas), int(precision))
+                      int(ctas), int(precision), float(barrier_timeout_s), int(test_skip_arrival), 0)
         h = C.c_void_p()
         _check(L.magnus_plan_create(C.byref(h), self.dim, len(terms), tarr, carr, C.byref(opt),
                                     _stream_ptr(self.stream)))
@@ -358,7 +359,7 @@ class Batch:
         self.count = len(problems)
         self.dims = [int(p[0]) for p in problems]
         opt = Options(float(tol), float(tol if tol_abs is None else tol_abs), float(rho_max), int(m_max), 1,
-                      int(ctas), FP64)
+                      int(ctas), FP64, 0.0, 0, 0)
         h = C.c_void_p()
         code = L.magnus_batch_create(C.byref(h), self.count, arr, C.byref(opt), None)
         if code != OK:

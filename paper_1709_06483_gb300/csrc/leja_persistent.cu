@@ -112,6 +112,9 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_magnus_persistent(Persis
     double s = 0.0;
     for (int64_t r = lo + tid; r < hi; r += blockDim.x) s += cabs2(a.psi[base + r]);
     block_reduce_store(s, 0.0);
+    // testing hook: CTA 0 leaves before its first barrier (a participant that never arrives), so
+    // that every other CTA's bounded wait runs out
+    if (a.skip_arrival && b == 0) return;
     if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { fail(MAGNUS_ETIMEOUT); return; }
     if (warp == 0)
       for (int v = 0; v < nv; v++) {

@@ -120,6 +120,13 @@ magnus_status ensure_mlog(magnus_plan_t p, int64_t cap) {
   return MAGNUS_OK;
 }
 
+// bounded wait at a grid barrier: the plan's barrier_timeout_s, default 4 s (far above any
+// legitimate wait: one Leja iteration takes well under 100 ms)
+long long spin_limit(magnus_plan_t p) {
+  const double s = p->opt.barrier_timeout_s > 0.0 ? p->opt.barrier_timeout_s : 4.0;
+  return (long long)(s * 1e9);
+}
+
 // grid: nvec * gv blocks, all co-resident (cooperative launch)
 void choose_grid(magnus_plan_t p, int *grid, int *gv) {
   const int maxg = p->num_sms * std::max(1, p->max_blocks_per_sm);
@@ -186,7 +193,8 @@ magnus_status run_persistent(magnus_plan_t p, void *psi, int64_t nexp, magnus_st
   a.counters = p->counters;
   a.mlog = want_log ? p->mlog : nullptr;
   a.mlog_cap = want_log;
-  a.spin_limit_ns = 4000000000LL;  // 4 s: far above any legitimate wait at a barrier
+  a.spin_limit_ns = spin_limit(p);
+  a.skip_arrival = p->opt.test_skip_arrival;
   a.fam = p->fam;
   a.lbits = p->lbits;
   a.dlo = p->dlo;
@@ -272,6 +280,8 @@ magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms
   if (!(o.tol_rel >= 0.0) || !(o.tol_abs >= 0.0) || !(o.tol_rel + o.tol_abs > 0.0))
     return set_err(nullptr, MAGNUS_EINVAL, "tolerances must be >= 0 and not both 0");
   if (!(o.rho_max > 0.0)) return set_err(nullptr, MAGNUS_EINVAL, "rho_max must be > 0");
+  if (!(o.barrier_timeout_s >= 0.0) || o.barrier_timeout_s > 600.0)
+    return set_err(nullptr, MAGNUS_EINVAL, "barrier_timeout_s must be in [0, 600]");
   if (o.m_max < 2 || o.m_max > kMmaxLimit) return set_err(nullptr, MAGNUS_EINVAL, "m_max must be 2..%d", kMmaxLimit);
   if (o.nvec < 1 || o.nvec > 64) return set_err(nullptr, MAGNUS_EINVAL, "nvec must be 1..64");
   if (o.precision != MAGNUS_FP64 && o.precision != MAGNUS_FP32_SPLIT)
@@ -629,7 +639,7 @@ magnus_status magnus_adjoint_grad(magnus_plan_t p, const void *psi0, const void 
   a.partials = p->partials;
   a.bar = p->bar;
   a.counters = p->counters;
-  a.spin_limit_ns = 4000000000LL;
+  a.spin_limit_ns = spin_limit(p);
   a.fam = p->fam;
   a.lbits = p->lbits;
   a.dlo = p->dlo;
@@ -659,7 +669,7 @@ magnus_status magnus_adjoint_grad(magnus_plan_t p, const void *psi0, const void 
   g.partials = apart;
   g.bar = p->bar;
   g.counters = p->counters;
-  g.spin_limit_ns = 4000000000LL;
+  g.spin_limit_ns = spin_limit(p);
   g.dlo = p->dlo;
   g.dhi = p->dhi;
 

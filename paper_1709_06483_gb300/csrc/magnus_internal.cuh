@@ -128,6 +128,7 @@ struct PersistArgs {
   int *mlog;               // [capacity] degrees of the substeps (may be null)
   long long mlog_cap;
   long long spin_limit_ns; // bounded waits
+  int skip_arrival;        // testing: CTA 0 leaves before its first grid barrier
   int fam;                 // operator family: FAM_GENERIC, FAM_CSR (every term CSR), FAM_MF (XXZ + field)
   int lbits;               // FAM_MF: split of the basis index for the diagonal tables
   const double *dlo;       // FAM_MF: diagonal of H_xxz from the low lbits+1 bits   [2^(lbits+1)]

@@ -234,3 +234,20 @@ def test_workload2_full_size_first_steps(mg, wl2, kind, variant):
     ref, mlog = cache[variant]
     assert np.array_equal(st["m_log"], mlog)
     assert rel(psi.cpu().numpy(), ref) < REL_TOL
+
+
+def test_barrier_timeout_is_reported_and_context_survives(mg):
+    """A grid-barrier wait that nothing satisfies (CTA 0 leaves before arriving) runs out after the
+    plan's short limit; the call returns MAGNUS_ETIMEOUT and the next plan runs normally."""
+    c = mi.xxz_chain(27, 12, 0.01, 4)
+    plan = mg.Plan(c.dim, chain_terms(mg, c, "csr"), drives_gpu(mg, c), ctas=8, barrier_timeout_s=0.05,
+                   test_skip_arrival=1)
+    with pytest.raises(mg.MagnusError) as e:
+        plan.propagate(cuda(c.psi0), 0.0, c.h, c.nsteps, "CF4")
+    assert e.value.code == mg.ETIMEOUT
+    plan.close()
+    ok = mg.Plan(c.dim, chain_terms(mg, c, "csr"), drives_gpu(mg, c), ctas=8)
+    psi = cuda(c.psi0)
+    ok.propagate(psi, 0.0, c.h, c.nsteps, "CF4")
+    ref = oracle_problem(c).propagate(c.psi0, 0.0, c.h, c.nsteps, "CF4")
+    assert rel(psi.cpu().numpy(), ref) < REL_TOL
