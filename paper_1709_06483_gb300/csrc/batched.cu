@@ -169,8 +169,8 @@ __global__ void __launch_bounds__(BS) k_batched(BatchArgs A) {
             double2 pr = (j == 1) ? cmul(d0, wr) : nxt[r];
             pr = cfma(dj, y, pr);
             nxt[r] = pr;
-            sw += cabs2(y);
-            sp += cabs2(pr);
+            sw = fma(y.x, y.x, fma(y.y, y.y, sw));
+            sp = fma(pr.x, pr.x, fma(pr.y, pr.y, sp));
           }
           block_sums(sw, sp);
           const double ej = sqrt(cabs2(dj)) * sqrt(s_tot[0]);

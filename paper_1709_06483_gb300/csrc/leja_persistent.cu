@@ -38,6 +38,7 @@ constexpr int kBlock = 256;
 constexpr int kMinBlocks = MG_PERSIST_MIN_BLOCKS;  // resident CTAs per SM the register budget targets
 constexpr int kMaxVec = 64;
 
+
 // --------------------------------------------------------------------- kernel
 template <int FAM>
 __global__ void __launch_bounds__(kBlock, kMinBlocks) k_magnus_persistent(PersistArgs a) {
@@ -170,6 +171,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_magnus_persistent(Persis
         double sw = 0.0, sp = 0.0;
         if (mine) {
           for (int64_t r = lo + tid; r < hi; r += blockDim.x) {
+
             double2 y, wr;
             if (R.mode == MODE_M4) {
               y = make_double2(0.0, 0.0);
@@ -194,8 +196,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_magnus_persistent(Persis
             double2 pr = (j == 1) ? cmul(d0, wr) : nxt[base + r];
             pr = cfma(dj, y, pr);
             nxt[base + r] = pr;
-            sw += cabs2(y);
-            sp += cabs2(pr);
+            sw = fma(y.x, y.x, fma(y.y, y.y, sw));
+            sp = fma(pr.x, pr.x, fma(pr.y, pr.y, sp));
           }
         }
         block_reduce_store(sw, sp);

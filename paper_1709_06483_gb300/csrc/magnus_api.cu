@@ -295,6 +295,7 @@ magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms
       case MAGNUS_TERM_CSR:
         if (!t.rowptr || !t.col || !t.val || t.nnz < 0)
           return set_err(nullptr, MAGNUS_EINVAL, "term %d: CSR arrays missing", k);
+        if (((uintptr_t)t.val) % 16) return set_err(nullptr, MAGNUS_EINVAL, "term %d: CSR values must be 16-byte aligned", k);
         break;
       case MAGNUS_TERM_DENSE:
         if (!t.val) return set_err(nullptr, MAGNUS_EINVAL, "term %d: dense matrix missing", k);

@@ -99,6 +99,23 @@ static __device__ __forceinline__ double2 fieldx_row(int n, const double2 *x, in
   return acc;
 }
 
+// coef * sum_i x[r ^ bit_i] accumulated with FMAs: on GB300 a DFMA with register operands issues
+// faster than a DADD (measured 0.60 vs 0.51 T/s), and the weight costs no extra multiply.
+static __device__ __forceinline__ double2 fieldx_row_scaled(int n, double coef, const double2 *x, int64_t r,
+                                                           double2 acc) {
+  int b = 0;
+  for (; b + 4 <= n; b += 4) {
+    const double2 v0 = ldv(x + (r ^ ((int64_t)1 << b))), v1 = ldv(x + (r ^ ((int64_t)2 << b))),
+                  v2 = ldv(x + (r ^ ((int64_t)4 << b))), v3 = ldv(x + (r ^ ((int64_t)8 << b)));
+    acc = rfma(coef, v0, acc);
+    acc = rfma(coef, v1, acc);
+    acc = rfma(coef, v2, acc);
+    acc = rfma(coef, v3, acc);
+  }
+  for (; b < n; b++) acc = rfma(coef, ldv(x + (r ^ ((int64_t)1 << b))), acc);
+  return acc;
+}
+
 static __device__ __forceinline__ double2 term_row_generic(const Term &t, const double2 *x, int64_t r) {
   switch (t.kind) {
     case MAGNUS_TERM_CSR: return csr_row(t, x, r);
@@ -165,8 +182,7 @@ struct Op {
                                                   int64_t r, double2 &xr) {
     if (FAM == FAM_MF) {
       double2 y = mf_xxz_row(c, c.jb, R.bg[0], shift, x, r, xr);
-      const double2 f = fieldx_row(c.n, x, r);
-      return rfma(R.bg[1], f, y);
+      return fieldx_row_scaled(c.n, R.bg[1], x, r, y);
     }
     double2 y = make_double2(0.0, 0.0);
     for (int k = 0; k < c.nt; k++) y = rfma(R.bg[k], term(c, k, x, r), y);
