@@ -404,7 +404,7 @@ def run_batch512(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"batch_512_xxz_chains_8to14spins_{args.storage}_{args.variant.lower()}",
                    "chains": len(chains), "rows": rows, "nnz": nnz, "h": 0.01, "variant": args.variant,
-                   "cta_size": st["block"]},
+                   "cta_size": st["block"], "cluster_size": st["cluster"]},
         "chain_steps_per_s": round(len(chains) * args.steps / (gms / 1e3), 1),
         "leja_iterations": st["n_matvec"], "matvec_gbs": round(gbs, 1),
         "roofline": {"bound": "hbm" if args.storage == "csr" else "alu", "kernel": "k_batched",

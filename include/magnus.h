@@ -257,7 +257,7 @@ typedef struct {
   int64_t m_log_cap_per_item;
   double graph_ms;              /* device time of the replayed graph (setup + persistent kernel)    */
   int32_t block;                /* CTA size the autotuner chose                                     */
-  int32_t _pad;
+  int32_t cluster;              /* CTAs per thread-block cluster (one problem per cluster)          */
 } magnus_batch_stats;
 
 typedef struct magnus_batch_s *magnus_batch_t;
@@ -268,7 +268,9 @@ typedef struct magnus_batch_s *magnus_batch_t;
  * launch: every CTA takes whole problems from a work queue, largest first, and synchronises only
  * within itself.  Computes, once, the Gershgorin enclosure of every term and the Leja points.
  * opt: as for plans, with nvec = 1 (one state per problem) and precision MAGNUS_FP64; ctas > 0
- * caps the CTAs, ctas < 0 forces the CTA size -ctas (128, 256, 512 or 1024) instead of the autotuner.
+ * caps the CTAs; ctas < 0 replaces the autotuner: -ctas = bs + 65536 * cs forces the CTA size bs
+ * (128, 256, 512 or 1024) and the cluster size cs (1, 2 or 4; 0 means 1).
+ * Each problem runs on one thread-block cluster of cs CTAs that split its rows.
  * The batch uses its own CUDA stream (the stream argument is ignored).  Errors: EINVAL, ENOMEM, ECUDA.
  */
 MAGNUS_API magnus_status magnus_batch_create(magnus_batch_t *batch, int32_t count, const magnus_batch_item *items,
@@ -276,8 +278,8 @@ MAGNUS_API magnus_status magnus_batch_create(magnus_batch_t *batch, int32_t coun
 
 /*
  * psi[i] (device complex128 [dim_i], in/out; psi is a HOST array of count device pointers) <- nsteps
- * Magnus steps of size h from t0 for every problem.  The first call times the candidate CTA sizes on
- * copies of the states (2 steps each) and keeps the fastest; the setup launches and the persistent
+ * Magnus steps of size h from t0 for every problem.  The first call times the candidate CTA sizes
+ * x cluster sizes on copies of the states (2 steps each) and keeps the fastest; the setup launches and the persistent
  * kernel are captured into a CUDA graph once per (t0, h, nsteps, variant) and replayed.  Synchronous.
  * Errors: EINVAL, ENOCONV, ENONFINITE, ECUDA (the first error of any problem).
  */

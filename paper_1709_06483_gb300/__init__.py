@@ -72,7 +72,7 @@ class BatchStats(C.Structure):
     _fields_ = [("n_exp", C.c_int64), ("n_substeps", C.c_int64), ("n_matvec", C.c_int64),
                 ("n_termapply", C.c_int64), ("max_m", C.c_int32), ("status", C.c_int32),
                 ("m_log", C.POINTER(C.c_int32)), ("m_log_cap_per_item", C.c_int64), ("graph_ms", C.c_double),
-                ("block", C.c_int32), ("_pad", C.c_int32)]
+                ("block", C.c_int32), ("cluster", C.c_int32)]
 
 
 _lib = None
@@ -393,7 +393,7 @@ class Batch:
         if rc != OK:
             raise MagnusError(rc, L.magnus_batch_last_error(self._h).decode(errors="replace"))
         out = {k: getattr(st, k) for k in ("n_exp", "n_substeps", "n_matvec", "n_termapply", "max_m", "status",
-                                           "graph_ms", "block")}
+                                           "graph_ms", "block", "cluster")}
         if log is not None:
             out["m_log"] = log
         return out

@@ -15,9 +15,13 @@
 #include <string>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "magnus_internal.cuh"
 #include "persist_common.cuh"
 #include "rows.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace mg {
 
@@ -52,19 +56,30 @@ namespace {
 
 using namespace rows;
 
+// One problem per thread-block cluster: the cluster's CTAs split the problem's rows, exchange their
+// partial norms through distributed shared memory and synchronise with the hardware cluster
+// barrier (release/acquire at cluster scope), so a large chain runs on several SMs at once.
+// Cluster size 1 is the plain CTA-per-problem case.
 template <int FAM, int BS>
 __global__ void __launch_bounds__(BS) k_batched(BatchArgs A) {
-  __shared__ int s_item;
+  __shared__ int s_next;            // rank 0: the problem index taken from the queue
+  __shared__ int s_item;            // every CTA: its copy of that index
   __shared__ BatchItem sI;
   __shared__ Term sT[kMaxTerms];
   __shared__ ExpRec sR;
   __shared__ double s_jb[kMaxSpins], s_j2[kMaxSpins];
   __shared__ double s_red[2][BS / 32];
+  __shared__ double s_part[2][2];   // this CTA's partial sums, two slots (alternating reductions)
   __shared__ double s_tot[2];
 
+  cg::cluster_group cl = cg::this_cluster();
+  const unsigned crank = cl.block_rank(), csize = cl.num_blocks();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  // block-wide sums of two values, identical in every thread afterwards (fixed order)
-  auto block_sums = [&](double x0, double x1) {
+  unsigned slot = 0;
+  // sums of two values over all threads of the cluster, identical in every thread afterwards
+  // (fixed order: warps, then CTAs by rank); the cluster barrier also publishes this CTA's
+  // vector writes to the other CTAs of the cluster
+  auto cluster_sums = [&](double x0, double x1) {
     x0 = warp_sum(x0);
     x1 = warp_sum(x1);
     if (lane == 0) { s_red[0][warp] = x0; s_red[1][warp] = x1; }
@@ -72,22 +87,39 @@ __global__ void __launch_bounds__(BS) k_batched(BatchArgs A) {
     if (tid == 0) {
       double y0 = 0.0, y1 = 0.0;
       for (int w = 0; w < BS / 32; w++) { y0 += s_red[0][w]; y1 += s_red[1][w]; }
+      s_part[slot][0] = y0;
+      s_part[slot][1] = y1;
+    }
+    cl.sync();
+    if (tid == 0) {
+      double y0 = 0.0, y1 = 0.0;
+      for (unsigned q = 0; q < csize; q++) {
+        const double *rp = cl.map_shared_rank(&s_part[slot][0], q);
+        y0 += rp[0];
+        y1 += rp[1];
+      }
       s_tot[0] = y0;
       s_tot[1] = y1;
     }
     __syncthreads();
+    slot ^= 1u;
   };
 
   for (;;) {
-    __syncthreads();
-    if (tid == 0) s_item = (int)atomicAdd(A.next, 1u);
-    __syncthreads();
+    cl.sync();
+    if (crank == 0 && tid == 0) s_next = (int)atomicAdd(A.next, 1u);
+    cl.sync();
+    if (tid == 0) s_item = *cl.map_shared_rank(&s_next, 0);
+    cl.sync();  // every CTA has read rank 0's index before any CTA may leave the kernel
     const int q = s_item;
     if (q >= A.count) break;
     if (tid == 0) sI = A.items[A.order[q]];
     __syncthreads();
     const int64_t D = sI.dim;
     const int nt = sI.nterms;
+    // this CTA's rows: whole warps of consecutive rows
+    const int64_t rows_per = (((D + csize - 1) / csize) + 31) & ~(int64_t)31;
+    const int64_t lo = min(D, (int64_t)crank * rows_per), hi = min(D, lo + rows_per);
     for (int i = tid; i < nt * (int)sizeof(Term) / 4; i += BS)
       reinterpret_cast<int *>(sT)[i] = reinterpret_cast<const int *>(sI.terms)[i];
     __syncthreads();
@@ -105,8 +137,8 @@ __global__ void __launch_bounds__(BS) k_batched(BatchArgs A) {
       for (int p = 1 + tid; p < cx.n; p += BS) s_j2[p - 1] = 2.0 * sT[0].J[cx.n - p - 1];
 
     double s0 = 0.0;
-    for (int64_t r = tid; r < D; r += BS) s0 += cabs2(sI.psi[r]);
-    block_sums(s0, 0.0);
+    for (int64_t r = lo + tid; r < hi; r += BS) s0 += cabs2(sI.psi[r]);
+    cluster_sums(s0, 0.0);
     double vn = sqrt(s_tot[0]);
 
     double2 *cur = sI.psi, *nxt = sI.alt;
@@ -124,8 +156,8 @@ __global__ void __launch_bounds__(BS) k_batched(BatchArgs A) {
       const double2 *d = sI.dd + e * (int64_t)(A.m_max + 1);
       if (!(R.gamma > 0.0)) {
         const double2 ph = d[0];
-        for (int64_t r = tid; r < D; r += BS) nxt[r] = cmul(ph, cur[r]);
-        __syncthreads();
+        for (int64_t r = lo + tid; r < hi; r += BS) nxt[r] = cmul(ph, cur[r]);
+        cl.sync();
         double2 *tmp = cur; cur = nxt; nxt = tmp;
         continue;
       }
@@ -139,12 +171,12 @@ __global__ void __launch_bounds__(BS) k_batched(BatchArgs A) {
           const double shift = R.cg + A.xi[j - 1];
           const double2 dj = d[j];
           if (R.mode == MODE_M4) {
-            for (int64_t r = tid; r < D; r += BS)
+            for (int64_t r = lo + tid; r < hi; r += BS)
               for (int k = 0; k < nt; k++) sI.u[(size_t)k * D + r] = Op<FAM>::term(cx, k, src, r);
-            __syncthreads();
+            cl.sync();
           }
           double sw = 0.0, sp = 0.0;
-          for (int64_t r = tid; r < D; r += BS) {
+          for (int64_t r = lo + tid; r < hi; r += BS) {
             double2 y, wr;
             if (R.mode == MODE_M4) {
               y = make_double2(0.0, 0.0);
@@ -160,7 +192,7 @@ __global__ void __launch_bounds__(BS) k_batched(BatchArgs A) {
               }
               y.x += z.y;
               y.y -= z.x;
-              wr = src[r];
+              wr = ldv(src + r);
               y = rfma(-shift, wr, y);
             } else {
               y = Op<FAM>::combo(cx, R, shift, src, r, wr);
@@ -172,7 +204,7 @@ __global__ void __launch_bounds__(BS) k_batched(BatchArgs A) {
             sw = fma(y.x, y.x, fma(y.y, y.y, sw));
             sp = fma(pr.x, pr.x, fma(pr.y, pr.y, sp));
           }
-          block_sums(sw, sp);
+          cluster_sums(sw, sp);
           const double ej = sqrt(cabs2(dj)) * sqrt(s_tot[0]);
           pn = sqrt(s_tot[1]);
           if (!isfinite(ej) || !isfinite(pn)) { status = MAGNUS_ENONFINITE; m = j; break; }
@@ -180,7 +212,7 @@ __global__ void __launch_bounds__(BS) k_batched(BatchArgs A) {
           ep = ej;
         }
         if (status == MAGNUS_OK && m == 0) { status = MAGNUS_ENOCONV; m = A.m_max; }
-        if (tid == 0) {
+        if (crank == 0 && tid == 0) {
           atomicAdd((unsigned long long *)&A.counters->n_matvec, (unsigned long long)m);
           atomicAdd((unsigned long long *)&A.counters->n_termapply,
                     (unsigned long long)m * nt * (R.mode == MODE_M4 ? 2 : 1));
@@ -190,15 +222,14 @@ __global__ void __launch_bounds__(BS) k_batched(BatchArgs A) {
         }
         sub_counter++;
         vn = pn;
-        __syncthreads();
         double2 *tmp = cur; cur = nxt; nxt = tmp;
       }
-      if (tid == 0) atomicAdd((unsigned long long *)&A.counters->n_exp, 1ULL);
+      if (crank == 0 && tid == 0) atomicAdd((unsigned long long *)&A.counters->n_exp, 1ULL);
     }
     if (status != MAGNUS_OK) {
-      if (tid == 0) atomicCAS(&A.counters->status, 0, status);
+      if (crank == 0 && tid == 0) atomicCAS(&A.counters->status, 0, status);
     } else if (cur != sI.psi) {
-      for (int64_t r = tid; r < D; r += BS) sI.psi[r] = cur[r];
+      for (int64_t r = lo + tid; r < hi; r += BS) sI.psi[r] = cur[r];
     }
   }
 }
@@ -262,6 +293,7 @@ struct magnus_batch_s {
   int64_t g_nsteps = -1;
   int g_variant = 0, g_bs = 0, g_mlog = 0;
   int tuned_bs = 0;
+  int tuned_cs = 1;
   std::vector<double> tune_ms;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::string err;
@@ -307,7 +339,7 @@ void batch_free(magnus_batch_t b) {
   delete b;
 }
 
-magnus_status enqueue_run(magnus_batch_t b, int variant, double t0, double h, int64_t nsteps, int bs,
+magnus_status enqueue_run(magnus_batch_t b, int variant, double t0, double h, int64_t nsteps, int bs, int cs,
                           const BatchItem *items_dev) {
   const int64_t nexp = nsteps * exps_per_step(variant);
   for (int i = 0; i < b->count; i++)
@@ -332,9 +364,22 @@ magnus_status enqueue_run(magnus_batch_t b, int variant, double t0, double h, in
   BTRY(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel_for(b->fam, bs), bs, 0));
   int grid = b->num_sms * std::max(1, per_sm);
   if (b->opt.ctas > 0) grid = std::min(grid, b->opt.ctas);
-  grid = std::min(grid, b->count);
+  grid = std::min(grid, b->count * cs);
+  grid = std::max(cs, grid - grid % cs);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(bs);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = b->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   void *args[] = {&A};
-  BTRY(b, cudaLaunchKernel(batched_kernel_for(b->fam, bs), dim3(grid), dim3(bs), args, 0, b->stream));
+  BTRY(b, cudaLaunchKernelExC(&cfg, batched_kernel_for(b->fam, bs), args));
   return MAGNUS_OK;
 }
 
@@ -590,7 +635,8 @@ MAGNUS_API magnus_status magnus_batch_propagate(magnus_batch_t b, void *const *p
   // autotune the CTA size once: time each candidate on copies of the states, first steps only
   if (!b->tuned_bs) {
     if (b->opt.ctas < 0) {
-      b->tuned_bs = -b->opt.ctas;  // forced CTA size (testing)
+      b->tuned_bs = (-b->opt.ctas) & 0xffff;            // forced CTA size (testing)
+      b->tuned_cs = std::max(1, (-b->opt.ctas) >> 16);  // and cluster size in the high bits
     } else {
       size_t total = 0;
       for (int i = 0; i < b->count; i++) total += (size_t)b->dims[i];
@@ -609,30 +655,32 @@ MAGNUS_API magnus_status magnus_batch_propagate(magnus_batch_t b, void *const *p
       BTRY(b, balloc(b, &tdev, b->count));
       BTRY(b, cudaMemcpyAsync(tdev, ti.data(), sizeof(BatchItem) * b->count, cudaMemcpyHostToDevice, b->stream));
       const int cands[4] = {128, 256, 512, 1024};
+      const int clusters[3] = {1, 2, 4};
       const int64_t tsteps = std::min<int64_t>(nsteps, 2);
       double best = 1e30;
       b->tune_ms.clear();
-      for (int bs : cands) {
-        BTRY(b, cudaEventRecord(b->ev0, b->stream));
-        magnus_status s = enqueue_run(b, variant, t0, h, tsteps, bs, tdev);
-        if (s != MAGNUS_OK) return s;
-        BTRY(b, cudaEventRecord(b->ev1, b->stream));
-        BTRY(b, cudaStreamSynchronize(b->stream));
-        float ms = 0.f;
-        BTRY(b, cudaEventElapsedTime(&ms, b->ev0, b->ev1));
-        b->tune_ms.push_back(ms);
-        if (ms < best) { best = ms; b->tuned_bs = bs; }
-      }
+      for (int cs : clusters)
+        for (int bs : cands) {
+          BTRY(b, cudaEventRecord(b->ev0, b->stream));
+          magnus_status s = enqueue_run(b, variant, t0, h, tsteps, bs, cs, tdev);
+          if (s != MAGNUS_OK) return s;
+          BTRY(b, cudaEventRecord(b->ev1, b->stream));
+          BTRY(b, cudaStreamSynchronize(b->stream));
+          float ms = 0.f;
+          BTRY(b, cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+          b->tune_ms.push_back(ms);
+          if (ms < best) { best = ms; b->tuned_bs = bs; b->tuned_cs = cs; }
+        }
     }
   }
   // graph of (setup launches + persistent kernel), captured once per (t0, h, nsteps, variant)
   const bool same = b->graph && b->g_t0 == t0 && b->g_h == h && b->g_nsteps == nsteps && b->g_variant == variant &&
-                    b->g_bs == b->tuned_bs && b->g_mlog == want_log;
+                    b->g_bs == b->tuned_bs && b->g_mlog == want_log;  // tuning happens once, before any graph
   if (!same) {
     if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
     cudaGraph_t g = nullptr;
     BTRY(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-    magnus_status s = enqueue_run(b, variant, t0, h, nsteps, b->tuned_bs, b->items_dev);
+    magnus_status s = enqueue_run(b, variant, t0, h, nsteps, b->tuned_bs, b->tuned_cs, b->items_dev);
     cudaError_t ce = cudaStreamEndCapture(b->stream, &g);
     if (s != MAGNUS_OK) { if (g) cudaGraphDestroy(g); return s; }
     BTRY(b, ce);
@@ -658,6 +706,7 @@ MAGNUS_API magnus_status magnus_batch_propagate(magnus_batch_t b, void *const *p
     stats->status = c.status;
     stats->graph_ms = ms;
     stats->block = b->tuned_bs;
+    stats->cluster = b->tuned_cs;
     if (want_log) {
       std::vector<int> tmp((size_t)b->count * b->mlog_cap);
       BTRY(b, cudaMemcpy(tmp.data(), b->mlog, sizeof(int) * tmp.size(), cudaMemcpyDeviceToHost));

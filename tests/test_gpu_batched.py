@@ -62,18 +62,20 @@ def test_batch_matches_oracle(mg, small_chains, kind, variant):
         ref, mlog = oracle_run(c, 0.0, c.h, c.nsteps, variant)
         assert rel(psis[i].cpu().numpy(), ref) < REL_TOL, i
         assert np.array_equal(st["m_log"][i, :mlog.size], mlog), i
-    assert st["block"] in (128, 256, 512, 1024)
+    assert st["block"] in (128, 256, 512, 1024) and st["cluster"] in (1, 2, 4)
 
 
+@pytest.mark.parametrize("cs", [1, 2, 4])
 @pytest.mark.parametrize("bs", [128, 256, 512, 1024])
-def test_every_cta_size(mg, small_chains, bs):
+def test_every_cta_and_cluster_size(mg, small_chains, bs, cs):
+    """Each problem on a cluster of cs CTAs of bs threads (rows split across the cluster)."""
     chains = small_chains[:6]
-    B = mg.Batch(problems(mg, chains, "csr"), ctas=-bs)
+    B = mg.Batch(problems(mg, chains, "csr" if bs != 512 else "mfree"), ctas=-(bs + 65536 * cs))
     psis = [torch.from_numpy(c.psi0.copy()).cuda() for c in chains]
-    st = B.propagate(psis, 0.0, chains[0].h, 5, "CF4")
-    assert st["block"] == bs
+    st = B.propagate(psis, 0.0, chains[0].h, 5, "CF4" if cs != 2 else "M4")
+    assert st["block"] == bs and st["cluster"] == cs
     for i, c in enumerate(chains):
-        ref, _ = oracle_run(c, 0.0, c.h, 5, "CF4")
+        ref, _ = oracle_run(c, 0.0, c.h, 5, "CF4" if cs != 2 else "M4")
         assert rel(psis[i].cpu().numpy(), ref) < REL_TOL
 
 
