@@ -63,8 +63,8 @@ typedef enum {
 
 typedef enum {
   MAGNUS_FP64 = 0,       /* plain FP64 matvecs                                                     */
-  MAGNUS_FP32_SPLIT = 1, /* reserved: FP32 hi/lo split matvecs, FP64 accumulation                  */
-  MAGNUS_TF32_SPLIT = 2  /* reserved: tensor-core split matvecs                                    */
+  MAGNUS_FP32_SPLIT = 1,   /* dense terms: FP32 (hi, lo) split matvecs, FP64 accumulation          */
+  MAGNUS_TENSOR_SLICED = 2 /* dense terms: exact bf16 digit products on the tensor cores           */
 } magnus_precision;
 
 /*
@@ -108,7 +108,15 @@ typedef struct {
  *   m_max [100]:  largest Leja degree per substep (at most 255)
  *   nvec [1]:     number of state vectors propagated together
  *   ctas [0]:     CTAs of the persistent kernel (0 = automatic)
- *   precision [MAGNUS_FP64]
+ *   precision [MAGNUS_FP64]: arithmetic of the dense-term matvecs.  MAGNUS_FP32_SPLIT and
+ *                     MAGNUS_TENSOR_SLICED need real-valued dense terms (the drive may add
+ *                     MAGNUS_TERM_FIELD_X terms); MAGNUS_TENSOR_SLICED also needs dim a multiple of
+ *                     128.  MAGNUS_TENSOR_SLICED cuts every dense row (row scale 2^e_r) and every
+ *                     state component column (scale 2^e_c) into 5 signed 7-bit digits, forms the 15
+ *                     digit products of weight >= 2^-42 on the bf16 tensor cores (exact in FP32 over
+ *                     128 columns) and carries their sums in int64; the neglected part of one output
+ *                     entry is below dim * 2^-32 * max_j |H_rj| * max_j |w_j| (not part of the
+ *                     paper, which computes in FP64 only).
  *   barrier_timeout_s [0 = 4 s]: limit of every device-side wait at a grid barrier; a wait that runs
  *                     out makes the call return MAGNUS_ETIMEOUT and leaves the context usable
  *   test_skip_arrival [0]: testing only -- if nonzero, CTA 0 of the sparse/matrix-free propagation

@@ -21,7 +21,7 @@ OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ENONFINITE, ETIMEOUT = range(7)
 M4, CF4, CF4_3, M2 = 1, 2, 3, 4
 VARIANTS = {"M4": M4, "CF4": CF4, "CF4_3": CF4_3, "M2": M2}
 TERM_CSR, TERM_DENSE, TERM_XXZ, TERM_FIELD_X = 0, 1, 2, 3
-FP64, FP32_SPLIT, TF32_SPLIT = 0, 1, 2
+FP64, FP32_SPLIT, TENSOR_SLICED = 0, 1, 2
 
 # Every symbol the header declares (checked by the CPU test suite).
 EXPORTS = (

@@ -15,6 +15,8 @@
 // reads the same totals and takes the same decisions.
 #include <math.h>
 
+#include <cuda_bf16.h>
+
 #include "magnus_internal.cuh"
 #include "persist_common.cuh"
 
@@ -185,9 +187,165 @@ __device__ __forceinline__ double2 fieldx_at(int n, const double2 *x, int64_t r)
   return acc;
 }
 
+// ----------------------------------------------------------------- sliced tensor-core GEMM
+// Exact-slice products on the bf16 tensor cores (MAGNUS_TENSOR_SLICED).  Every row of H and every
+// column of the vectors is scaled by a power of two into (-1, 1) and cut into kSl signed 7-bit
+// integer digits (|digit| <= 128, exact in bf16):  x = 2^e sum_t D_t 2^{-7t} + O(2^{e-7 kSl}).
+// The products of digit pairs with t + u <= kSl + 1 are summed on the tensor cores in FP32; within
+// a K-chunk of kChunk columns every partial sum is an integer below 2^24, so FP32 holds it exactly.
+// Chunk sums are carried in int64 (shifted to a common scale), and converted to FP64 once per tile.
+constexpr int kSl = 5;          // digits per value (35 bits)
+constexpr int kChunk = 128;     // exact FP32 accumulation length: 5 pairs x 128 x 2^14 < 2^24
+constexpr int kKS = 32;         // columns per shared-memory stage
+constexpr int kRowPad = 40;     // bf16 per staged row (32 + 8: conflict-free ldmatrix)
+constexpr int kTcCols = 2 * kVecMax;  // real columns: (re, im) of every vector
+struct TcSmem {
+  __nv_bfloat16 a[kSl][kTM][kRowPad];
+  __nv_bfloat16 b[kSl][kTcCols][kRowPad];
+};
+constexpr size_t kTcSmemBytes = sizeof(TcSmem) > sizeof(double) * kTM * kTcCols ? sizeof(TcSmem)
+                                                                                : sizeof(double) * kTM * kTcCols;
+
+__device__ __forceinline__ void ldsm_x4(unsigned (&r)[4], const void *p) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a));
+}
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+  asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+               "{%0,%1,%2,%3};"
+               : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+               : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// y[i][q] += coef * sum_j H[r0 + 2 ty + i][j] W[v = tx + 16 q][j] for the (ty, tx) output layout.
+// hs: digits of H [kSl][D][D], eh: row exponents; ws: digits of the vectors [kSl][2 nv][D] (column
+// c = 2 v + {0: re, 1: im}), ew: column exponents.  Tile 32 rows x 128 columns, 8 warps of 16 x 32.
+__device__ void gemm_tile_sliced(unsigned char *smem, const __nv_bfloat16 *hs, const int *eh, const __nv_bfloat16 *ws,
+                                 const int *ew, double coef, int64_t D, int nv, int64_t r0, double2 (&y)[2][4]) {
+  TcSmem &S = *reinterpret_cast<TcSmem *>(smem);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wr = warp >> 2, wc = warp & 3;  // warp rows wr*16, columns wc*32
+  const int ncols = 2 * nv;
+  long long sum64[4][4];
+#pragma unroll
+  for (int nt = 0; nt < 4; nt++)
+#pragma unroll
+    for (int i = 0; i < 4; i++) sum64[nt][i] = 0;
+  const size_t sl_h = (size_t)D * D, sl_w = (size_t)ncols * D;
+  for (int64_t c0 = 0; c0 < D; c0 += kChunk) {
+    float acc[kSl][4][4];
+#pragma unroll
+    for (int g = 0; g < kSl; g++)
+#pragma unroll
+      for (int nt = 0; nt < 4; nt++)
+#pragma unroll
+        for (int i = 0; i < 4; i++) acc[g][nt][i] = 0.f;
+    for (int64_t k0 = c0; k0 < c0 + kChunk; k0 += kKS) {
+      __syncthreads();
+      // stage digits: A rows r0..r0+31, B columns 0..127, columns k0..k0+31 (16-byte pieces)
+      for (int i = tid; i < kSl * kTM * 4; i += kDBlock) {
+        const int t = i / (kTM * 4), rr = (i / 4) % kTM, piece = i % 4;
+        cp_async16(&S.a[t][rr][piece * 8], hs + t * sl_h + (size_t)(r0 + rr) * D + k0 + piece * 8);
+      }
+      for (int i = tid; i < kSl * kTcCols * 4; i += kDBlock) {
+        const int u = i / (kTcCols * 4), cc = (i / 4) % kTcCols, piece = i % 4;
+        if (cc < ncols) cp_async16(&S.b[u][cc][piece * 8], ws + u * sl_w + (size_t)cc * D + k0 + piece * 8);
+        else *reinterpret_cast<uint4 *>(&S.b[u][cc][piece * 8]) = make_uint4(0, 0, 0, 0);
+      }
+      cp_async_wait_all();
+      __syncthreads();
+#pragma unroll
+      for (int ks = 0; ks < kKS; ks += 16) {
+        unsigned af[kSl][4];
+#pragma unroll
+        for (int t = 0; t < kSl; t++)
+          ldsm_x4(af[t], &S.a[t][wr * 16 + (lane & 15)][ks + (lane >> 4) * 8]);
+#pragma unroll
+        for (int np = 0; np < 2; np++) {  // n-tile pairs (2 np, 2 np + 1)
+          unsigned bf[kSl][4];
+#pragma unroll
+          for (int u = 0; u < kSl; u++)
+            ldsm_x4(bf[u], &S.b[u][wc * 32 + np * 16 + (lane & 7) + ((lane >> 4) << 3)][ks + ((lane >> 3) & 1) * 8]);
+#pragma unroll
+          for (int t = 0; t < kSl; t++)
+#pragma unroll
+            for (int u = 0; u < kSl; u++) {
+              if (t + u > kSl - 1) continue;  // keep digit pairs with (t+1)+(u+1) <= kSl + 1
+              mma_bf16(acc[t + u][2 * np], af[t], bf[u][0], bf[u][1]);
+              mma_bf16(acc[t + u][2 * np + 1], af[t], bf[u][2], bf[u][3]);
+            }
+        }
+      }
+    }
+    // exact integer chunk sums -> int64 at the common scale 2^{-7 (kSl + 1)}
+#pragma unroll
+    for (int g = 0; g < kSl; g++)
+#pragma unroll
+      for (int nt = 0; nt < 4; nt++)
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+          sum64[nt][i] += (long long)__float2int_rn(acc[g][nt][i]) << (7 * (kSl - 1 - g));
+  }
+  // scale back: value = sum64 * 2^{e_row + e_col - 7 (kSl + 1)}; stage through shared memory into
+  // the (ty, tx) layout of the FP64 epilogue
+  __syncthreads();
+  double *Y = reinterpret_cast<double *>(smem);  // [kTM][kTcCols]
+#pragma unroll
+  for (int nt = 0; nt < 4; nt++)
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+      const int row = wr * 16 + (lane >> 2) + (i >= 2 ? 8 : 0);
+      const int col = wc * 32 + nt * 8 + (lane & 3) * 2 + (i & 1);
+      double v = 0.0;
+      if (col < ncols) v = ldexp((double)sum64[nt][i], eh[r0 + row] + ew[col] - 7 * (kSl + 1));
+      Y[row * kTcCols + col] = v;
+    }
+  __syncthreads();
+  const int ty = tid >> 4, tx = tid & 15;
+#pragma unroll
+  for (int i = 0; i < 2; i++)
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int v = tx + 16 * q;
+      if (v < nv) {
+        const int row = 2 * ty + i;
+        y[i][q].x = fma(coef, Y[row * kTcCols + 2 * v], y[i][q].x);
+        y[i][q].y = fma(coef, Y[row * kTcCols + 2 * v + 1], y[i][q].y);
+      }
+    }
+  __syncthreads();
+}
+
+// Digits of one value with exponent e: x = 2^e sum_t d_t 2^{-7t} + rest (exact FP64 steps).
+__device__ __forceinline__ void slice_value(double x, int e, __nv_bfloat16 *out, size_t stride) {
+  double a = ldexp(x, -e);
+#pragma unroll
+  for (int t = 1; t <= kSl; t++) {
+    const double sc = ldexp(1.0, 7 * t);
+    const double q = rint(a * sc);
+    out[(t - 1) * stride] = __float2bfloat16_rn((float)q);
+    a = fma(-q, 1.0 / sc, a);
+  }
+}
+
+// exponent e with |x| < 2^e for all |x| <= m (0 for m == 0)
+__device__ __forceinline__ int cover_exponent(double m) {
+  int e = 0;
+  if (m > 0.0) frexp(m, &e);
+  return e;
+}
+
 // ------------------------------------------------------------------ kernel
-template <bool REAL, bool TILED, bool SPLIT>
+template <bool REAL, bool TILED, int PREC>
 __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) {
+  constexpr bool SPLIT = PREC == 1;
+  constexpr bool SLICED = PREC == 2;
   __shared__ Term sT[kMaxTerms];
   __shared__ ExpRec sR;
   __shared__ double s_vn[kVecMax], s_ep[kVecMax], s_pn[kVecMax];
@@ -196,6 +354,9 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
   __shared__ int s_flag;
   __shared__ TileSmem TS;
   DenseSmem &S = TS.d;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ unsigned long long s_cmax[kTcCols];
+  __shared__ int s_cexp[kTcCols];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ty = tid >> 4, tx = tid & 15;
@@ -273,6 +434,46 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
 
   // y[i][q] = sum_k coef_k (H_k src)[row][vec] (+ field), for this thread's outputs
   // tiled: rows r0 + 2 ty + i, vectors tx + 16 q.  warp path: row r, vector 0 (lane 0 holds it).
+  // Slicing pass for a vector set X [nv][D] (MAGNUS_TENSOR_SLICED): column maxima of this block's
+  // rows -> global atomicMax, barrier, every block derives the same column exponents and writes the
+  // digits of its rows, barrier.  Column-maximum slots rotate over three, the one after next is
+  // cleared during each pass.
+  unsigned slice_ev = 0;
+  auto slice_set = [&](const double2 *X, void *digits, int *exps) -> bool {
+    unsigned long long *cm = a.colmax + (size_t)(slice_ev % 3u) * kTcCols;
+    for (int c = tid; c < kTcCols; c += blockDim.x) s_cmax[c] = 0ull;
+    __syncthreads();
+    for (int v = 0; v < nv; v++)
+      for (int64_t r = lo + tid; r < hi; r += blockDim.x) {
+        const double2 x = X[(int64_t)v * D + r];
+        atomicMax(&s_cmax[2 * v], (unsigned long long)__double_as_longlong(fabs(x.x)));
+        atomicMax(&s_cmax[2 * v + 1], (unsigned long long)__double_as_longlong(fabs(x.y)));
+      }
+    __syncthreads();
+    for (int c = tid; c < 2 * nv; c += blockDim.x)
+      if (s_cmax[c]) atomicMax(&cm[c], s_cmax[c]);
+    if (!grid_barrier(a.bar, G, a.spin_limit_ns)) return false;
+    for (int c = tid; c < 2 * nv; c += blockDim.x) {
+      s_cexp[c] = cover_exponent(__longlong_as_double((long long)cm[c]));
+      if (b == 0) exps[c] = s_cexp[c];
+    }
+    if (b == 0)
+      for (int c = tid; c < kTcCols; c += blockDim.x) a.colmax[(size_t)((slice_ev + 2) % 3u) * kTcCols + c] = 0ull;
+    __syncthreads();
+    __nv_bfloat16 *dg = (__nv_bfloat16 *)digits;
+    const size_t stride = (size_t)2 * nv * D;
+    for (int v = 0; v < nv; v++)
+      for (int64_t r = lo + tid; r < hi; r += blockDim.x) {
+        const double2 x = X[(int64_t)v * D + r];
+        slice_value(x.x, s_cexp[2 * v], dg + (size_t)(2 * v) * D + r, stride);
+        slice_value(x.y, s_cexp[2 * v + 1], dg + (size_t)(2 * v + 1) * D + r, stride);
+      }
+    slice_ev++;
+    return grid_barrier(a.bar, G, a.spin_limit_ns);
+  };
+
+  const void *sl_src[kMaxTerms] = {nullptr, nullptr, nullptr, nullptr};  // digits of the vectors being read
+  const int *ex_src[kMaxTerms] = {nullptr, nullptr, nullptr, nullptr};
   auto apply_terms = [&](const double *coef, const double2 *const *srcs, const float4 *const *shs, int64_t r0,
                          double2 (&y)[2][4]) {
     if (TILED) {
@@ -283,7 +484,10 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
       for (int k = 0; k < nt; k++) {
         if (coef[k] == 0.0) continue;
         if (sT[k].kind == MAGNUS_TERM_DENSE) {
-          if (SPLIT)
+          if (SLICED)
+            gemm_tile_sliced(dsm, (const __nv_bfloat16 *)a.hslice[k], a.hexp[k], (const __nv_bfloat16 *)sl_src[k],
+                             ex_src[k], coef[k], D, nv, r0, y);
+          else if (SPLIT)
             gemm_tile_split(TS.f, a.hsplit[k], coef[k], shs[k], D, nv, r0, hi, y);
           else
             gemm_tile<REAL>(S, sT[k].val, coef[k], srcs[k], D, nv, r0, hi, y);
@@ -370,6 +574,9 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
             a.sh_cur[(int64_t)v * D + r] = split4(cur[(int64_t)v * D + r]);
         if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { fail(MAGNUS_ETIMEOUT); return; }
       }
+      if (SLICED) {
+        if (!slice_set(cur, a.sl_cur, a.ex_cur)) { fail(MAGNUS_ETIMEOUT); return; }
+      }
       __syncthreads();
       bool done = false;
       for (int j = 1; j <= a.m_max; j++) {
@@ -381,6 +588,11 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
         const double2 dj = d[j];
         const double2 *srcs[kMaxTerms] = {src, src, src, src};
         const float4 *shs[kMaxTerms] = {src_sh, src_sh, src_sh, src_sh};
+        if (SLICED) {
+          const void *d_src = (j == 1) ? a.sl_cur : (((j - 2) & 1) ? a.sl_w1 : a.sl_w0);
+          const int *e_src = (j == 1) ? a.ex_cur : (((j - 2) & 1) ? a.ex_w1 : a.ex_w0);
+          for (int k = 0; k < kMaxTerms; k++) { sl_src[k] = d_src; ex_src[k] = e_src; }
+        }
         if (R.mode == MODE_M4) {
           // phase 1: u_k = H_k src for every vector, this block's rows
           double one[kMaxTerms];
@@ -412,6 +624,14 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
             }
           }
           if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { fail(MAGNUS_ETIMEOUT); return; }
+          if (SLICED)
+            for (int k = 0; k < nt; k++) {
+              const size_t set = (size_t)kSl * 2 * nv * D;
+              if (!slice_set(a.u + (size_t)k * nv * D, (__nv_bfloat16 *)a.sl_u + k * set, a.ex_u + k * kTcCols)) {
+                fail(MAGNUS_ETIMEOUT);
+                return;
+              }
+            }
         }
         double sw[4] = {0, 0, 0, 0}, sp[4] = {0, 0, 0, 0};
         // epilogue for one output (row r, vector v) with y = the combined matvec
@@ -445,7 +665,18 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
                 hl[q] = a.sh_u + (size_t)k * nv * D;
               }
               double2 z1[2][4], z2[2][4];
+              const size_t set = (size_t)kSl * 2 * nv * D;
+              if (SLICED)
+                for (int q = 0; q < kMaxTerms; q++) {
+                  sl_src[q] = (const __nv_bfloat16 *)a.sl_u + l * set;
+                  ex_src[q] = a.ex_u + l * kTcCols;
+                }
               apply_terms(ck, sk, hk, r0, z1);
+              if (SLICED)
+                for (int q = 0; q < kMaxTerms; q++) {
+                  sl_src[q] = (const __nv_bfloat16 *)a.sl_u + k * set;
+                  ex_src[q] = a.ex_u + k * kTcCols;
+                }
               apply_terms(cl, sl, hl, r0, z2);
               for (int i = 0; i < 2; i++)
                 for (int q = 0; q < 4; q++) {
@@ -522,6 +753,12 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
         it++;
         if (s_flag == 2) { fail(MAGNUS_ENONFINITE); return; }
         if (s_flag == 1) { done = true; break; }
+        if (SLICED && j < a.m_max) {  // digits of w_j for the next iteration's tensor-core products
+          if (!slice_set(dst, ((j - 1) & 1) ? a.sl_w1 : a.sl_w0, ((j - 1) & 1) ? a.ex_w1 : a.ex_w0)) {
+            fail(MAGNUS_ETIMEOUT);
+            return;
+          }
+        }
       }
       if (!done) { fail(MAGNUS_ENOCONV); return; }
       if (tid < nv) s_vn[tid] = s_pn[tid];
@@ -547,11 +784,21 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
       for (int64_t r = lo + tid; r < hi; r += blockDim.x) a.psi[(int64_t)v * D + r] = cur[(int64_t)v * D + r];
 }
 
-const void *dense_kernel(bool real, bool tiled, bool split) {
-  if (split) return (const void *)k_dense_persistent<true, true, true>;
+const void *dense_kernel(bool real, bool tiled, int prec) {
+  if (prec == 1) return (const void *)k_dense_persistent<true, true, 1>;
+  if (prec == 2) return (const void *)k_dense_persistent<true, true, 2>;
   if (real)
-    return tiled ? (const void *)k_dense_persistent<true, true, false> : (const void *)k_dense_persistent<true, false, false>;
-  return tiled ? (const void *)k_dense_persistent<false, true, false> : (const void *)k_dense_persistent<false, false, false>;
+    return tiled ? (const void *)k_dense_persistent<true, true, 0> : (const void *)k_dense_persistent<true, false, 0>;
+  return tiled ? (const void *)k_dense_persistent<false, true, 0> : (const void *)k_dense_persistent<false, false, 0>;
+}
+
+cudaError_t sliced_attr() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(dense_kernel(true, true, 2), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kTcSmemBytes);
+  if (e == cudaSuccess) done = true;
+  return e;
 }
 
 }  // namespace
@@ -569,6 +816,30 @@ __global__ void k_split_dense(const double2 *H, float2 *out, int64_t n) {
 }
 }  // namespace
 
+namespace {
+// one warp per row: row maximum -> exponent, then the row's digits
+__global__ void k_slice_dense(const double2 *H, int64_t D, __nv_bfloat16 *digits, int *rexp) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < D; r += nw) {
+    double m = 0.0;
+    for (int64_t c = lane; c < D; c += 32) m = fmax(m, fabs(H[r * D + c].x));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(kFull, m, o));
+    const int e = cover_exponent(m);
+    if (lane == 0) rexp[r] = e;
+    for (int64_t c = lane; c < D; c += 32) slice_value(H[r * D + c].x, e, digits + r * D + c, (size_t)D * D);
+  }
+}
+}  // namespace
+
+cudaError_t launch_slice_dense(const double2 *H, int64_t D, void *digits, int *rexp, cudaStream_t st) {
+  k_slice_dense<<<152 * 8, 256, 0, st>>>(H, D, (__nv_bfloat16 *)digits, rexp);
+  return cudaGetLastError();
+}
+
+size_t dense_sliced_smem_bytes() { return kTcSmemBytes; }
+
 cudaError_t launch_split_dense(const double2 *H, float2 *out, int64_t n, cudaStream_t st) {
   k_split_dense<<<152 * 8, 256, 0, st>>>(H, out, n);
   return cudaGetLastError();
@@ -576,10 +847,14 @@ cudaError_t launch_split_dense(const double2 *H, float2 *out, int64_t n, cudaStr
 
 cudaError_t dense_max_blocks_per_sm(int *n) {
   int best = 1 << 30;
+  cudaError_t e0 = sliced_attr();
+  if (e0 != cudaSuccess) return e0;
   for (int r = 0; r < 2; r++)
-    for (int t = 0; t < 3; t++) {
+    for (int t = 0; t < 4; t++) {
       int k = 0;
-      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, dense_kernel(r, t > 0, t == 2), kDBlock, 0);
+      const int prec = t >= 2 ? t - 1 : 0;
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, dense_kernel(r, t > 0, prec), kDBlock,
+                                                                    prec == 2 ? kTcSmemBytes : 0);
       if (e != cudaSuccess) return e;
       best = k < best ? k : best;
     }
@@ -590,8 +865,13 @@ cudaError_t dense_max_blocks_per_sm(int *n) {
 cudaError_t launch_dense_persistent(const PersistArgs &a, bool real_valued, int grid, cudaStream_t st) {
   PersistArgs copy = a;
   void *args[] = {&copy};
-  return cudaLaunchCooperativeKernel(dense_kernel(real_valued, a.nvec > 1 || a.split, a.split != 0), dim3(grid),
-                                     dim3(kDBlock), args, 0, st);
+  const int prec = a.sliced ? 2 : (a.split ? 1 : 0);
+  if (prec == 2) {
+    cudaError_t e = sliced_attr();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaLaunchCooperativeKernel(dense_kernel(real_valued, a.nvec > 1 || prec > 0, prec), dim3(grid),
+                                     dim3(kDBlock), args, prec == 2 ? kTcSmemBytes : 0, st);
 }
 
 }  // namespace mg

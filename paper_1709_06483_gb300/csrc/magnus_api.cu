@@ -46,6 +46,11 @@ struct magnus_plan_s {
   bool dense_real = true;
   float2 *hsplit[kMaxTerms] = {nullptr, nullptr, nullptr, nullptr};
   float4 *sh_cur = nullptr, *sh_w0 = nullptr, *sh_w1 = nullptr, *sh_u = nullptr;
+  uint16_t *hslice[kMaxTerms] = {nullptr, nullptr, nullptr, nullptr};
+  int *hexp[kMaxTerms] = {nullptr, nullptr, nullptr, nullptr};
+  uint16_t *sl_cur = nullptr, *sl_w0 = nullptr, *sl_w1 = nullptr, *sl_u = nullptr;
+  int *ex_sets = nullptr;                // [3 + nterms][128] column exponents
+  unsigned long long *colmax = nullptr;  // [3][128]
   int lbits = 0;
   double *dlo = nullptr, *dhi = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -85,7 +90,9 @@ void free_plan(magnus_plan_t p) {
   if (!p) return;
   void *bufs[] = {p->terms, p->coeffs, p->term_ab, p->xi, p->cand, p->counter, p->bar, p->counters, p->partials,
                   p->alt, p->w0, p->w1, p->u, p->recs, p->dd, p->mlog, p->dlo, p->dhi,
-                  p->hsplit[0], p->hsplit[1], p->hsplit[2], p->hsplit[3], p->sh_cur, p->sh_w0, p->sh_w1, p->sh_u};
+                  p->hsplit[0], p->hsplit[1], p->hsplit[2], p->hsplit[3], p->sh_cur, p->sh_w0, p->sh_w1, p->sh_u,
+                  p->hslice[0], p->hslice[1], p->hslice[2], p->hslice[3], p->hexp[0], p->hexp[1], p->hexp[2],
+                  p->hexp[3], p->sl_cur, p->sl_w0, p->sl_w1, p->sl_u, p->ex_sets, p->colmax};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (p->ev0) cudaEventDestroy(p->ev0);
@@ -144,7 +151,7 @@ magnus_status run_persistent(magnus_plan_t p, void *psi, int64_t nexp, magnus_st
   int grid, gv;
   size_t need;
   if (p->fam == FAM_DENSE) {
-    const bool tiled = p->opt.nvec > 1 || p->opt.precision == MAGNUS_FP32_SPLIT;
+    const bool tiled = p->opt.nvec > 1 || p->opt.precision != MAGNUS_FP64;
     const int64_t units = (p->dim + dense_rows_per_unit(tiled) - 1) / dense_rows_per_unit(tiled);
     const int64_t maxg = (int64_t)p->num_sms * std::max(1, p->dense_blocks_per_sm);
     // the warp-per-row kernel handles 8 rows per block pass; give each block at least 8 rows
@@ -170,6 +177,7 @@ magnus_status run_persistent(magnus_plan_t p, void *psi, int64_t nexp, magnus_st
   }
   CUDA_TRY(p, cudaMemsetAsync(p->bar, 0, sizeof(GridBar), p->stream));
   CUDA_TRY(p, cudaMemsetAsync(p->counters, 0, sizeof(Counters), p->stream));
+  if (p->colmax) CUDA_TRY(p, cudaMemsetAsync(p->colmax, 0, sizeof(unsigned long long) * 3 * 128, p->stream));
   PersistArgs a{};
   a.dim = p->dim;
   a.nvec = p->opt.nvec;
@@ -205,6 +213,22 @@ magnus_status run_persistent(magnus_plan_t p, void *psi, int64_t nexp, magnus_st
   a.sh_w0 = p->sh_w0;
   a.sh_w1 = p->sh_w1;
   a.sh_u = p->sh_u;
+  a.sliced = p->opt.precision == MAGNUS_TENSOR_SLICED;
+  for (int k = 0; k < kMaxTerms; k++) {
+    a.hslice[k] = p->hslice[k];
+    a.hexp[k] = p->hexp[k];
+  }
+  a.sl_cur = p->sl_cur;
+  a.sl_w0 = p->sl_w0;
+  a.sl_w1 = p->sl_w1;
+  a.sl_u = p->sl_u;
+  if (p->ex_sets) {
+    a.ex_cur = p->ex_sets;
+    a.ex_w0 = p->ex_sets + 128;
+    a.ex_w1 = p->ex_sets + 256;
+    a.ex_u = p->ex_sets + 384;
+  }
+  a.colmax = p->colmax;
   CUDA_TRY(p, cudaEventRecord(p->ev0, p->stream));
   if (p->fam == FAM_DENSE)
     CUDA_TRY(p, launch_dense_persistent(a, p->dense_real, grid, p->stream));
@@ -284,8 +308,8 @@ magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms
     return set_err(nullptr, MAGNUS_EINVAL, "barrier_timeout_s must be in [0, 600]");
   if (o.m_max < 2 || o.m_max > kMmaxLimit) return set_err(nullptr, MAGNUS_EINVAL, "m_max must be 2..%d", kMmaxLimit);
   if (o.nvec < 1 || o.nvec > 64) return set_err(nullptr, MAGNUS_EINVAL, "nvec must be 1..64");
-  if (o.precision != MAGNUS_FP64 && o.precision != MAGNUS_FP32_SPLIT)
-    return set_err(nullptr, MAGNUS_EINVAL, "precision must be MAGNUS_FP64 or MAGNUS_FP32_SPLIT");
+  if (o.precision != MAGNUS_FP64 && o.precision != MAGNUS_FP32_SPLIT && o.precision != MAGNUS_TENSOR_SLICED)
+    return set_err(nullptr, MAGNUS_EINVAL, "precision must be MAGNUS_FP64, MAGNUS_FP32_SPLIT or MAGNUS_TENSOR_SLICED");
   for (int k = 0; k < nterms; k++) {
     const magnus_term &t = terms[k];
     const magnus_coeff &c = coeffs[k];
@@ -434,6 +458,26 @@ magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms
       PLAN_TRY(dalloc(&p->sh_w0, nd));
       PLAN_TRY(dalloc(&p->sh_w1, nd));
       PLAN_TRY(dalloc(&p->sh_u, nd * nterms));
+    }
+    if (o.precision == MAGNUS_TENSOR_SLICED) {
+      if (p->fam != FAM_DENSE || !p->dense_real || dim % 128 != 0) {
+        set_err(p, MAGNUS_EINVAL, "MAGNUS_TENSOR_SLICED needs real-valued dense terms and dim a multiple of 128");
+        return fail(MAGNUS_EINVAL);
+      }
+      const size_t kDigits = 5;  // bf16 digits per value
+      for (int k = 0; k < nterms; k++)
+        if (p->terms_host[k].kind == MAGNUS_TERM_DENSE) {
+          PLAN_TRY(dalloc(&p->hslice[k], kDigits * (size_t)dim * dim));
+          PLAN_TRY(dalloc(&p->hexp[k], (size_t)dim));
+          PLAN_TRY(launch_slice_dense(p->terms_host[k].val, dim, p->hslice[k], p->hexp[k], p->stream));
+        }
+      const size_t set = kDigits * 2 * (size_t)nd;
+      PLAN_TRY(dalloc(&p->sl_cur, set));
+      PLAN_TRY(dalloc(&p->sl_w0, set));
+      PLAN_TRY(dalloc(&p->sl_w1, set));
+      PLAN_TRY(dalloc(&p->sl_u, set * nterms));
+      PLAN_TRY(dalloc(&p->ex_sets, (size_t)128 * (3 + nterms)));
+      PLAN_TRY(dalloc(&p->colmax, (size_t)3 * 128));
     }
     if (mf) {
       const int n = p->terms_host[0].nspins;

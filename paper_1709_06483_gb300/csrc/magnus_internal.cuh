@@ -138,6 +138,15 @@ struct PersistArgs {
   int split;
   const float2 *hsplit[kMaxTerms];
   float4 *sh_cur, *sh_w0, *sh_w1, *sh_u;
+  // FAM_DENSE with MAGNUS_TENSOR_SLICED: bf16 digits of the dense terms ([5][D][D], row exponents)
+  // and of every vector set a dense matvec reads ([5][2 nvec][D], column exponents), and the
+  // rotating column-maximum slots of the slicing passes ([3][128], zero at launch)
+  int sliced;
+  const void *hslice[kMaxTerms];
+  const int *hexp[kMaxTerms];
+  void *sl_cur, *sl_w0, *sl_w1, *sl_u;
+  int *ex_cur, *ex_w0, *ex_w1, *ex_u;
+  unsigned long long *colmax;
 };
 enum { FAM_GENERIC = 0, FAM_CSR = 1, FAM_MF = 2, FAM_DENSE = 3 };
 cudaError_t launch_persistent(const PersistArgs &a, int grid, int block, cudaStream_t st);
@@ -150,6 +159,10 @@ int dense_rows_per_unit(bool tiled);
 cudaError_t dense_max_blocks_per_sm(int *n);
 // partials must hold 4 * grid * nvec + 4 * nvec doubles
 cudaError_t launch_dense_persistent(const PersistArgs &a, bool real_valued, int grid, cudaStream_t st);
+
+// Dense term (complex128, real parts used) -> bf16 digits [5][D][D] and row exponents [D].
+cudaError_t launch_slice_dense(const double2 *H, int64_t D, void *digits, int *rexp, cudaStream_t st);
+size_t dense_sliced_smem_bytes();
 
 // H (complex128, real parts used) -> FP32 (hi, lo) pairs, n entries.
 cudaError_t launch_split_dense(const double2 *H, float2 *out, int64_t n, cudaStream_t st);

@@ -135,3 +135,60 @@ def test_fp32_split_rejects_complex_terms(mg):
     with pytest.raises(mg.MagnusError) as e:
         mg.Plan(32, [mg.DenseTerm(cuda(A + A.conj().T))], [mg.Drive.const()], nvec=2, precision=mg.FP32_SPLIT)
     assert e.value.code == mg.EINVAL
+
+
+@pytest.mark.parametrize("variant", ["CF4", "M4"])
+@pytest.mark.parametrize("field", ["dense", "mfree"])
+@pytest.mark.parametrize("nspins,nvec", [(8, 6), (7, 1), (9, 64)])
+def test_tensor_sliced_precision(mg, variant, field, nspins, nvec):
+    """MAGNUS_TENSOR_SLICED: dense matvecs as exact bf16 digit products on the tensor cores.
+    Stated accuracy: state error <= 1e-9 relative to the FP64 oracle; the Leja degrees may differ
+    by rounding, so they are not compared."""
+    if variant == "M4" and nvec == 64:
+        pytest.skip("covered by the smaller M4 cases")
+    c = mi.workload3(nvec=nvec, nspins=nspins, h=0.02, nsteps=6)
+    Hs = mg.build_longrange_dense(c.nspins, c.hz, 1.5, c.delta)
+    Hd = mg.build_field_x_dense(c.nspins) if field == "dense" else mg.FieldXTerm(c.nspins)
+    terms = [mg.DenseTerm(Hs), mg.DenseTerm(Hd) if field == "dense" else Hd]
+    plan = mg.Plan(c.dim, terms, drive_pair(mg, c), nvec=nvec, precision=mg.TENSOR_SLICED)
+    psi = cuda(c.psi0)
+    plan.propagate(psi, 0.0, c.h, c.nsteps, variant)
+    P = oracle_dense(c, oracle.longrange_dense(c.nspins, c.hz, 1.5, c.delta), oracle.field_x_dense(c.nspins))
+    out = psi.cpu().numpy().reshape(nvec, -1)
+    psi0 = c.psi0.reshape(nvec, -1)
+    check = range(nvec) if nvec <= 8 else [0, 1, 31, 62, 63]
+    errs = [rel(out[v], P.propagate(psi0[v], 0.0, c.h, c.nsteps, variant)) for v in check]
+    assert max(errs) < 1e-9, errs
+
+
+def test_tensor_sliced_wide_spread_states(mg):
+    """Columns whose entries span many binades (one large entry, the rest tiny) and a zero state:
+    the per-column exponent keeps the large entry exact and the zero column stays zero."""
+    c = mi.workload3(nvec=3, nspins=8, h=0.02, nsteps=4)
+    psi0 = c.psi0.reshape(3, -1).copy()
+    psi0[1] *= 1e-6
+    psi0[1][7] = 1.0
+    psi0[2] = 0.0
+    Hs = mg.build_longrange_dense(c.nspins, c.hz, 1.5, c.delta)
+    plan = mg.Plan(c.dim, [mg.DenseTerm(Hs), mg.FieldXTerm(c.nspins)], drive_pair(mg, c), nvec=3,
+                   precision=mg.TENSOR_SLICED)
+    psi = cuda(psi0)
+    plan.propagate(psi, 0.0, c.h, c.nsteps, "CF4")
+    P = oracle_dense(c, oracle.longrange_dense(c.nspins, c.hz, 1.5, c.delta), oracle.field_x_dense(c.nspins))
+    out = psi.cpu().numpy()
+    for v in range(2):
+        assert rel(out[v], P.propagate(psi0[v], 0.0, c.h, c.nsteps, "CF4")) < 1e-9
+    assert not np.any(out[2])
+
+
+def test_tensor_sliced_rejects_unsupported(mg):
+    rng = np.random.default_rng(6)
+    A = rng.standard_normal((128, 128)) + 1j * rng.standard_normal((128, 128))
+    with pytest.raises(mg.MagnusError) as e:
+        mg.Plan(128, [mg.DenseTerm(cuda(A + A.conj().T))], [mg.Drive.const()], nvec=2, precision=mg.TENSOR_SLICED)
+    assert e.value.code == mg.EINVAL
+    B = rng.standard_normal((64, 64))
+    with pytest.raises(mg.MagnusError) as e:
+        mg.Plan(64, [mg.DenseTerm(cuda((B + B.T).astype(np.complex128)))], [mg.Drive.const()], nvec=2,
+                precision=mg.TENSOR_SLICED)
+    assert e.value.code == mg.EINVAL
