@@ -71,6 +71,8 @@ def dist_env():
 def workload_terms(mg, c, storage):
     if storage == "csr":
         return [mg.build_xxz_csr(c.nspins, c.J, c.hz, c.delta), mg.build_field_x_csr(c.nspins)]
+    if storage == "csr_real":  # float64 values: 12 B per stored entry
+        return [mg.build_xxz_csr(c.nspins, c.J, c.hz, c.delta).as_real(), mg.build_field_x_csr(c.nspins).as_real()]
     return [mg.XXZTerm(c.nspins, c.J, c.hz, c.delta), mg.FieldXTerm(c.nspins)]
 
 
@@ -81,7 +83,8 @@ def drives(mg, c):
 def algorithmic_per_iteration(c, storage, variant, nnz_total):
     """Bytes and FP64 work one Leja iteration needs (real-valued Hamiltonian, complex state).
 
-    Bytes, CSR: per stored entry 16 B value + 4 B column, per row 8 B row pointer per term, plus per
+    Bytes, CSR: per stored entry 16 B value (8 B in real storage) + 4 B column, per row 8 B row
+    pointer per term, plus per
     row 16 B read of w_{j-1}, 16 B write of w_j and 16 + 16 B read and write of p; matrix-free: the
     vector traffic only.  M4 applies every term twice and writes and reads back u_k (2 x 32 B/row).
 
@@ -97,8 +100,8 @@ def algorithmic_per_iteration(c, storage, variant, nnz_total):
     vec_bytes = 64 * D
     if variant == "M4":
         vec_bytes += 2 * 16 * D * 2
-    if storage == "csr":
-        mat = 20 * nnz_total + 2 * 8 * (D + 1)
+    if storage in ("csr", "csr_real"):
+        mat = (20 if storage == "csr" else 12) * nnz_total + 2 * 8 * (D + 1)
         inst = passes * 2 * nnz_total + (4 + 2 + 4 + 4) * D
     else:
         n = c.nspins
@@ -188,7 +191,7 @@ def run_ours(args):
     variant, storage = args.variant, args.storage
     stream = torch.cuda.current_stream()
     terms = workload_terms(mg, c, storage)
-    nnz_total = sum(t.col.numel() for t in terms) if storage == "csr" else None
+    nnz_total = sum(t.col.numel() for t in terms) if storage.startswith("csr") else None
     plan = mg.Plan(c.dim, terms, drives(mg, c))
     psi0 = torch.from_numpy(c.psi0).cuda()
     psi = psi0.clone()
@@ -261,7 +264,7 @@ def run_ours(args):
         "config": {"workload": f"xxz_chain_20spins_{storage}_{variant.lower()}", "spins": c.nspins, "dim": c.dim,
                    "nnz": nnz_total, "h": c.h, "t0": c.t0, "variant": variant, "storage": storage,
                    "leja_tol": 1e-10, "l2": "inputs larger than L2: the 640 MB CSR is streamed every iteration"
-                   if storage == "csr" else "matrix-free; 4 state vectors of 16 MB stay L2-resident",
+                   if storage.startswith("csr") else "matrix-free; 4 state vectors of 16 MB stay L2-resident",
                    "parallelism": f"replicas x{world}"},
         "matvec_gbs": round(gbs, 1),
         "leja": {"iterations": nmv, "max_degree": st["max_m"], "exponentials": st["n_exp"]},
@@ -378,9 +381,8 @@ def run_batch512(args):
     probs = []
     nnz = 0
     for c in chains:
-        terms = ([mg.build_xxz_csr(c.nspins, c.J, c.hz, c.delta), mg.build_field_x_csr(c.nspins)]
-                 if args.storage == "csr" else [mg.XXZTerm(c.nspins, c.J, c.hz, c.delta), mg.FieldXTerm(c.nspins)])
-        if args.storage == "csr":
+        terms = workload_terms(mg, c, args.storage)
+        if args.storage.startswith("csr"):
             nnz += sum(t.col.numel() for t in terms)
         probs.append((c.dim, terms, drives(mg, c)))
     B = mg.Batch(probs)
@@ -400,7 +402,9 @@ def run_batch512(args):
         wall = time.perf_counter() - t
     gms = st["graph_ms"]
     rows = sum(c.dim for c in chains)
-    bytes_it = 20 * nnz + sum(2 * 8 * (c.dim + 1) for c in chains) + 64 * rows if args.storage == "csr" else 64 * rows
+    vb = 20 if args.storage == "csr" else 12
+    bytes_it = (vb * nnz + sum(2 * 8 * (c.dim + 1) for c in chains) + 64 * rows if args.storage.startswith("csr")
+                else 64 * rows)
     # Leja iterations differ per chain; algorithmic bytes weighted by each chain's iterations are
     # approximated with the mean iteration count per chain
     iters_per_chain = st["n_matvec"] / len(chains)
@@ -416,7 +420,7 @@ def run_batch512(args):
                    "cta_size": st["block"], "cluster_size": st["cluster"]},
         "chain_steps_per_s": round(len(chains) * args.steps / (gms / 1e3), 1),
         "leja_iterations": st["n_matvec"], "matvec_gbs": round(gbs, 1),
-        "roofline": {"bound": "hbm" if args.storage == "csr" else "alu", "kernel": "k_batched",
+        "roofline": {"bound": "hbm" if args.storage.startswith("csr") else "alu", "kernel": "k_batched",
                      "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s", "frac": round(gbs / hbm_peak, 4),
                      "traffic": None, "note": "graph time includes the per-chain setup launches"},
         "wall_ms": round(wall * 1e3, 2), "gpu_launches": len(chains) + 1, "clocks": clk.summary(),
@@ -544,7 +548,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--variant", choices=["CF4", "M4", "CF4_3", "M2"], default="CF4")
-    ap.add_argument("--storage", choices=["csr", "mfree"], default="csr")
+    ap.add_argument("--storage", choices=["csr", "csr_real", "mfree"], default="csr")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")

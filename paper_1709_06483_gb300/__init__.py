@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_PKG, "libmagnus_gb300.so")
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ENONFINITE, ETIMEOUT = range(7)
 M4, CF4, CF4_3, M2 = 1, 2, 3, 4
 VARIANTS = {"M4": M4, "CF4": CF4, "CF4_3": CF4_3, "M2": M2}
-TERM_CSR, TERM_DENSE, TERM_XXZ, TERM_FIELD_X = 0, 1, 2, 3
+TERM_CSR, TERM_DENSE, TERM_XXZ, TERM_FIELD_X, TERM_CSR_REAL, TERM_DENSE_REAL = 0, 1, 2, 3, 4, 5
 FP64, FP32_SPLIT, TENSOR_SLICED = 0, 1, 2
 
 # Every symbol the header declares (checked by the CPU test suite).
@@ -29,7 +29,7 @@ EXPORTS = (
     "magnus_propagate", "magnus_term_interval", "magnus_leja_points", "magnus_divided_differences",
     "magnus_xxz_nnz", "magnus_build_xxz_csr", "magnus_build_field_x_csr", "magnus_build_longrange_dense",
     "magnus_build_field_x_dense", "magnus_expv_xxz_static", "magnus_batch_create", "magnus_batch_propagate",
-    "magnus_batch_destroy", "magnus_batch_last_error", "magnus_adjoint_grad",
+    "magnus_batch_destroy", "magnus_batch_last_error", "magnus_adjoint_grad", "magnus_real_parts",
 )
 
 
@@ -103,6 +103,7 @@ def _declare(L):
         "magnus_batch_destroy": (I32, [P]),
         "magnus_batch_last_error": (C.c_char_p, [P]),
         "magnus_adjoint_grad": (I32, [P, P, P, D, D, I64, I32, I32, I32, C.POINTER(D), C.POINTER(D), C.POINTER(Stats)]),
+        "magnus_real_parts": (I32, [P, I64, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -157,32 +158,55 @@ def _f64(a):
 
 
 # ------------------------------------------------------------------ terms / coefficients
+def real_parts(z, stream=None):
+    """float64 copy of the real parts of a CUDA complex128 tensor; MagnusError(EINVAL) if some
+    imaginary part is nonzero (the conversion to real storage must be exact)."""
+    import torch
+    z = z.contiguous()
+    out = torch.empty(z.shape, dtype=torch.float64, device=z.device)
+    _check(load().magnus_real_parts(_dptr(z), z.numel(), _dptr(out), _stream_ptr(stream)))
+    return out
+
+
 class CSRTerm:
-    """Complex128 CSR term on the device (int64 row pointers, int32 columns)."""
+    """CSR term on the device (int64 row pointers, int32 columns).  Complex values give
+    MAGNUS_TERM_CSR (20 B per entry); float64 values give MAGNUS_TERM_CSR_REAL (12 B per entry) for a
+    real symmetric matrix."""
 
     def __init__(self, rowptr, col, val):
         import torch
         self.rowptr = rowptr.to(torch.int64).contiguous()
         self.col = col.to(torch.int32).contiguous()
-        self.val = val.to(torch.complex128).contiguous()
+        self.real = not val.is_complex()
+        self.val = val.to(torch.float64 if self.real else torch.complex128).contiguous()
+
+    def as_real(self, stream=None) -> "CSRTerm":
+        """The same matrix in real storage (exact; raises if it is not real)."""
+        return self if self.real else CSRTerm(self.rowptr, self.col, real_parts(self.val, stream))
 
     def ctype(self):
         t = Term()
-        t.kind, t.nnz = TERM_CSR, self.col.numel()
+        t.kind, t.nnz = (TERM_CSR_REAL if self.real else TERM_CSR), self.col.numel()
         t.rowptr, t.col, t.val = _dptr(self.rowptr), _dptr(self.col), _dptr(self.val)
         return t
 
 
 class DenseTerm:
-    """Complex128 dense term on the device, row-major dim x dim."""
+    """Dense term on the device, row-major dim x dim: complex128 (MAGNUS_TERM_DENSE) or float64 for a
+    real symmetric matrix (MAGNUS_TERM_DENSE_REAL, half the bytes)."""
 
     def __init__(self, H):
         import torch
-        self.val = H.to(torch.complex128).contiguous()
+        self.real = not H.is_complex()
+        self.val = H.to(torch.float64 if self.real else torch.complex128).contiguous()
+
+    def as_real(self, stream=None) -> "DenseTerm":
+        """The same matrix in real storage (exact; raises if it is not real)."""
+        return self if self.real else DenseTerm(real_parts(self.val, stream))
 
     def ctype(self):
         t = Term()
-        t.kind, t.nnz = TERM_DENSE, self.val.numel()
+        t.kind, t.nnz = (TERM_DENSE_REAL if self.real else TERM_DENSE), self.val.numel()
         t.val = _dptr(self.val)
         return t
 

@@ -446,15 +446,14 @@ MAGNUS_API magnus_status magnus_batch_create(magnus_batch_t *out, int32_t count,
       const magnus_term &t = it.terms[k];
       Term &T = b->terms_host[i][k];
       memset(&T, 0, sizeof T);
-      T.kind = t.kind;
+      set_term_storage(T, t);
       T.nspins = t.nspins;
       T.nnz = t.nnz;
       T.rowptr = t.rowptr;
       T.col = t.col;
-      T.val = (const double2 *)t.val;
       T.delta = t.delta;
       const bool pow2 = t.nspins >= 1 && t.nspins <= kMaxSpins && it.dim == ((int64_t)1 << t.nspins);
-      if (t.kind == MAGNUS_TERM_CSR) {
+      if (t.kind == MAGNUS_TERM_CSR || t.kind == MAGNUS_TERM_CSR_REAL) {
         if (!t.rowptr || !t.col || !t.val) { berr(b, MAGNUS_EINVAL, "item %d term %d: CSR arrays missing", i, k); return fail(MAGNUS_EINVAL); }
       } else if (t.kind == MAGNUS_TERM_XXZ) {
         if (!pow2 || t.nspins < 2 || !t.J || !t.hz) { berr(b, MAGNUS_EINVAL, "item %d term %d: bad XXZ term", i, k); return fail(MAGNUS_EINVAL); }
@@ -466,7 +465,7 @@ MAGNUS_API magnus_status magnus_batch_create(magnus_batch_t *out, int32_t count,
         berr(b, MAGNUS_EINVAL, "item %d term %d: batches take CSR, XXZ and FIELD_X terms", i, k);
         return fail(MAGNUS_EINVAL);
       }
-      all_csr &= t.kind == MAGNUS_TERM_CSR;
+      all_csr &= T.kind == MAGNUS_TERM_CSR;
       const magnus_coeff &c = it.coeffs[k];
       if (c.nmodes < 0 || c.nmodes > kMaxModes || (c.nmodes > 0 && !c.om)) {
         berr(b, MAGNUS_EINVAL, "item %d coefficient %d: bad modes", i, k);
@@ -513,7 +512,7 @@ MAGNUS_API magnus_status magnus_batch_create(magnus_batch_t *out, int32_t count,
   BCREATE(cudaMemsetAsync(flags, 0, sizeof(int) * count * kMaxTerms, b->stream));
   for (int i = 0; i < count; i++)
     for (int k = 0; k < b->nterms[i]; k++)
-      if (b->terms_host[i][k].kind == MAGNUS_TERM_CSR && b->terms_host[i][k].nnz > 0)
+      if (b->terms_host[i][k].kind == MAGNUS_TERM_CSR && b->terms_host[i][k].rs == 2 && b->terms_host[i][k].nnz > 0)
         BCREATE(launch_imag_check(b->terms_host[i][k].val, b->terms_host[i][k].nnz, flags + i * kMaxTerms + k, b->stream));
   std::vector<int> fh((size_t)count * kMaxTerms);
   BCREATE(cudaMemcpyAsync(fh.data(), flags, sizeof(int) * fh.size(), cudaMemcpyDeviceToHost, b->stream));
@@ -523,7 +522,7 @@ MAGNUS_API magnus_status magnus_batch_create(magnus_batch_t *out, int32_t count,
   for (int i = 0; i < count; i++)
     for (int k = 0; k < kMaxTerms; k++) {
       Term &T = b->terms_host[i][k];
-      T.real_valued = T.kind == MAGNUS_TERM_CSR && !fh[(size_t)i * kMaxTerms + k];
+      T.real_valued = T.kind == MAGNUS_TERM_CSR && (T.rs == 1 || !fh[(size_t)i * kMaxTerms + k]);
       tflat[(size_t)i * kMaxTerms + k] = T;
       cflat[(size_t)i * kMaxTerms + k] = b->coeffs_host[i][k];
     }

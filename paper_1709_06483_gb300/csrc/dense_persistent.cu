@@ -113,8 +113,11 @@ __device__ __forceinline__ void gemm_tile_split(SplitSmem &S, const float2 *H2, 
 
 // acc[i][q] += sum_j coef * H[r0 + 2 ty + i][j] * W[tx + 16 q][j] over all columns j.
 template <bool REAL>
-__device__ __forceinline__ void gemm_tile(DenseSmem &S, const double2 *H, double coef, const double2 *W, int64_t D,
+__device__ __forceinline__ void gemm_tile(DenseSmem &S, const Term &T, double coef, const double2 *W, int64_t D,
                                           int nv, int64_t r0, int64_t rend, double2 (&acc)[2][4]) {
+  const double2 *H = T.val;
+  const double *Hr = T.rv;
+  const int64_t rs = T.rs;
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
   for (int64_t k0 = 0; k0 < D; k0 += kTK) {
     __syncthreads();
@@ -122,10 +125,14 @@ __device__ __forceinline__ void gemm_tile(DenseSmem &S, const double2 *H, double
     for (int i = tid; i < kTM * kTK; i += kDBlock) {
       const int rr = i / kTK, kk = i % kTK;
       const int64_t row = r0 + rr, col = k0 + kk;
-      double2 v = make_double2(0.0, 0.0);
-      if (row < rend && col < D) v = __ldg(H + row * D + col);
-      S.h[rr][kk] = coef * v.x;
-      if (!REAL) S.hi[rr][kk] = coef * v.y;
+      if (REAL) {
+        S.h[rr][kk] = (row < rend && col < D) ? coef * __ldg(Hr + (row * D + col) * rs) : 0.0;
+      } else {
+        double2 v = make_double2(0.0, 0.0);
+        if (row < rend && col < D) v = __ldg(H + row * D + col);
+        S.h[rr][kk] = coef * v.x;
+        S.hi[rr][kk] = coef * v.y;
+      }
     }
     for (int i = tid; i < kVecMax * kTK; i += kDBlock) {
       const int vv = i / kTK, kk = i % kTK;
@@ -156,11 +163,21 @@ __device__ __forceinline__ void gemm_tile(DenseSmem &S, const double2 *H, double
 
 // one row of a dense term times one vector, by a whole warp (lane-strided columns)
 template <bool REAL>
-__device__ __forceinline__ double2 gemv_row_partial(const double2 *H, const double2 *x, int64_t D, int64_t r) {
+__device__ __forceinline__ double2 gemv_row_partial(const Term &T, const double2 *x, int64_t D, int64_t r) {
   const int lane = threadIdx.x & 31;
   double2 acc = make_double2(0.0, 0.0);
-  const double2 *row = H + r * D;
   int64_t j = lane;
+  if (REAL && T.rs == 1) {  // real storage: 8 B per element
+    const double *row = T.rv + r * D;
+    for (; j + 96 < D; j += 128) {
+      const double a0 = __ldg(row + j), a1 = __ldg(row + j + 32), a2 = __ldg(row + j + 64), a3 = __ldg(row + j + 96);
+      const double2 x0 = ldv(x + j), x1 = ldv(x + j + 32), x2 = ldv(x + j + 64), x3 = ldv(x + j + 96);
+      acc = rfma(a0, x0, acc); acc = rfma(a1, x1, acc); acc = rfma(a2, x2, acc); acc = rfma(a3, x3, acc);
+    }
+    for (; j < D; j += 32) acc = rfma(__ldg(row + j), ldv(x + j), acc);
+    return acc;
+  }
+  const double2 *row = T.val + r * D;
   for (; j + 96 < D; j += 128) {
     const double2 a0 = __ldg(row + j), a1 = __ldg(row + j + 32), a2 = __ldg(row + j + 64), a3 = __ldg(row + j + 96);
     const double2 x0 = ldv(x + j), x1 = ldv(x + j + 32), x2 = ldv(x + j + 64), x3 = ldv(x + j + 96);
@@ -490,7 +507,7 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
           else if (SPLIT)
             gemm_tile_split(TS.f, a.hsplit[k], coef[k], shs[k], D, nv, r0, hi, y);
           else
-            gemm_tile<REAL>(S, sT[k].val, coef[k], srcs[k], D, nv, r0, hi, y);
+            gemm_tile<REAL>(S, sT[k], coef[k], srcs[k], D, nv, r0, hi, y);
         } else if (sT[k].kind == MAGNUS_TERM_FIELD_X) {
 #pragma unroll
           for (int i = 0; i < 2; i++) {
@@ -509,7 +526,7 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
       for (int k = 0; k < nt; k++) {
         if (coef[k] == 0.0) continue;
         if (sT[k].kind == MAGNUS_TERM_DENSE) {
-          const double2 part = gemv_row_partial<REAL>(sT[k].val, srcs[k], D, r0);
+          const double2 part = gemv_row_partial<REAL>(sT[k], srcs[k], D, r0);
           acc = rfma(coef[k], part, acc);
         } else if (sT[k].kind == MAGNUS_TERM_FIELD_X && lane == 0) {
           acc = rfma(coef[k], fieldx_at(sT[k].nspins, srcs[k], r0), acc);
@@ -807,9 +824,9 @@ int dense_block_size() { return kDBlock; }
 int dense_rows_per_unit(bool tiled) { return tiled ? kTM : 1; }
 
 namespace {
-__global__ void k_split_dense(const double2 *H, float2 *out, int64_t n) {
+__global__ void k_split_dense(const double *Hr, int rs, float2 *out, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double x = H[i].x;
+    const double x = Hr[i * rs];
     const float hi = __double2float_rn(x);
     out[i] = make_float2(hi, __double2float_rn(x - (double)hi));
   }
@@ -818,30 +835,30 @@ __global__ void k_split_dense(const double2 *H, float2 *out, int64_t n) {
 
 namespace {
 // one warp per row: row maximum -> exponent, then the row's digits
-__global__ void k_slice_dense(const double2 *H, int64_t D, __nv_bfloat16 *digits, int *rexp) {
+__global__ void k_slice_dense(const double *Hr, int rs, int64_t D, __nv_bfloat16 *digits, int *rexp) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < D; r += nw) {
     double m = 0.0;
-    for (int64_t c = lane; c < D; c += 32) m = fmax(m, fabs(H[r * D + c].x));
+    for (int64_t c = lane; c < D; c += 32) m = fmax(m, fabs(Hr[(r * D + c) * rs]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(kFull, m, o));
     const int e = cover_exponent(m);
     if (lane == 0) rexp[r] = e;
-    for (int64_t c = lane; c < D; c += 32) slice_value(H[r * D + c].x, e, digits + r * D + c, (size_t)D * D);
+    for (int64_t c = lane; c < D; c += 32) slice_value(Hr[(r * D + c) * rs], e, digits + r * D + c, (size_t)D * D);
   }
 }
 }  // namespace
 
-cudaError_t launch_slice_dense(const double2 *H, int64_t D, void *digits, int *rexp, cudaStream_t st) {
-  k_slice_dense<<<152 * 8, 256, 0, st>>>(H, D, (__nv_bfloat16 *)digits, rexp);
+cudaError_t launch_slice_dense(const double *Hr, int rs, int64_t D, void *digits, int *rexp, cudaStream_t st) {
+  k_slice_dense<<<152 * 8, 256, 0, st>>>(Hr, rs, D, (__nv_bfloat16 *)digits, rexp);
   return cudaGetLastError();
 }
 
 size_t dense_sliced_smem_bytes() { return kTcSmemBytes; }
 
-cudaError_t launch_split_dense(const double2 *H, float2 *out, int64_t n, cudaStream_t st) {
-  k_split_dense<<<152 * 8, 256, 0, st>>>(H, out, n);
+cudaError_t launch_split_dense(const double *Hr, int rs, float2 *out, int64_t n, cudaStream_t st) {
+  k_split_dense<<<152 * 8, 256, 0, st>>>(Hr, rs, out, n);
   return cudaGetLastError();
 }
 

@@ -277,6 +277,24 @@ void noalloc_set_error(const char *msg) { g_global_err = msg; }
 
 extern "C" {
 
+MAGNUS_API magnus_status magnus_real_parts(const void *z, int64_t n, double *out, void *stream) {
+  if (n < 0 || (n > 0 && (!z || !out))) return set_err(nullptr, MAGNUS_EINVAL, "real_parts: bad arguments");
+  if (n == 0) return MAGNUS_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  int *flag = nullptr;
+  CUDA_TRY(nullptr, dalloc(&flag, 1));
+  int fh = 0;
+  cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = launch_real_parts((const double2 *)z, n, out, flag, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&fh, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(flag);
+  CUDA_TRY(nullptr, e);
+  if (fh) return set_err(nullptr, MAGNUS_EINVAL, "real_parts: some imaginary part is nonzero");
+  return MAGNUS_OK;
+}
+
+
 const char *magnus_status_string(magnus_status s) {
   switch (s) {
     case MAGNUS_OK: return "MAGNUS_OK";
@@ -321,8 +339,16 @@ magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms
           return set_err(nullptr, MAGNUS_EINVAL, "term %d: CSR arrays missing", k);
         if (((uintptr_t)t.val) % 16) return set_err(nullptr, MAGNUS_EINVAL, "term %d: CSR values must be 16-byte aligned", k);
         break;
+      case MAGNUS_TERM_CSR_REAL:
+        if (!t.rowptr || !t.col || !t.val || t.nnz < 0)
+          return set_err(nullptr, MAGNUS_EINVAL, "term %d: CSR arrays missing", k);
+        if (((uintptr_t)t.val) % 8) return set_err(nullptr, MAGNUS_EINVAL, "term %d: real CSR values must be 8-byte aligned", k);
+        break;
       case MAGNUS_TERM_DENSE:
+      case MAGNUS_TERM_DENSE_REAL:
         if (!t.val) return set_err(nullptr, MAGNUS_EINVAL, "term %d: dense matrix missing", k);
+        if (((uintptr_t)t.val) % (t.kind == MAGNUS_TERM_DENSE ? 16 : 8))
+          return set_err(nullptr, MAGNUS_EINVAL, "term %d: dense values misaligned", k);
         if (dim > 65536) return set_err(nullptr, MAGNUS_EINVAL, "term %d: dense terms need dim <= 65536", k);
         break;
       case MAGNUS_TERM_XXZ:
@@ -367,12 +393,11 @@ magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms
     const magnus_term &t = terms[k];
     Term &T = p->terms_host[k];
     memset(&T, 0, sizeof T);
-    T.kind = t.kind;
+    set_term_storage(T, t);
     T.nspins = t.nspins;
     T.nnz = t.nnz;
     T.rowptr = t.rowptr;
     T.col = t.col;
-    T.val = (const double2 *)t.val;
     T.delta = t.delta;
     if (t.kind == MAGNUS_TERM_XXZ) {
       for (int i = 0; i < t.nspins - 1; i++) T.J[i] = t.J[i];
@@ -408,6 +433,7 @@ magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms
   PLAN_TRY(dalloc(&flag, kMaxTerms));
   PLAN_TRY(cudaMemsetAsync(flag, 0, sizeof(int) * kMaxTerms, p->stream));
   for (int k = 0; k < nterms; k++) {
+    if (p->terms_host[k].rs == 1) continue;  // real storage
     if (p->terms_host[k].kind == MAGNUS_TERM_CSR && p->terms_host[k].nnz > 0)
       PLAN_TRY(launch_imag_check(p->terms_host[k].val, p->terms_host[k].nnz, flag + k, p->stream));
     if (p->terms_host[k].kind == MAGNUS_TERM_DENSE)
@@ -452,7 +478,7 @@ magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms
       for (int k = 0; k < nterms; k++)
         if (p->terms_host[k].kind == MAGNUS_TERM_DENSE) {
           PLAN_TRY(dalloc(&p->hsplit[k], (size_t)dim * dim));
-          PLAN_TRY(launch_split_dense(p->terms_host[k].val, p->hsplit[k], dim * dim, p->stream));
+          PLAN_TRY(launch_split_dense(p->terms_host[k].rv, p->terms_host[k].rs, p->hsplit[k], dim * dim, p->stream));
         }
       PLAN_TRY(dalloc(&p->sh_cur, nd));
       PLAN_TRY(dalloc(&p->sh_w0, nd));
@@ -469,7 +495,7 @@ magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms
         if (p->terms_host[k].kind == MAGNUS_TERM_DENSE) {
           PLAN_TRY(dalloc(&p->hslice[k], kDigits * (size_t)dim * dim));
           PLAN_TRY(dalloc(&p->hexp[k], (size_t)dim));
-          PLAN_TRY(launch_slice_dense(p->terms_host[k].val, dim, p->hslice[k], p->hexp[k], p->stream));
+          PLAN_TRY(launch_slice_dense(p->terms_host[k].rv, p->terms_host[k].rs, dim, p->hslice[k], p->hexp[k], p->stream));
         }
       const size_t set = kDigits * 2 * (size_t)nd;
       PLAN_TRY(dalloc(&p->sl_cur, set));

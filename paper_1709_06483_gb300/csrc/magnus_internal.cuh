@@ -21,15 +21,28 @@ struct Term {
   int kind;          // magnus_term_kind
   int nspins;        // matrix-free terms
   int real_valued;   // CSR / DENSE: every imaginary part is zero (then only the real parts are multiplied)
-  int _pad;
+  int rs;            // CSR / DENSE with real_valued: real part of entry e at rv[e * rs] (2: complex storage, 1: real storage)
   int64_t nnz;
   const int64_t *rowptr;
   const int32_t *col;
-  const double2 *val;
+  const double2 *val;  // complex storage (nullptr for real storage)
+  const double *rv;    // real parts (complex storage viewed as doubles, or the real storage itself)
   double J[kMaxSpins];   // XXZ bond couplings J_1..J_{n-1}
   double hz[kMaxSpins];  // XXZ longitudinal fields h_1..h_n
   double delta;          // XXZ zz anisotropy
 };
+
+// Public term (magnus_term) -> storage fields of the internal Term: real-storage kinds become CSR /
+// DENSE with real_valued values read at stride 1, complex storage keeps val and exposes its real
+// parts at stride 2.
+inline void set_term_storage(Term &T, const magnus_term &t) {
+  const bool real_store = t.kind == MAGNUS_TERM_CSR_REAL || t.kind == MAGNUS_TERM_DENSE_REAL;
+  T.kind = t.kind == MAGNUS_TERM_CSR_REAL ? MAGNUS_TERM_CSR : (t.kind == MAGNUS_TERM_DENSE_REAL ? MAGNUS_TERM_DENSE : t.kind);
+  T.val = real_store ? nullptr : (const double2 *)t.val;
+  T.rv = (const double *)t.val;
+  T.rs = real_store ? 1 : 2;
+  if (real_store) T.real_valued = 1;
+}
 
 // Drive coefficient f_k(t) = a0 + sum_m (ac_m cos(om_m t) + as_m sin(om_m t)).
 struct Coeff {
@@ -97,6 +110,7 @@ cudaError_t launch_gershgorin(const Term *t_dev, const Term &t_host, int64_t dim
                               double *out, cudaStream_t st);
 // Real-valuedness check of a CSR / dense term: flag (device int) set to 1 if any imaginary part != 0.
 cudaError_t launch_imag_check(const double2 *val, int64_t n, int *flag, cudaStream_t st);
+cudaError_t launch_real_parts(const double2 *z, int64_t n, double *out, int *flag, cudaStream_t st);
 // Per-exponential records + divided-difference tables for a whole propagation.
 cudaError_t launch_exp_setup(int variant, double t0, double h, int64_t nsteps, int nterms, const Coeff *coeffs,
                              const double *term_ab, const double *xi, int m_max, double rho_max, ExpRec *recs,
@@ -161,11 +175,11 @@ cudaError_t dense_max_blocks_per_sm(int *n);
 cudaError_t launch_dense_persistent(const PersistArgs &a, bool real_valued, int grid, cudaStream_t st);
 
 // Dense term (complex128, real parts used) -> bf16 digits [5][D][D] and row exponents [D].
-cudaError_t launch_slice_dense(const double2 *H, int64_t D, void *digits, int *rexp, cudaStream_t st);
+cudaError_t launch_slice_dense(const double *Hr, int rs, int64_t D, void *digits, int *rexp, cudaStream_t st);
 size_t dense_sliced_smem_bytes();
 
-// H (complex128, real parts used) -> FP32 (hi, lo) pairs, n entries.
-cudaError_t launch_split_dense(const double2 *H, float2 *out, int64_t n, cudaStream_t st);
+// H (real parts Hr[e * rs]) -> FP32 (hi, lo) pairs, n entries.
+cudaError_t launch_split_dense(const double *Hr, int rs, float2 *out, int64_t n, cudaStream_t st);
 
 // Adjoint: the augmented-block Leja kernel for one exponential and its helpers (adjoint.cu).
 struct AugArgs {

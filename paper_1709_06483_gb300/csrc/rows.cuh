@@ -12,54 +12,59 @@ namespace rows {
 // ------------------------------------------------------------- rows of H_k x
 // CSR row: sum_e val[e] x[col[e]].  Entries go in rounds of eight (real values) or four (complex)
 // so that the column/value loads and the gathers of a whole round are in flight together.
-static __device__ __forceinline__ double2 csr_row(const Term &t, const double2 *x, int64_t r) {
+template <int RS>
+static __device__ __forceinline__ double2 csr_row_real(const Term &t, const double2 *x, int64_t e, int64_t e1) {
   double2 acc = make_double2(0.0, 0.0);
+  const double *rv = t.rv;
+  for (; e + 8 <= e1; e += 8) {
+    int c[8];
+    double a[8];
+    double2 xv[8];
+#pragma unroll
+    for (int q = 0; q < 8; q++) c[q] = __ldg(t.col + e + q);
+#pragma unroll
+    for (int q = 0; q < 8; q++) a[q] = __ldg(rv + (e + q) * RS);
+#pragma unroll
+    for (int q = 0; q < 8; q++) xv[q] = ldv(x + c[q]);
+#pragma unroll
+    for (int q = 0; q < 8; q++) acc = rfma(a[q], xv[q], acc);
+  }
+  if (e + 4 <= e1) {
+    int c[4];
+    double a[4];
+    double2 xv[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) c[q] = __ldg(t.col + e + q);
+#pragma unroll
+    for (int q = 0; q < 4; q++) a[q] = __ldg(rv + (e + q) * RS);
+#pragma unroll
+    for (int q = 0; q < 4; q++) xv[q] = ldv(x + c[q]);
+#pragma unroll
+    for (int q = 0; q < 4; q++) acc = rfma(a[q], xv[q], acc);
+    e += 4;
+  }
+  for (; e < e1; e++) acc = rfma(__ldg(rv + e * RS), ldv(x + __ldg(t.col + e)), acc);
+  return acc;
+}
+
+static __device__ __forceinline__ double2 csr_row(const Term &t, const double2 *x, int64_t r) {
   int64_t e = __ldg(t.rowptr + r);
   const int64_t e1 = __ldg(t.rowptr + r + 1);
-  if (t.real_valued) {
-    for (; e + 8 <= e1; e += 8) {
-      int c[8];
-      double a[8];
-      double2 xv[8];
+  if (t.real_valued) return t.rs == 1 ? csr_row_real<1>(t, x, e, e1) : csr_row_real<2>(t, x, e, e1);
+  double2 acc = make_double2(0.0, 0.0);
+  for (; e + 4 <= e1; e += 4) {
+    int c[4];
+    double2 a[4], xv[4];
 #pragma unroll
-      for (int q = 0; q < 8; q++) c[q] = __ldg(t.col + e + q);
+    for (int q = 0; q < 4; q++) c[q] = __ldg(t.col + e + q);
 #pragma unroll
-      for (int q = 0; q < 8; q++) a[q] = __ldg(&t.val[e + q].x);
+    for (int q = 0; q < 4; q++) a[q] = __ldg(t.val + e + q);
 #pragma unroll
-      for (int q = 0; q < 8; q++) xv[q] = ldv(x + c[q]);
+    for (int q = 0; q < 4; q++) xv[q] = ldv(x + c[q]);
 #pragma unroll
-      for (int q = 0; q < 8; q++) acc = rfma(a[q], xv[q], acc);
-    }
-    if (e + 4 <= e1) {
-      int c[4];
-      double a[4];
-      double2 xv[4];
-#pragma unroll
-      for (int q = 0; q < 4; q++) c[q] = __ldg(t.col + e + q);
-#pragma unroll
-      for (int q = 0; q < 4; q++) a[q] = __ldg(&t.val[e + q].x);
-#pragma unroll
-      for (int q = 0; q < 4; q++) xv[q] = ldv(x + c[q]);
-#pragma unroll
-      for (int q = 0; q < 4; q++) acc = rfma(a[q], xv[q], acc);
-      e += 4;
-    }
-    for (; e < e1; e++) acc = rfma(__ldg(&t.val[e].x), ldv(x + __ldg(t.col + e)), acc);
-  } else {
-    for (; e + 4 <= e1; e += 4) {
-      int c[4];
-      double2 a[4], xv[4];
-#pragma unroll
-      for (int q = 0; q < 4; q++) c[q] = __ldg(t.col + e + q);
-#pragma unroll
-      for (int q = 0; q < 4; q++) a[q] = __ldg(t.val + e + q);
-#pragma unroll
-      for (int q = 0; q < 4; q++) xv[q] = ldv(x + c[q]);
-#pragma unroll
-      for (int q = 0; q < 4; q++) acc = cfma(a[q], xv[q], acc);
-    }
-    for (; e < e1; e++) acc = cfma(__ldg(t.val + e), ldv(x + __ldg(t.col + e)), acc);
+    for (int q = 0; q < 4; q++) acc = cfma(a[q], xv[q], acc);
   }
+  for (; e < e1; e++) acc = cfma(__ldg(t.val + e), ldv(x + __ldg(t.col + e)), acc);
   return acc;
 }
 

@@ -305,13 +305,17 @@ __global__ void k_exp_setup_beta(BetaArg beta, int nterms, const double *term_ab
 // --------------------------------------------------------------- Gershgorin
 // spec(H) within [min_i (Re H_ii - R_i), max_i (Re H_ii + R_i)], R_i = sum_{j != i} |H_ij|.
 __device__ __forceinline__ double cabs_(double2 v) { return hypot(v.x, v.y); }
+// entry e of a CSR / dense term in either storage
+__device__ __forceinline__ double2 term_val(const Term &t, int64_t e) {
+  return t.rs == 1 ? make_double2(t.rv[e], 0.0) : t.val[e];
+}
 
 __device__ void row_center_radius(const Term &t, int64_t dim, int64_t i, double &c, double &R) {
   c = 0.0;
   R = 0.0;
   if (t.kind == MAGNUS_TERM_CSR) {
     for (int64_t e = t.rowptr[i]; e < t.rowptr[i + 1]; e++) {
-      double2 v = t.val[e];
+      double2 v = term_val(t, e);
       if (t.col[e] == i) c += v.x; else R += cabs_(v);
     }
   } else if (t.kind == MAGNUS_TERM_XXZ) {
@@ -340,9 +344,8 @@ __global__ void k_gershgorin_rows(const Term *tp, int64_t dim, double *part) {
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t i = warp; i < dim; i += nwarps) {
       double c = 0.0, R = 0.0;
-      const double2 *row = t.val + i * dim;
       for (int64_t j = lane; j < dim; j += 32) {
-        double2 v = row[j];
+        double2 v = term_val(t, i * dim + j);
         if (j == i) c += v.x; else R += cabs_(v);
       }
       c = warp_sum(c);
@@ -387,6 +390,16 @@ __global__ void k_imag_check(const double2 *val, int64_t n, int *flag) {
   bool any = false;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     any |= (val[i].y != 0.0);
+  if (__any_sync(kFull, any) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+}
+
+__global__ void k_real_parts(const double2 *z, int64_t n, double *out, int *flag) {
+  bool any = false;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 v = z[i];
+    out[i] = v.x;
+    any |= (v.y != 0.0);
+  }
   if (__any_sync(kFull, any) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
 }
 
@@ -556,6 +569,11 @@ cudaError_t launch_gershgorin(const Term *t_dev, const Term &t_host, int64_t dim
 
 cudaError_t launch_imag_check(const double2 *val, int64_t n, int *flag, cudaStream_t st) {
   k_imag_check<<<grid_for(n, 256), 256, 0, st>>>(val, n, flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_real_parts(const double2 *z, int64_t n, double *out, int *flag, cudaStream_t st) {
+  k_real_parts<<<grid_for(n, 256), 256, 0, st>>>(z, n, out, flag);
   return cudaGetLastError();
 }
 

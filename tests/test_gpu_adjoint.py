@@ -34,7 +34,7 @@ def control_chain(n, nmodes, T, seed):
     return c, ck, om, phi
 
 
-@pytest.mark.parametrize("kind", ["csr", "mfree"])
+@pytest.mark.parametrize("kind", ["csr", "csr_real", "mfree"])
 @pytest.mark.parametrize("variant,ckpt", [("CF4", 3), ("CF4_3", 4), ("M2", 7)])
 def test_adjoint_matches_oracle(mg, kind, variant, ckpt):
     n, nmodes, T, h, N = 8, 6, 1.0, 0.04, 25
@@ -42,6 +42,8 @@ def test_adjoint_matches_oracle(mg, kind, variant, ckpt):
     ac = 0.1 * np.ones(nmodes)
     if kind == "csr":
         terms = [mg.build_xxz_csr(n, c.J, c.hz, c.delta), mg.build_field_x_csr(n)]
+    elif kind == "csr_real":
+        terms = [mg.build_xxz_csr(n, c.J, c.hz, c.delta).as_real(), mg.build_field_x_csr(n).as_real()]
     else:
         terms = [mg.XXZTerm(n, c.J, c.hz, c.delta), mg.FieldXTerm(n)]
     plan = mg.Plan(c.dim, terms, [mg.Drive.const(), mg.Drive(0.2, ac, ck, om)], tol=1e-12)

@@ -32,6 +32,8 @@ def problems(mg, chains, kind):
     for c in chains:
         if kind == "csr":
             terms = [mg.build_xxz_csr(c.nspins, c.J, c.hz, c.delta), mg.build_field_x_csr(c.nspins)]
+        elif kind == "csr_real":
+            terms = [mg.build_xxz_csr(c.nspins, c.J, c.hz, c.delta).as_real(), mg.build_field_x_csr(c.nspins).as_real()]
         else:
             terms = [mg.XXZTerm(c.nspins, c.J, c.hz, c.delta), mg.FieldXTerm(c.nspins)]
         out.append((c.dim, terms, [mg.Drive.const(), mg.Drive(c.drive_a0, c.drive_ac, c.drive_as, c.drive_om)]))
@@ -51,7 +53,7 @@ def small_chains():
     return mi.workload4(count=14, nmin=3, nmax=9, nsteps=12)
 
 
-@pytest.mark.parametrize("kind", ["csr", "mfree"])
+@pytest.mark.parametrize("kind", ["csr", "csr_real", "mfree"])
 @pytest.mark.parametrize("variant", ["CF4", "M4"])
 def test_batch_matches_oracle(mg, small_chains, kind, variant):
     chains = small_chains

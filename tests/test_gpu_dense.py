@@ -192,3 +192,22 @@ def test_tensor_sliced_rejects_unsupported(mg):
         mg.Plan(64, [mg.DenseTerm(cuda((B + B.T).astype(np.complex128)))], [mg.Drive.const()], nvec=2,
                 precision=mg.TENSOR_SLICED)
     assert e.value.code == mg.EINVAL
+
+
+@pytest.mark.parametrize("precision", ["FP64", "FP32_SPLIT", "TENSOR_SLICED"])
+@pytest.mark.parametrize("nvec", [1, 4])
+def test_dense_real_storage(mg, precision, nvec):
+    """MAGNUS_TERM_DENSE_REAL (float64, 8 B per element) in every precision against the oracle."""
+    c = mi.workload3(nvec=nvec, nspins=8, h=0.02, nsteps=6)
+    Hs = mg.DenseTerm(mg.build_longrange_dense(c.nspins, c.hz, 1.5, c.delta)).as_real()
+    Hd = mg.DenseTerm(mg.build_field_x_dense(c.nspins)).as_real()
+    assert Hs.real and Hs.val.dtype == torch.float64
+    plan = mg.Plan(c.dim, [Hs, Hd], drive_pair(mg, c), nvec=nvec, precision=getattr(mg, precision))
+    psi = cuda(c.psi0)
+    plan.propagate(psi, 0.0, c.h, c.nsteps, "CF4")
+    P = oracle_dense(c, oracle.longrange_dense(c.nspins, c.hz, 1.5, c.delta), oracle.field_x_dense(c.nspins))
+    out = psi.cpu().numpy().reshape(nvec, -1)
+    tol = REL_TOL if precision == "FP64" else 1e-9
+    for v in range(nvec):
+        ref = P.propagate(c.psi0.reshape(nvec, -1)[v], 0.0, c.h, c.nsteps, "CF4")
+        assert rel(out[v], ref) < tol, (v, rel(out[v], ref))

@@ -36,6 +36,8 @@ def chain_terms(mg, c, kind):
     n = c.nspins
     if kind == "csr":
         return [mg.build_xxz_csr(n, c.J, c.hz, c.delta), mg.build_field_x_csr(n)]
+    if kind == "csr_real":  # float64 value arrays (MAGNUS_TERM_CSR_REAL)
+        return [mg.build_xxz_csr(n, c.J, c.hz, c.delta).as_real(), mg.build_field_x_csr(n).as_real()]
     if kind == "mfree":
         return [mg.XXZTerm(n, c.J, c.hz, c.delta), mg.FieldXTerm(n)]
     raise ValueError(kind)
@@ -122,8 +124,32 @@ def test_expv_parity(mg, kind, beta):
     assert np.array_equal(st["m_log"], ost.m_log)
 
 
+# ----------------------------------------------------------------- real-valued storage
+def test_real_storage_same_arithmetic_as_complex_storage(mg):
+    """Real storage multiplies the same real parts in the same order as complex storage with zero
+    imaginary parts, so the two propagations agree bit for bit (and with the oracle to 1e-10)."""
+    c = mi.xxz_chain(23, 10, 0.01, 20)
+    out = {}
+    for kind in ("csr", "csr_real"):
+        plan = mg.Plan(c.dim, chain_terms(mg, c, kind), drives_gpu(mg, c))
+        psi = cuda(c.psi0)
+        plan.propagate(psi, 0.0, c.h, c.nsteps, "CF4")
+        out[kind] = psi.cpu().numpy()
+    assert np.array_equal(out["csr"], out["csr_real"])
+    assert rel(out["csr_real"], oracle_problem(c).propagate(c.psi0, 0.0, c.h, c.nsteps, "CF4")) < REL_TOL
+
+
+def test_real_parts_rejects_complex_values(mg):
+    z = torch.tensor([1.0 + 0j, 2.0 + 1e-300j], dtype=torch.complex128, device="cuda")
+    with pytest.raises(mg.MagnusError) as e:
+        mg.real_parts(z)
+    assert e.value.code == mg.EINVAL
+    r = mg.real_parts(torch.tensor([1.5 + 0j, -2.0 + 0j], dtype=torch.complex128, device="cuda"))
+    assert r.dtype == torch.float64 and r.cpu().tolist() == [1.5, -2.0]
+
+
 # ----------------------------------------------------------------- propagation, workload 1
-@pytest.mark.parametrize("kind", ["csr", "mfree"])
+@pytest.mark.parametrize("kind", ["csr", "csr_real", "mfree"])
 @pytest.mark.parametrize("variant", ["CF4", "M4"])
 def test_propagate_workload1(mg, kind, variant):
     c = mi.workload1()
@@ -137,10 +163,11 @@ def test_propagate_workload1(mg, kind, variant):
     assert rel(psi.cpu().numpy(), ref) < REL_TOL
 
 
+@pytest.mark.parametrize("kind", ["csr", "csr_real"])
 @pytest.mark.parametrize("variant", ["CF4_3", "M2"])
-def test_propagate_other_methods(mg, variant):
+def test_propagate_other_methods(mg, variant, kind):
     c = mi.xxz_chain(21, 9, 0.02, 30)
-    plan = mg.Plan(c.dim, chain_terms(mg, c, "csr"), drives_gpu(mg, c))
+    plan = mg.Plan(c.dim, chain_terms(mg, c, kind), drives_gpu(mg, c))
     psi = cuda(c.psi0)
     plan.propagate(psi, 0.1, c.h, c.nsteps, variant)
     ref = oracle_problem(c).propagate(c.psi0, 0.1, c.h, c.nsteps, variant)
@@ -151,7 +178,7 @@ def test_propagate_other_methods(mg, variant):
 def test_ragged_block_partitions(mg, ctas):
     """Many tiles and a ragged tail: 2^11 rows over ctas blocks of 256 threads."""
     c = mi.xxz_chain(22, 11, 0.01, 10)
-    for kind in ("csr", "mfree"):
+    for kind in ("csr", "csr_real", "mfree"):
         plan = mg.Plan(c.dim, chain_terms(mg, c, kind), drives_gpu(mg, c), ctas=ctas)
         psi = cuda(c.psi0)
         plan.propagate(psi, 0.0, c.h, c.nsteps, "M4")
