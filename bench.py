@@ -158,8 +158,11 @@ class ClockSampler:
 
 
 def kernel_source_hash():
-    p = os.path.join(ROOT, "paper_1709_06483_gb300", "csrc", "leja_persistent.cu")
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+    """Hash of every source file k_magnus_persistent is compiled from."""
+    h = hashlib.sha256()
+    for f in ("leja_persistent.cu", "rows.cuh", "persist_common.cuh", "magnus_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1709_06483_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def profiled_traffic(workload_key):

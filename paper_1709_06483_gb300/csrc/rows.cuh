@@ -143,8 +143,10 @@ struct Ctx {
 };
 
 // H_xxz row with the diagonal from the two tables (FAM_MF).  coefj: per-bond coefficients.
-// Every bond's partner entry is loaded whether or not the bond is active (all loads in flight at
-// once); only the multiply-add depends on the spins.
+// The bonds are visited over the union of the active (anti-parallel) bonds of the warp's rows: a
+// warp's rows share their high bits, so high bonds are active for all lanes or none and an inactive
+// one costs no FP64 slot; only the low bonds (bits below 5) are taken per lane.  Ascending bond order
+// in every case, so the sum is the same as over all active bonds in order.
 [[maybe_unused]] constexpr int kMaxBonds = kMaxSpins - 1;
 static __device__ __forceinline__ double2 mf_xxz_row(const Ctx &c, const double *coefj, double dscale, double dshift,
                                               const double2 *x, int64_t r, double2 &xr) {
@@ -155,15 +157,28 @@ static __device__ __forceinline__ double2 mf_xxz_row(const Ctx &c, const double 
   acc.x = cr * xr.x;
   acc.y = cr * xr.y;
   const int nb = c.n - 1;
-  for (int p0 = 0; p0 < nb; p0 += 4) {
+  // bit b of `mine`: bond at bits (b + 1, b) is anti-parallel in row r
+  const unsigned mine = (unsigned)((r ^ (r >> 1)) & (((int64_t)1 << nb) - 1));
+  unsigned mw = __reduce_or_sync(__activemask(), mine);
+  while (__popc(mw) >= 4) {
+    int bq[4];
     double2 v[4];
 #pragma unroll
-    for (int q = 0; q < 4; q++) v[q] = ldv(x + (r ^ ((int64_t)3 << min(p0 + q, nb - 1))));
-#pragma unroll
     for (int q = 0; q < 4; q++) {
-      const int p = p0 + q + 1;  // bond at bits (p, p-1)
-      if (p <= nb && (((r >> p) ^ (r >> (p - 1))) & 1)) acc = rfma(coefj[p - 1], v[q], acc);
+      bq[q] = __ffs(mw) - 1;
+      mw &= mw - 1;
     }
+#pragma unroll
+    for (int q = 0; q < 4; q++) v[q] = ldv(x + (r ^ ((int64_t)3 << bq[q])));
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+      if ((mine >> bq[q]) & 1u) acc = rfma(coefj[bq[q]], v[q], acc);
+  }
+  while (mw) {
+    const int b = __ffs(mw) - 1;
+    mw &= mw - 1;
+    const double2 v = ldv(x + (r ^ ((int64_t)3 << b)));
+    if ((mine >> b) & 1u) acc = rfma(coefj[b], v, acc);
   }
   return acc;
 }
