@@ -266,6 +266,7 @@ struct magnus_batch_s {
   magnus_options opt{};
   std::vector<int64_t> dims;
   std::vector<int> nterms;
+  int *nterms_dev = nullptr;      // [count]
   std::vector<std::vector<Term>> terms_host;
   std::vector<std::vector<Coeff>> coeffs_host;
   std::vector<int> lbits;
@@ -342,11 +343,8 @@ void batch_free(magnus_batch_t b) {
 magnus_status enqueue_run(magnus_batch_t b, int variant, double t0, double h, int64_t nsteps, int bs, int cs,
                           const BatchItem *items_dev) {
   const int64_t nexp = nsteps * exps_per_step(variant);
-  for (int i = 0; i < b->count; i++)
-    BTRY(b, launch_exp_setup(variant, t0, h, nsteps, b->nterms[i], b->coeffs + (size_t)i * kMaxTerms,
-                             b->term_ab + (size_t)i * 2 * kMaxTerms, b->xi, b->opt.m_max, b->opt.rho_max,
-                             b->recs + (size_t)i * b->recs_cap, b->dd + (size_t)i * b->recs_cap * (b->opt.m_max + 1),
-                             nexp, b->stream));
+  BTRY(b, launch_exp_setup_batch(variant, t0, h, nsteps, b->count, b->nterms_dev, b->coeffs, b->term_ab, b->xi,
+                                 b->opt.m_max, b->opt.rho_max, b->recs, b->dd, b->recs_cap, b->stream));
   BTRY(b, cudaMemsetAsync(b->next, 0, sizeof(unsigned), b->stream));
   BTRY(b, cudaMemsetAsync(b->counters, 0, sizeof(Counters), b->stream));
   BatchArgs A{};
@@ -497,6 +495,7 @@ MAGNUS_API magnus_status magnus_batch_create(magnus_batch_t *out, int32_t count,
   BCREATE(balloc(b, &b->next, 1));
   BCREATE(balloc(b, &b->counters, 1));
   BCREATE(balloc(b, &b->order, count));
+  BCREATE(balloc(b, &b->nterms_dev, count));
   BCREATE(balloc(b, &b->items_dev, count));
   size_t total = 0;
   b->scratch_off.resize(count);
@@ -557,6 +556,7 @@ MAGNUS_API magnus_status magnus_batch_create(magnus_batch_t *out, int32_t count,
   std::iota(ord.begin(), ord.end(), 0);
   std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return b->dims[x] > b->dims[y]; });
   BCREATE(cudaMemcpyAsync(b->order, ord.data(), sizeof(int) * count, cudaMemcpyHostToDevice, b->stream));
+  BCREATE(cudaMemcpyAsync(b->nterms_dev, b->nterms.data(), sizeof(int) * count, cudaMemcpyHostToDevice, b->stream));
   std::vector<double> ab((size_t)count * 2 * kMaxTerms);
   BCREATE(cudaMemcpyAsync(ab.data(), b->term_ab, sizeof(double) * ab.size(), cudaMemcpyDeviceToHost, b->stream));
   BCREATE(cudaStreamSynchronize(b->stream));

@@ -116,6 +116,9 @@ cudaError_t launch_exp_setup(int variant, double t0, double h, int64_t nsteps, i
                              const double *term_ab, const double *xi, int m_max, double rho_max, ExpRec *recs,
                              double2 *dd, int64_t nexp, cudaStream_t st);
 // Records for a single exponential exp(-i sum_k beta_k H_k) (beta on the host).
+cudaError_t launch_exp_setup_batch(int variant, double t0, double h, int64_t nsteps, int count, const int *nterms_dev,
+                                   const Coeff *coeffs, const double *term_ab, const double *xi, int m_max,
+                                   double rho_max, ExpRec *recs, double2 *dd, int64_t rec_stride, cudaStream_t st);
 cudaError_t launch_exp_setup_beta(const double *beta_host, int nterms, const double *term_ab, const double *xi,
                                   int m_max, double rho_max, ExpRec *recs, double2 *dd, cudaStream_t st);
 

@@ -208,11 +208,9 @@ __device__ void finish_record(ExpRec &R, const double *lin, int nterms, const do
 //         coef_kl = f_k(t2) f_l(t1) - f_l(t2) f_k(t1)  ([H_2,H_1] = sum_{k<l} coef_kl [H_k,H_l]).
 //  Cf4:   stage 0 (applied first): h (a2 f(t1) + a1 f(t2)), stage 1: h (a1 f(t1) + a2 f(t2)).
 //  Cf4:3: stage 0 uses the third row of the alpha table, stage 2 the first.
-__global__ void k_exp_setup(int variant, double t0, double h, long long nsteps, int nterms, const Coeff *coeffs,
-                            const double *term_ab, const double *xi, int m_max, double rho_max, ExpRec *recs,
-                            double2 *dd, long long nexp, int per_step) {
-  const long long e = (long long)blockIdx.x * (blockDim.x / 32) + (threadIdx.x / 32);
-  if (e >= nexp) return;  // whole warp exits together
+__device__ void exp_setup_warp(long long e, int variant, double t0, double h, int nterms, const Coeff *coeffs,
+                               const double *term_ab, const double *xi, int m_max, double rho_max, ExpRec *recs,
+                               double2 *dd, int per_step) {
   const int lane = threadIdx.x & 31;
   const long long n = e / per_step;
   const int stage = (int)(e % per_step);
@@ -277,6 +275,28 @@ __global__ void k_exp_setup(int variant, double t0, double h, long long nsteps, 
     for (int j = 1 + lane; j <= m_max; j += 32) d[j] = make_double2(0.0, 0.0);
   }
   if (lane == 0) recs[e] = R;
+}
+
+// one warp per exponential
+__global__ void k_exp_setup(int variant, double t0, double h, int nterms, const Coeff *coeffs, const double *term_ab,
+                            const double *xi, int m_max, double rho_max, ExpRec *recs, double2 *dd, long long nexp,
+                            int per_step) {
+  const long long e = (long long)blockIdx.x * (blockDim.x / 32) + (threadIdx.x / 32);
+  if (e >= nexp) return;  // whole warp exits together
+  exp_setup_warp(e, variant, t0, h, nterms, coeffs, term_ab, xi, m_max, rho_max, recs, dd, per_step);
+}
+
+// one warp per (problem, exponential) of a batch: problem i has nterms[i] terms, coefficients at
+// coeffs + i kMaxTerms, enclosures at term_ab + 2 i kMaxTerms, records at recs + i rec_stride and
+// tables at dd + i rec_stride (m_max + 1)
+__global__ void k_exp_setup_batch(int variant, double t0, double h, int count, const int *nterms, const Coeff *coeffs,
+                                  const double *term_ab, const double *xi, int m_max, double rho_max, ExpRec *recs,
+                                  double2 *dd, long long nexp, long long rec_stride, int per_step) {
+  const long long g = (long long)blockIdx.x * (blockDim.x / 32) + (threadIdx.x / 32);
+  if (g >= (long long)count * nexp) return;
+  const long long i = g / nexp, e = g % nexp;
+  exp_setup_warp(e, variant, t0, h, nterms[i], coeffs + i * kMaxTerms, term_ab + i * 2 * kMaxTerms, xi, m_max,
+                 rho_max, recs + i * rec_stride, dd + i * rec_stride * (m_max + 1), per_step);
 }
 
 struct BetaArg {
@@ -582,8 +602,21 @@ cudaError_t launch_exp_setup(int variant, double t0, double h, int64_t nsteps, i
                              double2 *dd, int64_t nexp, cudaStream_t st) {
   const int warps = 4;
   int64_t blocks = (nexp + warps - 1) / warps;
-  k_exp_setup<<<(unsigned)blocks, 32 * warps, 0, st>>>(variant, t0, h, nsteps, nterms, coeffs, term_ab, xi, m_max,
-                                                        rho_max, recs, dd, nexp, exps_per_step(variant));
+  k_exp_setup<<<(unsigned)blocks, 32 * warps, 0, st>>>(variant, t0, h, nterms, coeffs, term_ab, xi, m_max, rho_max,
+                                                        recs, dd, nexp, exps_per_step(variant));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_exp_setup_batch(int variant, double t0, double h, int64_t nsteps, int count, const int *nterms_dev,
+                                   const Coeff *coeffs, const double *term_ab, const double *xi, int m_max,
+                                   double rho_max, ExpRec *recs, double2 *dd, int64_t rec_stride, cudaStream_t st) {
+  const int64_t nexp = nsteps * exps_per_step(variant);
+  const int warps = 4;
+  const int64_t blocks = ((int64_t)count * nexp + warps - 1) / warps;
+  if (blocks == 0) return cudaSuccess;
+  k_exp_setup_batch<<<(unsigned)blocks, 32 * warps, 0, st>>>(variant, t0, h, count, nterms_dev, coeffs, term_ab, xi,
+                                                              m_max, rho_max, recs, dd, nexp, rec_stride,
+                                                              exps_per_step(variant));
   return cudaGetLastError();
 }
 
