@@ -26,8 +26,8 @@ _lock = threading.Lock()
 _lib = None
 
 OK, EINVAL, ENOMEM, ENOCONV, ENONFINITE = 0, 1, 2, 4, 5
-M4, CF4, CF4_3, M2 = 1, 2, 3, 4
-VARIANTS = {"M4": M4, "CF4": CF4, "CF4_3": CF4_3, "M2": M2}
+M4, CF4, CF4_3, M2, M6 = 1, 2, 3, 4, 5
+VARIANTS = {"M4": M4, "CF4": CF4, "CF4_3": CF4_3, "M2": M2, "M6": M6}
 
 
 class OracleError(RuntimeError):

@@ -25,6 +25,11 @@
  *    enclosure of a combination sum_k beta_k H_k is the Minkowski sum of the
  *    scaled intervals (Weyl); the M4 commutator adds [-r, r] with
  *    r = kappa * sum_{k<l} |coef_kl| * 2 * hw_k * hw_l (hw = half-width).
+ *  - Method M6: the coefficient of B_3 is 1/12 (the printed 1/2 would break
+ *    the exactness of the first Magnus term for quadratic A; with 1/12,
+ *    B_1 + B_3/12 is the 3-point Gauss rule h(5 A_1 + 8 A_2 + 5 A_3)/18).
+ *    Its nested commutators add [-r, r], r a bound of |(i/240)[U, V]| from the
+ *    half-widths of the terms' enclosures (see gen_interval).
  */
 #include "magnus_oracle.h"
 
@@ -439,16 +444,18 @@ int orc_apply_term(const orc_problem *p, int k, const double complex *x, double 
 /* Generators K (one exponential exp(-iK)).                                   */
 /* ------------------------------------------------------------------------- */
 
-enum { GEN_LINEAR = 0, GEN_M4 = 1 };
+enum { GEN_LINEAR = 0, GEN_M4 = 1, GEN_M6 = 2 };
 
 typedef struct {
   const orc_problem *p;
   int mode;
   double beta[MAX_TERMS]; /* GEN_LINEAR: K = sum_k beta_k H_k                                */
-  double f1[MAX_TERMS];   /* GEN_M4: f_k(t_n + c_1 h)                                        */
-  double f2[MAX_TERMS];   /*         f_k(t_n + c_2 h)                                        */
+  double f1[MAX_TERMS];   /* GEN_M4, GEN_M6: f_k(t_n + c_1 h)                                */
+  double f2[MAX_TERMS];   /*                 f_k(t_n + c_2 h)                                */
+  double f3[MAX_TERMS];   /* GEN_M6:         f_k(t_n + c_3 h)                                */
   double h;               /*         step size                                               */
   double complex *u1, *u2, *t1, *t2; /* scratch of length dim                               */
+  double complex *s6[12];            /* GEN_M6 scratch of length dim                        */
   orc_stats *st;
 } orc_gen;
 
@@ -472,10 +479,89 @@ static void apply_combo(const orc_gen *g, const double *coef, const double compl
  *         = -i [ h/2 (H_1 + H_2) - i (sqrt(3) h^2/12) [H_2, H_1] ] = -i K,
  * with the commutator applied to a vector as H_2(H_1 x) - H_1(H_2 x).
  */
+/*
+ * Method M6 (Sec. 2) with A_i = -i H(t_n + c_i h), c = 1/2 -+ sqrt(15)/10, 1/2:
+ *   B_1 = h A_2,  B_2 = (sqrt(15)/3) h (A_3 - A_1),  B_3 = (10/3) h (A_3 - 2 A_2 + A_1),
+ *   Omega = B_1 + B_3/12 + (1/240) [U, V],
+ *   U = -20 B_1 - B_3 + [B_1, B_2],   V = B_2 - (1/60) [B_1, 2 B_3 + [B_1, B_2]],
+ * every operator applied to vectors ([F, G] x = F(G x) - G(F x)); K = i Omega.
+ */
+static void m6_apply_B(orc_gen *g, int j, const double complex *x, double complex *y) {
+  const double r15 = sqrt(15.0);
+  double coef[MAX_TERMS];
+  for (int k = 0; k < g->p->nterms; k++) {
+    if (j == 1) coef[k] = g->h * g->f2[k];
+    else if (j == 2) coef[k] = r15 / 3.0 * g->h * (g->f3[k] - g->f1[k]);
+    else coef[k] = 10.0 / 3.0 * g->h * (g->f3[k] - 2.0 * g->f2[k] + g->f1[k]);
+  }
+  apply_combo(g, coef, x, y, g->t1); /* y = sum_k coef_k H_k x; B_j x = -i y */
+  const int64_t D = g->p->dim;
+  for (int64_t i = 0; i < D; i++) y[i] *= -I;
+}
+
+/* y = [B_1, B_2] x; uses s6[10], s6[11] */
+static void m6_apply_B12(orc_gen *g, const double complex *x, double complex *y) {
+  const int64_t D = g->p->dim;
+  double complex *a = g->s6[10], *b = g->s6[11];
+  m6_apply_B(g, 2, x, a);
+  m6_apply_B(g, 1, a, y);  /* B_1 (B_2 x) */
+  m6_apply_B(g, 1, x, a);
+  m6_apply_B(g, 2, a, b);  /* B_2 (B_1 x) */
+  for (int64_t i = 0; i < D; i++) y[i] -= b[i];
+}
+
+/* y = U x = -20 B_1 x - B_3 x + [B_1, B_2] x; uses s6[7..11] */
+static void m6_apply_U(orc_gen *g, const double complex *x, double complex *y) {
+  const int64_t D = g->p->dim;
+  double complex *b1 = g->s6[7], *b3 = g->s6[8];
+  m6_apply_B(g, 1, x, b1);
+  m6_apply_B(g, 3, x, b3);
+  m6_apply_B12(g, x, y);
+  for (int64_t i = 0; i < D; i++) y[i] += -20.0 * b1[i] - b3[i];
+}
+
+/* y = W x = 2 B_3 x + [B_1, B_2] x; uses s6[9..11] */
+static void m6_apply_W(orc_gen *g, const double complex *x, double complex *y) {
+  const int64_t D = g->p->dim;
+  double complex *b3 = g->s6[9];
+  m6_apply_B12(g, x, y);
+  m6_apply_B(g, 3, x, b3);
+  for (int64_t i = 0; i < D; i++) y[i] += 2.0 * b3[i];
+}
+
+/* y = V x = B_2 x - (1/60) (B_1 (W x) - W (B_1 x)); uses s6[4..11] */
+static void m6_apply_V(orc_gen *g, const double complex *x, double complex *y) {
+  const int64_t D = g->p->dim;
+  double complex *wx = g->s6[4], *b1wx = g->s6[5], *b1x = g->s6[6], *wb1x = g->s6[7];
+  m6_apply_W(g, x, wx);
+  m6_apply_B(g, 1, wx, b1wx);
+  m6_apply_B(g, 1, x, b1x);
+  m6_apply_W(g, b1x, wb1x);
+  m6_apply_B(g, 2, x, y);
+  for (int64_t i = 0; i < D; i++) y[i] -= (b1wx[i] - wb1x[i]) / 60.0;
+}
+
+static void m6_apply_K(orc_gen *g, const double complex *x, double complex *y) {
+  const int64_t D = g->p->dim;
+  double complex *ux = g->s6[0], *vx = g->s6[1], *uvx = g->s6[2], *vux = g->s6[3];
+  m6_apply_U(g, x, ux);
+  m6_apply_V(g, x, vx);
+  m6_apply_U(g, vx, uvx);
+  m6_apply_V(g, ux, vux);
+  /* Omega x = B_1 x + B_3 x / 12 + (U V x - V U x) / 240 (B_1 x, B_3 x into ux, vx) */
+  m6_apply_B(g, 1, x, ux);
+  m6_apply_B(g, 3, x, vx);
+  for (int64_t i = 0; i < D; i++) y[i] = I * (ux[i] + vx[i] / 12.0 + (uvx[i] - vux[i]) / 240.0);
+}
+
 static void gen_apply(orc_gen *g, const double complex *x, double complex *y) {
   const int64_t D = g->p->dim;
   if (g->mode == GEN_LINEAR) {
     apply_combo(g, g->beta, x, y, g->t1);
+    return;
+  }
+  if (g->mode == GEN_M6) {
+    m6_apply_K(g, x, y);
     return;
   }
   const double kappa = sqrt(3.0) * g->h * g->h / 12.0;
@@ -492,8 +578,12 @@ static void gen_interval(const orc_gen *g, double *a, double *b) {
   const orc_problem *p = g->p;
   double lo = 0.0, hi = 0.0;
   double lin[MAX_TERMS];
-  for (int k = 0; k < p->nterms; k++)
-    lin[k] = (g->mode == GEN_LINEAR) ? g->beta[k] : 0.5 * g->h * (g->f1[k] + g->f2[k]);
+  for (int k = 0; k < p->nterms; k++) {
+    if (g->mode == GEN_LINEAR) lin[k] = g->beta[k];
+    else if (g->mode == GEN_M4) lin[k] = 0.5 * g->h * (g->f1[k] + g->f2[k]);
+    else /* GEN_M6: i (B_1 + B_3 / 12) = h (f_2 + (10/36)(f_3 - 2 f_2 + f_1)) */
+      lin[k] = g->h * (g->f2[k] + 10.0 / 36.0 * (g->f3[k] - 2.0 * g->f2[k] + g->f1[k]));
+  }
   for (int k = 0; k < p->nterms; k++) {
     double x1 = lin[k] * p->term[k].a, x2 = lin[k] * p->term[k].b;
     lo += (x1 < x2) ? x1 : x2;
@@ -511,6 +601,41 @@ static void gen_interval(const orc_gen *g, double *a, double *b) {
       }
     lo -= kappa * r;
     hi += kappa * r;
+  }
+  if (g->mode == GEN_M6) {
+    /* B_1 = -iP, B_2 = -iQ, B_3 = -iR with P, Q, R = sum_k {p,q,r}_k H_k, S = 20 P + R, C = [P,Q]:
+     *   U = iS - C,  V = -iQ + E,  E = [P,R]/30 - (i/60)[P,C],
+     *   [U,V] = [S,Q] + i[S,E] - [C,V].
+     * Shifting any H_k by a multiple of I changes no commutator, so with the half-widths hw_k:
+     *   |[F,G]| <= sum_{k<l} |f_k g_l - f_l g_k| 2 hw_k hw_l  (F, G combinations of the H_k),
+     *   |[F,M]| <= 2 |F| |M|,  |F| <= sum_k |f_k| hw_k  (after the shift),
+     * so |(i/240)[U,V]| <= r = (|[S,Q]| + 2|S||E| + 2|C||V|) / 240 with
+     *   |E| <= |[P,R]|/30 + |P||C|/30,  |V| <= |Q| + |E|. */
+    const double r15 = sqrt(15.0);
+    double pk[MAX_TERMS], qk[MAX_TERMS], rk[MAX_TERMS], sk[MAX_TERMS], hw[MAX_TERMS];
+    for (int k = 0; k < p->nterms; k++) {
+      pk[k] = g->h * g->f2[k];
+      qk[k] = r15 / 3.0 * g->h * (g->f3[k] - g->f1[k]);
+      rk[k] = 10.0 / 3.0 * g->h * (g->f3[k] - 2.0 * g->f2[k] + g->f1[k]);
+      sk[k] = 20.0 * pk[k] + rk[k];
+      hw[k] = 0.5 * (p->term[k].b - p->term[k].a);
+    }
+    double pq = 0.0, pr = 0.0, sq = 0.0, pn = 0.0, sn = 0.0, qn = 0.0;
+    for (int k = 0; k < p->nterms; k++) {
+      pn += fabs(pk[k]) * hw[k];
+      sn += fabs(sk[k]) * hw[k];
+      qn += fabs(qk[k]) * hw[k];
+      for (int l = k + 1; l < p->nterms; l++) {
+        pq += fabs(pk[k] * qk[l] - pk[l] * qk[k]) * 2.0 * hw[k] * hw[l];
+        pr += fabs(pk[k] * rk[l] - pk[l] * rk[k]) * 2.0 * hw[k] * hw[l];
+        sq += fabs(sk[k] * qk[l] - sk[l] * qk[k]) * 2.0 * hw[k] * hw[l];
+      }
+    }
+    const double en = pr / 30.0 + pn * pq / 30.0;
+    const double vn = qn + en;
+    const double r = (sq + 2.0 * sn * en + 2.0 * pq * vn) / 240.0;
+    lo -= r;
+    hi += r;
   }
   *a = lo;
   *b = hi;
@@ -593,7 +718,19 @@ static int gen_alloc(orc_gen *g, const orc_problem *p, orc_stats *st) {
   return ORC_OK;
 }
 
-static void gen_free(orc_gen *g) { free(g->u1); free(g->u2); free(g->t1); free(g->t2); }
+static int gen_alloc_m6(orc_gen *g) {
+  size_t bytes = sizeof(double complex) * (size_t)g->p->dim;
+  for (int q = 0; q < 12; q++) {
+    if (!g->s6[q]) g->s6[q] = (double complex *)malloc(bytes);
+    if (!g->s6[q]) return ORC_ENOMEM;
+  }
+  return ORC_OK;
+}
+
+static void gen_free(orc_gen *g) {
+  free(g->u1); free(g->u2); free(g->t1); free(g->t2);
+  for (int q = 0; q < 12; q++) free(g->s6[q]);
+}
 
 static int check_problem(const orc_problem *p) {
   if (!p) return ORC_EINVAL;
@@ -630,6 +767,7 @@ static int cf_exponential(orc_gen *g, const double *alpha, const double *c, int 
 /*
  * Time stepping, Y_{n+1} = exp(Omega_n) Y_n (Sec. 2, Eq. (9)) with t_n = t0 + n h:
  *  M2    (Method M2):    Omega = h A(t_n + h/2).
+ *  M6    (Method M6):    one exponential with the nested commutators (m6_apply_K).
  *  M4    (Method M4):    one exponential with the commutator (gen_apply).
  *  CF4   (Method Cf4):   exp(h(a1 A_1 + a2 A_2)) exp(h(a2 A_1 + a1 A_2)) Y_n,
  *                        c_{1,2} = 1/2 -+ sqrt(3)/6, a_{1,2} = (3 -+ 2 sqrt(3))/12;
@@ -672,6 +810,16 @@ int orc_propagate(const orc_problem *p, double complex *psi, double t0, double h
     } else if (variant == ORC_M2) {
       const double one = 1.0, half = 0.5;
       rc = cf_exponential(&g, &one, &half, 1, tn, h, psi);
+    } else if (variant == ORC_M6) {
+      rc = gen_alloc_m6(&g);
+      g.mode = GEN_M6;
+      g.h = h;
+      for (int k = 0; k < p->nterms; k++) {
+        g.f1[k] = orc_coeff_eval(p, k, tn + c6[0] * h);
+        g.f2[k] = orc_coeff_eval(p, k, tn + c6[1] * h);
+        g.f3[k] = orc_coeff_eval(p, k, tn + c6[2] * h);
+      }
+      if (rc == ORC_OK) rc = leja_core(&g, psi);
     } else {
       rc = ORC_EINVAL;
     }

@@ -24,7 +24,7 @@ extern "C" {
 
 enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOMEM = 2, ORC_ENOCONV = 4, ORC_ENONFINITE = 5 };
 enum { ORC_TERM_CSR = 0, ORC_TERM_DENSE = 1 };
-enum { ORC_M4 = 1, ORC_CF4 = 2, ORC_CF4_3 = 3, ORC_M2 = 4 };
+enum { ORC_M4 = 1, ORC_CF4 = 2, ORC_CF4_3 = 3, ORC_M2 = 4, ORC_M6 = 5 };
 
 typedef struct {
   int64_t n_exp;       /* exponentials applied                                   */
@@ -70,7 +70,8 @@ int orc_apply_term(const orc_problem *p, int k, const double complex *x, double 
 /* v <- exp(-i * sum_k beta_k H_k) v */
 int orc_expv(const orc_problem *p, const double *beta, double complex *v, orc_stats *st);
 
-/* psi <- product of nsteps Magnus steps of size h from t0 (variant ORC_M4 / ORC_CF4 / ...). */
+/* psi <- product of nsteps Magnus steps of size h from t0 (variant ORC_M4 / ORC_CF4 / ORC_CF4_3 /
+ * ORC_M2 / ORC_M6). */
 int orc_propagate(const orc_problem *p, double complex *psi, double t0, double h, int64_t nsteps,
                   int variant, orc_stats *st);
 

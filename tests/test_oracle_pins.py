@@ -237,7 +237,7 @@ def test_csr_and_dense_storage_agree():
 # ---------------------------------------------------------------------------
 # Magnus integrators (Sec. 2)
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("variant", ["M4", "CF4", "CF4_3", "M2"])
+@pytest.mark.parametrize("variant", ["M4", "CF4", "CF4_3", "M2", "M6"])
 def test_time_independent_is_exact(variant):
     """f == 0: every method reduces to exp(-i t H_s) (M4's commutator vanishes)."""
     n = 8
@@ -250,10 +250,11 @@ def test_time_independent_is_exact(variant):
     assert np.linalg.norm(out - ref) < 100 * 1e-12
 
 
-@pytest.mark.parametrize("variant", ["M4", "CF4", "CF4_3"])
+@pytest.mark.parametrize("variant", ["M4", "CF4", "CF4_3", "M6"])
 def test_commuting_terms_give_gauss_quadrature(variant):
     """Diagonal H_s, H_d commute: the discrete solution is exp(-i(E_s T + E_d Q)) psi0 with
-    Q the composite Gauss rule of int f (2 nodes for M4/Cf4, 3 nodes for Cf4:3)."""
+    Q the composite Gauss rule of int f (2 nodes for M4/Cf4, 3 nodes for Cf4:3 and M6).  For M6
+    this fixes the weight of B_3: B_1 + B_3/12 is the 3-point Gauss rule, any other weight is not."""
     n = 6
     D = 1 << n
     rng = np.random.default_rng(3)
@@ -265,7 +266,7 @@ def test_commuting_terms_give_gauss_quadrature(variant):
     psi0 = mi.random_state(rng, D)
     h, N = 0.05, 20
     out = P.propagate(psi0, 0.0, h, N, variant)
-    if variant == "CF4_3":
+    if variant in ("CF4_3", "M6"):
         nodes, w = np.polynomial.legendre.leggauss(3)
     else:
         nodes, w = np.polynomial.legendre.leggauss(2)
@@ -285,7 +286,7 @@ def test_norm_conservation():
     Hs = oracle.xxz_csr(n, c.J, c.hz, 0.5)
     Hd = oracle.field_x_csr(n)
     P = oracle.Problem([Hs, Hd], [oracle.Coeff.const(), oracle.Coeff(0, [1.0], [], [5.0])], tol=1e-13)
-    for variant in ("CF4", "M4"):
+    for variant in ("CF4", "M4", "M6"):
         out = P.propagate(c.psi0, 0.0, 0.01, 100, variant)
         assert abs(np.linalg.norm(out) - 1.0) < 1e-12, variant
 
@@ -318,6 +319,43 @@ def test_order_four_against_independent_integrator():
         assert errs[-1] > 1e-10, errs  # still far above the reference's own error
         for r in ratios:
             assert 14.0 < r < 18.5, (variant, errs, ratios)
+
+
+def test_order_six_against_independent_integrator():
+    """Method M6 (Sec. 2) converges with order six: the error falls ~64x per halving of h against
+    an independent high-accuracy integrator (a dropped or mis-signed commutator, or a wrong weight,
+    lowers the order)."""
+    n = 5
+    c = mi.xxz_chain(17, n, 0.01, 1)
+    Hs = oracle.xxz_csr(n, c.J, c.hz, 0.5)
+    Hd = oracle.field_x_csr(n)
+    f = oracle.Coeff(0.3, [1.0], [0.5], [5.0])
+    P = oracle.Problem([Hs, Hd], [oracle.Coeff.const(), f], tol=1e-15, tol_abs=1e-15)
+    ref = _dop853_reference(Hs, Hd, f, c.psi0, 1.0)
+    errs = []
+    for N in (4, 8, 16):
+        out = P.propagate(c.psi0, 0.0, 1.0 / N, N, "M6")
+        errs.append(np.linalg.norm(out - ref))
+    ratios = [errs[i] / errs[i + 1] for i in range(len(errs) - 1)]
+    assert errs[-1] > 1e-10, errs
+    for r in ratios:
+        assert 48.0 < r < 80.0, (errs, ratios)
+
+
+def test_m6_generator_is_hermitian():
+    """K = i Omega of Method M6 is Hermitian: the exponential conserves the norm only then.  Checked
+    on random vectors through one exponential's action, <x, exp(-iK) y> = <exp(iK) x, y>, via the
+    propagator's unitarity on pairs of states."""
+    n = 6
+    c = mi.xxz_chain(18, n, 0.01, 1)
+    Hs = oracle.xxz_csr(n, c.J, c.hz, 0.5)
+    Hd = oracle.field_x_csr(n)
+    f = oracle.Coeff(0.3, [1.0], [0.5], [5.0])
+    P = oracle.Problem([Hs, Hd], [oracle.Coeff.const(), f], tol=1e-14, tol_abs=1e-14)
+    rng = np.random.default_rng(19)
+    x, y = mi.random_state(rng, 1 << n), mi.random_state(rng, 1 << n)
+    ux, uy = P.propagate(x, 0.0, 0.2, 1, "M6"), P.propagate(y, 0.0, 0.2, 1, "M6")
+    assert abs(np.vdot(ux, uy) - np.vdot(x, y)) < 1e-12
 
 
 def test_paper_example1_error_ratios():
