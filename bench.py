@@ -94,12 +94,20 @@ def algorithmic_per_iteration(c, storage, variant, nnz_total):
     instructions per stored entry; the matrix-free XXZ row needs 4 for the diagonal, 2 per active
     bond ((n-1)/2 on average) and 2 n for the field sum plus 2 to weight it; both need 4 for the
     weighted combination (CSR) or none extra (matrix-free), 2 for the shift, 4 for the Newton update
-    of p and 4 for the two squared norms."""
+    of p and 4 for the two squared norms.
+
+    M6 applies every term 17 times per iteration (once per input vector of its five passes and the
+    final one); its 23 intermediate vectors are each written once and read back once or twice:
+    17 gathered inputs + 23 writes + 16 re-reads of 16 B per row on top of the Leja update, and 27
+    combinations of the term values (2 instructions per term each) plus about 70 instructions of
+    commutator arithmetic per row."""
     D = c.dim
-    passes = 2 if variant == "M4" else 1
+    passes = {"M4": 2, "M6": 17}.get(variant, 1)
     vec_bytes = 64 * D
     if variant == "M4":
         vec_bytes += 2 * 16 * D * 2
+    if variant == "M6":
+        vec_bytes += (17 + 23 + 16) * 16 * D
     if storage in ("csr", "csr_real"):
         mat = (20 if storage == "csr" else 12) * nnz_total + 2 * 8 * (D + 1)
         inst = passes * 2 * nnz_total + (4 + 2 + 4 + 4) * D
@@ -109,6 +117,8 @@ def algorithmic_per_iteration(c, storage, variant, nnz_total):
         inst = passes * D * (4 + (n - 1) + 2 * n + 2) + (2 + 4 + 4) * D
     if variant == "M4":
         inst += 8 * D  # commutator difference and its weight
+    if variant == "M6":
+        inst += (27 * 2 * 2 + 70 - 4) * D  # combinations and commutator arithmetic (no separate weighting)
     return passes * mat + vec_bytes, 2 * inst
 
 
@@ -550,7 +560,7 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--variant", choices=["CF4", "M4", "CF4_3", "M2"], default="CF4")
+    ap.add_argument("--variant", choices=["CF4", "M4", "CF4_3", "M2", "M6"], default="CF4")
     ap.add_argument("--storage", choices=["csr", "csr_real", "mfree"], default="csr")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--cpu-steps", type=int, default=4)

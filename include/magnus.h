@@ -51,7 +51,11 @@ typedef enum {
   MAGNUS_M4 = 1,   /* Sec. 2, Method M4 (commutator applied matrix-free)        */
   MAGNUS_CF4 = 2,  /* Sec. 2, Method Cf4 (two exponentials)                     */
   MAGNUS_CF4_3 = 3,/* Sec. 2, Method Cf4:3 (three exponentials)                 */
-  MAGNUS_M2 = 4    /* Sec. 2, Method M2 (exponential midpoint rule)             */
+  MAGNUS_M2 = 4,   /* Sec. 2, Method M2 (exponential midpoint rule)             */
+  MAGNUS_M6 = 5    /* Sec. 2, Method M6 (order six, nested commutators applied
+                      matrix-free; CSR and matrix-free terms, not dense terms or
+                      batches).  The weight of B_3 is 1/12: with it B_1 + B_3/12
+                      is the 3-point Gauss rule the first Magnus term needs.    */
 } magnus_variant;
 
 typedef enum {

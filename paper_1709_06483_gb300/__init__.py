@@ -18,8 +18,8 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libmagnus_gb300.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ENONFINITE, ETIMEOUT = range(7)
-M4, CF4, CF4_3, M2 = 1, 2, 3, 4
-VARIANTS = {"M4": M4, "CF4": CF4, "CF4_3": CF4_3, "M2": M2}
+M4, CF4, CF4_3, M2, M6 = 1, 2, 3, 4, 5
+VARIANTS = {"M4": M4, "CF4": CF4, "CF4_3": CF4_3, "M2": M2, "M6": M6}
 TERM_CSR, TERM_DENSE, TERM_XXZ, TERM_FIELD_X, TERM_CSR_REAL, TERM_DENSE_REAL = 0, 1, 2, 3, 4, 5
 FP64, FP32_SPLIT, TENSOR_SLICED = 0, 1, 2
 

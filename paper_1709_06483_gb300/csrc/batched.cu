@@ -585,6 +585,7 @@ MAGNUS_API magnus_status magnus_batch_propagate(magnus_batch_t b, void *const *p
     if (!psi[i] || ((uintptr_t)psi[i]) % 16) return berr(b, MAGNUS_EINVAL, "psi[%d] null or not 16-byte aligned", i);
   const int per = exps_per_step(variant);
   if (per == 0) return berr(b, MAGNUS_EINVAL, "unknown variant %d", variant);
+  if (variant == MAGNUS_M6) return berr(b, MAGNUS_EINVAL, "batches take M2, M4, CF4 and CF4_3");
   if (nsteps < 0 || !(h == h) || !(t0 == t0)) return berr(b, MAGNUS_EINVAL, "bad nsteps / t0 / h");
   int32_t *ulog = stats ? stats->m_log : nullptr;
   const int64_t ucap = stats ? stats->m_log_cap_per_item : 0;

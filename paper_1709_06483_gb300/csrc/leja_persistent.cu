@@ -39,8 +39,23 @@ constexpr int kMinBlocks = MG_PERSIST_MIN_BLOCKS;  // resident CTAs per SM the r
 constexpr int kMaxVec = 64;
 
 
+// M6 intermediate vectors (slots of PersistArgs::m6), named by the operator word applied to w, u
+// or v: e.g. PQW = P(Q w).
+enum {
+  S_PW, S_QW, S_RW, S_PQW, S_QPW, S_PRW, S_RPW, S_PPW, S_U, S_V, S_PU, S_QU, S_RU, S_PV, S_QV, S_RV,
+  S_PQU, S_QPU, S_PRU, S_RPU, S_PPU, S_PQV, S_QPV
+};
+static_assert(S_QPV + 1 == kM6Slots, "M6 slot count");
+
+__device__ __forceinline__ double2 mul_i(double2 z) { return make_double2(-z.y, z.x); }  // i z
+__device__ __forceinline__ double2 add2(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 sub2(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 scal2(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
+
 // --------------------------------------------------------------------- kernel
-template <int FAM>
+// HM6: the instantiation that also carries Method M6 (launched only for MAGNUS_M6, so that its
+// extra code does not weigh on the register budget of the other methods).
+template <int FAM, bool HM6>
 __global__ void __launch_bounds__(kBlock, kMinBlocks) k_magnus_persistent(PersistArgs a) {
   __shared__ Term sT[kMaxTerms];
   __shared__ ExpRec sR;
@@ -168,12 +183,119 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_magnus_persistent(Persis
               for (int k = 0; k < nt; k++) a.u[((size_t)k * nv) * D + base + r] = Op<FAM>::term(cx, k, src + base, r);
           if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { fail(MAGNUS_ETIMEOUT); return; }
         }
+        // Method M6: K w = P w + R w / 12 + (i/240) (U (V w) - V (U w)) with
+        //   U = i(20 P + R) - [P, Q],   V = -i Q + [P, R]/30 - (i/60) [P, [P, Q]],
+        // built in five passes over this block's rows, each followed by a grid barrier; every pass
+        // applies the terms once per input vector and forms all combinations it needs.
+        if (HM6 && R.mode == MODE_M6) {
+          const size_t sl = (size_t)nv * D;
+          auto V6 = [&](int k) { return a.m6 + (size_t)k * sl + base; };
+          double2 t[kMaxTerms];
+          auto terms_of = [&](const double2 *x, int64_t r) {
+            for (int k = 0; k < nt; k++) t[k] = Op<FAM>::term(cx, k, x, r);
+          };
+          auto lc = [&](const double *c) {
+            double2 z = make_double2(0.0, 0.0);
+            for (int k = 0; k < nt; k++) z = rfma(c[k], t[k], z);
+            return z;
+          };
+          const double *P6 = R.p6, *Q6 = R.q6, *R6 = R.r6;
+          if (mine)  // pass 1: P w, Q w, R w
+            for (int64_t r = lo + tid; r < hi; r += blockDim.x) {
+              terms_of(src + base, r);
+              V6(S_PW)[r] = lc(P6);
+              V6(S_QW)[r] = lc(Q6);
+              V6(S_RW)[r] = lc(R6);
+            }
+          if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { fail(MAGNUS_ETIMEOUT); return; }
+          if (mine)  // pass 2: P(Q w), Q(P w), R(P w), P(P w), P(R w)
+            for (int64_t r = lo + tid; r < hi; r += blockDim.x) {
+              terms_of(V6(S_QW), r);
+              V6(S_PQW)[r] = lc(P6);
+              terms_of(V6(S_PW), r);
+              V6(S_QPW)[r] = lc(Q6);
+              V6(S_RPW)[r] = lc(R6);
+              V6(S_PPW)[r] = lc(P6);
+              terms_of(V6(S_RW), r);
+              V6(S_PRW)[r] = lc(P6);
+            }
+          if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { fail(MAGNUS_ETIMEOUT); return; }
+          if (mine)  // pass 3: u = U w, v = V w
+            for (int64_t r = lo + tid; r < hi; r += blockDim.x) {
+              terms_of(V6(S_PQW), r);
+              const double2 ppq = lc(P6);
+              terms_of(V6(S_QPW), r);
+              const double2 pqp = lc(P6);
+              terms_of(V6(S_PPW), r);
+              const double2 qpp = lc(Q6);
+              const double2 pw = ldv(V6(S_PW) + r), qw = ldv(V6(S_QW) + r), rw = ldv(V6(S_RW) + r);
+              const double2 pqw = ldv(V6(S_PQW) + r), qpw = ldv(V6(S_QPW) + r);
+              const double2 prw = ldv(V6(S_PRW) + r), rpw = ldv(V6(S_RPW) + r);
+              const double2 uw = sub2(mul_i(add2(scal2(20.0, pw), rw)), sub2(pqw, qpw));
+              const double2 nest = add2(sub2(ppq, scal2(2.0, pqp)), qpp);  // [P,[P,Q]] w
+              const double2 vw = sub2(add2(mul_i(scal2(-1.0, qw)), scal2(1.0 / 30.0, sub2(prw, rpw))),
+                                      scal2(1.0 / 60.0, mul_i(nest)));
+              V6(S_U)[r] = uw;
+              V6(S_V)[r] = vw;
+            }
+          if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { fail(MAGNUS_ETIMEOUT); return; }
+          if (mine)  // pass 4: P u, Q u, R u, P v, Q v, R v
+            for (int64_t r = lo + tid; r < hi; r += blockDim.x) {
+              terms_of(V6(S_U), r);
+              V6(S_PU)[r] = lc(P6);
+              V6(S_QU)[r] = lc(Q6);
+              V6(S_RU)[r] = lc(R6);
+              terms_of(V6(S_V), r);
+              V6(S_PV)[r] = lc(P6);
+              V6(S_QV)[r] = lc(Q6);
+              V6(S_RV)[r] = lc(R6);
+            }
+          if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { fail(MAGNUS_ETIMEOUT); return; }
+          if (mine)  // pass 5: P(Q u), Q(P u), R(P u), P(P u), P(R u), P(Q v), Q(P v)
+            for (int64_t r = lo + tid; r < hi; r += blockDim.x) {
+              terms_of(V6(S_QU), r);
+              V6(S_PQU)[r] = lc(P6);
+              terms_of(V6(S_PU), r);
+              V6(S_QPU)[r] = lc(Q6);
+              V6(S_RPU)[r] = lc(R6);
+              V6(S_PPU)[r] = lc(P6);
+              terms_of(V6(S_RU), r);
+              V6(S_PRU)[r] = lc(P6);
+              terms_of(V6(S_QV), r);
+              V6(S_PQV)[r] = lc(P6);
+              terms_of(V6(S_PV), r);
+              V6(S_QPV)[r] = lc(Q6);
+            }
+          if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { fail(MAGNUS_ETIMEOUT); return; }
+        }
         double sw = 0.0, sp = 0.0;
         if (mine) {
           for (int64_t r = lo + tid; r < hi; r += blockDim.x) {
 
             double2 y, wr;
-            if (R.mode == MODE_M4) {
+            if (HM6 && R.mode == MODE_M6) {  // pass 6: V u, U v and K w, fused with the Leja update
+              const size_t sl = (size_t)nv * D;
+              auto V6 = [&](int k) { return a.m6 + (size_t)k * sl + base; };
+              double2 t6[kMaxTerms];
+              double2 ppq = make_double2(0.0, 0.0), pqp = ppq, qpp = ppq;
+              for (int k = 0; k < nt; k++) t6[k] = Op<FAM>::term(cx, k, V6(S_PQU), r);
+              for (int k = 0; k < nt; k++) ppq = rfma(R.p6[k], t6[k], ppq);
+              for (int k = 0; k < nt; k++) t6[k] = Op<FAM>::term(cx, k, V6(S_QPU), r);
+              for (int k = 0; k < nt; k++) pqp = rfma(R.p6[k], t6[k], pqp);
+              for (int k = 0; k < nt; k++) t6[k] = Op<FAM>::term(cx, k, V6(S_PPU), r);
+              for (int k = 0; k < nt; k++) qpp = rfma(R.q6[k], t6[k], qpp);
+              const double2 qu = ldv(V6(S_QU) + r), pru = ldv(V6(S_PRU) + r), rpu = ldv(V6(S_RPU) + r);
+              const double2 nest = add2(sub2(ppq, scal2(2.0, pqp)), qpp);  // [P,[P,Q]] u
+              const double2 vu = sub2(add2(mul_i(scal2(-1.0, qu)), scal2(1.0 / 30.0, sub2(pru, rpu))),
+                                      scal2(1.0 / 60.0, mul_i(nest)));
+              const double2 pv = ldv(V6(S_PV) + r), rv = ldv(V6(S_RV) + r);
+              const double2 pqv = ldv(V6(S_PQV) + r), qpv = ldv(V6(S_QPV) + r);
+              const double2 uv = sub2(mul_i(add2(scal2(20.0, pv), rv)), sub2(pqv, qpv));
+              const double2 pw = ldv(V6(S_PW) + r), rw = ldv(V6(S_RW) + r);
+              const double2 kw = add2(add2(pw, scal2(1.0 / 12.0, rw)), scal2(1.0 / 240.0, mul_i(sub2(uv, vu))));
+              wr = ldv(src + base + r);
+              y = rfma(-shift, wr, scal2(1.0 / R.gamma, kw));
+            } else if (R.mode == MODE_M4) {
               y = make_double2(0.0, 0.0);
               double2 z = make_double2(0.0, 0.0);
               int pi = 0;
@@ -236,7 +358,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_magnus_persistent(Persis
         for (int v = 0; v < nv; v++) {
           const int m = s_m[v];
           c->n_matvec += m;
-          c->n_termapply += (long long)m * nt * (R.mode == MODE_M4 ? 2 : 1);
+          c->n_termapply += (long long)m * nt * (R.mode == MODE_M4 ? 2 : (R.mode == MODE_M6 ? 17 : 1));
           if (m > c->max_m) c->max_m = m;
           if (a.mlog && sub_counter * nv + v < a.mlog_cap) a.mlog[sub_counter * nv + v] = m;
         }
@@ -252,11 +374,18 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_magnus_persistent(Persis
     for (int64_t r = lo + tid; r < hi; r += blockDim.x) a.psi[base + r] = cur[base + r];
 }
 
-const void *kernel_for(int fam) {
+const void *kernel_for(int fam, bool m6) {
+  if (m6) {
+    switch (fam) {
+      case FAM_CSR: return (const void *)k_magnus_persistent<FAM_CSR, true>;
+      case FAM_MF: return (const void *)k_magnus_persistent<FAM_MF, true>;
+      default: return (const void *)k_magnus_persistent<FAM_GENERIC, true>;
+    }
+  }
   switch (fam) {
-    case FAM_CSR: return (const void *)k_magnus_persistent<FAM_CSR>;
-    case FAM_MF: return (const void *)k_magnus_persistent<FAM_MF>;
-    default: return (const void *)k_magnus_persistent<FAM_GENERIC>;
+    case FAM_CSR: return (const void *)k_magnus_persistent<FAM_CSR, false>;
+    case FAM_MF: return (const void *)k_magnus_persistent<FAM_MF, false>;
+    default: return (const void *)k_magnus_persistent<FAM_GENERIC, false>;
   }
 }
 
@@ -267,20 +396,21 @@ int persistent_block_size() { return kBlock; }
 // Smallest occupancy over the families: the grid of any plan fits on the device at once.
 cudaError_t persistent_max_blocks_per_sm(int *n) {
   int best = 1 << 30;
-  for (int fam = 0; fam < 3; fam++) {
-    int k = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, kernel_for(fam), kBlock, 0);
-    if (e != cudaSuccess) return e;
-    best = k < best ? k : best;
-  }
+  for (int fam = 0; fam < 3; fam++)
+    for (int m6 = 0; m6 < 2; m6++) {
+      int k = 0;
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, kernel_for(fam, m6 != 0), kBlock, 0);
+      if (e != cudaSuccess) return e;
+      best = k < best ? k : best;
+    }
   *n = best;
   return cudaSuccess;
 }
 
-cudaError_t launch_persistent(const PersistArgs &a, int grid, int block, cudaStream_t st) {
+cudaError_t launch_persistent(const PersistArgs &a, int grid, int block, bool m6, cudaStream_t st) {
   PersistArgs copy = a;
   void *args[] = {&copy};
-  return cudaLaunchCooperativeKernel(kernel_for(a.fam), dim3(grid), dim3(block), args, 0, st);
+  return cudaLaunchCooperativeKernel(kernel_for(a.fam, m6), dim3(grid), dim3(block), args, 0, st);
 }
 
 }  // namespace mg

@@ -51,6 +51,7 @@ struct magnus_plan_s {
   uint16_t *sl_cur = nullptr, *sl_w0 = nullptr, *sl_w1 = nullptr, *sl_u = nullptr;
   int *ex_sets = nullptr;                // [3 + nterms][128] column exponents
   unsigned long long *colmax = nullptr;  // [3][128]
+  double2 *m6 = nullptr;                 // M6 intermediate vectors [kM6Slots][nvec][dim], on first use
   int lbits = 0;
   double *dlo = nullptr, *dhi = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -92,7 +93,7 @@ void free_plan(magnus_plan_t p) {
                   p->alt, p->w0, p->w1, p->u, p->recs, p->dd, p->mlog, p->dlo, p->dhi,
                   p->hsplit[0], p->hsplit[1], p->hsplit[2], p->hsplit[3], p->sh_cur, p->sh_w0, p->sh_w1, p->sh_u,
                   p->hslice[0], p->hslice[1], p->hslice[2], p->hslice[3], p->hexp[0], p->hexp[1], p->hexp[2],
-                  p->hexp[3], p->sl_cur, p->sl_w0, p->sl_w1, p->sl_u, p->ex_sets, p->colmax};
+                  p->hexp[3], p->sl_cur, p->sl_w0, p->sl_w1, p->sl_u, p->ex_sets, p->colmax, p->m6};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (p->ev0) cudaEventDestroy(p->ev0);
@@ -147,7 +148,7 @@ void choose_grid(magnus_plan_t p, int *grid, int *gv) {
   *grid = per_vec * nv;
 }
 
-magnus_status run_persistent(magnus_plan_t p, void *psi, int64_t nexp, magnus_stats *stats) {
+magnus_status run_persistent(magnus_plan_t p, void *psi, int64_t nexp, magnus_stats *stats, bool m6 = false) {
   int grid, gv;
   size_t need;
   if (p->fam == FAM_DENSE) {
@@ -229,11 +230,12 @@ magnus_status run_persistent(magnus_plan_t p, void *psi, int64_t nexp, magnus_st
     a.ex_u = p->ex_sets + 384;
   }
   a.colmax = p->colmax;
+  a.m6 = p->m6;
   CUDA_TRY(p, cudaEventRecord(p->ev0, p->stream));
   if (p->fam == FAM_DENSE)
     CUDA_TRY(p, launch_dense_persistent(a, p->dense_real, grid, p->stream));
   else
-    CUDA_TRY(p, launch_persistent(a, grid, persistent_block_size(), p->stream));
+    CUDA_TRY(p, launch_persistent(a, grid, persistent_block_size(), m6, p->stream));
   CUDA_TRY(p, cudaEventRecord(p->ev1, p->stream));
   Counters c{};
   CUDA_TRY(p, cudaMemcpyAsync(&c, p->counters, sizeof c, cudaMemcpyDeviceToHost, p->stream));
@@ -559,13 +561,16 @@ magnus_status magnus_propagate(magnus_plan_t p, void *psi, double t0, double h, 
     stats->m_log = log;
     stats->m_log_cap = cap;
   }
+  if (variant == MAGNUS_M6 && p->fam == FAM_DENSE)
+    return set_err(p, MAGNUS_EINVAL, "MAGNUS_M6 takes CSR and matrix-free terms, not dense terms");
   if (nsteps == 0) return MAGNUS_OK;
   const int64_t nexp = nsteps * per;
   magnus_status s = ensure_exp_capacity(p, nexp);
   if (s != MAGNUS_OK) return s;
+  if (variant == MAGNUS_M6 && !p->m6) CUDA_TRY(p, dalloc(&p->m6, (size_t)kM6Slots * p->dim * p->opt.nvec));
   CUDA_TRY(p, launch_exp_setup(variant, t0, h, nsteps, p->nterms, p->coeffs, p->term_ab, p->xi, p->opt.m_max,
                                p->opt.rho_max, p->recs, p->dd, nexp, p->stream));
-  return run_persistent(p, psi, nexp, stats);
+  return run_persistent(p, psi, nexp, stats, variant == MAGNUS_M6);
 }
 
 magnus_status leja_expv(magnus_plan_t p, const double *beta, const void *v, void *out, magnus_stats *stats) {
@@ -721,7 +726,7 @@ magnus_status magnus_adjoint_grad(magnus_plan_t p, const void *psi0, const void 
     q.dd = DD;
     q.nexp = cnt;
     q.psi = x;
-    return launch_persistent(q, grid, persistent_block_size(), st);
+    return launch_persistent(q, grid, persistent_block_size(), false, st);
   };
   AugArgs g{};
   g.dim = D;

@@ -54,7 +54,7 @@ struct Coeff {
 
 // Everything one exponential exp(-iK) needs inside the persistent kernel.  K is shifted and
 // scaled to X = (K - cI)/gamma with spectrum in [-2,2]; the stored weights already carry 1/gamma.
-enum { MODE_LINEAR = 0, MODE_M4 = 1 };
+enum { MODE_LINEAR = 0, MODE_M4 = 1, MODE_M6 = 2 };
 struct ExpRec {
   double bg[kMaxTerms];  // beta_k / gamma      (linear part: K = sum_k beta_k H_k + ...)
   double kg[kMaxPairs];  // M4: kappa * coef_kl / gamma, pairs (k<l) in row-major order
@@ -63,8 +63,12 @@ struct ExpRec {
   double c;              // centre of the enclosure
   double a, b;           // the enclosure itself (diagnostics)
   int s;                 // substeps
-  int mode;              // MODE_LINEAR or MODE_M4
+  int mode;              // MODE_LINEAR, MODE_M4 or MODE_M6
+  // M6: B_1 = -iP, B_2 = -iQ, B_3 = -iR with P, Q, R = sum_k {p6,q6,r6}_k H_k (not divided by gamma)
+  double p6[kMaxTerms], q6[kMaxTerms], r6[kMaxTerms];
 };
+
+constexpr int kM6Slots = 23;  // vectors the M6 generator keeps between its stages
 
 // Sense-reversing grid barrier state (one per plan, zero-initialised).
 struct GridBar {
@@ -158,6 +162,7 @@ struct PersistArgs {
   // FAM_DENSE with MAGNUS_TENSOR_SLICED: bf16 digits of the dense terms ([5][D][D], row exponents)
   // and of every vector set a dense matvec reads ([5][2 nvec][D], column exponents), and the
   // rotating column-maximum slots of the slicing passes ([3][128], zero at launch)
+  double2 *m6;  // M6 intermediate vectors, kM6Slots x [nvec][dim]
   int sliced;
   const void *hslice[kMaxTerms];
   const int *hexp[kMaxTerms];
@@ -166,7 +171,7 @@ struct PersistArgs {
   unsigned long long *colmax;
 };
 enum { FAM_GENERIC = 0, FAM_CSR = 1, FAM_MF = 2, FAM_DENSE = 3 };
-cudaError_t launch_persistent(const PersistArgs &a, int grid, int block, cudaStream_t st);
+cudaError_t launch_persistent(const PersistArgs &a, int grid, int block, bool m6, cudaStream_t st);
 int persistent_block_size();
 cudaError_t persistent_max_blocks_per_sm(int *n);
 

@@ -173,7 +173,7 @@ extern "C" MAGNUS_API magnus_status magnus_expv_xxz_static(int32_t nspins, const
     a.mlog = nullptr;
     a.mlog_cap = 0;
     a.spin_limit_ns = 4000000000LL;
-    e = launch_persistent(a, grid, persistent_block_size(), stream);
+    e = launch_persistent(a, grid, persistent_block_size(), false, stream);
   }
   Counters c{};
   if (e == cudaSuccess) e = cudaMemcpyAsync(&c, counters, sizeof c, cudaMemcpyDeviceToHost, stream);

@@ -208,6 +208,7 @@ __device__ void finish_record(ExpRec &R, const double *lin, int nterms, const do
 //         coef_kl = f_k(t2) f_l(t1) - f_l(t2) f_k(t1)  ([H_2,H_1] = sum_{k<l} coef_kl [H_k,H_l]).
 //  Cf4:   stage 0 (applied first): h (a2 f(t1) + a1 f(t2)), stage 1: h (a1 f(t1) + a2 f(t2)).
 //  Cf4:3: stage 0 uses the third row of the alpha table, stage 2 the first.
+//  M6:    one exponential; P, Q, R of the three Gauss nodes (see the branch below).
 __device__ void exp_setup_warp(long long e, int variant, double t0, double h, int nterms, const Coeff *coeffs,
                                const double *term_ab, const double *xi, int m_max, double rho_max, ExpRec *recs,
                                double2 *dd, int per_step) {
@@ -218,10 +219,45 @@ __device__ void exp_setup_warp(long long e, int variant, double t0, double h, in
   const double r3 = sqrt(3.0), r15 = sqrt(15.0);
   ExpRec R;
   for (int k = 0; k < kMaxPairs; k++) R.kg[k] = 0.0;
+  for (int k = 0; k < kMaxTerms; k++) R.p6[k] = R.q6[k] = R.r6[k] = 0.0;
   double lin[kMaxTerms] = {0.0, 0.0, 0.0, 0.0};
   double r = 0.0;
   R.mode = MODE_LINEAR;
-  if (variant == MAGNUS_M2) {
+  if (variant == MAGNUS_M6) {
+    // Method M6 with A_i = -i H(t_n + c_i h): B_1 = -iP, B_2 = -iQ, B_3 = -iR,
+    //   P = h H(t2), Q = (sqrt(15)/3) h (H(t3) - H(t1)), R = (10/3) h (H(t3) - 2 H(t2) + H(t1)),
+    // K = i Omega = P + R/12 + (i/240)[U, V]; the linear part P + R/12 gives the enclosure and
+    // the commutator adds +-r (bound from the half-widths, S = 20 P + R, C = [P, Q]):
+    //   r = (|[S,Q]| + 2 |S| |E| + 2 |C| (|Q| + |E|)) / 240,  |E| = (|[P,R]| + |P| |C|) / 30.
+    R.mode = MODE_M6;
+    const double c6[3] = {0.5 - r15 / 10.0, 0.5, 0.5 + r15 / 10.0};
+    double hw[kMaxTerms], sk[kMaxTerms];
+    for (int k = 0; k < nterms; k++) {
+      const double f1 = coeff_eval(coeffs[k], tn + c6[0] * h);
+      const double f2 = coeff_eval(coeffs[k], tn + c6[1] * h);
+      const double f3 = coeff_eval(coeffs[k], tn + c6[2] * h);
+      R.p6[k] = h * f2;
+      R.q6[k] = r15 / 3.0 * h * (f3 - f1);
+      R.r6[k] = 10.0 / 3.0 * h * (f3 - 2.0 * f2 + f1);
+      lin[k] = R.p6[k] + R.r6[k] / 12.0;
+      sk[k] = 20.0 * R.p6[k] + R.r6[k];
+      hw[k] = 0.5 * (term_ab[2 * k + 1] - term_ab[2 * k]);
+    }
+    double pq = 0.0, pr = 0.0, sq = 0.0, pn = 0.0, sn = 0.0, qn = 0.0;
+    for (int k = 0; k < nterms; k++) {
+      pn += fabs(R.p6[k]) * hw[k];
+      sn += fabs(sk[k]) * hw[k];
+      qn += fabs(R.q6[k]) * hw[k];
+      for (int l = k + 1; l < nterms; l++) {
+        const double w2 = 2.0 * hw[k] * hw[l];
+        pq += fabs(R.p6[k] * R.q6[l] - R.p6[l] * R.q6[k]) * w2;
+        pr += fabs(R.p6[k] * R.r6[l] - R.p6[l] * R.r6[k]) * w2;
+        sq += fabs(sk[k] * R.q6[l] - sk[l] * R.q6[k]) * w2;
+      }
+    }
+    const double en = (pr + pn * pq) / 30.0;
+    r = (sq + 2.0 * sn * en + 2.0 * pq * (qn + en)) / 240.0;
+  } else if (variant == MAGNUS_M2) {
     for (int k = 0; k < nterms; k++) lin[k] = h * coeff_eval(coeffs[k], tn + 0.5 * h);
   } else if (variant == MAGNUS_CF4) {
     const double c1 = 0.5 - r3 / 6.0, c2 = 0.5 + r3 / 6.0;
@@ -564,6 +600,7 @@ int exps_per_step(int variant) {
     case MAGNUS_CF4_3: return 3;
     case MAGNUS_M4: return 1;
     case MAGNUS_M2: return 1;
+    case MAGNUS_M6: return 1;
     default: return 0;
   }
 }

@@ -174,6 +174,49 @@ def test_propagate_other_methods(mg, variant, kind):
     assert rel(psi.cpu().numpy(), ref) < REL_TOL
 
 
+@pytest.mark.parametrize("kind", ["csr", "csr_real", "mfree"])
+def test_propagate_m6(mg, kind):
+    """Method M6 (nested commutators applied matrix-free in five passes) against the oracle."""
+    c = mi.workload1()
+    plan = mg.Plan(c.dim, chain_terms(mg, c, kind), drives_gpu(mg, c))
+    psi = cuda(c.psi0)
+    st = plan.propagate(psi, c.t0, c.h, 40, "M6", log_cap=512)
+    ost = oracle.Stats(512)
+    ref = oracle_problem(c).propagate(c.psi0, c.t0, c.h, 40, "M6", ost)
+    assert st["n_exp"] == ost.n_exp and st["n_substeps"] == ost.n_substeps
+    assert np.array_equal(st["m_log"], ost.m_log)
+    assert rel(psi.cpu().numpy(), ref) < REL_TOL
+
+
+def test_m6_many_vectors_ragged_blocks(mg):
+    """M6 with 3 state vectors over 7 blocks of 256 rows (2^11 rows: several tiles, ragged tail),
+    large steps so that substepping (s > 1) occurs."""
+    c = mi.xxz_chain(24, 11, 0.3, 4, nvec=3)
+    for kind in ("csr", "mfree"):
+        plan = mg.Plan(c.dim, chain_terms(mg, c, kind), drives_gpu(mg, c), nvec=3, ctas=7)
+        psi = cuda(c.psi0)
+        st = plan.propagate(psi, 0.0, c.h, c.nsteps, "M6")
+        out = psi.cpu().numpy().reshape(3, -1)
+        P = oracle_problem(c)
+        for v in range(3):
+            ref = P.propagate(c.psi0.reshape(3, -1)[v], 0.0, c.h, c.nsteps, "M6")
+            assert rel(out[v], ref) < REL_TOL, (kind, v)
+        assert st["n_substeps"] > 3 * st["n_exp"]  # some exponential took more than one substep
+
+
+def test_m6_rejected_where_not_supported(mg):
+    c = mi.xxz_chain(25, 7, 0.01, 2)
+    Hs = mg.build_longrange_dense(c.nspins, c.hz, 1.5, c.delta)
+    plan = mg.Plan(c.dim, [mg.DenseTerm(Hs), mg.FieldXTerm(c.nspins)], drives_gpu(mg, c))
+    with pytest.raises(mg.MagnusError) as e:
+        plan.propagate(cuda(c.psi0), 0.0, 0.01, 1, "M6")
+    assert e.value.code == mg.EINVAL
+    B = mg.Batch([(c.dim, chain_terms(mg, c, "csr"), drives_gpu(mg, c))])
+    with pytest.raises(mg.MagnusError) as e:
+        B.propagate([cuda(c.psi0)], 0.0, 0.01, 1, "M6")
+    assert e.value.code == mg.EINVAL
+
+
 @pytest.mark.parametrize("ctas", [1, 3, 7, 64])
 def test_ragged_block_partitions(mg, ctas):
     """Many tiles and a ragged tail: 2^11 rows over ctas blocks of 256 threads."""
