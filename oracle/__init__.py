@@ -73,6 +73,7 @@ def lib():
                 "orc_set_coeff": (I32, [P, I32, D, I32, P, P, P]),
                 "orc_set_leja": (I32, [P, D, D, I32, D]),
                 "orc_term_interval": (I32, [P, I32, C.POINTER(D), C.POINTER(D)]),
+                "orc_set_interval_lanczos": (I32, [P, I32, I32]),
                 "orc_coeff_eval": (D, [P, I32, D]),
                 "orc_apply_term": (I32, [P, I32, P, P]),
                 "orc_expv": (I32, [P, P, P, C.POINTER(_Stats)]),
@@ -210,7 +211,8 @@ class Stats:
 class Problem:
     """H(t) = sum_k f_k(t) H_k with H_k CSR or dense (Sec. 4, H = H_1 + h(t) H_2)."""
 
-    def __init__(self, terms, coeffs, tol=1e-10, tol_abs=None, m_max=100, rho_max=4.0):
+    def __init__(self, terms, coeffs, tol=1e-10, tol_abs=None, m_max=100, rho_max=4.0, interval="gershgorin",
+                 lanczos_steps=48):
         assert len(terms) == len(coeffs) and len(terms) >= 1
         self.terms, self.coeffs = list(terms), list(coeffs)
         self.dim = terms[0].dim if isinstance(terms[0], CSR) else terms[0].shape[0]
@@ -232,6 +234,11 @@ class Problem:
             self._keep.append(c)
             _check(L.orc_set_coeff(self._h, k, c.a0, c.om.size, _ptr(c.ac), _ptr(c.as_), _ptr(c.om)), "set_coeff")
         _check(L.orc_set_leja(self._h, tol, tol if tol_abs is None else tol_abs, m_max, rho_max), "set_leja")
+        if interval == "lanczos":
+            for k in range(len(terms)):
+                _check(L.orc_set_interval_lanczos(self._h, k, lanczos_steps), "set_interval_lanczos")
+        elif interval != "gershgorin":
+            raise ValueError(interval)
 
     def __del__(self):
         if getattr(self, "_h", None):

@@ -381,6 +381,144 @@ int orc_set_dense(orc_problem *p, int k, const double complex *H) {
   return ORC_OK;
 }
 
+/* ------------------------------------------------------------------------- */
+/* Lanczos enclosure of a term's spectrum (the "estimate on the spectrum" of  */
+/* Sec. 3, tighter than Gershgorin).                                          */
+/* ------------------------------------------------------------------------- */
+
+/* SplitMix64 (Steele, Lea, Flood 2014) in counter form: output c of the stream that starts at
+ * `seed`, i.e. the mix of seed + (c + 1) * 0x9E3779B97F4A7C15. */
+static uint64_t splitmix64_at(uint64_t seed, uint64_t c) {
+  uint64_t z = seed + (c + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+static double unit_at(uint64_t seed, uint64_t c) { return (double)(splitmix64_at(seed, c) >> 11) * 0x1.0p-53; }
+
+/* number of eigenvalues of the symmetric tridiagonal T (diagonal al[0..m-1], off-diagonal
+ * be[1..m-1]) below x, by the signs of the Sturm sequence of the LDL^T pivots */
+static int sturm_count(const double *al, const double *be, int m, double x) {
+  int cnt = 0;
+  double q = 1.0;
+  for (int i = 0; i < m; i++) {
+    double off = (i > 0) ? be[i] * be[i] / q : 0.0;
+    q = al[i] - x - off;
+    if (q == 0.0) q = -1e-300;
+    if (q < 0.0) cnt++;
+  }
+  return cnt;
+}
+
+/* the idx-th smallest eigenvalue of T by bisection (Gershgorin start interval, 200 halvings) */
+static double tridiag_eig(const double *al, const double *be, int m, int idx) {
+  double lo = INFINITY, hi = -INFINITY;
+  for (int i = 0; i < m; i++) {
+    double r = (i > 0 ? fabs(be[i]) : 0.0) + (i + 1 < m ? fabs(be[i + 1]) : 0.0);
+    if (al[i] - r < lo) lo = al[i] - r;
+    if (al[i] + r > hi) hi = al[i] + r;
+  }
+  for (int it = 0; it < 200; it++) {
+    double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (sturm_count(al, be, m, mid) > idx) hi = mid; else lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+/* |last component| of the unit eigenvector of T for the eigenvalue theta: three steps of inverse
+ * iteration with the shift theta + shift (outside the spectrum, so T - shift I is definite and the
+ * tridiagonal solve needs no pivoting) */
+static double tridiag_last_component(const double *al, const double *be, int m, double theta, double shift) {
+  double *x = (double *)malloc(sizeof(double) * 3 * (size_t)m);
+  if (!x) return 1.0;
+  double *c = x + m, *d = x + 2 * m;
+  for (int i = 0; i < m; i++) x[i] = 1.0;
+  const double sig = theta + shift;
+  for (int it = 0; it < 3; it++) {
+    /* solve (T - sig I) y = x (Thomas), y into x */
+    double piv = al[0] - sig;
+    c[0] = (m > 1) ? be[1] / piv : 0.0;
+    d[0] = x[0] / piv;
+    for (int i = 1; i < m; i++) {
+      piv = (al[i] - sig) - be[i] * c[i - 1];
+      c[i] = (i + 1 < m) ? be[i + 1] / piv : 0.0;
+      d[i] = (x[i] - be[i] * d[i - 1]) / piv;
+    }
+    x[m - 1] = d[m - 1];
+    for (int i = m - 2; i >= 0; i--) x[i] = d[i] - c[i] * x[i + 1];
+    double n2 = 0.0;
+    for (int i = 0; i < m; i++) n2 += x[i] * x[i];
+    const double inv = 1.0 / sqrt(n2);
+    for (int i = 0; i < m; i++) x[i] *= inv;
+  }
+  const double last = fabs(x[m - 1]);
+  free(x);
+  return last;
+}
+
+/*
+ * Reading (the paper needs "an estimate on the spectrum" and defers to [ckor15]): m steps of the
+ * Lanczos recurrence on H_k from the start vector v_i = (2u_{2i} - 1) + i (2u_{2i+1} - 1),
+ * u_c = unit_at(1709064830, c), normalised:
+ *     w = H v_j;  al_j = Re <v_j, w>;  w -= al_j v_j + be_j v_{j-1};  be_{j+1} = |w|;  v_{j+1} = w / be_{j+1},
+ * stopped early when be_{j+1} <= 1e-12 (max |al| + max be) (an invariant subspace).  With
+ * theta_min/max the extreme eigenvalues of the tridiagonal T and r = be_m |s_last| the residual
+ * norms of their Ritz vectors, the enclosure is
+ *     [theta_min - r_min - 0.01 W, theta_max + r_max + 0.01 W] intersected with Gershgorin,
+ * W = theta_max - theta_min (Ritz values lie inside the spectrum; the residual and the 1 % margin
+ * cover the part of the spectrum the Krylov space has not resolved).
+ */
+int orc_set_interval_lanczos(orc_problem *p, int k, int m) {
+  if (!p || k < 0 || k >= p->nterms || !p->term[k].set || m < 1) return ORC_EINVAL;
+  const int64_t D = p->dim;
+  if (m > D) m = (int)D;
+  double complex *v0 = (double complex *)calloc((size_t)D, sizeof(double complex));
+  double complex *v1 = (double complex *)malloc(sizeof(double complex) * (size_t)D);
+  double complex *w = (double complex *)malloc(sizeof(double complex) * (size_t)D);
+  double *al = (double *)calloc((size_t)m + 1, sizeof(double));
+  double *be = (double *)calloc((size_t)m + 2, sizeof(double));
+  if (!v0 || !v1 || !w || !al || !be) { free(v0); free(v1); free(w); free(al); free(be); return ORC_ENOMEM; }
+  const uint64_t seed = 1709064830ull;
+  double n2 = 0.0;
+  for (int64_t i = 0; i < D; i++) {
+    v1[i] = (2.0 * unit_at(seed, 2 * (uint64_t)i) - 1.0) + I * (2.0 * unit_at(seed, 2 * (uint64_t)i + 1) - 1.0);
+    n2 += creal(v1[i]) * creal(v1[i]) + cimag(v1[i]) * cimag(v1[i]);
+  }
+  for (int64_t i = 0; i < D; i++) v1[i] /= sqrt(n2);
+  int mj = 0;
+  double amax = 0.0, bmax = 0.0;
+  for (int j = 0; j < m; j++) {
+    orc_apply_term(p, k, v1, w);
+    double a = 0.0;
+    for (int64_t i = 0; i < D; i++) a += creal(conj(v1[i]) * w[i]);
+    al[j] = a;
+    for (int64_t i = 0; i < D; i++) w[i] -= a * v1[i] + be[j] * v0[i];
+    double b2 = 0.0;
+    for (int64_t i = 0; i < D; i++) b2 += creal(w[i]) * creal(w[i]) + cimag(w[i]) * cimag(w[i]);
+    be[j + 1] = sqrt(b2);
+    mj = j + 1;
+    if (fabs(a) > amax) amax = fabs(a);
+    if (be[j + 1] > bmax) bmax = be[j + 1];
+    if (be[j + 1] <= 1e-12 * (amax + bmax)) { be[j + 1] = 0.0; break; }
+    for (int64_t i = 0; i < D; i++) { v0[i] = v1[i]; v1[i] = w[i] / be[j + 1]; }
+  }
+  const double tmin = tridiag_eig(al, be, mj, 0), tmax = tridiag_eig(al, be, mj, mj - 1);
+  const double W = tmax - tmin;
+  const double eps = 1e-9 * (fabs(tmin) + fabs(tmax) + W + 1e-300);
+  const double rmin = (mj > 1 || be[mj] > 0.0) ? be[mj] * tridiag_last_component(al, be, mj, tmin, -eps) : 0.0;
+  const double rmax = (mj > 1 || be[mj] > 0.0) ? be[mj] * tridiag_last_component(al, be, mj, tmax, eps) : 0.0;
+  double a = tmin - rmin - 0.01 * W, b = tmax + rmax + 0.01 * W;
+  orc_term *t = &p->term[k];
+  if (a < t->a) a = t->a;
+  if (b > t->b) b = t->b;
+  t->a = a;
+  t->b = b;
+  free(v0); free(v1); free(w); free(al); free(be);
+  return ORC_OK;
+}
+
 int orc_set_coeff(orc_problem *p, int k, double a0, int nmodes, const double *ac, const double *as,
                   const double *om) {
   if (!p || k < 0 || k >= p->nterms || nmodes < 0) return ORC_EINVAL;

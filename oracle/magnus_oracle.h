@@ -62,6 +62,8 @@ int orc_set_coeff(orc_problem *p, int k, double a0, int nmodes, const double *ac
                   const double *om);
 int orc_set_leja(orc_problem *p, double tol_rel, double tol_abs, int m_max, double rho_max);
 int orc_term_interval(const orc_problem *p, int k, double *a, double *b);
+/* Replace term k's enclosure by the Lanczos enclosure (m steps) intersected with Gershgorin. */
+int orc_set_interval_lanczos(orc_problem *p, int k, int m);
 double orc_coeff_eval(const orc_problem *p, int k, double t);
 
 /* y = H_k x */

@@ -387,3 +387,65 @@ def test_paper_example1_error_ratios():
     assert 12.0 < err["M4"][0] / err["M4"][1] < 20.0
     ratio = err["CF4"][1] / err["M4"][1]
     assert paper_ratio / 2 < ratio < paper_ratio * 2, (ratio, paper_ratio)
+
+
+# ---------------------------------------------------------------------------
+# Lanczos enclosure of a term's spectrum (Sec. 3: "an estimate on the spectrum")
+# ---------------------------------------------------------------------------
+def _rand_hermitian(rng, n):
+    A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    return (A + A.conj().T) / 2
+
+
+@pytest.mark.parametrize("n", [6, 8, 10])
+def test_lanczos_interval_encloses_spectrum_and_is_tighter(n):
+    """The Lanczos enclosure contains every eigenvalue (numpy eigvalsh), is inside Gershgorin, and
+    is within 5 % of the true spectral width for the XXZ chain."""
+    c = mi.xxz_chain(40 + n, n, 0.01, 1)
+    Hs = oracle.xxz_csr(n, c.J, c.hz, 0.5)
+    Hd = oracle.field_x_csr(n)
+    G = oracle.Problem([Hs, Hd], [oracle.Coeff.const()] * 2)
+    L = oracle.Problem([Hs, Hd], [oracle.Coeff.const()] * 2, interval="lanczos")
+    for k, H in enumerate((Hs, Hd)):
+        ev = np.linalg.eigvalsh(H.todense())
+        a, b = L.interval(k)
+        ga, gb = G.interval(k)
+        tol = 1e-12 * (abs(ev[0]) + abs(ev[-1]))  # eigvalsh's own rounding
+        assert a <= ev[0] + tol and ev[-1] - tol <= b, (k, a, b, ev[0], ev[-1])
+        assert ga <= a and b <= gb
+        assert (b - a) <= 1.05 * (ev[-1] - ev[0]) + 1e-12
+    assert L.interval(1) == (-float(n), float(n))  # sum sx: Gershgorin is already exact
+
+
+def test_lanczos_interval_dense_complex_and_small_dim():
+    """Complex Hermitian dense terms: enclosure of the spectrum; when dim <= the Lanczos steps the
+    recurrence reaches an invariant subspace and the Ritz values are the extreme eigenvalues."""
+    rng = np.random.default_rng(41)
+    A = _rand_hermitian(rng, 300)
+    B = _rand_hermitian(rng, 300)
+    P = oracle.Problem([A, B], [oracle.Coeff.const()] * 2, interval="lanczos")
+    for k, H in enumerate((A, B)):
+        ev = np.linalg.eigvalsh(H)
+        a, b = P.interval(k)
+        assert a <= ev[0] and ev[-1] <= b
+    S = _rand_hermitian(rng, 20)
+    P = oracle.Problem([S], [oracle.Coeff.const()], interval="lanczos", lanczos_steps=48)
+    ev = np.linalg.eigvalsh(S)
+    W = ev[-1] - ev[0]
+    a, b = P.interval(0)
+    assert abs(a - (ev[0] - 0.01 * W)) < 1e-9 * W and abs(b - (ev[-1] + 0.01 * W)) < 1e-9 * W
+
+
+def test_lanczos_interval_propagation_agrees_and_needs_fewer_matvecs():
+    c = mi.workload1()
+    Hs = oracle.xxz_csr(c.nspins, c.J, c.hz, 0.5)
+    Hd = oracle.field_x_csr(c.nspins)
+    f = oracle.Coeff(c.drive_a0, c.drive_ac, c.drive_as, c.drive_om)
+    out, mv = {}, {}
+    for iv in ("gershgorin", "lanczos"):
+        st = oracle.Stats(0)
+        P = oracle.Problem([Hs, Hd], [oracle.Coeff.const(), f], interval=iv)
+        out[iv] = P.propagate(c.psi0, 0.0, c.h, 50, "CF4", st)
+        mv[iv] = st.n_matvec
+    assert np.linalg.norm(out["gershgorin"] - out["lanczos"]) < 1e-11
+    assert mv["lanczos"] < 0.95 * mv["gershgorin"], mv
