@@ -205,7 +205,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     terms = workload_terms(mg, c, storage)
     nnz_total = sum(t.col.numel() for t in terms) if storage.startswith("csr") else None
-    plan = mg.Plan(c.dim, terms, drives(mg, c))
+    plan = mg.Plan(c.dim, terms, drives(mg, c), interval=args.interval)
     psi0 = torch.from_numpy(c.psi0).cuda()
     psi = psi0.clone()
 
@@ -276,6 +276,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"xxz_chain_20spins_{storage}_{variant.lower()}", "spins": c.nspins, "dim": c.dim,
                    "nnz": nnz_total, "h": c.h, "t0": c.t0, "variant": variant, "storage": storage,
+                   "interval": args.interval,
                    "leja_tol": 1e-10, "l2": "inputs larger than L2: the 640 MB CSR is streamed every iteration"
                    if storage.startswith("csr") else "matrix-free; 4 state vectors of 16 MB stay L2-resident",
                    "parallelism": f"replicas x{world}"},
@@ -288,7 +289,7 @@ def run_ours(args):
         "clocks": clk.summary(),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(c, variant, args.cpu_steps)
+        line["cpu_baseline"] = cpu_baseline(c, variant, args.cpu_steps, args.interval)
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()
@@ -508,17 +509,17 @@ def run_adjoint16(args):
 
 
 # --------------------------------------------------------------------------- oracle arm
-def oracle_problem(c):
+def oracle_problem(c, interval="gershgorin"):
     import oracle
     Hs = oracle.xxz_csr(c.nspins, c.J, c.hz, c.delta)
     Hd = oracle.field_x_csr(c.nspins)
     f = oracle.Coeff(c.drive_a0, c.drive_ac, c.drive_as, c.drive_om)
-    return oracle.Problem([Hs, Hd], [oracle.Coeff.const(), f])
+    return oracle.Problem([Hs, Hd], [oracle.Coeff.const(), f], interval=interval)
 
 
-def cpu_baseline(c, variant, nsteps):
+def cpu_baseline(c, variant, nsteps, interval="gershgorin"):
     """The FP64 CPU oracle as it stands (plain C, single thread) on the first nsteps steps."""
-    P = oracle_problem(c)
+    P = oracle_problem(c, interval)
     t = time.perf_counter()
     P.propagate(c.psi0, c.t0, c.h, nsteps, variant)
     dt = time.perf_counter() - t
@@ -533,7 +534,7 @@ def run_reference(args):
     if rank != 0:
         return
     c = mi.workload2()
-    P = oracle_problem(c)
+    P = oracle_problem(c, args.interval)
     psi = c.psi0.copy()
     if args.warmup:
         P.propagate(psi, c.t0, c.h, min(args.warmup, 1), args.variant)
@@ -546,7 +547,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 2),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"xxz_chain_20spins_{args.storage}_{args.variant.lower()}", "spins": c.nspins,
-                   "dim": c.dim, "h": c.h, "variant": args.variant},
+                   "dim": c.dim, "h": c.h, "variant": args.variant, "interval": args.interval},
         "cpu_baseline": {"value": round(value, 4), "unit": "steps/s", "cores": 1, "kind": "oracle",
                          "sample": f"{args.steps} {args.variant} steps of the 20-spin chain, plain C FP64 oracle"},
         "e2e": {"value": round(value, 4), "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -562,6 +563,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--variant", choices=["CF4", "M4", "CF4_3", "M2", "M6"], default="CF4")
     ap.add_argument("--storage", choices=["csr", "csr_real", "mfree"], default="csr")
+    ap.add_argument("--interval", choices=["gershgorin", "lanczos"], default="lanczos",
+                    help="spectral enclosure of each term (20-spin workload)")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")

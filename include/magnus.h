@@ -118,6 +118,13 @@ typedef struct {
   const double *om;
 } magnus_coeff;
 
+typedef enum {
+  MAGNUS_INTERVAL_GERSHGORIN = 0, /* Gershgorin enclosure of every term (rigorous)                       */
+  MAGNUS_INTERVAL_LANCZOS = 1     /* 48 Lanczos steps per term from a fixed start vector: Ritz extremes
+                                     widened by their residual norms and 1 % of the width, intersected
+                                     with Gershgorin (tighter, so lower Leja degrees)                     */
+} magnus_interval;
+
 /*
  * Options; pass NULL for the defaults in brackets.
  *   tol_rel, tol_abs [1e-10, 1e-10]: Leja early termination (Sec. 4: relative and absolute tolerance 1e-10)
@@ -138,6 +145,9 @@ typedef struct {
  *                     out makes the call return MAGNUS_ETIMEOUT and leaves the context usable
  *   test_skip_arrival [0]: testing only -- if nonzero, CTA 0 of the sparse/matrix-free propagation
  *                     kernel leaves before its first grid barrier, so the other CTAs' waits run out
+ *   interval [MAGNUS_INTERVAL_GERSHGORIN]: how each term's spectral enclosure is estimated (Sec. 3:
+ *                     the Leja parameters need "an estimate on the spectrum"); plans only, batches
+ *                     take Gershgorin
  */
 typedef struct {
   double tol_rel;
@@ -149,7 +159,7 @@ typedef struct {
   int32_t precision;
   double barrier_timeout_s;
   int32_t test_skip_arrival;
-  int32_t _pad;
+  int32_t interval;
 } magnus_options;
 
 typedef struct {

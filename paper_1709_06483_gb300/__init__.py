@@ -22,6 +22,7 @@ M4, CF4, CF4_3, M2, M6 = 1, 2, 3, 4, 5
 VARIANTS = {"M4": M4, "CF4": CF4, "CF4_3": CF4_3, "M2": M2, "M6": M6}
 TERM_CSR, TERM_DENSE, TERM_XXZ, TERM_FIELD_X, TERM_CSR_REAL, TERM_DENSE_REAL = 0, 1, 2, 3, 4, 5
 FP64, FP32_SPLIT, TENSOR_SLICED = 0, 1, 2
+INTERVALS = {"gershgorin": 0, "lanczos": 1}
 
 # Every symbol the header declares (checked by the CPU test suite).
 EXPORTS = (
@@ -53,7 +54,7 @@ class Coeff(C.Structure):
 class Options(C.Structure):
     _fields_ = [("tol_rel", C.c_double), ("tol_abs", C.c_double), ("rho_max", C.c_double), ("m_max", C.c_int32),
                 ("nvec", C.c_int32), ("ctas", C.c_int32), ("precision", C.c_int32), ("barrier_timeout_s", C.c_double),
-                ("test_skip_arrival", C.c_int32), ("_pad", C.c_int32)]
+                ("test_skip_arrival", C.c_int32), ("interval", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -264,7 +265,7 @@ class Plan:
     """A Magnus/Leja plan: dim, terms H_k with drives f_k, Leja tolerance, vectors per call."""
 
     def __init__(self, dim, terms, drives, tol=1e-10, tol_abs=None, rho_max=4.0, m_max=100, nvec=1, ctas=0,
-                 precision=FP64, stream=None, barrier_timeout_s=0.0, test_skip_arrival=0):
+                 precision=FP64, stream=None, barrier_timeout_s=0.0, test_skip_arrival=0, interval="gershgorin"):
         import torch
         L = load()
         assert len(terms) == len(drives)
@@ -274,7 +275,8 @@ class Plan:
         tarr = (Term * len(terms))(*[t.ctype() for t in terms])
         carr = (Coeff * len(drives))(*[d.ctype() for d in drives])
         opt = Options(float(tol), float(tol if tol_abs is None else tol_abs), float(rho_max), int(m_max), int(nvec),
-                      int(ctas), int(precision), float(barrier_timeout_s), int(test_skip_arrival), 0)
+                      int(ctas), int(precision), float(barrier_timeout_s), int(test_skip_arrival),
+                      INTERVALS[interval])
         h = C.c_void_p()
         _check(L.magnus_plan_create(C.byref(h), self.dim, len(terms), tarr, carr, C.byref(opt),
                                     _stream_ptr(self.stream)))

@@ -397,6 +397,8 @@ MAGNUS_API magnus_status magnus_batch_create(magnus_batch_t *out, int32_t count,
   if (opt) o = *opt;
   if (o.nvec != 1) return berr(nullptr, MAGNUS_EINVAL, "batch items carry one state each (nvec = 1)");
   if (o.precision != MAGNUS_FP64) return berr(nullptr, MAGNUS_EINVAL, "batches use MAGNUS_FP64");
+  if (o.interval != MAGNUS_INTERVAL_GERSHGORIN)
+    return berr(nullptr, MAGNUS_EINVAL, "batches use MAGNUS_INTERVAL_GERSHGORIN");
   if (o.m_max < 2 || o.m_max > kMmaxLimit || !(o.rho_max > 0.0) || !(o.tol_rel + o.tol_abs > 0.0))
     return berr(nullptr, MAGNUS_EINVAL, "bad options");
   magnus_batch_t b = new magnus_batch_s();

@@ -328,6 +328,8 @@ magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms
     return set_err(nullptr, MAGNUS_EINVAL, "barrier_timeout_s must be in [0, 600]");
   if (o.m_max < 2 || o.m_max > kMmaxLimit) return set_err(nullptr, MAGNUS_EINVAL, "m_max must be 2..%d", kMmaxLimit);
   if (o.nvec < 1 || o.nvec > 64) return set_err(nullptr, MAGNUS_EINVAL, "nvec must be 1..64");
+  if (o.interval != MAGNUS_INTERVAL_GERSHGORIN && o.interval != MAGNUS_INTERVAL_LANCZOS)
+    return set_err(nullptr, MAGNUS_EINVAL, "interval must be MAGNUS_INTERVAL_GERSHGORIN or MAGNUS_INTERVAL_LANCZOS");
   if (o.precision != MAGNUS_FP64 && o.precision != MAGNUS_FP32_SPLIT && o.precision != MAGNUS_TENSOR_SLICED)
     return set_err(nullptr, MAGNUS_EINVAL, "precision must be MAGNUS_FP64, MAGNUS_FP32_SPLIT or MAGNUS_TENSOR_SLICED");
   for (int k = 0; k < nterms; k++) {
@@ -523,6 +525,9 @@ magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms
   PLAN_TRY(dalloc(&gscratch, 2 * gblk));
   for (int k = 0; k < nterms; k++)
     PLAN_TRY(launch_gershgorin(p->terms + k, p->terms_host[k], dim, gscratch, gblk, p->term_ab + 2 * k, p->stream));
+  if (o.interval == MAGNUS_INTERVAL_LANCZOS)
+    for (int k = 0; k < nterms; k++)
+      PLAN_TRY(lanczos_interval(p->terms + k, p->terms_host[k], dim, kLanczosSteps, p->term_ab + 2 * k, p->stream));
   PLAN_TRY(launch_leja_points(p->xi, o.m_max, p->cand, p->counter, p->stream));
   PLAN_TRY(cudaMemcpyAsync(p->term_ab_host, p->term_ab, sizeof(double) * 2 * nterms, cudaMemcpyDeviceToHost, p->stream));
   PLAN_TRY(cudaStreamSynchronize(p->stream));

@@ -114,6 +114,10 @@ cudaError_t launch_gershgorin(const Term *t_dev, const Term &t_host, int64_t dim
                               double *out, cudaStream_t st);
 // Real-valuedness check of a CSR / dense term: flag (device int) set to 1 if any imaginary part != 0.
 cudaError_t launch_imag_check(const double2 *val, int64_t n, int *flag, cudaStream_t st);
+// ab_dev (in: the term's Gershgorin enclosure) <- its intersection with the Lanczos enclosure after
+// m steps; synchronises the stream
+cudaError_t lanczos_interval(const Term *t_dev, const Term &t_host, int64_t D, int m, double *ab_dev, cudaStream_t st);
+constexpr int kLanczosSteps = 48;
 cudaError_t launch_real_parts(const double2 *z, int64_t n, double *out, int *flag, cudaStream_t st);
 // Per-exponential records + divided-difference tables for a whole propagation.
 cudaError_t launch_exp_setup(int variant, double t0, double h, int64_t nsteps, int nterms, const Coeff *coeffs,

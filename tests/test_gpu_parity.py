@@ -148,6 +148,53 @@ def test_real_parts_rejects_complex_values(mg):
     assert r.dtype == torch.float64 and r.cpu().tolist() == [1.5, -2.0]
 
 
+# ----------------------------------------------------------------- Lanczos enclosures
+@pytest.mark.parametrize("kind", ["csr", "csr_real", "mfree"])
+def test_lanczos_intervals_match_oracle(mg, kind):
+    """The device Lanczos enclosure (same start vector, same recurrence, fixed-order reductions)
+    against the oracle's, and against the true spectrum."""
+    c = mi.xxz_chain(26, 10, 0.01, 1)
+    plan = mg.Plan(c.dim, chain_terms(mg, c, kind), drives_gpu(mg, c), interval="lanczos")
+    P = oracle_problem(c, interval="lanczos")
+    Hs = oracle.xxz_csr(c.nspins, c.J, c.hz, c.delta)
+    ev = np.linalg.eigvalsh(Hs.todense())
+    for k in range(2):
+        a, b = plan.interval(k)
+        ra, rb = P.interval(k)
+        assert abs(a - ra) < 1e-8 * (rb - ra) and abs(b - rb) < 1e-8 * (rb - ra), (k, a, b, ra, rb)
+    a, b = plan.interval(0)
+    assert a <= ev[0] + 1e-11 and ev[-1] - 1e-11 <= b
+
+
+def test_lanczos_intervals_dense(mg):
+    c = mi.workload3(nvec=1, nspins=8, h=0.02, nsteps=2)
+    Hs = mg.build_longrange_dense(c.nspins, c.hz, 1.5, c.delta)
+    plan = mg.Plan(c.dim, [mg.DenseTerm(Hs), mg.FieldXTerm(c.nspins)], drives_gpu(mg, c), interval="lanczos")
+    Ho = oracle.longrange_dense(c.nspins, c.hz, 1.5, c.delta)
+    P = oracle.Problem([Ho, oracle.field_x_csr(c.nspins)], [oracle.Coeff.const()] * 2, interval="lanczos")
+    a, b = plan.interval(0)
+    ra, rb = P.interval(0)
+    assert abs(a - ra) < 1e-8 * (rb - ra) and abs(b - rb) < 1e-8 * (rb - ra)
+    ev = np.linalg.eigvalsh(Ho)
+    assert a <= ev[0] + 1e-11 and ev[-1] - 1e-11 <= b
+
+
+@pytest.mark.parametrize("variant", ["CF4", "M4"])
+def test_lanczos_propagation_matches_oracle(mg, variant):
+    """Propagation on Lanczos enclosures: same state (1e-10) and Leja degrees as the oracle on its
+    own Lanczos enclosures, and fewer matvecs than on Gershgorin enclosures."""
+    c = mi.workload1()
+    plan = mg.Plan(c.dim, chain_terms(mg, c, "csr"), drives_gpu(mg, c), interval="lanczos")
+    psi = cuda(c.psi0)
+    st = plan.propagate(psi, c.t0, c.h, c.nsteps, variant, log_cap=512)
+    ost = oracle.Stats(512)
+    ref = oracle_problem(c, interval="lanczos").propagate(c.psi0, c.t0, c.h, c.nsteps, variant, ost)
+    assert np.array_equal(st["m_log"], ost.m_log)
+    assert rel(psi.cpu().numpy(), ref) < REL_TOL
+    g = mg.Plan(c.dim, chain_terms(mg, c, "csr"), drives_gpu(mg, c)).propagate(cuda(c.psi0), c.t0, c.h, c.nsteps, variant)
+    assert st["n_matvec"] < g["n_matvec"]
+
+
 # ----------------------------------------------------------------- propagation, workload 1
 @pytest.mark.parametrize("kind", ["csr", "csr_real", "mfree"])
 @pytest.mark.parametrize("variant", ["CF4", "M4"])
@@ -286,22 +333,25 @@ def test_errors_are_reported(mg):
 @pytest.fixture(scope="module")
 def wl2():
     c = mi.workload2()
-    return c, oracle_problem(c), {}
+    return c, {}, {}
 
 
+@pytest.mark.parametrize("interval", ["gershgorin", "lanczos"])
 @pytest.mark.parametrize("kind", ["csr", "mfree"])
 @pytest.mark.parametrize("variant", ["CF4", "M4"])
-def test_workload2_full_size_first_steps(mg, wl2, kind, variant):
+def test_workload2_full_size_first_steps(mg, wl2, kind, variant, interval):
     """20 spins (dim 2^20) in the bench's launch configuration: the first 2 steps against the oracle,
-    every entry compared."""
-    c, P, cache = wl2
-    plan = mg.Plan(c.dim, chain_terms(mg, c, kind), drives_gpu(mg, c))
+    every entry compared, on either enclosure."""
+    c, problems, cache = wl2
+    if interval not in problems:
+        problems[interval] = oracle_problem(c, interval=interval)
+    plan = mg.Plan(c.dim, chain_terms(mg, c, kind), drives_gpu(mg, c), interval=interval)
     psi = cuda(c.psi0)
     st = plan.propagate(psi, 0.0, c.h, 2, variant, log_cap=16)
-    if variant not in cache:
+    if (variant, interval) not in cache:
         ost = oracle.Stats(16)
-        cache[variant] = (P.propagate(c.psi0, 0.0, c.h, 2, variant, ost), ost.m_log)
-    ref, mlog = cache[variant]
+        cache[(variant, interval)] = (problems[interval].propagate(c.psi0, 0.0, c.h, 2, variant, ost), ost.m_log)
+    ref, mlog = cache[(variant, interval)]
     assert np.array_equal(st["m_log"], mlog)
     assert rel(psi.cpu().numpy(), ref) < REL_TOL
 
