@@ -349,8 +349,8 @@ def run_dense13(args):
                      "matvec_gbs": round(bytes_it * nmv / (kms / 1e3) / 1e9, 2),
                      "fp64_equiv_tflops": round(2 * fma_it * nmv / (kms / 1e3) / 1e12, 4), "clocks": r["clk"]}
         if prec == "tensor_sliced":
-            # issued bf16 MMA work: 15 digit pairs x 2 flops x D^2 x 128 padded columns per dense term
-            out[prec]["bf16_tflops_issued"] = round(15 * 2 * D * D * 128 * 2 * nmv / (kms / 1e3) / 1e12, 2)
+            # issued bf16 MMA work (tcgen05, Cf4): 10 digit pairs x 2 flops x D^2 x 128 columns per dense term
+            out[prec]["bf16_tflops_issued"] = round(10 * 2 * D * D * 128 * 2 * nmv / (kms / 1e3) / 1e12, 2)
     a = res["fp64"]["psi"].cpu().numpy()
     errs = {}
     for prec in ("fp32_split", "tensor_sliced"):

@@ -15,7 +15,10 @@
 // reads the same totals and takes the same decisions.
 #include <math.h>
 
+#include <algorithm>
 #include <cuda_bf16.h>
+
+#include "dense_tc.cuh"
 
 #include "magnus_internal.cuh"
 #include "persist_common.cuh"
@@ -359,10 +362,14 @@ __device__ __forceinline__ int cover_exponent(double m) {
 }
 
 // ------------------------------------------------------------------ kernel
+// PREC: 0 FP64, 1 FP32 split, 2 sliced digits on mma.sync (5 x 7 bits), 3 sliced digits on tcgen05
+// (4 x 8 bits, linear generators; the product phase of dense_tc.cuh).
 template <bool REAL, bool TILED, int PREC>
-__global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) {
+__global__ void __launch_bounds__(kDBlock, 1)
+    k_dense_persistent(PersistArgs a, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB) {
   constexpr bool SPLIT = PREC == 1;
   constexpr bool SLICED = PREC == 2;
+  constexpr bool TC = PREC == 3;
   __shared__ Term sT[kMaxTerms];
   __shared__ ExpRec sR;
   __shared__ double s_vn[kVecMax], s_ep[kVecMax], s_pn[kVecMax];
@@ -374,6 +381,7 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ unsigned long long s_cmax[kTcCols];
   __shared__ int s_cexp[kTcCols];
+  __shared__ tcg::Bars tc_bars;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ty = tid >> 4, tx = tid & 15;
@@ -390,6 +398,24 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
   for (int i = tid; i < nt * (int)sizeof(Term) / 4; i += blockDim.x)
     reinterpret_cast<int *>(sT)[i] = reinterpret_cast<const int *>(a.terms)[i];
   __syncthreads();
+  tcg::Pipe tc_pipe{0u, 0u};
+  tcg::Geometry tc_geom{};
+  if (TC) {
+    tc_geom.ndense = a.tc_ndense;
+    tc_geom.T = a.tc_T;
+    tc_geom.C = a.tc_T;
+    tc_geom.N = a.tc_N;
+    tc_geom.slots = a.tc_slots;
+    if (tid == 0) {
+      for (int i = 0; i < tcg::kNS; i++) {
+        tc::mbar_init(&tc_bars.full[i], 1);
+        tc::mbar_init(&tc_bars.empty[i], 1);
+      }
+      tc::mbar_init(&tc_bars.accr, 1);
+      tc::mbar_fence_init();
+    }
+    __syncthreads();
+  }
 
   double *partials = a.partials;                        // [2][G][nv][2]
   double *totals = a.partials + (size_t)4 * G * nv;     // [2][nv][2]
@@ -482,11 +508,49 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
     for (int v = 0; v < nv; v++)
       for (int64_t r = lo + tid; r < hi; r += blockDim.x) {
         const double2 x = X[(int64_t)v * D + r];
-        slice_value(x.x, s_cexp[2 * v], dg + (size_t)(2 * v) * D + r, stride);
-        slice_value(x.y, s_cexp[2 * v + 1], dg + (size_t)(2 * v + 1) * D + r, stride);
+        if (TC) {
+          tcg::slice_value(x.x, s_cexp[2 * v], dg + (size_t)(2 * v) * D + r, stride);
+          tcg::slice_value(x.y, s_cexp[2 * v + 1], dg + (size_t)(2 * v + 1) * D + r, stride);
+        } else {
+          slice_value(x.x, s_cexp[2 * v], dg + (size_t)(2 * v) * D + r, stride);
+          slice_value(x.y, s_cexp[2 * v + 1], dg + (size_t)(2 * v + 1) * D + r, stride);
+        }
       }
+    // the digits are read next by TMA (async proxy) in other CTAs
+    if (TC) asm volatile("fence.proxy.async.global;" ::: "memory");
     slice_ev++;
     return grid_barrier(a.bar, G, a.spin_limit_ns);
+  };
+
+  // tcgen05 path: vector set s of the digit buffer and its column exponents
+  auto tc_set_digits = [&](int set) { return (void *)((__nv_bfloat16 *)a.tc_wd + (size_t)set * tcg::kSl * 2 * nv * D); };
+  auto tc_set_exps = [&](int set) { return a.tc_ex + set * kTcCols; };
+  // y += coef (H_k W)[rows of this 32-row tile] from the partial tiles of the last product phase
+  auto tc_term = [&](int k, double coef, int64_t r0, double2 (&y)[2][4]) {
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+      const int64_t r = r0 + 2 * ty + i;
+      if (r >= hi) continue;
+      const long long tile = (long long)a.tc_dslot[k] * tc_geom.T + r / tcg::kM;
+      const int rr = (int)(r % tcg::kM);
+      int bf, bl;
+      tcg::tile_owners(tile, tc_geom, (int)G, &bf, &bl);
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        const int v = tx + 16 * q;
+        if (v >= nv) continue;
+        double sx = 0.0, sy = 0.0;
+        for (int bb = bf; bb <= bl; bb++) {
+          if (tcg::range_lo(bb, (int)G, tc_geom.N) == tcg::range_lo(bb + 1, (int)G, tc_geom.N)) continue;
+          const double *Pt =
+              a.tc_P + ((size_t)bb * tc_geom.slots + tcg::tile_slot(tile, bb, tc_geom, (int)G)) * (size_t)(tcg::kN * tcg::kM);
+          sx += Pt[(size_t)(2 * v) * tcg::kM + rr];
+          sy += Pt[(size_t)(2 * v + 1) * tcg::kM + rr];
+        }
+        y[i][q].x = fma(coef, sx, y[i][q].x);
+        y[i][q].y = fma(coef, sy, y[i][q].y);
+      }
+    }
   };
 
   const void *sl_src[kMaxTerms] = {nullptr, nullptr, nullptr, nullptr};  // digits of the vectors being read
@@ -501,7 +565,9 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
       for (int k = 0; k < nt; k++) {
         if (coef[k] == 0.0) continue;
         if (sT[k].kind == MAGNUS_TERM_DENSE) {
-          if (SLICED)
+          if (TC)
+            tc_term(k, coef[k], r0, y);
+          else if (SLICED)
             gemm_tile_sliced(dsm, (const __nv_bfloat16 *)a.hslice[k], a.hexp[k], (const __nv_bfloat16 *)sl_src[k],
                              ex_src[k], coef[k], D, nv, r0, y);
           else if (SPLIT)
@@ -594,6 +660,9 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
       if (SLICED) {
         if (!slice_set(cur, a.sl_cur, a.ex_cur)) { fail(MAGNUS_ETIMEOUT); return; }
       }
+      if (TC) {
+        if (!slice_set(cur, tc_set_digits(0), tc_set_exps(0))) { fail(MAGNUS_ETIMEOUT); return; }
+      }
       __syncthreads();
       bool done = false;
       for (int j = 1; j <= a.m_max; j++) {
@@ -605,6 +674,16 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
         const double2 dj = d[j];
         const double2 *srcs[kMaxTerms] = {src, src, src, src};
         const float4 *shs[kMaxTerms] = {src_sh, src_sh, src_sh, src_sh};
+        if (TC) {  // all dense products of this iteration on the tensor cores, then a barrier
+          if (R.mode != MODE_LINEAR) { fail(MAGNUS_EINVAL); return; }
+          const int set = (j == 1) ? 0 : (((j - 2) & 1) ? 2 : 1);
+          if (!tcg::gemm_phase(&tmA, &tmB, set, tc_geom, a.tc_eh, tc_set_exps(set), a.tc_P, dsm, tc_bars, tc_pipe,
+                               a.tc_spins)) {
+            fail(MAGNUS_ETIMEOUT);
+            return;
+          }
+          if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { fail(MAGNUS_ETIMEOUT); return; }
+        }
         if (SLICED) {
           const void *d_src = (j == 1) ? a.sl_cur : (((j - 2) & 1) ? a.sl_w1 : a.sl_w0);
           const int *e_src = (j == 1) ? a.ex_cur : (((j - 2) & 1) ? a.ex_w1 : a.ex_w0);
@@ -776,6 +855,13 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
             return;
           }
         }
+        if (TC && j < a.m_max) {
+          const int set = ((j - 1) & 1) ? 2 : 1;
+          if (!slice_set(dst, tc_set_digits(set), tc_set_exps(set))) {
+            fail(MAGNUS_ETIMEOUT);
+            return;
+          }
+        }
       }
       if (!done) { fail(MAGNUS_ENOCONV); return; }
       if (tid < nv) s_vn[tid] = s_pn[tid];
@@ -804,6 +890,7 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
 const void *dense_kernel(bool real, bool tiled, int prec) {
   if (prec == 1) return (const void *)k_dense_persistent<true, true, 1>;
   if (prec == 2) return (const void *)k_dense_persistent<true, true, 2>;
+  if (prec == 3) return (const void *)k_dense_persistent<true, true, 3>;
   if (real)
     return tiled ? (const void *)k_dense_persistent<true, true, 0> : (const void *)k_dense_persistent<true, false, 0>;
   return tiled ? (const void *)k_dense_persistent<false, true, 0> : (const void *)k_dense_persistent<false, false, 0>;
@@ -814,9 +901,14 @@ cudaError_t sliced_attr() {
   if (done) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(dense_kernel(true, true, 2), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)kTcSmemBytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(dense_kernel(true, true, 3), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tcg::kSmemBytes);
   if (e == cudaSuccess) done = true;
   return e;
 }
+
+size_t dyn_smem(int prec) { return prec == 2 ? kTcSmemBytes : (prec == 3 ? tcg::kSmemBytes : 0); }
 
 }  // namespace
 
@@ -857,6 +949,40 @@ cudaError_t launch_slice_dense(const double *Hr, int rs, int64_t D, void *digits
 
 size_t dense_sliced_smem_bytes() { return kTcSmemBytes; }
 
+namespace {
+// one warp per row: row maximum -> exponent, then the row's 4 digits of 8 bits
+__global__ void k_slice_dense_tc(const double *Hr, int rs, int64_t D, __nv_bfloat16 *digits, int *rexp) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < D; r += nw) {
+    double m = 0.0;
+    for (int64_t c = lane; c < D; c += 32) m = fmax(m, fabs(Hr[(r * D + c) * rs]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(kFull, m, o));
+    const int e = tcg::cover_exponent(m);
+    if (lane == 0) rexp[r] = e;
+    for (int64_t c = lane; c < D; c += 32) tcg::slice_value(Hr[(r * D + c) * rs], e, digits + r * D + c, (size_t)D * D);
+  }
+}
+}  // namespace
+
+cudaError_t launch_slice_dense_tc(const double *Hr, int rs, int64_t D, void *digits, int *rexp, cudaStream_t st) {
+  k_slice_dense_tc<<<152 * 8, 256, 0, st>>>(Hr, rs, D, (__nv_bfloat16 *)digits, rexp);
+  return cudaGetLastError();
+}
+
+size_t dense_tc_smem_bytes() { return tcg::kSmemBytes; }
+
+int dense_tc_slots(int ndense, int64_t D, int grid) {
+  const long long T = D / tcg::kM, N = (long long)ndense * T * T;
+  int slots = 1;
+  for (int b = 0; b < grid; b++) {
+    const long long i0 = tcg::range_lo(b, grid, N), i1 = tcg::range_lo(b + 1, grid, N);
+    if (i0 < i1) slots = std::max(slots, (int)((i1 - 1) / T - i0 / T + 1));
+  }
+  return slots;
+}
+
 cudaError_t launch_split_dense(const double *Hr, int rs, float2 *out, int64_t n, cudaStream_t st) {
   k_split_dense<<<152 * 8, 256, 0, st>>>(Hr, rs, out, n);
   return cudaGetLastError();
@@ -867,11 +993,11 @@ cudaError_t dense_max_blocks_per_sm(int *n) {
   cudaError_t e0 = sliced_attr();
   if (e0 != cudaSuccess) return e0;
   for (int r = 0; r < 2; r++)
-    for (int t = 0; t < 4; t++) {
+    for (int t = 0; t < 5; t++) {
       int k = 0;
       const int prec = t >= 2 ? t - 1 : 0;
       cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, dense_kernel(r, t > 0, prec), kDBlock,
-                                                                    prec == 2 ? kTcSmemBytes : 0);
+                                                                    dyn_smem(prec));
       if (e != cudaSuccess) return e;
       best = k < best ? k : best;
     }
@@ -879,16 +1005,20 @@ cudaError_t dense_max_blocks_per_sm(int *n) {
   return cudaSuccess;
 }
 
-cudaError_t launch_dense_persistent(const PersistArgs &a, bool real_valued, int grid, cudaStream_t st) {
+cudaError_t launch_dense_persistent(const PersistArgs &a, bool real_valued, int grid, const void *tmA, const void *tmB,
+                                    cudaStream_t st) {
   PersistArgs copy = a;
-  void *args[] = {&copy};
-  const int prec = a.sliced ? 2 : (a.split ? 1 : 0);
-  if (prec == 2) {
+  CUtensorMap ma{}, mb{};
+  if (tmA) ma = *(const CUtensorMap *)tmA;
+  if (tmB) mb = *(const CUtensorMap *)tmB;
+  void *args[] = {&copy, &ma, &mb};
+  const int prec = a.tc ? 3 : (a.sliced ? 2 : (a.split ? 1 : 0));
+  if (prec >= 2) {
     cudaError_t e = sliced_attr();
     if (e != cudaSuccess) return e;
   }
   return cudaLaunchCooperativeKernel(dense_kernel(real_valued, a.nvec > 1 || prec > 0, prec), dim3(grid),
-                                     dim3(kDBlock), args, prec == 2 ? kTcSmemBytes : 0, st);
+                                     dim3(kDBlock), args, dyn_smem(prec), st);
 }
 
 }  // namespace mg

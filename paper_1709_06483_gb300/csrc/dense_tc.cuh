@@ -1,0 +1,255 @@
+// Exact-digit dense products on the 5th-generation tensor cores (MAGNUS_TENSOR_SLICED, linear
+// generators).  Y_k = H_k W for every dense term k and one set W of up to 128 real columns (the real
+// and imaginary parts of up to 64 states), with H_k and W given as 4 signed 8-bit digits per value:
+//     H[r][j] = 2^{e_r} sum_t h_t[r][j] 2^{-8(t+1)},   W[c][j] = 2^{e_c} sum_u w_u[c][j] 2^{-8(u+1)},
+// |h_0|, |w_0| <= 256, the other digits <= 128, all exact in bf16.  The digit products of level
+// g = t + u <= 3 (10 of the 16 pairs) are summed by tcgen05.mma (kind::f16) into four FP32
+// accumulators in tensor memory, one 128 x 128 tile each (all 512 TMEM columns):
+//   * levels 0 and 1 restart every 128-column chunk of K; there every partial sum is an integer of
+//     magnitude below 2^24 (per K index at most 2^16 + 2^15), so FP32 holds it exactly, and the
+//     chunk sums are moved to int64 (S = 2^8 L_0 + L_1) after each chunk;
+//   * levels 2 and 3 (weights 2^-16 and 2^-24 of level 0) accumulate in FP32 over the whole range;
+//     their rounding is below 2^-40 of the product scale.
+// The value is Y[r][c] = 2^{e_r + e_c - 24} (S + (L_2 + L_3 2^-8) 2^-8).  The truncation after four
+// digits and the omitted levels 4..6 leave below D * 2^-30 * max_j |H_rj| * max_j |W_cj| per entry.
+//
+// Work split: the items (dense term, 128-row tile, K chunk) in that order are cut into G contiguous
+// ranges, one per CTA; a CTA accumulates consecutive chunks of the same tile and writes one FP64
+// partial tile per (tile it touched) into its own slots; the caller sums the partials of a tile in
+// CTA order after a grid barrier (deterministic).  Operands arrive by TMA (4-D tiled loads, one box
+// = 8 K x 128 rows x 4 digits, no swizzle) into a 3-deep ring of 64 KB stages; one thread issues the
+// loads and the MMAs, all 8 warps move the accumulators out of tensor memory.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "tcgen05.cuh"
+
+namespace mg {
+namespace tcg {
+
+constexpr int kSl = 4;                          // digits per value
+constexpr int kM = 128;                         // rows per tile (MMA M)
+constexpr int kN = 128;                         // columns (MMA N)
+constexpr int kKS = 32;                         // K per pipeline stage
+constexpr int kChunk = 128;                     // K per exact chunk
+constexpr int kStagesPerChunk = kChunk / kKS;   // 4
+constexpr int kNS = 3;                          // ring depth
+constexpr uint32_t kBox = 8 * kM * kSl * 2;     // 8 KB: one TMA box (8 K x 128 rows x 4 digits)
+constexpr uint32_t kStageA = 4 * kBox;          // 32 KB: the 4 K-cores of a stage
+constexpr uint32_t kStageBytes = 2 * kStageA;   // A and B
+constexpr size_t kSmemBytes = (size_t)kNS * kStageBytes + 1024;  // + alignment slack
+constexpr uint32_t kTmemCols = 512;             // 4 levels x 128 columns
+constexpr uint32_t kIdesc = tc::idesc_bf16(kM, kN);
+constexpr int kThreads = 256;                   // 8 warps: lane quadrant = warp % 4, column half = warp / 4
+
+struct Bars {
+  uint64_t full[kNS];
+  uint64_t empty[kNS];
+  uint64_t accr;
+  uint32_t tmem;
+  uint32_t _pad;
+};
+
+// running counters of the ring and of the chunk barrier; identical in every thread of the CTA
+struct Pipe {
+  uint32_t stage;  // stages issued so far
+  uint32_t chunk;  // chunks completed so far
+};
+
+struct Geometry {
+  int ndense;       // dense terms
+  int T;            // row tiles (D / 128)
+  int C;            // chunks per tile (D / 128)
+  long long N;      // items = ndense * T * C
+  int slots;        // partial tiles per CTA
+};
+
+__host__ __device__ inline long long range_lo(long long b, int G, long long N) { return b * N / G; }
+
+// one value -> 4 digits of 8 bits with exponent e (|x| < 2^e); exact FP64 steps
+__device__ __forceinline__ void slice_value(double x, int e, __nv_bfloat16 *out, size_t stride) {
+  double a = ldexp(x, -e);
+#pragma unroll
+  for (int t = 1; t <= kSl; t++) {
+    const double sc = ldexp(1.0, 8 * t);
+    const double q = rint(a * sc);
+    out[(t - 1) * stride] = __float2bfloat16_rn((float)q);
+    a = fma(-q, 1.0 / sc, a);
+  }
+}
+
+__device__ __forceinline__ int cover_exponent(double m) {
+  int e = 0;
+  if (m > 0.0) frexp(m, &e);
+  return e;
+}
+
+// Y_k = H_k W for the set `set` of the B map, this CTA's range.  P: partial tiles
+// [G][slots][kN cols][kM rows] (FP64, column-major in the tile); eh: row exponents [ndense][D];
+// ec: column exponents of the set [kN].  smem: kSmemBytes of dynamic shared memory.  Returns false
+// if a bounded wait ran out (the caller reports MAGNUS_ETIMEOUT).
+__device__ bool gemm_phase(const CUtensorMap *tmA, const CUtensorMap *tmB, int set, const Geometry &g,
+                           const int *eh, const int *ec, double *P, unsigned char *smem_raw, Bars &bars, Pipe &pipe,
+                           long long max_spins) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int b = blockIdx.x, G = gridDim.x;
+  unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const long long i0 = range_lo(b, G, g.N), i1 = range_lo(b + 1, G, g.N);
+  const long long D = (long long)g.T * kM;
+  if (i0 >= i1) return true;
+
+  if (warp == 0) tc::tmem_alloc(&bars.tmem, kTmemCols);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = bars.tmem;
+  bool ok = true;
+
+  const int quad = warp & 3, half = warp >> 2;
+  const int row = quad * 32 + lane;           // TMEM lane = tile row
+  const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
+  long long S[kN / 2];                        // exact levels 0, 1 of this thread's 64 columns
+
+  const long long nstages = (i1 - i0) * kStagesPerChunk;
+  // stage j of the range -> item i0 + j / 4, K offset
+  auto load_stage = [&](long long j) {
+    const uint32_t gs = pipe.stage + (uint32_t)j;
+    const int buf = (int)(gs % kNS);
+    const long long item = i0 + j / kStagesPerChunk;
+    const long long tile = item / g.C;
+    const int k0 = (int)(item % g.C) * kChunk + (int)(j % kStagesPerChunk) * kKS;
+    const int term = (int)(tile / g.T), r0 = (int)(tile % g.T) * kM;
+    unsigned char *sa = smem + (size_t)buf * kStageBytes, *sb = sa + kStageA;
+    tc::mbar_expect_tx(&bars.full[buf], kStageBytes);
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+      tc::tma_load_4d(sa + c * kBox, tmA, k0 + 8 * c, r0, 0, term, &bars.full[buf]);
+      tc::tma_load_4d(sb + c * kBox, tmB, k0 + 8 * c, 0, 0, set, &bars.full[buf]);
+    }
+  };
+
+  // the issuing thread: prologue loads (after making the generic-proxy writes of the digits visible)
+  if (tid == 0) {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    for (long long j = 0; j < nstages && j < kNS; j++) {
+      const uint32_t gs = pipe.stage + (uint32_t)j;
+      if (gs >= kNS && !tc::mbar_wait(&bars.empty[gs % kNS], ((gs / kNS) - 1) & 1u, max_spins)) ok = false;
+      if (ok) load_stage(j);
+    }
+  }
+
+  uint32_t fresh = 0xFu;  // levels whose next MMA starts a new sum
+  long long j = 0;        // next stage to issue
+  int slot = 0;
+  for (long long item = i0; item < i1; item++) {
+    const long long tile = item / g.C;
+    const bool tile_start = (item == i0) || (item % g.C == 0);
+    const bool tile_end = (item + 1 == i1) || ((item + 1) % g.C == 0);
+    if (tile_start) {
+#pragma unroll
+      for (int q = 0; q < kN / 2; q++) S[q] = 0;
+      fresh = 0xFu;
+    }
+    fresh |= 0x3u;  // levels 0 and 1 restart every chunk
+    // ---- issue the chunk's 4 stages (one thread)
+    if (tid == 0) {
+      for (int st = 0; st < kStagesPerChunk && ok; st++, j++) {
+        const uint32_t gs = pipe.stage + (uint32_t)j;
+        const int buf = (int)(gs % kNS);
+        if (!tc::mbar_wait(&bars.full[buf], (gs / kNS) & 1u, max_spins)) { ok = false; break; }
+        tc::fence_after_sync();
+        const uint32_t sa = tc::smem_u32(smem + (size_t)buf * kStageBytes), sb = sa + kStageA;
+#pragma unroll
+        for (int ks = 0; ks < kKS / 16; ks++) {
+#pragma unroll
+          for (int t = 0; t < kSl; t++)
+#pragma unroll
+            for (int u = 0; u < kSl; u++) {
+              const int lvl = t + u;
+              if (lvl > 3) continue;
+              const uint64_t ad = tc::smem_desc(sa + (uint32_t)(2 * ks) * kBox + (uint32_t)t * 2048u, kBox, 128);
+              const uint64_t bd = tc::smem_desc(sb + (uint32_t)(2 * ks) * kBox + (uint32_t)u * 2048u, kBox, 128);
+              const uint32_t acc = ((fresh >> lvl) & 1u) ? 0u : 1u;
+              fresh &= ~(1u << lvl);
+              tc::mma_bf16(tmem + (uint32_t)lvl * kN, ad, bd, kIdesc, acc);
+            }
+        }
+        tc::mma_commit(&bars.empty[buf]);
+        // refill the buffer of the previous stage once its MMAs are done
+        if (j >= 1 && j - 1 + kNS < nstages) {
+          const uint32_t gp = pipe.stage + (uint32_t)(j - 1);
+          if (!tc::mbar_wait(&bars.empty[gp % kNS], (gp / kNS) & 1u, max_spins)) { ok = false; break; }
+          load_stage(j - 1 + kNS);
+        }
+      }
+      tc::mma_commit(&bars.accr);
+    }
+    __syncwarp();
+    // ---- chunk accumulators -> int64 (all warps); a failed wait anywhere stops the whole CTA
+    const bool got = tc::mbar_wait(&bars.accr, pipe.chunk & 1u, max_spins);
+    pipe.chunk++;
+    ok = __syncthreads_and((ok && got) ? 1 : 0) != 0;
+    tc::fence_after_sync();
+    if (ok) {
+#pragma unroll
+      for (int c16 = 0; c16 < 4; c16++) {
+        uint32_t v0[16], v1[16];
+        const uint32_t col = (uint32_t)(half * 64 + c16 * 16);
+        tc::tmem_ld16(tmem + lane_base + 0 * kN + col, v0);
+        tc::tmem_ld16(tmem + lane_base + 1 * kN + col, v1);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int q = 0; q < 16; q++)
+          S[c16 * 16 + q] += ((long long)__float2int_rn(__uint_as_float(v0[q])) << 8) +
+                             (long long)__float2int_rn(__uint_as_float(v1[q]));
+      }
+    }
+    if (ok && tile_end) {
+      // FP64 partial tile: levels 0/1 exact, 2/3 from tensor memory
+      const int term = (int)(tile / g.T), r0 = (int)(tile % g.T) * kM;
+      const int er = eh[(long long)term * D + r0 + row];
+      double *out = P + ((size_t)b * g.slots + slot) * (size_t)(kN * kM);
+#pragma unroll
+      for (int c16 = 0; c16 < 4; c16++) {
+        uint32_t v2[16], v3[16];
+        const uint32_t col = (uint32_t)(half * 64 + c16 * 16);
+        tc::tmem_ld16(tmem + lane_base + 2 * kN + col, v2);
+        tc::tmem_ld16(tmem + lane_base + 3 * kN + col, v3);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int q = 0; q < 16; q++) {
+          const int cc = (int)col + q;
+          const double lo = ((double)__uint_as_float(v2[q]) + (double)__uint_as_float(v3[q]) * 0x1.0p-8) * 0x1.0p-8;
+          out[(size_t)cc * kM + row] = ldexp((double)S[c16 * 16 + q] + lo, er + ec[cc] - 24);
+        }
+      }
+      slot++;
+    }
+    tc::fence_before_sync();
+    __syncthreads();  // tensor memory free for the next chunk's (or tile's) restarting levels
+    tc::fence_after_sync();
+    if (!ok) break;
+  }
+  pipe.stage += (uint32_t)nstages;
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+  return ok;
+}
+
+// The CTAs whose ranges hold the chunks of tile `tile` (global tile index term * T + r), and for
+// each its slot; the caller sums P over them in this order.
+__host__ __device__ inline void tile_owners(long long tile, const Geometry &g, int G, int *b_first, int *b_last) {
+  const long long t0 = tile * g.C, t1 = t0 + g.C;  // items [t0, t1)
+  *b_first = (int)(((t0 + 1) * G - 1) / g.N);
+  *b_last = (int)((t1 * G - 1) / g.N);
+}
+__host__ __device__ inline int tile_slot(long long tile, int b, const Geometry &g, int G) {
+  return (int)(tile - range_lo(b, G, g.N) / g.C);
+}
+
+}  // namespace tcg
+}  // namespace mg

@@ -1,6 +1,8 @@
 // Host implementation of the C ABI declared in include/magnus.h.  Argument checking, device
 // allocation, and launching the kernels of setup_kernels.cu and leja_persistent.cu; no part of
 // the method's arithmetic runs on the host.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -52,6 +54,16 @@ struct magnus_plan_s {
   int *ex_sets = nullptr;                // [3 + nterms][128] column exponents
   unsigned long long *colmax = nullptr;  // [3][128]
   double2 *m6 = nullptr;                 // M6 intermediate vectors [kM6Slots][nvec][dim], on first use
+  // MAGNUS_TENSOR_SLICED on tcgen05 (linear generators)
+  uint16_t *tc_hd = nullptr;             // dense-term digits [ndense][4][dim][dim]
+  int *tc_eh = nullptr;                  // their row exponents [ndense][dim]
+  uint16_t *tc_wd = nullptr;             // vector-set digits [3][4][2 nvec][dim]
+  int *tc_ex = nullptr;                  // column exponents [3][128]
+  double *tc_P = nullptr;                // partial tiles [grid][slots][128][128]
+  int tc_grid = 0, tc_slots = 0, tc_ndense = 0;
+  int tc_dslot[kMaxTerms] = {0, 0, 0, 0};
+  CUtensorMap tmA{}, tmB{};
+  bool m4_sliced_ready = false;          // the 5 x 7-bit tables of the M4 path exist
   int lbits = 0;
   double *dlo = nullptr, *dhi = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -93,12 +105,63 @@ void free_plan(magnus_plan_t p) {
                   p->alt, p->w0, p->w1, p->u, p->recs, p->dd, p->mlog, p->dlo, p->dhi,
                   p->hsplit[0], p->hsplit[1], p->hsplit[2], p->hsplit[3], p->sh_cur, p->sh_w0, p->sh_w1, p->sh_u,
                   p->hslice[0], p->hslice[1], p->hslice[2], p->hslice[3], p->hexp[0], p->hexp[1], p->hexp[2],
-                  p->hexp[3], p->sl_cur, p->sl_w0, p->sl_w1, p->sl_u, p->ex_sets, p->colmax, p->m6};
+                  p->hexp[3], p->sl_cur, p->sl_w0, p->sl_w1, p->sl_u, p->ex_sets, p->colmax, p->m6,
+                  p->tc_hd, p->tc_eh, p->tc_wd, p->tc_ex, p->tc_P};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (p->ev0) cudaEventDestroy(p->ev0);
   if (p->ev1) cudaEventDestroy(p->ev1);
   delete p;
+}
+
+// cuTensorMapEncodeTiled from the driver (no link-time dependency on libcuda)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)f;
+  }
+  return fn;
+}
+
+// 4-D bf16 digit tensor {d0 (contiguous), d1, d2 = 4 digits, d3}, boxes of 8 x 128 x 4 x 1, no swizzle,
+// zero fill outside (columns beyond 2 nvec)
+bool encode_digits(CUtensorMap *m, void *base, uint64_t d0, uint64_t d1, uint64_t d3) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  cuuint64_t dims[4] = {d0, d1, 4, d3};
+  cuuint64_t strides[3] = {d0 * 2, d0 * d1 * 2, d0 * d1 * 4 * 2};
+  cuuint32_t box[4] = {8, 128, 4, 1};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
+// the 5 x 7-bit digit tables of the mma.sync path (M4 generators in MAGNUS_TENSOR_SLICED), made on
+// first use
+magnus_status ensure_m4_sliced(magnus_plan_t p) {
+  if (p->m4_sliced_ready) return MAGNUS_OK;
+  const size_t kDigits = 5;
+  const int64_t dim = p->dim;
+  const size_t nd = (size_t)dim * p->opt.nvec;
+  for (int k = 0; k < p->nterms; k++)
+    if (p->terms_host[k].kind == MAGNUS_TERM_DENSE) {
+      CUDA_TRY(p, dalloc(&p->hslice[k], kDigits * (size_t)dim * dim));
+      CUDA_TRY(p, dalloc(&p->hexp[k], (size_t)dim));
+      CUDA_TRY(p, launch_slice_dense(p->terms_host[k].rv, p->terms_host[k].rs, dim, p->hslice[k], p->hexp[k], p->stream));
+    }
+  const size_t set = kDigits * 2 * nd;
+  CUDA_TRY(p, dalloc(&p->sl_cur, set));
+  CUDA_TRY(p, dalloc(&p->sl_w0, set));
+  CUDA_TRY(p, dalloc(&p->sl_w1, set));
+  CUDA_TRY(p, dalloc(&p->sl_u, set * p->nterms));
+  CUDA_TRY(p, dalloc(&p->ex_sets, (size_t)128 * (3 + p->nterms)));
+  p->m4_sliced_ready = true;
+  return MAGNUS_OK;
 }
 
 bool is_pow2_dim(int64_t dim, int nspins) {
@@ -148,7 +211,8 @@ void choose_grid(magnus_plan_t p, int *grid, int *gv) {
   *grid = per_vec * nv;
 }
 
-magnus_status run_persistent(magnus_plan_t p, void *psi, int64_t nexp, magnus_stats *stats, bool m6 = false) {
+magnus_status run_persistent(magnus_plan_t p, void *psi, int64_t nexp, magnus_stats *stats, bool m6 = false,
+                             bool m4 = false) {
   int grid, gv;
   size_t need;
   if (p->fam == FAM_DENSE) {
@@ -214,7 +278,33 @@ magnus_status run_persistent(magnus_plan_t p, void *psi, int64_t nexp, magnus_st
   a.sh_w0 = p->sh_w0;
   a.sh_w1 = p->sh_w1;
   a.sh_u = p->sh_u;
-  a.sliced = p->opt.precision == MAGNUS_TENSOR_SLICED;
+  const bool tensor = p->opt.precision == MAGNUS_TENSOR_SLICED;
+  a.sliced = tensor && m4;
+  a.tc = tensor && !m4;
+  if (a.sliced) {
+    magnus_status ms = ensure_m4_sliced(p);
+    if (ms != MAGNUS_OK) return ms;
+  }
+  if (a.tc) {
+    if (p->tc_grid != grid) {  // partial tiles for this grid
+      if (p->tc_P) cudaFree(p->tc_P);
+      p->tc_P = nullptr;
+      p->tc_grid = 0;
+      p->tc_slots = dense_tc_slots(p->tc_ndense, p->dim, grid);
+      CUDA_TRY(p, dalloc(&p->tc_P, (size_t)grid * p->tc_slots * 128 * 128));
+      p->tc_grid = grid;
+    }
+    a.tc_ndense = p->tc_ndense;
+    a.tc_slots = p->tc_slots;
+    a.tc_T = (int)(p->dim / 128);
+    a.tc_N = (long long)p->tc_ndense * a.tc_T * a.tc_T;
+    a.tc_spins = 1ll << 26;
+    for (int k = 0; k < kMaxTerms; k++) a.tc_dslot[k] = p->tc_dslot[k];
+    a.tc_eh = p->tc_eh;
+    a.tc_wd = p->tc_wd;
+    a.tc_ex = p->tc_ex;
+    a.tc_P = p->tc_P;
+  }
   for (int k = 0; k < kMaxTerms; k++) {
     a.hslice[k] = p->hslice[k];
     a.hexp[k] = p->hexp[k];
@@ -233,7 +323,8 @@ magnus_status run_persistent(magnus_plan_t p, void *psi, int64_t nexp, magnus_st
   a.m6 = p->m6;
   CUDA_TRY(p, cudaEventRecord(p->ev0, p->stream));
   if (p->fam == FAM_DENSE)
-    CUDA_TRY(p, launch_dense_persistent(a, p->dense_real, grid, p->stream));
+    CUDA_TRY(p, launch_dense_persistent(a, p->dense_real, grid, a.tc ? &p->tmA : nullptr, a.tc ? &p->tmB : nullptr,
+                                        p->stream));
   else
     CUDA_TRY(p, launch_persistent(a, grid, persistent_block_size(), m6, p->stream));
   CUDA_TRY(p, cudaEventRecord(p->ev1, p->stream));
@@ -494,19 +585,28 @@ magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms
         set_err(p, MAGNUS_EINVAL, "MAGNUS_TENSOR_SLICED needs real-valued dense terms and dim a multiple of 128");
         return fail(MAGNUS_EINVAL);
       }
-      const size_t kDigits = 5;  // bf16 digits per value
+      // tcgen05 path (linear generators): 4 x 8-bit digits of every dense term in one tensor, the
+      // three vector sets in another, both read by TMA
+      int nden = 0;
       for (int k = 0; k < nterms; k++)
-        if (p->terms_host[k].kind == MAGNUS_TERM_DENSE) {
-          PLAN_TRY(dalloc(&p->hslice[k], kDigits * (size_t)dim * dim));
-          PLAN_TRY(dalloc(&p->hexp[k], (size_t)dim));
-          PLAN_TRY(launch_slice_dense(p->terms_host[k].rv, p->terms_host[k].rs, dim, p->hslice[k], p->hexp[k], p->stream));
-        }
-      const size_t set = kDigits * 2 * (size_t)nd;
-      PLAN_TRY(dalloc(&p->sl_cur, set));
-      PLAN_TRY(dalloc(&p->sl_w0, set));
-      PLAN_TRY(dalloc(&p->sl_w1, set));
-      PLAN_TRY(dalloc(&p->sl_u, set * nterms));
-      PLAN_TRY(dalloc(&p->ex_sets, (size_t)128 * (3 + nterms)));
+        if (p->terms_host[k].kind == MAGNUS_TERM_DENSE) p->tc_dslot[k] = nden++;
+      p->tc_ndense = nden;
+      const size_t dd = (size_t)dim * dim;
+      PLAN_TRY(dalloc(&p->tc_hd, (size_t)nden * 4 * dd));
+      PLAN_TRY(dalloc(&p->tc_eh, (size_t)nden * dim));
+      for (int k = 0; k < nterms; k++)
+        if (p->terms_host[k].kind == MAGNUS_TERM_DENSE)
+          PLAN_TRY(launch_slice_dense_tc(p->terms_host[k].rv, p->terms_host[k].rs, dim, p->tc_hd + (size_t)p->tc_dslot[k] * 4 * dd,
+                                         p->tc_eh + (size_t)p->tc_dslot[k] * dim, p->stream));
+      PLAN_TRY(dalloc(&p->tc_wd, (size_t)3 * 4 * 2 * nd));
+      PLAN_TRY(dalloc(&p->tc_ex, (size_t)3 * 128));
+      PLAN_TRY(cudaMemsetAsync(p->tc_wd, 0, sizeof(uint16_t) * 3 * 4 * 2 * nd, p->stream));
+      PLAN_TRY(cudaMemsetAsync(p->tc_ex, 0, sizeof(int) * 3 * 128, p->stream));
+      if (!encode_digits(&p->tmA, p->tc_hd, (uint64_t)dim, (uint64_t)dim, (uint64_t)nden) ||
+          !encode_digits(&p->tmB, p->tc_wd, (uint64_t)dim, (uint64_t)(2 * o.nvec), 3)) {
+        set_err(p, MAGNUS_ECUDA, "cuTensorMapEncodeTiled failed for the digit tensors");
+        return fail(MAGNUS_ECUDA);
+      }
       PLAN_TRY(dalloc(&p->colmax, (size_t)3 * 128));
     }
     if (mf) {
@@ -575,7 +675,7 @@ magnus_status magnus_propagate(magnus_plan_t p, void *psi, double t0, double h, 
   if (variant == MAGNUS_M6 && !p->m6) CUDA_TRY(p, dalloc(&p->m6, (size_t)kM6Slots * p->dim * p->opt.nvec));
   CUDA_TRY(p, launch_exp_setup(variant, t0, h, nsteps, p->nterms, p->coeffs, p->term_ab, p->xi, p->opt.m_max,
                                p->opt.rho_max, p->recs, p->dd, nexp, p->stream));
-  return run_persistent(p, psi, nexp, stats, variant == MAGNUS_M6);
+  return run_persistent(p, psi, nexp, stats, variant == MAGNUS_M6, variant == MAGNUS_M4);
 }
 
 magnus_status leja_expv(magnus_plan_t p, const double *beta, const void *v, void *out, magnus_stats *stats) {

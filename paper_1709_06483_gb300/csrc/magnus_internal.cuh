@@ -167,6 +167,16 @@ struct PersistArgs {
   // and of every vector set a dense matvec reads ([5][2 nvec][D], column exponents), and the
   // rotating column-maximum slots of the slicing passes ([3][128], zero at launch)
   double2 *m6;  // M6 intermediate vectors, kM6Slots x [nvec][dim]
+  // FAM_DENSE with MAGNUS_TENSOR_SLICED on tcgen05 (linear generators): 4 x 8-bit digits
+  int tc;
+  int tc_ndense, tc_slots, tc_T;
+  long long tc_N;
+  long long tc_spins;             // spin budget of every mbarrier wait
+  int tc_dslot[kMaxTerms];        // dense term k -> its index among the dense terms
+  const int *tc_eh;               // row exponents [ndense][dim]
+  void *tc_wd;                    // vector-set digits [3][4][2 nvec][dim] (sets: substep input, w0, w1)
+  int *tc_ex;                     // their column exponents [3][128]
+  double *tc_P;                   // partial product tiles [grid][slots][128][128]
   int sliced;
   const void *hslice[kMaxTerms];
   const int *hexp[kMaxTerms];
@@ -184,7 +194,12 @@ int dense_block_size();
 int dense_rows_per_unit(bool tiled);
 cudaError_t dense_max_blocks_per_sm(int *n);
 // partials must hold 4 * grid * nvec + 4 * nvec doubles
-cudaError_t launch_dense_persistent(const PersistArgs &a, bool real_valued, int grid, cudaStream_t st);
+cudaError_t launch_dense_persistent(const PersistArgs &a, bool real_valued, int grid, const void *tmA, const void *tmB,
+                                    cudaStream_t st);
+// Dense term (real parts Hr[e * rs]) -> 4 x 8-bit digits [4][D][D] at `digits`, row exponents at rexp.
+cudaError_t launch_slice_dense_tc(const double *Hr, int rs, int64_t D, void *digits, int *rexp, cudaStream_t st);
+size_t dense_tc_smem_bytes();
+int dense_tc_slots(int ndense, int64_t D, int grid);
 
 // Dense term (complex128, real parts used) -> bf16 digits [5][D][D] and row exponents [D].
 cudaError_t launch_slice_dense(const double *Hr, int rs, int64_t D, void *digits, int *rexp, cudaStream_t st);
