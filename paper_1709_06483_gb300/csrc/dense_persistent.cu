@@ -365,8 +365,7 @@ __device__ __forceinline__ int cover_exponent(double m) {
 // PREC: 0 FP64, 1 FP32 split, 2 sliced digits on mma.sync (5 x 7 bits), 3 sliced digits on tcgen05
 // (4 x 8 bits, linear generators; the product phase of dense_tc.cuh).
 template <bool REAL, bool TILED, int PREC>
-__global__ void __launch_bounds__(kDBlock, 1)
-    k_dense_persistent(PersistArgs a, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB) {
+__global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) {
   constexpr bool SPLIT = PREC == 1;
   constexpr bool SLICED = PREC == 2;
   constexpr bool TC = PREC == 3;
@@ -509,8 +508,8 @@ __global__ void __launch_bounds__(kDBlock, 1)
       for (int64_t r = lo + tid; r < hi; r += blockDim.x) {
         const double2 x = X[(int64_t)v * D + r];
         if (TC) {
-          tcg::slice_value(x.x, s_cexp[2 * v], dg + (size_t)(2 * v) * D + r, stride);
-          tcg::slice_value(x.y, s_cexp[2 * v + 1], dg + (size_t)(2 * v + 1) * D + r, stride);
+          tcg::slice_value_tiled(x.x, s_cexp[2 * v], dg, D, 2 * v, r);
+          tcg::slice_value_tiled(x.y, s_cexp[2 * v + 1], dg, D, 2 * v + 1, r);
         } else {
           slice_value(x.x, s_cexp[2 * v], dg + (size_t)(2 * v) * D + r, stride);
           slice_value(x.y, s_cexp[2 * v + 1], dg + (size_t)(2 * v + 1) * D + r, stride);
@@ -523,7 +522,7 @@ __global__ void __launch_bounds__(kDBlock, 1)
   };
 
   // tcgen05 path: vector set s of the digit buffer and its column exponents
-  auto tc_set_digits = [&](int set) { return (void *)((__nv_bfloat16 *)a.tc_wd + (size_t)set * tcg::kSl * 2 * nv * D); };
+  auto tc_set_digits = [&](int set) { return (void *)((__nv_bfloat16 *)a.tc_wd + (size_t)set * tcg::kSl * tcg::kN * D); };
   auto tc_set_exps = [&](int set) { return a.tc_ex + set * kTcCols; };
   // y += coef (H_k W)[rows of this 32-row tile] from the partial tiles of the last product phase
   auto tc_term = [&](int k, double coef, int64_t r0, double2 (&y)[2][4]) {
@@ -677,8 +676,8 @@ __global__ void __launch_bounds__(kDBlock, 1)
         if (TC) {  // all dense products of this iteration on the tensor cores, then a barrier
           if (R.mode != MODE_LINEAR) { fail(MAGNUS_EINVAL); return; }
           const int set = (j == 1) ? 0 : (((j - 2) & 1) ? 2 : 1);
-          if (!tcg::gemm_phase(&tmA, &tmB, set, tc_geom, a.tc_eh, tc_set_exps(set), a.tc_P, dsm, tc_bars, tc_pipe,
-                               a.tc_spins)) {
+          if (!tcg::gemm_phase((const __nv_bfloat16 *)a.tc_hd, (const __nv_bfloat16 *)tc_set_digits(set), tc_geom,
+                               a.tc_eh, tc_set_exps(set), a.tc_P, dsm, tc_bars, tc_pipe, a.tc_spins)) {
             fail(MAGNUS_ETIMEOUT);
             return;
           }
@@ -961,7 +960,7 @@ __global__ void k_slice_dense_tc(const double *Hr, int rs, int64_t D, __nv_bfloa
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(kFull, m, o));
     const int e = tcg::cover_exponent(m);
     if (lane == 0) rexp[r] = e;
-    for (int64_t c = lane; c < D; c += 32) tcg::slice_value(Hr[(r * D + c) * rs], e, digits + r * D + c, (size_t)D * D);
+    for (int64_t c = lane; c < D; c += 32) tcg::slice_value_tiled(Hr[(r * D + c) * rs], e, digits, D, r, c);
   }
 }
 }  // namespace
@@ -1005,13 +1004,9 @@ cudaError_t dense_max_blocks_per_sm(int *n) {
   return cudaSuccess;
 }
 
-cudaError_t launch_dense_persistent(const PersistArgs &a, bool real_valued, int grid, const void *tmA, const void *tmB,
-                                    cudaStream_t st) {
+cudaError_t launch_dense_persistent(const PersistArgs &a, bool real_valued, int grid, cudaStream_t st) {
   PersistArgs copy = a;
-  CUtensorMap ma{}, mb{};
-  if (tmA) ma = *(const CUtensorMap *)tmA;
-  if (tmB) mb = *(const CUtensorMap *)tmB;
-  void *args[] = {&copy, &ma, &mb};
+  void *args[] = {&copy};
   const int prec = a.tc ? 3 : (a.sliced ? 2 : (a.split ? 1 : 0));
   if (prec >= 2) {
     cudaError_t e = sliced_attr();

@@ -16,12 +16,17 @@
 // Work split: the items (dense term, 128-row tile, K chunk) in that order are cut into G contiguous
 // ranges, one per CTA; a CTA accumulates consecutive chunks of the same tile and writes one FP64
 // partial tile per (tile it touched) into its own slots; the caller sums the partials of a tile in
-// CTA order after a grid barrier (deterministic).  Operands arrive by TMA (4-D tiled loads, one box
-// = 8 K x 128 rows x 4 digits, no swizzle) into a 3-deep ring of 64 KB stages; one thread issues the
-// loads and the MMAs, all 8 warps move the accumulators out of tensor memory.
+// CTA order after a grid barrier (deterministic).
+//
+// Layout: the digits live in global memory already in the order the MMA reads them from shared
+// memory (K-major, no swizzle, core matrices of 8 rows x 16 B): a block of 8 K values is
+// [4 digits][128 rows][8] bf16 = 8 KB, and the blocks of consecutive K follow each other, so
+//   H digits: [term][row tile][D / 8 K-blocks][4][128][8],   vector digits: [set][D / 8][4][128][8]
+// and one pipeline stage (32 K) of either operand is one contiguous 32 KB bulk copy (TMA bulk
+// engine, cp.async.bulk) into a 3-deep ring of 64 KB stages.  One thread issues the copies and the
+// MMAs; all 8 warps move the accumulators out of tensor memory.
 #pragma once
 
-#include <cuda.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -69,6 +74,11 @@ struct Geometry {
 
 __host__ __device__ inline long long range_lo(long long b, int G, long long N) { return b * N / G; }
 
+// element offset of digit t of element (row r, K index j) in the tiled layout with K extent D
+__host__ __device__ inline size_t tiled_offset(int64_t D, int64_t r, int64_t j, int t) {
+  return ((((size_t)(r / kM) * (size_t)(D / 8) + (size_t)(j / 8)) * kSl + t) * kM + (size_t)(r % kM)) * 8 + (size_t)(j % 8);
+}
+
 // one value -> 4 digits of 8 bits with exponent e (|x| < 2^e); exact FP64 steps
 __device__ __forceinline__ void slice_value(double x, int e, __nv_bfloat16 *out, size_t stride) {
   double a = ldexp(x, -e);
@@ -81,18 +91,30 @@ __device__ __forceinline__ void slice_value(double x, int e, __nv_bfloat16 *out,
   }
 }
 
+// the same digits written to the tiled layout (row r = tile row or vector column, K index j)
+__device__ __forceinline__ void slice_value_tiled(double x, int e, __nv_bfloat16 *base, int64_t D, int64_t r, int64_t j) {
+  double a = ldexp(x, -e);
+#pragma unroll
+  for (int t = 1; t <= kSl; t++) {
+    const double sc = ldexp(1.0, 8 * t);
+    const double q = rint(a * sc);
+    base[tiled_offset(D, r, j, t - 1)] = __float2bfloat16_rn((float)q);
+    a = fma(-q, 1.0 / sc, a);
+  }
+}
+
 __device__ __forceinline__ int cover_exponent(double m) {
   int e = 0;
   if (m > 0.0) frexp(m, &e);
   return e;
 }
 
-// Y_k = H_k W for the set `set` of the B map, this CTA's range.  P: partial tiles
-// [G][slots][kN cols][kM rows] (FP64, column-major in the tile); eh: row exponents [ndense][D];
-// ec: column exponents of the set [kN].  smem: kSmemBytes of dynamic shared memory.  Returns false
-// if a bounded wait ran out (the caller reports MAGNUS_ETIMEOUT).
-__device__ bool gemm_phase(const CUtensorMap *tmA, const CUtensorMap *tmB, int set, const Geometry &g,
-                           const int *eh, const int *ec, double *P, unsigned char *smem_raw, Bars &bars, Pipe &pipe,
+// Y_k = H_k W for the vector digits wd (tiled, one set), this CTA's range.  hd: tiled digits of all
+// dense terms; P: partial tiles [G][slots][kN cols][kM rows] (FP64, column-major in the tile); eh:
+// row exponents [ndense][D]; ec: column exponents of the set [kN].  smem: kSmemBytes of dynamic
+// shared memory.  Returns false if a bounded wait ran out (the caller reports MAGNUS_ETIMEOUT).
+__device__ bool gemm_phase(const __nv_bfloat16 *hd, const __nv_bfloat16 *wd, const Geometry &g, const int *eh,
+                           const int *ec, double *P, unsigned char *smem_raw, Bars &bars, Pipe &pipe,
                            long long max_spins) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int b = blockIdx.x, G = gridDim.x;
@@ -120,15 +142,14 @@ __device__ bool gemm_phase(const CUtensorMap *tmA, const CUtensorMap *tmB, int s
     const int buf = (int)(gs % kNS);
     const long long item = i0 + j / kStagesPerChunk;
     const long long tile = item / g.C;
-    const int k0 = (int)(item % g.C) * kChunk + (int)(j % kStagesPerChunk) * kKS;
-    const int term = (int)(tile / g.T), r0 = (int)(tile % g.T) * kM;
+    const long long k0 = (item % g.C) * kChunk + (j % kStagesPerChunk) * kKS;
     unsigned char *sa = smem + (size_t)buf * kStageBytes, *sb = sa + kStageA;
+    // tile = term * T + row tile: its K-blocks start at tile * (D / 8) blocks of kBox bytes
+    const unsigned char *ga = (const unsigned char *)hd + ((size_t)tile * (size_t)(D / 8) + (size_t)(k0 / 8)) * kBox;
+    const unsigned char *gb = (const unsigned char *)wd + (size_t)(k0 / 8) * kBox;
     tc::mbar_expect_tx(&bars.full[buf], kStageBytes);
-#pragma unroll
-    for (int c = 0; c < 4; c++) {
-      tc::tma_load_4d(sa + c * kBox, tmA, k0 + 8 * c, r0, 0, term, &bars.full[buf]);
-      tc::tma_load_4d(sb + c * kBox, tmB, k0 + 8 * c, 0, 0, set, &bars.full[buf]);
-    }
+    tc::bulk_load(sa, ga, kStageA, &bars.full[buf]);
+    tc::bulk_load(sb, gb, kStageA, &bars.full[buf]);
   };
 
   // the issuing thread: prologue loads (after making the generic-proxy writes of the digits visible)

@@ -1,8 +1,6 @@
 // Host implementation of the C ABI declared in include/magnus.h.  Argument checking, device
 // allocation, and launching the kernels of setup_kernels.cu and leja_persistent.cu; no part of
 // the method's arithmetic runs on the host.
-#include <cuda.h>
-#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -55,14 +53,13 @@ struct magnus_plan_s {
   unsigned long long *colmax = nullptr;  // [3][128]
   double2 *m6 = nullptr;                 // M6 intermediate vectors [kM6Slots][nvec][dim], on first use
   // MAGNUS_TENSOR_SLICED on tcgen05 (linear generators)
-  uint16_t *tc_hd = nullptr;             // dense-term digits [ndense][4][dim][dim]
+  uint16_t *tc_hd = nullptr;             // dense-term digits, tiled [ndense][dim/128][dim/8][4][128][8]
   int *tc_eh = nullptr;                  // their row exponents [ndense][dim]
-  uint16_t *tc_wd = nullptr;             // vector-set digits [3][4][2 nvec][dim]
+  uint16_t *tc_wd = nullptr;             // vector-set digits, tiled [3][dim/8][4][128][8]
   int *tc_ex = nullptr;                  // column exponents [3][128]
   double *tc_P = nullptr;                // partial tiles [grid][slots][128][128]
   int tc_grid = 0, tc_slots = 0, tc_ndense = 0;
   int tc_dslot[kMaxTerms] = {0, 0, 0, 0};
-  CUtensorMap tmA{}, tmB{};
   bool m4_sliced_ready = false;          // the 5 x 7-bit tables of the M4 path exist
   int lbits = 0;
   double *dlo = nullptr, *dhi = nullptr;
@@ -112,33 +109,6 @@ void free_plan(magnus_plan_t p) {
   if (p->ev0) cudaEventDestroy(p->ev0);
   if (p->ev1) cudaEventDestroy(p->ev1);
   delete p;
-}
-
-// cuTensorMapEncodeTiled from the driver (no link-time dependency on libcuda)
-PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    void *f = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = (PFN_cuTensorMapEncodeTiled_v12000)f;
-  }
-  return fn;
-}
-
-// 4-D bf16 digit tensor {d0 (contiguous), d1, d2 = 4 digits, d3}, boxes of 8 x 128 x 4 x 1, no swizzle,
-// zero fill outside (columns beyond 2 nvec)
-bool encode_digits(CUtensorMap *m, void *base, uint64_t d0, uint64_t d1, uint64_t d3) {
-  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-  if (!enc) return false;
-  cuuint64_t dims[4] = {d0, d1, 4, d3};
-  cuuint64_t strides[3] = {d0 * 2, d0 * d1 * 2, d0 * d1 * 4 * 2};
-  cuuint32_t box[4] = {8, 128, 4, 1};
-  cuuint32_t es[4] = {1, 1, 1, 1};
-  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
-         CUDA_SUCCESS;
 }
 
 // the 5 x 7-bit digit tables of the mma.sync path (M4 generators in MAGNUS_TENSOR_SLICED), made on
@@ -300,6 +270,7 @@ magnus_status run_persistent(magnus_plan_t p, void *psi, int64_t nexp, magnus_st
     a.tc_N = (long long)p->tc_ndense * a.tc_T * a.tc_T;
     a.tc_spins = 1ll << 26;
     for (int k = 0; k < kMaxTerms; k++) a.tc_dslot[k] = p->tc_dslot[k];
+    a.tc_hd = p->tc_hd;
     a.tc_eh = p->tc_eh;
     a.tc_wd = p->tc_wd;
     a.tc_ex = p->tc_ex;
@@ -323,8 +294,7 @@ magnus_status run_persistent(magnus_plan_t p, void *psi, int64_t nexp, magnus_st
   a.m6 = p->m6;
   CUDA_TRY(p, cudaEventRecord(p->ev0, p->stream));
   if (p->fam == FAM_DENSE)
-    CUDA_TRY(p, launch_dense_persistent(a, p->dense_real, grid, a.tc ? &p->tmA : nullptr, a.tc ? &p->tmB : nullptr,
-                                        p->stream));
+    CUDA_TRY(p, launch_dense_persistent(a, p->dense_real, grid, p->stream));
   else
     CUDA_TRY(p, launch_persistent(a, grid, persistent_block_size(), m6, p->stream));
   CUDA_TRY(p, cudaEventRecord(p->ev1, p->stream));
@@ -585,8 +555,8 @@ magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms
         set_err(p, MAGNUS_EINVAL, "MAGNUS_TENSOR_SLICED needs real-valued dense terms and dim a multiple of 128");
         return fail(MAGNUS_EINVAL);
       }
-      // tcgen05 path (linear generators): 4 x 8-bit digits of every dense term in one tensor, the
-      // three vector sets in another, both read by TMA
+      // tcgen05 path (linear generators): 4 x 8-bit digits of every dense term and of the three
+      // vector sets, tiled in the order the tensor cores read them (columns beyond 2 nvec stay zero)
       int nden = 0;
       for (int k = 0; k < nterms; k++)
         if (p->terms_host[k].kind == MAGNUS_TERM_DENSE) p->tc_dslot[k] = nden++;
@@ -598,15 +568,11 @@ magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms
         if (p->terms_host[k].kind == MAGNUS_TERM_DENSE)
           PLAN_TRY(launch_slice_dense_tc(p->terms_host[k].rv, p->terms_host[k].rs, dim, p->tc_hd + (size_t)p->tc_dslot[k] * 4 * dd,
                                          p->tc_eh + (size_t)p->tc_dslot[k] * dim, p->stream));
-      PLAN_TRY(dalloc(&p->tc_wd, (size_t)3 * 4 * 2 * nd));
+      const size_t wset = (size_t)4 * 128 * dim;
+      PLAN_TRY(dalloc(&p->tc_wd, 3 * wset));
       PLAN_TRY(dalloc(&p->tc_ex, (size_t)3 * 128));
-      PLAN_TRY(cudaMemsetAsync(p->tc_wd, 0, sizeof(uint16_t) * 3 * 4 * 2 * nd, p->stream));
+      PLAN_TRY(cudaMemsetAsync(p->tc_wd, 0, sizeof(uint16_t) * 3 * wset, p->stream));
       PLAN_TRY(cudaMemsetAsync(p->tc_ex, 0, sizeof(int) * 3 * 128, p->stream));
-      if (!encode_digits(&p->tmA, p->tc_hd, (uint64_t)dim, (uint64_t)dim, (uint64_t)nden) ||
-          !encode_digits(&p->tmB, p->tc_wd, (uint64_t)dim, (uint64_t)(2 * o.nvec), 3)) {
-        set_err(p, MAGNUS_ECUDA, "cuTensorMapEncodeTiled failed for the digit tensors");
-        return fail(MAGNUS_ECUDA);
-      }
       PLAN_TRY(dalloc(&p->colmax, (size_t)3 * 128));
     }
     if (mf) {

@@ -173,8 +173,9 @@ struct PersistArgs {
   long long tc_N;
   long long tc_spins;             // spin budget of every mbarrier wait
   int tc_dslot[kMaxTerms];        // dense term k -> its index among the dense terms
+  const void *tc_hd;              // dense-term digits, tiled [ndense][dim/128][dim/8][4][128][8]
   const int *tc_eh;               // row exponents [ndense][dim]
-  void *tc_wd;                    // vector-set digits [3][4][2 nvec][dim] (sets: substep input, w0, w1)
+  void *tc_wd;                    // vector-set digits, tiled [3][dim/8][4][128][8] (sets: substep input, w0, w1)
   int *tc_ex;                     // their column exponents [3][128]
   double *tc_P;                   // partial product tiles [grid][slots][128][128]
   int sliced;
@@ -194,9 +195,9 @@ int dense_block_size();
 int dense_rows_per_unit(bool tiled);
 cudaError_t dense_max_blocks_per_sm(int *n);
 // partials must hold 4 * grid * nvec + 4 * nvec doubles
-cudaError_t launch_dense_persistent(const PersistArgs &a, bool real_valued, int grid, const void *tmA, const void *tmB,
-                                    cudaStream_t st);
-// Dense term (real parts Hr[e * rs]) -> 4 x 8-bit digits [4][D][D] at `digits`, row exponents at rexp.
+cudaError_t launch_dense_persistent(const PersistArgs &a, bool real_valued, int grid, cudaStream_t st);
+// Dense term (real parts Hr[e * rs]) -> 4 x 8-bit digits in the tiled layout at `digits`, row
+// exponents at rexp.
 cudaError_t launch_slice_dense_tc(const double *Hr, int rs, int64_t D, void *digits, int *rexp, cudaStream_t st);
 size_t dense_tc_smem_bytes();
 int dense_tc_slots(int ndense, int64_t D, int grid);

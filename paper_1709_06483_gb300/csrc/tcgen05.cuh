@@ -1,10 +1,9 @@
-// Inline-PTX wrappers for the Blackwell (sm_100 family) tensor-core path: mbarriers, TMA tiled
-// loads (cp.async.bulk.tensor), tensor-memory allocation, tcgen05.mma (kind::f16: bf16 operands,
+// Inline-PTX wrappers for the Blackwell (sm_100 family) tensor-core path: mbarriers, TMA bulk
+// copies (cp.async.bulk), tensor-memory allocation, tcgen05.mma (kind::f16: bf16 operands,
 // FP32 accumulators in TMEM) and tcgen05.ld.  Every wait is bounded by a spin count; a wait that
 // runs out returns false so that the caller can report an error instead of hanging.
 #pragma once
 
-#include <cuda.h>
 #include <stdint.h>
 
 namespace mg {
@@ -38,19 +37,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long l
   return false;
 }
 
-// 4-D tiled TMA load of one box into shared memory, completion counted on `bar` (bytes)
-__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int x, int y, int z, int w,
-                                            uint64_t *bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
-      "[%6];" ::"r"(smem_u32(dst)),
-      "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
-      : "memory");
+// bulk copy of `bytes` contiguous bytes (16-byte aligned, a multiple of 16) into shared memory,
+// completion counted on `bar`
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"((uint64_t)src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
 }
 
-// ncols columns of tensor memory, address written to dst_smem; one whole warp executes it.  The CTA
-// keeps its permit to allocate (it allocates and frees tensor memory once per product phase, and an
-// allocation after tcgen05.relinquish_alloc_permit is illegal).
 __device__ __forceinline__ void tmem_alloc(uint32_t *dst_smem, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
                "r"(ncols)
