@@ -402,7 +402,8 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
   if (TC) {
     tc_geom.ndense = a.tc_ndense;
     tc_geom.T = a.tc_T;
-    tc_geom.C = a.tc_T;
+    tc_geom.chunk = (D % tcg::kChunkMax == 0) ? tcg::kChunkMax : tcg::kM;
+    tc_geom.C = (int)(D / tc_geom.chunk);
     tc_geom.N = a.tc_N;
     tc_geom.slots = a.tc_slots;
     if (tid == 0) {
@@ -485,12 +486,25 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
     unsigned long long *cm = a.colmax + (size_t)(slice_ev % 3u) * kTcCols;
     for (int c = tid; c < kTcCols; c += blockDim.x) s_cmax[c] = 0ull;
     __syncthreads();
-    for (int v = 0; v < nv; v++)
+    // this block's column maxima: per thread, then per warp (64-bit integer max of the bits of |x|,
+    // which orders like |x|), one shared atomic per warp and column
+    for (int v = 0; v < nv; v++) {
+      unsigned long long m0 = 0ull, m1 = 0ull;
       for (int64_t r = lo + tid; r < hi; r += blockDim.x) {
         const double2 x = X[(int64_t)v * D + r];
-        atomicMax(&s_cmax[2 * v], (unsigned long long)__double_as_longlong(fabs(x.x)));
-        atomicMax(&s_cmax[2 * v + 1], (unsigned long long)__double_as_longlong(fabs(x.y)));
+        m0 = max(m0, (unsigned long long)__double_as_longlong(fabs(x.x)));
+        m1 = max(m1, (unsigned long long)__double_as_longlong(fabs(x.y)));
       }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        m0 = max(m0, __shfl_xor_sync(kFull, m0, o));
+        m1 = max(m1, __shfl_xor_sync(kFull, m1, o));
+      }
+      if (lane == 0 && (m0 | m1)) {
+        atomicMax(&s_cmax[2 * v], m0);
+        atomicMax(&s_cmax[2 * v + 1], m1);
+      }
+    }
     __syncthreads();
     for (int c = tid; c < 2 * nv; c += blockDim.x)
       if (s_cmax[c]) atomicMax(&cm[c], s_cmax[c]);
@@ -503,18 +517,31 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
       for (int c = tid; c < kTcCols; c += blockDim.x) a.colmax[(size_t)((slice_ev + 2) % 3u) * kTcCols + c] = 0ull;
     __syncthreads();
     __nv_bfloat16 *dg = (__nv_bfloat16 *)digits;
-    const size_t stride = (size_t)2 * nv * D;
-    for (int v = 0; v < nv; v++)
-      for (int64_t r = lo + tid; r < hi; r += blockDim.x) {
-        const double2 x = X[(int64_t)v * D + r];
-        if (TC) {
-          tcg::slice_value_tiled(x.x, s_cexp[2 * v], dg, D, 2 * v, r);
-          tcg::slice_value_tiled(x.y, s_cexp[2 * v + 1], dg, D, 2 * v + 1, r);
-        } else {
+    if (TC) {
+      // one work item = one column and 8 consecutive rows (this block's rows come in whole
+      // 32-row tiles): the digits of the 8 values go out as four 16-byte stores
+      const int ncol = 2 * nv;
+      const int64_t ngroups = (hi - lo) / 8;
+      for (int64_t w = tid; w < ngroups * ncol; w += blockDim.x) {
+        const int c = (int)(w % ncol), v = c >> 1;
+        const int64_t r0 = lo + 8 * (w / ncol);
+        double xv[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+          const double2 x = X[(int64_t)v * D + r0 + i];
+          xv[i] = (c & 1) ? x.y : x.x;
+        }
+        tcg::slice8_tiled(xv, s_cexp[c], dg, D, c, r0);
+      }
+    } else {
+      const size_t stride = (size_t)2 * nv * D;
+      for (int v = 0; v < nv; v++)
+        for (int64_t r = lo + tid; r < hi; r += blockDim.x) {
+          const double2 x = X[(int64_t)v * D + r];
           slice_value(x.x, s_cexp[2 * v], dg + (size_t)(2 * v) * D + r, stride);
           slice_value(x.y, s_cexp[2 * v + 1], dg + (size_t)(2 * v + 1) * D + r, stride);
         }
-      }
+    }
     // the digits are read next by TMA (async proxy) in other CTAs
     if (TC) asm volatile("fence.proxy.async.global;" ::: "memory");
     slice_ev++;
@@ -534,20 +561,25 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
       const int rr = (int)(r % tcg::kM);
       int bf, bl;
       tcg::tile_owners(tile, tc_geom, (int)G, &bf, &bl);
+      double sx[4] = {0.0, 0.0, 0.0, 0.0}, sy[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int bb = bf; bb <= bl; bb++) {  // the CTAs holding chunks of this tile, in order
+        const long long b_lo = tcg::range_lo(bb, (int)G, tc_geom.N);
+        if (b_lo == tcg::range_lo(bb + 1, (int)G, tc_geom.N)) continue;
+        const double *Pt = a.tc_P + ((size_t)bb * tc_geom.slots + (size_t)(tile - b_lo / tc_geom.C)) *
+                                        (size_t)(tcg::kN * tcg::kM) + rr;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          const int v = tx + 16 * q;
+          if (v < nv) {
+            sx[q] += Pt[(size_t)(2 * v) * tcg::kM];
+            sy[q] += Pt[(size_t)(2 * v + 1) * tcg::kM];
+          }
+        }
+      }
 #pragma unroll
       for (int q = 0; q < 4; q++) {
-        const int v = tx + 16 * q;
-        if (v >= nv) continue;
-        double sx = 0.0, sy = 0.0;
-        for (int bb = bf; bb <= bl; bb++) {
-          if (tcg::range_lo(bb, (int)G, tc_geom.N) == tcg::range_lo(bb + 1, (int)G, tc_geom.N)) continue;
-          const double *Pt =
-              a.tc_P + ((size_t)bb * tc_geom.slots + tcg::tile_slot(tile, bb, tc_geom, (int)G)) * (size_t)(tcg::kN * tcg::kM);
-          sx += Pt[(size_t)(2 * v) * tcg::kM + rr];
-          sy += Pt[(size_t)(2 * v + 1) * tcg::kM + rr];
-        }
-        y[i][q].x = fma(coef, sx, y[i][q].x);
-        y[i][q].y = fma(coef, sy, y[i][q].y);
+        y[i][q].x = fma(coef, sx[q], y[i][q].x);
+        y[i][q].y = fma(coef, sy[q], y[i][q].y);
       }
     }
   };
@@ -973,11 +1005,12 @@ cudaError_t launch_slice_dense_tc(const double *Hr, int rs, int64_t D, void *dig
 size_t dense_tc_smem_bytes() { return tcg::kSmemBytes; }
 
 int dense_tc_slots(int ndense, int64_t D, int grid) {
-  const long long T = D / tcg::kM, N = (long long)ndense * T * T;
+  const long long T = D / tcg::kM, C = D / ((D % tcg::kChunkMax == 0) ? tcg::kChunkMax : tcg::kM);
+  const long long N = (long long)ndense * T * C;
   int slots = 1;
   for (int b = 0; b < grid; b++) {
     const long long i0 = tcg::range_lo(b, grid, N), i1 = tcg::range_lo(b + 1, grid, N);
-    if (i0 < i1) slots = std::max(slots, (int)((i1 - 1) / T - i0 / T + 1));
+    if (i0 < i1) slots = std::max(slots, (int)((i1 - 1) / C - i0 / C + 1));
   }
   return slots;
 }

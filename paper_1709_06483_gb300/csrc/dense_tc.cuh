@@ -5,9 +5,10 @@
 // |h_0|, |w_0| <= 256, the other digits <= 128, all exact in bf16.  The digit products of level
 // g = t + u <= 3 (10 of the 16 pairs) are summed by tcgen05.mma (kind::f16) into four FP32
 // accumulators in tensor memory, one 128 x 128 tile each (all 512 TMEM columns):
-//   * levels 0 and 1 restart every 128-column chunk of K; there every partial sum is an integer of
-//     magnitude below 2^24 (per K index at most 2^16 + 2^15), so FP32 holds it exactly, and the
-//     chunk sums are moved to int64 (S = 2^8 L_0 + L_1) after each chunk;
+//   * levels 0 and 1 restart every chunk of 256 K values (128 if D is not a multiple of 256); per K
+//     index |h_0 w_0| <= 2^16 and |h_0 w_1 + h_1 w_0| <= 2^16, so every partial sum is an integer
+//     of magnitude at most 2^24, which FP32 holds exactly; the chunk sums are moved to int64
+//     (S = 2^8 L_0 + L_1) after each chunk;
 //   * levels 2 and 3 (weights 2^-16 and 2^-24 of level 0) accumulate in FP32 over the whole range;
 //     their rounding is below 2^-40 of the product scale.
 // The value is Y[r][c] = 2^{e_r + e_c - 24} (S + (L_2 + L_3 2^-8) 2^-8).  The truncation after four
@@ -39,8 +40,7 @@ constexpr int kSl = 4;                          // digits per value
 constexpr int kM = 128;                         // rows per tile (MMA M)
 constexpr int kN = 128;                         // columns (MMA N)
 constexpr int kKS = 32;                         // K per pipeline stage
-constexpr int kChunk = 128;                     // K per exact chunk
-constexpr int kStagesPerChunk = kChunk / kKS;   // 4
+constexpr int kChunkMax = 256;                  // K per exact chunk (256, or 128 when D is not a multiple of 256)
 constexpr int kNS = 3;                          // ring depth
 constexpr uint32_t kBox = 8 * kM * kSl * 2;     // 8 KB: one TMA box (8 K x 128 rows x 4 digits)
 constexpr uint32_t kStageA = 4 * kBox;          // 32 KB: the 4 K-cores of a stage
@@ -48,6 +48,7 @@ constexpr uint32_t kStageBytes = 2 * kStageA;   // A and B
 constexpr size_t kSmemBytes = (size_t)kNS * kStageBytes + 1024;  // + alignment slack
 constexpr uint32_t kTmemCols = 512;             // 4 levels x 128 columns
 constexpr uint32_t kIdesc = tc::idesc_bf16(kM, kN);
+constexpr uint32_t kIdesc2 = tc::idesc_bf16(kM, 2 * kN);  // two adjacent levels at once
 constexpr int kThreads = 256;                   // 8 warps: lane quadrant = warp % 4, column half = warp / 4
 
 struct Bars {
@@ -67,40 +68,75 @@ struct Pipe {
 struct Geometry {
   int ndense;       // dense terms
   int T;            // row tiles (D / 128)
-  int C;            // chunks per tile (D / 128)
+  int C;            // chunks per tile (D / chunk)
+  int chunk;        // K per chunk (256 or 128)
   long long N;      // items = ndense * T * C
   int slots;        // partial tiles per CTA
 };
 
-__host__ __device__ inline long long range_lo(long long b, int G, long long N) { return b * N / G; }
+// first item of CTA b's range (32-bit division when the product fits, the common case)
+__host__ __device__ inline long long range_lo(long long b, int G, long long N) {
+  const long long p = b * N;
+  return p < 2147483647ll ? (long long)((unsigned)p / (unsigned)G) : p / G;
+}
 
 // element offset of digit t of element (row r, K index j) in the tiled layout with K extent D
 __host__ __device__ inline size_t tiled_offset(int64_t D, int64_t r, int64_t j, int t) {
   return ((((size_t)(r / kM) * (size_t)(D / 8) + (size_t)(j / 8)) * kSl + t) * kM + (size_t)(r % kM)) * 8 + (size_t)(j % 8);
 }
 
-// one value -> 4 digits of 8 bits with exponent e (|x| < 2^e); exact FP64 steps
-__device__ __forceinline__ void slice_value(double x, int e, __nv_bfloat16 *out, size_t stride) {
-  double a = ldexp(x, -e);
-#pragma unroll
-  for (int t = 1; t <= kSl; t++) {
-    const double sc = ldexp(1.0, 8 * t);
-    const double q = rint(a * sc);
-    out[(t - 1) * stride] = __float2bfloat16_rn((float)q);
-    a = fma(-q, 1.0 / sc, a);
-  }
+// x (finite, |x| < 2^e) -> N = round(x 2^{32 - e}), |N| <= 2^32, from the bits of x (integer pipe
+// only: on this part the FP64 pipe is the scarce one)
+__device__ __forceinline__ long long fixed32(double x, int e) {
+  const long long bits = __double_as_longlong(x);
+  const int ex = (int)((bits >> 52) & 0x7FF);
+  if (ex == 0) return 0;                            // zero (or subnormal: below 2^-1022 <= 2^{e-32} here)
+  const long long mant = (bits & 0xFFFFFFFFFFFFFll) | 0x10000000000000ll;
+  const int sh = e + 1043 - ex;                     // x 2^{32-e} = mant 2^{-sh}; sh >= 21 as |x| < 2^e
+  long long n = sh >= 63 ? 0 : ((mant >> (sh - 1)) + 1) >> 1;  // round half up in magnitude
+  return bits < 0 ? -n : n;
 }
 
-// the same digits written to the tiled layout (row r = tile row or vector column, K index j)
+// N -> 4 balanced base-256 digits d_t (N = sum_t d_t 2^{8(3-t)}, |d_0| <= 256, |d_t| <= 128)
+__device__ __forceinline__ void digits4(long long n, int (&d)[kSl]) {
+  d[0] = (int)((n + (1ll << 23)) >> 24);
+  n -= (long long)d[0] << 24;
+  d[1] = (int)((n + (1ll << 15)) >> 16);
+  n -= (long long)d[1] << 16;
+  d[2] = (int)((n + (1ll << 7)) >> 8);
+  d[3] = (int)(n - ((long long)d[2] << 8));
+}
+
+// one value -> 4 digits of 8 bits with exponent e (|x| < 2^e), written to the tiled layout
+// (row r = tile row or vector column, K index j): x 2^-e = sum_t d_t 2^{-8(t+1)} + O(2^-33)
 __device__ __forceinline__ void slice_value_tiled(double x, int e, __nv_bfloat16 *base, int64_t D, int64_t r, int64_t j) {
-  double a = ldexp(x, -e);
+  int d[kSl];
+  digits4(fixed32(x, e), d);
 #pragma unroll
-  for (int t = 1; t <= kSl; t++) {
-    const double sc = ldexp(1.0, 8 * t);
-    const double q = rint(a * sc);
-    base[tiled_offset(D, r, j, t - 1)] = __float2bfloat16_rn((float)q);
-    a = fma(-q, 1.0 / sc, a);
+  for (int t = 0; t < kSl; t++) base[tiled_offset(D, r, j, t)] = __int2bfloat16_rn(d[t]);
+}
+
+// digits of 8 consecutive K values (j0 % 8 == 0) of one row/column r, packed: four 16-byte stores
+// into the tiled layout (digit t of the 8 values is one 16-byte piece)
+__device__ __forceinline__ void slice8_tiled(const double (&x)[8], int e, __nv_bfloat16 *base, int64_t D, int64_t r,
+                                             int64_t j0) {
+  uint32_t packed[kSl][4];
+#pragma unroll
+  for (int i = 0; i < 8; i += 2) {
+    int d0[kSl], d1[kSl];
+    digits4(fixed32(x[i], e), d0);
+    digits4(fixed32(x[i + 1], e), d1);
+#pragma unroll
+    for (int t = 0; t < kSl; t++) {
+      const uint32_t lo = __bfloat16_as_ushort(__int2bfloat16_rn(d0[t]));
+      const uint32_t hi = __bfloat16_as_ushort(__int2bfloat16_rn(d1[t]));
+      packed[t][i / 2] = lo | (hi << 16);
+    }
   }
+#pragma unroll
+  for (int t = 0; t < kSl; t++)
+    *reinterpret_cast<uint4 *>(base + tiled_offset(D, r, j0, t)) =
+        make_uint4(packed[t][0], packed[t][1], packed[t][2], packed[t][3]);
 }
 
 __device__ __forceinline__ int cover_exponent(double m) {
@@ -135,14 +171,15 @@ __device__ bool gemm_phase(const __nv_bfloat16 *hd, const __nv_bfloat16 *wd, con
   const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
   long long S[kN / 2];                        // exact levels 0, 1 of this thread's 64 columns
 
-  const long long nstages = (i1 - i0) * kStagesPerChunk;
+  const int spc = g.chunk / kKS;  // stages per chunk
+  const long long nstages = (i1 - i0) * spc;
   // stage j of the range -> item i0 + j / 4, K offset
   auto load_stage = [&](long long j) {
     const uint32_t gs = pipe.stage + (uint32_t)j;
     const int buf = (int)(gs % kNS);
-    const long long item = i0 + j / kStagesPerChunk;
+    const long long item = i0 + j / spc;
     const long long tile = item / g.C;
-    const long long k0 = (item % g.C) * kChunk + (j % kStagesPerChunk) * kKS;
+    const long long k0 = (item % g.C) * g.chunk + (j % spc) * kKS;
     unsigned char *sa = smem + (size_t)buf * kStageBytes, *sb = sa + kStageA;
     // tile = term * T + row tile: its K-blocks start at tile * (D / 8) blocks of kBox bytes
     const unsigned char *ga = (const unsigned char *)hd + ((size_t)tile * (size_t)(D / 8) + (size_t)(k0 / 8)) * kBox;
@@ -162,7 +199,7 @@ __device__ bool gemm_phase(const __nv_bfloat16 *hd, const __nv_bfloat16 *wd, con
     }
   }
 
-  uint32_t fresh = 0xFu;  // levels whose next MMA starts a new sum
+  const uint64_t desc0 = tc::smem_desc(tc::smem_u32(smem), kBox, 128);  // buffer 0, K-block 0, digit 0
   long long j = 0;        // next stage to issue
   int slot = 0;
   for (long long item = i0; item < i1; item++) {
@@ -172,30 +209,38 @@ __device__ bool gemm_phase(const __nv_bfloat16 *hd, const __nv_bfloat16 *wd, con
     if (tile_start) {
 #pragma unroll
       for (int q = 0; q < kN / 2; q++) S[q] = 0;
-      fresh = 0xFu;
     }
-    fresh |= 0x3u;  // levels 0 and 1 restart every chunk
     // ---- issue the chunk's 4 stages (one thread)
     if (tid == 0) {
-      for (int st = 0; st < kStagesPerChunk && ok; st++, j++) {
+      for (int st = 0; st < spc && ok; st++, j++) {
         const uint32_t gs = pipe.stage + (uint32_t)j;
         const int buf = (int)(gs % kNS);
         if (!tc::mbar_wait(&bars.full[buf], (gs / kNS) & 1u, max_spins)) { ok = false; break; }
         tc::fence_after_sync();
-        const uint32_t sa = tc::smem_u32(smem + (size_t)buf * kStageBytes), sb = sa + kStageA;
+        // descriptors differ only in their start-address field (address / 16, 14 bits: every
+        // shared-memory address fits), so each is the stage's base descriptor plus a constant
+        const uint64_t abase = desc0 + ((uint64_t)(buf * kStageBytes) >> 4);
+        const uint64_t bbase = abase + (kStageA >> 4);
+        const uint32_t reset = (st == 0 ? 0x3u : 0u) | ((st == 0 && tile_start) ? 0xCu : 0u);
 #pragma unroll
         for (int ks = 0; ks < kKS / 16; ks++) {
+          // digit t of H against the pair of vector digits (u, u + 1), stacked as one 256-row
+          // operand (digit planes are 2 KB apart, so the pair is contiguous), writes the adjacent
+          // accumulators of levels t + u and t + u + 1 in one N = 256 product; the last pair of
+          // rows t = 1 and t = 3 has a single digit left (N = 128)
+          const uint32_t ko = (uint32_t)(2 * ks) * kBox;
 #pragma unroll
           for (int t = 0; t < kSl; t++)
 #pragma unroll
-            for (int u = 0; u < kSl; u++) {
+            for (int u = 0; u + t <= 3; u += 2) {
               const int lvl = t + u;
-              if (lvl > 3) continue;
-              const uint64_t ad = tc::smem_desc(sa + (uint32_t)(2 * ks) * kBox + (uint32_t)t * 2048u, kBox, 128);
-              const uint64_t bd = tc::smem_desc(sb + (uint32_t)(2 * ks) * kBox + (uint32_t)u * 2048u, kBox, 128);
-              const uint32_t acc = ((fresh >> lvl) & 1u) ? 0u : 1u;
-              fresh &= ~(1u << lvl);
-              tc::mma_bf16(tmem + (uint32_t)lvl * kN, ad, bd, kIdesc, acc);
+              const bool pair = (lvl + 1 <= 3);
+              const uint64_t ad = abase + ((ko + (uint32_t)t * 2048u) >> 4);
+              const uint64_t bd = bbase + ((ko + (uint32_t)u * 2048u) >> 4);
+              // t = 0 opens every level (levels 0, 1 together, 2, 3 together) in the first K step of a
+              // stage where they restart (levels 0, 1 every chunk, 2, 3 every tile)
+              const uint32_t acc = (ks == 0 && t == 0 && ((reset >> lvl) & 1u)) ? 0u : 1u;
+              tc::mma_bf16(tmem + (uint32_t)lvl * kN, ad, bd, pair ? kIdesc2 : kIdesc, acc);
             }
         }
         tc::mma_commit(&bars.empty[buf]);
@@ -244,7 +289,10 @@ __device__ bool gemm_phase(const __nv_bfloat16 *hd, const __nv_bfloat16 *wd, con
         for (int q = 0; q < 16; q++) {
           const int cc = (int)col + q;
           const double lo = ((double)__uint_as_float(v2[q]) + (double)__uint_as_float(v3[q]) * 0x1.0p-8) * 0x1.0p-8;
-          out[(size_t)cc * kM + row] = ldexp((double)S[c16 * 16 + q] + lo, er + ec[cc] - 24);
+          // 2^{e_r + e_c - 24} from its exponent bits when it is a normal number
+          const int bx = er + ec[cc] - 24 + 1023;
+          const double sc = (bx > 0 && bx < 2047) ? __longlong_as_double((long long)bx << 52) : ldexp(1.0, bx - 1023);
+          out[(size_t)cc * kM + row] = fma((double)S[c16 * 16 + q], sc, lo * sc);
         }
       }
       slot++;
