@@ -211,3 +211,31 @@ def test_dense_real_storage(mg, precision, nvec):
     for v in range(nvec):
         ref = P.propagate(c.psi0.reshape(nvec, -1)[v], 0.0, c.h, c.nsteps, "CF4")
         assert rel(out[v], ref) < tol, (v, rel(out[v], ref))
+
+
+@pytest.fixture(scope="module")
+def dense13():
+    """The 13-spin long-range chain (dim 8192, 2 x 1.07 GB complex128 dense terms) and the oracle
+    built from the oracle's own dense matrices."""
+    c = mi.workload3()
+    Ho = oracle.longrange_dense(c.nspins, c.hz, 1.5, c.delta)
+    Hd = oracle.field_x_dense(c.nspins)
+    return c, oracle_dense(c, Ho, Hd)
+
+
+def test_dense13_full_size_tensor_sampled(mg, dense13):
+    """Full size, in the bench's launch configuration (64 states, tcgen05 digit products, Cf4): one
+    step; states 0 and 63 against the oracle (one by one), every state's norm conserved."""
+    c, P = dense13
+    Hs = mg.build_longrange_dense(c.nspins, c.hz, 1.5, c.delta)
+    Hd = mg.build_field_x_dense(c.nspins)
+    plan = mg.Plan(c.dim, [mg.DenseTerm(Hs), mg.DenseTerm(Hd)], drive_pair(mg, c), nvec=64,
+                   precision=mg.TENSOR_SLICED)
+    psi = cuda(c.psi0)
+    plan.propagate(psi, 0.0, c.h, 1, "CF4")
+    out = psi.cpu().numpy()
+    norms = np.linalg.norm(out, axis=1) / np.linalg.norm(c.psi0, axis=1)
+    assert np.max(np.abs(norms - 1.0)) < 1e-9
+    for v in (0, 63):
+        ref = P.propagate(c.psi0[v], 0.0, c.h, 1, "CF4")
+        assert rel(out[v], ref) < 1e-9, (v, rel(out[v], ref))
