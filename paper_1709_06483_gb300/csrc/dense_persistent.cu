@@ -10,9 +10,12 @@
 // Both are FP64-pipe bound on GB300 (2 FP64 FMA/clk/SM): a real-valued H x complex state costs 2
 // FMAs per element and vector.  A matrix-free sum_i sigma^x_i term may be mixed with dense terms.
 //
-// Per-vector stop decisions: each block writes its per-vector partial sums; after a barrier, block
-// v sums vector v's partials over all blocks in a fixed order; after a second barrier every block
-// reads the same totals and takes the same decisions.
+// Per-vector stop decisions: each block writes its per-vector partial sums; after a barrier every
+// block sums each vector's partials over all blocks in the same fixed order, so all blocks hold the
+// same totals and take the same decisions.
+//
+// MAGNUS_TENSOR_SLICED: exact digit products on the tensor cores (dense_tc.cuh on tcgen05 for the
+// linear generators, a warp-level mma.sync digit kernel for M4).
 #include <math.h>
 
 #include <algorithm>
@@ -374,6 +377,7 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
   __shared__ double s_vn[kVecMax], s_ep[kVecMax], s_pn[kVecMax];
   __shared__ int s_act[kVecMax], s_m[kVecMax];
   __shared__ double s_part[kDBlock / 32][kVecMax][2];
+  __shared__ double s_tot[kVecMax][2];  // per-vector totals of the last reduction
   __shared__ int s_flag;
   __shared__ TileSmem TS;
   DenseSmem &S = TS.d;
@@ -418,14 +422,13 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
   }
 
   double *partials = a.partials;                        // [2][G][nv][2]
-  double *totals = a.partials + (size_t)4 * G * nv;     // [2][nv][2]
   unsigned it = 0;
   auto fail = [&](int status) {
     if (tid == 0) atomicCAS(&a.counters->status, 0, status);
   };
 
   // Reduce per-thread per-vector sums (tiled: vectors tx + 16 q; warp-per-row: the lane's own
-  // vector 0) to this block's partials, barrier, per-vector totals by block v, barrier.
+  // vector 0) to this block's partials, barrier, every block sums the partials (into s_tot).
   auto reduce_and_share = [&](double (&sw)[4], double (&sp)[4]) -> bool {
     double *slot = partials + (size_t)(it & 1u) * G * nv * 2;
     if (TILED) {
@@ -458,21 +461,23 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
       }
     }
     if (!grid_barrier(a.bar, G, a.spin_limit_ns)) return false;
-    if (warp == 0)
-      for (int v = b; v < nv; v += G) {  // block b sums the vectors v = b, b + G, ...
-        double y0 = 0.0, y1 = 0.0;
-        for (int q = lane; q < (int)G; q += 32) {
-          y0 += slot[((size_t)q * nv + v) * 2];
-          y1 += slot[((size_t)q * nv + v) * 2 + 1];
-        }
-        y0 = warp_sum(y0);
-        y1 = warp_sum(y1);
-        if (lane == 0) {
-          totals[((it & 1u) * nv + v) * 2] = y0;
-          totals[((it & 1u) * nv + v) * 2 + 1] = y1;
-        }
+    // every block sums every vector's partials itself, in the same fixed order (one warp per
+    // vector): the totals are identical in all blocks and no second barrier is needed
+    for (int v = warp; v < nv; v += kDBlock / 32) {
+      double y0 = 0.0, y1 = 0.0;
+      for (int q = lane; q < (int)G; q += 32) {
+        y0 += slot[((size_t)q * nv + v) * 2];
+        y1 += slot[((size_t)q * nv + v) * 2 + 1];
       }
-    return grid_barrier(a.bar, G, a.spin_limit_ns);
+      y0 = warp_sum(y0);
+      y1 = warp_sum(y1);
+      if (lane == 0) {
+        s_tot[v][0] = y0;
+        s_tot[v][1] = y1;
+      }
+    }
+    __syncthreads();
+    return true;
   };
 
   // y[i][q] = sum_k coef_k (H_k src)[row][vec] (+ field), for this thread's outputs
@@ -653,7 +658,7 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
       sw[0] = warp_sum(sw[0]);
     }
     if (!reduce_and_share(sw, sp)) { fail(MAGNUS_ETIMEOUT); return; }
-    if (tid < nv) s_vn[tid] = sqrt(totals[((it & 1u) * nv + tid) * 2]);
+    if (tid < nv) s_vn[tid] = sqrt(s_tot[tid][0]);
     __syncthreads();
     it++;
   }
@@ -762,11 +767,17 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
         }
         double sw[4] = {0, 0, 0, 0}, sp[4] = {0, 0, 0, 0};
         // epilogue for one output (row r, vector v) with y = the combined matvec
+        // tcgen05 path: column maxima of the new w_j, gathered here for the next slicing pass
+        unsigned long long cmx[4] = {0ull, 0ull, 0ull, 0ull}, cmy[4] = {0ull, 0ull, 0ull, 0ull};
         auto finish = [&](int64_t r, int v, double2 y, int q) {
           const int64_t idx = (int64_t)v * D + r;
           const double2 wr = ldv(src + idx);
           y = rfma(-shift, wr, y);
           dst[idx] = y;
+          if (TC) {
+            cmx[q] = max(cmx[q], (unsigned long long)__double_as_longlong(fabs(y.x)));
+            cmy[q] = max(cmy[q], (unsigned long long)__double_as_longlong(fabs(y.y)));
+          }
           if (SPLIT) dst_sh[idx] = split4(y);
           double2 pr = (j == 1) ? cmul(d0, wr) : nxt[idx];
           pr = cfma(dj, y, pr);
@@ -855,6 +866,27 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
           }
         }
         if (!TILED) sw[0] = warp_sum(sw[0]), sp[0] = warp_sum(sp[0]);
+        if (TC && j < a.m_max) {  // this block's column maxima -> the epilogue slot (published by the next barrier)
+          for (int c = tid; c < kTcCols; c += blockDim.x) s_cmax[c] = 0ull;
+          __syncthreads();
+#pragma unroll
+          for (int q = 0; q < 4; q++) {
+            cmx[q] = max(cmx[q], __shfl_xor_sync(kFull, cmx[q], 16));
+            cmy[q] = max(cmy[q], __shfl_xor_sync(kFull, cmy[q], 16));
+          }
+          if (lane < 16)
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+              const int v = tx + 16 * q;
+              if (v < nv) {
+                if (cmx[q]) atomicMax(&s_cmax[2 * v], cmx[q]);
+                if (cmy[q]) atomicMax(&s_cmax[2 * v + 1], cmy[q]);
+              }
+            }
+          __syncthreads();
+          for (int c = tid; c < 2 * nv; c += blockDim.x)
+            if (s_cmax[c]) atomicMax(&a.colmax[3 * kTcCols + c], s_cmax[c]);
+        }
         if (!reduce_and_share(sw, sp)) { fail(MAGNUS_ETIMEOUT); return; }
         if (warp == 0) {
           int any = 0, bad = 0;
@@ -862,7 +894,7 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
           if (lane == 0)
             for (int v = 0; v < nv; v++) {
               if (!s_act[v]) continue;
-              const double tw = totals[((it & 1u) * nv + v) * 2], tp = totals[((it & 1u) * nv + v) * 2 + 1];
+              const double tw = s_tot[v][0], tp = s_tot[v][1];
               const double ej = adj * sqrt(tw), pn = sqrt(tp);
               if (!isfinite(ej) || !isfinite(pn)) bad = 1;
               if (ej + s_ep[v] <= a.tol_abs + a.tol_rel * pn) {
@@ -879,19 +911,48 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
         __syncthreads();
         it++;
         if (s_flag == 2) { fail(MAGNUS_ENONFINITE); return; }
-        if (s_flag == 1) { done = true; break; }
+        if (s_flag == 1) {
+          // nothing reads the gathered maxima of this iteration: clear them for the next substep
+          if (TC && b == 0)
+            for (int c = tid; c < kTcCols; c += blockDim.x) a.colmax[3 * kTcCols + c] = 0ull;
+          done = true;
+          break;
+        }
         if (SLICED && j < a.m_max) {  // digits of w_j for the next iteration's tensor-core products
           if (!slice_set(dst, ((j - 1) & 1) ? a.sl_w1 : a.sl_w0, ((j - 1) & 1) ? a.ex_w1 : a.ex_w0)) {
             fail(MAGNUS_ETIMEOUT);
             return;
           }
         }
-        if (TC && j < a.m_max) {
+        if (TC && j < a.m_max) {  // digits of w_j from the maxima gathered in the epilogue
           const int set = ((j - 1) & 1) ? 2 : 1;
-          if (!slice_set(dst, tc_set_digits(set), tc_set_exps(set))) {
-            fail(MAGNUS_ETIMEOUT);
-            return;
+          const unsigned long long *cm = a.colmax + 3 * kTcCols;
+          int *exps = tc_set_exps(set);
+          for (int c = tid; c < 2 * nv; c += blockDim.x) {
+            s_cexp[c] = cover_exponent(__longlong_as_double((long long)cm[c]));
+            if (b == 0) exps[c] = s_cexp[c];
           }
+          __syncthreads();
+          __nv_bfloat16 *dg = (__nv_bfloat16 *)tc_set_digits(set);
+          const int ncol = 2 * nv;
+          const int64_t ngroups = (hi - lo) / 8;
+          for (int64_t w = tid; w < ngroups * ncol; w += blockDim.x) {
+            const int c = (int)(w % ncol), v = c >> 1;
+            const int64_t r0 = lo + 8 * (w / ncol);
+            double xv[8];
+#pragma unroll
+            for (int i = 0; i < 8; i++) {
+              const double2 x = dst[(int64_t)v * D + r0 + i];
+              // a vector that stopped keeps its old w: its products are not used, its digits are 0
+              xv[i] = s_act[v] ? ((c & 1) ? x.y : x.x) : 0.0;
+            }
+            tcg::slice8_tiled(xv, s_cexp[c], dg, D, c, r0);
+          }
+          asm volatile("fence.proxy.async.global;" ::: "memory");
+          if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { fail(MAGNUS_ETIMEOUT); return; }
+          // every block has read the gathered maxima: block 0 clears them before its next barrier
+          if (b == 0)
+            for (int c = tid; c < kTcCols; c += blockDim.x) a.colmax[3 * kTcCols + c] = 0ull;
         }
       }
       if (!done) { fail(MAGNUS_ENOCONV); return; }

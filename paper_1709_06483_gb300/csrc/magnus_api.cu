@@ -50,7 +50,7 @@ struct magnus_plan_s {
   int *hexp[kMaxTerms] = {nullptr, nullptr, nullptr, nullptr};
   uint16_t *sl_cur = nullptr, *sl_w0 = nullptr, *sl_w1 = nullptr, *sl_u = nullptr;
   int *ex_sets = nullptr;                // [3 + nterms][128] column exponents
-  unsigned long long *colmax = nullptr;  // [3][128]
+  unsigned long long *colmax = nullptr;  // [4][128]: 3 rotating slicing slots + the epilogue's
   double2 *m6 = nullptr;                 // M6 intermediate vectors [kM6Slots][nvec][dim], on first use
   // MAGNUS_TENSOR_SLICED on tcgen05 (linear generators)
   uint16_t *tc_hd = nullptr;             // dense-term digits, tiled [ndense][dim/128][dim/8][4][128][8]
@@ -212,7 +212,7 @@ magnus_status run_persistent(magnus_plan_t p, void *psi, int64_t nexp, magnus_st
   }
   CUDA_TRY(p, cudaMemsetAsync(p->bar, 0, sizeof(GridBar), p->stream));
   CUDA_TRY(p, cudaMemsetAsync(p->counters, 0, sizeof(Counters), p->stream));
-  if (p->colmax) CUDA_TRY(p, cudaMemsetAsync(p->colmax, 0, sizeof(unsigned long long) * 3 * 128, p->stream));
+  if (p->colmax) CUDA_TRY(p, cudaMemsetAsync(p->colmax, 0, sizeof(unsigned long long) * 4 * 128, p->stream));
   PersistArgs a{};
   a.dim = p->dim;
   a.nvec = p->opt.nvec;
@@ -573,7 +573,7 @@ magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms
       PLAN_TRY(dalloc(&p->tc_ex, (size_t)3 * 128));
       PLAN_TRY(cudaMemsetAsync(p->tc_wd, 0, sizeof(uint16_t) * 3 * wset, p->stream));
       PLAN_TRY(cudaMemsetAsync(p->tc_ex, 0, sizeof(int) * 3 * 128, p->stream));
-      PLAN_TRY(dalloc(&p->colmax, (size_t)3 * 128));
+      PLAN_TRY(dalloc(&p->colmax, (size_t)4 * 128));
     }
     if (mf) {
       const int n = p->terms_host[0].nspins;

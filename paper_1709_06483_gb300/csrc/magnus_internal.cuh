@@ -165,7 +165,8 @@ struct PersistArgs {
   float4 *sh_cur, *sh_w0, *sh_w1, *sh_u;
   // FAM_DENSE with MAGNUS_TENSOR_SLICED: bf16 digits of the dense terms ([5][D][D], row exponents)
   // and of every vector set a dense matvec reads ([5][2 nvec][D], column exponents), and the
-  // rotating column-maximum slots of the slicing passes ([3][128], zero at launch)
+  // column-maximum slots of the slicing passes ([4][128], zero at launch: three rotate, the fourth
+  // collects the maxima the tcgen05 path gathers in its epilogue)
   double2 *m6;  // M6 intermediate vectors, kM6Slots x [nvec][dim]
   // FAM_DENSE with MAGNUS_TENSOR_SLICED on tcgen05 (linear generators): 4 x 8-bit digits
   int tc;
@@ -183,6 +184,8 @@ struct PersistArgs {
   const int *hexp[kMaxTerms];
   void *sl_cur, *sl_w0, *sl_w1, *sl_u;
   int *ex_cur, *ex_w0, *ex_w1, *ex_u;
+  // column-maximum slots of the slicing passes ([4][128], zero at launch): three rotate, the fourth
+  // collects the maxima the tcgen05 path gathers in its epilogue
   unsigned long long *colmax;
 };
 enum { FAM_GENERIC = 0, FAM_CSR = 1, FAM_MF = 2, FAM_DENSE = 3 };
