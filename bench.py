@@ -167,22 +167,26 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
-def kernel_source_hash():
-    """Hash of every source file k_magnus_persistent is compiled from."""
+PERSISTENT_SOURCES = ("leja_persistent.cu", "rows.cuh", "persist_common.cuh", "magnus_internal.cuh")
+DENSE_TC_SOURCES = ("dense_persistent.cu", "dense_tc.cuh", "tcgen05.cuh", "persist_common.cuh", "magnus_internal.cuh")
+
+
+def kernel_source_hash(files=PERSISTENT_SOURCES):
+    """Hash of every source file a kernel is compiled from."""
     h = hashlib.sha256()
-    for f in ("leja_persistent.cu", "rows.cuh", "persist_common.cuh", "magnus_internal.cuh"):
+    for f in files:
         h.update(open(os.path.join(ROOT, "paper_1709_06483_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload_key):
+def profiled_traffic(workload_key, files=PERSISTENT_SOURCES):
     """DRAM bytes per Leja iteration from a committed ncu summary, if it matches this kernel source."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(p)).get(workload_key)
     except (OSError, ValueError):
         return None
-    if not rec or rec.get("kernel_sha") != kernel_source_hash():
+    if not rec or rec.get("kernel_sha") != kernel_source_hash(files):
         return None
     return rec.get("dram_bytes_per_iteration")
 
@@ -368,9 +372,14 @@ def run_dense13(args):
     if "tensor_sliced" in out:
         # the dominant kernel of the timed path: k_dense_persistent<..., 3>, its tensor-core work
         ts = out["tensor_sliced"]
+        # DRAM bytes per Leja iteration from the 12-spin capture (dim 4096), scaled by (dim / 4096)^2:
+        # the traffic is the digits of the dense terms, read once per iteration
+        t12 = profiled_traffic("dense_tc_12spins_64states", DENSE_TC_SOURCES)
         roof = {"bound": "tensor", "kernel": "k_dense_persistent (tcgen05 digit products)",
                 "achieved": ts["bf16_tflops_issued"], "peak": bf16_peak, "unit": "TFLOP/s",
-                "frac": round(ts["bf16_tflops_issued"] / bf16_peak, 4), "traffic": None,
+                "frac": round(ts["bf16_tflops_issued"] / bf16_peak, 4),
+                "traffic": None if t12 is None or nv != 64 else int(t12 * (D / 4096) ** 2),
+                "traffic_unit": "DRAM bytes per Leja iteration (12-spin ncu capture scaled by (dim/4096)^2)",
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured",
                 "work": "10 bf16 digit-pair products x 2 flops x dim^2 x 128 columns per dense term per Leja iteration"}
     else:
