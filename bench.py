@@ -452,6 +452,25 @@ def run_batch512(args):
     gbs = bytes_it * iters_per_chain / (gms / 1e3) / 1e9
     peaks = measured_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", HBM_PEAK_FALLBACK))
+    # the plain FP64 GPU path for comparison: one plan and one persistent launch per chain, on a
+    # sample of every 16th chain (the sizes are drawn independently, so the sample is unbiased),
+    # extrapolated by the chain count
+    seq_steps = min(args.steps, 20)
+    sample = chains[::16]
+    seq_ms = 0.0
+    for c in sample:
+        q = mg.Plan(c.dim, workload_terms(mg, c, args.storage), drives(mg, c))
+        x = torch.from_numpy(c.psi0).cuda()
+        q.propagate(x, 0.0, 0.01, 1, args.variant)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        q.propagate(x, 0.0, 0.01, seq_steps, args.variant)
+        torch.cuda.synchronize()
+        seq_ms += (time.perf_counter() - t) * 1e3
+        q.close()
+    share = len(sample) / len(chains)
+    seq_rate = seq_steps / (seq_ms / share / 1e3)
+    batch_rate = args.steps / (gms / 1e3)
     line = {
         "metric": METRIC, "value": round(args.steps / (gms / 1e3), 3), "unit": "steps/s (all 512 chains per step)",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(gms / args.steps, 4),
@@ -460,6 +479,10 @@ def run_batch512(args):
                    "chains": len(chains), "rows": rows, "nnz": nnz, "h": 0.01, "variant": args.variant,
                    "cta_size": st["block"], "cluster_size": st["cluster"]},
         "chain_steps_per_s": round(len(chains) * args.steps / (gms / 1e3), 1),
+        "plain_fp64_path": {"steps_per_s": round(seq_rate, 3), "how": f"one plan and launch per chain, {len(sample)} "
+                            f"of 512 chains x {seq_steps} steps, wall time scaled by the chain count "
+                            f"(x {1 / share:.0f})"},
+        "speedup_vs_plain_fp64_path": round(batch_rate / seq_rate, 2),
         "leja_iterations": st["n_matvec"], "matvec_gbs": round(gbs, 1),
         "roofline": {"bound": "hbm" if args.storage.startswith("csr") else "alu", "kernel": "k_batched",
                      "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s", "frac": round(gbs / hbm_peak, 4),
@@ -529,6 +552,9 @@ def run_adjoint16(args):
                    "T": 10.0, "h": c.h, "checkpoint_every": 16},
         "F": F, "gradient_time_s": round(t_grad, 4), "forward_time_s": round(t_fwd, 4),
         "gradient_over_forward": round(t_grad / t_fwd, 3), "max_abs_err_vs_central_differences": max(errs),
+        # the plain FP64 GPU alternative: central differences need 2 forward propagations per parameter
+        "speedup_vs_central_differences": round(2 * grad.size * t_fwd / t_grad, 2),
+        "parameters": int(grad.size),
         "gpu_launches": "about 4 per exponential (recompute, augmented Leja, dot, costate)", "clocks": clk.summary(),
     }
     if rank == 0:

@@ -372,7 +372,7 @@ __device__ void row_center_radius(const Term &t, int64_t dim, int64_t i, double 
   if (t.kind == MAGNUS_TERM_CSR) {
     for (int64_t e = t.rowptr[i]; e < t.rowptr[i + 1]; e++) {
       double2 v = term_val(t, e);
-      if (t.col[e] == i) c += v.x; else R += cabs_(v);
+      if (t.col[e] == i) c += v.x; else R += t.real_valued ? fabs(v.x) : cabs_(v);
     }
   } else if (t.kind == MAGNUS_TERM_XXZ) {
     const int n = t.nspins;
@@ -402,7 +402,7 @@ __global__ void k_gershgorin_rows(const Term *tp, int64_t dim, double *part) {
       double c = 0.0, R = 0.0;
       for (int64_t j = lane; j < dim; j += 32) {
         double2 v = term_val(t, i * dim + j);
-        if (j == i) c += v.x; else R += cabs_(v);
+        if (j == i) c += v.x; else R += t.real_valued ? fabs(v.x) : cabs_(v);
       }
       c = warp_sum(c);
       R = warp_sum(R);
