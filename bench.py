@@ -561,6 +561,67 @@ def run_adjoint16(args):
         print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------------------- the matvec alone
+def run_spmv20(args):
+    """The generator matvec in isolation (magnus_apply): y = (H_s + H_d) x on the 20-spin chain,
+    one state; --steps applications timed with CUDA events after --warmup.  Algorithmic bytes per
+    application: CSR 20 B (real storage 12 B) per stored entry + 2 x 8 B row pointers per row + 16 B
+    read of x (each element once) + 16 B write of y per row; matrix-free 32 B per row.  FP64 work in
+    FMA-equivalent flops as in the Leja iteration, without the shift, update and norms."""
+    import torch
+
+    import magnus_inputs as mi
+    import paper_1709_06483_gb300 as mg
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    mg.load()
+    c = mi.workload2()
+    terms = workload_terms(mg, c, args.storage)
+    plan = mg.Plan(c.dim, terms, drives(mg, c))
+    x = torch.from_numpy(c.psi0).cuda()
+    y = torch.empty_like(x)
+    beta = np.array([1.0, 1.0])
+    for _ in range(max(args.warmup, 3)):
+        plan.apply(beta, x, y)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            plan.apply(beta, x, y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    D, n = c.dim, c.nspins
+    if args.storage.startswith("csr"):
+        nnz = sum(t.col.numel() for t in terms)
+        nbytes = (20 if args.storage == "csr" else 12) * nnz + 2 * 8 * (D + 1) + 32 * D
+        inst = 2 * nnz + 4 * D
+    else:
+        nbytes = 32 * D
+        inst = D * (4 + (n - 1) + 2 * n + 2)
+    gbs = nbytes / (ms / 1e3) / 1e9
+    tflops = 2 * inst / (ms / 1e3) / 1e12
+    peaks = measured_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", HBM_PEAK_FALLBACK))
+    line = {
+        "metric": METRIC, "value": round(gbs, 1), "unit": "GB/s (generator matvec alone)", "n_gpus": world,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(ms, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"matvec_xxz_chain_20spins_{args.storage}", "spins": n, "dim": D, "states": 1,
+                   "l2": "inputs larger than L2" if args.storage.startswith("csr") else "matrix-free, L2-resident"},
+        "roofline": {"bound": "alu", "kernel": "k_apply", "achieved": round(tflops, 4),
+                     "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s", "frac": round(tflops / FP64_PEAK_TFLOPS, 4),
+                     "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 4), "traffic": None,
+                     "algorithmic_bytes": nbytes},
+        "gpu_launches": args.steps, "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 # --------------------------------------------------------------------------- oracle arm
 def oracle_problem(c, interval="gershgorin"):
     import oracle
@@ -625,7 +686,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--spins", type=int, default=13, help="dense13 only: chain length (profiling smaller cases)")
     ap.add_argument("--states", type=int, default=64, help="dense13 only: states sharing H")
-    ap.add_argument("--workload", choices=["xxz20", "dense13", "batch512", "adjoint16"], default="xxz20",
+    ap.add_argument("--workload", choices=["xxz20", "dense13", "batch512", "adjoint16", "spmv20"], default="xxz20",
                     help="xxz20: the headline 20-spin chain; dense13: 13-spin dense chain, 64 states, FP64 vs split")
     args = ap.parse_args()
     if args.workload == "dense13" and args.impl == "ours":
@@ -636,6 +697,9 @@ def main():
         return
     if args.workload == "adjoint16" and args.impl == "ours":
         run_adjoint16(args)
+        return
+    if args.workload == "spmv20" and args.impl == "ours":
+        run_spmv20(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -234,7 +234,16 @@ MAGNUS_API magnus_status magnus_adjoint_grad(magnus_plan_t plan, const void *psi
                                              int64_t nsteps, int32_t variant, int32_t kd, int32_t ckpt_every, double *F,
                                              double *grad, magnus_stats *stats);
 
-/* Gershgorin enclosure [*a, *b] of term k (computed at plan creation). */
+/*
+ * y = sum_k beta_k H_k x for every state: the generator matvec of the Leja recurrence (Sec. 3, the
+ * operation the method's cost is made of), as a call of its own (expectation values, timing).
+ * beta: host, nterms reals.  x, y: device complex128 [nvec][dim], distinct, 16-byte aligned.
+ * Asynchronous on the plan's stream (no synchronisation).  Errors: EINVAL, ECUDA.
+ */
+MAGNUS_API magnus_status magnus_apply(magnus_plan_t plan, const double *beta, const void *x, void *y);
+
+/* Spectral enclosure [*a, *b] of term k (computed at plan creation: Gershgorin, or its
+ * intersection with the Lanczos enclosure). */
 MAGNUS_API magnus_status magnus_term_interval(magnus_plan_t plan, int32_t k, double *a, double *b);
 
 /* Copy the plan's m_max+1 Leja points (device-computed) to host xi[]. */

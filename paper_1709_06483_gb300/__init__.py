@@ -30,7 +30,7 @@ EXPORTS = (
     "magnus_propagate", "magnus_term_interval", "magnus_leja_points", "magnus_divided_differences",
     "magnus_xxz_nnz", "magnus_build_xxz_csr", "magnus_build_field_x_csr", "magnus_build_longrange_dense",
     "magnus_build_field_x_dense", "magnus_expv_xxz_static", "magnus_batch_create", "magnus_batch_propagate",
-    "magnus_batch_destroy", "magnus_batch_last_error", "magnus_adjoint_grad", "magnus_real_parts",
+    "magnus_batch_destroy", "magnus_batch_last_error", "magnus_adjoint_grad", "magnus_real_parts", "magnus_apply",
 )
 
 
@@ -105,6 +105,7 @@ def _declare(L):
         "magnus_batch_last_error": (C.c_char_p, [P]),
         "magnus_adjoint_grad": (I32, [P, P, P, D, D, I64, I32, I32, I32, C.POINTER(D), C.POINTER(D), C.POINTER(Stats)]),
         "magnus_real_parts": (I32, [P, I64, P, P]),
+        "magnus_apply": (I32, [P, C.POINTER(D), P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -328,6 +329,18 @@ class Plan:
         _check(load().leja_expv(self._h, b.ctypes.data_as(C.POINTER(C.c_double)), C.c_void_p(_dptr(v)),
                                 C.c_void_p(_dptr(out)), C.byref(st)), self._h)
         return out, _as_dict(st, log)
+
+    def apply(self, beta, x, y=None):
+        """y = sum_k beta_k H_k x for every state (CUDA complex128 [nvec][dim]; asynchronous)."""
+        import torch
+        self._check_state(x)
+        if y is None:
+            y = torch.empty_like(x)
+        b = _f64(beta)
+        assert b.size == self.nterms
+        _check(load().magnus_apply(self._h, b.ctypes.data_as(C.POINTER(C.c_double)), C.c_void_p(_dptr(x)),
+                                   C.c_void_p(_dptr(y))), self._h)
+        return y
 
     def adjoint_grad(self, psi0, phi, t0, h, nsteps, variant="CF4", kd=1, ckpt_every=16):
         """F = |<phi|psi(T)>|^2 and dF/d(a0, ac_m, as_m) of term kd's drive (adjoint, checkpointed)."""

@@ -668,6 +668,19 @@ magnus_status leja_expv(magnus_plan_t p, const double *beta, const void *v, void
   return run_persistent(p, out, 1, stats);
 }
 
+magnus_status magnus_apply(magnus_plan_t p, const double *beta, const void *x, void *y) {
+  if (!p) return set_err(nullptr, MAGNUS_EINVAL, "plan is null");
+  p->err.clear();
+  if (!beta || !x || !y) return set_err(p, MAGNUS_EINVAL, "null argument");
+  if (x == y) return set_err(p, MAGNUS_EINVAL, "x and y must be distinct buffers");
+  if (((uintptr_t)x) % 16 || ((uintptr_t)y) % 16) return set_err(p, MAGNUS_EINVAL, "vectors must be 16-byte aligned");
+  for (int k = 0; k < p->nterms; k++)
+    if (!(beta[k] == beta[k]) || beta[k] - beta[k] != 0.0) return set_err(p, MAGNUS_EINVAL, "beta[%d] not finite", k);
+  CUDA_TRY(p, launch_apply(p->fam, p->terms, p->nterms, beta, p->lbits, p->dlo, p->dhi, (const double2 *)x,
+                           (double2 *)y, p->dim, p->opt.nvec, p->num_sms, p->stream));
+  return MAGNUS_OK;
+}
+
 magnus_status magnus_term_interval(magnus_plan_t p, int32_t k, double *a, double *b) {
   if (!p || !a || !b || k < 0 || k >= p->nterms) return set_err(p, MAGNUS_EINVAL, "bad argument");
   *a = p->term_ab_host[2 * k];
