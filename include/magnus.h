@@ -235,6 +235,13 @@ MAGNUS_API magnus_status magnus_adjoint_grad(magnus_plan_t plan, const void *psi
                                              double *grad, magnus_stats *stats);
 
 /*
+ * Replace the drive coefficient f_k of term k (host struct, copied): the next calls on the plan use
+ * it (stream-ordered).  The spectral enclosures are those of the terms and do not change.
+ * Errors: EINVAL, ECUDA.
+ */
+MAGNUS_API magnus_status magnus_set_coeff(magnus_plan_t plan, int32_t k, const magnus_coeff *c);
+
+/*
  * y = sum_k beta_k H_k x for every state: the generator matvec of the Leja recurrence (Sec. 3, the
  * operation the method's cost is made of), as a call of its own (expectation values, timing).
  * beta: host, nterms reals.  x, y: device complex128 [nvec][dim], distinct, 16-byte aligned.

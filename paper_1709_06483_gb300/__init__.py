@@ -31,6 +31,7 @@ EXPORTS = (
     "magnus_xxz_nnz", "magnus_build_xxz_csr", "magnus_build_field_x_csr", "magnus_build_longrange_dense",
     "magnus_build_field_x_dense", "magnus_expv_xxz_static", "magnus_batch_create", "magnus_batch_propagate",
     "magnus_batch_destroy", "magnus_batch_last_error", "magnus_adjoint_grad", "magnus_real_parts", "magnus_apply",
+    "magnus_set_coeff",
 )
 
 
@@ -106,6 +107,7 @@ def _declare(L):
         "magnus_adjoint_grad": (I32, [P, P, P, D, D, I64, I32, I32, I32, C.POINTER(D), C.POINTER(D), C.POINTER(Stats)]),
         "magnus_real_parts": (I32, [P, I64, P, P]),
         "magnus_apply": (I32, [P, C.POINTER(D), P, P]),
+        "magnus_set_coeff": (I32, [P, I32, C.POINTER(Coeff)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -330,6 +332,12 @@ class Plan:
                                 C.c_void_p(_dptr(out)), C.byref(st)), self._h)
         return out, _as_dict(st, log)
 
+    def set_drive(self, k, drive):
+        """Replace the drive f_k of term k (stream-ordered; enclosures unchanged)."""
+        self._drives[k] = drive
+        c = drive.ctype()
+        _check(load().magnus_set_coeff(self._h, int(k), C.byref(c)), self._h)
+
     def apply(self, beta, x, y=None):
         """y = sum_k beta_k H_k x for every state (CUDA complex128 [nvec][dim]; asynchronous)."""
         import torch
@@ -502,3 +510,42 @@ def expv_xxz_static(nspins, J, hz, delta, beta, v, out=None, tol=1e-10, stream=N
                                          b.ctypes.data_as(P), C.c_void_p(_dptr(v)), C.c_void_p(_dptr(out)),
                                          float(tol), _stream_ptr(stream)))
     return out
+
+
+# ------------------------------------------------------------------ autograd
+def _fidelity_function():
+    import torch
+
+    class FidelityFunction(torch.autograd.Function):
+        """F(c) = |<phi|psi(T)>|^2 for the drive coefficients c = (a0, ac[0..m), as[0..m)) of term kd;
+        backward returns dF/dc from the adjoint kernels (magnus_adjoint_grad)."""
+
+        @staticmethod
+        def forward(ctx, params, plan, kd, psi0, phi, t0, h, nsteps, variant, ckpt_every):
+            om = plan._drives[kd].om
+            nm = om.size
+            p = params.detach().to("cpu", torch.float64).numpy()
+            plan.set_drive(kd, Drive(p[0], p[1:1 + nm], p[1 + nm:1 + 2 * nm], om))
+            F, grad, _ = plan.adjoint_grad(psi0, phi, t0, h, nsteps, variant, kd=kd, ckpt_every=ckpt_every)
+            ctx.save_for_backward(torch.from_numpy(grad))
+            return params.new_tensor(F)
+
+        @staticmethod
+        def backward(ctx, gF):
+            (grad,) = ctx.saved_tensors
+            return (gF * grad.to(gF.device, gF.dtype),) + (None,) * 9
+
+    return FidelityFunction
+
+
+_FIDELITY = None
+
+
+def fidelity(plan, params, psi0, phi, t0, h, nsteps, variant="CF4", kd=1, ckpt_every=16):
+    """Differentiable F = |<phi|psi(T)>|^2 with respect to params = (a0, ac, as) of term kd's drive
+    (a float64 tensor of 1 + 2 nmodes entries, the drive's frequencies fixed); the plan's drive for
+    term kd is set to params."""
+    global _FIDELITY
+    if _FIDELITY is None:
+        _FIDELITY = _fidelity_function()
+    return _FIDELITY.apply(params, plan, kd, psi0, phi, t0, h, nsteps, variant, ckpt_every)

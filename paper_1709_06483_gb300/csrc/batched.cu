@@ -711,7 +711,8 @@ MAGNUS_API magnus_status magnus_batch_propagate(magnus_batch_t b, void *const *p
     stats->cluster = b->tuned_cs;
     if (want_log) {
       std::vector<int> tmp((size_t)b->count * b->mlog_cap);
-      BTRY(b, cudaMemcpy(tmp.data(), b->mlog, sizeof(int) * tmp.size(), cudaMemcpyDeviceToHost));
+      BTRY(b, cudaMemcpyAsync(tmp.data(), b->mlog, sizeof(int) * tmp.size(), cudaMemcpyDeviceToHost, b->stream));
+      BTRY(b, cudaStreamSynchronize(b->stream));
       for (int i = 0; i < b->count; i++)
         memcpy(ulog + (size_t)i * ucap, tmp.data() + (size_t)i * b->mlog_cap, sizeof(int) * ucap);
     }

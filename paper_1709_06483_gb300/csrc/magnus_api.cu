@@ -61,6 +61,7 @@ struct magnus_plan_s {
   int tc_grid = 0, tc_slots = 0, tc_ndense = 0;
   int tc_dslot[kMaxTerms] = {0, 0, 0, 0};
   bool m4_sliced_ready = false;          // the 5 x 7-bit tables of the M4 path exist
+  Coeff coeff_host[kMaxTerms];           // staging of magnus_set_coeff
   int lbits = 0;
   double *dlo = nullptr, *dhi = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -668,6 +669,27 @@ magnus_status leja_expv(magnus_plan_t p, const double *beta, const void *v, void
   return run_persistent(p, out, 1, stats);
 }
 
+magnus_status magnus_set_coeff(magnus_plan_t p, int32_t k, const magnus_coeff *c) {
+  if (!p) return set_err(nullptr, MAGNUS_EINVAL, "plan is null");
+  p->err.clear();
+  if (!c || k < 0 || k >= p->nterms) return set_err(p, MAGNUS_EINVAL, "bad term index or null coefficient");
+  if (c->nmodes < 0 || c->nmodes > kMaxModes || (c->nmodes > 0 && !c->om))
+    return set_err(p, MAGNUS_EINVAL, "nmodes must be 0..%d with om given", kMaxModes);
+  Coeff &C = p->coeff_host[k];
+  memset(&C, 0, sizeof C);
+  C.a0 = c->a0;
+  C.nmodes = c->nmodes;
+  for (int m = 0; m < C.nmodes; m++) {
+    C.ac[m] = c->ac ? c->ac[m] : 0.0;
+    C.as[m] = c->as ? c->as[m] : 0.0;
+    C.om[m] = c->om[m];
+  }
+  // stream-ordered: launches issued after this call see the new coefficients (pageable source:
+  // the copy is staged before the call returns)
+  CUDA_TRY(p, cudaMemcpyAsync(p->coeffs + k, &C, sizeof(Coeff), cudaMemcpyHostToDevice, p->stream));
+  return MAGNUS_OK;
+}
+
 magnus_status magnus_apply(magnus_plan_t p, const double *beta, const void *x, void *y) {
   if (!p) return set_err(nullptr, MAGNUS_EINVAL, "plan is null");
   p->err.clear();
@@ -747,7 +769,8 @@ magnus_status magnus_adjoint_grad(magnus_plan_t p, const void *psi0, const void 
   int nm = 0;
   {
     Coeff ch{};
-    CUDA_TRY(p, cudaMemcpy(&ch, p->coeffs + kd, sizeof(Coeff), cudaMemcpyDeviceToHost));
+    CUDA_TRY(p, cudaMemcpyAsync(&ch, p->coeffs + kd, sizeof(Coeff), cudaMemcpyDeviceToHost, p->stream));
+    CUDA_TRY(p, cudaStreamSynchronize(p->stream));
     nm = ch.nmodes;
   }
   const int ngrad = 1 + 2 * nm;

@@ -84,3 +84,26 @@ def test_workload5_full_size_vs_central_differences(mg):
         fd = (fid(up) - fid(dn)) / (2 * dl)
         g = grad[1 + om.size + k]  # dF/das_k
         assert abs(g - fd) < 1e-8 + 1e-5 * abs(fd), (k, g, fd)
+
+
+def test_fidelity_autograd_function(mg):
+    """torch.autograd: F(c) through mg.fidelity, F.backward() gives the oracle's adjoint gradient,
+    and a gradient-ascent step on c increases F."""
+    n, nmodes, T, h, N = 8, 6, 1.0, 0.04, 25
+    c, ck, om, phi = control_chain(n, nmodes, T, 52)
+    ac = 0.1 * np.ones(nmodes)
+    terms = [mg.XXZTerm(n, c.J, c.hz, c.delta), mg.FieldXTerm(n)]
+    plan = mg.Plan(c.dim, terms, [mg.Drive.const(), mg.Drive(0.0, np.zeros(nmodes), np.zeros(nmodes), om)], tol=1e-12)
+    params = torch.tensor(np.concatenate([[0.2], ac, ck]), dtype=torch.float64, requires_grad=True)
+    psi0, phit = cuda(c.psi0), cuda(phi)
+    F = mg.fidelity(plan, params, psi0, phit, 0.0, h, N, "CF4", kd=1, ckpt_every=5)
+    F.backward()
+    P = oracle.Problem([oracle.xxz_csr(n, c.J, c.hz, c.delta), oracle.field_x_csr(n)],
+                       [oracle.Coeff.const(), oracle.Coeff(0.2, ac, ck, om)], tol=1e-12)
+    Fr, gr = P.adjoint_grad(c.psi0, phi, 0.0, h, N, "CF4", kd=1)
+    assert abs(F.item() - Fr) < 1e-12
+    assert np.max(np.abs(params.grad.numpy() - gr)) < 1e-9
+    with torch.no_grad():
+        stepped = params + 0.05 * params.grad / params.grad.norm()
+    F2 = mg.fidelity(plan, stepped, psi0, phit, 0.0, h, N, "CF4", kd=1, ckpt_every=5)
+    assert F2.item() > F.item()
