@@ -394,3 +394,65 @@ def test_apply_matches_oracle_terms(mg, kind):
         xv = c.psi0.reshape(3, -1)[v]
         ref = beta[0] * P.apply_term(0, xv) + beta[1] * P.apply_term(1, xv)
         assert rel(y[v], ref) < 1e-13, (kind, v, rel(y[v], ref))
+
+
+# ----------------------------------------------------------------- general matrices
+def _random_hermitian_csr(rng, D, density, complex_values=True):
+    """Random sparse Hermitian matrix with a ragged row-length mix (some rows hold only the diagonal)."""
+    A = np.zeros((D, D), dtype=np.complex128)
+    mask = rng.random((D, D)) < density
+    vals = rng.standard_normal((D, D)) + (1j * rng.standard_normal((D, D)) if complex_values else 0.0)
+    A[mask] = vals[mask]
+    A = (A + A.conj().T) / 2
+    A[np.diag_indices(D)] = rng.uniform(-2, 2, D)
+    rows, cols = np.nonzero(A)
+    rowptr = np.zeros(D + 1, dtype=np.int64)
+    np.add.at(rowptr, rows + 1, 1)
+    rowptr = np.cumsum(rowptr)
+    return oracle.CSR(rowptr, cols.astype(np.int32), A[rows, cols]), A
+
+
+@pytest.mark.parametrize("interval", ["gershgorin", "lanczos"])
+def test_general_complex_csr_odd_dimension(mg, interval):
+    """A complex Hermitian CSR term (complex products, no real-value path) plus a real one, dim 1003
+    (not a multiple of the warp or block), 2 states, Cf4 and M4, against the oracle."""
+    rng = np.random.default_rng(29)
+    D = 1003
+    H1, _ = _random_hermitian_csr(rng, D, 0.004, complex_values=True)
+    H2, _ = _random_hermitian_csr(rng, D, 0.002, complex_values=False)
+    psi0 = np.stack([mi.random_state(rng, D), mi.random_state(rng, D)])
+    f = oracle.Coeff(0.2, [1.0], [0.3], [4.0])
+    P = oracle.Problem([H1, H2], [oracle.Coeff.const(), f], interval=interval)
+    terms = [mg.CSRTerm(cuda(H.rowptr), cuda(H.col), cuda(H.val)) for H in (H1, H2)]
+    plan = mg.Plan(D, terms, [mg.Drive.const(), mg.Drive(0.2, [1.0], [0.3], [4.0])], nvec=2, interval=interval)
+    for k in range(2):
+        a, b = plan.interval(k)
+        ra, rb = P.interval(k)
+        assert abs(a - ra) < 1e-8 * (rb - ra) and abs(b - rb) < 1e-8 * (rb - ra)
+    for variant in ("CF4", "M4"):
+        psi = cuda(psi0)
+        plan.propagate(psi, 0.0, 0.05, 10, variant)
+        out = psi.cpu().numpy()
+        for v in range(2):
+            ref = P.propagate(psi0[v], 0.0, 0.05, 10, variant)
+            assert rel(out[v], ref) < REL_TOL, (variant, v, rel(out[v], ref))
+
+
+def test_general_complex_dense_odd_dimension(mg):
+    """A complex Hermitian dense term (complex FP64 tile path), dim 200, 3 states, against the oracle."""
+    rng = np.random.default_rng(30)
+    D = 200
+    A = rng.standard_normal((D, D)) + 1j * rng.standard_normal((D, D))
+    A = (A + A.conj().T) / 4
+    B = rng.standard_normal((D, D))
+    B = ((B + B.T) / 4).astype(np.complex128)
+    psi0 = np.stack([mi.random_state(rng, D) for _ in range(3)])
+    f = oracle.Coeff(0.0, [1.0], [], [3.0])
+    P = oracle.Problem([A, B], [oracle.Coeff.const(), f])
+    plan = mg.Plan(D, [mg.DenseTerm(cuda(A)), mg.DenseTerm(cuda(B))], [mg.Drive.const(), mg.Drive(0.0, [1.0], [], [3.0])],
+                   nvec=3)
+    psi = cuda(psi0)
+    plan.propagate(psi, 0.0, 0.02, 8, "CF4")
+    out = psi.cpu().numpy()
+    for v in range(3):
+        assert rel(out[v], P.propagate(psi0[v], 0.0, 0.02, 8, "CF4")) < REL_TOL
