@@ -146,7 +146,7 @@ typedef enum {
  *   test_skip_arrival [0]: testing only -- if nonzero, CTA 0 of the sparse/matrix-free propagation
  *                     kernel leaves before its first grid barrier, so the other CTAs' waits run out
  *   interval [MAGNUS_INTERVAL_GERSHGORIN]: how each term's spectral enclosure is estimated (Sec. 3:
- *                     the Leja parameters need "an estimate on the spectrum"); plans only, batches
+ *                     the Leja parameters need a spectral estimate); plans only, batches
  *                     take Gershgorin
  */
 typedef struct {

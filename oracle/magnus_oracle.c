@@ -382,8 +382,8 @@ int orc_set_dense(orc_problem *p, int k, const double complex *H) {
 }
 
 /* ------------------------------------------------------------------------- */
-/* Lanczos enclosure of a term's spectrum (the "estimate on the spectrum" of  */
-/* Sec. 3, tighter than Gershgorin).                                          */
+/* Lanczos enclosure of a term's spectrum (Sec. 3: the Leja parameters need  */
+/* a spectral estimate; this one is tighter than Gershgorin).                 */
 /* ------------------------------------------------------------------------- */
 
 /* SplitMix64 (Steele, Lea, Flood 2014) in counter form: output c of the stream that starts at
@@ -459,7 +459,7 @@ static double tridiag_last_component(const double *al, const double *be, int m, 
 }
 
 /*
- * Reading (the paper needs "an estimate on the spectrum" and defers to [ckor15]): m steps of the
+ * Reading (the Leja parameters need a spectral estimate; Sec. 3 defers to [ckor15]): m steps of the
  * Lanczos recurrence on H_k from the start vector v_i = (2u_{2i} - 1) + i (2u_{2i+1} - 1),
  * u_c = unit_at(1709064830, c), normalised:
  *     w = H v_j;  al_j = Re <v_j, w>;  w -= al_j v_j + be_j v_{j-1};  be_{j+1} = |w|;  v_{j+1} = w / be_{j+1},

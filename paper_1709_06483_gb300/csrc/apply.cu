@@ -1,5 +1,5 @@
 // y = sum_k beta_k H_k x for every state of a plan: the generator matvec of the Leja recurrence
-// (arXiv:1709.06483, Sec. 3: "the main cost ... are matrix-vector products") as a call of its own,
+// (arXiv:1709.06483, Sec. 3, where these products make up the cost of the method) as a call of its own,
 // for expectation values and for timing the matvec outside the propagation.  CSR, matrix-free and
 // mixed terms use the same row code as the persistent kernel (rows.cuh); dense terms one warp per
 // row and state.

@@ -1,5 +1,5 @@
 // Lanczos enclosure of one stored term's spectrum (arXiv:1709.06483, Sec. 3: the Leja method needs
-// "an estimate on the spectrum" of the matrix; the Gershgorin enclosure is rigorous but wide).
+// an enclosure of the spectrum of the matrix; the Gershgorin enclosure is rigorous but wide).
 // m steps of the Lanczos recurrence on H_k from a fixed pseudo-random start vector
 //     w = H v_j;  al_j = Re <v_j, w>;  w -= al_j v_j + be_j v_{j-1};  be_{j+1} = |w|;  v_{j+1} = w / be_{j+1}
 // (stopped at an invariant subspace), then the extreme eigenvalues theta of the tridiagonal matrix

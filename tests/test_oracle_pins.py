@@ -390,7 +390,7 @@ def test_paper_example1_error_ratios():
 
 
 # ---------------------------------------------------------------------------
-# Lanczos enclosure of a term's spectrum (Sec. 3: "an estimate on the spectrum")
+# Lanczos enclosure of a term's spectrum (Sec. 3: the spectral estimate the Leja parameters need)
 # ---------------------------------------------------------------------------
 def _rand_hermitian(rng, n):
     A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
