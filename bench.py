@@ -80,21 +80,28 @@ def drives(mg, c):
     return [mg.Drive.const(), mg.Drive(c.drive_a0, c.drive_ac, c.drive_as, c.drive_om)]
 
 
-def algorithmic_per_iteration(c, storage, variant, nnz_total):
+def algorithmic_per_iteration(c, storage, variant, nnz_terms, fixed=False, subs_per_it=0.0):
     """Bytes and FP64 work one Leja iteration needs (real-valued Hamiltonian, complex state).
 
+    nnz_terms: stored entries of (H_s, sum_i sx_i) for CSR storage.  fixed: the pattern term
+    sum_i sx_i (every stored value 1) is summed in exact 64-bit fixed point (linear generators).
+
     Bytes, CSR: per stored entry 16 B value (8 B in real storage) + 4 B column, per row 8 B row
-    pointer per term, plus per
-    row 16 B read of w_{j-1}, 16 B write of w_j and 16 + 16 B read and write of p; matrix-free: the
-    vector traffic only.  M4 applies every term twice and writes and reads back u_k (2 x 32 B/row).
+    pointer per term, plus per row 16 B read of w_{j-1}, 16 B write of w_j and 16 + 16 B read and
+    write of p; matrix-free: the vector traffic only.  With fixed sums the pattern term needs its
+    columns only (4 B per entry), and every row adds the 16 B write of the fixed-point copy of w_j
+    and the 16 B read of that of w_{j-1}; the copy of each substep input costs 16 + 16 B per row
+    once per substep (subs_per_it substeps per iteration).  M4 applies every term twice and writes
+    and reads back u_k (2 x 32 B/row).
 
     FP64 work is counted in FMA-equivalent flops: every FP64 instruction the method needs (add,
     multiply or fused multiply-add) counts 2, because on GB300 each occupies one slot of the FP64
     pipe (2 per clock per SM, peak 152 x 2 x 2 x 2070 MHz = 1.259 TFLOP/s).  Per row: CSR needs 2
-    instructions per stored entry; the matrix-free XXZ row needs 4 for the diagonal, 2 per active
-    bond ((n-1)/2 on average) and 2 n for the field sum plus 2 to weight it; both need 4 for the
-    weighted combination (CSR) or none extra (matrix-free), 2 for the shift, 4 for the Newton update
-    of p and 4 for the two squared norms.
+    instructions per stored entry of a term summed in FP64; the matrix-free XXZ row needs 4 for the
+    diagonal, 2 per active bond ((n-1)/2 on average) and, with FP64 sums, 2 n for the field sum,
+    plus 2 to weight it; both need 4 for the weighted combination (CSR) or none extra
+    (matrix-free), 2 for the shift, 4 for the Newton update of p and 4 for the two squared norms.
+    Fixed-point sums are integer additions, outside the FP64 count.
 
     M6 applies every term 17 times per iteration (once per input vector of its five passes and the
     final one); its 23 intermediate vectors are each written once and read back once or twice:
@@ -103,23 +110,28 @@ def algorithmic_per_iteration(c, storage, variant, nnz_total):
     commutator arithmetic per row."""
     D = c.dim
     passes = {"M4": 2, "M6": 17}.get(variant, 1)
+    fixed = fixed and variant not in ("M4", "M6")
     vec_bytes = 64 * D
+    if fixed:
+        vec_bytes += 32 * D + 32 * D * subs_per_it
     if variant == "M4":
         vec_bytes += 2 * 16 * D * 2
     if variant == "M6":
         vec_bytes += (17 + 23 + 16) * 16 * D
     if storage in ("csr", "csr_real"):
-        mat = (20 if storage == "csr" else 12) * nnz_total + 2 * 8 * (D + 1)
-        inst = passes * 2 * nnz_total + (4 + 2 + 4 + 4) * D
+        nnz_s, nnz_c = nnz_terms
+        per_entry = 20 if storage == "csr" else 12
+        mat = per_entry * nnz_s + (4 if fixed else per_entry) * nnz_c + 2 * 8 * (D + 1)
+        inst = passes * 2 * (nnz_s + (0 if fixed else nnz_c)) + (4 + 2 + 4 + 4) * D
     else:
         n = c.nspins
         mat = 0
-        inst = passes * D * (4 + (n - 1) + 2 * n + 2) + (2 + 4 + 4) * D
+        inst = passes * D * (4 + (n - 1) + (0 if fixed else 2 * n) + 2) + (2 + 4 + 4) * D
     if variant == "M4":
         inst += 8 * D  # commutator difference and its weight
     if variant == "M6":
         inst += (27 * 2 * 2 + 70 - 4) * D  # combinations and commutator arithmetic (no separate weighting)
-    return passes * mat + vec_bytes, 2 * inst
+    return int(passes * mat + vec_bytes), int(2 * inst)
 
 
 class ClockSampler:
@@ -208,8 +220,9 @@ def run_ours(args):
     variant, storage = args.variant, args.storage
     stream = torch.cuda.current_stream()
     terms = workload_terms(mg, c, storage)
-    nnz_total = sum(t.col.numel() for t in terms) if storage.startswith("csr") else None
-    plan = mg.Plan(c.dim, terms, drives(mg, c), interval=args.interval)
+    nnz_terms = tuple(t.col.numel() for t in terms) if storage.startswith("csr") else (0, 0)
+    nnz_total = sum(nnz_terms) if storage.startswith("csr") else None
+    plan = mg.Plan(c.dim, terms, drives(mg, c), interval=args.interval, fixed_sums=bool(args.fixed_sums))
     psi0 = torch.from_numpy(c.psi0).cuda()
     psi = psi0.clone()
 
@@ -234,14 +247,15 @@ def run_ours(args):
 
     # roofline of the persistent Leja kernel, from its own CUDA-event duration
     nmv = st["n_matvec"]
-    bytes_it, flops_it = algorithmic_per_iteration(c, storage, variant, nnz_total or 0)
+    fixed = bool(st["fixed_sums"])
+    bytes_it, flops_it = algorithmic_per_iteration(c, storage, variant, nnz_terms, fixed, st["n_substeps"] / nmv)
     kms = st["kernel_ms"]
     gbs = bytes_it * nmv / (kms / 1e3) / 1e9
     tflops = flops_it * nmv / (kms / 1e3) / 1e12
     peaks = measured_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", HBM_PEAK_FALLBACK))
     t_hbm, t_alu = bytes_it / (hbm_peak * 1e9), flops_it / (FP64_PEAK_TFLOPS * 1e12)
-    key = f"wl2_{storage}_{variant}"
+    key = f"wl2_{storage}_{variant}" + ("_fixed" if fixed else "")
     traffic_it = profiled_traffic(key)
     if t_alu >= t_hbm:
         roof = {"bound": "alu", "achieved": round(tflops, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
@@ -277,10 +291,11 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+i64" if fixed else "f64", "data": "synthetic",
         "config": {"workload": f"xxz_chain_20spins_{storage}_{variant.lower()}", "spins": c.nspins, "dim": c.dim,
                    "nnz": nnz_total, "h": c.h, "t0": c.t0, "variant": variant, "storage": storage,
                    "interval": args.interval,
+                   "sums": "sum_i sx_i rows in exact int64 fixed point, the rest FP64" if fixed else "FP64",
                    "leja_tol": 1e-10, "l2": "inputs larger than L2: the 640 MB CSR is streamed every iteration"
                    if storage.startswith("csr") else "matrix-free; 4 state vectors of 16 MB stay L2-resident",
                    "parallelism": f"replicas x{world}"},
@@ -690,6 +705,8 @@ def main():
     ap.add_argument("--interval", choices=["gershgorin", "lanczos"], default="lanczos",
                     help="spectral enclosure of each term (20-spin workload)")
     ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--fixed-sums", type=int, choices=[0, 1], default=1,
+                    help="xxz20: pattern-term sums in fixed point (1) or FP64 (0)")
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--spins", type=int, default=13, help="dense13 only: chain length (profiling smaller cases)")

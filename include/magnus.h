@@ -148,6 +148,13 @@ typedef enum {
  *   interval [MAGNUS_INTERVAL_GERSHGORIN]: how each term's spectral enclosure is estimated (Sec. 3:
  *                     the Leja parameters need a spectral estimate); plans only, batches
  *                     take Gershgorin
+ *   fixed_sums [1]:   sum the rows of pattern terms -- real CSR terms whose stored values are all
+ *                     equal (v sum_e x[col_e]), and MAGNUS_TERM_FIELD_X next to MAGNUS_TERM_XXZ --
+ *                     exactly in 64-bit integers on a fixed-point copy of each Leja vector, scaled
+ *                     from a bound on its largest component (truncation below 2^-55 of that bound
+ *                     per component for rows of up to 32 entries), for the linear generators (M2,
+ *                     CF4, CF4:3) of plans with only CSR terms or the matrix-free chain; 0 = FP64
+ *                     sums.  Not part of the paper, which computes in FP64 only.
  */
 typedef struct {
   double tol_rel;
@@ -160,6 +167,8 @@ typedef struct {
   double barrier_timeout_s;
   int32_t test_skip_arrival;
   int32_t interval;
+  int32_t fixed_sums;
+  int32_t _reserved;
 } magnus_options;
 
 typedef struct {
@@ -174,6 +183,8 @@ typedef struct {
   double kernel_ms;     /* device time of the persistent Leja kernel (CUDA events on the plan's stream) */
   int32_t grid;         /* CTAs of that launch                                */
   int32_t block;        /* threads per CTA                                    */
+  int32_t fixed_sums;   /* 1 if the pattern-term sums ran in fixed point (options.fixed_sums) */
+  int32_t _pad;
 } magnus_stats;
 
 typedef struct magnus_plan_s *magnus_plan_t;

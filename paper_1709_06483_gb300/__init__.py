@@ -55,14 +55,15 @@ class Coeff(C.Structure):
 class Options(C.Structure):
     _fields_ = [("tol_rel", C.c_double), ("tol_abs", C.c_double), ("rho_max", C.c_double), ("m_max", C.c_int32),
                 ("nvec", C.c_int32), ("ctas", C.c_int32), ("precision", C.c_int32), ("barrier_timeout_s", C.c_double),
-                ("test_skip_arrival", C.c_int32), ("interval", C.c_int32)]
+                ("test_skip_arrival", C.c_int32), ("interval", C.c_int32), ("fixed_sums", C.c_int32),
+                ("_reserved", C.c_int32)]
 
 
 class Stats(C.Structure):
     _fields_ = [("n_exp", C.c_int64), ("n_substeps", C.c_int64), ("n_matvec", C.c_int64),
                 ("n_termapply", C.c_int64), ("max_m", C.c_int32), ("status", C.c_int32),
                 ("m_log", C.POINTER(C.c_int32)), ("m_log_cap", C.c_int64), ("kernel_ms", C.c_double),
-                ("grid", C.c_int32), ("block", C.c_int32)]
+                ("grid", C.c_int32), ("block", C.c_int32), ("fixed_sums", C.c_int32), ("_pad", C.c_int32)]
 
 
 class BatchItem(C.Structure):
@@ -268,7 +269,8 @@ class Plan:
     """A Magnus/Leja plan: dim, terms H_k with drives f_k, Leja tolerance, vectors per call."""
 
     def __init__(self, dim, terms, drives, tol=1e-10, tol_abs=None, rho_max=4.0, m_max=100, nvec=1, ctas=0,
-                 precision=FP64, stream=None, barrier_timeout_s=0.0, test_skip_arrival=0, interval="gershgorin"):
+                 precision=FP64, stream=None, barrier_timeout_s=0.0, test_skip_arrival=0, interval="gershgorin",
+                 fixed_sums=True):
         import torch
         L = load()
         assert len(terms) == len(drives)
@@ -279,7 +281,7 @@ class Plan:
         carr = (Coeff * len(drives))(*[d.ctype() for d in drives])
         opt = Options(float(tol), float(tol if tol_abs is None else tol_abs), float(rho_max), int(m_max), int(nvec),
                       int(ctas), int(precision), float(barrier_timeout_s), int(test_skip_arrival),
-                      INTERVALS[interval])
+                      INTERVALS[interval], int(bool(fixed_sums)), 0)
         h = C.c_void_p()
         _check(L.magnus_plan_create(C.byref(h), self.dim, len(terms), tarr, carr, C.byref(opt),
                                     _stream_ptr(self.stream)))
@@ -382,7 +384,7 @@ class Plan:
 
 def _as_dict(st: Stats, log):
     out = {k: getattr(st, k) for k in ("n_exp", "n_substeps", "n_matvec", "n_termapply", "max_m", "status",
-                                       "kernel_ms", "grid", "block")}
+                                       "kernel_ms", "grid", "block", "fixed_sums")}
     if log is not None:
         out["m_log"] = log[: min(st.n_substeps, log.size)].copy()
     return out
@@ -406,7 +408,7 @@ class Batch:
         self.count = len(problems)
         self.dims = [int(p[0]) for p in problems]
         opt = Options(float(tol), float(tol if tol_abs is None else tol_abs), float(rho_max), int(m_max), 1,
-                      int(ctas), FP64, 0.0, 0, 0)
+                      int(ctas), FP64, 0.0, 0, 0, 0, 0)
         h = C.c_void_p()
         code = L.magnus_batch_create(C.byref(h), self.count, arr, C.byref(opt), None)
         if code != OK:

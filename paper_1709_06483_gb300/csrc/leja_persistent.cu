@@ -21,6 +21,8 @@
 // loads; only the immutable matrices use the read-only path.
 #include <math.h>
 
+#include <type_traits>
+
 #include "magnus_internal.cuh"
 #include "persist_common.cuh"
 #include "rows.cuh"
@@ -32,10 +34,16 @@ namespace {
 using namespace rows;
 
 constexpr int kBlock = 256;
-#ifndef MG_PERSIST_MIN_BLOCKS
-#define MG_PERSIST_MIN_BLOCKS 3
+// Resident CTAs per SM the register budget targets: 4 (64 registers) for the CSR family, whose
+// time goes to gather latency that more warps hide; 3 (80 registers) for the matrix-free family,
+// which is FP64-bound and spills at 64, and for the M6 instantiations.
+#ifndef MG_CSR_MIN_BLOCKS
+#define MG_CSR_MIN_BLOCKS 4
 #endif
-constexpr int kMinBlocks = MG_PERSIST_MIN_BLOCKS;  // resident CTAs per SM the register budget targets
+template <int FAM, bool HM6>
+constexpr int min_blocks() {
+  return (FAM == FAM_CSR && !HM6) ? MG_CSR_MIN_BLOCKS : 3;
+}
 constexpr int kMaxVec = 64;
 
 
@@ -56,13 +64,17 @@ __device__ __forceinline__ double2 scal2(double s, double2 a) { return make_doub
 // HM6: the instantiation that also carries Method M6 (launched only for MAGNUS_M6, so that its
 // extra code does not weigh on the register budget of the other methods).
 template <int FAM, bool HM6>
-__global__ void __launch_bounds__(kBlock, kMinBlocks) k_magnus_persistent(PersistArgs a) {
+__global__ void __launch_bounds__(kBlock, (min_blocks<FAM, HM6>())) k_magnus_persistent(PersistArgs a) {
   __shared__ Term sT[kMaxTerms];
   __shared__ ExpRec sR;
   __shared__ double s_jb[kMaxSpins], s_j2[kMaxSpins];
   __shared__ double s_vn[kMaxVec], s_ep[kMaxVec], s_pn[kMaxVec];
+  // largest component max(|Re|, |Im|) of the substep input, of p at the stop and of the last w
+  __shared__ double s_vm[kMaxVec], s_pm[kMaxVec], s_wm[kMaxVec];
+  __shared__ double s_wz[kMaxTerms];  // weights of the fixed-point pattern sums: bg_k v_k
   __shared__ int s_act[kMaxVec], s_m[kMaxVec];
   __shared__ double s_red[2][kBlock / 32];
+  __shared__ unsigned s_rmx[2][kBlock / 32];
   __shared__ int s_flag;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -95,48 +107,74 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_magnus_persistent(Persis
   }
 
   unsigned it = 0;  // slot counter of the partial sums: consecutive reductions alternate slots
-  auto block_reduce_store = [&](double x0, double x1) {
+  // per block: two sums and two maxima (high words of non-negative doubles, abshi)
+  auto block_reduce_store = [&](double x0, double x1, unsigned m0, unsigned m1) {
     x0 = warp_sum(x0);
     x1 = warp_sum(x1);
-    if (lane == 0) { s_red[0][warp] = x0; s_red[1][warp] = x1; }
+    m0 = __reduce_max_sync(kFull, m0);
+    m1 = __reduce_max_sync(kFull, m1);
+    if (lane == 0) { s_red[0][warp] = x0; s_red[1][warp] = x1; s_rmx[0][warp] = m0; s_rmx[1][warp] = m1; }
     __syncthreads();
     if (tid == 0) {
       double y0 = 0.0, y1 = 0.0;
-      for (int w = 0; w < kBlock / 32; w++) { y0 += s_red[0][w]; y1 += s_red[1][w]; }
-      double *slot = a.partials + (size_t)(it & 1u) * G * 2;
-      slot[2 * b] = y0;
-      slot[2 * b + 1] = y1;
+      unsigned n0 = 0, n1 = 0;
+      for (int w = 0; w < kBlock / 32; w++) {
+        y0 += s_red[0][w];
+        y1 += s_red[1][w];
+        n0 = max(n0, s_rmx[0][w]);
+        n1 = max(n1, s_rmx[1][w]);
+      }
+      double *slot = a.partials + (size_t)(it & 1u) * G * 4;
+      slot[4 * b] = y0;
+      slot[4 * b + 1] = y1;
+      slot[4 * b + 2] = __hiloint2double((int)n0, 0);
+      slot[4 * b + 3] = __hiloint2double((int)n1, 0);
     }
   };
-  // totals of vector v from the current slot, identical in every block (fixed order)
-  auto vector_totals = [&](int v, double &t0, double &t1) {
-    const double *slot = a.partials + (size_t)(it & 1u) * G * 2;
+  // totals of vector v from the current slot, identical in every block (fixed order), and upper
+  // bounds of its two maxima
+  auto vector_totals = [&](int v, double &t0, double &t1, double *mx0 = nullptr, double *mx1 = nullptr) {
+    const double *slot = a.partials + (size_t)(it & 1u) * G * 4;
     double y0 = 0.0, y1 = 0.0;
+    unsigned n0 = 0, n1 = 0;
     for (int q = lane; q < a.gv; q += 32) {
-      y0 += slot[2 * (v * a.gv + q)];
-      y1 += slot[2 * (v * a.gv + q) + 1];
+      const double *pq = slot + 4 * (v * a.gv + q);
+      y0 += pq[0];
+      y1 += pq[1];
+      n0 = max(n0, (unsigned)__double2hiint(pq[2]));
+      n1 = max(n1, (unsigned)__double2hiint(pq[3]));
     }
     t0 = warp_sum(y0);
     t1 = warp_sum(y1);
+    if (mx0) *mx0 = abshi_bound(__reduce_max_sync(kFull, n0));
+    if (mx1) *mx1 = abshi_bound(__reduce_max_sync(kFull, n1));
   };
   auto fail = [&](int status) {
     if (tid == 0) atomicCAS(&a.counters->status, 0, status);
   };
 
-  // ||psi|| of every vector
+  // ||psi|| and the largest component of every vector
   {
     double s = 0.0;
-    for (int64_t r = lo + tid; r < hi; r += blockDim.x) s += cabs2(a.psi[base + r]);
-    block_reduce_store(s, 0.0);
+    unsigned mx = 0;
+    for (int64_t r = lo + tid; r < hi; r += blockDim.x) {
+      const double2 v = a.psi[base + r];
+      s += cabs2(v);
+      mx = max(mx, abshi(v));
+    }
+    block_reduce_store(s, 0.0, mx, 0);
     // testing hook: CTA 0 leaves before its first barrier (a participant that never arrives), so
     // that every other CTA's bounded wait runs out
     if (a.skip_arrival && b == 0) return;
     if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { fail(MAGNUS_ETIMEOUT); return; }
     if (warp == 0)
       for (int v = 0; v < nv; v++) {
-        double t0, t1;
-        vector_totals(v, t0, t1);
-        if (lane == 0) s_vn[v] = sqrt(t0);
+        double t0, t1, m0;
+        vector_totals(v, t0, t1, &m0);
+        if (lane == 0) {
+          s_vn[v] = sqrt(t0);
+          s_vm[v] = m0;
+        }
       }
     __syncthreads();
     it++;
@@ -151,11 +189,19 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_magnus_persistent(Persis
     const ExpRec &R = sR;
     if (FAM == FAM_MF)
       for (int p = 1 + tid; p < cx.n; p += blockDim.x) s_jb[p - 1] = s_j2[p - 1] * R.bg[0];
+    // fixed-point pattern sums: linear generators of the CSR and matrix-free families
+    const bool zf = FAM != FAM_GENERIC && a.zfix && R.mode == MODE_LINEAR;
+    double opnorm = 0.0;  // sum_k |bg_k| ||H_k||_inf: with |shift|, a bound of ||X - shift||_inf
+    if (zf) {
+      if (tid < nt) s_wz[tid] = R.bg[tid] * sT[tid].pval;
+      for (int k = 0; k < nt; k++) opnorm = fma(fabs(R.bg[k]), sT[k].gnorm, opnorm);
+    }
     const double2 *d = a.dd + e * (int64_t)(a.m_max + 1);
     if (!(R.gamma > 0.0)) {  // scalar generator: a phase
       const double2 ph = d[0];
       for (int64_t r = lo + tid; r < hi; r += blockDim.x) nxt[base + r] = cmul(ph, cur[base + r]);
       if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { fail(MAGNUS_ETIMEOUT); return; }
+      if (tid < nv) s_vm[tid] *= sqrt(cabs2(ph)) * (1.0 + 0x1p-40);
       double2 *tmp = cur; cur = nxt; nxt = tmp;
       if (b == 0 && tid == 0) a.counters->n_exp++;
       continue;
@@ -168,6 +214,12 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_magnus_persistent(Persis
         s_m[tid] = 0;
       }
       __syncthreads();
+      int zs_src = 0;  // scale of the Z copy of this iteration's input
+      if (zf) {        // Z copy of the substep input
+        zs_src = fix_scale(s_vm[vec], a.zhb);
+        for (int64_t r = lo + tid; r < hi; r += blockDim.x) a.zc[base + r] = fix2(cur[base + r], zs_src);
+        if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { fail(MAGNUS_ETIMEOUT); return; }
+      }
       bool done = false;
       int j;
       for (j = 1; j <= a.m_max; j++) {
@@ -269,7 +321,34 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_magnus_persistent(Persis
           if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { fail(MAGNUS_ETIMEOUT); return; }
         }
         double sw = 0.0, sp = 0.0;
-        if (mine) {
+        unsigned mw = 0, mp = 0;
+        int zs_dst = 0;
+        if (zf && mine) {  // linear generator with fixed-point pattern sums
+          // |Re w_j|, |Im w_j| <= ||X - shift||_inf max(|Re w_{j-1}|, |Im w_{j-1}|) (x2 for complex terms)
+          const double msrc = (j == 1) ? s_vm[vec] : s_wm[vec];
+          zs_dst = fix_scale((opnorm + fabs(shift)) * (a.zreal ? 1.0 : 2.0) * msrc * (1.0 + 0x1p-20), a.zhb);
+          const longlong2 *zsrc = ((j == 1) ? a.zc : (((j - 2) & 1) ? a.zw1 : a.zw0)) + base;
+          longlong2 *zdst = (((j - 1) & 1) ? a.zw1 : a.zw0) + base;
+          // p starts as d_0 v in the first iteration: its own loop, so that no other iteration
+          // spends FP64 slots on that product
+          auto rows_z = [&](auto first) {
+            for (int64_t r = lo + tid; r < hi; r += blockDim.x) {
+              double2 wr;
+              const double2 y = Op<FAM>::combo_z(cx, R, s_wz, shift, src + base, zsrc, zs_src, r, wr);
+              dst[base + r] = y;
+              zdst[r] = fix2(y, zs_dst);
+              double2 pr;
+              if constexpr (decltype(first)::value) pr = cmul(d0, wr); else pr = nxt[base + r];
+              pr = cfma(dj, y, pr);
+              nxt[base + r] = pr;
+              sw = fma(y.x, y.x, fma(y.y, y.y, sw));
+              sp = fma(pr.x, pr.x, fma(pr.y, pr.y, sp));
+              mw = max(mw, abshi(y));
+              mp = max(mp, abshi(pr));
+            }
+          };
+          if (j == 1) rows_z(std::true_type{}); else rows_z(std::false_type{});
+        } else if (mine) {
           for (int64_t r = lo + tid; r < hi; r += blockDim.x) {
 
             double2 y, wr;
@@ -320,24 +399,29 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_magnus_persistent(Persis
             nxt[base + r] = pr;
             sw = fma(y.x, y.x, fma(y.y, y.y, sw));
             sp = fma(pr.x, pr.x, fma(pr.y, pr.y, sp));
+            mw = max(mw, abshi(y));  // kept on every path: a later linear generator scales from them
+            mp = max(mp, abshi(pr));
           }
         }
-        block_reduce_store(sw, sp);
+        block_reduce_store(sw, sp, mw, mp);
         if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { fail(MAGNUS_ETIMEOUT); return; }
+        zs_src = zs_dst;
         if (warp == 0) {
           int any = 0, bad = 0;
           const double adj = sqrt(cabs2(dj));
           for (int v = 0; v < nv; v++) {
             if (!s_act[v]) continue;  // uniform across the warp
-            double tw, tp;
-            vector_totals(v, tw, tp);
+            double tw, tp, mxw, mxp;
+            vector_totals(v, tw, tp, &mxw, &mxp);
             if (lane == 0) {
               const double ej = adj * sqrt(tw), pn = sqrt(tp);
+              s_wm[v] = mxw;
               if (!isfinite(ej) || !isfinite(pn)) bad = 1;
               if (ej + s_ep[v] <= a.tol_abs + a.tol_rel * pn) {
                 s_act[v] = 0;
                 s_m[v] = j;
                 s_pn[v] = pn;
+                s_pm[v] = mxp;
               } else {
                 s_ep[v] = ej;
                 any = 1;
@@ -352,7 +436,10 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_magnus_persistent(Persis
         if (s_flag == 1) { done = true; break; }
       }
       if (!done) { fail(MAGNUS_ENOCONV); return; }
-      if (tid < nv) s_vn[tid] = s_pn[tid];
+      if (tid < nv) {
+        s_vn[tid] = s_pn[tid];
+        s_vm[tid] = s_pm[tid];
+      }
       if (b == 0 && tid == 0) {
         Counters *c = a.counters;
         for (int v = 0; v < nv; v++) {
@@ -393,18 +480,10 @@ const void *kernel_for(int fam, bool m6) {
 
 int persistent_block_size() { return kBlock; }
 
-// Smallest occupancy over the families: the grid of any plan fits on the device at once.
-cudaError_t persistent_max_blocks_per_sm(int *n) {
-  int best = 1 << 30;
-  for (int fam = 0; fam < 3; fam++)
-    for (int m6 = 0; m6 < 2; m6++) {
-      int k = 0;
-      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, kernel_for(fam, m6 != 0), kBlock, 0);
-      if (e != cudaSuccess) return e;
-      best = k < best ? k : best;
-    }
-  *n = best;
-  return cudaSuccess;
+// Resident CTAs per SM of the instantiation for this family (and method M6 or not): the largest
+// cooperative grid of that launch.
+cudaError_t persistent_max_blocks_per_sm(int fam, bool m6, int *n) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, kernel_for(fam, m6), kBlock, 0);
 }
 
 cudaError_t launch_persistent(const PersistArgs &a, int grid, int block, bool m6, cudaStream_t st) {

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -17,7 +18,8 @@ using namespace mg;
 struct magnus_plan_s {
   int device = 0;
   int num_sms = 0;
-  int max_blocks_per_sm = 0;
+  int max_blocks_per_sm = 0;             // persistent kernel of the plan's family, linear / M4 generators
+  int max_blocks_m6 = 0;                 // its M6 instantiation
   cudaStream_t stream = nullptr;
   int64_t dim = 0;
   int nterms = 0;
@@ -64,6 +66,10 @@ struct magnus_plan_s {
   Coeff coeff_host[kMaxTerms];           // staging of magnus_set_coeff
   int lbits = 0;
   double *dlo = nullptr, *dhi = nullptr;
+  // exact fixed-point sums of pattern terms: Z copies of the substep input and the Leja vectors
+  longlong2 *zc = nullptr, *zw0 = nullptr, *zw1 = nullptr;
+  int zhb = 0;
+  bool zreal = true;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::string err;
 };
@@ -104,7 +110,7 @@ void free_plan(magnus_plan_t p) {
                   p->hsplit[0], p->hsplit[1], p->hsplit[2], p->hsplit[3], p->sh_cur, p->sh_w0, p->sh_w1, p->sh_u,
                   p->hslice[0], p->hslice[1], p->hslice[2], p->hslice[3], p->hexp[0], p->hexp[1], p->hexp[2],
                   p->hexp[3], p->sl_cur, p->sl_w0, p->sl_w1, p->sl_u, p->ex_sets, p->colmax, p->m6,
-                  p->tc_hd, p->tc_eh, p->tc_wd, p->tc_ex, p->tc_P};
+                  p->tc_hd, p->tc_eh, p->tc_wd, p->tc_ex, p->tc_P, p->zc, p->zw0, p->zw1};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (p->ev0) cudaEventDestroy(p->ev0);
@@ -170,8 +176,8 @@ long long spin_limit(magnus_plan_t p) {
 }
 
 // grid: nvec * gv blocks, all co-resident (cooperative launch)
-void choose_grid(magnus_plan_t p, int *grid, int *gv) {
-  const int maxg = p->num_sms * std::max(1, p->max_blocks_per_sm);
+void choose_grid(magnus_plan_t p, int *grid, int *gv, bool m6 = false) {
+  const int maxg = p->num_sms * std::max(1, m6 ? p->max_blocks_m6 : p->max_blocks_per_sm);
   const int nv = p->opt.nvec;
   int per_vec = std::max(1, maxg / nv);
   if (p->opt.ctas > 0) per_vec = std::max(1, std::min(per_vec, p->opt.ctas / nv));
@@ -196,8 +202,8 @@ magnus_status run_persistent(magnus_plan_t p, void *psi, int64_t nexp, magnus_st
     gv = grid;
     need = (size_t)4 * grid * p->opt.nvec + (size_t)4 * p->opt.nvec;
   } else {
-    choose_grid(p, &grid, &gv);
-    need = (size_t)4 * grid;
+    choose_grid(p, &grid, &gv, m6);
+    need = (size_t)8 * grid;  // two slots x grid x (two sums, two maxima)
   }
   if ((int64_t)need > p->partials_cap) {
     if (p->partials) cudaFree(p->partials);
@@ -293,6 +299,12 @@ magnus_status run_persistent(magnus_plan_t p, void *psi, int64_t nexp, magnus_st
   }
   a.colmax = p->colmax;
   a.m6 = p->m6;
+  a.zfix = p->zc != nullptr;
+  a.zc = p->zc;
+  a.zw0 = p->zw0;
+  a.zw1 = p->zw1;
+  a.zhb = p->zhb;
+  a.zreal = p->zreal;
   CUDA_TRY(p, cudaEventRecord(p->ev0, p->stream));
   if (p->fam == FAM_DENSE)
     CUDA_TRY(p, launch_dense_persistent(a, p->dense_real, grid, p->stream));
@@ -321,6 +333,7 @@ magnus_status run_persistent(magnus_plan_t p, void *psi, int64_t nexp, magnus_st
     stats->kernel_ms = ms;
     stats->grid = grid;
     stats->block = p->fam == FAM_DENSE ? dense_block_size() : persistent_block_size();
+    stats->fixed_sums = a.zfix && !m6 && !m4;
   }
   if (c.status != MAGNUS_OK) {
     const char *what = c.status == MAGNUS_ENOCONV      ? "Leja interpolation did not converge within m_max"
@@ -382,9 +395,11 @@ magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms
   if (nterms < 1 || nterms > kMaxTerms) return set_err(nullptr, MAGNUS_EINVAL, "nterms must be 1..%d", kMaxTerms);
   if (!terms || !coeffs) return set_err(nullptr, MAGNUS_EINVAL, "terms/coeffs are null");
   magnus_options o{1e-10, 1e-10, 4.0, 100, 1, 0, MAGNUS_FP64};
+  o.fixed_sums = 1;
   if (opt) o = *opt;
   if (!(o.tol_rel >= 0.0) || !(o.tol_abs >= 0.0) || !(o.tol_rel + o.tol_abs > 0.0))
     return set_err(nullptr, MAGNUS_EINVAL, "tolerances must be >= 0 and not both 0");
+  if (o.fixed_sums != 0 && o.fixed_sums != 1) return set_err(nullptr, MAGNUS_EINVAL, "fixed_sums must be 0 or 1");
   if (!(o.rho_max > 0.0)) return set_err(nullptr, MAGNUS_EINVAL, "rho_max must be > 0");
   if (!(o.barrier_timeout_s >= 0.0) || o.barrier_timeout_s > 600.0)
     return set_err(nullptr, MAGNUS_EINVAL, "barrier_timeout_s must be in [0, 600]");
@@ -450,7 +465,6 @@ magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms
 
   PLAN_TRY(cudaGetDevice(&p->device));
   PLAN_TRY(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device));
-  PLAN_TRY(persistent_max_blocks_per_sm(&p->max_blocks_per_sm));
   PLAN_TRY(cudaEventCreate(&p->ev0));
   PLAN_TRY(cudaEventCreate(&p->ev1));
 
@@ -514,6 +528,39 @@ magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms
         (p->terms_host[k].kind == MAGNUS_TERM_CSR || p->terms_host[k].kind == MAGNUS_TERM_DENSE) && !fh[k];
   for (int k = 0; k < nterms; k++)
     if (p->terms_host[k].kind == MAGNUS_TERM_DENSE && !p->terms_host[k].real_valued) p->dense_real = false;
+  // pattern terms: real CSR terms with one stored value (summed in fixed point when fixed_sums)
+  {
+    int *pflag = nullptr;
+    unsigned long long *prow = nullptr;
+    PLAN_TRY(dalloc(&pflag, kMaxTerms));
+    PLAN_TRY(dalloc(&prow, kMaxTerms));
+    PLAN_TRY(cudaMemsetAsync(pflag, 0, sizeof(int) * kMaxTerms, p->stream));
+    PLAN_TRY(cudaMemsetAsync(prow, 0, sizeof(unsigned long long) * kMaxTerms, p->stream));
+    double v0[kMaxTerms] = {0.0, 0.0, 0.0, 0.0};
+    for (int k = 0; k < nterms; k++) {
+      const Term &T = p->terms_host[k];
+      if (T.kind != MAGNUS_TERM_CSR || !T.real_valued || T.nnz <= 0) continue;
+      PLAN_TRY(launch_pattern_check(T.rowptr, T.rv, T.rs, dim, pflag + k, prow + k, p->stream));
+      PLAN_TRY(cudaMemcpyAsync(v0 + k, T.rv, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+    }
+    int pf[kMaxTerms] = {1, 1, 1, 1};
+    unsigned long long pr[kMaxTerms] = {0, 0, 0, 0};
+    PLAN_TRY(cudaMemcpyAsync(pf, pflag, sizeof pf, cudaMemcpyDeviceToHost, p->stream));
+    PLAN_TRY(cudaMemcpyAsync(pr, prow, sizeof pr, cudaMemcpyDeviceToHost, p->stream));
+    PLAN_TRY(cudaStreamSynchronize(p->stream));
+    cudaFree(pflag);
+    cudaFree(prow);
+    for (int k = 0; k < nterms; k++) {
+      Term &T = p->terms_host[k];
+      if (T.kind != MAGNUS_TERM_CSR || !T.real_valued || T.nnz <= 0 || (pf[k] & 1)) continue;
+      int bits = 0;
+      while (bits < 40 && (1ull << bits) < pr[k]) bits++;
+      T.pattern = 1;
+      T.pbits = bits;
+      T.pval = v0[k];
+      T.plen = (pf[k] & 2) || pr[k] > (1u << 20) ? 0 : (int)pr[k];
+    }
+  }
   PLAN_TRY(cudaMemcpyAsync(p->terms, p->terms_host, sizeof(Term) * nterms, cudaMemcpyHostToDevice, p->stream));
 
   // operator family of the persistent kernel
@@ -586,12 +633,19 @@ magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms
     }
   }
 
+  if (p->fam != FAM_DENSE) {
+    PLAN_TRY(persistent_max_blocks_per_sm(p->fam, false, &p->max_blocks_per_sm));
+    PLAN_TRY(persistent_max_blocks_per_sm(p->fam, true, &p->max_blocks_m6));
+  }
+
   // Gershgorin enclosures (one pass over every term) and the Leja points
   const int gblk = std::max(1, std::min(p->num_sms * 4, (int)((dim + 255) / 256)));
   double *gscratch = nullptr;
   PLAN_TRY(dalloc(&gscratch, 2 * gblk));
   for (int k = 0; k < nterms; k++)
     PLAN_TRY(launch_gershgorin(p->terms + k, p->terms_host[k], dim, gscratch, gblk, p->term_ab + 2 * k, p->stream));
+  double gab[2 * kMaxTerms] = {0.0};  // the Gershgorin enclosures, before Lanczos narrows them
+  PLAN_TRY(cudaMemcpyAsync(gab, p->term_ab, sizeof(double) * 2 * nterms, cudaMemcpyDeviceToHost, p->stream));
   if (o.interval == MAGNUS_INTERVAL_LANCZOS)
     for (int k = 0; k < nterms; k++)
       PLAN_TRY(lanczos_interval(p->terms + k, p->terms_host[k], dim, kLanczosSteps, p->term_ab + 2 * k, p->stream));
@@ -604,6 +658,35 @@ magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms
       set_err(p, MAGNUS_EINVAL, "term %d: spectral enclosure is not finite (NaN/Inf in the matrix?)", k);
       return fail(MAGNUS_EINVAL);
     }
+  // ||H_k||_inf = max_r (|Re H_rr| + sum_{c != r} |H_rc|) = max(|a_k|, |b_k|) of the Gershgorin
+  // enclosure (real diagonal), widened by 2^-40 for its rounding
+  for (int k = 0; k < nterms; k++)
+    p->terms_host[k].gnorm = std::max(std::fabs(gab[2 * k]), std::fabs(gab[2 * k + 1])) * (1.0 + 0x1p-40);
+  // fixed-point pattern sums: CSR plans with a pattern term, and the matrix-free chain's field
+  if (o.fixed_sums && (p->fam == FAM_CSR || p->fam == FAM_MF)) {
+    int hb = -1;
+    if (p->fam == FAM_MF) {
+      Term &F = p->terms_host[1];
+      int bits = 0;
+      while ((1 << bits) < F.nspins) bits++;
+      F.pattern = 1;
+      F.pbits = bits;
+      F.pval = 1.0;
+      hb = bits;
+    } else {
+      for (int k = 0; k < nterms; k++)
+        if (p->terms_host[k].pattern) hb = std::max(hb, p->terms_host[k].pbits);
+    }
+    if (hb >= 0 && hb <= 30) {
+      p->zhb = hb + 1;  // row sums of up to 2^hb entries of |Z| < 2^(61-hb) stay below 2^61
+      for (int k = 0; k < nterms; k++) p->zreal &= p->fam == FAM_MF || p->terms_host[k].real_valued != 0;
+      PLAN_TRY(dalloc(&p->zc, nd));
+      PLAN_TRY(dalloc(&p->zw0, nd));
+      PLAN_TRY(dalloc(&p->zw1, nd));
+    }
+  }
+  PLAN_TRY(cudaMemcpyAsync(p->terms, p->terms_host, sizeof(Term) * nterms, cudaMemcpyHostToDevice, p->stream));
+  PLAN_TRY(cudaStreamSynchronize(p->stream));
 #undef PLAN_TRY
   *out = p;
   return MAGNUS_OK;
@@ -792,12 +875,12 @@ magnus_status magnus_adjoint_grad(magnus_plan_t p, const void *psi0, const void 
 
   int grid, gv;
   choose_grid(p, &grid, &gv);
-  if ((int64_t)4 * grid > p->partials_cap) {
+  if ((int64_t)8 * grid > p->partials_cap) {
     if (p->partials) cudaFree(p->partials);
     p->partials = nullptr;
     p->partials_cap = 0;
-    CUDA_TRY(p, dalloc(&p->partials, (size_t)4 * grid));
-    p->partials_cap = (int64_t)4 * grid;
+    CUDA_TRY(p, dalloc(&p->partials, (size_t)8 * grid));
+    p->partials_cap = (int64_t)8 * grid;
   }
   cudaStream_t st = p->stream;
   CUDA_TRY(p, launch_exp_setup(variant, t0, h, nsteps, p->nterms, p->coeffs, p->term_ab, p->xi, p->opt.m_max,
@@ -827,6 +910,12 @@ magnus_status magnus_adjoint_grad(magnus_plan_t p, const void *psi0, const void 
   a.lbits = p->lbits;
   a.dlo = p->dlo;
   a.dhi = p->dhi;
+  a.zfix = p->zc != nullptr;
+  a.zc = p->zc;
+  a.zw0 = p->zw0;
+  a.zw1 = p->zw1;
+  a.zhb = p->zhb;
+  a.zreal = p->zreal;
   auto persist = [&](double2 *x, const ExpRec *R, const double2 *DD, int64_t cnt) -> cudaError_t {
     PersistArgs q = a;
     q.recs = R;

@@ -30,6 +30,12 @@ struct Term {
   double J[kMaxSpins];   // XXZ bond couplings J_1..J_{n-1}
   double hz[kMaxSpins];  // XXZ longitudinal fields h_1..h_n
   double delta;          // XXZ zz anisotropy
+  int pattern;           // CSR, real-valued, every stored value equal to pval (sums taken in fixed point)
+  int pbits;             // ceil(log2(longest row)) of a pattern term
+  int plen;              // pattern term whose rows all hold plen entries (rowptr[r] = r plen), else 0
+  int _pad2;
+  double pval;
+  double gnorm;          // upper bound of ||H_k||_inf (max absolute row sum, from the Gershgorin pass)
 };
 
 // Public term (magnus_term) -> storage fields of the internal Term: real-storage kinds become CSR /
@@ -122,6 +128,11 @@ cudaError_t launch_apply(int fam, const Term *terms, int nt, const double *beta,
 // m steps; synchronises the stream
 cudaError_t lanczos_interval(const Term *t_dev, const Term &t_host, int64_t D, int m, double *ab_dev, cudaStream_t st);
 constexpr int kLanczosSteps = 48;
+// Real-valued CSR term (values rv[e * rs], nnz > 0): flag |= 1 unless every stored value equals the
+// first, |= 2 unless every row holds rowmax entries and rowptr[0] = 0; rowmax (device, zeroed by the
+// caller) = longest row.
+cudaError_t launch_pattern_check(const int64_t *rowptr, const double *rv, int rs, int64_t dim, int *flag,
+                                 unsigned long long *rowmax, cudaStream_t st);
 cudaError_t launch_real_parts(const double2 *z, int64_t n, double *out, int *flag, cudaStream_t st);
 // Per-exponential records + divided-difference tables for a whole propagation.
 cudaError_t launch_exp_setup(int variant, double t0, double h, int64_t nsteps, int nterms, const Coeff *coeffs,
@@ -151,7 +162,7 @@ struct PersistArgs {
   double2 *alt;            // second state buffer
   double2 *w0, *w1;        // Leja ping-pong vectors
   double2 *u;              // M4: [nterms][nvec][dim]
-  double *partials;        // [2][grid][2]
+  double *partials;        // [2][grid][4]: two sums and two maxima per block
   GridBar *bar;
   Counters *counters;
   int *mlog;               // [capacity] degrees of the substeps (may be null)
@@ -191,11 +202,16 @@ struct PersistArgs {
   // column-maximum slots of the slicing passes ([4][128], zero at launch): three rotate, the fourth
   // collects the maxima the tcgen05 path gathers in its epilogue
   unsigned long long *colmax;
+  // exact fixed-point sums of pattern terms (FAM_CSR with pattern terms, FAM_MF): Z copies of the
+  // substep input and of the two Leja vectors ([nvec][dim] each), headroom bits of the row sums,
+  // and whether every term is real-valued (then |Re (X w)_r| <= ||X||_inf max |Re w|)
+  longlong2 *zc, *zw0, *zw1;
+  int zfix, zhb, zreal;
 };
 enum { FAM_GENERIC = 0, FAM_CSR = 1, FAM_MF = 2, FAM_DENSE = 3 };
 cudaError_t launch_persistent(const PersistArgs &a, int grid, int block, bool m6, cudaStream_t st);
 int persistent_block_size();
-cudaError_t persistent_max_blocks_per_sm(int *n);
+cudaError_t persistent_max_blocks_per_sm(int fam, bool m6, int *n);
 
 // Dense family (dense terms, optionally with a matrix-free field term): rows of all vectors per block.
 int dense_block_size();

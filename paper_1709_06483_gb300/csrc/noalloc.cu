@@ -36,8 +36,8 @@ constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // Byte layout of the scratch array.
 constexpr size_t kOffVec = 0;                                                   // alt, w0, w1
 constexpr size_t kVecBytes = align256(sizeof(double2) * kStaticMaxDim);
-constexpr size_t kOffPartials = kOffVec + 3 * kVecBytes;                        // [2][grid][2]
-constexpr size_t kOffTerms = kOffPartials + align256(sizeof(double) * 4 * kStaticMaxGrid);
+constexpr size_t kOffPartials = kOffVec + 3 * kVecBytes;                        // [2][grid][4]
+constexpr size_t kOffTerms = kOffPartials + align256(sizeof(double) * 8 * kStaticMaxGrid);
 constexpr size_t kOffTermAB = kOffTerms + align256(sizeof(Term) * 2);
 constexpr size_t kOffXi = kOffTermAB + align256(sizeof(double) * 4);
 constexpr size_t kOffCand = kOffXi + align256(sizeof(double) * (kStaticMmax + 1));
@@ -105,7 +105,7 @@ extern "C" MAGNUS_API magnus_status magnus_expv_xxz_static(int32_t nspins, const
         return fail(MAGNUS_ECUDA, "magnus_expv_xxz_static: cudaGetSymbolAddress failed");
       unsigned char *base = (unsigned char *)ptr;
       if (cudaDeviceGetAttribute(&s.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-          persistent_max_blocks_per_sm(&s.blocks_per_sm) != cudaSuccess)
+          persistent_max_blocks_per_sm(FAM_MF, false, &s.blocks_per_sm) != cudaSuccess)
         return fail(MAGNUS_ECUDA, "magnus_expv_xxz_static: device query failed");
       if (launch_leja_points((double *)(base + kOffXi), kStaticMmax, (double *)(base + kOffCand),
                              (unsigned *)(base + kOffCounter), stream) != cudaSuccess ||

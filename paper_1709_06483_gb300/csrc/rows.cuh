@@ -47,6 +47,61 @@ static __device__ __forceinline__ double2 csr_row_real(const Term &t, const doub
   return acc;
 }
 
+// The same sum with a warp-uniform trip count: every lane runs to the longest row among the warp's
+// active lanes, loads nothing past its own row and adds zeros there.  Rounds of different lengths
+// on different lanes would each take their FP64 slots (1.5x the entries of an XXZ row, whose
+// lengths vary by up to 5 within a warp); this way a warp spends exactly its longest row.  Same
+// entries in the same order as csr_row_real, so the same result.  Call with the warp converged.
+#ifndef MG_CSR_ROUND
+#define MG_CSR_ROUND 8
+#endif
+constexpr int kRound = MG_CSR_ROUND;  // entries per load round of the warp-uniform rows (8 or 4)
+
+template <int RS>
+static __device__ __forceinline__ double2 csr_row_real_w(const Term &t, const double2 *x, int64_t r) {
+  const int64_t e0 = __ldg(t.rowptr + r);
+  const int len = (int)(__ldg(t.rowptr + r + 1) - e0);
+  const int lmax = __reduce_max_sync(__activemask(), len);
+  const int32_t *col = t.col + e0;
+  const double *rv = t.rv + e0 * RS;
+  double2 acc = make_double2(0.0, 0.0);
+  int k = 0;
+  for (; k + kRound <= lmax; k += kRound) {
+    int c[kRound];
+    double a[kRound];
+    double2 xv[kRound];
+#pragma unroll
+    for (int q = 0; q < kRound; q++) c[q] = (k + q < len) ? __ldg(col + k + q) : -1;
+#pragma unroll
+    for (int q = 0; q < kRound; q++) a[q] = (k + q < len) ? __ldg(rv + (k + q) * RS) : 0.0;
+#pragma unroll
+    for (int q = 0; q < kRound; q++) xv[q] = (c[q] >= 0) ? ldv(x + c[q]) : make_double2(0.0, 0.0);
+#pragma unroll
+    for (int q = 0; q < kRound; q++) acc = rfma(a[q], xv[q], acc);
+  }
+  if (kRound == 8 && k + 4 <= lmax) {
+    int c[4];
+    double a[4];
+    double2 xv[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) c[q] = (k + q < len) ? __ldg(col + k + q) : -1;
+#pragma unroll
+    for (int q = 0; q < 4; q++) a[q] = (k + q < len) ? __ldg(rv + (k + q) * RS) : 0.0;
+#pragma unroll
+    for (int q = 0; q < 4; q++) xv[q] = (c[q] >= 0) ? ldv(x + c[q]) : make_double2(0.0, 0.0);
+#pragma unroll
+    for (int q = 0; q < 4; q++) acc = rfma(a[q], xv[q], acc);
+    k += 4;
+  }
+  for (; k < lmax; k++) {
+    const bool in = k < len;
+    const double a = in ? __ldg(rv + k * RS) : 0.0;
+    const double2 v = in ? ldv(x + __ldg(col + k)) : make_double2(0.0, 0.0);
+    acc = rfma(a, v, acc);
+  }
+  return acc;
+}
+
 static __device__ __forceinline__ double2 csr_row(const Term &t, const double2 *x, int64_t r) {
   int64_t e = __ldg(t.rowptr + r);
   const int64_t e1 = __ldg(t.rowptr + r + 1);
@@ -118,6 +173,112 @@ static __device__ __forceinline__ double2 fieldx_row_scaled(int n, double coef, 
     acc = rfma(coef, v3, acc);
   }
   for (; b < n; b++) acc = rfma(coef, ldv(x + (r ^ ((int64_t)1 << b))), acc);
+  return acc;
+}
+
+// ------------------------------------------------ exact fixed-point sums of pattern terms
+// A pattern term stores one value v on every entry (the transverse field sum_i sx_i, an adjacency
+// pattern), so its row is v sum_e x[col_e]: additions only.  On GB300 one FP64 instruction takes
+// the issue time of about 32 integer ones, so these sums run in 64-bit integers, exactly, on a
+// fixed-point copy Z = trunc(x 2^s) of the vector.  Each vector has one scale s, chosen from a
+// bound B >= max_r max(|Re x_r|, |Im x_r|) so that |Z| < 2^(62-hb) and a row sum of up to 2^(hb-1)
+// entries stays below 2^61 (fix_scale); the truncation is below 2^-s < 2^(hb-61) B per component.
+// The row sum goes back to FP64 once, rounded to nearest (unfix).
+
+// scale s for components bounded by B: the smallest e with B < 2^e gives s = 62 - hb - e
+// (clamped to [-900, 1000], where unfix still builds normal doubles; B = 0 takes the largest)
+static __device__ __forceinline__ int fix_scale(double B, int hb) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(B);
+  const int ex = (int)(b >> 52) & 0x7FF;  // B in [2^(ex-1023), 2^(ex-1022)); B < 2^-1022 if ex = 0
+  int s = 62 - hb - (ex - 1022);
+  if (!(B > 0.0)) s = 1000;
+  return min(max(s, -900), 1000);
+}
+
+// trunc(x 2^s) from the bits of x (integer operations only)
+static __device__ __forceinline__ long long fix64(double x, int s) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)(b >> 52) & 0x7FF;
+  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (ex ? 0x10000000000000ull : 0ull);
+  const int sh = max(ex, 1) - 1075 + s;  // x = m 2^(max(ex,1) - 1075)
+  // for |x| <= B the shift is at most 9 to the left; the clamps only keep Inf/NaN shifts defined
+  const unsigned long long v = sh >= 0 ? (m << min(sh, 11)) : (sh > -64 ? (m >> -sh) : 0ull);
+  return (b >> 63) ? -(long long)v : (long long)v;
+}
+static __device__ __forceinline__ longlong2 fix2(double2 v, int s) { return make_longlong2(fix64(v.x, s), fix64(v.y, s)); }
+
+// n 2^-s rounded to the nearest double (ties to even), built from the bits of n
+static __device__ __forceinline__ double unfix(long long n, int s) {
+  const unsigned long long sg = (unsigned long long)n & 0x8000000000000000ull;
+  const unsigned long long a0 = sg ? 0ull - (unsigned long long)n : (unsigned long long)n;
+  const int lz = __clzll((long long)a0);
+  const unsigned long long a = a0 << (lz & 63);  // leading one at bit 63 (a0 != 0)
+  unsigned long long m = a >> 11;                // 53 significant bits
+  const unsigned rb = (unsigned)a & 0x7FFu;      // the 11 bits below them
+  m += (rb > 0x400u || (rb == 0x400u && (m & 1ull))) ? 1ull : 0ull;
+  // value = (m / 2^52) 2^(63 - lz - s); m's leading one (or its carry to 2^53) lands in the exponent
+  const unsigned long long bits = sg | (((unsigned long long)(1085 - lz - s) << 52) + m);
+  return a0 ? __longlong_as_double((long long)bits) : 0.0;
+}
+static __device__ __forceinline__ double2 unfix2(longlong2 n, int s) { return make_double2(unfix(n.x, s), unfix(n.y, s)); }
+
+// High word of max(|Re v|, |Im v|): non-negative doubles order like their bit patterns, so the
+// double with high word h + 1 and low word 0 bounds every value whose high word is at most h.
+static __device__ __forceinline__ unsigned abshi(double2 v) {
+  return max((unsigned)__double2hiint(v.x) & 0x7FFFFFFFu, (unsigned)__double2hiint(v.y) & 0x7FFFFFFFu);
+}
+static __device__ __forceinline__ double abshi_bound(unsigned h) { return __hiloint2double((int)(h + 1u), 0); }
+
+static __device__ __forceinline__ longlong2 ldz(const longlong2 *p) { return __ldca(p); }
+static __device__ __forceinline__ void zadd(longlong2 &acc, longlong2 v) {
+  acc.x += v.x;
+  acc.y += v.y;
+}
+
+// sum_e Z[col_e] over a CSR row, rounds of kRound entries (rows of one length plen start at r plen:
+// no row-pointer load before the column loads)
+static __device__ __forceinline__ longlong2 csr_row_zsum(const Term &t, const longlong2 *z, int64_t r) {
+  int64_t e = t.plen ? r * t.plen : __ldg(t.rowptr + r);
+  const int64_t e1 = t.plen ? e + t.plen : __ldg(t.rowptr + r + 1);
+  longlong2 acc = make_longlong2(0, 0);
+  for (; e + kRound <= e1; e += kRound) {
+    int c[kRound];
+    longlong2 v[kRound];
+#pragma unroll
+    for (int q = 0; q < kRound; q++) c[q] = __ldg(t.col + e + q);
+#pragma unroll
+    for (int q = 0; q < kRound; q++) v[q] = ldz(z + c[q]);
+#pragma unroll
+    for (int q = 0; q < kRound; q++) zadd(acc, v[q]);
+  }
+  if (kRound == 8 && e + 4 <= e1) {
+    int c[4];
+    longlong2 v[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) c[q] = __ldg(t.col + e + q);
+#pragma unroll
+    for (int q = 0; q < 4; q++) v[q] = ldz(z + c[q]);
+#pragma unroll
+    for (int q = 0; q < 4; q++) zadd(acc, v[q]);
+    e += 4;
+  }
+  for (; e < e1; e++) zadd(acc, ldz(z + __ldg(t.col + e)));
+  return acc;
+}
+
+// sum_i Z[r ^ bit_i] (the transverse field)
+static __device__ __forceinline__ longlong2 fieldx_row_zsum(int n, const longlong2 *z, int64_t r) {
+  longlong2 acc = make_longlong2(0, 0);
+  int b = 0;
+  for (; b + 4 <= n; b += 4) {
+    const longlong2 v0 = ldz(z + (r ^ ((int64_t)1 << b))), v1 = ldz(z + (r ^ ((int64_t)2 << b))),
+                    v2 = ldz(z + (r ^ ((int64_t)4 << b))), v3 = ldz(z + (r ^ ((int64_t)8 << b)));
+    zadd(acc, v0);
+    zadd(acc, v1);
+    zadd(acc, v2);
+    zadd(acc, v3);
+  }
+  for (; b < n; b++) zadd(acc, ldz(z + (r ^ ((int64_t)1 << b))));
   return acc;
 }
 
@@ -208,6 +369,29 @@ struct Op {
     for (int k = 0; k < c.nt; k++) y = rfma(R.bg[k], term(c, k, x, r), y);
     xr = ldv(x + r);
     return rfma(-shift, xr, y);
+  }
+  // combo with the pattern terms summed exactly on Z = trunc(x 2^zs) and weighted by wz[k] =
+  // bg_k v_k (FAM_CSR: terms flagged `pattern`; FAM_MF: the transverse field)
+  __device__ static __forceinline__ double2 combo_z(const Ctx &c, const ExpRec &R, const double *wz, double shift,
+                                                    const double2 *x, const longlong2 *z, int zs, int64_t r,
+                                                    double2 &xr) {
+    if constexpr (FAM == FAM_MF) {
+      double2 y = mf_xxz_row(c, c.jb, R.bg[0], shift, x, r, xr);
+      return rfma(wz[1], unfix2(fieldx_row_zsum(c.n, z, r), zs), y);
+    } else {
+      double2 y = make_double2(0.0, 0.0);
+      for (int k = 0; k < c.nt; k++) {
+        const Term &t = c.T[k];
+        if (t.pattern)
+          y = rfma(wz[k], unfix2(csr_row_zsum(t, z, r), zs), y);
+        else if (t.real_valued)
+          y = rfma(R.bg[k], t.rs == 1 ? csr_row_real_w<1>(t, x, r) : csr_row_real_w<2>(t, x, r), y);
+        else
+          y = rfma(R.bg[k], csr_row(t, x, r), y);
+      }
+      xr = ldv(x + r);
+      return rfma(-shift, xr, y);
+    }
   }
 };
 

@@ -449,6 +449,26 @@ __global__ void k_imag_check(const double2 *val, int64_t n, int *flag) {
   if (__any_sync(kFull, any) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
 }
 
+// Pattern check of a real-valued CSR term: flag |= 1 if some stored value differs from the first
+// (or is NaN), |= 2 if some row's length differs from the first row's or rowptr[0] != 0 (rows of
+// one length then start at r * length); rowmax = longest row.
+__global__ void k_pattern_check(const int64_t *rowptr, const double *rv, int rs, int64_t dim, int *flag,
+                                unsigned long long *rowmax) {
+  const double v0 = rv[0];
+  const int64_t len0 = rowptr[1] - rowptr[0];
+  bool differs = false, ragged = rowptr[0] != 0;
+  unsigned long long lmax = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < dim; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e0 = rowptr[i], e1 = rowptr[i + 1];
+    lmax = max(lmax, (unsigned long long)(e1 - e0));
+    ragged |= (e1 - e0) != len0;
+    for (int64_t e = e0; e < e1; e++) differs |= !(rv[e * rs] == v0);
+  }
+  if (__any_sync(kFull, differs) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+  if (__any_sync(kFull, ragged) && (threadIdx.x & 31) == 0) atomicOr(flag, 2);
+  atomicMax(rowmax, lmax);
+}
+
 __global__ void k_real_parts(const double2 *z, int64_t n, double *out, int *flag) {
   bool any = false;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -626,6 +646,12 @@ cudaError_t launch_gershgorin(const Term *t_dev, const Term &t_host, int64_t dim
 
 cudaError_t launch_imag_check(const double2 *val, int64_t n, int *flag, cudaStream_t st) {
   k_imag_check<<<grid_for(n, 256), 256, 0, st>>>(val, n, flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pattern_check(const int64_t *rowptr, const double *rv, int rs, int64_t dim, int *flag,
+                                 unsigned long long *rowmax, cudaStream_t st) {
+  k_pattern_check<<<grid_for(dim, 256), 256, 0, st>>>(rowptr, rv, rs, dim, flag, rowmax);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,185 @@
+"""Exact fixed-point sums of pattern terms (options.fixed_sums) against the FP64 CPU oracle.
+
+A pattern term stores one value on every entry (the transverse field sum_i sx_i, adjacency
+patterns); with fixed_sums its row sums run in 64-bit integers on a fixed-point copy of each Leja
+vector, scaled from a bound on the vector's largest component.  The method's result is unchanged:
+the same tolerance as every other parity test (relative 2-norm error <= 1e-10, identical Leja
+degrees), with the FP64 sums (fixed_sums=False) checked the same way beside it.
+"""
+import numpy as np
+import pytest
+
+import magnus_inputs as mi
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def mg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1709_06483_gb300 as m
+    m.load()
+    return m
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def cuda(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def chain_terms(mg, c, kind):
+    n = c.nspins
+    if kind == "csr":
+        return [mg.build_xxz_csr(n, c.J, c.hz, c.delta), mg.build_field_x_csr(n)]
+    if kind == "csr_real":
+        return [mg.build_xxz_csr(n, c.J, c.hz, c.delta).as_real(), mg.build_field_x_csr(n).as_real()]
+    return [mg.XXZTerm(n, c.J, c.hz, c.delta), mg.FieldXTerm(n)]
+
+
+def drives(mg, c):
+    return [mg.Drive.const(), mg.Drive(c.drive_a0, c.drive_ac, c.drive_as, c.drive_om)]
+
+
+def chain_problem(c, **kw):
+    return oracle.Problem([oracle.xxz_csr(c.nspins, c.J, c.hz, c.delta), oracle.field_x_csr(c.nspins)],
+                          [oracle.Coeff.const(), oracle.Coeff(c.drive_a0, c.drive_ac, c.drive_as, c.drive_om)], **kw)
+
+
+@pytest.mark.parametrize("kind", ["csr", "csr_real", "mfree"])
+@pytest.mark.parametrize("variant", ["CF4", "CF4_3", "M2"])
+def test_fixed_and_fp64_sums_match_oracle(mg, kind, variant):
+    c = mi.xxz_chain(41, 11, 0.01, 30)
+    ost = oracle.Stats(512)
+    ref = chain_problem(c).propagate(c.psi0, 0.0, c.h, c.nsteps, variant, ost)
+    out = {}
+    for fixed in (True, False):
+        plan = mg.Plan(c.dim, chain_terms(mg, c, kind), drives(mg, c), fixed_sums=fixed)
+        psi = cuda(c.psi0)
+        st = plan.propagate(psi, 0.0, c.h, c.nsteps, variant, log_cap=512)
+        assert st["fixed_sums"] == int(fixed)
+        assert np.array_equal(st["m_log"], ost.m_log)
+        out[fixed] = psi.cpu().numpy()
+        assert rel(out[fixed], ref) < REL_TOL, (fixed, rel(out[fixed], ref))
+    # both summations are FP64-accurate: they differ by rounding only
+    assert rel(out[True], out[False]) < 1e-12
+
+
+def test_methods_with_commutators_keep_fp64_sums(mg):
+    """M4 generators take the FP64 sums on the same plan; a later Cf4 call on that plan scales its
+    fixed-point copies from the maxima the M4 call left."""
+    c = mi.xxz_chain(42, 10, 0.01, 12)
+    plan = mg.Plan(c.dim, chain_terms(mg, c, "csr"), drives(mg, c))
+    P = chain_problem(c)
+    psi = cuda(c.psi0)
+    st = plan.propagate(psi, 0.0, c.h, 6, "M4")
+    assert st["fixed_sums"] == 0
+    st = plan.propagate(psi, 6 * c.h, c.h, 6, "CF4")
+    assert st["fixed_sums"] == 1
+    ref = P.propagate(P.propagate(c.psi0, 0.0, c.h, 6, "M4"), 6 * c.h, c.h, 6, "CF4")
+    assert rel(psi.cpu().numpy(), ref) < REL_TOL
+
+
+@pytest.mark.parametrize("kind", ["csr", "mfree"])
+def test_wide_dynamic_range_state(mg, kind):
+    """Components spread over 250 decades: the fixed-point copy resolves the large ones to 2^-55 of
+    the largest and the tiny ones to zero, which leaves the norm-wise error at the FP64 level."""
+    c = mi.xxz_chain(43, 10, 0.01, 10)
+    rng = np.random.default_rng(431)
+    psi0 = c.psi0 * 10.0 ** (-rng.integers(0, 250, c.dim))
+    psi0 /= np.linalg.norm(psi0)
+    ref = chain_problem(c).propagate(psi0, 0.0, c.h, c.nsteps, "CF4")
+    plan = mg.Plan(c.dim, chain_terms(mg, c, kind), drives(mg, c))
+    psi = cuda(psi0)
+    plan.propagate(psi, 0.0, c.h, c.nsteps, "CF4")
+    assert rel(psi.cpu().numpy(), ref) < REL_TOL
+
+
+@pytest.mark.parametrize("kind", ["csr", "mfree"])
+def test_zero_state_stays_zero(mg, kind):
+    c = mi.xxz_chain(44, 8, 0.01, 4)
+    plan = mg.Plan(c.dim, chain_terms(mg, c, kind), drives(mg, c))
+    psi = torch.zeros(c.dim, dtype=torch.complex128, device="cuda")
+    st = plan.propagate(psi, 0.0, c.h, c.nsteps, "CF4")
+    assert st["fixed_sums"] == 1
+    assert not torch.any(psi != 0)
+
+
+def _pattern_csr(rng, D, value, max_degree):
+    """Symmetric pattern with ragged rows (empty ones included, the longest max_degree entries),
+    every stored value `value`."""
+    deg = rng.integers(0, max_degree // 4 + 1, D)
+    A = np.zeros((D, D), dtype=bool)
+    for r in range(D):
+        A[r, rng.choice(D, deg[r], replace=False)] = True
+    A = A | A.T
+    np.fill_diagonal(A, False)
+    empty = rng.choice(D, D // 20, replace=False)
+    rest = np.setdiff1d(np.arange(D), empty)
+    heavy = int(rng.choice(rest))
+    A[empty, :] = A[:, empty] = False
+    A[heavy, :] = A[:, heavy] = False
+    others = rng.choice(np.setdiff1d(rest, [heavy]), max_degree, replace=False)
+    A[heavy, others] = A[others, heavy] = True
+    rows, cols = np.nonzero(A)
+    rowptr = np.zeros(D + 1, dtype=np.int64)
+    np.add.at(rowptr, rows + 1, 1)
+    rowptr = np.cumsum(rowptr)
+    return rowptr, cols.astype(np.int32), np.full(rows.size, value)
+
+
+def _hermitian_csr(rng, D, density):
+    A = np.zeros((D, D), dtype=np.complex128)
+    mask = rng.random((D, D)) < density
+    A[mask] = rng.standard_normal(mask.sum()) + 1j * rng.standard_normal(mask.sum())
+    A = (A + A.conj().T) / 2
+    A[np.diag_indices(D)] = rng.uniform(-2, 2, D)
+    rows, cols = np.nonzero(A)
+    rowptr = np.zeros(D + 1, dtype=np.int64)
+    np.add.at(rowptr, rows + 1, 1)
+    return np.cumsum(rowptr), cols.astype(np.int32), A[rows, cols]
+
+
+@pytest.mark.parametrize("storage", ["complex", "real"])
+def test_ragged_pattern_with_complex_term_odd_dimension(mg, storage):
+    """A pattern term of value 0.7 (rows of 0 to 70 entries) beside a complex Hermitian term, dim
+    1003, 2 states: the pattern is detected, its sums run in fixed point with the complex-term bound."""
+    rng = np.random.default_rng(45)
+    D = 1003
+    prow, pcol, pval = _pattern_csr(rng, D, 0.7, 70)
+    assert np.diff(prow).max() == 70 and np.diff(prow).min() == 0
+    hrow, hcol, hval = _hermitian_csr(rng, D, 0.004)
+    psi0 = np.stack([mi.random_state(rng, D), mi.random_state(rng, D)])
+    f = oracle.Coeff(0.2, [1.0], [0.3], [4.0])
+    P = oracle.Problem([oracle.CSR(hrow, hcol, hval), oracle.CSR(prow, pcol, pval.astype(np.complex128))],
+                       [oracle.Coeff.const(), f])
+    pv = cuda(pval) if storage == "real" else cuda(pval.astype(np.complex128))
+    terms = [mg.CSRTerm(cuda(hrow), cuda(hcol), cuda(hval)), mg.CSRTerm(cuda(prow), cuda(pcol), pv)]
+    plan = mg.Plan(D, terms, [mg.Drive.const(), mg.Drive(0.2, [1.0], [0.3], [4.0])], nvec=2)
+    psi = cuda(psi0)
+    st = plan.propagate(psi, 0.0, 0.05, 10, "CF4")
+    assert st["fixed_sums"] == 1
+    out = psi.cpu().numpy()
+    for v in range(2):
+        ref = P.propagate(psi0[v], 0.0, 0.05, 10, "CF4")
+        assert rel(out[v], ref) < REL_TOL, (v, rel(out[v], ref))
+
+
+def test_no_pattern_term_means_fp64_sums(mg):
+    """A plan whose CSR terms all carry varying values has nothing to sum in fixed point."""
+    rng = np.random.default_rng(46)
+    D = 300
+    h1 = _hermitian_csr(rng, D, 0.01)
+    h2 = _hermitian_csr(rng, D, 0.01)
+    terms = [mg.CSRTerm(cuda(r), cuda(c), cuda(v)) for r, c, v in (h1, h2)]
+    plan = mg.Plan(D, terms, [mg.Drive.const(), mg.Drive(0.0, [1.0], [], [2.0])])
+    psi = cuda(mi.random_state(rng, D))
+    st = plan.propagate(psi, 0.0, 0.05, 2, "CF4")
+    assert st["fixed_sums"] == 0
