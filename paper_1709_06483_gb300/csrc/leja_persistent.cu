@@ -34,15 +34,15 @@ namespace {
 using namespace rows;
 
 constexpr int kBlock = 256;
-// Resident CTAs per SM the register budget targets: 4 (64 registers) for the CSR family, whose
-// time goes to gather latency that more warps hide; 3 (80 registers) for the matrix-free family,
-// which is FP64-bound and spills at 64, and for the M6 instantiations.
+// Resident CTAs per SM the register budget targets: 4 (64 registers) for the CSR family with
+// fixed-point pattern sums, whose time goes to gather latency that more warps hide; 3 (80
+// registers) for the matrix-free family, which is FP64-bound and spills at 64, and for the others.
 #ifndef MG_CSR_MIN_BLOCKS
 #define MG_CSR_MIN_BLOCKS 4
 #endif
-template <int FAM, bool HM6>
+template <int FAM, bool HM6, bool ZF>
 constexpr int min_blocks() {
-  return (FAM == FAM_CSR && !HM6) ? MG_CSR_MIN_BLOCKS : 3;
+  return (FAM == FAM_CSR && ZF) ? MG_CSR_MIN_BLOCKS : 3;
 }
 constexpr int kMaxVec = 64;
 
@@ -62,9 +62,11 @@ __device__ __forceinline__ double2 scal2(double s, double2 a) { return make_doub
 
 // --------------------------------------------------------------------- kernel
 // HM6: the instantiation that also carries Method M6 (launched only for MAGNUS_M6, so that its
-// extra code does not weigh on the register budget of the other methods).
-template <int FAM, bool HM6>
-__global__ void __launch_bounds__(kBlock, (min_blocks<FAM, HM6>())) k_magnus_persistent(PersistArgs a) {
+// extra code does not weigh on the register budget of the other methods).  ZF: the instantiation
+// for linear generators with fixed-point pattern sums (M2, Cf4, Cf4:3 with options.fixed_sums),
+// which carries only that path.
+template <int FAM, bool HM6, bool ZF>
+__global__ void __launch_bounds__(kBlock, (min_blocks<FAM, HM6, ZF>())) k_magnus_persistent(PersistArgs a) {
   __shared__ Term sT[kMaxTerms];
   __shared__ ExpRec sR;
   __shared__ double s_jb[kMaxSpins], s_j2[kMaxSpins];
@@ -190,7 +192,8 @@ __global__ void __launch_bounds__(kBlock, (min_blocks<FAM, HM6>())) k_magnus_per
     if (FAM == FAM_MF)
       for (int p = 1 + tid; p < cx.n; p += blockDim.x) s_jb[p - 1] = s_j2[p - 1] * R.bg[0];
     // fixed-point pattern sums: linear generators of the CSR and matrix-free families
-    const bool zf = FAM != FAM_GENERIC && a.zfix && R.mode == MODE_LINEAR;
+    constexpr bool zf = ZF && FAM != FAM_GENERIC;
+    if (ZF && R.mode != MODE_LINEAR) { fail(MAGNUS_EINVAL); return; }  // the host launches ZF for linear generators only
     double opnorm = 0.0;  // sum_k |bg_k| ||H_k||_inf: with |shift|, a bound of ||X - shift||_inf
     if (zf) {
       if (tid < nt) s_wz[tid] = R.bg[tid] * sT[tid].pval;
@@ -228,7 +231,7 @@ __global__ void __launch_bounds__(kBlock, (min_blocks<FAM, HM6>())) k_magnus_per
         const double shift = R.cg + a.xi[j - 1];
         const double2 dj = d[j];
         const bool mine = s_act[vec] != 0;
-        if (R.mode == MODE_M4) {
+        if (!ZF && R.mode == MODE_M4) {
           // phase 1: u_k = H_k w for this block's rows
           if (mine)
             for (int64_t r = lo + tid; r < hi; r += blockDim.x)
@@ -323,7 +326,8 @@ __global__ void __launch_bounds__(kBlock, (min_blocks<FAM, HM6>())) k_magnus_per
         double sw = 0.0, sp = 0.0;
         unsigned mw = 0, mp = 0;
         int zs_dst = 0;
-        if (zf && mine) {  // linear generator with fixed-point pattern sums
+        if constexpr (zf) {
+         if (mine) {  // linear generator with fixed-point pattern sums
           // |Re w_j|, |Im w_j| <= ||X - shift||_inf max(|Re w_{j-1}|, |Im w_{j-1}|) (x2 for complex terms)
           const double msrc = (j == 1) ? s_vm[vec] : s_wm[vec];
           zs_dst = fix_scale((opnorm + fabs(shift)) * (a.zreal ? 1.0 : 2.0) * msrc * (1.0 + 0x1p-20), a.zhb);
@@ -348,6 +352,7 @@ __global__ void __launch_bounds__(kBlock, (min_blocks<FAM, HM6>())) k_magnus_per
             }
           };
           if (j == 1) rows_z(std::true_type{}); else rows_z(std::false_type{});
+         }
         } else if (mine) {
           for (int64_t r = lo + tid; r < hi; r += blockDim.x) {
 
@@ -461,18 +466,20 @@ __global__ void __launch_bounds__(kBlock, (min_blocks<FAM, HM6>())) k_magnus_per
     for (int64_t r = lo + tid; r < hi; r += blockDim.x) a.psi[base + r] = cur[base + r];
 }
 
-const void *kernel_for(int fam, bool m6) {
+const void *kernel_for(int fam, bool m6, bool zf) {
   if (m6) {
     switch (fam) {
-      case FAM_CSR: return (const void *)k_magnus_persistent<FAM_CSR, true>;
-      case FAM_MF: return (const void *)k_magnus_persistent<FAM_MF, true>;
-      default: return (const void *)k_magnus_persistent<FAM_GENERIC, true>;
+      case FAM_CSR: return (const void *)k_magnus_persistent<FAM_CSR, true, false>;
+      case FAM_MF: return (const void *)k_magnus_persistent<FAM_MF, true, false>;
+      default: return (const void *)k_magnus_persistent<FAM_GENERIC, true, false>;
     }
   }
+  if (zf && fam == FAM_CSR) return (const void *)k_magnus_persistent<FAM_CSR, false, true>;
+  if (zf && fam == FAM_MF) return (const void *)k_magnus_persistent<FAM_MF, false, true>;
   switch (fam) {
-    case FAM_CSR: return (const void *)k_magnus_persistent<FAM_CSR, false>;
-    case FAM_MF: return (const void *)k_magnus_persistent<FAM_MF, false>;
-    default: return (const void *)k_magnus_persistent<FAM_GENERIC, false>;
+    case FAM_CSR: return (const void *)k_magnus_persistent<FAM_CSR, false, false>;
+    case FAM_MF: return (const void *)k_magnus_persistent<FAM_MF, false, false>;
+    default: return (const void *)k_magnus_persistent<FAM_GENERIC, false, false>;
   }
 }
 
@@ -480,16 +487,17 @@ const void *kernel_for(int fam, bool m6) {
 
 int persistent_block_size() { return kBlock; }
 
-// Resident CTAs per SM of the instantiation for this family (and method M6 or not): the largest
-// cooperative grid of that launch.
-cudaError_t persistent_max_blocks_per_sm(int fam, bool m6, int *n) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, kernel_for(fam, m6), kBlock, 0);
+// Resident CTAs per SM of the instantiation for this family (method M6, fixed-point linear
+// generators or the rest): the largest cooperative grid of that launch.
+cudaError_t persistent_max_blocks_per_sm(int fam, bool m6, bool zf, int *n) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, kernel_for(fam, m6, zf), kBlock, 0);
 }
 
 cudaError_t launch_persistent(const PersistArgs &a, int grid, int block, bool m6, cudaStream_t st) {
   PersistArgs copy = a;
   void *args[] = {&copy};
-  return cudaLaunchCooperativeKernel(kernel_for(a.fam, m6), dim3(grid), dim3(block), args, 0, st);
+  return cudaLaunchCooperativeKernel(kernel_for(a.fam, m6, persistent_fixed_kernel(a, m6)), dim3(grid), dim3(block),
+                                     args, 0, st);
 }
 
 }  // namespace mg

@@ -20,6 +20,7 @@ struct magnus_plan_s {
   int num_sms = 0;
   int max_blocks_per_sm = 0;             // persistent kernel of the plan's family, linear / M4 generators
   int max_blocks_m6 = 0;                 // its M6 instantiation
+  int max_blocks_zf = 0;                 // its instantiation with fixed-point pattern sums
   cudaStream_t stream = nullptr;
   int64_t dim = 0;
   int nterms = 0;
@@ -176,8 +177,8 @@ long long spin_limit(magnus_plan_t p) {
 }
 
 // grid: nvec * gv blocks, all co-resident (cooperative launch)
-void choose_grid(magnus_plan_t p, int *grid, int *gv, bool m6 = false) {
-  const int maxg = p->num_sms * std::max(1, m6 ? p->max_blocks_m6 : p->max_blocks_per_sm);
+void choose_grid(magnus_plan_t p, int *grid, int *gv, bool m6 = false, bool zf = false) {
+  const int maxg = p->num_sms * std::max(1, m6 ? p->max_blocks_m6 : (zf ? p->max_blocks_zf : p->max_blocks_per_sm));
   const int nv = p->opt.nvec;
   int per_vec = std::max(1, maxg / nv);
   if (p->opt.ctas > 0) per_vec = std::max(1, std::min(per_vec, p->opt.ctas / nv));
@@ -202,7 +203,7 @@ magnus_status run_persistent(magnus_plan_t p, void *psi, int64_t nexp, magnus_st
     gv = grid;
     need = (size_t)4 * grid * p->opt.nvec + (size_t)4 * p->opt.nvec;
   } else {
-    choose_grid(p, &grid, &gv, m6);
+    choose_grid(p, &grid, &gv, m6, p->zc != nullptr && !m6 && !m4);
     need = (size_t)8 * grid;  // two slots x grid x (two sums, two maxima)
   }
   if ((int64_t)need > p->partials_cap) {
@@ -299,7 +300,7 @@ magnus_status run_persistent(magnus_plan_t p, void *psi, int64_t nexp, magnus_st
   }
   a.colmax = p->colmax;
   a.m6 = p->m6;
-  a.zfix = p->zc != nullptr;
+  a.zfix = p->zc != nullptr && !m6 && !m4;  // linear generators only
   a.zc = p->zc;
   a.zw0 = p->zw0;
   a.zw1 = p->zw1;
@@ -333,7 +334,7 @@ magnus_status run_persistent(magnus_plan_t p, void *psi, int64_t nexp, magnus_st
     stats->kernel_ms = ms;
     stats->grid = grid;
     stats->block = p->fam == FAM_DENSE ? dense_block_size() : persistent_block_size();
-    stats->fixed_sums = a.zfix && !m6 && !m4;
+    stats->fixed_sums = a.zfix;
   }
   if (c.status != MAGNUS_OK) {
     const char *what = c.status == MAGNUS_ENOCONV      ? "Leja interpolation did not converge within m_max"
@@ -634,8 +635,9 @@ magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms
   }
 
   if (p->fam != FAM_DENSE) {
-    PLAN_TRY(persistent_max_blocks_per_sm(p->fam, false, &p->max_blocks_per_sm));
-    PLAN_TRY(persistent_max_blocks_per_sm(p->fam, true, &p->max_blocks_m6));
+    PLAN_TRY(persistent_max_blocks_per_sm(p->fam, false, false, &p->max_blocks_per_sm));
+    PLAN_TRY(persistent_max_blocks_per_sm(p->fam, true, false, &p->max_blocks_m6));
+    PLAN_TRY(persistent_max_blocks_per_sm(p->fam, false, true, &p->max_blocks_zf));
   }
 
   // Gershgorin enclosures (one pass over every term) and the Leja points
@@ -874,7 +876,7 @@ magnus_status magnus_adjoint_grad(magnus_plan_t p, const void *psi0, const void 
   cdev = p->coeffs + kd;
 
   int grid, gv;
-  choose_grid(p, &grid, &gv);
+  choose_grid(p, &grid, &gv, false, p->zc != nullptr);  // the linear generators take the fixed-point kernel
   if ((int64_t)8 * grid > p->partials_cap) {
     if (p->partials) cudaFree(p->partials);
     p->partials = nullptr;

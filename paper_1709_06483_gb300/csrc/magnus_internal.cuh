@@ -209,9 +209,14 @@ struct PersistArgs {
   int zfix, zhb, zreal;
 };
 enum { FAM_GENERIC = 0, FAM_CSR = 1, FAM_MF = 2, FAM_DENSE = 3 };
+// a.zfix (which callers set for linear generators only: M2, Cf4, Cf4:3) selects the instantiation
+// with fixed-point pattern sums.
 cudaError_t launch_persistent(const PersistArgs &a, int grid, int block, bool m6, cudaStream_t st);
+inline bool persistent_fixed_kernel(const PersistArgs &a, bool m6) {
+  return a.zfix && !m6 && (a.fam == FAM_CSR || a.fam == FAM_MF);
+}
 int persistent_block_size();
-cudaError_t persistent_max_blocks_per_sm(int fam, bool m6, int *n);
+cudaError_t persistent_max_blocks_per_sm(int fam, bool m6, bool zf, int *n);
 
 // Dense family (dense terms, optionally with a matrix-free field term): rows of all vectors per block.
 int dense_block_size();
