@@ -435,13 +435,15 @@ def run_batch512(args):
     mg.load()
     chains = mi.workload4()
     probs = []
-    nnz = 0
+    nnz_s = nnz_c = 0  # stored entries of H_s and of sum_i sx_i over all chains
     for c in chains:
         terms = workload_terms(mg, c, args.storage)
         if args.storage.startswith("csr"):
-            nnz += sum(t.col.numel() for t in terms)
+            nnz_s += terms[0].col.numel()
+            nnz_c += terms[1].col.numel()
         probs.append((c.dim, terms, drives(mg, c)))
-    B = mg.Batch(probs)
+    nnz = nnz_s + nnz_c
+    B = mg.Batch(probs, fixed_sums=bool(args.fixed_sums))
     psi0 = [torch.from_numpy(c.psi0).cuda() for c in chains]
     psis = [p.clone() for p in psi0]
     B.propagate(psis, 0.0, 0.01, args.warmup or 1, args.variant)  # autotune + warm-up
@@ -458,17 +460,21 @@ def run_batch512(args):
         wall = time.perf_counter() - t
     gms = st["graph_ms"]
     rows = sum(c.dim for c in chains)
+    fixed = bool(st["fixed_sums"])
     vb = 20 if args.storage == "csr" else 12
-    bytes_it = (vb * nnz + sum(2 * 8 * (c.dim + 1) for c in chains) + 64 * rows if args.storage.startswith("csr")
-                else 64 * rows)
+    # as algorithmic_per_iteration: with fixed sums the field term needs its columns only and the
+    # vectors add the fixed-point copies (32 B per row, and 32 B per row once per substep)
+    vec = 64 * rows + ((32 + 32 * st["n_substeps"] / st["n_matvec"]) * rows if fixed else 0)
+    bytes_it = (vb * nnz_s + (4 if fixed else vb) * nnz_c + sum(2 * 8 * (c.dim + 1) for c in chains) + vec
+                if args.storage.startswith("csr") else vec)
     # Leja iterations differ per chain; algorithmic bytes weighted by each chain's iterations are
     # approximated with the mean iteration count per chain
     iters_per_chain = st["n_matvec"] / len(chains)
     gbs = bytes_it * iters_per_chain / (gms / 1e3) / 1e9
     if args.storage.startswith("csr"):
-        inst_it = 2 * nnz + 14 * rows
+        inst_it = 2 * (nnz_s + (0 if fixed else nnz_c)) + 14 * rows
     else:
-        inst_it = sum(c.dim * (4 + (c.nspins - 1) + 2 * c.nspins + 2) + 10 * c.dim for c in chains)
+        inst_it = sum(c.dim * (4 + (c.nspins - 1) + (0 if fixed else 2 * c.nspins) + 2) + 10 * c.dim for c in chains)
     tflops = 2 * inst_it * iters_per_chain / (gms / 1e3) / 1e12
     peaks = measured_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", HBM_PEAK_FALLBACK))
@@ -479,7 +485,7 @@ def run_batch512(args):
     sample = chains[::16]
     seq_ms = 0.0
     for c in sample:
-        q = mg.Plan(c.dim, workload_terms(mg, c, args.storage), drives(mg, c))
+        q = mg.Plan(c.dim, workload_terms(mg, c, args.storage), drives(mg, c), fixed_sums=bool(args.fixed_sums))
         x = torch.from_numpy(c.psi0).cuda()
         q.propagate(x, 0.0, 0.01, 1, args.variant)
         torch.cuda.synchronize()
@@ -494,23 +500,26 @@ def run_batch512(args):
     line = {
         "metric": METRIC, "value": round(args.steps / (gms / 1e3), 3), "unit": "steps/s (all 512 chains per step)",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(gms / args.steps, 4),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+i64" if fixed else "f64",
+        "data": "synthetic",
         "config": {"workload": f"batch_512_xxz_chains_8to14spins_{args.storage}_{args.variant.lower()}",
                    "chains": len(chains), "rows": rows, "nnz": nnz, "h": 0.01, "variant": args.variant,
-                   "cta_size": st["block"], "cluster_size": st["cluster"]},
+                   "cta_size": st["block"], "cluster_size": st["cluster"],
+                   "sums": "sum_i sx_i rows in exact int64 fixed point, the rest FP64" if fixed else "FP64"},
         "chain_steps_per_s": round(len(chains) * args.steps / (gms / 1e3), 1),
-        "plain_fp64_path": {"steps_per_s": round(seq_rate, 3), "how": f"one plan and launch per chain, {len(sample)} "
-                            f"of 512 chains x {seq_steps} steps, wall time scaled by the chain count "
-                            f"(x {1 / share:.0f})"},
-        "speedup_vs_plain_fp64_path": round(batch_rate / seq_rate, 2),
+        "per_chain_plans": {"steps_per_s": round(seq_rate, 3), "how": f"one plan and launch per chain (same "
+                            f"arithmetic), {len(sample)} of 512 chains x {seq_steps} steps, wall time scaled by the "
+                            f"chain count (x {1 / share:.0f})"},
+        "speedup_vs_per_chain_plans": round(batch_rate / seq_rate, 2),
         "leja_iterations": st["n_matvec"], "matvec_gbs": round(gbs, 1),
-        # FP64-pipe bound like the single-chain kernel (90 % of the pipe busy in ncu): FMA-equivalent
-        # flops per iteration as in algorithmic_per_iteration, summed over the chains
+        # FP64-pipe bound like the single-chain kernel: FMA-equivalent flops per iteration as in
+        # algorithmic_per_iteration, summed over the chains
         "roofline": {"bound": "alu", "kernel": "k_batched", "achieved": round(tflops, 4),
                      "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s", "frac": round(tflops / FP64_PEAK_TFLOPS, 4),
                      "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 4),
-                     "traffic": None, "note": "graph time includes the per-chain setup launches"},
-        "wall_ms": round(wall * 1e3, 2), "gpu_launches": len(chains) + 1, "clocks": clk.summary(),
+                     "traffic": None, "note": "graph time includes the batch's setup launch"},
+        "wall_ms": round(wall * 1e3, 2), "gpu_launches": 2,
+        "gpu_launches_detail": "graph: k_exp_setup_batch + k_batched (plus two memsets)", "clocks": clk.summary(),
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

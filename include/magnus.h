@@ -320,6 +320,8 @@ typedef struct {
   double graph_ms;              /* device time of the replayed graph (setup + persistent kernel)    */
   int32_t block;                /* CTA size the autotuner chose                                     */
   int32_t cluster;              /* CTAs per thread-block cluster (one problem per cluster)          */
+  int32_t fixed_sums;           /* 1 if the pattern-term sums ran in fixed point (options.fixed_sums) */
+  int32_t _pad;
 } magnus_batch_stats;
 
 typedef struct magnus_batch_s *magnus_batch_t;

@@ -75,7 +75,7 @@ class BatchStats(C.Structure):
     _fields_ = [("n_exp", C.c_int64), ("n_substeps", C.c_int64), ("n_matvec", C.c_int64),
                 ("n_termapply", C.c_int64), ("max_m", C.c_int32), ("status", C.c_int32),
                 ("m_log", C.POINTER(C.c_int32)), ("m_log_cap_per_item", C.c_int64), ("graph_ms", C.c_double),
-                ("block", C.c_int32), ("cluster", C.c_int32)]
+                ("block", C.c_int32), ("cluster", C.c_int32), ("fixed_sums", C.c_int32), ("_pad", C.c_int32)]
 
 
 _lib = None
@@ -395,7 +395,7 @@ class Batch:
     """Many independent problems (dim_i, terms_i, drives_i) advanced together in one persistent launch
     under a replayed CUDA graph, with an autotuned CTA size."""
 
-    def __init__(self, problems, tol=1e-10, tol_abs=None, rho_max=4.0, m_max=100, ctas=0):
+    def __init__(self, problems, tol=1e-10, tol_abs=None, rho_max=4.0, m_max=100, ctas=0, fixed_sums=True):
         L = load()
         self._keep = []
         arr = (BatchItem * len(problems))()
@@ -408,7 +408,7 @@ class Batch:
         self.count = len(problems)
         self.dims = [int(p[0]) for p in problems]
         opt = Options(float(tol), float(tol if tol_abs is None else tol_abs), float(rho_max), int(m_max), 1,
-                      int(ctas), FP64, 0.0, 0, 0, 0, 0)
+                      int(ctas), FP64, 0.0, 0, 0, int(bool(fixed_sums)), 0)
         h = C.c_void_p()
         code = L.magnus_batch_create(C.byref(h), self.count, arr, C.byref(opt), None)
         if code != OK:
@@ -442,7 +442,7 @@ class Batch:
         if rc != OK:
             raise MagnusError(rc, L.magnus_batch_last_error(self._h).decode(errors="replace"))
         out = {k: getattr(st, k) for k in ("n_exp", "n_substeps", "n_matvec", "n_termapply", "max_m", "status",
-                                           "graph_ms", "block", "cluster")}
+                                           "graph_ms", "block", "cluster", "fixed_sums")}
         if log is not None:
             out["m_log"] = log
         return out

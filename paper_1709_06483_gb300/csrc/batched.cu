@@ -37,6 +37,9 @@ struct BatchItem {
   double2 *alt, *w0, *w1, *u;
   int *mlog;              // degrees of the substeps, [mlog_cap]
   int mlog_cap;
+  int zhb;                // fixed-point pattern sums: headroom bits of the row sums
+  longlong2 *zc, *zw0, *zw1;  // their copies of the substep input and the Leja vectors (null: FP64 sums)
+  int zreal;              // every term real-valued
   int _pad;
 };
 
@@ -59,8 +62,10 @@ using namespace rows;
 // One problem per thread-block cluster: the cluster's CTAs split the problem's rows, exchange their
 // partial norms through distributed shared memory and synchronise with the hardware cluster
 // barrier (release/acquire at cluster scope), so a large chain runs on several SMs at once.
-// Cluster size 1 is the plain CTA-per-problem case.
-template <int FAM, int BS>
+// Cluster size 1 is the plain CTA-per-problem case.  ZF: the instantiation for linear generators
+// whose pattern terms are summed in fixed point (as in the single-problem kernel); it also
+// tracks the largest component of every vector, from which the fixed-point scales follow.
+template <int FAM, int BS, bool ZF>
 __global__ void __launch_bounds__(BS) k_batched(BatchArgs A) {
   __shared__ int s_next;            // rank 0: the problem index taken from the queue
   __shared__ int s_item;            // every CTA: its copy of that index
@@ -69,37 +74,59 @@ __global__ void __launch_bounds__(BS) k_batched(BatchArgs A) {
   __shared__ ExpRec sR;
   __shared__ double s_jb[kMaxSpins], s_j2[kMaxSpins];
   __shared__ double s_red[2][BS / 32];
-  __shared__ double s_part[2][2];   // this CTA's partial sums, two slots (alternating reductions)
-  __shared__ double s_tot[2];
+  __shared__ unsigned s_rmx[2][BS / 32];
+  __shared__ double s_part[2][4];   // this CTA's partial sums and maxima, two slots (alternating reductions)
+  __shared__ double s_tot[4];       // cluster totals: two sums, then bounds of the two maxima
+  __shared__ double s_wz[kMaxTerms];
 
   cg::cluster_group cl = cg::this_cluster();
   const unsigned crank = cl.block_rank(), csize = cl.num_blocks();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   unsigned slot = 0;
   // sums of two values over all threads of the cluster, identical in every thread afterwards
-  // (fixed order: warps, then CTAs by rank); the cluster barrier also publishes this CTA's
-  // vector writes to the other CTAs of the cluster
-  auto cluster_sums = [&](double x0, double x1) {
+  // (fixed order: warps, then CTAs by rank), and (ZF) bounds of two maxima given as abshi high
+  // words; the cluster barrier also publishes this CTA's vector writes to the other CTAs of the
+  // cluster
+  auto cluster_sums = [&](double x0, double x1, unsigned m0 = 0u, unsigned m1 = 0u) {
     x0 = warp_sum(x0);
     x1 = warp_sum(x1);
-    if (lane == 0) { s_red[0][warp] = x0; s_red[1][warp] = x1; }
+    if (ZF) {
+      m0 = __reduce_max_sync(kFull, m0);
+      m1 = __reduce_max_sync(kFull, m1);
+    }
+    if (lane == 0) {
+      s_red[0][warp] = x0;
+      s_red[1][warp] = x1;
+      if (ZF) { s_rmx[0][warp] = m0; s_rmx[1][warp] = m1; }
+    }
     __syncthreads();
     if (tid == 0) {
       double y0 = 0.0, y1 = 0.0;
-      for (int w = 0; w < BS / 32; w++) { y0 += s_red[0][w]; y1 += s_red[1][w]; }
+      unsigned n0 = 0, n1 = 0;
+      for (int w = 0; w < BS / 32; w++) {
+        y0 += s_red[0][w];
+        y1 += s_red[1][w];
+        if (ZF) { n0 = max(n0, s_rmx[0][w]); n1 = max(n1, s_rmx[1][w]); }
+      }
       s_part[slot][0] = y0;
       s_part[slot][1] = y1;
+      s_part[slot][2] = __hiloint2double((int)n0, 0);
+      s_part[slot][3] = __hiloint2double((int)n1, 0);
     }
     cl.sync();
     if (tid == 0) {
       double y0 = 0.0, y1 = 0.0;
+      unsigned n0 = 0, n1 = 0;
       for (unsigned q = 0; q < csize; q++) {
         const double *rp = cl.map_shared_rank(&s_part[slot][0], q);
         y0 += rp[0];
         y1 += rp[1];
+        if (ZF) { n0 = max(n0, (unsigned)__double2hiint(rp[2])); n1 = max(n1, (unsigned)__double2hiint(rp[3])); }
       }
       s_tot[0] = y0;
       s_tot[1] = y1;
+      s_tot[2] = abshi_bound(n0);
+      s_tot[3] = abshi_bound(n1);
     }
     __syncthreads();
     slot ^= 1u;
@@ -137,9 +164,15 @@ __global__ void __launch_bounds__(BS) k_batched(BatchArgs A) {
       for (int p = 1 + tid; p < cx.n; p += BS) s_j2[p - 1] = 2.0 * sT[0].J[cx.n - p - 1];
 
     double s0 = 0.0;
-    for (int64_t r = lo + tid; r < hi; r += BS) s0 += cabs2(sI.psi[r]);
-    cluster_sums(s0, 0.0);
+    unsigned m0 = 0;
+    for (int64_t r = lo + tid; r < hi; r += BS) {
+      const double2 v = sI.psi[r];
+      s0 += cabs2(v);
+      if (ZF) m0 = max(m0, abshi(v));
+    }
+    cluster_sums(s0, 0.0, m0, 0u);
     double vn = sqrt(s_tot[0]);
+    double vm = s_tot[2];  // ZF: bound of the largest component of the substep input
 
     double2 *cur = sI.psi, *nxt = sI.alt;
     int sub_counter = 0;
@@ -149,8 +182,15 @@ __global__ void __launch_bounds__(BS) k_batched(BatchArgs A) {
       if (tid == 0) sR = sI.recs[e];
       __syncthreads();
       const ExpRec &R = sR;
+      if (ZF && R.mode != MODE_LINEAR) { status = MAGNUS_EINVAL; break; }  // ZF runs linear generators only
       if (FAM == FAM_MF) {
         for (int p = 1 + tid; p < cx.n; p += BS) s_jb[p - 1] = s_j2[p - 1] * R.bg[0];
+        __syncthreads();
+      }
+      double opnorm = 0.0;  // ZF: sum_k |bg_k| ||H_k||_inf
+      if (ZF) {
+        if (tid < nt) s_wz[tid] = R.bg[tid] * sT[tid].pval;
+        for (int k = 0; k < nt; k++) opnorm = fma(fabs(R.bg[k]), sT[k].gnorm, opnorm);
         __syncthreads();
       }
       const double2 *d = sI.dd + e * (int64_t)(A.m_max + 1);
@@ -158,18 +198,56 @@ __global__ void __launch_bounds__(BS) k_batched(BatchArgs A) {
         const double2 ph = d[0];
         for (int64_t r = lo + tid; r < hi; r += BS) nxt[r] = cmul(ph, cur[r]);
         cl.sync();
+        vm *= sqrt(cabs2(ph)) * (1.0 + 0x1p-40);
         double2 *tmp = cur; cur = nxt; nxt = tmp;
         continue;
       }
       const double2 d0 = d[0];
       for (int sub = 0; sub < R.s && status == MAGNUS_OK; sub++) {
-        double ep = sqrt(cabs2(d0)) * vn, pn = vn;
+        double ep = sqrt(cabs2(d0)) * vn, pn = vn, pm = vm, wm = vm;
         int m = 0;
+        int zs_src = 0;
+        if (ZF) {  // fixed-point copy of the substep input
+          zs_src = fix_scale(vm, sI.zhb);
+          for (int64_t r = lo + tid; r < hi; r += BS) sI.zc[r] = fix2(cur[r], zs_src);
+          cl.sync();
+        }
         for (int j = 1; j <= A.m_max; j++) {
           const double2 *src = (j == 1) ? cur : (((j - 2) & 1) ? sI.w1 : sI.w0);
           double2 *dst = ((j - 1) & 1) ? sI.w1 : sI.w0;
           const double shift = R.cg + A.xi[j - 1];
           const double2 dj = d[j];
+          if constexpr (ZF) {
+            // |Re w_j|, |Im w_j| <= ||X - shift||_inf max(|Re w_{j-1}|, |Im w_{j-1}|) (x2 for complex terms)
+            const int zs_dst = fix_scale((opnorm + fabs(shift)) * (sI.zreal ? 1.0 : 2.0) * wm * (1.0 + 0x1p-20), sI.zhb);
+            const longlong2 *zsrc = (j == 1) ? sI.zc : (((j - 2) & 1) ? sI.zw1 : sI.zw0);
+            longlong2 *zdst = ((j - 1) & 1) ? sI.zw1 : sI.zw0;
+            double sw = 0.0, sp = 0.0;
+            unsigned mw = 0, mp = 0;
+            for (int64_t r = lo + tid; r < hi; r += BS) {
+              double2 wr;
+              const double2 y = Op<FAM>::combo_z(cx, R, s_wz, shift, src, zsrc, zs_src, r, wr);
+              dst[r] = y;
+              zdst[r] = fix2(y, zs_dst);
+              double2 pr = (j == 1) ? cmul(d0, wr) : nxt[r];
+              pr = cfma(dj, y, pr);
+              nxt[r] = pr;
+              sw = fma(y.x, y.x, fma(y.y, y.y, sw));
+              sp = fma(pr.x, pr.x, fma(pr.y, pr.y, sp));
+              mw = max(mw, abshi(y));
+              mp = max(mp, abshi(pr));
+            }
+            cluster_sums(sw, sp, mw, mp);
+            zs_src = zs_dst;
+            wm = s_tot[2];
+            pm = s_tot[3];
+            const double ej = sqrt(cabs2(dj)) * sqrt(s_tot[0]);
+            pn = sqrt(s_tot[1]);
+            if (!isfinite(ej) || !isfinite(pn)) { status = MAGNUS_ENONFINITE; m = j; break; }
+            if (ej + ep <= A.tol_abs + A.tol_rel * pn) { m = j; break; }
+            ep = ej;
+            continue;
+          }
           if (R.mode == MODE_M4) {
             for (int64_t r = lo + tid; r < hi; r += BS)
               for (int k = 0; k < nt; k++) sI.u[(size_t)k * D + r] = Op<FAM>::term(cx, k, src, r);
@@ -222,6 +300,7 @@ __global__ void __launch_bounds__(BS) k_batched(BatchArgs A) {
         }
         sub_counter++;
         vn = pn;
+        vm = pm;
         double2 *tmp = cur; cur = nxt; nxt = tmp;
       }
       if (crank == 0 && tid == 0) atomicAdd((unsigned long long *)&A.counters->n_exp, 1ULL);
@@ -235,20 +314,22 @@ __global__ void __launch_bounds__(BS) k_batched(BatchArgs A) {
 }
 
 template <int BS>
-const void *batched_kernel(int fam) {
+const void *batched_kernel(int fam, bool zf) {
+  if (zf && fam == FAM_CSR) return (const void *)k_batched<FAM_CSR, BS, true>;
+  if (zf && fam == FAM_MF) return (const void *)k_batched<FAM_MF, BS, true>;
   switch (fam) {
-    case FAM_CSR: return (const void *)k_batched<FAM_CSR, BS>;
-    case FAM_MF: return (const void *)k_batched<FAM_MF, BS>;
-    default: return (const void *)k_batched<FAM_GENERIC, BS>;
+    case FAM_CSR: return (const void *)k_batched<FAM_CSR, BS, false>;
+    case FAM_MF: return (const void *)k_batched<FAM_MF, BS, false>;
+    default: return (const void *)k_batched<FAM_GENERIC, BS, false>;
   }
 }
 
-const void *batched_kernel_for(int fam, int bs) {
+const void *batched_kernel_for(int fam, int bs, bool zf) {
   switch (bs) {
-    case 128: return batched_kernel<128>(fam);
-    case 512: return batched_kernel<512>(fam);
-    case 1024: return batched_kernel<1024>(fam);
-    default: return batched_kernel<256>(fam);
+    case 128: return batched_kernel<128>(fam, zf);
+    case 512: return batched_kernel<512>(fam, zf);
+    case 1024: return batched_kernel<1024>(fam, zf);
+    default: return batched_kernel<256>(fam, zf);
   }
 }
 
@@ -280,6 +361,10 @@ struct magnus_batch_s {
   Counters *counters = nullptr;
   double2 *scratch = nullptr;     // alt, w0, w1, u per item
   std::vector<size_t> scratch_off;
+  bool zf = false;                // linear generators sum pattern terms in fixed point
+  longlong2 *zscratch = nullptr;  // their copies: substep input, w0, w1 per item (at 3 scratch_z_off[i])
+  std::vector<size_t> zoff;
+  std::vector<int> zhb, zreal;
   int *order = nullptr;
   BatchItem *items_dev = nullptr;
   std::vector<BatchItem> items_host;
@@ -343,6 +428,7 @@ void batch_free(magnus_batch_t b) {
 magnus_status enqueue_run(magnus_batch_t b, int variant, double t0, double h, int64_t nsteps, int bs, int cs,
                           const BatchItem *items_dev) {
   const int64_t nexp = nsteps * exps_per_step(variant);
+  const bool zf = b->zf && variant != MAGNUS_M4;
   BTRY(b, launch_exp_setup_batch(variant, t0, h, nsteps, b->count, b->nterms_dev, b->coeffs, b->term_ab, b->xi,
                                  b->opt.m_max, b->opt.rho_max, b->recs, b->dd, b->recs_cap, b->stream));
   BTRY(b, cudaMemsetAsync(b->next, 0, sizeof(unsigned), b->stream));
@@ -359,7 +445,7 @@ magnus_status enqueue_run(magnus_batch_t b, int variant, double t0, double h, in
   A.next = b->next;
   A.counters = b->counters;
   int per_sm = 0;
-  BTRY(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel_for(b->fam, bs), bs, 0));
+  BTRY(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel_for(b->fam, bs, zf), bs, 0));
   int grid = b->num_sms * std::max(1, per_sm);
   if (b->opt.ctas > 0) grid = std::min(grid, b->opt.ctas);
   grid = std::min(grid, b->count * cs);
@@ -377,7 +463,7 @@ magnus_status enqueue_run(magnus_batch_t b, int variant, double t0, double h, in
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   void *args[] = {&A};
-  BTRY(b, cudaLaunchKernelExC(&cfg, batched_kernel_for(b->fam, bs), args));
+  BTRY(b, cudaLaunchKernelExC(&cfg, batched_kernel_for(b->fam, bs, zf), args));
   return MAGNUS_OK;
 }
 
@@ -394,8 +480,10 @@ MAGNUS_API magnus_status magnus_batch_create(magnus_batch_t *out, int32_t count,
   *out = nullptr;
   if (count < 1 || !items) return berr(nullptr, MAGNUS_EINVAL, "count must be >= 1 with items given");
   magnus_options o{1e-10, 1e-10, 4.0, 100, 1, 0, MAGNUS_FP64};
+  o.fixed_sums = 1;
   if (opt) o = *opt;
   if (o.nvec != 1) return berr(nullptr, MAGNUS_EINVAL, "batch items carry one state each (nvec = 1)");
+  if (o.fixed_sums != 0 && o.fixed_sums != 1) return berr(nullptr, MAGNUS_EINVAL, "fixed_sums must be 0 or 1");
   if (o.precision != MAGNUS_FP64) return berr(nullptr, MAGNUS_EINVAL, "batches use MAGNUS_FP64");
   if (o.interval != MAGNUS_INTERVAL_GERSHGORIN)
     return berr(nullptr, MAGNUS_EINVAL, "batches use MAGNUS_INTERVAL_GERSHGORIN");
@@ -568,6 +656,72 @@ MAGNUS_API magnus_status magnus_batch_create(magnus_batch_t *out, int32_t count,
         berr(b, MAGNUS_EINVAL, "item %d term %d: spectral enclosure not finite", i, k);
         return fail(MAGNUS_EINVAL);
       }
+
+  // fixed-point pattern sums (as for plans): ||H_k||_inf from the Gershgorin enclosures, the
+  // pattern terms (matrix-free transverse fields; real CSR terms with one stored value), and per
+  // item the headroom bits and three Z vectors
+  if (o.fixed_sums && (b->fam == FAM_CSR || b->fam == FAM_MF)) {
+    int *pflag = nullptr;
+    unsigned long long *prow = nullptr;
+    BCREATE(balloc(b, &pflag, (size_t)count * kMaxTerms));
+    BCREATE(balloc(b, &prow, (size_t)count * kMaxTerms));
+    BCREATE(cudaMemsetAsync(pflag, 0, sizeof(int) * count * kMaxTerms, b->stream));
+    BCREATE(cudaMemsetAsync(prow, 0, sizeof(unsigned long long) * count * kMaxTerms, b->stream));
+    std::vector<double> v0((size_t)count * kMaxTerms, 0.0);
+    for (int i = 0; i < count; i++)
+      for (int k = 0; k < b->nterms[i]; k++) {
+        const Term &T = b->terms_host[i][k];
+        if (b->fam != FAM_CSR) continue;
+        const size_t q = (size_t)i * kMaxTerms + k;
+        if (T.kind != MAGNUS_TERM_CSR || !(T.rs == 1 || !fh[q])) continue;  // real-valued CSR only
+        if (T.nnz <= 0) continue;
+        BCREATE(launch_pattern_check(T.rowptr, T.rv, T.rs, b->dims[i], pflag + q, prow + q, b->stream));
+        BCREATE(cudaMemcpyAsync(v0.data() + q, T.rv, sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+      }
+    std::vector<int> pf((size_t)count * kMaxTerms);
+    std::vector<unsigned long long> pr((size_t)count * kMaxTerms);
+    BCREATE(cudaMemcpyAsync(pf.data(), pflag, sizeof(int) * pf.size(), cudaMemcpyDeviceToHost, b->stream));
+    BCREATE(cudaMemcpyAsync(pr.data(), prow, sizeof(unsigned long long) * pr.size(), cudaMemcpyDeviceToHost, b->stream));
+    BCREATE(cudaStreamSynchronize(b->stream));
+    b->zhb.assign(count, 1);
+    b->zreal.assign(count, 1);
+    b->zoff.resize(count);
+    size_t ztotal = 0;
+    for (int i = 0; i < count; i++) {
+      int hb = 0;
+      for (int k = 0; k < b->nterms[i]; k++) {
+        Term &T = b->terms_host[i][k];
+        const size_t q = (size_t)i * kMaxTerms + k;
+        T.gnorm = std::max(std::fabs(ab[2 * q]), std::fabs(ab[2 * q + 1])) * (1.0 + 0x1p-40);
+        int bits = 0;
+        if (b->fam == FAM_MF && k == 1) {
+          while ((1 << bits) < T.nspins) bits++;
+          T.pattern = 1;
+          T.pval = 1.0;
+          T.pbits = bits;
+        } else if (b->fam == FAM_CSR) {
+          T.real_valued = T.kind == MAGNUS_TERM_CSR && (T.rs == 1 || !fh[q]);
+          b->zreal[i] &= T.real_valued ? 1 : 0;
+          if (T.real_valued && T.nnz > 0 && !(pf[q] & 1)) {
+            while (bits < 40 && (1ull << bits) < pr[q]) bits++;
+            T.pattern = 1;
+            T.pval = v0[q];
+            T.pbits = bits;
+            T.plen = (pf[q] & 2) || pr[q] > (1u << 20) ? 0 : (int)pr[q];
+          }
+        }
+        if (T.pattern) hb = std::max(hb, T.pbits);
+      }
+      b->zhb[i] = std::min(hb, 30) + 1;
+      b->zoff[i] = ztotal;
+      ztotal += (size_t)3 * b->dims[i];
+      for (int k = 0; k < kMaxTerms; k++) tflat[(size_t)i * kMaxTerms + k] = b->terms_host[i][k];
+    }
+    BCREATE(balloc(b, &b->zscratch, ztotal));
+    BCREATE(cudaMemcpyAsync(b->terms, tflat.data(), sizeof(Term) * tflat.size(), cudaMemcpyHostToDevice, b->stream));
+    BCREATE(cudaStreamSynchronize(b->stream));
+    b->zf = true;
+  }
 #undef BCREATE
   *out = b;
   return MAGNUS_OK;
@@ -631,6 +785,11 @@ MAGNUS_API magnus_status magnus_batch_propagate(magnus_batch_t b, void *const *p
     I.u = base + 3 * D;
     I.mlog = want_log ? b->mlog + (size_t)i * b->mlog_cap : nullptr;
     I.mlog_cap = want_log ? (int)std::min<int64_t>(b->mlog_cap, 1 << 30) : 0;
+    I.zc = b->zf ? b->zscratch + b->zoff[i] : nullptr;
+    I.zw0 = b->zf ? I.zc + D : nullptr;
+    I.zw1 = b->zf ? I.zc + 2 * D : nullptr;
+    I.zhb = b->zf ? b->zhb[i] : 0;
+    I.zreal = b->zf ? b->zreal[i] : 1;
   }
   BTRY(b, cudaMemcpyAsync(b->items_dev, b->items_host.data(), sizeof(BatchItem) * b->count, cudaMemcpyHostToDevice,
                           b->stream));
@@ -709,6 +868,7 @@ MAGNUS_API magnus_status magnus_batch_propagate(magnus_batch_t b, void *const *p
     stats->graph_ms = ms;
     stats->block = b->tuned_bs;
     stats->cluster = b->tuned_cs;
+    stats->fixed_sums = b->zf && variant != MAGNUS_M4;
     if (want_log) {
       std::vector<int> tmp((size_t)b->count * b->mlog_cap);
       BTRY(b, cudaMemcpyAsync(tmp.data(), b->mlog, sizeof(int) * tmp.size(), cudaMemcpyDeviceToHost, b->stream));

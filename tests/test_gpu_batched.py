@@ -112,3 +112,51 @@ def test_workload4_full_size_sampled(mg):
     for i in (int(np.argmin(dims)), int(np.argmax(dims)), 7, 300):
         ref, _ = oracle_run(chains[i], 0.0, 0.01, 100, "CF4")
         assert rel(psis[i].cpu().numpy(), ref) < REL_TOL, i
+
+
+@pytest.mark.parametrize("kind", ["csr", "csr_real", "mfree"])
+@pytest.mark.parametrize("variant", ["CF4", "CF4_3", "M2"])
+def test_batch_fixed_and_fp64_sums(mg, small_chains, kind, variant):
+    """Linear generators sum the transverse field in fixed point (options.fixed_sums), on every
+    CTA and cluster size the autotuner may pick; FP64 sums beside them; both against the oracle."""
+    chains = small_chains[:8]
+    for fixed in (True, False):
+        B = mg.Batch(problems(mg, chains, kind), fixed_sums=fixed)
+        psis = [torch.from_numpy(c.psi0.copy()).cuda() for c in chains]
+        st = B.propagate(psis, 0.0, chains[0].h, 8, variant, log_cap=128)
+        assert st["fixed_sums"] == int(fixed)
+        for i, c in enumerate(chains):
+            ref, mlog = oracle_run(c, 0.0, c.h, 8, variant)
+            assert rel(psis[i].cpu().numpy(), ref) < REL_TOL, (fixed, i)
+            assert np.array_equal(st["m_log"][i, :mlog.size], mlog), (fixed, i)
+
+
+@pytest.mark.parametrize("cs", [1, 4])
+def test_batch_fixed_sums_m4_then_cf4(mg, small_chains, cs):
+    """M4 keeps FP64 sums in a batch that sums in fixed point; a Cf4 call after it scales its copies
+    from the maxima the M4 launch left (clusters of cs CTAs)."""
+    chains = small_chains[:6]
+    B = mg.Batch(problems(mg, chains, "mfree"), ctas=-(256 + 65536 * cs))
+    psis = [torch.from_numpy(c.psi0.copy()).cuda() for c in chains]
+    h = chains[0].h
+    assert B.propagate(psis, 0.0, h, 4, "M4")["fixed_sums"] == 0
+    assert B.propagate(psis, 4 * h, h, 4, "CF4")["fixed_sums"] == 1
+    for i, c in enumerate(chains):
+        mid, _ = oracle_run(c, 0.0, h, 4, "M4")
+        d = type(c)(**{**c.__dict__, "psi0": mid})
+        ref, _ = oracle_run(d, 4 * h, h, 4, "CF4")
+        assert rel(psis[i].cpu().numpy(), ref) < REL_TOL, i
+
+
+def test_workload4_full_size_sampled_matrix_free(mg):
+    """The 512 chains with matrix-free terms and fixed-point field sums, 100 Cf4 steps; four chains
+    compared with the oracle entry by entry."""
+    chains = mi.workload4()
+    B = mg.Batch(problems(mg, chains, "mfree"))
+    psis = [torch.from_numpy(c.psi0.copy()).cuda() for c in chains]
+    st = B.propagate(psis, 0.0, 0.01, 100, "CF4")
+    assert st["fixed_sums"] == 1 and st["n_exp"] == 512 * 200
+    dims = np.array([c.dim for c in chains])
+    for i in (int(np.argmin(dims)), int(np.argmax(dims)), 11, 400):
+        ref, _ = oracle_run(chains[i], 0.0, 0.01, 100, "CF4")
+        assert rel(psis[i].cpu().numpy(), ref) < REL_TOL, i
