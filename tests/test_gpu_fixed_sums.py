@@ -183,3 +183,41 @@ def test_no_pattern_term_means_fp64_sums(mg):
     psi = cuda(mi.random_state(rng, D))
     st = plan.propagate(psi, 0.0, 0.05, 2, "CF4")
     assert st["fixed_sums"] == 0
+
+
+def _banded_csr(rng, D, wmin, wmax, value=None):
+    """Real symmetric banded matrix, half-bandwidth w_r ~ U{wmin..wmax} per row (ragged rows of
+    moderate spread), all values `value` if given."""
+    A = np.zeros((D, D))
+    for r in range(D):
+        w = int(rng.integers(wmin, wmax + 1))
+        for c in range(max(0, r - w), min(D, r + w + 1)):
+            A[r, c] = A[c, r] = rng.uniform(-1, 1) if value is None else value
+    if value is None:
+        A[np.diag_indices(D)] = rng.uniform(-2, 2, D)
+    rows, cols = np.nonzero(A)
+    rowptr = np.zeros(D + 1, dtype=np.int64)
+    np.add.at(rowptr, rows + 1, 1)
+    return np.cumsum(rowptr), cols.astype(np.int32), A[rows, cols]
+
+
+@pytest.mark.parametrize("D", [1003, 4096])
+def test_ragged_banded_rows_odd_and_even_dimension(mg, D):
+    """A real banded term (rows of 5 to 13 entries: the warp-uniform trip count pads every lane to
+    its warp's longest row) and a ragged banded pattern term of value 0.5 (row pointers loaded), with
+    a partial last warp for dim 1003."""
+    rng = np.random.default_rng(47 + D)
+    h1 = _banded_csr(rng, D, 2, 6)
+    h2 = _banded_csr(rng, D, 1, 3, value=0.5)
+    psi0 = mi.random_state(rng, D)
+    f = oracle.Coeff(0.3, [1.0], [], [2.5])
+    P = oracle.Problem([oracle.CSR(r, c, v.astype(np.complex128)) for r, c, v in (h1, h2)], [oracle.Coeff.const(), f])
+    terms = [mg.CSRTerm(cuda(r), cuda(c), cuda(v)) for r, c, v in (h1, h2)]
+    plan = mg.Plan(D, terms, [mg.Drive.const(), mg.Drive(0.3, [1.0], [], [2.5])])
+    ost = oracle.Stats(256)
+    ref = P.propagate(psi0, 0.0, 0.05, 12, "CF4", ost)
+    psi = cuda(psi0)
+    st = plan.propagate(psi, 0.0, 0.05, 12, "CF4", log_cap=256)
+    assert st["fixed_sums"] == 1
+    assert np.array_equal(st["m_log"], ost.m_log)
+    assert rel(psi.cpu().numpy(), ref) < REL_TOL
