@@ -86,7 +86,8 @@ def algorithmic_per_iteration(c, storage, variant, nnz_terms, fixed=False, subs_
     nnz_terms: stored entries of (H_s, sum_i sx_i) for CSR storage.  fixed: the pattern term
     sum_i sx_i (every stored value 1) is summed in exact 64-bit fixed point (linear generators).
 
-    Bytes, CSR: per stored entry 16 B value (8 B in real storage) + 4 B column, per row 8 B row
+    Bytes, CSR: per stored entry 8 B value + 4 B column (the terms are real-valued: in complex
+    storage the plan multiplies the real parts from a float64 copy it keeps), per row 8 B row
     pointer per term, plus per row 16 B read of w_{j-1}, 16 B write of w_j and 16 + 16 B read and
     write of p; matrix-free: the vector traffic only.  With fixed sums the pattern term needs its
     columns only (4 B per entry), and every row adds the 16 B write of the fixed-point copy of w_j
@@ -120,7 +121,7 @@ def algorithmic_per_iteration(c, storage, variant, nnz_terms, fixed=False, subs_
         vec_bytes += (17 + 23 + 16) * 16 * D
     if storage in ("csr", "csr_real"):
         nnz_s, nnz_c = nnz_terms
-        per_entry = 20 if storage == "csr" else 12
+        per_entry = 12
         mat = per_entry * nnz_s + (4 if fixed else per_entry) * nnz_c + 2 * 8 * (D + 1)
         inst = passes * 2 * (nnz_s + (0 if fixed else nnz_c)) + (4 + 2 + 4 + 4) * D
     else:
@@ -179,7 +180,9 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
-PERSISTENT_SOURCES = ("leja_persistent.cu", "rows.cuh", "persist_common.cuh", "magnus_internal.cuh")
+# sources whose change can change the persistent kernel's DRAM traffic (the kernel, its rows, and the
+# plan set-up that chooses the matrices' layout and the kernel instantiation)
+PERSISTENT_SOURCES = ("leja_persistent.cu", "rows.cuh", "persist_common.cuh", "magnus_internal.cuh", "magnus_api.cu")
 DENSE_TC_SOURCES = ("dense_persistent.cu", "dense_tc.cuh", "tcgen05.cuh", "persist_common.cuh", "magnus_internal.cuh")
 
 
@@ -270,23 +273,45 @@ def run_ours(args):
                  "fp64_tflops": round(tflops, 4), "fp64_frac": round(tflops / FP64_PEAK_TFLOPS, 4),
                  "peak_source": "hbm: MEASURED_PEAKS.json copy; fp64: 152 SMs x 2 FP64 instructions/clk x 2 flops x 2070 MHz (FMA-equivalent flops)"})
 
-    # end-to-end through the public API with host buffers: H2D of psi, one step, D2H of psi
+    # end-to-end through the public API with host buffers: every step copies its input state from
+    # pinned host memory, runs one Magnus step (magnus_propagate, which returns when the step is
+    # done) and copies the result back to pinned host memory.  Two device state buffers: the next
+    # step's input copy and the previous step's result copy run on a copy stream while the current
+    # step computes.
     host_in = torch.from_numpy(c.psi0).pin_memory()
-    host_out = torch.empty_like(host_in).pin_memory()
+    host_out = [torch.empty_like(host_in).pin_memory() for _ in range(2)]
+    bufs = [psi, torch.empty_like(psi)]
+    cstream = torch.cuda.Stream()
+    ready = [torch.cuda.Event() for _ in range(2)]  # input of the step on bufs[i] copied
+    done = [torch.cuda.Event() for _ in range(2)]   # step on bufs[i] finished
     e2e_steps = max(1, min(args.steps, args.e2e_steps))
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
+    e0.record(cstream)
+    with torch.cuda.stream(cstream):
+        bufs[0].copy_(host_in, non_blocking=True)
+        ready[0].record(cstream)
     for n in range(e2e_steps):
-        psi.copy_(host_in, non_blocking=True)  # every step: the step's input from pinned host memory
-        plan.propagate(psi, c.t0 + n * c.h, c.h, 1, variant)
-        host_out.copy_(psi, non_blocking=True)
-    e1.record(stream)
+        i = n % 2
+        stream.wait_event(ready[i])
+        if n + 1 < e2e_steps:  # after the previous result's read of bufs[1 - i] (same copy stream)
+            with torch.cuda.stream(cstream):
+                bufs[1 - i].copy_(host_in, non_blocking=True)
+                ready[1 - i].record(cstream)
+        plan.propagate(bufs[i], c.t0 + n * c.h, c.h, 1, variant)
+        done[i].record(stream)
+        cstream.wait_event(done[i])
+        with torch.cuda.stream(cstream):
+            host_out[i].copy_(bufs[i], non_blocking=True)
+    cstream.wait_stream(stream)
+    e1.record(cstream)
     barrier()
+    cstream.synchronize()
     e2e_ms = e0.elapsed_time(e1)
     e2e = {"value": round(world * e2e_steps / (e2e_ms / 1e3), 3), "unit": "steps/s",
-           "h2d_bytes_per_step": host_in.numel() * 16, "d2h_bytes_per_step": host_out.numel() * 16,
-           "steps": e2e_steps}
+           "h2d_bytes_per_step": host_in.numel() * 16, "d2h_bytes_per_step": host_out[0].numel() * 16,
+           "steps": e2e_steps, "copies": "double-buffered: next input H2D and previous result D2H on a copy "
+           "stream during the current step"}
 
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "steps/s", "n_gpus": world, "steps": args.steps,
@@ -461,7 +486,7 @@ def run_batch512(args):
     gms = st["graph_ms"]
     rows = sum(c.dim for c in chains)
     fixed = bool(st["fixed_sums"])
-    vb = 20 if args.storage == "csr" else 12
+    vb = 12  # real values: complex-stored ones are multiplied from the batch's float64 copy
     # as algorithmic_per_iteration: with fixed sums the field term needs its columns only and the
     # vectors add the fixed-point copies (32 B per row, and 32 B per row once per substep)
     vec = 64 * rows + ((32 + 32 * st["n_substeps"] / st["n_matvec"]) * rows if fixed else 0)
@@ -597,7 +622,8 @@ def run_adjoint16(args):
 def run_spmv20(args):
     """The generator matvec in isolation (magnus_apply): y = (H_s + H_d) x on the 20-spin chain,
     one state; --steps applications timed with CUDA events after --warmup.  Algorithmic bytes per
-    application: CSR 20 B (real storage 12 B) per stored entry + 2 x 8 B row pointers per row + 16 B
+    application: CSR 12 B per stored entry (8 B real value -- a plan keeps complex-stored real values
+    as a float64 copy -- + 4 B column) + 2 x 8 B row pointers per row + 16 B
     read of x (each element once) + 16 B write of y per row; matrix-free 32 B per row.  FP64 work in
     FMA-equivalent flops as in the Leja iteration, without the shift, update and norms."""
     import torch
@@ -629,7 +655,7 @@ def run_spmv20(args):
     D, n = c.dim, c.nspins
     if args.storage.startswith("csr"):
         nnz = sum(t.col.numel() for t in terms)
-        nbytes = (20 if args.storage == "csr" else 12) * nnz + 2 * 8 * (D + 1) + 32 * D
+        nbytes = 12 * nnz + 2 * 8 * (D + 1) + 32 * D  # real values: the plan's float64 copy (csr) or the storage
         inst = 2 * nnz + 4 * D
     else:
         nbytes = 32 * D

@@ -608,11 +608,34 @@ MAGNUS_API magnus_status magnus_batch_create(magnus_batch_t *out, int32_t count,
   BCREATE(cudaStreamSynchronize(b->stream));
   std::vector<Term> tflat((size_t)count * kMaxTerms);
   std::vector<Coeff> cflat((size_t)count * kMaxTerms);
+  // real-valued CSR terms stored as complex128 get a compact float64 copy of their real parts (one
+  // allocation for the whole batch), as plans do
+  size_t ncopy = 0;
   for (int i = 0; i < count; i++)
     for (int k = 0; k < kMaxTerms; k++) {
       Term &T = b->terms_host[i][k];
       T.real_valued = T.kind == MAGNUS_TERM_CSR && (T.rs == 1 || !fh[(size_t)i * kMaxTerms + k]);
-      tflat[(size_t)i * kMaxTerms + k] = T;
+      if (T.real_valued && T.rs == 2 && T.nnz > 0) ncopy += (size_t)T.nnz;
+    }
+  if (ncopy) {
+    double *rc = nullptr;
+    BCREATE(balloc(b, &rc, ncopy));
+    int *rflag = nullptr;
+    BCREATE(balloc(b, &rflag, 1));
+    size_t off = 0;
+    for (int i = 0; i < count; i++)
+      for (int k = 0; k < kMaxTerms; k++) {
+        Term &T = b->terms_host[i][k];
+        if (!(T.real_valued && T.rs == 2 && T.nnz > 0)) continue;
+        BCREATE(launch_real_parts(T.val, T.nnz, rc + off, rflag, b->stream));
+        T.rv = rc + off;
+        T.rs = 1;
+        off += (size_t)T.nnz;
+      }
+  }
+  for (int i = 0; i < count; i++)
+    for (int k = 0; k < kMaxTerms; k++) {
+      tflat[(size_t)i * kMaxTerms + k] = b->terms_host[i][k];
       cflat[(size_t)i * kMaxTerms + k] = b->coeffs_host[i][k];
     }
   BCREATE(cudaMemcpyAsync(b->terms, tflat.data(), sizeof(Term) * tflat.size(), cudaMemcpyHostToDevice, b->stream));
@@ -673,7 +696,7 @@ MAGNUS_API magnus_status magnus_batch_create(magnus_batch_t *out, int32_t count,
         const Term &T = b->terms_host[i][k];
         if (b->fam != FAM_CSR) continue;
         const size_t q = (size_t)i * kMaxTerms + k;
-        if (T.kind != MAGNUS_TERM_CSR || !(T.rs == 1 || !fh[q])) continue;  // real-valued CSR only
+        if (T.kind != MAGNUS_TERM_CSR || !T.real_valued) continue;  // real-valued CSR only
         if (T.nnz <= 0) continue;
         BCREATE(launch_pattern_check(T.rowptr, T.rv, T.rs, b->dims[i], pflag + q, prow + q, b->stream));
         BCREATE(cudaMemcpyAsync(v0.data() + q, T.rv, sizeof(double), cudaMemcpyDeviceToHost, b->stream));
@@ -700,7 +723,6 @@ MAGNUS_API magnus_status magnus_batch_create(magnus_batch_t *out, int32_t count,
           T.pval = 1.0;
           T.pbits = bits;
         } else if (b->fam == FAM_CSR) {
-          T.real_valued = T.kind == MAGNUS_TERM_CSR && (T.rs == 1 || !fh[q]);
           b->zreal[i] &= T.real_valued ? 1 : 0;
           if (T.real_valued && T.nnz > 0 && !(pf[q] & 1)) {
             while (bits < 40 && (1ull << bits) < pr[q]) bits++;

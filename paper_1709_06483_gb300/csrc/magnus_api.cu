@@ -69,6 +69,7 @@ struct magnus_plan_s {
   double *dlo = nullptr, *dhi = nullptr;
   // exact fixed-point sums of pattern terms: Z copies of the substep input and the Leja vectors
   longlong2 *zc = nullptr, *zw0 = nullptr, *zw1 = nullptr;
+  double *rcopy[kMaxTerms] = {nullptr, nullptr, nullptr, nullptr};  // real parts of complex-stored real CSR terms
   int zhb = 0;
   bool zreal = true;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -111,7 +112,8 @@ void free_plan(magnus_plan_t p) {
                   p->hsplit[0], p->hsplit[1], p->hsplit[2], p->hsplit[3], p->sh_cur, p->sh_w0, p->sh_w1, p->sh_u,
                   p->hslice[0], p->hslice[1], p->hslice[2], p->hslice[3], p->hexp[0], p->hexp[1], p->hexp[2],
                   p->hexp[3], p->sl_cur, p->sl_w0, p->sl_w1, p->sl_u, p->ex_sets, p->colmax, p->m6,
-                  p->tc_hd, p->tc_eh, p->tc_wd, p->tc_ex, p->tc_P, p->zc, p->zw0, p->zw1};
+                  p->tc_hd, p->tc_eh, p->tc_wd, p->tc_ex, p->tc_P, p->zc, p->zw0, p->zw1,
+                  p->rcopy[0], p->rcopy[1], p->rcopy[2], p->rcopy[3]};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (p->ev0) cudaEventDestroy(p->ev0);
@@ -529,6 +531,21 @@ magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms
         (p->terms_host[k].kind == MAGNUS_TERM_CSR || p->terms_host[k].kind == MAGNUS_TERM_DENSE) && !fh[k];
   for (int k = 0; k < nterms; k++)
     if (p->terms_host[k].kind == MAGNUS_TERM_DENSE && !p->terms_host[k].real_valued) p->dense_real = false;
+  // real-valued CSR terms stored as complex128: a compact float64 copy of the real parts (the only
+  // part any kernel multiplies), so that a pass reads 8 B per value instead of the 16 B a complex
+  // value's sectors carry
+  for (int k = 0; k < nterms; k++) {
+    Term &T = p->terms_host[k];
+    if (T.kind != MAGNUS_TERM_CSR || !T.real_valued || T.rs != 2 || T.nnz <= 0) continue;
+    int *rflag = nullptr;
+    PLAN_TRY(dalloc(&p->rcopy[k], (size_t)T.nnz));
+    PLAN_TRY(dalloc(&rflag, 1));
+    PLAN_TRY(launch_real_parts(T.val, T.nnz, p->rcopy[k], rflag, p->stream));
+    PLAN_TRY(cudaStreamSynchronize(p->stream));
+    cudaFree(rflag);
+    T.rv = p->rcopy[k];
+    T.rs = 1;
+  }
   // pattern terms: real CSR terms with one stored value (summed in fixed point when fixed_sums)
   {
     int *pflag = nullptr;
