@@ -83,26 +83,31 @@ def drives(mg, c):
 def algorithmic_per_iteration(c, storage, variant, nnz_terms, fixed=False, subs_per_it=0.0):
     """Bytes and FP64 work one Leja iteration needs (real-valued Hamiltonian, complex state).
 
-    nnz_terms: stored entries of (H_s, sum_i sx_i) for CSR storage.  fixed: the pattern term
-    sum_i sx_i (every stored value 1) is summed in exact 64-bit fixed point (linear generators).
+    nnz_terms: stored entries of (H_s, sum_i sx_i) for CSR storage.  fixed: the fixed-point
+    arithmetic of the linear generators: the pattern term sum_i sx_i (every stored value 1) is
+    summed exactly in 64-bit integers, and (CSR) the products of H_s are 62-bit value mantissas
+    times the fixed-point vector.
 
     Bytes, CSR: per stored entry 8 B value + 4 B column (the terms are real-valued: in complex
-    storage the plan multiplies the real parts from a float64 copy it keeps), per row 8 B row
-    pointer per term, plus per row 16 B read of w_{j-1}, 16 B write of w_j and 16 + 16 B read and
-    write of p; matrix-free: the vector traffic only.  With fixed sums the pattern term needs its
-    columns only (4 B per entry), and every row adds the 16 B write of the fixed-point copy of w_j
-    and the 16 B read of that of w_{j-1}; the copy of each substep input costs 16 + 16 B per row
-    once per substep (subs_per_it substeps per iteration).  M4 applies every term twice and writes
-    and reads back u_k (2 x 32 B/row).
+    storage the plan multiplies the real parts from a float64 copy it keeps; in fixed point the
+    value is an 8 B mantissa), per row 8 B row pointer per term, plus per row 16 B read of w_{j-1},
+    16 B write of w_j and 16 + 16 B read and write of p; matrix-free: the vector traffic only.  With
+    fixed-point arithmetic the pattern term needs its columns only (4 B per entry, rows of one length
+    need no row pointers), H_s adds a 2 B row exponent, and every row adds the 16 B write of the
+    fixed-point copy of w_j and the 16 B read of that of w_{j-1}; the copy of each substep input
+    costs 16 + 16 B per row once per substep (subs_per_it substeps per iteration).  M4 applies every
+    term twice and writes and reads back u_k (2 x 32 B/row).
 
     FP64 work is counted in FMA-equivalent flops: every FP64 instruction the method needs (add,
     multiply or fused multiply-add) counts 2, because on GB300 each occupies one slot of the FP64
     pipe (2 per clock per SM, peak 152 x 2 x 2 x 2070 MHz = 1.259 TFLOP/s).  Per row: CSR needs 2
-    instructions per stored entry of a term summed in FP64; the matrix-free XXZ row needs 4 for the
-    diagonal, 2 per active bond ((n-1)/2 on average) and, with FP64 sums, 2 n for the field sum,
-    plus 2 to weight it; both need 4 for the weighted combination (CSR) or none extra
-    (matrix-free), 2 for the shift, 4 for the Newton update of p and 4 for the two squared norms.
-    Fixed-point sums are integer additions, outside the FP64 count.
+    instructions per stored entry of a term multiplied in FP64 (none in fixed point); the
+    matrix-free XXZ row needs 4 for the
+    diagonal, 2 per active bond ((n-1)/2 on average), 2 n for the field sum and 2 to weight it;
+    both need 4 for the weighted combination (CSR) or none extra (matrix-free), 2 for the shift, 4
+    for the Newton update of p and 4 for the two squared norms.  Fixed-point sums and products are
+    integer work, outside the FP64 count: what stays FP64 is 14 instructions per row in both
+    families.
 
     M6 applies every term 17 times per iteration (once per input vector of its five passes and the
     final one); its 23 intermediate vectors are each written once and read back once or twice:
@@ -121,13 +126,21 @@ def algorithmic_per_iteration(c, storage, variant, nnz_terms, fixed=False, subs_
         vec_bytes += (17 + 23 + 16) * 16 * D
     if storage in ("csr", "csr_real"):
         nnz_s, nnz_c = nnz_terms
-        per_entry = 12
-        mat = per_entry * nnz_s + (4 if fixed else per_entry) * nnz_c + 2 * 8 * (D + 1)
-        inst = passes * 2 * (nnz_s + (0 if fixed else nnz_c)) + (4 + 2 + 4 + 4) * D
+        if fixed:
+            mat = 12 * nnz_s + 4 * nnz_c + 8 * (D + 1) + 2 * D
+            inst = (4 + 2 + 4 + 4) * D
+        else:
+            mat = 12 * (nnz_s + nnz_c) + 2 * 8 * (D + 1)
+            inst = passes * 2 * (nnz_s + nnz_c) + (4 + 2 + 4 + 4) * D
+    elif fixed:
+        # matrix-free in fixed point: bonds and field are integer work; FP64 keeps the diagonal (2),
+        # adding it to the converted bond sum (2), weighting the field (2), p (4) and the norms (4)
+        mat = 0
+        inst = (2 + 2 + 2 + 4 + 4) * D
     else:
         n = c.nspins
         mat = 0
-        inst = passes * D * (4 + (n - 1) + (0 if fixed else 2 * n) + 2) + (2 + 4 + 4) * D
+        inst = passes * D * (4 + (n - 1) + 2 * n + 2) + (2 + 4 + 4) * D
     if variant == "M4":
         inst += 8 * D  # commutator difference and its weight
     if variant == "M6":

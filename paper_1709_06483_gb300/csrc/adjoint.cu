@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(kABlock, 2) k_aug_persistent(AugArgs a) {
     reinterpret_cast<int *>(sT)[i] = reinterpret_cast<const int *>(a.terms)[i];
   if (tid == 0) sR = *a.rec;
   __syncthreads();
-  Ctx cx;
+  Ctx cx{};
   cx.T = sT;
   cx.nt = nt;
   cx.n = sT[0].nspins;

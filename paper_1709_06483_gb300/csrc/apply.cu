@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(256) k_apply(const Term *terms, int nt, Beta b
   if (tid == 0)
     for (int k = 0; k < kMaxTerms; k++) sR.bg[k] = (k < nt) ? beta.b[k] : 0.0;
   __syncthreads();
-  Ctx cx;
+  Ctx cx{};
   cx.T = sT;
   cx.nt = nt;
   cx.n = sT[0].nspins;

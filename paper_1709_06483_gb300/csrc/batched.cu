@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(BS) k_batched(BatchArgs A) {
     for (int i = tid; i < nt * (int)sizeof(Term) / 4; i += BS)
       reinterpret_cast<int *>(sT)[i] = reinterpret_cast<const int *>(sI.terms)[i];
     __syncthreads();
-    Ctx cx;
+    Ctx cx{};
     cx.T = sT;
     cx.nt = nt;
     cx.n = sT[0].nspins;

@@ -74,6 +74,8 @@ __global__ void __launch_bounds__(kBlock, (min_blocks<FAM, HM6, ZF>())) k_magnus
   // largest component max(|Re|, |Im|) of the substep input, of p at the stop and of the last w
   __shared__ double s_vm[kMaxVec], s_pm[kMaxVec], s_wm[kMaxVec];
   __shared__ double s_wz[kMaxTerms];  // weights of the fixed-point pattern sums: bg_k v_k
+  __shared__ long long s_cb[kMaxSpins];  // FAM_MF fixed point: bond weights as 62-bit mantissas
+  __shared__ int s_cbe;
   __shared__ int s_act[kMaxVec], s_m[kMaxVec];
   __shared__ double s_red[2][kBlock / 32];
   __shared__ unsigned s_rmx[2][kBlock / 32];
@@ -93,7 +95,7 @@ __global__ void __launch_bounds__(kBlock, (min_blocks<FAM, HM6, ZF>())) k_magnus
   for (int i = tid; i < nt * (int)sizeof(Term) / 4; i += blockDim.x)
     reinterpret_cast<int *>(sT)[i] = reinterpret_cast<const int *>(a.terms)[i];
   __syncthreads();
-  Ctx cx;
+  Ctx cx{};
   cx.T = sT;
   cx.nt = nt;
   cx.n = sT[0].nspins;
@@ -103,6 +105,8 @@ __global__ void __launch_bounds__(kBlock, (min_blocks<FAM, HM6, ZF>())) k_magnus
   cx.dhi = a.dhi;
   cx.jb = s_jb;
   cx.j2 = s_j2;
+  cx.cb = (ZF && FAM == FAM_MF) ? s_cb : nullptr;
+  cx.cbe = 0;
   if (FAM == FAM_MF) {
     // bond at bits (p, p-1) couples spins s = n-p and s+1 with J[s-1] = J[n-p-1]
     for (int p = 1 + tid; p < cx.n; p += blockDim.x) s_j2[p - 1] = 2.0 * sT[0].J[cx.n - p - 1];
@@ -198,6 +202,20 @@ __global__ void __launch_bounds__(kBlock, (min_blocks<FAM, HM6, ZF>())) k_magnus
     if (zf) {
       if (tid < nt) s_wz[tid] = R.bg[tid] * sT[tid].pval;
       for (int k = 0; k < nt; k++) opnorm = fma(fabs(R.bg[k]), sT[k].gnorm, opnorm);
+      if (FAM == FAM_MF) {  // bond weights 2 J bg_0 as mantissas at one exponent: max |w| < 2^s_cbe
+        __syncthreads();
+        if (tid == 0) {
+          double wmax = 0.0;
+          for (int p = 0; p < cx.n - 1; p++) wmax = fmax(wmax, fabs(s_jb[p]));
+          int E = 0;
+          if (wmax > 0.0) frexp(wmax, &E);
+          E = max(-400, min(400, E));
+          for (int p = 0; p < cx.n - 1; p++) s_cb[p] = llrint(ldexp(s_jb[p], 62 - E));
+          s_cbe = E;
+        }
+        __syncthreads();
+        cx.cbe = s_cbe;
+      }
     }
     const double2 *d = a.dd + e * (int64_t)(a.m_max + 1);
     if (!(R.gamma > 0.0)) {  // scalar generator: a phase

@@ -70,6 +70,9 @@ struct magnus_plan_s {
   // exact fixed-point sums of pattern terms: Z copies of the substep input and the Leja vectors
   longlong2 *zc = nullptr, *zw0 = nullptr, *zw1 = nullptr;
   double *rcopy[kMaxTerms] = {nullptr, nullptr, nullptr, nullptr};  // real parts of complex-stored real CSR terms
+  long long *fval[kMaxTerms] = {nullptr, nullptr, nullptr, nullptr};  // fixed-point values of real CSR terms
+  int16_t *fexp[kMaxTerms] = {nullptr, nullptr, nullptr, nullptr};    // and their row exponents
+  unsigned long long rowmax[kMaxTerms] = {0, 0, 0, 0};                // longest row of each real CSR term
   int zhb = 0;
   bool zreal = true;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -113,7 +116,8 @@ void free_plan(magnus_plan_t p) {
                   p->hslice[0], p->hslice[1], p->hslice[2], p->hslice[3], p->hexp[0], p->hexp[1], p->hexp[2],
                   p->hexp[3], p->sl_cur, p->sl_w0, p->sl_w1, p->sl_u, p->ex_sets, p->colmax, p->m6,
                   p->tc_hd, p->tc_eh, p->tc_wd, p->tc_ex, p->tc_P, p->zc, p->zw0, p->zw1,
-                  p->rcopy[0], p->rcopy[1], p->rcopy[2], p->rcopy[3]};
+                  p->rcopy[0], p->rcopy[1], p->rcopy[2], p->rcopy[3], p->fval[0], p->fval[1], p->fval[2],
+                  p->fval[3], p->fexp[0], p->fexp[1], p->fexp[2], p->fexp[3]};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (p->ev0) cudaEventDestroy(p->ev0);
@@ -562,9 +566,9 @@ magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms
       PLAN_TRY(cudaMemcpyAsync(v0 + k, T.rv, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
     }
     int pf[kMaxTerms] = {1, 1, 1, 1};
-    unsigned long long pr[kMaxTerms] = {0, 0, 0, 0};
+    unsigned long long *pr = p->rowmax;
     PLAN_TRY(cudaMemcpyAsync(pf, pflag, sizeof pf, cudaMemcpyDeviceToHost, p->stream));
-    PLAN_TRY(cudaMemcpyAsync(pr, prow, sizeof pr, cudaMemcpyDeviceToHost, p->stream));
+    PLAN_TRY(cudaMemcpyAsync(pr, prow, sizeof(unsigned long long) * kMaxTerms, cudaMemcpyDeviceToHost, p->stream));
     PLAN_TRY(cudaStreamSynchronize(p->stream));
     cudaFree(pflag);
     cudaFree(prow);
@@ -681,9 +685,11 @@ magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms
   // enclosure (real diagonal), widened by 2^-40 for its rounding
   for (int k = 0; k < nterms; k++)
     p->terms_host[k].gnorm = std::max(std::fabs(gab[2 * k]), std::fabs(gab[2 * k + 1])) * (1.0 + 0x1p-40);
-  // fixed-point pattern sums: CSR plans with a pattern term, and the matrix-free chain's field
+  // fixed-point arithmetic: CSR plans with a pattern term (exact sums) or another real CSR term
+  // (products of 62-bit value mantissas and Z), and the matrix-free chain's field
   if (o.fixed_sums && (p->fam == FAM_CSR || p->fam == FAM_MF)) {
-    int hb = -1;
+    int zhb = 0;  // headroom bits of Z: |Z| < 2^(62 - zhb)
+    bool any = false;
     if (p->fam == FAM_MF) {
       Term &F = p->terms_host[1];
       int bits = 0;
@@ -691,17 +697,57 @@ magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms
       F.pattern = 1;
       F.pbits = bits;
       F.pval = 1.0;
-      hb = bits;
+      zhb = bits + 1;
+      any = true;
     } else {
-      for (int k = 0; k < nterms; k++)
-        if (p->terms_host[k].pattern) hb = std::max(hb, p->terms_host[k].pbits);
+      for (int k = 0; k < nterms; k++) {
+        Term &T = p->terms_host[k];
+        if (!T.real_valued || T.nnz <= 0) continue;
+        int bits = 0;  // ceil(log2(longest row))
+        while (bits < 40 && (1ull << bits) < p->rowmax[k]) bits++;
+        if (bits > 30) continue;
+        if (T.pattern) {
+          zhb = std::max(zhb, bits + 1);  // row sums of up to 2^bits entries of |Z| < 2^(61-bits) stay below 2^61
+          any = true;
+        } else {
+          // products: |fval Z| / 2^64 < 2^(60 - zhb); rows of up to 2^bits entries stay below 2^63
+          zhb = std::max(zhb, bits - 2);
+          any = true;
+        }
+      }
+      zhb = std::max(zhb, 1);
     }
-    if (hb >= 0 && hb <= 30) {
-      p->zhb = hb + 1;  // row sums of up to 2^hb entries of |Z| < 2^(61-hb) stay below 2^61
+    if (any) {
+      p->zhb = zhb;
       for (int k = 0; k < nterms; k++) p->zreal &= p->fam == FAM_MF || p->terms_host[k].real_valued != 0;
       PLAN_TRY(dalloc(&p->zc, nd));
       PLAN_TRY(dalloc(&p->zw0, nd));
       PLAN_TRY(dalloc(&p->zw1, nd));
+      // fixed-point values of the real CSR terms that are not patterns
+      if (p->fam == FAM_CSR)
+        for (int k = 0; k < nterms; k++) {
+          Term &T = p->terms_host[k];
+          if (!T.real_valued || T.pattern || T.nnz <= 0 || p->rowmax[k] > (1ull << 30)) continue;
+          int *wide = nullptr;
+          PLAN_TRY(dalloc(&p->fval[k], (size_t)T.nnz));
+          PLAN_TRY(dalloc(&p->fexp[k], (size_t)dim));
+          PLAN_TRY(dalloc(&wide, 1));
+          PLAN_TRY(cudaMemsetAsync(wide, 0, sizeof(int), p->stream));
+          PLAN_TRY(launch_fixed_values(T.rowptr, T.rv, T.rs, dim, p->fval[k], p->fexp[k], wide, p->stream));
+          int wh = 0;
+          PLAN_TRY(cudaMemcpyAsync(&wh, wide, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+          PLAN_TRY(cudaStreamSynchronize(p->stream));
+          cudaFree(wide);
+          if (wh) {  // values beyond the scales' range: this term keeps FP64 products
+            cudaFree(p->fval[k]);
+            cudaFree(p->fexp[k]);
+            p->fval[k] = nullptr;
+            p->fexp[k] = nullptr;
+            continue;
+          }
+          T.fval = p->fval[k];
+          T.fexp = p->fexp[k];
+        }
     }
   }
   PLAN_TRY(cudaMemcpyAsync(p->terms, p->terms_host, sizeof(Term) * nterms, cudaMemcpyHostToDevice, p->stream));

@@ -36,6 +36,10 @@ struct Term {
   int _pad2;
   double pval;
   double gnorm;          // upper bound of ||H_k||_inf (max absolute row sum, from the Gershgorin pass)
+  // fixed-point products (real CSR terms in the fixed-point kernel; null: FP64 products): entry e
+  // of row r as fval[e] = round(a_e 2^(62 - fexp[r])), with max_e |a_e| < 2^fexp[r]
+  const long long *fval;
+  const int16_t *fexp;
 };
 
 // Public term (magnus_term) -> storage fields of the internal Term: real-storage kinds become CSR /
@@ -128,6 +132,12 @@ cudaError_t launch_apply(int fam, const Term *terms, int nt, const double *beta,
 // m steps; synchronises the stream
 cudaError_t lanczos_interval(const Term *t_dev, const Term &t_host, int64_t D, int m, double *ab_dev, cudaStream_t st);
 constexpr int kLanczosSteps = 48;
+// Fixed-point copy of a real CSR term's values (rv[e * rs]): per row r the exponent fexp[r] with
+// max_e |a_e| < 2^fexp[r] (0 for an empty or all-zero row) and fval[e] = round(a_e 2^(62 - fexp[r])).
+// *wide |= 1 (device int, zeroed by the caller) if a row's exponent is outside [-400, 400] or a value
+// is not finite: the copy is then unusable.
+cudaError_t launch_fixed_values(const int64_t *rowptr, const double *rv, int rs, int64_t dim, long long *fval,
+                                int16_t *fexp, int *wide, cudaStream_t st);
 // Real-valued CSR term (values rv[e * rs], nnz > 0): flag |= 1 unless every stored value equals the
 // first, |= 2 unless every row holds rowmax entries and rowptr[0] = 0; rowmax (device, zeroed by the
 // caller) = longest row.

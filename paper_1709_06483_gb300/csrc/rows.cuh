@@ -266,6 +266,45 @@ static __device__ __forceinline__ longlong2 csr_row_zsum(const Term &t, const lo
   return acc;
 }
 
+// sum_e fval[e] Z[col_e] / 2^64 over a CSR row in fixed point (each product's high 64 bits:
+// |fval| < 2^62 and |Z| < 2^(62-hb) keep every product below 2^(60-hb) and the sum exact), with a
+// warp-uniform trip count; returns the sum and, in fe, the row's exponent.  The row's value is
+// sum 2^(fe + 2 - zs) with zs the scale of Z.  Call with the warp converged.
+static __device__ __forceinline__ longlong2 csr_row_zprod_w(const Term &t, const longlong2 *z, int64_t r, int &fe) {
+  const int64_t e0 = __ldg(t.rowptr + r);
+  const int len = (int)(__ldg(t.rowptr + r + 1) - e0);
+  const int lmax = __reduce_max_sync(__activemask(), len);
+  fe = __ldg(t.fexp + r);
+  const int32_t *col = t.col + e0;
+  const long long *fv = t.fval + e0;
+  longlong2 acc = make_longlong2(0, 0);
+  int k = 0;
+  for (; k + kRound <= lmax; k += kRound) {
+    int c[kRound];
+    long long a[kRound];
+    longlong2 v[kRound];
+#pragma unroll
+    for (int q = 0; q < kRound; q++) c[q] = (k + q < len) ? __ldg(col + k + q) : -1;
+#pragma unroll
+    for (int q = 0; q < kRound; q++) a[q] = (k + q < len) ? __ldg(fv + k + q) : 0ll;
+#pragma unroll
+    for (int q = 0; q < kRound; q++) v[q] = (c[q] >= 0) ? ldz(z + c[q]) : make_longlong2(0, 0);
+#pragma unroll
+    for (int q = 0; q < kRound; q++) {
+      acc.x += __mul64hi(a[q], v[q].x);
+      acc.y += __mul64hi(a[q], v[q].y);
+    }
+  }
+  for (; k < lmax; k++) {
+    const bool in = k < len;
+    const long long a = in ? __ldg(fv + k) : 0ll;
+    const longlong2 v = in ? ldz(z + __ldg(col + k)) : make_longlong2(0, 0);
+    acc.x += __mul64hi(a, v.x);
+    acc.y += __mul64hi(a, v.y);
+  }
+  return acc;
+}
+
 // sum_i Z[r ^ bit_i] (the transverse field)
 static __device__ __forceinline__ longlong2 fieldx_row_zsum(int n, const longlong2 *z, int64_t r) {
   longlong2 acc = make_longlong2(0, 0);
@@ -301,6 +340,8 @@ struct Ctx {
   const double *dlo, *dhi;
   const double *jb;   // shared: 2 J_bond * bg[0] per bond, bond at bits (p, p-1) stored at p-1
   const double *j2;   // shared: 2 J_bond (unscaled), same indexing
+  const long long *cb;  // shared (fixed-point kernel): jb as 62-bit mantissas, cb = round(jb 2^(62 - cbe))
+  int cbe;              // with max |jb| < 2^cbe
 };
 
 // H_xxz row with the diagonal from the two tables (FAM_MF).  coefj: per-bond coefficients.
@@ -344,6 +385,47 @@ static __device__ __forceinline__ double2 mf_xxz_row(const Ctx &c, const double 
   return acc;
 }
 
+// The same row with the bond flips taken in fixed point: each active bond adds the high 64 bits of
+// cb[b] Z[r ^ (3 << b)] (|cb| < 2^62, |Z| < 2^(62-hb)), exactly summed in int64, and the sum goes back
+// to FP64 once; the diagonal stays FP64.  Same visiting order as mf_xxz_row.
+static __device__ __forceinline__ double2 mf_xxz_row_z(const Ctx &c, double dscale, double dshift, const double2 *x,
+                                                const longlong2 *z, int zs, int64_t r, double2 &xr) {
+  xr = ldv(x + r);
+  const double dg = __ldg(c.dhi + (r >> c.lbits)) + __ldg(c.dlo + (r & c.lomask));
+  const double cr = fma(dscale, dg, -dshift);
+  const int nb = c.n - 1;
+  const unsigned mine = (unsigned)((r ^ (r >> 1)) & (((int64_t)1 << nb) - 1));
+  unsigned mw = __reduce_or_sync(__activemask(), mine);
+  longlong2 acc = make_longlong2(0, 0);
+  while (__popc(mw) >= 4) {
+    int bq[4];
+    longlong2 v[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      bq[q] = __ffs(mw) - 1;
+      mw &= mw - 1;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; q++) v[q] = ldz(z + (r ^ ((int64_t)3 << bq[q])));
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const long long w = ((mine >> bq[q]) & 1u) ? c.cb[bq[q]] : 0ll;
+      acc.x += __mul64hi(w, v[q].x);
+      acc.y += __mul64hi(w, v[q].y);
+    }
+  }
+  while (mw) {
+    const int b = __ffs(mw) - 1;
+    mw &= mw - 1;
+    const longlong2 v = ldz(z + (r ^ ((int64_t)3 << b)));
+    const long long w = ((mine >> b) & 1u) ? c.cb[b] : 0ll;
+    acc.x += __mul64hi(w, v.x);
+    acc.y += __mul64hi(w, v.y);
+  }
+  const double2 bonds = unfix2(acc, zs - c.cbe - 2);
+  return make_double2(fma(cr, xr.x, bonds.x), fma(cr, xr.y, bonds.y));
+}
+
 template <int FAM>
 struct Op {
   // (H_k x)[r]
@@ -376,15 +458,19 @@ struct Op {
                                                     const double2 *x, const longlong2 *z, int zs, int64_t r,
                                                     double2 &xr) {
     if constexpr (FAM == FAM_MF) {
-      double2 y = mf_xxz_row(c, c.jb, R.bg[0], shift, x, r, xr);
+      double2 y = c.cb ? mf_xxz_row_z(c, R.bg[0], shift, x, z, zs, r, xr) : mf_xxz_row(c, c.jb, R.bg[0], shift, x, r, xr);
       return rfma(wz[1], unfix2(fieldx_row_zsum(c.n, z, r), zs), y);
     } else {
       double2 y = make_double2(0.0, 0.0);
       for (int k = 0; k < c.nt; k++) {
         const Term &t = c.T[k];
-        if (t.pattern)
+        if (t.pattern) {
           y = rfma(wz[k], unfix2(csr_row_zsum(t, z, r), zs), y);
-        else if (t.real_valued)
+        } else if (t.fval) {
+          int fe;
+          const longlong2 hs = csr_row_zprod_w(t, z, r, fe);
+          y = rfma(R.bg[k], unfix2(hs, zs - fe - 2), y);
+        } else if (t.real_valued)
           y = rfma(R.bg[k], t.rs == 1 ? csr_row_real_w<1>(t, x, r) : csr_row_real_w<2>(t, x, r), y);
         else
           y = rfma(R.bg[k], csr_row(t, x, r), y);

@@ -469,6 +469,23 @@ __global__ void k_pattern_check(const int64_t *rowptr, const double *rv, int rs,
   atomicMax(rowmax, lmax);
 }
 
+// one thread per row: the row's exponent, then its entries as 62-bit signed mantissas at that scale
+__global__ void k_fixed_values(const int64_t *rowptr, const double *rv, int rs, int64_t dim, long long *fval,
+                               int16_t *fexp, int *wide) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < dim; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e0 = rowptr[i], e1 = rowptr[i + 1];
+    double amax = 0.0;
+    for (int64_t e = e0; e < e1; e++) amax = fmax(amax, fabs(rv[e * rs]));
+    int E = 0;
+    if (amax > 0.0) {
+      frexp(amax, &E);  // amax = f 2^E, f in [0.5, 1): amax < 2^E
+    }
+    if (E > 400 || E < -400 || !(amax <= 1.7e308)) atomicOr(wide, 1);  // outside the range the scales cover
+    fexp[i] = (int16_t)max(-400, min(400, E));
+    for (int64_t e = e0; e < e1; e++) fval[e] = llrint(ldexp(rv[e * rs], 62 - E));
+  }
+}
+
 __global__ void k_real_parts(const double2 *z, int64_t n, double *out, int *flag) {
   bool any = false;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -652,6 +669,12 @@ cudaError_t launch_imag_check(const double2 *val, int64_t n, int *flag, cudaStre
 cudaError_t launch_pattern_check(const int64_t *rowptr, const double *rv, int rs, int64_t dim, int *flag,
                                  unsigned long long *rowmax, cudaStream_t st) {
   k_pattern_check<<<grid_for(dim, 256), 256, 0, st>>>(rowptr, rv, rs, dim, flag, rowmax);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fixed_values(const int64_t *rowptr, const double *rv, int rs, int64_t dim, long long *fval,
+                                int16_t *fexp, int *wide, cudaStream_t st) {
+  k_fixed_values<<<grid_for(dim, 256), 256, 0, st>>>(rowptr, rv, rs, dim, fval, fexp, wide);
   return cudaGetLastError();
 }
 

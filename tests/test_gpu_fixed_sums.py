@@ -221,3 +221,65 @@ def test_ragged_banded_rows_odd_and_even_dimension(mg, D):
     assert st["fixed_sums"] == 1
     assert np.array_equal(st["m_log"], ost.m_log)
     assert rel(psi.cpu().numpy(), ref) < REL_TOL
+
+
+def _random_real_csr(rng, D, density, decades):
+    """Real symmetric CSR with values of random sign spread over 2 x decades decades around 1, some
+    rows empty (the diagonal too)."""
+    A = np.zeros((D, D))
+    mask = rng.random((D, D)) < density
+    A[mask] = rng.choice([-1.0, 1.0], mask.sum()) * 10.0 ** rng.uniform(-decades, decades, mask.sum())
+    A = (A + A.T) / 2
+    empty = rng.choice(D, D // 25, replace=False)
+    A[empty, :] = 0.0
+    A[:, empty] = 0.0
+    rows, cols = np.nonzero(A)
+    rowptr = np.zeros(D + 1, dtype=np.int64)
+    np.add.at(rowptr, rows + 1, 1)
+    return np.cumsum(rowptr), cols.astype(np.int32), A[rows, cols]
+
+
+@pytest.mark.parametrize("decades", [0.5, 8.0])
+def test_fixed_point_products_wide_value_range(mg, decades):
+    """Real CSR values spread over up to 16 decades inside a row (row-scaled 62-bit mantissas times
+    the fixed-point vector), beside a pattern term of value -0.3, dim 777, 2 states, against the
+    oracle; with FP64 products checked the same way."""
+    rng = np.random.default_rng(48 + int(decades))
+    D = 777
+    h1 = _random_real_csr(rng, D, 0.01, decades)
+    h2 = _pattern_csr(rng, D, -0.3, 24)
+    scale = 1.0 / np.max(np.abs(h1[2]))  # |H_1| <= 1 so that h = 0.05 stays a moderate step
+    h1 = (h1[0], h1[1], h1[2] * scale)
+    psi0 = np.stack([mi.random_state(rng, D), mi.random_state(rng, D)])
+    f = oracle.Coeff(0.1, [1.0], [], [3.0])
+    P = oracle.Problem([oracle.CSR(r, c, v.astype(np.complex128)) for r, c, v in (h1, h2)], [oracle.Coeff.const(), f])
+    refs = [P.propagate(psi0[v], 0.0, 0.05, 10, "CF4") for v in range(2)]
+    for fixed in (True, False):
+        terms = [mg.CSRTerm(cuda(r), cuda(c), cuda(v)) for r, c, v in (h1, h2)]
+        plan = mg.Plan(D, terms, [mg.Drive.const(), mg.Drive(0.1, [1.0], [], [3.0])], nvec=2, fixed_sums=fixed)
+        psi = cuda(psi0)
+        st = plan.propagate(psi, 0.0, 0.05, 10, "CF4")
+        assert st["fixed_sums"] == int(fixed)
+        out = psi.cpu().numpy()
+        for v in range(2):
+            assert rel(out[v], refs[v]) < REL_TOL, (fixed, v, rel(out[v], refs[v]))
+
+
+def test_values_beyond_the_fixed_point_range_keep_fp64_products(mg):
+    """Values near 1e121 (row exponents beyond the range the scales cover) keep FP64 products; the
+    step h = 1e-121 keeps the exponentials moderate.  The pattern term still sums in fixed point."""
+    rng = np.random.default_rng(49)
+    D = 300
+    h1 = _banded_csr(rng, D, 1, 3)
+    h1 = (h1[0], h1[1], h1[2] * 1e121)
+    h2 = _pattern_csr(rng, D, 1.0, 12)
+    psi0 = mi.random_state(rng, D)
+    f = oracle.Coeff(0.0, [1e121], [], [1e120])
+    P = oracle.Problem([oracle.CSR(r, c, v.astype(np.complex128)) for r, c, v in (h1, h2)], [oracle.Coeff.const(), f])
+    ref = P.propagate(psi0, 0.0, 1e-121, 6, "CF4")
+    terms = [mg.CSRTerm(cuda(r), cuda(c), cuda(v)) for r, c, v in (h1, h2)]
+    plan = mg.Plan(D, terms, [mg.Drive.const(), mg.Drive(0.0, [1e121], [], [1e120])])
+    psi = cuda(psi0)
+    st = plan.propagate(psi, 0.0, 1e-121, 6, "CF4")
+    assert st["fixed_sums"] == 1
+    assert rel(psi.cpu().numpy(), ref) < REL_TOL
