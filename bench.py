@@ -503,16 +503,21 @@ def run_batch512(args):
     # as algorithmic_per_iteration: with fixed sums the field term needs its columns only and the
     # vectors add the fixed-point copies (32 B per row, and 32 B per row once per substep)
     vec = 64 * rows + ((32 + 32 * st["n_substeps"] / st["n_matvec"]) * rows if fixed else 0)
-    bytes_it = (vb * nnz_s + (4 if fixed else vb) * nnz_c + sum(2 * 8 * (c.dim + 1) for c in chains) + vec
-                if args.storage.startswith("csr") else vec)
+    if fixed:  # H_s mantissas + columns, its row pointers and exponents; the field's columns only
+        mat = 12 * nnz_s + 4 * nnz_c + sum(8 * (c.dim + 1) + 2 * c.dim for c in chains)
+    else:
+        mat = vb * nnz + sum(2 * 8 * (c.dim + 1) for c in chains)
+    bytes_it = mat + vec if args.storage.startswith("csr") else vec
     # Leja iterations differ per chain; algorithmic bytes weighted by each chain's iterations are
     # approximated with the mean iteration count per chain
     iters_per_chain = st["n_matvec"] / len(chains)
     gbs = bytes_it * iters_per_chain / (gms / 1e3) / 1e9
-    if args.storage.startswith("csr"):
-        inst_it = 2 * (nnz_s + (0 if fixed else nnz_c)) + 14 * rows
+    if fixed:  # fixed-point sums and products: 14 FP64 instructions per row remain in both families
+        inst_it = 14 * rows
+    elif args.storage.startswith("csr"):
+        inst_it = 2 * nnz + 14 * rows
     else:
-        inst_it = sum(c.dim * (4 + (c.nspins - 1) + (0 if fixed else 2 * c.nspins) + 2) + 10 * c.dim for c in chains)
+        inst_it = sum(c.dim * (4 + (c.nspins - 1) + 2 * c.nspins + 2) + 10 * c.dim for c in chains)
     tflops = 2 * inst_it * iters_per_chain / (gms / 1e3) / 1e12
     peaks = measured_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", HBM_PEAK_FALLBACK))
@@ -550,12 +555,17 @@ def run_batch512(args):
                             f"chain count (x {1 / share:.0f})"},
         "speedup_vs_per_chain_plans": round(batch_rate / seq_rate, 2),
         "leja_iterations": st["n_matvec"], "matvec_gbs": round(gbs, 1),
-        # FP64-pipe bound like the single-chain kernel: FMA-equivalent flops per iteration as in
-        # algorithmic_per_iteration, summed over the chains
-        "roofline": {"bound": "alu", "kernel": "k_batched", "achieved": round(tflops, 4),
-                     "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s", "frac": round(tflops / FP64_PEAK_TFLOPS, 4),
-                     "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 4),
-                     "traffic": None, "note": "graph time includes the batch's setup launch"},
+        # the larger of the FP64 and HBM times per iteration sets the bound, as for the single chain:
+        # FMA-equivalent flops and bytes per iteration as in algorithmic_per_iteration, summed over
+        # the chains
+        "roofline": dict(({"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                           "frac": round(gbs / hbm_peak, 4)}
+                          if gbs / hbm_peak > tflops / FP64_PEAK_TFLOPS else
+                          {"bound": "alu", "achieved": round(tflops, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+                           "unit": "TFLOP/s", "frac": round(tflops / FP64_PEAK_TFLOPS, 4)}),
+                         kernel="k_batched", hbm_gbs=round(gbs, 1), hbm_frac=round(gbs / hbm_peak, 4),
+                         fp64_tflops=round(tflops, 4), fp64_frac=round(tflops / FP64_PEAK_TFLOPS, 4),
+                         traffic=None, note="graph time includes the batch's setup launch"),
         "wall_ms": round(wall * 1e3, 2), "gpu_launches": 2,
         "gpu_launches_detail": "graph: k_exp_setup_batch + k_batched (plus two memsets)", "clocks": clk.summary(),
     }

@@ -11,6 +11,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -78,6 +79,8 @@ __global__ void __launch_bounds__(BS) k_batched(BatchArgs A) {
   __shared__ double s_part[2][4];   // this CTA's partial sums and maxima, two slots (alternating reductions)
   __shared__ double s_tot[4];       // cluster totals: two sums, then bounds of the two maxima
   __shared__ double s_wz[kMaxTerms];
+  __shared__ long long s_cb[kMaxSpins];  // ZF, FAM_MF: bond weights as 62-bit mantissas
+  __shared__ int s_cbe;
 
   cg::cluster_group cl = cg::this_cluster();
   const unsigned crank = cl.block_rank(), csize = cl.num_blocks();
@@ -160,6 +163,7 @@ __global__ void __launch_bounds__(BS) k_batched(BatchArgs A) {
     cx.dhi = sI.dhi;
     cx.jb = s_jb;
     cx.j2 = s_j2;
+    cx.cb = (ZF && FAM == FAM_MF) ? s_cb : nullptr;
     if (FAM == FAM_MF)
       for (int p = 1 + tid; p < cx.n; p += BS) s_j2[p - 1] = 2.0 * sT[0].J[cx.n - p - 1];
 
@@ -191,7 +195,17 @@ __global__ void __launch_bounds__(BS) k_batched(BatchArgs A) {
       if (ZF) {
         if (tid < nt) s_wz[tid] = R.bg[tid] * sT[tid].pval;
         for (int k = 0; k < nt; k++) opnorm = fma(fabs(R.bg[k]), sT[k].gnorm, opnorm);
+        if (FAM == FAM_MF && tid == 0) {  // bond weights 2 J bg_0 as mantissas: max |w| < 2^s_cbe
+          double wmax = 0.0;
+          for (int p = 0; p < cx.n - 1; p++) wmax = fmax(wmax, fabs(s_jb[p]));
+          int E = 0;
+          if (wmax > 0.0) frexp(wmax, &E);
+          E = max(-400, min(400, E));
+          for (int p = 0; p < cx.n - 1; p++) s_cb[p] = llrint(ldexp(s_jb[p], 62 - E));
+          s_cbe = E;
+        }
         __syncthreads();
+        cx.cbe = s_cbe;
       }
       const double2 *d = sI.dd + e * (int64_t)(A.m_max + 1);
       if (!(R.gamma > 0.0)) {
@@ -709,9 +723,10 @@ MAGNUS_API magnus_status magnus_batch_create(magnus_batch_t *out, int32_t count,
     b->zhb.assign(count, 1);
     b->zreal.assign(count, 1);
     b->zoff.resize(count);
-    size_t ztotal = 0;
+    size_t ztotal = 0, ftotal = 0, etotal = 0;
+    std::vector<size_t> foff((size_t)count * kMaxTerms, SIZE_MAX), eoff((size_t)count * kMaxTerms, 0);
     for (int i = 0; i < count; i++) {
-      int hb = 0;
+      int zhb = 1;
       for (int k = 0; k < b->nterms[i]; k++) {
         Term &T = b->terms_host[i][k];
         const size_t q = (size_t)i * kMaxTerms + k;
@@ -724,22 +739,58 @@ MAGNUS_API magnus_status magnus_batch_create(magnus_batch_t *out, int32_t count,
           T.pbits = bits;
         } else if (b->fam == FAM_CSR) {
           b->zreal[i] &= T.real_valued ? 1 : 0;
-          if (T.real_valued && T.nnz > 0 && !(pf[q] & 1)) {
+          if (T.real_valued && T.nnz > 0) {
             while (bits < 40 && (1ull << bits) < pr[q]) bits++;
-            T.pattern = 1;
-            T.pval = v0[q];
-            T.pbits = bits;
-            T.plen = (pf[q] & 2) || pr[q] > (1u << 20) ? 0 : (int)pr[q];
+            if (!(pf[q] & 1)) {
+              T.pattern = 1;
+              T.pval = v0[q];
+              T.pbits = bits;
+              T.plen = (pf[q] & 2) || pr[q] > (1u << 20) ? 0 : (int)pr[q];
+            } else if (bits <= 30) {  // fixed-point products: mantissas at offset foff, exponents at eoff
+              foff[q] = ftotal;
+              eoff[q] = etotal;
+              ftotal += (size_t)T.nnz;
+              etotal += (size_t)b->dims[i];
+              zhb = std::max(zhb, bits - 2);
+            }
           }
         }
-        if (T.pattern) hb = std::max(hb, T.pbits);
+        if (T.pattern) zhb = std::max(zhb, std::min(T.pbits, 30) + 1);
       }
-      b->zhb[i] = std::min(hb, 30) + 1;
+      b->zhb[i] = zhb;
       b->zoff[i] = ztotal;
       ztotal += (size_t)3 * b->dims[i];
       for (int k = 0; k < kMaxTerms; k++) tflat[(size_t)i * kMaxTerms + k] = b->terms_host[i][k];
     }
     BCREATE(balloc(b, &b->zscratch, ztotal));
+    if (ftotal) {  // row-scaled mantissas of the real CSR terms that are not patterns
+      long long *fv = nullptr;
+      int16_t *fe = nullptr;
+      int *wide = nullptr;
+      BCREATE(balloc(b, &fv, ftotal));
+      BCREATE(balloc(b, &fe, etotal));
+      BCREATE(balloc(b, &wide, (size_t)count * kMaxTerms));
+      BCREATE(cudaMemsetAsync(wide, 0, sizeof(int) * count * kMaxTerms, b->stream));
+      for (int i = 0; i < count; i++)
+        for (int k = 0; k < b->nterms[i]; k++) {
+          const size_t q = (size_t)i * kMaxTerms + k;
+          if (foff[q] == SIZE_MAX) continue;
+          const Term &T = b->terms_host[i][k];
+          BCREATE(launch_fixed_values(T.rowptr, T.rv, T.rs, b->dims[i], fv + foff[q], fe + eoff[q], wide + q, b->stream));
+        }
+      std::vector<int> wh((size_t)count * kMaxTerms);
+      BCREATE(cudaMemcpyAsync(wh.data(), wide, sizeof(int) * wh.size(), cudaMemcpyDeviceToHost, b->stream));
+      BCREATE(cudaStreamSynchronize(b->stream));
+      for (int i = 0; i < count; i++)
+        for (int k = 0; k < b->nterms[i]; k++) {
+          const size_t q = (size_t)i * kMaxTerms + k;
+          if (foff[q] == SIZE_MAX || wh[q]) continue;  // out-of-range values keep FP64 products
+          Term &T = b->terms_host[i][k];
+          T.fval = fv + foff[q];
+          T.fexp = fe + eoff[q];
+          tflat[q] = T;
+        }
+    }
     BCREATE(cudaMemcpyAsync(b->terms, tflat.data(), sizeof(Term) * tflat.size(), cudaMemcpyHostToDevice, b->stream));
     BCREATE(cudaStreamSynchronize(b->stream));
     b->zf = true;
