@@ -107,12 +107,15 @@ __global__ void k_leja_init(double *xi, int m, unsigned *counter) {
 constexpr int kDDRegs = (kMmaxLimit + 1) / 32;
 
 __device__ void warp_divided_differences(const double *xi, int m, double rho, double2 phase, double2 *d) {
+  // lane l holds entries j = kDDRegs l + r, so that the bidiagonal product needs one value from the
+  // neighbouring lane per term; convergence is tested every fourth term (each test is two warp
+  // reductions, the latency that bounds this single-warp computation)
   const int lane = threadIdx.x & 31;
   double2 y[kDDRegs];
   double x[kDDRegs];
 #pragma unroll
   for (int r = 0; r < kDDRegs; r++) {
-    int j = lane + 32 * r;
+    const int j = kDDRegs * lane + r;
     x[r] = (j <= m) ? xi[j] : 0.0;
     y[r] = make_double2((j == 0) ? 1.0 : 0.0, 0.0);
   }
@@ -126,39 +129,39 @@ __device__ void warp_divided_differences(const double *xi, int m, double rho, do
     for (int r = 0; r < kDDRegs; r++) { term[r] = y[r]; sum[r] = y[r]; }
     for (int k = 1; k <= 40; k++) {
       // term <- (-i t / k) Z term ;  (Z v)_j = xi_j v_j + v_{j-1}
-      double2 below[kDDRegs];
-#pragma unroll
-      for (int r = 0; r < kDDRegs; r++) {
-        double bx = __shfl_up_sync(kFull, term[r].x, 1);
-        double by = __shfl_up_sync(kFull, term[r].y, 1);
-        double cx = __shfl_sync(kFull, r > 0 ? term[r > 0 ? r - 1 : 0].x : 0.0, 31);
-        double cy = __shfl_sync(kFull, r > 0 ? term[r > 0 ? r - 1 : 0].y : 0.0, 31);
-        below[r] = (lane == 0) ? make_double2(cx, cy) : make_double2(bx, by);
-      }
-      double tmax = 0.0, smax = 0.0;
+      const double px = __shfl_up_sync(kFull, term[kDDRegs - 1].x, 1);
+      const double py = __shfl_up_sync(kFull, term[kDDRegs - 1].y, 1);
       const double f = t / k;
 #pragma unroll
-      for (int r = 0; r < kDDRegs; r++) {
-        int j = lane + 32 * r;
-        double zx = fma(x[r], term[r].x, below[r].x);
-        double zy = fma(x[r], term[r].y, below[r].y);
+      for (int r = kDDRegs - 1; r >= 0; r--) {  // high to low: term[r - 1] is still the old value
+        const int j = kDDRegs * lane + r;
+        const double bx = r > 0 ? term[r > 0 ? r - 1 : 0].x : (lane > 0 ? px : 0.0);
+        const double by = r > 0 ? term[r > 0 ? r - 1 : 0].y : (lane > 0 ? py : 0.0);
+        const double zx = fma(x[r], term[r].x, bx);
+        const double zy = fma(x[r], term[r].y, by);
         // (-i f) (zx + i zy) = f zy - i f zx
         term[r] = (j <= m) ? make_double2(f * zy, -f * zx) : make_double2(0.0, 0.0);
         sum[r].x += term[r].x;
         sum[r].y += term[r].y;
-        tmax = fmax(tmax, fabs(term[r].x) + fabs(term[r].y));
-        smax = fmax(smax, fabs(sum[r].x) + fabs(sum[r].y));
       }
-      tmax = warp_max(tmax);
-      smax = warp_max(smax);
-      if (tmax <= 1e-18 * smax) break;
+      if ((k & 3) == 0) {
+        double tmax = 0.0, smax = 0.0;
+#pragma unroll
+        for (int r = 0; r < kDDRegs; r++) {
+          tmax = fmax(tmax, fabs(term[r].x) + fabs(term[r].y));
+          smax = fmax(smax, fabs(sum[r].x) + fabs(sum[r].y));
+        }
+        tmax = warp_max(tmax);
+        smax = warp_max(smax);
+        if (tmax <= 1e-18 * smax) break;
+      }
     }
 #pragma unroll
     for (int r = 0; r < kDDRegs; r++) y[r] = sum[r];
   }
 #pragma unroll
   for (int r = 0; r < kDDRegs; r++) {
-    int j = lane + 32 * r;
+    const int j = kDDRegs * lane + r;
     if (j <= m) d[j] = cmul(phase, y[r]);
   }
 }
