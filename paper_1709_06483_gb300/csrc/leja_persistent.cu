@@ -40,9 +40,9 @@ constexpr int kBlock = 256;
 #ifndef MG_CSR_MIN_BLOCKS
 #define MG_CSR_MIN_BLOCKS 4
 #endif
-template <int FAM, bool HM6, bool ZF>
+template <int FAM, bool HM6, int ZF>
 constexpr int min_blocks() {
-  return (FAM == FAM_CSR && ZF) ? MG_CSR_MIN_BLOCKS : 3;
+  return (FAM == FAM_CSR && ZF == 1) ? MG_CSR_MIN_BLOCKS : 3;
 }
 constexpr int kMaxVec = 64;
 
@@ -62,10 +62,10 @@ __device__ __forceinline__ double2 scal2(double s, double2 a) { return make_doub
 
 // --------------------------------------------------------------------- kernel
 // HM6: the instantiation that also carries Method M6 (launched only for MAGNUS_M6, so that its
-// extra code does not weigh on the register budget of the other methods).  ZF: the instantiation
-// for linear generators with fixed-point pattern sums (M2, Cf4, Cf4:3 with options.fixed_sums),
-// which carries only that path.
-template <int FAM, bool HM6, bool ZF>
+// extra code does not weigh on the register budget of the other methods).  ZF: the instantiations
+// with fixed-point sums and products (options.fixed_sums): 1 for linear generators (M2, Cf4, Cf4:3),
+// which carries only that path, 2 for M4 (its two phases on fixed-point copies of w and of u_k).
+template <int FAM, bool HM6, int ZF>
 __global__ void __launch_bounds__(kBlock, (min_blocks<FAM, HM6, ZF>())) k_magnus_persistent(PersistArgs a) {
   __shared__ Term sT[kMaxTerms];
   __shared__ ExpRec sR;
@@ -76,6 +76,8 @@ __global__ void __launch_bounds__(kBlock, (min_blocks<FAM, HM6, ZF>())) k_magnus
   __shared__ double s_wz[kMaxTerms];  // weights of the fixed-point pattern sums: bg_k v_k
   __shared__ long long s_cb[kMaxSpins];  // FAM_MF fixed point: bond weights as 62-bit mantissas
   __shared__ int s_cbe;
+  __shared__ long long s_c2[kMaxSpins];  // FAM_MF fixed-point M4: the unscaled weights 2 J likewise
+  __shared__ int s_c2e;
   __shared__ int s_act[kMaxVec], s_m[kMaxVec];
   __shared__ double s_red[2][kBlock / 32];
   __shared__ unsigned s_rmx[2][kBlock / 32];
@@ -107,9 +109,25 @@ __global__ void __launch_bounds__(kBlock, (min_blocks<FAM, HM6, ZF>())) k_magnus
   cx.j2 = s_j2;
   cx.cb = (ZF && FAM == FAM_MF) ? s_cb : nullptr;
   cx.cbe = 0;
+  cx.c2 = (ZF == 2 && FAM == FAM_MF) ? s_c2 : nullptr;
+  cx.c2e = 0;
   if (FAM == FAM_MF) {
     // bond at bits (p, p-1) couples spins s = n-p and s+1 with J[s-1] = J[n-p-1]
     for (int p = 1 + tid; p < cx.n; p += blockDim.x) s_j2[p - 1] = 2.0 * sT[0].J[cx.n - p - 1];
+    if (ZF == 2) {
+      __syncthreads();
+      if (tid == 0) {
+        double wmax = 0.0;
+        for (int p = 0; p < cx.n - 1; p++) wmax = fmax(wmax, fabs(s_j2[p]));
+        int E = 0;
+        if (wmax > 0.0) frexp(wmax, &E);
+        E = max(-400, min(400, E));
+        for (int p = 0; p < cx.n - 1; p++) s_c2[p] = llrint(ldexp(s_j2[p], 62 - E));
+        s_c2e = E;
+      }
+      __syncthreads();
+      cx.c2e = s_c2e;
+    }
   }
 
   unsigned it = 0;  // slot counter of the partial sums: consecutive reductions alternate slots
@@ -196,12 +214,21 @@ __global__ void __launch_bounds__(kBlock, (min_blocks<FAM, HM6, ZF>())) k_magnus
     if (FAM == FAM_MF)
       for (int p = 1 + tid; p < cx.n; p += blockDim.x) s_jb[p - 1] = s_j2[p - 1] * R.bg[0];
     // fixed-point pattern sums: linear generators of the CSR and matrix-free families
-    constexpr bool zf = ZF && FAM != FAM_GENERIC;
-    if (ZF && R.mode != MODE_LINEAR) { fail(MAGNUS_EINVAL); return; }  // the host launches ZF for linear generators only
-    double opnorm = 0.0;  // sum_k |bg_k| ||H_k||_inf: with |shift|, a bound of ||X - shift||_inf
+    constexpr bool zf = ZF != 0 && FAM != FAM_GENERIC;
+    // the host launches ZF = 1 for linear generators and ZF = 2 for M4 (whose records may be linear)
+    if ((ZF == 1 && R.mode != MODE_LINEAR) || (ZF == 2 && R.mode != MODE_LINEAR && R.mode != MODE_M4)) {
+      fail(MAGNUS_EINVAL);
+      return;
+    }
+    // sum_k |bg_k| ||H_k||_inf (+ the M4 commutator's sum_{k<l} |kg| 2 ||H_k||_inf ||H_l||_inf): with
+    // |shift|, a bound of ||X - shift||_inf
+    double opnorm = 0.0;
     if (zf) {
       if (tid < nt) s_wz[tid] = R.bg[tid] * sT[tid].pval;
       for (int k = 0; k < nt; k++) opnorm = fma(fabs(R.bg[k]), sT[k].gnorm, opnorm);
+      if (ZF == 2 && R.mode == MODE_M4)
+        for (int k = 0, pi = 0; k < nt; k++)
+          for (int l = k + 1; l < nt; l++, pi++) opnorm = fma(fabs(R.kg[pi]), 2.0 * sT[k].gnorm * sT[l].gnorm, opnorm);
       if (FAM == FAM_MF) {  // bond weights 2 J bg_0 as mantissas at one exponent: max |w| < 2^s_cbe
         __syncthreads();
         if (tid == 0) {
@@ -255,6 +282,25 @@ __global__ void __launch_bounds__(kBlock, (min_blocks<FAM, HM6, ZF>())) k_magnus
             for (int64_t r = lo + tid; r < hi; r += blockDim.x)
               for (int k = 0; k < nt; k++) a.u[((size_t)k * nv) * D + base + r] = Op<FAM>::term(cx, k, src + base, r);
           if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { fail(MAGNUS_ETIMEOUT); return; }
+        }
+        // fixed-point M4, phase 1: u_k = H_k w from the copy of w, and the copy of u_k, scaled from
+        // |u_k| <= ||H_k||_inf max|w| (x2 for complex terms)
+        int zs_u[kMaxTerms] = {0, 0, 0, 0};
+        if constexpr (ZF == 2 && zf) {
+          if (R.mode == MODE_M4) {
+            const double msrc = (j == 1) ? s_vm[vec] : s_wm[vec];
+            const longlong2 *zw = ((j == 1) ? a.zc : (((j - 2) & 1) ? a.zw1 : a.zw0)) + base;
+            for (int k = 0; k < nt; k++)
+              zs_u[k] = fix_scale(sT[k].gnorm * (a.zreal ? 1.0 : 2.0) * msrc * (1.0 + 0x1p-20), a.zhb);
+            if (mine)
+              for (int64_t r = lo + tid; r < hi; r += blockDim.x)
+                for (int k = 0; k < nt; k++) {
+                  const double2 hk = Op<FAM>::term_z(cx, k, src + base, zw, zs_src, r);
+                  a.u[((size_t)k * nv) * D + base + r] = hk;
+                  a.zu[((size_t)k * nv) * D + base + r] = fix2(hk, zs_u[k]);
+                }
+            if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { fail(MAGNUS_ETIMEOUT); return; }
+          }
         }
         // Method M6: K w = P w + R w / 12 + (i/240) (U (V w) - V (U w)) with
         //   U = i(20 P + R) - [P, Q],   V = -i Q + [P, R]/30 - (i/60) [P, [P, Q]],
@@ -356,7 +402,28 @@ __global__ void __launch_bounds__(kBlock, (min_blocks<FAM, HM6, ZF>())) k_magnus
           auto rows_z = [&](auto first) {
             for (int64_t r = lo + tid; r < hi; r += blockDim.x) {
               double2 wr;
-              const double2 y = Op<FAM>::combo_z(cx, R, s_wz, shift, src + base, zsrc, zs_src, r, wr);
+              double2 y;
+              if (ZF == 2 && R.mode == MODE_M4) {
+                // phase 2: sum_k bg_k u_k + sum_{k<l} kg (H_k u_l - H_l u_k) (times -i) - shift w
+                y = make_double2(0.0, 0.0);
+                double2 zq = make_double2(0.0, 0.0);
+                for (int k = 0, pi = 0; k < nt; k++) {
+                  const size_t ok = ((size_t)k * nv) * D + base;
+                  y = rfma(R.bg[k], ldv(a.u + ok + r), y);
+                  for (int l = k + 1; l < nt; l++, pi++) {
+                    const size_t ol = ((size_t)l * nv) * D + base;
+                    const double2 hkul = Op<FAM>::term_z(cx, k, a.u + ol, a.zu + ol, zs_u[l], r);
+                    const double2 hluk = Op<FAM>::term_z(cx, l, a.u + ok, a.zu + ok, zs_u[k], r);
+                    zq = rfma(R.kg[pi], make_double2(hkul.x - hluk.x, hkul.y - hluk.y), zq);
+                  }
+                }
+                y.x += zq.y;  // -i zq
+                y.y -= zq.x;
+                wr = ldv(src + base + r);
+                y = rfma(-shift, wr, y);
+              } else {
+                y = Op<FAM>::combo_z(cx, R, s_wz, shift, src + base, zsrc, zs_src, r, wr);
+              }
               dst[base + r] = y;
               zdst[r] = fix2(y, zs_dst);
               double2 pr;
@@ -484,20 +551,22 @@ __global__ void __launch_bounds__(kBlock, (min_blocks<FAM, HM6, ZF>())) k_magnus
     for (int64_t r = lo + tid; r < hi; r += blockDim.x) a.psi[base + r] = cur[base + r];
 }
 
-const void *kernel_for(int fam, bool m6, bool zf) {
+const void *kernel_for(int fam, bool m6, int zf) {
   if (m6) {
     switch (fam) {
-      case FAM_CSR: return (const void *)k_magnus_persistent<FAM_CSR, true, false>;
-      case FAM_MF: return (const void *)k_magnus_persistent<FAM_MF, true, false>;
-      default: return (const void *)k_magnus_persistent<FAM_GENERIC, true, false>;
+      case FAM_CSR: return (const void *)k_magnus_persistent<FAM_CSR, true, 0>;
+      case FAM_MF: return (const void *)k_magnus_persistent<FAM_MF, true, 0>;
+      default: return (const void *)k_magnus_persistent<FAM_GENERIC, true, 0>;
     }
   }
-  if (zf && fam == FAM_CSR) return (const void *)k_magnus_persistent<FAM_CSR, false, true>;
-  if (zf && fam == FAM_MF) return (const void *)k_magnus_persistent<FAM_MF, false, true>;
+  if (zf == 1 && fam == FAM_CSR) return (const void *)k_magnus_persistent<FAM_CSR, false, 1>;
+  if (zf == 1 && fam == FAM_MF) return (const void *)k_magnus_persistent<FAM_MF, false, 1>;
+  if (zf == 2 && fam == FAM_CSR) return (const void *)k_magnus_persistent<FAM_CSR, false, 2>;
+  if (zf == 2 && fam == FAM_MF) return (const void *)k_magnus_persistent<FAM_MF, false, 2>;
   switch (fam) {
-    case FAM_CSR: return (const void *)k_magnus_persistent<FAM_CSR, false, false>;
-    case FAM_MF: return (const void *)k_magnus_persistent<FAM_MF, false, false>;
-    default: return (const void *)k_magnus_persistent<FAM_GENERIC, false, false>;
+    case FAM_CSR: return (const void *)k_magnus_persistent<FAM_CSR, false, 0>;
+    case FAM_MF: return (const void *)k_magnus_persistent<FAM_MF, false, 0>;
+    default: return (const void *)k_magnus_persistent<FAM_GENERIC, false, 0>;
   }
 }
 
@@ -507,7 +576,7 @@ int persistent_block_size() { return kBlock; }
 
 // Resident CTAs per SM of the instantiation for this family (method M6, fixed-point linear
 // generators or the rest): the largest cooperative grid of that launch.
-cudaError_t persistent_max_blocks_per_sm(int fam, bool m6, bool zf, int *n) {
+cudaError_t persistent_max_blocks_per_sm(int fam, bool m6, int zf, int *n) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, kernel_for(fam, m6, zf), kBlock, 0);
 }
 

@@ -20,7 +20,8 @@ struct magnus_plan_s {
   int num_sms = 0;
   int max_blocks_per_sm = 0;             // persistent kernel of the plan's family, linear / M4 generators
   int max_blocks_m6 = 0;                 // its M6 instantiation
-  int max_blocks_zf = 0;                 // its instantiation with fixed-point pattern sums
+  int max_blocks_zf = 0;                 // its instantiation with fixed-point sums and products
+  int max_blocks_zf4 = 0;                // and that of fixed-point M4
   cudaStream_t stream = nullptr;
   int64_t dim = 0;
   int nterms = 0;
@@ -69,6 +70,7 @@ struct magnus_plan_s {
   double *dlo = nullptr, *dhi = nullptr;
   // exact fixed-point sums of pattern terms: Z copies of the substep input and the Leja vectors
   longlong2 *zc = nullptr, *zw0 = nullptr, *zw1 = nullptr;
+  longlong2 *zu = nullptr;  // M4 in fixed point: copies of u_k, on first use
   double *rcopy[kMaxTerms] = {nullptr, nullptr, nullptr, nullptr};  // real parts of complex-stored real CSR terms
   long long *fval[kMaxTerms] = {nullptr, nullptr, nullptr, nullptr};  // fixed-point values of real CSR terms
   int16_t *fexp[kMaxTerms] = {nullptr, nullptr, nullptr, nullptr};    // and their row exponents
@@ -115,7 +117,7 @@ void free_plan(magnus_plan_t p) {
                   p->hsplit[0], p->hsplit[1], p->hsplit[2], p->hsplit[3], p->sh_cur, p->sh_w0, p->sh_w1, p->sh_u,
                   p->hslice[0], p->hslice[1], p->hslice[2], p->hslice[3], p->hexp[0], p->hexp[1], p->hexp[2],
                   p->hexp[3], p->sl_cur, p->sl_w0, p->sl_w1, p->sl_u, p->ex_sets, p->colmax, p->m6,
-                  p->tc_hd, p->tc_eh, p->tc_wd, p->tc_ex, p->tc_P, p->zc, p->zw0, p->zw1,
+                  p->tc_hd, p->tc_eh, p->tc_wd, p->tc_ex, p->tc_P, p->zc, p->zw0, p->zw1, p->zu,
                   p->rcopy[0], p->rcopy[1], p->rcopy[2], p->rcopy[3], p->fval[0], p->fval[1], p->fval[2],
                   p->fval[3], p->fexp[0], p->fexp[1], p->fexp[2], p->fexp[3]};
   for (void *b : bufs)
@@ -183,8 +185,9 @@ long long spin_limit(magnus_plan_t p) {
 }
 
 // grid: nvec * gv blocks, all co-resident (cooperative launch)
-void choose_grid(magnus_plan_t p, int *grid, int *gv, bool m6 = false, bool zf = false) {
-  const int maxg = p->num_sms * std::max(1, m6 ? p->max_blocks_m6 : (zf ? p->max_blocks_zf : p->max_blocks_per_sm));
+void choose_grid(magnus_plan_t p, int *grid, int *gv, bool m6 = false, int zf = 0) {
+  const int per_sm = m6 ? p->max_blocks_m6 : (zf == 2 ? p->max_blocks_zf4 : (zf == 1 ? p->max_blocks_zf : p->max_blocks_per_sm));
+  const int maxg = p->num_sms * std::max(1, per_sm);
   const int nv = p->opt.nvec;
   int per_vec = std::max(1, maxg / nv);
   if (p->opt.ctas > 0) per_vec = std::max(1, std::min(per_vec, p->opt.ctas / nv));
@@ -210,7 +213,7 @@ magnus_status run_persistent(magnus_plan_t p, void *psi, int64_t nexp, magnus_st
     gv = grid;
     need = (size_t)4 * grid * p->opt.nvec + (size_t)4 * p->opt.nvec;
   } else {
-    choose_grid(p, &grid, &gv, m6, p->zc != nullptr && !m6 && !m4);
+    choose_grid(p, &grid, &gv, m6, (p->zc != nullptr && !m6) ? (m4 ? 2 : 1) : 0);
     need = (size_t)8 * grid;  // two slots x grid x (two sums, two maxima)
   }
   if ((int64_t)need > p->partials_cap) {
@@ -307,7 +310,9 @@ magnus_status run_persistent(magnus_plan_t p, void *psi, int64_t nexp, magnus_st
   }
   a.colmax = p->colmax;
   a.m6 = p->m6;
-  a.zfix = p->zc != nullptr && !m6 && !m4;  // linear generators only
+  a.zfix = (p->zc != nullptr && !m6) ? (m4 ? 2 : 1) : 0;  // fixed-point linear generators (1) or M4 (2)
+  if (a.zfix == 2 && !p->zu) CUDA_TRY(p, dalloc(&p->zu, (size_t)p->nterms * p->dim * p->opt.nvec));
+  a.zu = p->zu;
   a.zc = p->zc;
   a.zw0 = p->zw0;
   a.zw1 = p->zw1;
@@ -341,7 +346,7 @@ magnus_status run_persistent(magnus_plan_t p, void *psi, int64_t nexp, magnus_st
     stats->kernel_ms = ms;
     stats->grid = grid;
     stats->block = p->fam == FAM_DENSE ? dense_block_size() : persistent_block_size();
-    stats->fixed_sums = a.zfix;
+    stats->fixed_sums = a.zfix != 0;
   }
   if (c.status != MAGNUS_OK) {
     const char *what = c.status == MAGNUS_ENOCONV      ? "Leja interpolation did not converge within m_max"
@@ -657,9 +662,10 @@ magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms
   }
 
   if (p->fam != FAM_DENSE) {
-    PLAN_TRY(persistent_max_blocks_per_sm(p->fam, false, false, &p->max_blocks_per_sm));
-    PLAN_TRY(persistent_max_blocks_per_sm(p->fam, true, false, &p->max_blocks_m6));
-    PLAN_TRY(persistent_max_blocks_per_sm(p->fam, false, true, &p->max_blocks_zf));
+    PLAN_TRY(persistent_max_blocks_per_sm(p->fam, false, 0, &p->max_blocks_per_sm));
+    PLAN_TRY(persistent_max_blocks_per_sm(p->fam, true, 0, &p->max_blocks_m6));
+    PLAN_TRY(persistent_max_blocks_per_sm(p->fam, false, 1, &p->max_blocks_zf));
+    PLAN_TRY(persistent_max_blocks_per_sm(p->fam, false, 2, &p->max_blocks_zf4));
   }
 
   // Gershgorin enclosures (one pass over every term) and the Leja points
@@ -940,7 +946,7 @@ magnus_status magnus_adjoint_grad(magnus_plan_t p, const void *psi0, const void 
   cdev = p->coeffs + kd;
 
   int grid, gv;
-  choose_grid(p, &grid, &gv, false, p->zc != nullptr);  // the linear generators take the fixed-point kernel
+  choose_grid(p, &grid, &gv, false, p->zc != nullptr ? 1 : 0);  // linear generators: the fixed-point kernel
   if ((int64_t)8 * grid > p->partials_cap) {
     if (p->partials) cudaFree(p->partials);
     p->partials = nullptr;
@@ -976,7 +982,7 @@ magnus_status magnus_adjoint_grad(magnus_plan_t p, const void *psi0, const void 
   a.lbits = p->lbits;
   a.dlo = p->dlo;
   a.dhi = p->dhi;
-  a.zfix = p->zc != nullptr;
+  a.zfix = p->zc != nullptr ? 1 : 0;
   a.zc = p->zc;
   a.zw0 = p->zw0;
   a.zw1 = p->zw1;

@@ -216,17 +216,18 @@ struct PersistArgs {
   // substep input and of the two Leja vectors ([nvec][dim] each), headroom bits of the row sums,
   // and whether every term is real-valued (then |Re (X w)_r| <= ||X||_inf max |Re w|)
   longlong2 *zc, *zw0, *zw1;
-  int zfix, zhb, zreal;
+  longlong2 *zu;  // M4 in fixed point: copies of u_k, [nterms][nvec][dim]
+  int zfix, zhb, zreal;  // zfix: 0 FP64, 1 fixed-point linear generators, 2 fixed-point M4
 };
 enum { FAM_GENERIC = 0, FAM_CSR = 1, FAM_MF = 2, FAM_DENSE = 3 };
-// a.zfix (which callers set for linear generators only: M2, Cf4, Cf4:3) selects the instantiation
-// with fixed-point pattern sums.
+// a.zfix selects the instantiation with fixed-point sums and products: 1 for linear generators
+// (M2, Cf4, Cf4:3), 2 for M4 (which also needs a.zu); never with M6.
 cudaError_t launch_persistent(const PersistArgs &a, int grid, int block, bool m6, cudaStream_t st);
-inline bool persistent_fixed_kernel(const PersistArgs &a, bool m6) {
-  return a.zfix && !m6 && (a.fam == FAM_CSR || a.fam == FAM_MF);
+inline int persistent_fixed_kernel(const PersistArgs &a, bool m6) {
+  return (!m6 && (a.fam == FAM_CSR || a.fam == FAM_MF)) ? a.zfix : 0;
 }
 int persistent_block_size();
-cudaError_t persistent_max_blocks_per_sm(int fam, bool m6, bool zf, int *n);
+cudaError_t persistent_max_blocks_per_sm(int fam, bool m6, int zf, int *n);
 
 // Dense family (dense terms, optionally with a matrix-free field term): rows of all vectors per block.
 int dense_block_size();

@@ -105,7 +105,7 @@ extern "C" MAGNUS_API magnus_status magnus_expv_xxz_static(int32_t nspins, const
         return fail(MAGNUS_ECUDA, "magnus_expv_xxz_static: cudaGetSymbolAddress failed");
       unsigned char *base = (unsigned char *)ptr;
       if (cudaDeviceGetAttribute(&s.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-          persistent_max_blocks_per_sm(FAM_MF, false, false, &s.blocks_per_sm) != cudaSuccess)
+          persistent_max_blocks_per_sm(FAM_MF, false, 0, &s.blocks_per_sm) != cudaSuccess)
         return fail(MAGNUS_ECUDA, "magnus_expv_xxz_static: device query failed");
       if (launch_leja_points((double *)(base + kOffXi), kStaticMmax, (double *)(base + kOffCand),
                              (unsigned *)(base + kOffCounter), stream) != cudaSuccess ||

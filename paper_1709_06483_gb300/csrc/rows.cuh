@@ -342,6 +342,8 @@ struct Ctx {
   const double *j2;   // shared: 2 J_bond (unscaled), same indexing
   const long long *cb;  // shared (fixed-point kernel): jb as 62-bit mantissas, cb = round(jb 2^(62 - cbe))
   int cbe;              // with max |jb| < 2^cbe
+  const long long *c2;  // shared (fixed-point M4): j2 as mantissas, c2 = round(j2 2^(62 - c2e))
+  int c2e;
 };
 
 // H_xxz row with the diagonal from the two tables (FAM_MF).  coefj: per-bond coefficients.
@@ -388,8 +390,9 @@ static __device__ __forceinline__ double2 mf_xxz_row(const Ctx &c, const double 
 // The same row with the bond flips taken in fixed point: each active bond adds the high 64 bits of
 // cb[b] Z[r ^ (3 << b)] (|cb| < 2^62, |Z| < 2^(62-hb)), exactly summed in int64, and the sum goes back
 // to FP64 once; the diagonal stays FP64.  Same visiting order as mf_xxz_row.
-static __device__ __forceinline__ double2 mf_xxz_row_z(const Ctx &c, double dscale, double dshift, const double2 *x,
-                                                const longlong2 *z, int zs, int64_t r, double2 &xr) {
+static __device__ __forceinline__ double2 mf_xxz_row_z(const Ctx &c, const long long *cb, int cbe, double dscale,
+                                                double dshift, const double2 *x, const longlong2 *z, int zs, int64_t r,
+                                                double2 &xr) {
   xr = ldv(x + r);
   const double dg = __ldg(c.dhi + (r >> c.lbits)) + __ldg(c.dlo + (r & c.lomask));
   const double cr = fma(dscale, dg, -dshift);
@@ -409,7 +412,7 @@ static __device__ __forceinline__ double2 mf_xxz_row_z(const Ctx &c, double dsca
     for (int q = 0; q < 4; q++) v[q] = ldz(z + (r ^ ((int64_t)3 << bq[q])));
 #pragma unroll
     for (int q = 0; q < 4; q++) {
-      const long long w = ((mine >> bq[q]) & 1u) ? c.cb[bq[q]] : 0ll;
+      const long long w = ((mine >> bq[q]) & 1u) ? cb[bq[q]] : 0ll;
       acc.x += __mul64hi(w, v[q].x);
       acc.y += __mul64hi(w, v[q].y);
     }
@@ -418,11 +421,11 @@ static __device__ __forceinline__ double2 mf_xxz_row_z(const Ctx &c, double dsca
     const int b = __ffs(mw) - 1;
     mw &= mw - 1;
     const longlong2 v = ldz(z + (r ^ ((int64_t)3 << b)));
-    const long long w = ((mine >> b) & 1u) ? c.cb[b] : 0ll;
+    const long long w = ((mine >> b) & 1u) ? cb[b] : 0ll;
     acc.x += __mul64hi(w, v.x);
     acc.y += __mul64hi(w, v.y);
   }
-  const double2 bonds = unfix2(acc, zs - c.cbe - 2);
+  const double2 bonds = unfix2(acc, zs - cbe - 2);
   return make_double2(fma(cr, xr.x, bonds.x), fma(cr, xr.y, bonds.y));
 }
 
@@ -452,13 +455,39 @@ struct Op {
     xr = ldv(x + r);
     return rfma(-shift, xr, y);
   }
+  // (H_k x)[r] from the fixed-point copy Z = trunc(x 2^zs) where the term allows it (pattern sums,
+  // mantissa products, matrix-free flips), else in FP64 from x (M4 phases of the fixed-point kernel)
+  __device__ static __forceinline__ double2 term_z(const Ctx &c, int k, const double2 *x, const longlong2 *z, int zs,
+                                                   int64_t r) {
+    if constexpr (FAM == FAM_MF) {
+      if (k == 0) {
+        double2 xr;
+        return mf_xxz_row_z(c, c.c2, c.c2e, 1.0, 0.0, x, z, zs, r, xr);
+      }
+      const double2 f = unfix2(fieldx_row_zsum(c.n, z, r), zs);
+      return f;
+    } else {
+      const Term &t = c.T[k];
+      if (t.pattern) {
+        const double2 f = unfix2(csr_row_zsum(t, z, r), zs);
+        return make_double2(t.pval * f.x, t.pval * f.y);
+      }
+      if (t.fval) {
+        int fe;
+        const longlong2 hs = csr_row_zprod_w(t, z, r, fe);
+        return unfix2(hs, zs - fe - 2);
+      }
+      return csr_row(t, x, r);
+    }
+  }
   // combo with the pattern terms summed exactly on Z = trunc(x 2^zs) and weighted by wz[k] =
   // bg_k v_k (FAM_CSR: terms flagged `pattern`; FAM_MF: the transverse field)
   __device__ static __forceinline__ double2 combo_z(const Ctx &c, const ExpRec &R, const double *wz, double shift,
                                                     const double2 *x, const longlong2 *z, int zs, int64_t r,
                                                     double2 &xr) {
     if constexpr (FAM == FAM_MF) {
-      double2 y = c.cb ? mf_xxz_row_z(c, R.bg[0], shift, x, z, zs, r, xr) : mf_xxz_row(c, c.jb, R.bg[0], shift, x, r, xr);
+      double2 y = c.cb ? mf_xxz_row_z(c, c.cb, c.cbe, R.bg[0], shift, x, z, zs, r, xr)
+                       : mf_xxz_row(c, c.jb, R.bg[0], shift, x, r, xr);
       return rfma(wz[1], unfix2(fieldx_row_zsum(c.n, z, r), zs), y);
     } else {
       double2 y = make_double2(0.0, 0.0);

@@ -54,7 +54,7 @@ def chain_problem(c, **kw):
 
 
 @pytest.mark.parametrize("kind", ["csr", "csr_real", "mfree"])
-@pytest.mark.parametrize("variant", ["CF4", "CF4_3", "M2"])
+@pytest.mark.parametrize("variant", ["CF4", "CF4_3", "M2", "M4"])
 def test_fixed_and_fp64_sums_match_oracle(mg, kind, variant):
     c = mi.xxz_chain(41, 11, 0.01, 30)
     ost = oracle.Stats(512)
@@ -72,18 +72,20 @@ def test_fixed_and_fp64_sums_match_oracle(mg, kind, variant):
     assert rel(out[True], out[False]) < 1e-12
 
 
-def test_methods_with_commutators_keep_fp64_sums(mg):
-    """M4 generators take the FP64 sums on the same plan; a later Cf4 call on that plan scales its
-    fixed-point copies from the maxima the M4 call left."""
+@pytest.mark.parametrize("kind", ["csr", "mfree"])
+def test_methods_in_turn_on_one_plan(mg, kind):
+    """M6 (FP64 sums), then M4 and Cf4 (fixed point) on one plan: each call scales its fixed-point
+    copies from the maxima the previous call left."""
     c = mi.xxz_chain(42, 10, 0.01, 12)
-    plan = mg.Plan(c.dim, chain_terms(mg, c, "csr"), drives(mg, c))
+    plan = mg.Plan(c.dim, chain_terms(mg, c, kind), drives(mg, c))
     P = chain_problem(c)
     psi = cuda(c.psi0)
-    st = plan.propagate(psi, 0.0, c.h, 6, "M4")
-    assert st["fixed_sums"] == 0
-    st = plan.propagate(psi, 6 * c.h, c.h, 6, "CF4")
-    assert st["fixed_sums"] == 1
-    ref = P.propagate(P.propagate(c.psi0, 0.0, c.h, 6, "M4"), 6 * c.h, c.h, 6, "CF4")
+    assert plan.propagate(psi, 0.0, c.h, 4, "M6")["fixed_sums"] == 0
+    assert plan.propagate(psi, 4 * c.h, c.h, 4, "M4")["fixed_sums"] == 1
+    assert plan.propagate(psi, 8 * c.h, c.h, 4, "CF4")["fixed_sums"] == 1
+    ref = P.propagate(c.psi0, 0.0, c.h, 4, "M6")
+    ref = P.propagate(ref, 4 * c.h, c.h, 4, "M4")
+    ref = P.propagate(ref, 8 * c.h, c.h, 4, "CF4")
     assert rel(psi.cpu().numpy(), ref) < REL_TOL
 
 
@@ -163,13 +165,14 @@ def test_ragged_pattern_with_complex_term_odd_dimension(mg, storage):
     pv = cuda(pval) if storage == "real" else cuda(pval.astype(np.complex128))
     terms = [mg.CSRTerm(cuda(hrow), cuda(hcol), cuda(hval)), mg.CSRTerm(cuda(prow), cuda(pcol), pv)]
     plan = mg.Plan(D, terms, [mg.Drive.const(), mg.Drive(0.2, [1.0], [0.3], [4.0])], nvec=2)
-    psi = cuda(psi0)
-    st = plan.propagate(psi, 0.0, 0.05, 10, "CF4")
-    assert st["fixed_sums"] == 1
-    out = psi.cpu().numpy()
-    for v in range(2):
-        ref = P.propagate(psi0[v], 0.0, 0.05, 10, "CF4")
-        assert rel(out[v], ref) < REL_TOL, (v, rel(out[v], ref))
+    for variant in ("CF4", "M4"):
+        psi = cuda(psi0)
+        st = plan.propagate(psi, 0.0, 0.05, 10, variant)
+        assert st["fixed_sums"] == 1
+        out = psi.cpu().numpy()
+        for v in range(2):
+            ref = P.propagate(psi0[v], 0.0, 0.05, 10, variant)
+            assert rel(out[v], ref) < REL_TOL, (variant, v, rel(out[v], ref))
 
 
 def test_no_pattern_term_means_fp64_sums(mg):
