@@ -116,33 +116,35 @@ def algorithmic_per_iteration(c, storage, variant, nnz_terms, fixed=False, subs_
     commutator arithmetic per row."""
     D = c.dim
     passes = {"M4": 2, "M6": 17}.get(variant, 1)
-    fixed = fixed and variant not in ("M4", "M6")
+    fixed = fixed and variant != "M6"
     vec_bytes = 64 * D
     if fixed:
         vec_bytes += 32 * D + 32 * D * subs_per_it
     if variant == "M4":
-        vec_bytes += 2 * 16 * D * 2
+        # u_k written and read back (2 x 32 B/row); in fixed point also their copies (2 x 32 B/row)
+        vec_bytes += 2 * 16 * D * 2 * (2 if fixed else 1)
     if variant == "M6":
         vec_bytes += (17 + 23 + 16) * 16 * D
     if storage in ("csr", "csr_real"):
         nnz_s, nnz_c = nnz_terms
         if fixed:
             mat = 12 * nnz_s + 4 * nnz_c + 8 * (D + 1) + 2 * D
-            inst = (4 + 2 + 4 + 4) * D
+            # FP64 left per row: linear 14; M4 24 (scaling the pattern term's sums, the weighted
+            # u_k, the commutator difference and its weight, -i, shift, p, norms)
+            inst = (24 if variant == "M4" else 14) * D
         else:
             mat = 12 * (nnz_s + nnz_c) + 2 * 8 * (D + 1)
-            inst = passes * 2 * (nnz_s + nnz_c) + (4 + 2 + 4 + 4) * D
+            inst = passes * 2 * (nnz_s + nnz_c) + (4 + 2 + 4 + 4) * D + (8 * D if variant == "M4" else 0)
     elif fixed:
         # matrix-free in fixed point: bonds and field are integer work; FP64 keeps the diagonal (2),
-        # adding it to the converted bond sum (2), weighting the field (2), p (4) and the norms (4)
+        # adding it to the converted bond sum (2), weighting the field (2), p (4) and the norms (4);
+        # M4 26 per row (the XXZ diagonal in both phases, the weighted u_k, the commutator, -i, shift)
         mat = 0
-        inst = (2 + 2 + 2 + 4 + 4) * D
+        inst = (26 if variant == "M4" else 2 + 2 + 2 + 4 + 4) * D
     else:
         n = c.nspins
         mat = 0
-        inst = passes * D * (4 + (n - 1) + 2 * n + 2) + (2 + 4 + 4) * D
-    if variant == "M4":
-        inst += 8 * D  # commutator difference and its weight
+        inst = passes * D * (4 + (n - 1) + 2 * n + 2) + (2 + 4 + 4) * D + (8 * D if variant == "M4" else 0)
     if variant == "M6":
         inst += (27 * 2 * 2 + 70 - 4) * D  # combinations and commutator arithmetic (no separate weighting)
     return int(passes * mat + vec_bytes), int(2 * inst)

@@ -148,13 +148,16 @@ typedef enum {
  *   interval [MAGNUS_INTERVAL_GERSHGORIN]: how each term's spectral enclosure is estimated (Sec. 3:
  *                     the Leja parameters need a spectral estimate); plans only, batches
  *                     take Gershgorin
- *   fixed_sums [1]:   sum the rows of pattern terms -- real CSR terms whose stored values are all
- *                     equal (v sum_e x[col_e]), and MAGNUS_TERM_FIELD_X next to MAGNUS_TERM_XXZ --
- *                     exactly in 64-bit integers on a fixed-point copy of each Leja vector, scaled
+ *   fixed_sums [1]:   fixed-point arithmetic on a copy Z of each Leja vector in int64 pairs, scaled
  *                     from a bound on its largest component (truncation below 2^-55 of that bound
- *                     per component for rows of up to 32 entries), for the linear generators (M2,
- *                     CF4, CF4:3) of plans with only CSR terms or the matrix-free chain; 0 = FP64
- *                     sums.  Not part of the paper, which computes in FP64 only.
+ *                     per component for rows of up to 32 entries): the rows of pattern terms (real
+ *                     CSR terms whose stored values are all equal, v sum_e x[col_e], and
+ *                     MAGNUS_TERM_FIELD_X next to MAGNUS_TERM_XXZ) are summed exactly in int64;
+ *                     the other real CSR terms multiply row-scaled 62-bit mantissas of their values
+ *                     by Z (high 64 bits of each product, summed exactly), and the XXZ bond flips
+ *                     their weights likewise.  Plans with only CSR terms or the matrix-free chain,
+ *                     generators M2, CF4, CF4:3 and M4 (M6 keeps FP64); batches: M2, CF4, CF4:3.
+ *                     0 = FP64 throughout.  Not part of the paper, which computes in FP64 only.
  */
 typedef struct {
   double tol_rel;
