@@ -80,7 +80,8 @@ struct ExpRec {
 
 constexpr int kM6Slots = 23;  // vectors the M6 generator keeps between its stages
 
-// Sense-reversing grid barrier state (one per plan, zero-initialised).
+// Grid barrier state (one per plan, zero-initialised): count's top bit flips at every completed
+// barrier (grid_barrier); gen is unused.
 struct GridBar {
   unsigned int count;
   unsigned int gen;

@@ -22,28 +22,29 @@ static __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
 static __device__ __forceinline__ double2 ldv(const double2 *p) { return __ldca(p); }
 
 // Grid-wide barrier with a bounded wait.  Returns false (in every thread of the block) if the
-// wait gave up or another block reported an error; the caller then leaves the kernel.
+// wait gave up or another block reported an error; the caller then leaves the kernel.  Every block
+// adds 1 to one counter, block 0 adds 2^31 - (nblocks - 1): the counter's top bit flips exactly at
+// the last arrival (its low 31 bits, zero at launch, return to zero for the next barrier), so the
+// waiters only watch that bit and the last block does no extra atomic.
 static __device__ __noinline__ bool grid_barrier(GridBar *bar, unsigned nblocks, long long limit_ns) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    const unsigned g = ld_acquire_gpu(&bar->gen);
+    const unsigned add = (blockIdx.x == 0) ? 0x80000000u - (nblocks - 1u) : 1u;
     __threadfence();
-    const unsigned prev = atomicAdd(&bar->count, 1u);
-    if (prev == nblocks - 1) {
-      atomicExch(&bar->count, 0u);
-      __threadfence();
-      atomicAdd(&bar->gen, 1u);
-    } else {
+    const unsigned old = atomicAdd(&bar->count, add);
+    if (!(((old + add) ^ old) & 0x80000000u)) {  // not the last arrival: wait for the flip
       const long long t0 = globaltimer_ns();
       for (unsigned spin = 0;; spin++) {
-        if (ld_acquire_gpu(&bar->gen) != g) break;
-        if (*(volatile int *)&bar->error) { ok = 0; break; }
-        if ((spin & 31u) == 31u && (globaltimer_ns() - t0 > limit_ns || spin > (1u << 28))) {
-          atomicExch(&bar->error, 1);
-          ok = 0;
-          break;
+        if ((ld_acquire_gpu(&bar->count) ^ old) & 0x80000000u) break;
+        if ((spin & 31u) == 31u) {
+          if (*(volatile int *)&bar->error) { ok = 0; break; }
+          if (globaltimer_ns() - t0 > limit_ns || spin > (1u << 28)) {
+            atomicExch(&bar->error, 1);
+            ok = 0;
+            break;
+          }
         }
         __nanosleep(20);
       }
