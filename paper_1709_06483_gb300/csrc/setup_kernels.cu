@@ -104,9 +104,10 @@ __global__ void k_leja_init(double *xi, int m, unsigned *counter) {
 // propagated directly: d = exp(-i rho Z) e_0 = (exp(-i (rho/q) Z))^q e_0 with q chosen so that
 // ||(rho/q) Z||_1 <= 1/2, each factor by its Taylor series acting on the vector.  One warp per
 // table; entry j lives in lane j % 32, register j / 32.
-constexpr int kDDRegs = (kMmaxLimit + 1) / 32;
+static_assert(kMmaxLimit + 1 <= 8 * 32, "divided differences: at most 8 entries per lane");
 
-__device__ void warp_divided_differences(const double *xi, int m, double rho, double2 phase, double2 *d) {
+template <int kDDRegs>
+__device__ void warp_divided_differences_r(const double *xi, int m, double rho, double2 phase, double2 *d) {
   // lane l holds entries j = kDDRegs l + r, so that the bidiagonal product needs one value from the
   // neighbouring lane per term; convergence is tested every fourth term (each test is two warp
   // reductions, the latency that bounds this single-warp computation)
@@ -164,6 +165,15 @@ __device__ void warp_divided_differences(const double *xi, int m, double rho, do
     const int j = kDDRegs * lane + r;
     if (j <= m) d[j] = cmul(phase, y[r]);
   }
+}
+
+// entries per lane: 4 (m <= 127, the default m_max = 100) or 8 (m <= 255); every entry a lane holds
+// costs FP64 instructions whether or not it is used
+__device__ void warp_divided_differences(const double *xi, int m, double rho, double2 phase, double2 *d) {
+  if (m < 128)
+    warp_divided_differences_r<4>(xi, m, rho, phase, d);
+  else
+    warp_divided_differences_r<8>(xi, m, rho, phase, d);
 }
 
 __global__ void k_divided_differences(const double *xi, int m, double rho, double2 *d) {

@@ -64,12 +64,14 @@ def test_leja_points_match_oracle(mg):
     assert xi[0] == 2.0 and xi[1] == -2.0 and xi[2] == 0.0
 
 
+@pytest.mark.parametrize("m_max", [100, 200])
 @pytest.mark.parametrize("rho", [0.0, 0.05, 0.9, 2.5, 4.0])
-def test_divided_differences_match_oracle(mg, rho):
+def test_divided_differences_match_oracle(mg, rho, m_max):
+    """Both lane layouts of the device computation (4 entries per lane up to m_max 127, else 8)."""
     c = mi.xxz_chain(1, 6, 0.01, 1)
-    plan = mg.Plan(c.dim, chain_terms(mg, c, "mfree"), drives_gpu(mg, c), m_max=100)
-    d = plan.divided_differences(rho, 101)
-    ref = oracle.divided_differences(oracle.leja_points(100), rho)
+    plan = mg.Plan(c.dim, chain_terms(mg, c, "mfree"), drives_gpu(mg, c), m_max=m_max)
+    d = plan.divided_differences(rho, m_max + 1)
+    ref = oracle.divided_differences(oracle.leja_points(m_max), rho)
     assert np.max(np.abs(d - ref)) < 2e-15
 
 
