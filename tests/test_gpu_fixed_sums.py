@@ -286,3 +286,36 @@ def test_values_beyond_the_fixed_point_range_keep_fp64_products(mg):
     st = plan.propagate(psi, 0.0, 1e-121, 6, "CF4")
     assert st["fixed_sums"] == 1
     assert rel(psi.cpu().numpy(), ref) < REL_TOL
+
+
+@pytest.mark.parametrize("kind", ["csr", "mfree"])
+@pytest.mark.parametrize("variant", ["CF4", "M4"])
+def test_many_vectors_each_with_its_own_scales(mg, kind, variant):
+    """5 states of very different size (1e-6 to 1e6) in one plan: every state has its own
+    fixed-point scales and maxima; each against the oracle with its own Leja degrees."""
+    c = mi.xxz_chain(50, 9, 0.01, 12, nvec=5)
+    psi0 = c.psi0 * (10.0 ** np.arange(-6, 7, 3))[:, None]
+    plan = mg.Plan(c.dim, chain_terms(mg, c, kind), drives(mg, c), nvec=5)
+    psi = cuda(psi0)
+    st = plan.propagate(psi, 0.0, c.h, c.nsteps, variant, log_cap=4096)
+    assert st["fixed_sums"] == 1
+    out = psi.cpu().numpy()
+    P = chain_problem(c)
+    for v in range(5):
+        ost = oracle.Stats(4096)
+        ref = P.propagate(psi0[v], 0.0, c.h, c.nsteps, variant, ost)
+        assert rel(out[v], ref) < REL_TOL, (v, rel(out[v], ref))
+        assert np.array_equal(st["m_log"].reshape(-1, 5)[:, v], ost.m_log)
+
+
+@pytest.mark.parametrize("ctas", [1, 3, 7])
+def test_ragged_block_partitions_fixed_point(mg, ctas):
+    """2^11 rows over a few blocks (partial warps at the block ends): Cf4 and M4 in fixed point."""
+    c = mi.xxz_chain(51, 11, 0.01, 8)
+    for kind in ("csr", "mfree"):
+        plan = mg.Plan(c.dim, chain_terms(mg, c, kind), drives(mg, c), ctas=ctas)
+        for variant in ("CF4", "M4"):
+            psi = cuda(c.psi0)
+            assert plan.propagate(psi, 0.0, c.h, c.nsteps, variant)["fixed_sums"] == 1
+            ref = chain_problem(c).propagate(c.psi0, 0.0, c.h, c.nsteps, variant)
+            assert rel(psi.cpu().numpy(), ref) < REL_TOL, (kind, variant)
