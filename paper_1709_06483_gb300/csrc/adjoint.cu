@@ -26,13 +26,19 @@ using namespace rows;
 
 constexpr int kABlock = 256;
 
-template <int FAM>
+// ZF: fixed-point sums and products (as in the propagation kernel) on copies of both stacked
+// vectors; their scales follow from bounds of each block's largest component, tracked with the norms.
+template <int FAM, bool ZF>
 __global__ void __launch_bounds__(kABlock, 2) k_aug_persistent(AugArgs a) {
   __shared__ Term sT[kMaxTerms];
   __shared__ ExpRec sR;
   __shared__ double s_jb[kMaxSpins], s_j2[kMaxSpins];
   __shared__ double s_red[2][kABlock / 32];
-  __shared__ double s_tot[2];
+  __shared__ unsigned s_rmx[4][kABlock / 32];
+  __shared__ double s_tot[6];  // two sums, then bounds of four maxima (a, b, p_a, p_b)
+  __shared__ double s_wz[kMaxTerms];
+  __shared__ long long s_cb[kMaxSpins], s_c2[kMaxSpins];
+  __shared__ int s_cbe, s_c2e;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned G = gridDim.x;
@@ -61,30 +67,92 @@ __global__ void __launch_bounds__(kABlock, 2) k_aug_persistent(AugArgs a) {
       s_j2[p - 1] = 2.0 * sT[0].J[cx.n - p - 1];
       s_jb[p - 1] = s_j2[p - 1] * R.bg[0];
     }
+  double opnorm = 0.0;  // ZF: sum_k |bg_k| ||H_k||_inf
+  if (ZF) {
+    __syncthreads();
+    if (tid < nt) s_wz[tid] = R.bg[tid] * sT[tid].pval;
+    for (int k = 0; k < nt; k++) opnorm = fma(fabs(R.bg[k]), sT[k].gnorm, opnorm);
+    if (FAM == FAM_MF && tid == 0) {  // bond weights (scaled and unscaled) as 62-bit mantissas
+      double w1 = 0.0, w2 = 0.0;
+      for (int p = 0; p < cx.n - 1; p++) {
+        w1 = fmax(w1, fabs(s_jb[p]));
+        w2 = fmax(w2, fabs(s_j2[p]));
+      }
+      int E1 = 0, E2 = 0;
+      if (w1 > 0.0) frexp(w1, &E1);
+      if (w2 > 0.0) frexp(w2, &E2);
+      E1 = max(-400, min(400, E1));
+      E2 = max(-400, min(400, E2));
+      for (int p = 0; p < cx.n - 1; p++) {
+        s_cb[p] = llrint(ldexp(s_jb[p], 62 - E1));
+        s_c2[p] = llrint(ldexp(s_j2[p], 62 - E2));
+      }
+      s_cbe = E1;
+      s_c2e = E2;
+    }
+    __syncthreads();
+    if (FAM == FAM_MF) {
+      cx.cb = s_cb;
+      cx.cbe = s_cbe;
+      cx.c2 = s_c2;
+      cx.c2e = s_c2e;
+    }
+  }
   unsigned it = 0;
   auto fail = [&](int status) {
     if (tid == 0) atomicCAS(&a.counters->status, 0, status);
   };
-  // partial sums of this block -> slot; barrier; every block sums all slots in the same order
-  auto reduce_all = [&](double x0, double x1) -> bool {
+  // partial sums (and, ZF, maxima as abshi high words) of this block -> slot; barrier; every block
+  // sums all slots in the same order
+  auto reduce_all = [&](double x0, double x1, unsigned m0 = 0u, unsigned m1 = 0u, unsigned m2 = 0u,
+                        unsigned m3 = 0u) -> bool {
     x0 = warp_sum(x0);
     x1 = warp_sum(x1);
-    if (lane == 0) { s_red[0][warp] = x0; s_red[1][warp] = x1; }
+    if (ZF) {
+      m0 = __reduce_max_sync(kFull, m0);
+      m1 = __reduce_max_sync(kFull, m1);
+      m2 = __reduce_max_sync(kFull, m2);
+      m3 = __reduce_max_sync(kFull, m3);
+    }
+    if (lane == 0) {
+      s_red[0][warp] = x0;
+      s_red[1][warp] = x1;
+      if (ZF) { s_rmx[0][warp] = m0; s_rmx[1][warp] = m1; s_rmx[2][warp] = m2; s_rmx[3][warp] = m3; }
+    }
     __syncthreads();
-    double *slot = a.partials + (size_t)(it & 1u) * G * 2;
+    double *slot = a.partials + (size_t)(it & 1u) * G * 6;
     if (tid == 0) {
       double y0 = 0.0, y1 = 0.0;
-      for (int w = 0; w < kABlock / 32; w++) { y0 += s_red[0][w]; y1 += s_red[1][w]; }
-      slot[2 * b] = y0;
-      slot[2 * b + 1] = y1;
+      unsigned n[4] = {0u, 0u, 0u, 0u};
+      for (int w = 0; w < kABlock / 32; w++) {
+        y0 += s_red[0][w];
+        y1 += s_red[1][w];
+        if (ZF)
+          for (int q = 0; q < 4; q++) n[q] = max(n[q], s_rmx[q][w]);
+      }
+      slot[6 * b] = y0;
+      slot[6 * b + 1] = y1;
+      for (int q = 0; q < 4; q++) slot[6 * b + 2 + q] = __hiloint2double((int)n[q], 0);
     }
     if (!grid_barrier(a.bar, G, a.spin_limit_ns)) return false;
     if (warp == 0) {
       double y0 = 0.0, y1 = 0.0;
-      for (int q = lane; q < (int)G; q += 32) { y0 += slot[2 * q]; y1 += slot[2 * q + 1]; }
+      unsigned n[4] = {0u, 0u, 0u, 0u};
+      for (int q = lane; q < (int)G; q += 32) {
+        y0 += slot[6 * q];
+        y1 += slot[6 * q + 1];
+        if (ZF)
+          for (int c = 0; c < 4; c++) n[c] = max(n[c], (unsigned)__double2hiint(slot[6 * q + 2 + c]));
+      }
       y0 = warp_sum(y0);
       y1 = warp_sum(y1);
-      if (lane == 0) { s_tot[0] = y0; s_tot[1] = y1; }
+      if (ZF)
+        for (int c = 0; c < 4; c++) n[c] = __reduce_max_sync(kFull, n[c]);
+      if (lane == 0) {
+        s_tot[0] = y0;
+        s_tot[1] = y1;
+        for (int c = 0; c < 4; c++) s_tot[2 + c] = abshi_bound(n[c]);
+      }
     }
     __syncthreads();
     it++;
@@ -93,14 +161,17 @@ __global__ void __launch_bounds__(kABlock, 2) k_aug_persistent(AugArgs a) {
 
   // [a; b] = [0; v]
   double s = 0.0;
+  unsigned mv = 0u;
   for (int64_t r = lo + tid; r < hi; r += blockDim.x) {
     const double2 v = a.v[r];
     a.acur[r] = make_double2(0.0, 0.0);
     a.bcur[r] = v;
     s += cabs2(v);
+    if (ZF) mv = max(mv, abshi(v));
   }
-  if (!reduce_all(s, 0.0)) { fail(MAGNUS_ETIMEOUT); return; }
+  if (!reduce_all(s, 0.0, 0u, mv)) { fail(MAGNUS_ETIMEOUT); return; }
   double vn = sqrt(s_tot[0]);
+  double vma = 0.0, vmb = s_tot[3];  // ZF: bounds of the largest components of the substep input
   const double2 *d = a.dd;
   double2 *ca = a.acur, *cb = a.bcur, *na = a.anxt, *nb = a.bnxt;
   if (!(R.gamma > 0.0)) {
@@ -114,8 +185,20 @@ __global__ void __launch_bounds__(kABlock, 2) k_aug_persistent(AugArgs a) {
   }
   const double invg = 1.0 / R.gamma;
   const double2 d0 = d[0];
+  const double zfac = a.zreal ? 1.0 : 2.0;
   for (int sub = 0; sub < R.s; sub++) {
     double ep = sqrt(cabs2(d0)) * vn, pn = vn;
+    double ma = vma, mb = vmb, pma = vma, pmb = vmb;
+    int zs_a = 0, zs_b = 0;
+    if (ZF) {  // fixed-point copies of the substep input
+      zs_a = fix_scale(vma, a.zhb);
+      zs_b = fix_scale(vmb, a.zhb);
+      for (int64_t r = lo + tid; r < hi; r += blockDim.x) {
+        a.zca[r] = fix2(ca[r], zs_a);
+        a.zcb[r] = fix2(cb[r], zs_b);
+      }
+      if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { fail(MAGNUS_ETIMEOUT); return; }
+    }
     bool done = false;
     for (int j = 1; j <= a.m_max; j++) {
       const double2 *sa = (j == 1) ? ca : (((j - 2) & 1) ? a.wa1 : a.wa0);
@@ -125,23 +208,64 @@ __global__ void __launch_bounds__(kABlock, 2) k_aug_persistent(AugArgs a) {
       const double shift = R.cg + a.xi[j - 1];
       const double2 dj = d[j];
       double sw = 0.0, sp = 0.0;
-      for (int64_t r = lo + tid; r < hi; r += blockDim.x) {
-        double2 xa, xb;
-        double2 ya = Op<FAM>::combo(cx, R, shift, sa, r, xa);
-        ya = rfma(invg, Op<FAM>::term(cx, a.kd, sb, r), ya);
-        const double2 yb = Op<FAM>::combo(cx, R, shift, sb, r, xb);
-        da[r] = ya;
-        db[r] = yb;
-        double2 pa = (j == 1) ? cmul(d0, xa) : na[r];
-        double2 pb = (j == 1) ? cmul(d0, xb) : nb[r];
-        pa = cfma(dj, ya, pa);
-        pb = cfma(dj, yb, pb);
-        na[r] = pa;
-        nb[r] = pb;
-        sw += cabs2(ya) + cabs2(yb);
-        sp += cabs2(pa) + cabs2(pb);
+      unsigned mya = 0u, myb = 0u, mpa = 0u, mpb = 0u;
+      int ys_a = 0, ys_b = 0;
+      if constexpr (ZF) {
+        // |y_a| <= (||X - shift|| max|a| + ||H_kd|| max|b| / gamma) (x2 complex), |y_b| <= ||X - shift|| max|b|
+        const double on = opnorm + fabs(shift);
+        ys_a = fix_scale(zfac * (on * ma + invg * sT[a.kd].gnorm * mb) * (1.0 + 0x1p-20), a.zhb);
+        ys_b = fix_scale(zfac * on * mb * (1.0 + 0x1p-20), a.zhb);
+        const longlong2 *za = (j == 1) ? a.zca : (((j - 2) & 1) ? a.zwa1 : a.zwa0);
+        const longlong2 *zb = (j == 1) ? a.zcb : (((j - 2) & 1) ? a.zwb1 : a.zwb0);
+        longlong2 *zda = ((j - 1) & 1) ? a.zwa1 : a.zwa0;
+        longlong2 *zdb = ((j - 1) & 1) ? a.zwb1 : a.zwb0;
+        for (int64_t r = lo + tid; r < hi; r += blockDim.x) {
+          double2 xa, xb;
+          double2 ya = Op<FAM>::combo_z(cx, R, s_wz, shift, sa, za, zs_a, r, xa);
+          ya = rfma(invg, Op<FAM>::term_z(cx, a.kd, sb, zb, zs_b, r), ya);
+          const double2 yb = Op<FAM>::combo_z(cx, R, s_wz, shift, sb, zb, zs_b, r, xb);
+          da[r] = ya;
+          db[r] = yb;
+          zda[r] = fix2(ya, ys_a);
+          zdb[r] = fix2(yb, ys_b);
+          double2 pa = (j == 1) ? cmul(d0, xa) : na[r];
+          double2 pb = (j == 1) ? cmul(d0, xb) : nb[r];
+          pa = cfma(dj, ya, pa);
+          pb = cfma(dj, yb, pb);
+          na[r] = pa;
+          nb[r] = pb;
+          sw += cabs2(ya) + cabs2(yb);
+          sp += cabs2(pa) + cabs2(pb);
+          mya = max(mya, abshi(ya));
+          myb = max(myb, abshi(yb));
+          mpa = max(mpa, abshi(pa));
+          mpb = max(mpb, abshi(pb));
+        }
+      } else {
+        for (int64_t r = lo + tid; r < hi; r += blockDim.x) {
+          double2 xa, xb;
+          double2 ya = Op<FAM>::combo(cx, R, shift, sa, r, xa);
+          ya = rfma(invg, Op<FAM>::term(cx, a.kd, sb, r), ya);
+          const double2 yb = Op<FAM>::combo(cx, R, shift, sb, r, xb);
+          da[r] = ya;
+          db[r] = yb;
+          double2 pa = (j == 1) ? cmul(d0, xa) : na[r];
+          double2 pb = (j == 1) ? cmul(d0, xb) : nb[r];
+          pa = cfma(dj, ya, pa);
+          pb = cfma(dj, yb, pb);
+          na[r] = pa;
+          nb[r] = pb;
+          sw += cabs2(ya) + cabs2(yb);
+          sp += cabs2(pa) + cabs2(pb);
+        }
       }
-      if (!reduce_all(sw, sp)) { fail(MAGNUS_ETIMEOUT); return; }
+      if (!reduce_all(sw, sp, mya, myb, mpa, mpb)) { fail(MAGNUS_ETIMEOUT); return; }
+      zs_a = ys_a;
+      zs_b = ys_b;
+      ma = s_tot[2];
+      mb = s_tot[3];
+      pma = s_tot[4];
+      pmb = s_tot[5];
       const double ej = sqrt(cabs2(dj)) * sqrt(s_tot[0]);
       pn = sqrt(s_tot[1]);
       if (!isfinite(ej) || !isfinite(pn)) { fail(MAGNUS_ENONFINITE); return; }
@@ -157,6 +281,8 @@ __global__ void __launch_bounds__(kABlock, 2) k_aug_persistent(AugArgs a) {
     }
     if (!done) { fail(MAGNUS_ENOCONV); return; }
     vn = pn;
+    vma = pma;
+    vmb = pmb;
     double2 *t = ca; ca = na; na = t;
     t = cb; cb = nb; nb = t;
   }
@@ -263,11 +389,13 @@ __global__ void k_adjoint_contract(const double2 *G, const double2 *z, const Coe
   }
 }
 
-const void *aug_kernel(int fam) {
+const void *aug_kernel(int fam, bool zf) {
+  if (zf && fam == FAM_CSR) return (const void *)k_aug_persistent<FAM_CSR, true>;
+  if (zf && fam == FAM_MF) return (const void *)k_aug_persistent<FAM_MF, true>;
   switch (fam) {
-    case FAM_CSR: return (const void *)k_aug_persistent<FAM_CSR>;
-    case FAM_MF: return (const void *)k_aug_persistent<FAM_MF>;
-    default: return (const void *)k_aug_persistent<FAM_GENERIC>;
+    case FAM_CSR: return (const void *)k_aug_persistent<FAM_CSR, false>;
+    case FAM_MF: return (const void *)k_aug_persistent<FAM_MF, false>;
+    default: return (const void *)k_aug_persistent<FAM_GENERIC, false>;
   }
 }
 
@@ -277,12 +405,13 @@ int aug_block_size() { return kABlock; }
 
 cudaError_t aug_max_blocks_per_sm(int *n) {
   int best = 1 << 30;
-  for (int fam = 0; fam < 3; fam++) {
-    int k = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, aug_kernel(fam), kABlock, 0);
-    if (e != cudaSuccess) return e;
-    best = k < best ? k : best;
-  }
+  for (int fam = 0; fam < 3; fam++)
+    for (int zf = 0; zf < 2; zf++) {
+      int k = 0;
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, aug_kernel(fam, zf != 0), kABlock, 0);
+      if (e != cudaSuccess) return e;
+      best = k < best ? k : best;
+    }
   *n = best;
   return cudaSuccess;
 }
@@ -290,7 +419,8 @@ cudaError_t aug_max_blocks_per_sm(int *n) {
 cudaError_t launch_aug_persistent(const AugArgs &a, int grid, cudaStream_t st) {
   AugArgs copy = a;
   void *args[] = {&copy};
-  return cudaLaunchCooperativeKernel(aug_kernel(a.fam), dim3(grid), dim3(kABlock), args, 0, st);
+  const bool zf = a.zfix && (a.fam == FAM_CSR || a.fam == FAM_MF);
+  return cudaLaunchCooperativeKernel(aug_kernel(a.fam, zf), dim3(grid), dim3(kABlock), args, 0, st);
 }
 
 cudaError_t launch_negate_records(const ExpRec *in, const double2 *din, ExpRec *out, double2 *dout, int64_t nexp,

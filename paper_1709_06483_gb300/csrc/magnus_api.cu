@@ -942,7 +942,9 @@ magnus_status magnus_adjoint_grad(magnus_plan_t p, const void *psi0, const void 
   CUDA_TRY(p, grab((void **)&G, sizeof(double2) * nexp));
   CUDA_TRY(p, grab((void **)&z, sizeof(double2)));
   CUDA_TRY(p, grab((void **)&gradd, sizeof(double) * ngrad));
-  CUDA_TRY(p, grab((void **)&apart, sizeof(double) * 4 * agrid));
+  CUDA_TRY(p, grab((void **)&apart, sizeof(double) * 12 * agrid));  // two slots x agrid x (2 sums, 4 maxima)
+  longlong2 *zaug = nullptr;  // fixed-point copies of the augmented vectors (substep input, ping-pong)
+  if (p->zc) CUDA_TRY(p, grab((void **)&zaug, sizeof(longlong2) * 6 * D));
   cdev = p->coeffs + kd;
 
   int grid, gv;
@@ -1016,6 +1018,13 @@ magnus_status magnus_adjoint_grad(magnus_plan_t p, const void *psi0, const void 
   g.spin_limit_ns = spin_limit(p);
   g.dlo = p->dlo;
   g.dhi = p->dhi;
+  g.zfix = zaug != nullptr;
+  g.zhb = p->zhb;
+  g.zreal = p->zreal;
+  if (zaug) {
+    g.zca = zaug; g.zcb = zaug + D; g.zwa0 = zaug + 2 * D; g.zwb0 = zaug + 3 * D; g.zwa1 = zaug + 4 * D;
+    g.zwb1 = zaug + 5 * D;
+  }
 
   // forward with a checkpoint at the start of every segment; the final state ends in p->alt's partner
   double2 *psiw = lam;  // lam doubles as the forward work vector until the backward pass starts

@@ -261,11 +261,15 @@ struct AugArgs {
   const double2 *v;        // input state
   double2 *out_a;          // L(Omega, -i H_kd) v
   double2 *acur, *bcur, *anxt, *bnxt, *wa0, *wb0, *wa1, *wb1;
-  double *partials;        // [2][grid][2]
+  double *partials;        // [2][grid][6]: two sums and four maxima per block
   GridBar *bar;
   Counters *counters;
   long long spin_limit_ns;
   const double *dlo, *dhi;
+  // fixed-point arithmetic (as in PersistArgs): copies of the substep input (zca, zcb) and of the
+  // ping-pong vectors of both blocks
+  int zfix, zhb, zreal;
+  longlong2 *zca, *zcb, *zwa0, *zwb0, *zwa1, *zwb1;
 };
 int aug_block_size();
 cudaError_t aug_max_blocks_per_sm(int *n);
