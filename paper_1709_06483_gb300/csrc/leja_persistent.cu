@@ -16,7 +16,10 @@
 // minimal and many independent loads in flight:
 //   FAM_CSR     every term CSR (real-valued values multiply only the real parts);
 //   FAM_MF      matrix-free XXZ chain + transverse field, diagonal from two small tables;
-//   FAM_GENERIC any mix of CSR and matrix-free terms.
+//   FAM_GENERIC any mix of CSR and matrix-free terms;
+// and per arithmetic: ZF = 0 FP64 throughout; ZF = 1 (linear generators) and ZF = 2 (M4) take the
+// matvecs in fixed point on int64 copies of the vectors (exact sums of pattern terms, products of
+// row-scaled value mantissas, rows.cuh), which leaves 14 FP64 instructions per row.
 // Vectors written by other blocks between barriers are read with ordinary (coherent, L1-cached)
 // loads; only the immutable matrices use the read-only path.
 #include <math.h>

@@ -1,6 +1,7 @@
-// Rows of the operators: (H_k x)[r] for CSR, matrix-free XXZ and transverse-field terms, and the
-// compile-time operator families of the persistent kernels.  Shared by the single-problem kernel
-// (leja_persistent.cu) and the batched kernel (batched.cu).
+// Rows of the operators: (H_k x)[r] for CSR, matrix-free XXZ and transverse-field terms, in FP64
+// and in fixed point (on an int64 copy of x), and the compile-time operator families of the
+// persistent kernels.  Shared by the single-problem kernel (leja_persistent.cu), the batched kernel
+// (batched.cu), the adjoint's augmented kernel (adjoint.cu) and the matvec entry point (apply.cu).
 #pragma once
 
 #include "magnus_internal.cuh"
