@@ -31,6 +31,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Magnus steps/s and Leja matvec GB/s vs plain FP64 GPU path at ≤1e-8 error"
+SUMS_FIXED = ("exact int64 fixed point: the sum_i sx_i row sums and the H_s (or bond) products; FP64: "
+              "the conversions back, the Leja update and the norms")
 HBM_PEAK_FALLBACK = 6800.0
 SMS, FP64_FMA_PER_CLK, SM_MAX_MHZ = 152, 2, 2070.0
 FP64_PEAK_TFLOPS = SMS * FP64_FMA_PER_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12  # 1.259 TFLOP/s derived
@@ -336,7 +338,7 @@ def run_ours(args):
         "config": {"workload": f"xxz_chain_20spins_{storage}_{variant.lower()}", "spins": c.nspins, "dim": c.dim,
                    "nnz": nnz_total, "h": c.h, "t0": c.t0, "variant": variant, "storage": storage,
                    "interval": args.interval,
-                   "sums": "sum_i sx_i rows in exact int64 fixed point, the rest FP64" if fixed else "FP64",
+                   "sums": SUMS_FIXED if fixed else "FP64",
                    "leja_tol": 1e-10, "l2": "inputs larger than L2: the 640 MB CSR is streamed every iteration"
                    if storage.startswith("csr") else "matrix-free; 4 state vectors of 16 MB stay L2-resident",
                    "parallelism": f"replicas x{world}"},
@@ -551,7 +553,7 @@ def run_batch512(args):
         "config": {"workload": f"batch_512_xxz_chains_8to14spins_{args.storage}_{args.variant.lower()}",
                    "chains": len(chains), "rows": rows, "nnz": nnz, "h": 0.01, "variant": args.variant,
                    "cta_size": st["block"], "cluster_size": st["cluster"],
-                   "sums": "sum_i sx_i rows in exact int64 fixed point, the rest FP64" if fixed else "FP64"},
+                   "sums": SUMS_FIXED if fixed else "FP64"},
         "chain_steps_per_s": round(len(chains) * args.steps / (gms / 1e3), 1),
         "per_chain_plans": {"steps_per_s": round(seq_rate, 3), "how": f"one plan and launch per chain (same "
                             f"arithmetic), {len(sample)} of 512 chains x {seq_steps} steps, wall time scaled by the "
@@ -647,11 +649,19 @@ def run_adjoint16(args):
 # --------------------------------------------------------------------------- the matvec alone
 def run_spmv20(args):
     """The generator matvec in isolation (magnus_apply): y = (H_s + H_d) x on the 20-spin chain,
-    one state; --steps applications timed with CUDA events after --warmup.  Algorithmic bytes per
-    application: CSR 12 B per stored entry (8 B real value -- a plan keeps complex-stored real values
-    as a float64 copy -- + 4 B column) + 2 x 8 B row pointers per row + 16 B
-    read of x (each element once) + 16 B write of y per row; matrix-free 32 B per row.  FP64 work in
-    FMA-equivalent flops as in the Leja iteration, without the shift, update and norms."""
+    one state; --steps applications timed with CUDA events after --warmup.
+
+    FP64 arithmetic (--fixed-sums 0), algorithmic bytes per application: CSR 12 B per stored entry
+    (8 B real value -- a plan keeps complex-stored real values as a float64 copy -- + 4 B column)
+    + 2 x 8 B row pointers per row + 16 B read of x (each element once) + 16 B write of y per row;
+    matrix-free 32 B per row.  Bound by the FP64 pipe: FMA-equivalent flops as in the Leja
+    iteration, without the shift, update and norms.
+
+    Fixed point (default): 12 B per H_s entry (62-bit value mantissa + column), 4 B per entry of the
+    pattern term sum_i sx_i (column only), 8 B of row pointer and 2 B of row exponent per row, and
+    80 B per row of vectors: x read twice (max |x|, then the copy Z = trunc(x 2^s)), Z written and
+    read once, y written.  About 6 FP64 instructions per row remain (the weighted conversions back
+    to FP64), so the bound is HBM."""
     import torch
 
     import magnus_inputs as mi
@@ -662,7 +672,8 @@ def run_spmv20(args):
     mg.load()
     c = mi.workload2()
     terms = workload_terms(mg, c, args.storage)
-    plan = mg.Plan(c.dim, terms, drives(mg, c))
+    fixed = bool(args.fixed_sums)
+    plan = mg.Plan(c.dim, terms, drives(mg, c), fixed_sums=fixed)
     x = torch.from_numpy(c.psi0).cuda()
     y = torch.empty_like(x)
     beta = np.array([1.0, 1.0])
@@ -680,27 +691,38 @@ def run_spmv20(args):
     ms = e0.elapsed_time(e1) / args.steps
     D, n = c.dim, c.nspins
     if args.storage.startswith("csr"):
-        nnz = sum(t.col.numel() for t in terms)
-        nbytes = 12 * nnz + 2 * 8 * (D + 1) + 32 * D  # real values: the plan's float64 copy (csr) or the storage
-        inst = 2 * nnz + 4 * D
+        nnz_s, nnz_d = (t.col.numel() for t in terms)
+        if fixed:
+            nbytes = 12 * nnz_s + 4 * nnz_d + 8 * (D + 1) + 2 * D + 80 * D
+            inst = 6 * D
+        else:
+            nbytes = 12 * (nnz_s + nnz_d) + 2 * 8 * (D + 1) + 32 * D  # real values: the plan's float64 copy
+            inst = 2 * (nnz_s + nnz_d) + 4 * D
     else:
-        nbytes = 32 * D
-        inst = D * (4 + (n - 1) + 2 * n + 2)
+        nbytes = 80 * D if fixed else 32 * D
+        inst = D * 8 if fixed else D * (4 + (n - 1) + 2 * n + 2)
     gbs = nbytes / (ms / 1e3) / 1e9
     tflops = 2 * inst / (ms / 1e3) / 1e12
     peaks = measured_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", HBM_PEAK_FALLBACK))
+    if fixed:  # the FP64 pipe holds only the conversions back: HBM bytes are the bound
+        roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": round(hbm_peak, 1), "unit": "GB/s",
+                "frac": round(gbs / hbm_peak, 4), "fp64_tflops": round(tflops, 4),
+                "fp64_frac": round(tflops / FP64_PEAK_TFLOPS, 4)}
+    else:
+        roof = {"bound": "alu", "achieved": round(tflops, 4), "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
+                "frac": round(tflops / FP64_PEAK_TFLOPS, 4), "hbm_gbs": round(gbs, 1),
+                "hbm_frac": round(gbs / hbm_peak, 4)}
+    roof.update({"kernel": "k_apply", "traffic": None, "algorithmic_bytes": nbytes})
     line = {
         "metric": METRIC, "value": round(gbs, 1), "unit": "GB/s (generator matvec alone)", "n_gpus": world,
         "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(ms, 4), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+i64" if fixed else "f64", "data": "synthetic",
         "config": {"workload": f"matvec_xxz_chain_20spins_{args.storage}", "spins": n, "dim": D, "states": 1,
+                   "sums": SUMS_FIXED if fixed else "FP64",
                    "l2": "inputs larger than L2" if args.storage.startswith("csr") else "matrix-free, L2-resident"},
-        "roofline": {"bound": "alu", "kernel": "k_apply", "achieved": round(tflops, 4),
-                     "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s", "frac": round(tflops / FP64_PEAK_TFLOPS, 4),
-                     "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 4), "traffic": None,
-                     "algorithmic_bytes": nbytes},
-        "gpu_launches": args.steps, "clocks": clk.summary(),
+        "roofline": roof,
+        "gpu_launches": args.steps * (3 if fixed else 1), "clocks": clk.summary(),
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -156,8 +156,11 @@ typedef enum {
  *                     the other real CSR terms multiply row-scaled 62-bit mantissas of their values
  *                     by Z (high 64 bits of each product, summed exactly), and the XXZ bond flips
  *                     their weights likewise.  Plans with only CSR terms or the matrix-free chain,
- *                     generators M2, CF4, CF4:3 and M4 (M6 keeps FP64); batches: M2, CF4, CF4:3.
- *                     0 = FP64 throughout.  Not part of the paper, which computes in FP64 only.
+ *                     generators M2, CF4, CF4:3 and M4 (M6 keeps FP64) and magnus_apply; batches:
+ *                     M2, CF4, CF4:3.  The scale follows the vector across the whole double range;
+ *                     a converted result below 2^-1022 flushes to zero (FP64 would keep a
+ *                     subnormal).  0 = FP64 throughout.  Not part of the paper, which computes in
+ *                     FP64 only.
  */
 typedef struct {
   double tol_rel;
@@ -259,6 +262,11 @@ MAGNUS_API magnus_status magnus_set_coeff(magnus_plan_t plan, int32_t k, const m
  * y = sum_k beta_k H_k x for every state: the generator matvec of the Leja recurrence (Sec. 3, the
  * operation the method's cost is made of), as a call of its own (expectation values, timing).
  * beta: host, nterms reals.  x, y: device complex128 [nvec][dim], distinct, 16-byte aligned.
+ * Plans with fixed_sums (CSR with a pattern or real term, matrix-free chains) take the rows as the
+ * Leja iteration does: the plan's fixed-point copy of x (one scale per state, from max |x|), exact
+ * integer row sums and value products, one rounding back to FP64 per row and term; a state holding
+ * an Inf or NaN takes the FP64 rows.  Three launches then, one otherwise; the plan's copy buffers
+ * are in use until they finish (stream-ordered).
  * Asynchronous on the plan's stream (no synchronisation).  Errors: EINVAL, ECUDA.
  */
 MAGNUS_API magnus_status magnus_apply(magnus_plan_t plan, const double *beta, const void *x, void *y);

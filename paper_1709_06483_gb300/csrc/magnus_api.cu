@@ -71,6 +71,7 @@ struct magnus_plan_s {
   // exact fixed-point sums of pattern terms: Z copies of the substep input and the Leja vectors
   longlong2 *zc = nullptr, *zw0 = nullptr, *zw1 = nullptr;
   longlong2 *zu = nullptr;  // M4 in fixed point: copies of u_k, on first use
+  unsigned *zmax = nullptr;  // magnus_apply in fixed point: max |x| per state (high words)
   double *rcopy[kMaxTerms] = {nullptr, nullptr, nullptr, nullptr};  // real parts of complex-stored real CSR terms
   long long *fval[kMaxTerms] = {nullptr, nullptr, nullptr, nullptr};  // fixed-point values of real CSR terms
   int16_t *fexp[kMaxTerms] = {nullptr, nullptr, nullptr, nullptr};    // and their row exponents
@@ -117,7 +118,7 @@ void free_plan(magnus_plan_t p) {
                   p->hsplit[0], p->hsplit[1], p->hsplit[2], p->hsplit[3], p->sh_cur, p->sh_w0, p->sh_w1, p->sh_u,
                   p->hslice[0], p->hslice[1], p->hslice[2], p->hslice[3], p->hexp[0], p->hexp[1], p->hexp[2],
                   p->hexp[3], p->sl_cur, p->sl_w0, p->sl_w1, p->sl_u, p->ex_sets, p->colmax, p->m6,
-                  p->tc_hd, p->tc_eh, p->tc_wd, p->tc_ex, p->tc_P, p->zc, p->zw0, p->zw1, p->zu,
+                  p->tc_hd, p->tc_eh, p->tc_wd, p->tc_ex, p->tc_P, p->zc, p->zw0, p->zw1, p->zu, p->zmax,
                   p->rcopy[0], p->rcopy[1], p->rcopy[2], p->rcopy[3], p->fval[0], p->fval[1], p->fval[2],
                   p->fval[3], p->fexp[0], p->fexp[1], p->fexp[2], p->fexp[3]};
   for (void *b : bufs)
@@ -730,6 +731,7 @@ magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms
       PLAN_TRY(dalloc(&p->zc, nd));
       PLAN_TRY(dalloc(&p->zw0, nd));
       PLAN_TRY(dalloc(&p->zw1, nd));
+      PLAN_TRY(dalloc(&p->zmax, o.nvec));
       // fixed-point values of the real CSR terms that are not patterns
       if (p->fam == FAM_CSR)
         for (int k = 0; k < nterms; k++) {
@@ -854,7 +856,7 @@ magnus_status magnus_apply(magnus_plan_t p, const double *beta, const void *x, v
   for (int k = 0; k < p->nterms; k++)
     if (!(beta[k] == beta[k]) || beta[k] - beta[k] != 0.0) return set_err(p, MAGNUS_EINVAL, "beta[%d] not finite", k);
   CUDA_TRY(p, launch_apply(p->fam, p->terms, p->nterms, beta, p->lbits, p->dlo, p->dhi, (const double2 *)x,
-                           (double2 *)y, p->dim, p->opt.nvec, p->num_sms, p->stream));
+                           (double2 *)y, p->dim, p->opt.nvec, p->zc, p->zmax, p->zhb, p->num_sms, p->stream));
   return MAGNUS_OK;
 }
 

@@ -125,10 +125,12 @@ cudaError_t launch_gershgorin(const Term *t_dev, const Term &t_host, int64_t dim
                               double *out, cudaStream_t st);
 // Real-valuedness check of a CSR / dense term: flag (device int) set to 1 if any imaginary part != 0.
 cudaError_t launch_imag_check(const double2 *val, int64_t n, int *flag, cudaStream_t st);
-// y = sum_k beta_k H_k x for nv states (the plan's operator family)
+// y = sum_k beta_k H_k x for nv states (the plan's operator family).  With zc and zmax (CSR and
+// matrix-free plans in fixed point): the Z copy of x goes to zc [nv][D] at the scale of max |x| per
+// state (reduced into zmax[nv]), and the pattern sums and value products run on it; else FP64.
 cudaError_t launch_apply(int fam, const Term *terms, int nt, const double *beta, int lbits, const double *dlo,
-                         const double *dhi, const double2 *x, double2 *y, int64_t D, int nv, int num_sms,
-                         cudaStream_t st);
+                         const double *dhi, const double2 *x, double2 *y, int64_t D, int nv, longlong2 *zc,
+                         unsigned *zmax, int zhb, int num_sms, cudaStream_t st);
 // ab_dev (in: the term's Gershgorin enclosure) <- its intersection with the Lanczos enclosure after
 // m steps; synchronises the stream
 cudaError_t lanczos_interval(const Term *t_dev, const Term &t_host, int64_t D, int m, double *ab_dev, cudaStream_t st);

@@ -186,14 +186,15 @@ static __device__ __forceinline__ double2 fieldx_row_scaled(int n, double coef, 
 // entries stays below 2^61 (fix_scale); the truncation is below 2^-s < 2^(hb-61) B per component.
 // The row sum goes back to FP64 once, rounded to nearest (unfix).
 
-// scale s for components bounded by B: the smallest e with B < 2^e gives s = 62 - hb - e
-// (clamped to [-900, 1000], where unfix still builds normal doubles; B = 0 takes the largest)
+// scale s for components bounded by B: the smallest e with B < 2^e gives s = 62 - hb - e, in
+// [-963 - hb, 1084 - hb] for every B up to Inf (B = 0 takes the largest), so the copy keeps its
+// 62 - hb bits at any magnitude of the vector
 static __device__ __forceinline__ int fix_scale(double B, int hb) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(B);
   const int ex = (int)(b >> 52) & 0x7FF;  // B in [2^(ex-1023), 2^(ex-1022)); B < 2^-1022 if ex = 0
   int s = 62 - hb - (ex - 1022);
-  if (!(B > 0.0)) s = 1000;
-  return min(max(s, -900), 1000);
+  if (!(B > 0.0)) s = 1084;
+  return min(max(s, -1000), 1100);
 }
 
 // trunc(x 2^s) from the bits of x (integer operations only)
@@ -208,7 +209,9 @@ static __device__ __forceinline__ long long fix64(double x, int s) {
 }
 static __device__ __forceinline__ longlong2 fix2(double2 v, int s) { return make_longlong2(fix64(v.x, s), fix64(v.y, s)); }
 
-// n 2^-s rounded to the nearest double (ties to even), built from the bits of n
+// n 2^-s rounded to the nearest double (ties to even), built from the bits of n; a result below
+// 2^-1022 flushes to a signed zero and one above the largest double gives a signed infinity (the
+// scales of products, s - fe - 2, reach past both ends)
 static __device__ __forceinline__ double unfix(long long n, int s) {
   const unsigned long long sg = (unsigned long long)n & 0x8000000000000000ull;
   const unsigned long long a0 = sg ? 0ull - (unsigned long long)n : (unsigned long long)n;
@@ -217,9 +220,12 @@ static __device__ __forceinline__ double unfix(long long n, int s) {
   unsigned long long m = a >> 11;                // 53 significant bits
   const unsigned rb = (unsigned)a & 0x7FFu;      // the 11 bits below them
   m += (rb > 0x400u || (rb == 0x400u && (m & 1ull))) ? 1ull : 0ull;
-  // value = (m / 2^52) 2^(63 - lz - s); m's leading one (or its carry to 2^53) lands in the exponent
-  const unsigned long long bits = sg | (((unsigned long long)(1085 - lz - s) << 52) + m);
-  return a0 ? __longlong_as_double((long long)bits) : 0.0;
+  // value = (m / 2^52) 2^(63 - lz - s); m's leading one (or its carry to 2^53) lands in the exponent,
+  // whose field is ef + 1 (ef + 2 after a carry): normal for ef in [0, 2045], 2046 + a carry is Inf
+  const int ef = 1085 - lz - s;
+  const unsigned long long bits = sg | (((unsigned long long)ef << 52) + m);
+  if (!a0 || ef < 0) return __longlong_as_double((long long)sg);
+  return __longlong_as_double((long long)(ef > 2045 ? (sg | 0x7FF0000000000000ull) : bits));
 }
 static __device__ __forceinline__ double2 unfix2(longlong2 n, int s) { return make_double2(unfix(n.x, s), unfix(n.y, s)); }
 

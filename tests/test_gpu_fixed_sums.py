@@ -319,3 +319,81 @@ def test_ragged_block_partitions_fixed_point(mg, ctas):
             assert plan.propagate(psi, 0.0, c.h, c.nsteps, variant)["fixed_sums"] == 1
             ref = chain_problem(c).propagate(c.psi0, 0.0, c.h, c.nsteps, variant)
             assert rel(psi.cpu().numpy(), ref) < REL_TOL, (kind, variant)
+
+
+# ----------------------------------------------------------------- the generator matvec alone
+def rel_scaled(a, b):
+    """rel() after dividing both by max |b|, so that vectors near the ends of the double range do
+    not overflow or underflow inside the norms."""
+    s = np.max(np.abs(b))
+    return rel(a / s, b / s)
+
+
+@pytest.mark.parametrize("kind", ["csr", "csr_real", "mfree"])
+def test_apply_fixed_point_any_magnitude(mg, kind):
+    """magnus_apply in fixed point: states of size 1e-290, 1e-3, 1e5 and 1e290 (each with its own
+    scale; the copy keeps its full width at both ends of the double range) and a zero state, against
+    the oracle's term products and beside the FP64 matvec."""
+    c = mi.xxz_chain(52, 10, 0.01, 1, nvec=5)
+    x0 = c.psi0 * np.array([1e-290, 1e-3, 1e5, 1e290, 0.0])[:, None]
+    beta = np.array([0.7, -1.3])
+    ys = {}
+    for fixed in (True, False):
+        plan = mg.Plan(c.dim, chain_terms(mg, c, kind), drives(mg, c), nvec=5, fixed_sums=fixed)
+        ys[fixed] = plan.apply(beta, cuda(x0)).cpu().numpy()
+        plan.close()
+    P = chain_problem(c)
+    for v in range(4):
+        ref = beta[0] * P.apply_term(0, x0[v]) + beta[1] * P.apply_term(1, x0[v])
+        for fixed in (True, False):
+            assert rel_scaled(ys[fixed][v], ref) < 1e-13, (fixed, v, rel_scaled(ys[fixed][v], ref))
+    assert not np.any(ys[True][4] != 0)
+
+
+@pytest.mark.parametrize("kind", ["csr", "mfree"])
+def test_apply_fixed_point_nonfinite_state_takes_fp64_rows(mg, kind):
+    """A state holding an Inf and a NaN: its rows run in FP64 and give the FP64 matvec's non-finite
+    entries; the finite state beside it keeps the fixed-point rows."""
+    c = mi.xxz_chain(53, 9, 0.01, 1, nvec=2)
+    x0 = c.psi0.copy()
+    x0[0, 17] = np.inf
+    x0[0, 300] = complex(0.0, np.nan)
+    beta = np.array([0.9, 0.4])
+    ys = {}
+    for fixed in (True, False):
+        plan = mg.Plan(c.dim, chain_terms(mg, c, kind), drives(mg, c), nvec=2, fixed_sums=fixed)
+        ys[fixed] = plan.apply(beta, cuda(x0)).cpu().numpy()
+        plan.close()
+    for part in (np.real, np.imag):
+        a, b = part(ys[True][0]), part(ys[False][0])
+        assert np.array_equal(np.isnan(a), np.isnan(b))
+        assert np.array_equal(np.isinf(a), np.isinf(b))
+        fin = np.isfinite(b)
+        assert not np.all(fin)
+        assert np.allclose(a[fin], b[fin], rtol=1e-12, atol=0.0)
+    P = chain_problem(c)
+    ref = beta[0] * P.apply_term(0, x0[1]) + beta[1] * P.apply_term(1, x0[1])
+    assert rel(ys[True][1], ref) < 1e-13
+
+
+def test_apply_fixed_point_general_terms(mg):
+    """magnus_apply on a ragged pattern term beside a real term whose values span 8 decades (value
+    mantissas at per-row exponents) and a complex term (FP64 rows), dim 1003, 3 states."""
+    rng = np.random.default_rng(531)
+    D = 1003
+    mats = (_pattern_csr(rng, D, -0.75, 24), _random_real_csr(rng, D, 0.01, 8), _hermitian_csr(rng, D, 0.005))
+    terms = [mg.CSRTerm(cuda(r), cuda(c), cuda(v)) for r, c, v in mats]
+    const = [mg.Drive.const()] * 3
+    x0 = ((rng.standard_normal((3, D)) + 1j * rng.standard_normal((3, D))) *
+          np.array([1e-200, 1.0, 1e200])[:, None])
+    beta = np.array([1.1, -0.3, 0.6])
+    ys = {}
+    for fixed in (True, False):
+        plan = mg.Plan(D, terms, const, nvec=3, fixed_sums=fixed)
+        ys[fixed] = plan.apply(beta, cuda(x0)).cpu().numpy()
+        plan.close()
+    P = oracle.Problem([oracle.CSR(r, c, v.astype(np.complex128)) for r, c, v in mats], [oracle.Coeff.const()] * 3)
+    for v in range(3):
+        ref = sum(beta[k] * P.apply_term(k, x0[v]) for k in range(3))
+        for fixed in (True, False):
+            assert rel_scaled(ys[fixed][v], ref) < 1e-13, (fixed, v, rel_scaled(ys[fixed][v], ref))
