@@ -10,8 +10,6 @@
 // pipe left with the per-row conversions.
 #include <cuda_runtime.h>
 
-#include <algorithm>
-
 #include "magnus_internal.cuh"
 #include "persist_common.cuh"
 #include "rows.cuh"
@@ -31,26 +29,45 @@ constexpr int apply_min_blocks() {
   return ZF ? (FAM == FAM_CSR ? 4 : 3) : 0;
 }
 
-// m[v] = max over the rows of state v of abshi(x) (m zeroed by the launcher); grid (blocks, nv)
+// the two passes over x take kPassRows rows per thread (loads issued together, coalesced), grid
+// (ceil(D / (256 kPassRows)), nv)
+constexpr int kPassRows = 4;
+
+// m[v] = max over the rows of state v of abshi(x) (m zeroed by the launcher); one atomic per
+// block (atomics of every warp on the one word serialise at L2)
 __global__ void __launch_bounds__(256) k_apply_absmax(const double2 *x, int64_t D, unsigned *m) {
+  __shared__ unsigned s_h[8];
   const double2 *xv = x + (int64_t)blockIdx.y * D;
+  const int64_t r0 = (int64_t)blockIdx.x * blockDim.x * kPassRows + threadIdx.x;
   unsigned h = 0;
-  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < D; r += (int64_t)gridDim.x * blockDim.x)
-    h = max(h, abshi(xv[r]));
+#pragma unroll
+  for (int u = 0; u < kPassRows; u++) {
+    const int64_t r = r0 + (int64_t)u * blockDim.x;
+    if (r < D) h = max(h, abshi(xv[r]));
+  }
   h = __reduce_max_sync(0xFFFFFFFFu, h);
-  if ((threadIdx.x & 31) == 0 && h) atomicMax(m + blockIdx.y, h);
+  if ((threadIdx.x & 31) == 0) s_h[threadIdx.x >> 5] = h;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < 8; w++) h = max(h, s_h[w]);
+    if (h) atomicMax(m + blockIdx.y, h);
+  }
 }
 
 // Z copy of state v at the scale of its bound (a state with a non-finite entry is left to the
-// FP64 rows); grid (blocks, nv)
+// FP64 rows)
 __global__ void __launch_bounds__(256) k_apply_fix(const double2 *x, int64_t D, const unsigned *m, int hb,
                                                    longlong2 *z) {
   const unsigned h = m[blockIdx.y];
   if (h >= 0x7FF00000u) return;
   const int zs = fix_scale(abshi_bound(h), hb);
   const int64_t off = (int64_t)blockIdx.y * D;
-  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < D; r += (int64_t)gridDim.x * blockDim.x)
-    z[off + r] = fix2(x[off + r], zs);
+  const int64_t r0 = (int64_t)blockIdx.x * blockDim.x * kPassRows + threadIdx.x;
+#pragma unroll
+  for (int u = 0; u < kPassRows; u++) {
+    const int64_t r = r0 + (int64_t)u * blockDim.x;
+    if (r < D) z[off + r] = fix2(x[off + r], zs);
+  }
 }
 
 template <int FAM, bool ZF>
@@ -157,15 +174,16 @@ cudaError_t launch_apply(int fam, const Term *terms, int nt, const double *beta,
   if (zc && zmax && (fam == FAM_CSR || fam == FAM_MF)) {
     cudaError_t e = cudaMemsetAsync(zmax, 0, sizeof(unsigned) * nv, st);
     if (e != cudaSuccess) return e;
-    // one pass over x each: num_sms x 4 blocks of 256 rows per state cover the 2^20-row chains in ~7 rounds
-    const int64_t per = (D + 255) / 256;
-    const dim3 g2((unsigned)std::min<int64_t>(per, (int64_t)num_sms * 4), (unsigned)nv);
+    const dim3 g2((unsigned)((D + 256 * kPassRows - 1) / (256 * kPassRows)), (unsigned)nv);
     k_apply_absmax<<<g2, 256, 0, st>>>(x, D, zmax);
     k_apply_fix<<<g2, 256, 0, st>>>(x, D, zmax, zhb, zc);
+    // the rows: one wave of resident blocks
     if (fam == FAM_CSR)
-      k_apply<FAM_CSR, true><<<grid, 256, 0, st>>>(terms, nt, b, lbits, dlo, dhi, x, y, D, nv, zc, zmax, zhb);
+      k_apply<FAM_CSR, true><<<num_sms * apply_min_blocks<FAM_CSR, true>(), 256, 0, st>>>(
+          terms, nt, b, lbits, dlo, dhi, x, y, D, nv, zc, zmax, zhb);
     else
-      k_apply<FAM_MF, true><<<grid, 256, 0, st>>>(terms, nt, b, lbits, dlo, dhi, x, y, D, nv, zc, zmax, zhb);
+      k_apply<FAM_MF, true><<<num_sms * apply_min_blocks<FAM_MF, true>(), 256, 0, st>>>(
+          terms, nt, b, lbits, dlo, dhi, x, y, D, nv, zc, zmax, zhb);
     return cudaGetLastError();
   }
   switch (fam) {
