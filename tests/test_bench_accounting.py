@@ -1,0 +1,89 @@
+"""bench.py's algorithmic accounting and its reference-arm JSON line, on CPU.
+
+The roofline fraction of the bench line divides the algorithmic bytes of one Leja iteration by the
+kernel's time, so those bytes are pinned here to a count made independently: the stored entries of
+the XXZ chain come from the oracle's CSR builders (checked against Kronecker products in
+test_oracle_pins.py), and the per-entry and per-row sizes are those of the data layout (int32
+columns, int64 row pointers, float64 values or 62-bit mantissas, int16 row exponents, complex128
+vectors and their int64-pair fixed-point copies).
+"""
+import json
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+import bench
+import magnus_inputs as mi
+import oracle
+
+
+def _chain_nnz(n):
+    c = mi.xxz_chain(7, n, 0.01, 1)
+    Hs = oracle.xxz_csr(n, c.J, c.hz, c.delta)
+    Hd = oracle.field_x_csr(n)
+    return c, int(Hs.rowptr[-1]), int(Hd.rowptr[-1])
+
+
+@pytest.mark.parametrize("n", [4, 7, 10])
+def test_chain_entry_counts(n):
+    """H_s: the diagonal plus one entry per anti-parallel bond (half the rows per bond); the field:
+    one entry per single-bit flip."""
+    c, nnz_s, nnz_d = _chain_nnz(n)
+    D = 2 ** n
+    assert c.dim == D
+    assert nnz_s == D + (n - 1) * D // 2
+    assert nnz_d == n * D
+
+
+def test_bytes_per_iteration_fixed_point_csr():
+    """Cf4, 20 spins, fixed point, one substep per exponential and 7 Leja iterations per exponential
+    (the substep inputs' copies are shared by 7 iterations)."""
+    c = mi.workload2()
+    D, n = c.dim, c.nspins
+    nnz_s, nnz_d = D + (n - 1) * D // 2, n * D
+    nbytes, flops = bench.algorithmic_per_iteration(c, "csr", "CF4", (nnz_s, nnz_d), fixed=True,
+                                                    subs_per_it=1.0 / 7.0)
+    matrix = nnz_s * (8 + 4) + nnz_d * 4 + (D + 1) * 8 + D * 2
+    vectors = D * (16 + 16 + 32) + D * (16 + 16) + D * (16 + 16) / 7.0
+    assert nbytes == int(matrix + vectors) == 331949210
+    assert flops == 2 * 14 * D
+
+
+def test_bytes_per_iteration_fp64_csr_and_matrix_free():
+    c = mi.workload2()
+    D, n = c.dim, c.nspins
+    nnz = (D + (n - 1) * D // 2, n * D)
+    nbytes, flops = bench.algorithmic_per_iteration(c, "csr", "CF4", nnz, fixed=False)
+    assert nbytes == sum(nnz) * 12 + 2 * (D + 1) * 8 + 64 * D
+    assert flops == 2 * (2 * sum(nnz) + 14 * D)
+    nbytes, flops = bench.algorithmic_per_iteration(c, "mfree", "CF4", (0, 0), fixed=False)
+    assert nbytes == 64 * D
+    assert flops == 2 * D * ((4 + (n - 1) + 2 * n + 2) + 10)
+
+
+def test_m4_applies_every_term_twice():
+    c = mi.workload2()
+    D, n = c.dim, c.nspins
+    nnz = (D + (n - 1) * D // 2, n * D)
+    b1, _ = bench.algorithmic_per_iteration(c, "csr", "CF4", nnz, fixed=False)
+    b4, _ = bench.algorithmic_per_iteration(c, "csr", "M4", nnz, fixed=False)
+    matrix = sum(nnz) * 12 + 2 * (D + 1) * 8
+    assert b4 - b1 == matrix + 2 * 32 * D  # the second pass over the matrix, u_k written and read back
+
+
+def test_reference_arm_json_line():
+    """`bench.py --impl reference` times the FP64 CPU oracle and prints the contract's line."""
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0"],
+                         cwd=bench.ROOT, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference"
+    assert line["unit"] == "steps/s" and line["value"] > 0 and line["steps"] == 1
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    assert np.isclose(line["e2e"]["value"], line["value"])
