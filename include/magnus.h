@@ -189,7 +189,7 @@ typedef struct {
   double kernel_ms;     /* device time of the persistent Leja kernel (CUDA events on the plan's stream) */
   int32_t grid;         /* CTAs of that launch                                */
   int32_t block;        /* threads per CTA                                    */
-  int32_t fixed_sums;   /* 1 if the pattern-term sums ran in fixed point (options.fixed_sums) */
+  int32_t fixed_sums;   /* 1 if the call's matvecs ran in fixed point (options.fixed_sums)      */
   int32_t _pad;
 } magnus_stats;
 
@@ -331,7 +331,7 @@ typedef struct {
   double graph_ms;              /* device time of the replayed graph (setup + persistent kernel)    */
   int32_t block;                /* CTA size the autotuner chose                                     */
   int32_t cluster;              /* CTAs per thread-block cluster (one problem per cluster)          */
-  int32_t fixed_sums;           /* 1 if the pattern-term sums ran in fixed point (options.fixed_sums) */
+  int32_t fixed_sums;           /* 1 if the matvecs ran in fixed point (options.fixed_sums)         */
   int32_t _pad;
 } magnus_batch_stats;
 
