@@ -23,7 +23,8 @@ struct Beta {
   double b[kMaxTerms];
 };
 
-// fixed-point rows: registers capped as in the persistent kernel's fixed-point instantiation
+// fixed-point rows: registers capped as in the persistent kernel's fixed-point instantiation (4
+// resident CTAs per SM for CSR, 3 for the matrix-free chain); 0 = no occupancy hint (FP64 rows)
 template <int FAM, bool ZF>
 constexpr int apply_min_blocks() {
   return ZF ? (FAM == FAM_CSR ? 4 : 3) : 0;
