@@ -310,7 +310,7 @@ def test_order_four_against_independent_integrator():
     f = oracle.Coeff(0, [1.0], [], [5.0])
     P = oracle.Problem([Hs, Hd], [oracle.Coeff.const(), f], tol=1e-14, tol_abs=1e-14)
     ref = _dop853_reference(Hs, Hd, f, c.psi0, 1.0)
-    for variant in ("M4", "CF4"):
+    for variant in ("M4", "CF4", "CF4_3"):
         errs = []
         for N in (8, 16, 32):
             out = P.propagate(c.psi0, 0.0, 1.0 / N, N, variant)
@@ -319,6 +319,22 @@ def test_order_four_against_independent_integrator():
         assert errs[-1] > 1e-10, errs  # still far above the reference's own error
         for r in ratios:
             assert 14.0 < r < 18.5, (variant, errs, ratios)
+
+
+def test_order_two_of_the_midpoint_method():
+    """Method M2 (one exponential of the generator at the midpoint of the step) converges with
+    order two: the error falls 4x per halving of h against an independent integrator."""
+    n = 6
+    c = mi.xxz_chain(16, n, 0.01, 1)
+    Hs = oracle.xxz_csr(n, c.J, c.hz, 0.5)
+    Hd = oracle.field_x_csr(n)
+    f = oracle.Coeff(0.2, [1.0], [0.4], [5.0])
+    P = oracle.Problem([Hs, Hd], [oracle.Coeff.const(), f], tol=1e-14, tol_abs=1e-14)
+    ref = _dop853_reference(Hs, Hd, f, c.psi0, 1.0)
+    errs = [np.linalg.norm(P.propagate(c.psi0, 0.0, 1.0 / N, N, "M2") - ref) for N in (16, 32, 64)]
+    ratios = [errs[i] / errs[i + 1] for i in range(len(errs) - 1)]
+    for r in ratios:
+        assert 3.6 < r < 4.4, (errs, ratios)
 
 
 def test_order_six_against_independent_integrator():
