@@ -289,7 +289,9 @@ def run_ours(args):
                  "algorithmic_bytes_per_iteration": bytes_it, "algorithmic_flops_per_iteration": flops_it,
                  "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 4),
                  "fp64_tflops": round(tflops, 4), "fp64_frac": round(tflops / FP64_PEAK_TFLOPS, 4),
-                 "peak_source": "hbm: MEASURED_PEAKS.json copy; fp64: 152 SMs x 2 FP64 instructions/clk x 2 flops x 2070 MHz (FMA-equivalent flops)"})
+                 "peak_source": ("hbm: MEASURED_PEAKS.json copy, of measured" if "hbm_gbs" in peaks else
+                                 f"hbm: {HBM_PEAK_FALLBACK:.0f} GB/s, of fallback (no MEASURED_PEAKS.json)")
+                                + "; fp64: 152 SMs x 2 FP64 instructions/clk x 2 flops x 2070 MHz (FMA-equivalent flops)"})
 
     # end-to-end through the public API with host buffers: every step copies its input state from
     # pinned host memory, runs one Magnus step (magnus_propagate, which returns when the step is
@@ -438,7 +440,8 @@ def run_dense13(args):
                 "frac": round(ts["bf16_tflops_issued"] / bf16_peak, 4),
                 "traffic": None if t12 is None or nv != 64 else int(t12 * (D / 4096) ** 2),
                 "traffic_unit": "DRAM bytes per Leja iteration (12-spin ncu capture scaled by (dim/4096)^2)",
-                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured",
+                "peak_source": ("MEASURED_PEAKS.json bf16_tflops (burst), of measured" if "bf16_tflops" in peaks
+                                else "1900 TFLOP/s bf16 burst, of fallback (no MEASURED_PEAKS.json)"),
                 "work": "10 bf16 digit-pair products x 2 flops x dim^2 x 128 columns per dense term per Leja iteration"}
     else:
         roof = {"bound": "alu", "kernel": "k_dense_persistent (FP64 path)",
