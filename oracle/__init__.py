@@ -52,40 +52,48 @@ class _Stats(C.Structure):
                 ("m_log", C.POINTER(C.c_int32)), ("m_log_cap", C.c_int64)]
 
 
+def _signatures():
+    P, D, I64, I32 = C.c_void_p, C.c_double, C.c_int64, C.c_int
+    return {
+        "orc_leja_points": (I32, [I32, P]),
+        "orc_divided_differences": (I32, [I32, P, D, P]),
+        "orc_xxz_nnz": (I64, [I32, P, D]),
+        "orc_build_xxz_csr": (I32, [I32, P, P, D, P, P, P]),
+        "orc_build_field_x_csr": (I32, [I32, P, P, P]),
+        "orc_build_longrange_dense": (I32, [I32, D, P, D, P]),
+        "orc_build_field_x_dense": (I32, [I32, P]),
+        "orc_problem_new": (P, [I64, I32]),
+        "orc_problem_free": (None, [P]),
+        "orc_set_csr": (I32, [P, I32, P, P, P]),
+        "orc_set_dense": (I32, [P, I32, P]),
+        "orc_set_coeff": (I32, [P, I32, D, I32, P, P, P]),
+        "orc_set_leja": (I32, [P, D, D, I32, D]),
+        "orc_term_interval": (I32, [P, I32, C.POINTER(D), C.POINTER(D)]),
+        "orc_set_interval_lanczos": (I32, [P, I32, I32]),
+        "orc_coeff_eval": (D, [P, I32, D]),
+        "orc_apply_term": (I32, [P, I32, P, P]),
+        "orc_expv": (I32, [P, P, P, C.POINTER(_Stats)]),
+        "orc_propagate": (I32, [P, P, D, D, I64, I32, C.POINTER(_Stats)]),
+        "orc_frechet_expv": (I32, [P, P, I32, P, P, P, C.POINTER(_Stats)]),
+        "orc_adjoint_grad": (I32, [P, P, P, D, D, I64, I32, I32, C.POINTER(D), P]),
+    }
+
+
+def load(path: str):
+    """Open a build of ``magnus_oracle.c`` at ``path`` and declare its entry points' signatures."""
+    L = C.CDLL(path)
+    for name, (res, args) in _signatures().items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = C.CDLL(build())
-            P, D, I64, I32 = C.c_void_p, C.c_double, C.c_int64, C.c_int
-            sig = {
-                "orc_leja_points": (I32, [I32, P]),
-                "orc_divided_differences": (I32, [I32, P, D, P]),
-                "orc_xxz_nnz": (I64, [I32, P, D]),
-                "orc_build_xxz_csr": (I32, [I32, P, P, D, P, P, P]),
-                "orc_build_field_x_csr": (I32, [I32, P, P, P]),
-                "orc_build_longrange_dense": (I32, [I32, D, P, D, P]),
-                "orc_build_field_x_dense": (I32, [I32, P]),
-                "orc_problem_new": (P, [I64, I32]),
-                "orc_problem_free": (None, [P]),
-                "orc_set_csr": (I32, [P, I32, P, P, P]),
-                "orc_set_dense": (I32, [P, I32, P]),
-                "orc_set_coeff": (I32, [P, I32, D, I32, P, P, P]),
-                "orc_set_leja": (I32, [P, D, D, I32, D]),
-                "orc_term_interval": (I32, [P, I32, C.POINTER(D), C.POINTER(D)]),
-                "orc_set_interval_lanczos": (I32, [P, I32, I32]),
-                "orc_coeff_eval": (D, [P, I32, D]),
-                "orc_apply_term": (I32, [P, I32, P, P]),
-                "orc_expv": (I32, [P, P, P, C.POINTER(_Stats)]),
-                "orc_propagate": (I32, [P, P, D, D, I64, I32, C.POINTER(_Stats)]),
-                "orc_frechet_expv": (I32, [P, P, I32, P, P, P, C.POINTER(_Stats)]),
-                "orc_adjoint_grad": (I32, [P, P, P, D, D, I64, I32, I32, C.POINTER(D), P]),
-            }
-            for name, (res, args) in sig.items():
-                f = getattr(L, name)
-                f.restype = res
-                f.argtypes = args
-            _lib = L
+            _lib = load(build())
     return _lib
 
 

@@ -171,6 +171,28 @@ def test_apply_term_and_gershgorin():
     assert abs(P.coeff(1, 0.3) - np.cos(1.5)) < 1e-16 and P.coeff(0, 0.3) == 1.0
 
 
+def test_apply_term_complex_hermitian_csr():
+    """A complex Hermitian CSR term with ragged rows: the product against numpy's dense product and
+    the Gershgorin enclosure against its definition (centre H_ii, radius sum_{j != i} |H_ij|)."""
+    D = 37
+    rng = np.random.default_rng(23)
+    H = np.zeros((D, D), dtype=complex)
+    for i in range(D):
+        for j in rng.choice(D, size=rng.integers(0, 6), replace=False):
+            H[i, j] = rng.standard_normal() + 1j * rng.standard_normal()
+    H = H + H.conj().T
+    H[np.arange(D), np.arange(D)] = rng.uniform(-2, 2, D)
+    rows, cols = np.nonzero(H)
+    rp = np.searchsorted(rows, np.arange(D + 1))
+    T = oracle.CSR(rp, cols, H[rows, cols])
+    P = oracle.Problem([T], [oracle.Coeff.const()])
+    x = mi.random_state(rng, D)
+    assert np.max(np.abs(P.apply_term(0, x) - H @ x)) < 1e-13
+    R = np.sum(np.abs(H), axis=1) - np.abs(np.diag(H))
+    a, b = P.interval(0)
+    assert abs(a - np.min(np.diag(H).real - R)) < 1e-13 and abs(b - np.max(np.diag(H).real + R)) < 1e-13
+
+
 # ---------------------------------------------------------------------------
 # Action of the exponential (Sec. 3) against eigendecomposition and scipy
 # ---------------------------------------------------------------------------
