@@ -42,6 +42,23 @@ def test_frechet_matches_daleckii_krein(beta):
     assert np.linalg.norm(b - P.expv(np.array(beta), c.psi0)) < 1e-12
 
 
+def test_frechet_of_a_scalar_generator():
+    """Omega = -i c I (a multiple of the identity): the block matrix [[Omega, E], [0, Omega]] has
+    exponential e^{-ic} [[I, E], [0, I]], so L(Omega, E) v = e^{-ic} E v and the second block is
+    e^{-ic} v (the Daleckii-Krein form with all eigenvalues equal).  Covers K = 0 and K = 0.7 I."""
+    n = 5
+    D = 1 << n
+    c = oracle.CSR(np.arange(D + 1), np.arange(D), np.ones(D))  # the identity
+    Hd = oracle.field_x_csr(n)
+    P = oracle.Problem([c, Hd], [oracle.Coeff.const(), oracle.Coeff.const()], tol=1e-13, tol_abs=1e-13)
+    v = mi.random_state(np.random.default_rng(35), D)
+    for shift in (0.0, 0.7):
+        a, b = P.frechet_expv(np.array([shift, 0.0]), 1, v)
+        ph = np.exp(-1j * shift)
+        assert np.max(np.abs(a - ph * (-1j) * (Hd.todense() @ v))) < 1e-14
+        assert np.max(np.abs(b - ph * v)) < 1e-15
+
+
 def test_frechet_matches_finite_difference():
     n = 6
     c, Hs, Hd, P = chain_problem(n, 32, oracle.Coeff.const())

@@ -23,6 +23,9 @@ MUTANTS = [
     # Leja points (Sec. 3)
     ("leja_second_point", "xi[1] = -2.0;", "xi[1] = 0.0;",
      [pins.test_leja_first_points_closed_form]),
+    ("leja_tie_to_smaller_x", "if (cl[g] >= best - 1e-10 && cx[g] > pick) pick = cx[g];",
+     "if (cl[g] >= best - 1e-10 && (pick == -INFINITY || cx[g] < pick)) pick = cx[g];",
+     [pins.test_leja_first_points_closed_form]),
     ("leja_bisection_direction", "if (slope > 0.0) lo = mid; else hi = mid;",
      "if (slope > 0.0) hi = mid; else lo = mid;",
      [pins.test_leja_first_points_closed_form]),
@@ -44,6 +47,8 @@ MUTANTS = [
      [lambda: pins.test_xxz_and_field_csr_match_kronecker(5)]),
     ("longrange_exponent", "1.0 / pow((double)(j - i), alpha);", "1.0 / pow((double)(j - i), 1.0);",
      [lambda: pins.test_longrange_dense_matches_kronecker(4)]),
+    ("longrange_pairs_twice", "for (int j = i + 1; j <= nspins; j++) {", "for (int j = 1; j <= nspins; j++) if (j != i) {",
+     [lambda: pins.test_longrange_dense_matches_kronecker(4)]),
     # term products, Gershgorin enclosure, drive coefficients
     ("csr_value_conjugated", "acc += t->val[e] * x[t->col[e]];", "acc += conj(t->val[e]) * x[t->col[e]];",
      [pins.test_apply_term_complex_hermitian_csr]),
@@ -54,6 +59,11 @@ MUTANTS = [
     ("drive_cos_sin_swapped", "f += c->ac[m] * cos(c->om[m] * t) + c->as[m] * sin(c->om[m] * t);",
      "f += c->ac[m] * sin(c->om[m] * t) + c->as[m] * cos(c->om[m] * t);",
      [pins.test_apply_term_and_gershgorin]),
+    ("gershgorin_dense_centre_modulus", "if (j == i) c += creal(t->val[i * D + j]);",
+     "if (j == i) c += cabs(t->val[i * D + j]);",
+     [pins.test_lanczos_interval_dense_complex_and_small_dim, pins.test_csr_and_dense_storage_agree]),
+    ("weyl_sum_ignores_sign", "lo += (x1 < x2) ? x1 : x2;", "lo += x1;",
+     [lambda: adj.test_adjoint_gradient_matches_central_differences("M2")]),  # the costate has beta < 0
     # Newton-form Leja recurrence (Sec. 3)
     ("newton_shift_sign", "w[i] = (Kw[i] - c * w[i]) / gamma", "w[i] = (Kw[i] + c * w[i]) / gamma",
      [pins.test_expv_matches_scipy_expm_multiply]),
@@ -63,6 +73,8 @@ MUTANTS = [
      [pins.test_expv_matches_scipy_expm_multiply]),
     ("newton_no_substeps", "int s = (int)ceil(gamma / p->rho_max);\n  if (s < 1) s = 1;\n  const double rho",
      "int s = 1;\n  const double rho", [lambda: pins.test_expv_matches_eigh_dim1024((3.0, -1.5))]),
+    ("substep_phase_not_split", "cexp(-I * c / s);\n  int rc = ORC_OK;", "cexp(-I * c);\n  int rc = ORC_OK;",
+     [lambda: pins.test_expv_matches_eigh_dim1024((3.0, -1.5))]),
     # Magnus integrators (Sec. 2)
     ("m4_commutator_sign", "- I * kappa * (y[i] - g->t2[i]);", "+ I * kappa * (y[i] - g->t2[i]);",
      [pins.test_order_four_against_independent_integrator]),
@@ -83,6 +95,16 @@ MUTANTS = [
      [lambda: pins.test_commuting_terms_give_gauss_quadrature("M6")]),
     ("m6_commutator_sign", "(uvx[i] - vux[i]) / 240.0", "(vux[i] - uvx[i]) / 240.0",
      [pins.test_order_six_against_independent_integrator]),
+    ("exponent_without_step", "g->beta[k] = h * s;", "g->beta[k] = s;",
+     [lambda: pins.test_time_independent_is_exact("CF4")]),
+    ("m6_b2_weight", "else if (j == 2) coef[k] = r15 / 3.0 * g->h", "else if (j == 2) coef[k] = r15 / 2.0 * g->h",
+     [pins.test_order_six_against_independent_integrator]),
+    ("m6_v_weight", "y[i] -= (b1wx[i] - wb1x[i]) / 60.0;", "y[i] -= (b1wx[i] - wb1x[i]) / 30.0;",
+     [pins.test_order_six_against_independent_integrator]),
+    ("m6_w_weight", "y[i] += 2.0 * b3[i];", "y[i] += b3[i];",
+     [pins.test_order_six_against_independent_integrator]),
+    ("m6_u_b3_sign", "y[i] += -20.0 * b1[i] - b3[i];", "y[i] += -20.0 * b1[i] + b3[i];",
+     [pins.test_order_six_with_two_driven_terms]),
     # augmented block matrix and adjoint gradient
     ("frechet_block_sign", "(ka[i] + g.u1[i] - c * wa[i])", "(ka[i] - g.u1[i] - c * wa[i])",
      [lambda: adj.test_frechet_matches_daleckii_krein((0.03, 0.02))]),
@@ -90,6 +112,16 @@ MUTANTS = [
      [lambda: adj.test_adjoint_gradient_matches_central_differences("M2")]),
     ("adjoint_weight_derivative", "dbeta[e * ng + 1 + m] = h * sc;", "dbeta[e * ng + 1 + m] = sc;",
      [lambda: adj.test_adjoint_gradient_matches_central_differences("M2")]),
+    ("adjoint_constant_derivative", "dbeta[e * ng] = h * s0;", "dbeta[e * ng] = s0;",
+     [lambda: adj.test_adjoint_gradient_matches_central_differences("M2")]),
+    ("fidelity_gradient_unconjugated", "grad[q] = 2.0 * creal(conj(z) * dz[q]);", "grad[q] = 2.0 * creal(z * dz[q]);",
+     [lambda: adj.test_adjoint_gradient_matches_central_differences("M2")]),
+    ("frechet_node_index", "- p->xi[j - 1] * wb[i];", "- p->xi[j] * wb[i];",
+     [lambda: adj.test_frechet_matches_daleckii_krein((0.03, 0.02))]),
+    ("frechet_scalar_block_sign", "a[i] = ph * (a[i] - I * g.u1[i]);", "a[i] = ph * (a[i] + I * g.u1[i]);",
+     [adj.test_frechet_of_a_scalar_generator]),
+    ("adjoint_cf43_stage_order", "w[q][j] = al[2 - q][j];", "w[q][j] = al[q][j];",
+     [lambda: adj.test_adjoint_gradient_matches_central_differences("CF4_3")]),
 ]
 
 

@@ -380,6 +380,29 @@ def test_order_six_against_independent_integrator():
         assert 48.0 < r < 80.0, (errs, ratios)
 
 
+def test_order_six_with_two_driven_terms():
+    """Order six when both terms carry their own drive.  With a single driven term every commutator
+    of B_2 and B_3 vanishes (both are multiples of the driven H_k), so only a problem whose terms are
+    driven independently fixes the terms of Method M6 that contain B_3 inside the bracket."""
+    n = 5
+    c = mi.xxz_chain(17, n, 0.01, 1)
+    Hs = oracle.xxz_csr(n, c.J, c.hz, 0.5)
+    Hd = oracle.field_x_csr(n)
+    fs = oracle.Coeff(1.0, [0.0], [0.6], [3.0])
+    fd = oracle.Coeff(0.3, [1.0], [0.5], [5.0])
+    P = oracle.Problem([Hs, Hd], [fs, fd], tol=1e-15, tol_abs=1e-15)
+    integ = pytest.importorskip("scipy.integrate")
+    A, B = Hs.todense(), Hd.todense()
+    sol = integ.solve_ivp(lambda t, y: -1j * (fs(t) * (A @ y) + fd(t) * (B @ y)), (0.0, 1.0), c.psi0,
+                          method="DOP853", rtol=1e-13, atol=1e-15)
+    ref = sol.y[:, -1]
+    errs = [np.linalg.norm(P.propagate(c.psi0, 0.0, 1.0 / N, N, "M6") - ref) for N in (6, 12, 24)]
+    ratios = [errs[i] / errs[i + 1] for i in range(len(errs) - 1)]
+    assert errs[-1] > 1e-10, errs
+    for r in ratios:
+        assert 48.0 < r < 80.0, (errs, ratios)
+
+
 def test_m6_generator_is_hermitian():
     """K = i Omega of Method M6 is Hermitian: the exponential conserves the norm only then.  Checked
     on random vectors through one exponential's action, <x, exp(-iK) y> = <exp(iK) x, y>, via the
