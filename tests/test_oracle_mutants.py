@@ -64,6 +64,24 @@ MUTANTS = [
      [pins.test_lanczos_interval_dense_complex_and_small_dim, pins.test_csr_and_dense_storage_agree]),
     ("weyl_sum_ignores_sign", "lo += (x1 < x2) ? x1 : x2;", "lo += x1;",
      [lambda: adj.test_adjoint_gradient_matches_central_differences("M2")]),  # the costate has beta < 0
+    # Lanczos enclosure (the tighter spectral estimate)
+    ("lanczos_three_term_dropped", "w[i] -= a * v1[i] + be[j] * v0[i];", "w[i] -= a * v1[i];",
+     [lambda: pins.test_lanczos_interval_encloses_spectrum_and_is_tighter(6)]),
+    ("lanczos_alpha_imaginary_part", "a += creal(conj(v1[i]) * w[i]);", "a += cimag(conj(v1[i]) * w[i]);",
+     [lambda: pins.test_lanczos_interval_encloses_spectrum_and_is_tighter(6)]),
+    ("sturm_count_sign", "if (q < 0.0) cnt++;", "if (q > 0.0) cnt++;",
+     [lambda: pins.test_lanczos_interval_encloses_spectrum_and_is_tighter(6)]),
+    ("ritz_second_largest", "tmax = tridiag_eig(al, be, mj, mj - 1);", "tmax = tridiag_eig(al, be, mj, mj > 1 ? mj - 2 : 0);",
+     [lambda: pins.test_lanczos_interval_encloses_spectrum_and_is_tighter(6)]),
+    ("lanczos_not_intersected", "if (a < t->a) a = t->a;\n  if (b > t->b) b = t->b;",
+     "if (a > t->a) a = t->a;\n  if (b < t->b) b = t->b;",
+     [lambda: pins.test_lanczos_interval_encloses_spectrum_and_is_tighter(6)]),
+    ("ritz_residual_dropped", "double a = tmin - rmin - 0.01 * W, b = tmax + rmax + 0.01 * W;",
+     "double a = tmin - 0.01 * W, b = tmax + 0.01 * W;", [pins.test_lanczos_residuals_on_three_eigenvalues]),
+    ("ritz_margin_dropped", "double a = tmin - rmin - 0.01 * W, b = tmax + rmax + 0.01 * W;",
+     "double a = tmin - rmin, b = tmax + rmax;", [pins.test_lanczos_residuals_on_three_eigenvalues]),
+    ("inverse_iteration_sign", "d[i] = (x[i] - be[i] * d[i - 1]) / piv;", "d[i] = (x[i] + be[i] * d[i - 1]) / piv;",
+     [pins.test_lanczos_residuals_on_three_eigenvalues]),
     # Newton-form Leja recurrence (Sec. 3)
     ("newton_shift_sign", "w[i] = (Kw[i] - c * w[i]) / gamma", "w[i] = (Kw[i] + c * w[i]) / gamma",
      [pins.test_expv_matches_scipy_expm_multiply]),

@@ -497,6 +497,47 @@ def test_lanczos_interval_dense_complex_and_small_dim():
     assert abs(a - (ev[0] - 0.01 * W)) < 1e-9 * W and abs(b - (ev[-1] + 0.01 * W)) < 1e-9 * W
 
 
+def test_lanczos_residuals_on_three_eigenvalues():
+    """Unconverged Ritz values, where the residual term of the enclosure matters.  H has the
+    eigenvalues -1, 0, 1 (16 copies each, rotated so that Gershgorin is much wider).  Lanczos on H
+    only sees the start vector's weights p_-1, p_0, p_1 in the three eigenspaces, so it runs exactly
+    like Lanczos on diag(-1, 0, 1) with the start vector (sqrt p_-1, sqrt p_0, sqrt p_1):
+    * 1 step: the interval is alpha -+ beta_1 with alpha = p_1 - p_-1 and
+      beta_1^2 = p_1 + p_-1 - alpha^2, which gives the weights;
+    * 2 steps: Ritz values of the 2-dim Krylov space and their residual norms |H y - theta y|,
+      computed directly in the 3-dim space (not from beta_2 |s_2|), give the interval
+      [theta_1 - r_1 - 0.01 W, theta_2 + r_2 + 0.01 W];
+    * 3 steps: the Krylov space is invariant, the residuals vanish: [-1.02, 1.02]."""
+    rng = np.random.default_rng(43)
+    Q, _ = np.linalg.qr(rng.standard_normal((48, 48)))
+    H = (Q * np.repeat([-1.0, 0.0, 1.0], 16)) @ Q.T
+    R = np.sum(np.abs(H), axis=1) - np.abs(np.diag(H))
+    ga, gb = np.min(np.diag(H) - R), np.max(np.diag(H) + R)
+    assert ga < -1.5 and gb > 1.5  # Gershgorin clips none of the intervals below
+
+    def interval(steps):
+        return oracle.Problem([H.astype(complex)], [oracle.Coeff.const()], interval="lanczos",
+                              lanczos_steps=steps).interval(0)
+
+    a1, b1 = interval(1)
+    alpha, beta1 = 0.5 * (a1 + b1), 0.5 * (b1 - a1)
+    assert beta1 > 0.1
+    p_hi = 0.5 * (alpha ** 2 + beta1 ** 2 + alpha)
+    p_lo = 0.5 * (alpha ** 2 + beta1 ** 2 - alpha)
+    u = np.sqrt([p_lo, 1.0 - p_lo - p_hi, p_hi])
+    L = np.diag([-1.0, 0.0, 1.0])
+    V, _ = np.linalg.qr(np.column_stack([u, L @ u]))
+    theta, S = np.linalg.eigh(V.T @ L @ V)
+    Y = V @ S
+    r = np.linalg.norm(L @ Y - Y * theta, axis=0)
+    W = theta[1] - theta[0]
+    a2, b2 = interval(2)
+    assert abs(a2 - (theta[0] - r[0] - 0.01 * W)) < 1e-10 and abs(b2 - (theta[1] + r[1] + 0.01 * W)) < 1e-10
+    assert min(r) > 1e-3  # the residuals are part of what was checked
+    a3, b3 = interval(3)
+    assert abs(a3 + 1.02) < 1e-10 and abs(b3 - 1.02) < 1e-10
+
+
 def test_lanczos_interval_propagation_agrees_and_needs_fewer_matvecs():
     c = mi.workload1()
     Hs = oracle.xxz_csr(c.nspins, c.J, c.hz, 0.5)
