@@ -74,6 +74,7 @@ def _signatures():
         "orc_apply_term": (I32, [P, I32, P, P]),
         "orc_expv": (I32, [P, P, P, C.POINTER(_Stats)]),
         "orc_propagate": (I32, [P, P, D, D, I64, I32, C.POINTER(_Stats)]),
+        "orc_generator_interval": (I32, [P, I32, D, D, C.POINTER(D), C.POINTER(D)]),
         "orc_frechet_expv": (I32, [P, P, I32, P, P, P, C.POINTER(_Stats)]),
         "orc_adjoint_grad": (I32, [P, P, P, D, D, I64, I32, I32, C.POINTER(D), P]),
     }
@@ -281,6 +282,13 @@ class Problem:
         _check(lib().orc_propagate(self._h, _ptr(out), float(t0), float(h), int(nsteps), code,
                                    C.byref(st) if st else None), "propagate")
         return out
+
+    def generator_interval(self, variant, tn, h):
+        """Spectral enclosure of the generator K of one M4 or M6 step of size h from tn."""
+        a, b = C.c_double(), C.c_double()
+        _check(lib().orc_generator_interval(self._h, VARIANTS[variant], float(tn), float(h), C.byref(a), C.byref(b)),
+               "generator_interval")
+        return a.value, b.value
 
     def frechet_expv(self, beta, kd, v):
         """(L(Omega, -i H_kd) v, exp(Omega) v) for Omega = -i sum_k beta_k H_k (augmented block matrix)."""

@@ -966,6 +966,32 @@ int orc_propagate(const orc_problem *p, double complex *psi, double t0, double h
   return rc;
 }
 
+/* The enclosure gen_interval gives the generator of one M4 or M6 step (the nodes of orc_propagate). */
+int orc_generator_interval(const orc_problem *p, int variant, double tn, double h, double *a, double *b) {
+  int rc = check_problem(p);
+  if (rc) return rc;
+  if (!a || !b || (variant != ORC_M4 && variant != ORC_M6)) return ORC_EINVAL;
+  orc_gen g;
+  memset(&g, 0, sizeof(g));
+  g.p = p;
+  g.h = h;
+  const double r3 = sqrt(3.0), r15 = sqrt(15.0);
+  for (int k = 0; k < p->nterms; k++) {
+    if (variant == ORC_M4) {
+      g.mode = GEN_M4;
+      g.f1[k] = orc_coeff_eval(p, k, tn + (0.5 - r3 / 6.0) * h);
+      g.f2[k] = orc_coeff_eval(p, k, tn + (0.5 + r3 / 6.0) * h);
+    } else {
+      g.mode = GEN_M6;
+      g.f1[k] = orc_coeff_eval(p, k, tn + (0.5 - r15 / 10.0) * h);
+      g.f2[k] = orc_coeff_eval(p, k, tn + 0.5 * h);
+      g.f3[k] = orc_coeff_eval(p, k, tn + (0.5 + r15 / 10.0) * h);
+    }
+  }
+  gen_interval(&g, a, b);
+  return ORC_OK;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Adjoint: gradient of a state-transfer fidelity with respect to the drive.  */
 /* ------------------------------------------------------------------------- */

@@ -77,6 +77,10 @@ int orc_expv(const orc_problem *p, const double *beta, double complex *v, orc_st
 int orc_propagate(const orc_problem *p, double complex *psi, double t0, double h, int64_t nsteps,
                   int variant, orc_stats *st);
 
+/* [*a, *b]: the spectral enclosure of the generator K of one step of size h from tn of Method M4
+ * or M6 (variant ORC_M4 / ORC_M6), the interval whose shift and scale that step's exponential uses. */
+int orc_generator_interval(const orc_problem *p, int variant, double tn, double h, double *a, double *b);
+
 /*
  * Frechet derivative of the exponential by the augmented block matrix:
  * [a; b] = exp(Omega_aug) [0; v] with Omega_aug = [[Omega, E], [0, Omega]], Omega = -i sum_k beta_k H_k,

@@ -64,6 +64,10 @@ MUTANTS = [
      [pins.test_lanczos_interval_dense_complex_and_small_dim, pins.test_csr_and_dense_storage_agree]),
     ("weyl_sum_ignores_sign", "lo += (x1 < x2) ? x1 : x2;", "lo += x1;",
      [lambda: adj.test_adjoint_gradient_matches_central_differences("M2")]),  # the costate has beta < 0
+    ("m4_enclosure_radius_dropped", "lo -= kappa * r;\n    hi += kappa * r;", "lo -= 0.0 * r;\n    hi += 0.0 * r;",
+     [lambda: pins.test_commutator_enclosure_contains_the_generator_spectrum("M4")]),
+    ("m6_enclosure_radius_dropped", "    lo -= r;\n    hi += r;\n  }\n  *a = lo;", "  }\n  *a = lo;",
+     [lambda: pins.test_commutator_enclosure_contains_the_generator_spectrum("M6")]),
     # Lanczos enclosure (the tighter spectral estimate)
     ("lanczos_three_term_dropped", "w[i] -= a * v1[i] + be[j] * v0[i];", "w[i] -= a * v1[i];",
      [lambda: pins.test_lanczos_interval_encloses_spectrum_and_is_tighter(6)]),

@@ -403,6 +403,25 @@ def test_order_six_with_two_driven_terms():
         assert 48.0 < r < 80.0, (errs, ratios)
 
 
+@pytest.mark.parametrize("variant", ["M4", "M6"])
+def test_commutator_enclosure_contains_the_generator_spectrum(variant):
+    """The enclosure of an M4 / M6 generator holds its spectrum where only the commutator part
+    reaches beyond the linear part.  One spin, H_s = sz, drive f sx with f odd about the step's
+    midpoint: the linear part of the generator is h sz (spectrum +-h, Gershgorin exact), and the
+    commutators add a sy component, so the spectrum +-sqrt(h^2 + c^2) lies outside +-h.  The
+    spectrum is read from the oracle's own one-step propagator exp(-iK) (eigenvalues e^{-i lambda})."""
+    h, tmid = 0.5, 0.25
+    sz = np.diag([1.0, -1.0]).astype(complex)
+    sx = np.array([[0, 1], [1, 0]], dtype=complex)
+    f = oracle.Coeff(0.0, [-8.0 * np.sin(4 * tmid)], [8.0 * np.cos(4 * tmid)], [4.0])  # 8 sin(4 (t - tmid))
+    P = oracle.Problem([sz, sx], [oracle.Coeff.const(), f], tol=1e-15, tol_abs=1e-15)
+    U = np.column_stack([P.propagate(e, 0.0, h, 1, variant) for e in np.eye(2, dtype=complex)])
+    lam = -np.angle(np.linalg.eigvals(U))
+    a, b = P.generator_interval(variant, 0.0, h)
+    assert np.max(np.abs(lam)) > h + 1e-3  # the commutator part is what reaches past +-h
+    assert a <= lam.min() + 1e-12 and lam.max() <= b + 1e-12, (lam, a, b)
+
+
 def test_m6_generator_is_hermitian():
     """K = i Omega of Method M6 is Hermitian: the exponential conserves the norm only then.  Checked
     on random vectors through one exponential's action, <x, exp(-iK) y> = <exp(iK) x, y>, via the
