@@ -87,3 +87,20 @@ def test_reference_arm_json_line():
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
     assert np.isclose(line["e2e"]["value"], line["value"])
+
+
+def test_clock_summary_of_sampled_records():
+    """The clocks record of the bench line: median SM clock under load, the maximum, and every
+    throttle reason seen Active in any sample (nvidia-smi csv,noheader,nounits rows)."""
+    s = bench.ClockSampler(0)
+    s.out = "\n".join([
+        "0, 1965, 2070, 812.4, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 2070, 2070, 990.1, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 1800, 2070, 1201.0, 0x0000000000000008, Active, Not Active, Not Active, Not Active",
+        "garbage line",
+    ])
+    got = s.summary()
+    assert got["sm_mhz"] == 1965.0 and got["sm_max_mhz"] == 2070.0 and got["samples"] == 3
+    assert got["reasons"] == ["hw_slowdown", "sw_power_cap"]
+    s.out = ""
+    assert s.summary()["reasons"] == ["unavailable"]
