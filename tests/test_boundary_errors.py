@@ -232,3 +232,22 @@ def test_batch_create_rejects(L, case, expect):
     rc = L.magnus_batch_create(outp, count, items, C.byref(opt) if opt is not None else None, None)
     assert rc == mg.EINVAL
     assert expect in L.magnus_batch_last_error(None).decode(), L.magnus_batch_last_error(None)
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    """No CPU fallback: without the compiled library the binding raises instead of computing."""
+    monkeypatch.setattr(mg, "_lib", None)
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        mg.load(str(tmp_path / "libmissing.so"))
+
+
+def test_binding_refuses_host_tensors(L):
+    """Host (CPU) or strided tensors never reach the C ABI: the binding raises before the call."""
+    torch = pytest.importorskip("torch")
+    v = torch.zeros(16, dtype=torch.complex128)
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        mg.expv_xxz_static(4, J, HZ, 0.5, np.array([0.1, 0.05]), v)
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        mg._dptr(v)
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        mg._dptr(np.zeros(4))
