@@ -793,7 +793,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--fixed-sums", type=int, choices=[0, 1], default=1,
                     help="xxz20: pattern-term sums in fixed point (1) or FP64 (0)")
-    ap.add_argument("--cpu-steps", type=int, default=4)
+    ap.add_argument("--cpu-steps", type=int, default=16,
+                    help="steps of the CPU oracle sample (about 12 s on one Grace core)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--spins", type=int, default=13, help="dense13 only: chain length (profiling smaller cases)")
     ap.add_argument("--states", type=int, default=64, help="dense13 only: states sharing H")
