@@ -273,7 +273,8 @@ class Plan:
                  fixed_sums=True):
         import torch
         L = load()
-        assert len(terms) == len(drives)
+        if len(terms) != len(drives):
+            raise ValueError(f"{len(terms)} terms but {len(drives)} drives")
         self.dim, self.nvec, self.nterms = int(dim), int(nvec), len(terms)
         self._terms, self._drives = list(terms), list(drives)  # keep borrowed buffers alive
         self.stream = stream if stream is not None else torch.cuda.current_stream()
@@ -328,7 +329,8 @@ class Plan:
         if out is None:
             out = torch.empty_like(v)
         b = _f64(beta)
-        assert b.size == self.nterms
+        if b.size != self.nterms:
+            raise ValueError(f"beta needs {self.nterms} values, got {b.size}")
         st, log = self._stats(log_cap)
         _check(load().leja_expv(self._h, b.ctypes.data_as(C.POINTER(C.c_double)), C.c_void_p(_dptr(v)),
                                 C.c_void_p(_dptr(out)), C.byref(st)), self._h)
@@ -347,7 +349,8 @@ class Plan:
         if y is None:
             y = torch.empty_like(x)
         b = _f64(beta)
-        assert b.size == self.nterms
+        if b.size != self.nterms:
+            raise ValueError(f"beta needs {self.nterms} values, got {b.size}")
         _check(load().magnus_apply(self._h, b.ctypes.data_as(C.POINTER(C.c_double)), C.c_void_p(_dptr(x)),
                                    C.c_void_p(_dptr(y))), self._h)
         return y
@@ -428,7 +431,8 @@ class Batch:
 
     def propagate(self, psis, t0, h, nsteps, variant="CF4", log_cap=0):
         """psis: list of CUDA complex128 tensors (in place)."""
-        assert len(psis) == self.count
+        if len(psis) != self.count:
+            raise ValueError(f"expected {self.count} states, got {len(psis)}")
         ptrs = (C.c_void_p * self.count)(*[_dptr(p) for p in psis])
         st = BatchStats()
         log = None
@@ -501,12 +505,15 @@ def build_field_x_dense(nspins, device="cuda", stream=None):
 def expv_xxz_static(nspins, J, hz, delta, beta, v, out=None, tol=1e-10, stream=None):
     """out = exp(-i (beta_0 H_xxz + beta_1 sum_i sx_i)) v without a plan and without any device allocation
     inside the library (fixed ~3.2 MB scratch, nspins <= 16).  For callers that cannot call cudaMalloc.
-    The first call on a device does a one-time set-up; calls that overlap on the GPU race."""
+    The first call on a device does a one-time set-up; calls that overlap on the GPU race.  With
+    out=None this wrapper allocates the result tensor; pass out (it may be v itself) to allocate
+    nothing at all."""
     import torch
     if out is None:
         out = torch.empty_like(v)
     J, hz, b = _f64(J), _f64(hz), _f64(beta)
-    assert b.size == 2
+    if b.size != 2:
+        raise ValueError("beta holds the weights of the XXZ term and the field: 2 values")
     P = C.POINTER(C.c_double)
     _check(load().magnus_expv_xxz_static(int(nspins), J.ctypes.data_as(P), hz.ctypes.data_as(P), float(delta),
                                          b.ctypes.data_as(P), C.c_void_p(_dptr(v)), C.c_void_p(_dptr(out)),
