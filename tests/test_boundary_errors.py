@@ -251,3 +251,12 @@ def test_binding_refuses_host_tensors(L):
         mg._dptr(v)
     with pytest.raises(TypeError, match="CUDA tensor"):
         mg._dptr(np.zeros(4))
+
+
+def test_binding_argument_checks(L):
+    """Mismatched argument counts are refused by the binding before any CUDA call."""
+    torch = pytest.importorskip("torch")
+    with pytest.raises(ValueError, match="2 terms but 1 drives"):
+        mg.Plan(16, [mg.XXZTerm(4, J, HZ), mg.FieldXTerm(4)], [mg.Drive.const()])
+    with pytest.raises(ValueError, match="2 values"):
+        mg.expv_xxz_static(4, J, HZ, 0.5, np.array([0.1, 0.2, 0.3]), torch.zeros(16, dtype=torch.complex128))
