@@ -104,7 +104,8 @@ typedef struct {
 /*
  * out[e] = Re z[e] for e < n (z: device complex128, out: device float64, both caller-owned), on
  * `stream`; synchronises the stream.  Returns MAGNUS_EINVAL (out still written) if some Im z[e] != 0,
- * so a complex-stored real matrix converts to MAGNUS_TERM_CSR_REAL / DENSE_REAL storage exactly.
+ * so a complex-stored real matrix converts to MAGNUS_TERM_CSR_REAL / DENSE_REAL storage exactly
+ * (every Hamiltonian of Sec. 4 is real).  Also EINVAL for n < 0 or a null pointer; ENOMEM, ECUDA.
  */
 MAGNUS_API magnus_status magnus_real_parts(const void *z, int64_t n, double *out, void *stream);
 
@@ -252,7 +253,8 @@ MAGNUS_API magnus_status magnus_adjoint_grad(magnus_plan_t plan, const void *psi
                                              double *grad, magnus_stats *stats);
 
 /*
- * Replace the drive coefficient f_k of term k (host struct, copied): the next calls on the plan use
+ * Replace the drive coefficient f_k of term k (the time dependence h(t) of the split
+ * H = H_1 + h(t) H_2 of Sec. 4; host struct, copied): the next calls on the plan use
  * it (stream-ordered).  The spectral enclosures are those of the terms and do not change.
  * Errors: EINVAL, ECUDA.
  */
@@ -272,21 +274,30 @@ MAGNUS_API magnus_status magnus_set_coeff(magnus_plan_t plan, int32_t k, const m
 MAGNUS_API magnus_status magnus_apply(magnus_plan_t plan, const double *beta, const void *x, void *y);
 
 /* Spectral enclosure [*a, *b] of term k (computed at plan creation: Gershgorin, or its
- * intersection with the Lanczos enclosure). */
+ * intersection with the Lanczos enclosure), the estimate the Leja parameters of Sec. 3 are built
+ * on.  a, b: host.  Errors: EINVAL (null plan or pointer, k out of range). */
 MAGNUS_API magnus_status magnus_term_interval(magnus_plan_t plan, int32_t k, double *a, double *b);
 
-/* Copy the plan's m_max+1 Leja points (device-computed) to host xi[]. */
+/* Copy the first count (<= m_max+1) of the plan's Leja points on [-2,2] (Sec. 3, the
+ * interpolation nodes; device-computed) to host xi[].  Synchronises the plan's stream.
+ * Errors: EINVAL (null plan or pointer, count out of range), ECUDA. */
 MAGNUS_API magnus_status magnus_leja_points(magnus_plan_t plan, double *xi, int32_t count);
 
 /*
  * Divided differences d_j = g[xi_0..xi_j], j = 0..count-1, of g(x) = exp(-i rho x)
  * at the plan's Leja points (Sec. 3), computed on the device; d: host complex128[count].
+ * Synchronises the plan's stream.  Errors: EINVAL (count out of range, rho < 0 or NaN), ENOMEM, ECUDA.
  */
 MAGNUS_API magnus_status magnus_divided_differences(magnus_plan_t plan, double rho, void *d, int32_t count);
 
-/* ---- Hamiltonian builders (device kernels; all pointers device unless noted) ---- */
+/* ---- Hamiltonian builders (device kernels; all pointers device unless noted) ----
+ * The spin chains of Sec. 4 from the Pauli matrices in the Kronecker embedding (spin 1 leftmost).
+ * Each builder enqueues its kernel on `stream` and returns without synchronising.
+ * Errors: EINVAL (nspins out of range, null pointer), ECUDA (launch failure); the text is in
+ * magnus_last_error(NULL). */
 
-/* Number of stored entries of the XXZ CSR built below: 2^n + (n-1) 2^(n-1). */
+/* Number of stored entries of the XXZ CSR built below: 2^n + (n-1) 2^(n-1); -1 for nspins outside
+ * 2..30. */
 MAGNUS_API int64_t magnus_xxz_nnz(int32_t nspins);
 
 /*
@@ -353,7 +364,8 @@ MAGNUS_API magnus_status magnus_batch_create(magnus_batch_t *batch, int32_t coun
 
 /*
  * psi[i] (device complex128 [dim_i], in/out; psi is a HOST array of count device pointers) <- nsteps
- * Magnus steps of size h from t0 for every problem.  The first call times the candidate CTA sizes
+ * Magnus steps of size h from t0 for every problem (Sec. 2, Eq. (9), each exponential by the
+ * Leja interpolation of Sec. 3).  The first call times the candidate CTA sizes
  * x cluster sizes on copies of the states (2 steps each) and keeps the fastest; the setup launches and the persistent
  * kernel are captured into a CUDA graph once per (t0, h, nsteps, variant) and replayed.  Synchronous.
  * Errors: EINVAL, ENOCONV, ENONFINITE, ECUDA (the first error of any problem).
@@ -361,6 +373,7 @@ MAGNUS_API magnus_status magnus_batch_create(magnus_batch_t *batch, int32_t coun
 MAGNUS_API magnus_status magnus_batch_propagate(magnus_batch_t batch, void *const *psi, double t0, double h,
                                                 int64_t nsteps, int32_t variant, magnus_batch_stats *stats);
 
+/* Release the batch, its graph and its scratch.  NULL is accepted.  Returns MAGNUS_OK. */
 MAGNUS_API magnus_status magnus_batch_destroy(magnus_batch_t batch);
 
 /* Last error of this batch ("" if none); NULL gives the last error of magnus_batch_create. */

@@ -260,3 +260,16 @@ def test_binding_argument_checks(L):
         mg.Plan(16, [mg.XXZTerm(4, J, HZ), mg.FieldXTerm(4)], [mg.Drive.const()])
     with pytest.raises(ValueError, match="2 values"):
         mg.expv_xxz_static(4, J, HZ, 0.5, np.array([0.1, 0.2, 0.3]), torch.zeros(16, dtype=torch.complex128))
+
+
+def test_builders_reject_bad_sizes(L):
+    """The spin-chain builders refuse out-of-range chains and null buffers before any launch."""
+    assert L.magnus_xxz_nnz(1) == -1 and L.magnus_xxz_nnz(31) == -1 and L.magnus_xxz_nnz(2) == 4 + 2
+    assert L.magnus_build_xxz_csr(31, _dp(J), _dp(HZ), 0.5, FAKE, FAKE, FAKE, None) == mg.EINVAL
+    assert L.magnus_build_xxz_csr(4, _dp(J), _dp(HZ), 0.5, FAKE, None, FAKE, None) == mg.EINVAL
+    assert "build_xxz_csr: bad argument" in _last(L)
+    assert L.magnus_build_field_x_csr(0, FAKE, FAKE, FAKE, None) == mg.EINVAL
+    assert L.magnus_build_longrange_dense(16, 1.5, _dp(HZ), 0.5, FAKE, None) == mg.EINVAL  # dense: <= 15 spins
+    assert L.magnus_build_field_x_dense(4, None, None) == mg.EINVAL
+    assert "build_field_x_dense: bad argument" in _last(L)
+    assert L.magnus_batch_destroy(None) == mg.OK
