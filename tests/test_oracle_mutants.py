@@ -47,6 +47,8 @@ MUTANTS = [
      [lambda: pins.test_xxz_and_field_csr_match_kronecker(5)]),
     ("longrange_exponent", "1.0 / pow((double)(j - i), alpha);", "1.0 / pow((double)(j - i), 1.0);",
      [lambda: pins.test_longrange_dense_matches_kronecker(4)]),
+    ("field_dense_value", "H[x * D + (x ^ spin_bit(nspins, i))] = 1.0;", "H[x * D + (x ^ spin_bit(nspins, i))] = 2.0;",
+     [lambda: pins.test_longrange_dense_matches_kronecker(4)]),
     ("longrange_pairs_twice", "for (int j = i + 1; j <= nspins; j++) {", "for (int j = 1; j <= nspins; j++) if (j != i) {",
      [lambda: pins.test_longrange_dense_matches_kronecker(4)]),
     # term products, Gershgorin enclosure, drive coefficients
@@ -144,6 +146,11 @@ MUTANTS = [
      [adj.test_frechet_of_a_scalar_generator]),
     ("adjoint_cf43_stage_order", "w[q][j] = al[2 - q][j];", "w[q][j] = al[q][j];",
      [lambda: adj.test_adjoint_gradient_matches_central_differences("CF4_3")]),
+    ("adjoint_cf4_stage_order", "w[0][0] = a2; w[0][1] = a1;   /* right factor, applied first */\n    w[1][0] = a1; w[1][1] = a2;",
+     "w[0][0] = a1; w[0][1] = a2;   /* right factor, applied first */\n    w[1][0] = a2; w[1][1] = a1;",
+     [lambda: adj.test_adjoint_gradient_matches_central_differences("CF4")]),
+    ("overlap_unconjugated", "z += conj(phi[i]) * states[nexp * D + i];", "z += phi[i] * states[nexp * D + i];",
+     [lambda: adj.test_adjoint_gradient_matches_central_differences("M2")]),
 ]
 
 
