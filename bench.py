@@ -1,18 +1,24 @@
-"""Benchmark: Magnus steps/s and Leja matvec GB/s of the plain FP64 GPU path.
+"""Benchmark: Magnus steps/s and Leja matvec GB/s, against the plain FP64 GPU path.
 
-Workload (one Magnus step = one bench step): the open XXZ chain with 20 spins
-(dim 2^20, 31,981,568 stored entries as complex128 CSR), J_i ~ U[0.5,1.5],
-h_i ~ U[-1,1], drive cos(5t) on sum_i sigma^x_i, step h = 0.005 from t = 0, Leja
-tolerance 1e-10 (rel + abs), method Cf4.  Synthetic inputs from magnus_inputs
-(seeded).  The CSR matrix (640 MB) is larger than L2, so every Leja iteration
-streams it from HBM.
+Headline workload (one Magnus step = one bench step): the open XXZ chain with 20 spins
+(dim 2^20, 31,981,568 stored entries as complex128 CSR), J_i ~ U[0.5,1.5], h_i ~ U[-1,1],
+drive cos(5t) on sum_i sigma^x_i, step h = 0.005 from t = 0, Leja tolerance 1e-10 (rel + abs),
+method Cf4.  Synthetic inputs from magnus_inputs (seeded).  The CSR matrix (640 MB) is larger
+than L2, so every Leja iteration streams it from HBM.  The value is the median of --repeats timed
+regions of exactly --steps steps.
+
+Beside it, in the same JSON line (one GPU only): the plain FP64 GPU path on the same chain and
+steps (complex128 values multiplied in place, FP64 sums, Gershgorin enclosures), the speed-up over
+it and the headline state's error against it; the headline path with Gershgorin enclosures; and a
+short run of every other workload (10-spin chain CF4/M4, 20-spin M4 and matrix-free, the 13-spin
+dense chain in three precisions with their errors, the 512-chain batch, the 16-spin adjoint).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Multi-GPU: one process per GPU under torchrun; every rank propagates its own
-replica (the path has no exchange step), value = all ranks' steps / max time.
---impl reference times the FP64 CPU oracle (plain C, one host core) on the same
-workload, rank 0 only.
+Multi-GPU: one process per GPU under torchrun; every rank propagates its own replica (the path
+has no exchange step), value = all ranks' steps / max time; only the headline runs.
+--impl reference times the FP64 CPU oracle (plain C, one host core) on the same workload, rank 0
+only.
 """
 from __future__ import annotations
 
@@ -85,6 +91,9 @@ def drives(mg, c):
 def algorithmic_per_iteration(c, storage, variant, nnz_terms, fixed=False, subs_per_it=0.0):
     """Bytes and FP64 work one Leja iteration needs (real-valued Hamiltonian, complex state).
 
+    storage "csr_plain": the plain FP64 path (options.plain_values): complex128 values read in place
+    (16 B + 4 B column per entry) and multiplied as complex numbers (4 FP64 instructions per entry).
+
     nnz_terms: stored entries of (H_s, sum_i sx_i) for CSR storage.  fixed: the fixed-point
     arithmetic of the linear generators: the pattern term sum_i sx_i (every stored value 1) is
     summed exactly in 64-bit integers, and (CSR) the products of H_s are 62-bit value mantissas
@@ -127,7 +136,11 @@ def algorithmic_per_iteration(c, storage, variant, nnz_terms, fixed=False, subs_
         vec_bytes += 2 * 16 * D * 2 * (2 if fixed else 1)
     if variant == "M6":
         vec_bytes += (17 + 23 + 16) * 16 * D
-    if storage in ("csr", "csr_real"):
+    if storage == "csr_plain":  # complex128 values multiplied in place: 16 B value + 4 B column, 4 FMAs
+        nnz_s, nnz_c = nnz_terms
+        mat = 20 * (nnz_s + nnz_c) + 2 * 8 * (D + 1)
+        inst = passes * 4 * (nnz_s + nnz_c) + (4 + 2 + 4 + 4) * D + (8 * D if variant == "M4" else 0)
+    elif storage in ("csr", "csr_real"):
         nnz_s, nnz_c = nnz_terms
         if fixed:
             mat = 12 * nnz_s + 4 * nnz_c + 8 * (D + 1) + 2 * D
@@ -200,7 +213,8 @@ class ClockSampler:
 
 # sources whose change can change the persistent kernel's DRAM traffic (the kernel, its rows, and the
 # plan set-up that chooses the matrices' layout and the kernel instantiation)
-PERSISTENT_SOURCES = ("leja_persistent.cu", "rows.cuh", "persist_common.cuh", "magnus_internal.cuh", "magnus_api.cu")
+PERSISTENT_SOURCES = ("leja_persistent.cu", "rows.cuh", "csr_stage.cuh", "tcgen05.cuh", "persist_common.cuh",
+                      "magnus_internal.cuh", "magnus_api.cu")
 DENSE_TC_SOURCES = ("dense_persistent.cu", "dense_tc.cuh", "tcgen05.cuh", "persist_common.cuh", "magnus_internal.cuh")
 
 
@@ -225,6 +239,89 @@ def profiled_traffic(workload_key, files=PERSISTENT_SOURCES):
 
 
 # --------------------------------------------------------------------------- our arm
+def xxz_roofline(c, storage, variant, nnz_terms, st, kms, traffic_key=None):
+    """Roofline of the persistent Leja kernel from its own CUDA-event duration (kms): algorithmic
+    bytes and FMA-equivalent FP64 flops per Leja iteration (algorithmic_per_iteration) times the
+    iterations; the larger of the HBM and FP64 times sets the bound."""
+    nmv = st["n_matvec"]
+    fixed = bool(st["fixed_sums"])
+    bytes_it, flops_it = algorithmic_per_iteration(c, storage, variant, nnz_terms, fixed, st["n_substeps"] / nmv)
+    gbs = bytes_it * nmv / (kms / 1e3) / 1e9
+    tflops = flops_it * nmv / (kms / 1e3) / 1e12
+    peaks = measured_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", HBM_PEAK_FALLBACK))
+    t_hbm, t_alu = bytes_it / (hbm_peak * 1e9), flops_it / (FP64_PEAK_TFLOPS * 1e12)
+    traffic_it = profiled_traffic(traffic_key) if traffic_key else None
+    if t_alu >= t_hbm:
+        roof = {"bound": "alu", "achieved": round(tflops, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+                "unit": "TFLOP/s", "frac": round(tflops / FP64_PEAK_TFLOPS, 4)}
+    else:
+        roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(gbs / hbm_peak, 4)}
+    roof["traffic"] = None if traffic_it is None else int(traffic_it * nmv)
+    roof.update({"kernel": "k_magnus_persistent", "launch_ms": round(kms, 3), "leja_iterations": nmv,
+                 "algorithmic_bytes_per_iteration": bytes_it, "algorithmic_flops_per_iteration": flops_it,
+                 "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 4),
+                 "fp64_tflops": round(tflops, 4), "fp64_frac": round(tflops / FP64_PEAK_TFLOPS, 4),
+                 "peak_source": ("hbm: MEASURED_PEAKS.json copy, of measured" if "hbm_gbs" in peaks else
+                                 f"hbm: {HBM_PEAK_FALLBACK:.0f} GB/s, of fallback (no MEASURED_PEAKS.json)")
+                                + "; fp64: 152 SMs x 2 FP64 instructions/clk x 2 flops x 2070 MHz (FMA-equivalent flops)"})
+    return roof
+
+
+def measure_xxz(mg, c, terms, storage, variant, steps, warmup, repeats, interval="lanczos", fixed=True, staged=None,
+                plain=False, world=1, local=0, keep_state=False, traffic_key=None):
+    """Steps/s of magnus_propagate on chain c: `warmup` untimed steps, then `repeats` timed regions of
+    exactly `steps` steps from the same psi0 and t0, each bracketed by a barrier and a device
+    synchronisation, timed with CUDA events on the launching stream; clocks sampled over all of them.
+    The roofline comes from the persistent kernel's own CUDA-event time of the median repeat."""
+    import torch
+    stream = torch.cuda.current_stream()
+    nnz_terms = tuple(t.col.numel() for t in terms) if storage.startswith("csr") else (0, 0)
+    plan = mg.Plan(c.dim, terms, drives(mg, c), interval=interval, fixed_sums=fixed, staged=staged,
+                   plain_values=plain)
+    psi0 = torch.from_numpy(c.psi0).cuda()
+    psi = psi0.clone()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    if warmup:
+        plan.propagate(psi, 0.0, c.h, warmup, variant)
+    ms, sts = [], []
+    with ClockSampler(local) as clk:
+        for _ in range(max(1, repeats)):
+            psi.copy_(psi0)
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = plan.propagate(psi, c.t0, c.h, steps, variant)
+            e1.record(stream)
+            barrier()
+            ms.append(max_over_ranks(e0.elapsed_time(e1), "cuda"))
+            sts.append(st)
+    order = sorted(range(len(ms)), key=lambda i: ms[i])
+    mid = order[len(order) // 2]
+    rates = sorted(replica_rate(steps, m, world) for m in ms)
+    st = sts[mid]
+    rkey = "csr_plain" if plain else storage
+    out = {"steps_per_s": round(replica_rate(steps, ms[mid], world), 3),
+           "min": round(rates[0], 3), "max": round(rates[-1], 3), "repeats": len(ms), "steps": steps,
+           "ms_per_step": round(ms[mid] / steps, 4), "leja_iterations": st["n_matvec"], "max_degree": st["max_m"],
+           "us_per_leja_iteration": round(st["kernel_ms"] * 1e3 / max(1, st["n_matvec"]), 2),
+           "fixed_sums": st["fixed_sums"], "staged": st["staged"], "grid": st["grid"],
+           "roofline": xxz_roofline(c, rkey, variant, nnz_terms, st, st["kernel_ms"], traffic_key),
+           "clocks": clk.summary()}
+    if keep_state:
+        out["_psi"] = psi.clone()
+        out["_plan"] = plan
+    else:
+        plan.close()
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -243,61 +340,27 @@ def run_ours(args):
     terms = workload_terms(mg, c, storage)
     nnz_terms = tuple(t.col.numel() for t in terms) if storage.startswith("csr") else (0, 0)
     nnz_total = sum(nnz_terms) if storage.startswith("csr") else None
-    plan = mg.Plan(c.dim, terms, drives(mg, c), interval=args.interval, fixed_sums=bool(args.fixed_sums))
-    psi0 = torch.from_numpy(c.psi0).cuda()
-    psi = psi0.clone()
+    fixed = bool(args.fixed_sums)
+    staged = {0: None, 1: True, 2: False}[args.staged]
+    head = measure_xxz(mg, c, terms, storage, variant, args.steps, args.warmup, args.repeats, args.interval, fixed,
+                       staged, False, world, local, keep_state=True)
+    key = f"wl2_{storage}_{variant}" + ("_fixed" if head["fixed_sums"] else "") + ("_staged" if head["staged"] else "")
+    head["roofline"]["traffic"] = (None if profiled_traffic(key) is None
+                                   else int(profiled_traffic(key) * head["roofline"]["leja_iterations"]))
+    plan, psi_head = head.pop("_plan"), head.pop("_psi")
+    value = head["steps_per_s"]
+    psi = torch.empty_like(psi_head)
 
     def barrier():
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    # warm-up: W steps
-    if args.warmup:
-        plan.propagate(psi, 0.0, c.h, args.warmup, variant)
-    psi.copy_(psi0)
-    barrier()
-    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        start.record(stream)
-        st = plan.propagate(psi, c.t0, c.h, args.steps, variant)
-        end.record(stream)
-        barrier()
-    ms = max_over_ranks(start.elapsed_time(end), "cuda")
-    value = replica_rate(args.steps, ms, world)
-
-    # roofline of the persistent Leja kernel, from its own CUDA-event duration
-    nmv = st["n_matvec"]
-    fixed = bool(st["fixed_sums"])
-    bytes_it, flops_it = algorithmic_per_iteration(c, storage, variant, nnz_terms, fixed, st["n_substeps"] / nmv)
-    kms = st["kernel_ms"]
-    gbs = bytes_it * nmv / (kms / 1e3) / 1e9
-    tflops = flops_it * nmv / (kms / 1e3) / 1e12
-    peaks = measured_peaks()
-    hbm_peak = float(peaks.get("hbm_gbs", HBM_PEAK_FALLBACK))
-    t_hbm, t_alu = bytes_it / (hbm_peak * 1e9), flops_it / (FP64_PEAK_TFLOPS * 1e12)
-    key = f"wl2_{storage}_{variant}" + ("_fixed" if fixed else "")
-    traffic_it = profiled_traffic(key)
-    if t_alu >= t_hbm:
-        roof = {"bound": "alu", "achieved": round(tflops, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
-                "unit": "TFLOP/s", "frac": round(tflops / FP64_PEAK_TFLOPS, 4)}
-    else:
-        roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(gbs / hbm_peak, 4)}
-    roof["traffic"] = None if traffic_it is None else int(traffic_it * nmv)
-    roof.update({"kernel": "k_magnus_persistent", "launch_ms": round(kms, 3), "leja_iterations": nmv,
-                 "algorithmic_bytes_per_iteration": bytes_it, "algorithmic_flops_per_iteration": flops_it,
-                 "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 4),
-                 "fp64_tflops": round(tflops, 4), "fp64_frac": round(tflops / FP64_PEAK_TFLOPS, 4),
-                 "peak_source": ("hbm: MEASURED_PEAKS.json copy, of measured" if "hbm_gbs" in peaks else
-                                 f"hbm: {HBM_PEAK_FALLBACK:.0f} GB/s, of fallback (no MEASURED_PEAKS.json)")
-                                + "; fp64: 152 SMs x 2 FP64 instructions/clk x 2 flops x 2070 MHz (FMA-equivalent flops)"})
-
     # end-to-end through the public API with host buffers: every step copies its input state from
     # pinned host memory, runs one Magnus step (magnus_propagate, which returns when the step is
     # done) and copies the result back to pinned host memory.  Two device state buffers: the next
     # step's input copy and the previous step's result copy run on a copy stream while the current
-    # step computes.
+    # step computes.  Every step restarts from the same host state (independent one-step problems).
     host_in = torch.from_numpy(c.psi0).pin_memory()
     host_out = [torch.empty_like(host_in).pin_memory() for _ in range(2)]
     bufs = [psi, torch.empty_like(psi)]
@@ -327,46 +390,214 @@ def run_ours(args):
     e1.record(cstream)
     barrier()
     cstream.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), "cuda")
     e2e = {"value": round(world * e2e_steps / (e2e_ms / 1e3), 3), "unit": "steps/s",
            "h2d_bytes_per_step": host_in.numel() * 16, "d2h_bytes_per_step": host_out[0].numel() * 16,
            "steps": e2e_steps, "copies": "double-buffered: next input H2D and previous result D2H on a copy "
-           "stream during the current step"}
+           "stream during the current step; each step an independent one-step problem from the same host state"}
+    plan.close()
 
     line = {
-        "metric": METRIC, "value": round(value, 3), "unit": "steps/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64+i64" if fixed else "f64", "data": "synthetic",
+        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+i64" if head["fixed_sums"] else "f64",
+        "data": "synthetic",
         "config": {"workload": f"xxz_chain_20spins_{storage}_{variant.lower()}", "spins": c.nspins, "dim": c.dim,
                    "nnz": nnz_total, "h": c.h, "t0": c.t0, "variant": variant, "storage": storage,
-                   "interval": args.interval,
-                   "sums": SUMS_FIXED if fixed else "FP64",
+                   "interval": args.interval, "staged_rows": bool(head["staged"]),
+                   "sums": SUMS_FIXED if head["fixed_sums"] else "FP64",
                    "leja_tol": 1e-10, "l2": "inputs larger than L2: the 640 MB CSR is streamed every iteration"
                    if storage.startswith("csr") else "matrix-free; 4 state vectors of 16 MB stay L2-resident",
                    "parallelism": f"replicas x{world}"},
-        "matvec_gbs": round(gbs, 1),
-        "leja": {"iterations": nmv, "max_degree": st["max_m"], "exponentials": st["n_exp"]},
-        "roofline": roof,
+        "timing": {"repeats": head["repeats"], "steps_per_repeat": args.steps, "value": "median of the repeats",
+                   "min": head["min"], "max": head["max"]},
+        "matvec_gbs": head["roofline"]["hbm_gbs"],
+        "leja": {"iterations": head["leja_iterations"], "max_degree": head["max_degree"],
+                 "us_per_iteration": head["us_per_leja_iteration"]},
+        "roofline": head["roofline"],
         "e2e": e2e,
-        "gpu_launches": 2,
-        "gpu_launches_detail": "timed region: k_exp_setup + k_magnus_persistent (one persistent launch per call)",
-        "clocks": clk.summary(),
+        "gpu_launches": 2 * head["repeats"],
+        "gpu_launches_detail": "timed regions: k_exp_setup + k_magnus_persistent per magnus_propagate call, "
+                               "one call per repeat",
+        "clocks": head["clocks"],
     }
+    if world == 1 and not args.headline_only:
+        # the metric's comparison: the plain FP64 GPU path on the same chain, steps and start state
+        # (complex128 values multiplied in place, FP64 sums, Gershgorin enclosures, rows from global
+        # memory), and the state error of the headline path against it
+        try:
+            plain = measure_xxz(mg, c, workload_terms(mg, c, "csr"), "csr", variant, args.steps, 1,
+                                min(3, args.repeats), "gershgorin", False, False, True, world, local,
+                                keep_state=True, traffic_key=f"wl2_csr_plain_{variant}")
+            plain.pop("_plan").close()
+            pp = plain.pop("_psi")
+            err = float(torch.linalg.norm(psi_head - pp) / torch.linalg.norm(pp))
+            rig = measure_xxz(mg, c, terms, storage, variant, args.steps, 1, 1, "gershgorin", fixed,
+                              staged, False, world, local)
+            line["vs_plain_fp64"] = {
+                "plain_fp64": {k: plain[k] for k in ("steps_per_s", "min", "max", "repeats", "leja_iterations",
+                                                     "us_per_leja_iteration", "roofline")},
+                "plain_how": "complex128 CSR values multiplied in place (options.plain_values), FP64 sums, "
+                             "Gershgorin enclosures, rows read from global memory",
+                "speedup": round(value / plain["steps_per_s"], 3),
+                "state_error": err, "state_error_bound": 1e-8,
+                "state_error_how": f"relative 2-norm of the headline path's state after the {args.steps} timed "
+                                   "steps against the plain FP64 GPU path's, same psi0 and t0",
+                "gershgorin_enclosures": {k: rig[k] for k in ("steps_per_s", "leja_iterations",
+                                                              "us_per_leja_iteration")},
+                "gershgorin_how": "the headline path with rigorous Gershgorin enclosures instead of Lanczos"}
+        except Exception as exc:  # noqa: BLE001 - the headline line is still printed
+            line["vs_plain_fp64"] = {"error": repr(exc)[:300]}
+        line["workloads"] = run_all_workloads(args, mg, mi, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(c, variant, args.cpu_steps, args.interval)
+        line["cpu_baseline"] = cpu_baseline(variant, args.cpu_steps, args.interval)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    plan.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
+# --------------------------------------------------------------------------- every workload
+def wl_xxz(mg, mi, c, storage, variant, steps, repeats, interval, local, label):
+    terms = workload_terms(mg, c, storage)
+    r = measure_xxz(mg, c, terms, storage, variant, steps, 3, repeats, interval, True, None, False, 1, local)
+    r["workload"] = label
+    return r
+
+
+def run_all_workloads(args, mg, mi, local):
+    """One short run of every workload of the benchmark configs, each with its own roofline: the
+    10-spin chain (CF4 and M4, latency-bound), the 20-spin chain with M4 and matrix-free, the 13-spin
+    dense chain in three precisions with their state errors, the 512-chain batch and the 16-spin
+    adjoint gradient.  Each entry is independent; a failure is recorded and the rest still run."""
+    out = {}
+    jobs = [
+        ("cfg1_xxz10_csr_cf4", lambda: wl_xxz(mg, mi, mi.workload1(), "csr", "CF4", 100, 5, args.interval, local,
+                                               "10-spin XXZ chain, CSR, CF4, h = 0.01, t in [0, 1] (100 steps)")),
+        ("cfg1_xxz10_csr_m4", lambda: wl_xxz(mg, mi, mi.workload1(), "csr", "M4", 100, 5, args.interval, local,
+                                              "10-spin XXZ chain, CSR, M4, h = 0.01, t in [0, 1] (100 steps)")),
+        ("cfg2_xxz20_csr_m4", lambda: wl_xxz(mg, mi, mi.workload2(), "csr", "M4", 100, 3, args.interval, local,
+                                              "20-spin XXZ chain, CSR, M4, h = 0.005, 100 steps")),
+        ("cfg2_xxz20_mfree_cf4", lambda: wl_xxz(mg, mi, mi.workload2(), "mfree", "CF4", 100, 3, args.interval,
+                                                 local, "20-spin XXZ chain, matrix-free, CF4, h = 0.005, 100 steps")),
+        ("cfg3_dense13", lambda: dense_workload(mg, mi, local, nvec=64, nspins=13, rate_steps=(2, 4, 100),
+                                                err_states=4, err_steps=100)),
+        ("cfg4_batch512", lambda: batch_workload(mg, mi, local, steps=100, storage="csr", fixed=True)),
+        ("cfg5_adjoint16", lambda: adjoint_workload(mg, mi, local, nsteps=1000)),
+    ]
+    for name, fn in jobs:
+        t = time.perf_counter()
+        try:
+            out[name] = fn()
+        except Exception as exc:  # noqa: BLE001
+            out[name] = {"error": repr(exc)[:300]}
+        out[name]["wall_s"] = round(time.perf_counter() - t, 2)
+    return out
+
+
 # --------------------------------------------------------------------------- dense workload
+def dense_workload(mg, mi, local, nvec=64, nspins=13, rate_steps=(2, 4, 100), err_states=4, err_steps=100,
+                   variant="CF4", warmup=1, modes=("fp64", "fp32_split", "tensor_sliced")):
+    """Long-range chain with dense H_s and dense sum sx (dim 2^nspins), nvec states, h = 0.01: the
+    plain FP64 path, the FP32-split path and the tensor-core sliced path.  Rates from nvec states
+    over rate_steps[i] steps (FP64, split, tensor); state errors of the reduced-precision paths
+    against the FP64 GPU path on the first err_states states over err_steps steps (the states do not
+    interact: every state column has its own scales and stop test)."""
+    import torch
+    c = mi.workload3(nvec=nvec, nspins=nspins)
+    Hs = mg.build_longrange_dense(c.nspins, c.hz, 1.5, c.delta)
+    Hd = mg.build_field_x_dense(c.nspins)
+    stream = torch.cuda.current_stream()
+    prec_of = {"fp64": mg.FP64, "fp32_split": mg.FP32_SPLIT, "tensor_sliced": mg.TENSOR_SLICED}
+    D = c.dim
+    psi_all = torch.from_numpy(c.psi0).cuda()
+    res, finals = {}, {}
+    for i, prec in enumerate(("fp64", "fp32_split", "tensor_sliced")):
+        if prec not in modes:
+            continue
+        nsteps = rate_steps[i]
+        plan = mg.Plan(D, [mg.DenseTerm(Hs), mg.DenseTerm(Hd)], drives(mg, c), nvec=nvec, precision=prec_of[prec])
+        psi = psi_all.clone()
+        if warmup:
+            plan.propagate(psi, 0.0, c.h, 1, variant)
+        psi.copy_(psi_all)
+        torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            s0.record(stream)
+            st = plan.propagate(psi, 0.0, c.h, nsteps, variant)
+            s1.record(stream)
+            torch.cuda.synchronize()
+        ms = s0.elapsed_time(s1)
+        nmv = st["n_matvec"] / nvec  # Leja iterations (all vectors advance together)
+        # per Leja iteration: each dense term read once (16 B/element) + nvec vectors x 64 B/row;
+        # FP64 work: 2 FMAs per H element per vector per term (real H x complex state)
+        bytes_it = 2 * 16 * D * D + nvec * 64 * D
+        fma_it = 2 * 2 * D * D * nvec
+        kms = st["kernel_ms"]
+        r = {"steps_per_s": round(nsteps / (ms / 1e3), 4), "steps": nsteps, "ms_per_step": round(ms / nsteps, 3),
+             "leja_iterations": nmv, "kernel_ms": round(kms, 3),
+             "matvec_gbs": round(bytes_it * nmv / (kms / 1e3) / 1e9, 2),
+             "fp64_equiv_tflops": round(2 * fma_it * nmv / (kms / 1e3) / 1e12, 4), "clocks": clk.summary()}
+        if prec == "tensor_sliced":
+            # issued bf16 MMA work (tcgen05, Cf4): 10 digit pairs x 2 flops x D^2 x 128 columns per dense term
+            r["bf16_tflops_issued"] = round(10 * 2 * D * D * 128 * 2 * nmv / (kms / 1e3) / 1e12, 2)
+        if prec == "fp64":
+            r["roofline"] = {"bound": "alu", "achieved": r["fp64_equiv_tflops"], "peak": round(FP64_PEAK_TFLOPS, 4),
+                             "unit": "TFLOP/s", "frac": round(r["fp64_equiv_tflops"] / FP64_PEAK_TFLOPS, 4)}
+        res[prec] = r
+        if prec != "fp64" and nsteps >= err_steps:
+            finals[prec] = psi[:err_states].clone()
+        plan.close()
+    # state errors: the first err_states states over err_steps steps against the FP64 GPU path
+    errs = {}
+    want = [p for p in ("fp32_split", "tensor_sliced") if p in modes]
+    if "fp64" in modes and err_states > 0 and want:
+        plan = mg.Plan(D, [mg.DenseTerm(Hs), mg.DenseTerm(Hd)], drives(mg, c), nvec=err_states)
+        ref = psi_all[:err_states].clone()
+        plan.propagate(ref, 0.0, c.h, err_steps, variant)
+        plan.close()
+        for prec in want:
+            got = finals.get(prec)
+            if got is None:
+                plan = mg.Plan(D, [mg.DenseTerm(Hs), mg.DenseTerm(Hd)], drives(mg, c), nvec=err_states,
+                               precision=prec_of[prec])
+                got = psi_all[:err_states].clone()
+                plan.propagate(got, 0.0, c.h, err_steps, variant)
+                plan.close()
+            e = torch.linalg.norm(got - ref, dim=1) / torch.linalg.norm(ref, dim=1)
+            errs[prec] = float(e.max())
+    peaks = measured_peaks()
+    bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
+    if "tensor_sliced" in res:
+        ts = res["tensor_sliced"]
+        # DRAM bytes per Leja iteration from the 12-spin capture (dim 4096), scaled by (dim / 4096)^2:
+        # the traffic is the digits of the dense terms, read once per iteration
+        t12 = profiled_traffic("dense_tc_12spins_64states", DENSE_TC_SOURCES)
+        ts["roofline"] = {"bound": "tensor", "kernel": "k_dense_persistent (tcgen05 digit products)",
+                          "achieved": ts["bf16_tflops_issued"], "peak": bf16_peak, "unit": "TFLOP/s",
+                          "frac": round(ts["bf16_tflops_issued"] / bf16_peak, 4),
+                          "traffic": None if t12 is None or nvec != 64 else int(t12 * (D / 4096) ** 2),
+                          "traffic_unit": "DRAM bytes per Leja iteration (12-spin ncu capture scaled by (dim/4096)^2)",
+                          "peak_source": ("MEASURED_PEAKS.json bf16_tflops (burst), of measured"
+                                          if "bf16_tflops" in peaks else
+                                          "1900 TFLOP/s bf16 burst, of fallback (no MEASURED_PEAKS.json)"),
+                          "work": "10 bf16 digit-pair products x 2 flops x dim^2 x 128 columns per dense term per "
+                                  "Leja iteration"}
+    f64 = res.get("fp64")
+    return {"workload": f"long-range chain, {nspins} spins, dense H_s and sum sx (2 x {16 * D * D / 1e9:.2f} GB "
+                        f"complex128), {nvec} states, {variant}, h = 0.01",
+            "paths": res,
+            "speedup_vs_fp64": ({k: round(res[k]["steps_per_s"] / f64["steps_per_s"], 3) for k in res if k != "fp64"}
+                                if f64 else None),
+            "state_error_vs_fp64": errs,
+            "state_error_how": f"max over states 0..{err_states - 1} of the relative 2-norm error after {err_steps} "
+                               f"steps against the FP64 GPU path",
+            "state_error_bound": 1e-8}
+
+
 def run_dense13(args):
-    """13-spin long-range chain, dense H_s and dense sum sx (dim 8192, 2 x 1.07 GB complex128), 64
-    states, Cf4, h = 0.01: the plain FP64 path, the FP32-split path and the tensor-core sliced path
-    on the same states; each reduced-precision path's state error against the FP64 GPU result is
-    stated.  The line's value is the sliced path's rate."""
+    """The dense workload alone (one JSON line); the line's value is the fastest path's rate."""
     import torch
 
     import magnus_inputs as mi
@@ -375,197 +606,110 @@ def run_dense13(args):
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     mg.load()
-    c = mi.workload3(nvec=args.states, nspins=args.spins)
-    Hs = mg.build_longrange_dense(c.nspins, c.hz, 1.5, c.delta)
-    Hd = mg.build_field_x_dense(c.nspins)
-    stream = torch.cuda.current_stream()
-    res = {}
-    modes = {"fp64": mg.FP64, "fp32_split": mg.FP32_SPLIT, "tensor_sliced": mg.TENSOR_SLICED}
-    wanted = [m for m in args.dense_prec.split(",") if m]
-    for prec, mode in modes.items():
-        if prec not in wanted:
-            continue
-        plan = mg.Plan(c.dim, [mg.DenseTerm(Hs), mg.DenseTerm(Hd)], drives(mg, c), nvec=args.states,
-                       precision=mode)
-        psi0 = torch.from_numpy(c.psi0).cuda()
-        psi = psi0.clone()
-        if args.warmup:
-            plan.propagate(psi, 0.0, c.h, 1, args.variant)
-        psi.copy_(psi0)
-        torch.cuda.synchronize()
-        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with ClockSampler(local) as clk:
-            s0.record(stream)
-            st = plan.propagate(psi, 0.0, c.h, args.steps, args.variant)
-            s1.record(stream)
-            torch.cuda.synchronize()
-        ms = s0.elapsed_time(s1)
-        res[prec] = {"ms": ms, "st": st, "psi": psi.clone(), "clk": clk.summary()}
-        plan.close()
-    D, nv = c.dim, args.states
-    out = {}
-    for prec, r in res.items():
-        nmv = r["st"]["n_matvec"] / nv  # Leja iterations (all vectors advance together)
-        # per Leja iteration: each dense term read once (16 B/element) + 64 vectors x 64 B/row;
-        # FP64 work: 2 FMAs per H element per vector per term (real H x complex state)
-        bytes_it = 2 * 16 * D * D + nv * 64 * D
-        fma_it = 2 * 2 * D * D * nv
-        kms = r["st"]["kernel_ms"]
-        out[prec] = {"steps_per_s": round(args.steps / (r["ms"] / 1e3), 4), "ms_per_step": round(r["ms"] / args.steps, 3),
-                     "leja_iterations": nmv, "kernel_ms": round(kms, 3),
-                     "matvec_gbs": round(bytes_it * nmv / (kms / 1e3) / 1e9, 2),
-                     "fp64_equiv_tflops": round(2 * fma_it * nmv / (kms / 1e3) / 1e12, 4), "clocks": r["clk"]}
-        if prec == "tensor_sliced":
-            # issued bf16 MMA work (tcgen05, Cf4): 10 digit pairs x 2 flops x D^2 x 128 columns per dense term
-            out[prec]["bf16_tflops_issued"] = round(10 * 2 * D * D * 128 * 2 * nmv / (kms / 1e3) / 1e12, 2)
-    errs = {}
-    if "fp64" in res:
-        a = res["fp64"]["psi"].cpu().numpy()
-        for prec in ("fp32_split", "tensor_sliced"):
-            if prec in res:
-                b = res[prec]["psi"].cpu().numpy()
-                errs[prec] = float(np.max(np.linalg.norm(a - b, axis=1) / np.linalg.norm(a, axis=1)))
-    f64 = out.get("fp64")
-    best = out.get("tensor_sliced") or out.get("fp32_split") or f64
-    peaks = measured_peaks()
-    bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
-    if "tensor_sliced" in out:
-        # the dominant kernel of the timed path: k_dense_persistent<..., 3>, its tensor-core work
-        ts = out["tensor_sliced"]
-        # DRAM bytes per Leja iteration from the 12-spin capture (dim 4096), scaled by (dim / 4096)^2:
-        # the traffic is the digits of the dense terms, read once per iteration
-        t12 = profiled_traffic("dense_tc_12spins_64states", DENSE_TC_SOURCES)
-        roof = {"bound": "tensor", "kernel": "k_dense_persistent (tcgen05 digit products)",
-                "achieved": ts["bf16_tflops_issued"], "peak": bf16_peak, "unit": "TFLOP/s",
-                "frac": round(ts["bf16_tflops_issued"] / bf16_peak, 4),
-                "traffic": None if t12 is None or nv != 64 else int(t12 * (D / 4096) ** 2),
-                "traffic_unit": "DRAM bytes per Leja iteration (12-spin ncu capture scaled by (dim/4096)^2)",
-                "peak_source": ("MEASURED_PEAKS.json bf16_tflops (burst), of measured" if "bf16_tflops" in peaks
-                                else "1900 TFLOP/s bf16 burst, of fallback (no MEASURED_PEAKS.json)"),
-                "work": "10 bf16 digit-pair products x 2 flops x dim^2 x 128 columns per dense term per Leja iteration"}
-    else:
-        roof = {"bound": "alu", "kernel": "k_dense_persistent (FP64 path)",
-                "achieved": f64["fp64_equiv_tflops"], "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
-                "frac": round(f64["fp64_equiv_tflops"] / FP64_PEAK_TFLOPS, 4), "traffic": None}
+    modes = tuple(m for m in args.dense_prec.split(",") if m)
+    r = dense_workload(mg, mi, local, nvec=args.states, nspins=args.spins,
+                       rate_steps=(min(args.steps, 4), min(args.steps, 10), args.steps), err_states=min(4, args.states),
+                       err_steps=args.steps, variant=args.variant, warmup=args.warmup, modes=modes)
+    paths = r["paths"]
+    best = paths.get("tensor_sliced") or paths.get("fp32_split") or paths.get("fp64")
     line = {
         "metric": METRIC, "value": best["steps_per_s"], "unit": "steps/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": best["ms_per_step"],
+        "steps": best["steps"], "warmup": args.warmup, "ms_per_step": best["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16-digits(f64-equivalent)" if "tensor_sliced" in out else "f64",
-        "data": "synthetic",
-        "config": {"workload": f"longrange_chain_{c.nspins}spins_dense_{nv}states_cf4", "spins": c.nspins, "dim": D,
-                   "states": nv, "h": c.h, "variant": args.variant,
-                   "l2": f"inputs larger than L2: 2 x {16 * D * D / 1e9:.2f} GB dense terms"},
-        "paths": out,
-        "speedup_vs_fp64": {k: round(out[k]["steps_per_s"] / f64["steps_per_s"], 3) for k in errs} if f64 else None,
-        "state_error_vs_fp64": errs,
-        "roofline": roof,
-        "gpu_launches": 2,
+        "dtype": "bf16-digits(f64-equivalent)" if "tensor_sliced" in paths else "f64", "data": "synthetic",
+        "config": {"workload": f"longrange_chain_{args.spins}spins_dense_{args.states}states_{args.variant.lower()}",
+                   "spins": args.spins, "states": args.states, "variant": args.variant,
+                   "l2": "inputs larger than L2: two dense terms of 16 dim^2 bytes"},
+        "roofline": best.get("roofline"), "gpu_launches": 2, **{k: v for k, v in r.items() if k != "workload"},
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
 
 
 # --------------------------------------------------------------------------- batched workload
-def run_batch512(args):
-    """512 independent XXZ chains of 8-14 spins (dims 256..16384, CSR terms), per-chain drive
-    A cos(w t), Cf4, h = 0.01, one persistent launch under a replayed CUDA graph.  A step advances
-    every chain by one Magnus step."""
+def batch_workload(mg, mi, local, steps=100, storage="csr", fixed=True, variant="CF4", warmup=1, sample_every=32):
+    """512 independent XXZ chains of 8-14 spins (dims 256..16384), per-chain drive A cos(w t), Cf4,
+    h = 0.01, one persistent launch under a replayed CUDA graph.  A step advances every chain by one
+    Magnus step.  Compared with one plan and launch per chain on every sample_every-th chain."""
     import torch
-
-    import magnus_inputs as mi
-    import paper_1709_06483_gb300 as mg
-
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    mg.load()
     chains = mi.workload4()
     probs = []
     nnz_s = nnz_c = 0  # stored entries of H_s and of sum_i sx_i over all chains
     for c in chains:
-        terms = workload_terms(mg, c, args.storage)
-        if args.storage.startswith("csr"):
+        terms = workload_terms(mg, c, storage)
+        if storage.startswith("csr"):
             nnz_s += terms[0].col.numel()
             nnz_c += terms[1].col.numel()
         probs.append((c.dim, terms, drives(mg, c)))
     nnz = nnz_s + nnz_c
-    B = mg.Batch(probs, fixed_sums=bool(args.fixed_sums))
+    B = mg.Batch(probs, fixed_sums=fixed)
     psi0 = [torch.from_numpy(c.psi0).cuda() for c in chains]
     psis = [p.clone() for p in psi0]
-    B.propagate(psis, 0.0, 0.01, args.warmup or 1, args.variant)  # autotune + warm-up
+    B.propagate(psis, 0.0, 0.01, warmup or 1, variant)  # autotune + warm-up
     for p, q in zip(psis, psi0):
         p.copy_(q)
-    B.propagate(psis, 0.0, 0.01, args.steps, args.variant)         # captures the graph for these steps
+    B.propagate(psis, 0.0, 0.01, steps, variant)         # captures the graph for these steps
     for p, q in zip(psis, psi0):
         p.copy_(q)
     torch.cuda.synchronize()
-    stream = torch.cuda.current_stream()
     with ClockSampler(local) as clk:
         t = time.perf_counter()
-        st = B.propagate(psis, 0.0, 0.01, args.steps, args.variant)  # replay
+        st = B.propagate(psis, 0.0, 0.01, steps, variant)  # replay
         wall = time.perf_counter() - t
     gms = st["graph_ms"]
     rows = sum(c.dim for c in chains)
     fixed = bool(st["fixed_sums"])
-    vb = 12  # real values: complex-stored ones are multiplied from the batch's float64 copy
     # as algorithmic_per_iteration: with fixed sums the field term needs its columns only and the
     # vectors add the fixed-point copies (32 B per row, and 32 B per row once per substep)
     vec = 64 * rows + ((32 + 32 * st["n_substeps"] / st["n_matvec"]) * rows if fixed else 0)
     if fixed:  # H_s mantissas + columns, its row pointers and exponents; the field's columns only
         mat = 12 * nnz_s + 4 * nnz_c + sum(8 * (c.dim + 1) + 2 * c.dim for c in chains)
-    else:
-        mat = vb * nnz + sum(2 * 8 * (c.dim + 1) for c in chains)
-    bytes_it = mat + vec if args.storage.startswith("csr") else vec
+    else:  # real values: complex-stored ones are multiplied from the batch's float64 copy
+        mat = 12 * nnz + sum(2 * 8 * (c.dim + 1) for c in chains)
+    bytes_it = mat + vec if storage.startswith("csr") else vec
     # Leja iterations differ per chain; algorithmic bytes weighted by each chain's iterations are
     # approximated with the mean iteration count per chain
     iters_per_chain = st["n_matvec"] / len(chains)
     gbs = bytes_it * iters_per_chain / (gms / 1e3) / 1e9
     if fixed:  # fixed-point sums and products: 14 FP64 instructions per row remain in both families
         inst_it = 14 * rows
-    elif args.storage.startswith("csr"):
+    elif storage.startswith("csr"):
         inst_it = 2 * nnz + 14 * rows
     else:
         inst_it = sum(c.dim * (4 + (c.nspins - 1) + 2 * c.nspins + 2) + 10 * c.dim for c in chains)
     tflops = 2 * inst_it * iters_per_chain / (gms / 1e3) / 1e12
     peaks = measured_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", HBM_PEAK_FALLBACK))
-    # the plain FP64 GPU path for comparison: one plan and one persistent launch per chain, on a
-    # sample of every 16th chain (the sizes are drawn independently, so the sample is unbiased),
-    # extrapolated by the chain count
-    seq_steps = min(args.steps, 20)
-    sample = chains[::16]
+    # one plan and one persistent launch per chain for comparison (same arithmetic), on a sample of
+    # the chains (sizes drawn independently, so the sample is unbiased), extrapolated by the count
+    seq_steps = min(steps, 20)
+    sample = chains[::sample_every]
     seq_ms = 0.0
     for c in sample:
-        q = mg.Plan(c.dim, workload_terms(mg, c, args.storage), drives(mg, c), fixed_sums=bool(args.fixed_sums))
+        q = mg.Plan(c.dim, workload_terms(mg, c, storage), drives(mg, c), fixed_sums=fixed)
         x = torch.from_numpy(c.psi0).cuda()
-        q.propagate(x, 0.0, 0.01, 1, args.variant)
+        q.propagate(x, 0.0, 0.01, 1, variant)
         torch.cuda.synchronize()
         t = time.perf_counter()
-        q.propagate(x, 0.0, 0.01, seq_steps, args.variant)
+        q.propagate(x, 0.0, 0.01, seq_steps, variant)
         torch.cuda.synchronize()
         seq_ms += (time.perf_counter() - t) * 1e3
         q.close()
     share = len(sample) / len(chains)
     seq_rate = seq_steps / (seq_ms / share / 1e3)
-    batch_rate = args.steps / (gms / 1e3)
-    line = {
-        "metric": METRIC, "value": round(args.steps / (gms / 1e3), 3), "unit": "steps/s (all 512 chains per step)",
-        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(gms / args.steps, 4),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+i64" if fixed else "f64",
-        "data": "synthetic",
-        "config": {"workload": f"batch_512_xxz_chains_8to14spins_{args.storage}_{args.variant.lower()}",
-                   "chains": len(chains), "rows": rows, "nnz": nnz, "h": 0.01, "variant": args.variant,
-                   "cta_size": st["block"], "cluster_size": st["cluster"],
-                   "sums": SUMS_FIXED if fixed else "FP64"},
-        "chain_steps_per_s": round(len(chains) * args.steps / (gms / 1e3), 1),
+    batch_rate = steps / (gms / 1e3)
+    B.close()
+    return {
+        "workload": f"512 XXZ chains of 8-14 spins, {storage}, {variant}, h = 0.01, {steps} steps per graph replay",
+        "steps_per_s": round(batch_rate, 3), "steps": steps, "ms_per_step": round(gms / steps, 4),
+        "unit": "steps/s (all 512 chains per step)", "chain_steps_per_s": round(len(chains) * batch_rate, 1),
+        "chains": len(chains), "rows": rows, "nnz": nnz, "cta_size": st["block"], "cluster_size": st["cluster"],
+        "fixed_sums": int(fixed), "leja_iterations": st["n_matvec"], "matvec_gbs": round(gbs, 1),
         "per_chain_plans": {"steps_per_s": round(seq_rate, 3), "how": f"one plan and launch per chain (same "
                             f"arithmetic), {len(sample)} of 512 chains x {seq_steps} steps, wall time scaled by the "
                             f"chain count (x {1 / share:.0f})"},
         "speedup_vs_per_chain_plans": round(batch_rate / seq_rate, 2),
-        "leja_iterations": st["n_matvec"], "matvec_gbs": round(gbs, 1),
-        # the larger of the FP64 and HBM times per iteration sets the bound, as for the single chain:
-        # FMA-equivalent flops and bytes per iteration as in algorithmic_per_iteration, summed over
-        # the chains
+        # the larger of the FP64 and HBM times per iteration sets the bound, as for the single chain
         "roofline": dict(({"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                            "frac": round(gbs / hbm_peak, 4)}
                           if gbs / hbm_peak > tflops / FP64_PEAK_TFLOPS else
@@ -574,20 +718,11 @@ def run_batch512(args):
                          kernel="k_batched", hbm_gbs=round(gbs, 1), hbm_frac=round(gbs / hbm_peak, 4),
                          fp64_tflops=round(tflops, 4), fp64_frac=round(tflops / FP64_PEAK_TFLOPS, 4),
                          traffic=None, note="graph time includes the batch's setup launch"),
-        "wall_ms": round(wall * 1e3, 2), "gpu_launches": 2,
-        "gpu_launches_detail": "graph: k_exp_setup_batch + k_batched (plus two memsets)", "clocks": clk.summary(),
-    }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    B.close()
+        "wall_ms": round(wall * 1e3, 2), "clocks": clk.summary(),
+        "gpu_launches_detail": "graph: k_exp_setup_batch + k_batched (plus two memsets)"}
 
 
-# --------------------------------------------------------------------------- adjoint workload
-def run_adjoint16(args):
-    """Optimal-control gradient: 16-spin chain (matrix-free), f(t) = sum_{k=1}^{32} c_k sin(k pi t / T),
-    T = 10, 1000 Cf4 steps of 0.01, F = |<phi|psi(T)>|^2, dF/dc by the adjoint with checkpoints every
-    16 steps; timed against one forward propagation, and checked against central differences of F for
-    two coefficients."""
+def run_batch512(args):
     import torch
 
     import magnus_inputs as mi
@@ -596,6 +731,29 @@ def run_adjoint16(args):
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     mg.load()
+    r = batch_workload(mg, mi, local, steps=args.steps, storage=args.storage, fixed=bool(args.fixed_sums),
+                       variant=args.variant, warmup=args.warmup, sample_every=16)
+    line = {
+        "metric": METRIC, "value": r["steps_per_s"], "unit": r["unit"], "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64+i64" if r["fixed_sums"] else "f64", "data": "synthetic",
+        "config": {"workload": f"batch_512_xxz_chains_8to14spins_{args.storage}_{args.variant.lower()}",
+                   "chains": r["chains"], "rows": r["rows"], "nnz": r["nnz"], "h": 0.01, "variant": args.variant,
+                   "cta_size": r["cta_size"], "cluster_size": r["cluster_size"],
+                   "sums": SUMS_FIXED if r["fixed_sums"] else "FP64"},
+        "gpu_launches": 2, **{k: v for k, v in r.items() if k not in ("workload", "unit", "steps")},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- adjoint workload
+def adjoint_workload(mg, mi, local, nsteps=1000, fd_coefs=(0, 31)):
+    """Optimal-control gradient: 16-spin chain (matrix-free), f(t) = sum_{k=1}^{32} c_k sin(k pi t / T),
+    T = 10, nsteps Cf4 steps of 0.01, F = |<phi|psi(T)>|^2, dF/dc by the adjoint with checkpoints every
+    16 steps; timed against one forward propagation, and checked against central differences of F
+    for the coefficients fd_coefs."""
+    import torch
     c = mi.workload5()
     n, om, ck = c.nspins, c.drive_om, c.drive_as
 
@@ -605,7 +763,6 @@ def run_adjoint16(args):
 
     plan = plan_for(ck)
     psi0, phi = torch.from_numpy(c.psi0).cuda(), torch.from_numpy(c.phi).cuda()
-    nsteps = args.steps if args.steps != 100 else c.nsteps
     plan.adjoint_grad(psi0, phi, 0.0, c.h, min(nsteps, 32), "CF4", kd=1, ckpt_every=16)  # warm-up
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
@@ -616,7 +773,9 @@ def run_adjoint16(args):
     torch.cuda.synchronize()
     t = time.perf_counter()
     plan.propagate(psi, 0.0, c.h, nsteps, "CF4")
+    torch.cuda.synchronize()
     t_fwd = time.perf_counter() - t
+    plan.close()
 
     def fid(coefs):
         q = plan_for(coefs)
@@ -626,24 +785,43 @@ def run_adjoint16(args):
         return abs(torch.vdot(phi, x).item()) ** 2
 
     errs = []
-    for k in (0, 31):
+    for k in fd_coefs:
         up, dn = ck.copy(), ck.copy()
         up[k] += 1e-5
         dn[k] -= 1e-5
         fd = (fid(up) - fid(dn)) / 2e-5
         errs.append(abs(grad[1 + om.size + k] - fd))
+    return {
+        "workload": f"16-spin chain (matrix-free), 32 sine modes, T = 10, {nsteps} Cf4 steps of 0.01, checkpoints "
+                    "every 16 steps, gradient of |<phi|psi(T)>|^2 by the adjoint",
+        "steps_per_s": round(nsteps / t_grad, 2), "unit": "adjoint steps/s (forward + gradient)", "steps": nsteps,
+        "ms_per_step": round(t_grad * 1e3 / nsteps, 4), "F": F, "gradient_time_s": round(t_grad, 4),
+        "forward_time_s": round(t_fwd, 4), "gradient_over_forward": round(t_grad / t_fwd, 3),
+        "max_abs_err_vs_central_differences": max(errs), "fd_coefficients": list(fd_coefs),
+        # the plain alternative: central differences need 2 forward propagations per parameter
+        "speedup_vs_central_differences": round(2 * grad.size * t_fwd / t_grad, 2), "parameters": int(grad.size),
+        "clocks": clk.summary(),
+        "gpu_launches_detail": "about 4 per exponential (recompute, augmented Leja, dot, costate)"}
+
+
+def run_adjoint16(args):
+    import torch
+
+    import magnus_inputs as mi
+    import paper_1709_06483_gb300 as mg
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    mg.load()
+    nsteps = args.steps if args.steps != 100 else 1000
+    r = adjoint_workload(mg, mi, local, nsteps=nsteps)
     line = {
-        "metric": METRIC, "value": round(nsteps / t_grad, 2), "unit": "adjoint steps/s (forward + gradient)",
-        "n_gpus": world, "steps": nsteps, "warmup": 1, "ms_per_step": round(t_grad * 1e3 / nsteps, 4),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "adjoint_xxz_16spins_32modes_cf4", "spins": n, "dim": c.dim, "modes": int(om.size),
-                   "T": 10.0, "h": c.h, "checkpoint_every": 16},
-        "F": F, "gradient_time_s": round(t_grad, 4), "forward_time_s": round(t_fwd, 4),
-        "gradient_over_forward": round(t_grad / t_fwd, 3), "max_abs_err_vs_central_differences": max(errs),
-        # the plain FP64 GPU alternative: central differences need 2 forward propagations per parameter
-        "speedup_vs_central_differences": round(2 * grad.size * t_fwd / t_grad, 2),
-        "parameters": int(grad.size),
-        "gpu_launches": "about 4 per exponential (recompute, augmented Leja, dot, costate)", "clocks": clk.summary(),
+        "metric": METRIC, "value": r["steps_per_s"], "unit": r["unit"], "n_gpus": world, "steps": nsteps,
+        "warmup": 1, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "adjoint_xxz_16spins_32modes_cf4", "spins": 16, "modes": 32, "T": 10.0, "h": 0.01,
+                   "checkpoint_every": 16},
+        "gpu_launches": "about 4 per exponential", **{k: v for k, v in r.items() if k not in ("workload", "unit", "steps")},
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -740,15 +918,37 @@ def oracle_problem(c, interval="gershgorin"):
     return oracle.Problem([Hs, Hd], [oracle.Coeff.const(), f], interval=interval)
 
 
-def cpu_baseline(c, variant, nsteps, interval="gershgorin"):
-    """The FP64 CPU oracle as it stands (plain C, single thread) on the first nsteps steps."""
-    P = oracle_problem(c, interval)
-    t = time.perf_counter()
-    P.propagate(c.psi0, c.t0, c.h, nsteps, variant)
-    dt = time.perf_counter() - t
-    return {"value": round(nsteps / dt, 4), "unit": "steps/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {nsteps} of the 200 {variant} steps of the 20-spin chain (full state, full matrix)",
-            "host": os.uname().machine, "nproc": os.cpu_count()}
+def _oracle_timing(steps, variant, interval, threaded):
+    """Run oracle/cpu_timing.py in a process of its own (no CUDA context) and return its record."""
+    env = dict(os.environ)
+    if threaded:
+        env["OMP_NUM_THREADS"] = str(os.cpu_count() or 1)
+    cmd = [sys.executable, "-m", "oracle.cpu_timing", "--steps", str(steps), "--variant", variant,
+           "--interval", interval] + (["--threaded"] if threaded else [])
+    out = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-500:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(variant, nsteps, interval="gershgorin"):
+    """The FP64 CPU oracle as it stands (plain C) on the first nsteps steps of the 20-spin chain, timed
+    on the host cores: the single-threaded checker (the line's value) and the OpenMP build of the
+    same source on every core (its element-wise loops spread over threads, identical bits), the
+    analogue of the paper's multi-core CPU runs."""
+    one = _oracle_timing(nsteps, variant, interval, False)
+    rec = {"value": round(one["steps"] / one["seconds"], 4), "unit": "steps/s", "cores": 1, "kind": "oracle",
+           "sample": f"first {nsteps} of the 200 {variant} steps of the 20-spin chain (full state, full matrix), "
+                     f"{interval} enclosures, single-threaded",
+           "host": one["host"], "nproc": one["nproc"]}
+    try:
+        allc = _oracle_timing(nsteps, variant, interval, True)
+        rec["all_cores"] = {"value": round(allc["steps"] / allc["seconds"], 4), "unit": "steps/s",
+                            "cores": allc["threads"], "kind": "oracle (OpenMP build of the same source)",
+                            "sample": f"the same {nsteps} steps on {allc['threads']} threads"}
+    except Exception as exc:  # noqa: BLE001 - e.g. no OpenMP runtime on the host
+        rec["all_cores"] = {"unavailable": repr(exc)[:200]}
+    return rec
 
 
 def run_reference(args):
@@ -793,6 +993,13 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--fixed-sums", type=int, choices=[0, 1], default=1,
                     help="xxz20: pattern-term sums in fixed point (1) or FP64 (0)")
+    ap.add_argument("--staged", type=int, choices=[0, 1, 2], default=0,
+                    help="xxz20 CSR in fixed point: 1 = matrix runs staged in shared memory per warp tile, "
+                         "2 = rows read from global memory, 0 = the library's choice")
+    ap.add_argument("--repeats", type=int, default=5,
+                    help="timed regions of --steps steps each (the value is their median)")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="xxz20: skip the plain-FP64 comparison and the other workloads")
     ap.add_argument("--cpu-steps", type=int, default=16,
                     help="steps of the CPU oracle sample (about 12 s on one Grace core)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -162,6 +162,19 @@ typedef enum {
  *                     a converted result below 2^-1022 flushes to zero (FP64 would keep a
  *                     subnormal).  0 = FP64 throughout.  Not part of the paper, which computes in
  *                     FP64 only.
+ *   staged_rows [0]: how the CSR rows of fixed-point plans (every term CSR, fixed_sums, every term
+ *                     a pattern or a product term) read the matrix.  1 = staged: each warp's
+ *                     32-row tiles have their columns and mantissas copied into shared memory two
+ *                     tiles ahead by the TMA bulk engine (one CTA of 8 warps per SM); tiles whose
+ *                     runs do not fit a 9,472-byte slot are read from global memory, and a plan
+ *                     stages only if at most 1/64 of its tiles are such.  2 = rows read from global
+ *                     memory (4 CTAs per SM).  0 = the library's choice (currently 2).  The integer
+ *                     sums make both ways bit-identical.
+ *   plain_values [0]: 1 = multiply complex-stored CSR and dense values in place as complex128 numbers
+ *                     even when every imaginary part is zero (no real-valued specialisation, no
+ *                     float64 copy, no pattern or fixed-point rows): the plain FP64 path of the paper,
+ *                     kept as the baseline the faster paths are measured against.  Real storage
+ *                     (MAGNUS_TERM_*_REAL) is unaffected.  _reserved must be 0.
  */
 typedef struct {
   double tol_rel;
@@ -175,6 +188,8 @@ typedef struct {
   int32_t test_skip_arrival;
   int32_t interval;
   int32_t fixed_sums;
+  int32_t staged_rows;
+  int32_t plain_values;
   int32_t _reserved;
 } magnus_options;
 
@@ -191,7 +206,7 @@ typedef struct {
   int32_t grid;         /* CTAs of that launch                                */
   int32_t block;        /* threads per CTA                                    */
   int32_t fixed_sums;   /* 1 if the call's matvecs ran in fixed point (options.fixed_sums)      */
-  int32_t _pad;
+  int32_t staged;       /* 1 if its CSR rows were read from shared-memory slots (unstaged_rows) */
 } magnus_stats;
 
 typedef struct magnus_plan_s *magnus_plan_t;
@@ -399,6 +414,8 @@ MAGNUS_API const char *magnus_batch_last_error(magnus_batch_t batch);
  *  - v, out: device complex128 [2^nspins], 16-byte aligned, may alias.  stream: cudaStream_t or
  *    NULL.  The call synchronises the stream before it returns.
  *  - Calls no cudaMalloc, cudaFree or other allocating routine.  Error text: magnus_last_error(NULL).
+ *  - Arithmetic: FP64 sums and products throughout (the generic rows of the persistent kernel), where
+ *    a plan defaults to fixed-point sums; results agree with leja_expv to the Leja tolerance.
  */
 MAGNUS_API magnus_status magnus_expv_xxz_static(int32_t nspins, const double *J, const double *hz, double delta,
                                                 const double *beta, const void *v, void *out, double tol,

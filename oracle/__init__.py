@@ -22,8 +22,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "magnus_oracle.c")
 _HDR = os.path.join(_HERE, "magnus_oracle.h")
 _LIB = os.path.join(_HERE, "libmagnus_oracle.so")
+_LIB_OMP = os.path.join(_HERE, "libmagnus_oracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_lib_omp = None
 
 OK, EINVAL, ENOMEM, ENOCONV, ENONFINITE = 0, 1, 2, 4, 5
 M4, CF4, CF4_3, M2, M6 = 1, 2, 3, 4, 5
@@ -36,14 +38,18 @@ class OracleError(RuntimeError):
         self.code = code
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain -O2, no BLAS, no OpenMP)."""
-    stale = (not os.path.exists(_LIB)) or max(os.path.getmtime(_SRC), os.path.getmtime(_HDR)) > os.path.getmtime(_LIB)
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle with gcc (plain -O2, no BLAS).  The checker is the build without OpenMP;
+    openmp=True gives libmagnus_oracle_omp.so, the same source with its element-wise loops spread
+    over threads (identical bits), used only to time the CPU baseline on all host cores."""
+    lib_path = _LIB_OMP if openmp else _LIB
+    stale = (not os.path.exists(lib_path)) or max(os.path.getmtime(_SRC), os.path.getmtime(_HDR)) > os.path.getmtime(lib_path)
     if force or stale:
-        tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+        tmp = lib_path + f".{os.getpid()}.tmp"
+        flags = ["-fopenmp"] if openmp else []
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", *flags, "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 class _Stats(C.Structure):
@@ -90,9 +96,14 @@ def load(path: str):
     return L
 
 
-def lib():
-    global _lib
+def lib(threaded: bool = False):
+    """The checker (single-threaded build), or with threaded=True the OpenMP build."""
+    global _lib, _lib_omp
     with _lock:
+        if threaded:
+            if _lib_omp is None:
+                _lib_omp = load(build(openmp=True))
+            return _lib_omp
         if _lib is None:
             _lib = load(build())
     return _lib
@@ -221,12 +232,12 @@ class Problem:
     """H(t) = sum_k f_k(t) H_k with H_k CSR or dense (Sec. 4, H = H_1 + h(t) H_2)."""
 
     def __init__(self, terms, coeffs, tol=1e-10, tol_abs=None, m_max=100, rho_max=4.0, interval="gershgorin",
-                 lanczos_steps=48):
+                 lanczos_steps=48, threaded=False):
         assert len(terms) == len(coeffs) and len(terms) >= 1
         self.terms, self.coeffs = list(terms), list(coeffs)
         self.dim = terms[0].dim if isinstance(terms[0], CSR) else terms[0].shape[0]
         self._keep = []
-        L = lib()
+        L = self._L = lib(threaded)
         self._h = L.orc_problem_new(self.dim, len(terms))
         if not self._h:
             raise OracleError(EINVAL, "problem_new")
@@ -251,42 +262,42 @@ class Problem:
 
     def __del__(self):
         if getattr(self, "_h", None):
-            lib().orc_problem_free(self._h)
+            self._L.orc_problem_free(self._h)
             self._h = None
 
     def interval(self, k):
         a, b = C.c_double(), C.c_double()
-        _check(lib().orc_term_interval(self._h, k, C.byref(a), C.byref(b)), "term_interval")
+        _check(self._L.orc_term_interval(self._h, k, C.byref(a), C.byref(b)), "term_interval")
         return a.value, b.value
 
     def coeff(self, k, t):
-        return lib().orc_coeff_eval(self._h, k, float(t))
+        return self._L.orc_coeff_eval(self._h, k, float(t))
 
     def apply_term(self, k, x):
         x = np.ascontiguousarray(x, dtype=np.complex128)
         y = np.zeros_like(x)
-        _check(lib().orc_apply_term(self._h, k, _ptr(x), _ptr(y)), "apply_term")
+        _check(self._L.orc_apply_term(self._h, k, _ptr(x), _ptr(y)), "apply_term")
         return y
 
     def expv(self, beta, v, stats: Stats | None = None):
         beta = np.ascontiguousarray(beta, dtype=np.float64)
         out = np.array(v, dtype=np.complex128, copy=True, order="C")
         st = stats._s if stats else None
-        _check(lib().orc_expv(self._h, _ptr(beta), _ptr(out), C.byref(st) if st else None), "expv")
+        _check(self._L.orc_expv(self._h, _ptr(beta), _ptr(out), C.byref(st) if st else None), "expv")
         return out
 
     def propagate(self, psi, t0, h, nsteps, variant="CF4", stats: Stats | None = None):
         out = np.array(psi, dtype=np.complex128, copy=True, order="C")
         st = stats._s if stats else None
         code = VARIANTS[variant] if isinstance(variant, str) else int(variant)
-        _check(lib().orc_propagate(self._h, _ptr(out), float(t0), float(h), int(nsteps), code,
+        _check(self._L.orc_propagate(self._h, _ptr(out), float(t0), float(h), int(nsteps), code,
                                    C.byref(st) if st else None), "propagate")
         return out
 
     def generator_interval(self, variant, tn, h):
         """Spectral enclosure of the generator K of one M4 or M6 step of size h from tn."""
         a, b = C.c_double(), C.c_double()
-        _check(lib().orc_generator_interval(self._h, VARIANTS[variant], float(tn), float(h), C.byref(a), C.byref(b)),
+        _check(self._L.orc_generator_interval(self._h, VARIANTS[variant], float(tn), float(h), C.byref(a), C.byref(b)),
                "generator_interval")
         return a.value, b.value
 
@@ -295,7 +306,7 @@ class Problem:
         beta = np.ascontiguousarray(beta, dtype=np.float64)
         v = np.ascontiguousarray(v, dtype=np.complex128)
         a, b = np.zeros_like(v), np.zeros_like(v)
-        _check(lib().orc_frechet_expv(self._h, _ptr(beta), int(kd), _ptr(v), _ptr(a), _ptr(b), None), "frechet_expv")
+        _check(self._L.orc_frechet_expv(self._h, _ptr(beta), int(kd), _ptr(v), _ptr(a), _ptr(b), None), "frechet_expv")
         return a, b
 
     def adjoint_grad(self, psi0, phi, t0, h, nsteps, variant="CF4", kd=1):
@@ -306,6 +317,6 @@ class Problem:
         grad = np.zeros(ng)
         F = C.c_double()
         code = VARIANTS[variant] if isinstance(variant, str) else int(variant)
-        _check(lib().orc_adjoint_grad(self._h, _ptr(psi0), _ptr(phi), float(t0), float(h), int(nsteps), code, int(kd),
+        _check(self._L.orc_adjoint_grad(self._h, _ptr(psi0), _ptr(phi), float(t0), float(h), int(nsteps), code, int(kd),
                                       C.byref(F), _ptr(grad)), "adjoint_grad")
         return F.value, grad

@@ -30,6 +30,14 @@
  *    B_1 + B_3/12 is the 3-point Gauss rule h(5 A_1 + 8 A_2 + 5 A_3)/18).
  *    Its nested commutators add [-r, r], r a bound of |(i/240)[U, V]| from the
  *    half-widths of the terms' enclosures (see gen_interval).
+ *
+ * Threads.  Built without OpenMP (the checker) every loop runs in order on one
+ * thread.  The `#pragma omp parallel for` lines mark only the row loop of a term
+ * product and element-wise vector updates; a separate -fopenmp build, used only
+ * to time the CPU baseline on all host cores, spreads those loops over threads.
+ * Each entry is still computed by one thread with the same operations in the
+ * same order, and every reduction (norms, inner products) stays serial, so both
+ * builds give identical bits.
  */
 #include "magnus_oracle.h"
 
@@ -566,6 +574,7 @@ int orc_apply_term(const orc_problem *p, int k, const double complex *x, double 
   if (!p || k < 0 || k >= p->nterms || !p->term[k].set) return ORC_EINVAL;
   const orc_term *t = &p->term[k];
   const int64_t D = p->dim;
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < D; i++) {
     double complex acc = 0.0;
     if (t->kind == ORC_TERM_CSR) {
@@ -601,10 +610,12 @@ typedef struct {
 static void apply_combo(const orc_gen *g, const double *coef, const double complex *x, double complex *y,
                         double complex *tmp) {
   const int64_t D = g->p->dim;
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < D; i++) y[i] = 0.0;
   for (int k = 0; k < g->p->nterms; k++) {
     orc_apply_term(g->p, k, x, tmp);
     if (g->st) g->st->n_termapply++;
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < D; i++) y[i] += coef[k] * tmp[i];
   }
 }
@@ -707,6 +718,7 @@ static void gen_apply(orc_gen *g, const double complex *x, double complex *y) {
   apply_combo(g, g->f2, x, g->u2, g->t1);    /* u2 = H_2 x        */
   apply_combo(g, g->f2, g->u1, y, g->t1);    /* y  = H_2 (H_1 x)  */
   apply_combo(g, g->f1, g->u2, g->t2, g->t1);/* t2 = H_1 (H_2 x)  */
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < D; i++)
     y[i] = 0.5 * g->h * (g->u1[i] + g->u2[i]) - I * kappa * (y[i] - g->t2[i]);
 }
@@ -817,13 +829,16 @@ static int leja_core(orc_gen *g, double complex *v) {
   const double complex phase = cexp(-I * c / s);
   int rc = ORC_OK;
   for (int sub = 0; sub < s && rc == ORC_OK; sub++) {
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < D; i++) { w[i] = v[i]; pp[i] = d[0] * v[i]; }
     double e_prev = cabs(d[0]) * vnorm(w, D);
     int conv = 0, m = 0;
     for (int j = 1; j <= p->m_max; j++) {
       gen_apply(g, w, Kw);
       if (g->st) g->st->n_matvec++;
+#pragma omp parallel for schedule(static)
       for (int64_t i = 0; i < D; i++) w[i] = (Kw[i] - c * w[i]) / gamma - p->xi[j - 1] * w[i];
+#pragma omp parallel for schedule(static)
       for (int64_t i = 0; i < D; i++) pp[i] += d[j] * w[i];
       double e = cabs(d[j]) * vnorm(w, D);
       double pn = vnorm(pp, D);
@@ -837,6 +852,7 @@ static int leja_core(orc_gen *g, double complex *v) {
       if (m > g->st->max_m) g->st->max_m = m;
       if (g->st->m_log && g->st->n_substeps <= g->st->m_log_cap) g->st->m_log[g->st->n_substeps - 1] = m;
     }
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < D; i++) v[i] = phase * pp[i];
   }
   free(d); free(w); free(Kw); free(pp);

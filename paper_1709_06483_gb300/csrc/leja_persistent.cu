@@ -24,11 +24,13 @@
 // loads; only the immutable matrices use the read-only path.
 #include <math.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "magnus_internal.cuh"
 #include "persist_common.cuh"
 #include "rows.cuh"
+#include "csr_stage.cuh"
 
 namespace mg {
 
@@ -68,8 +70,13 @@ __device__ __forceinline__ double2 scal2(double s, double2 a) { return make_doub
 // extra code does not weigh on the register budget of the other methods).  ZF: the instantiations
 // with fixed-point sums and products (options.fixed_sums): 1 for linear generators (M2, Cf4, Cf4:3),
 // which carries only that path, 2 for M4 (its two phases on fixed-point copies of w and of u_k).
-template <int FAM, bool HM6, int ZF>
-__global__ void __launch_bounds__(kBlock, (min_blocks<FAM, HM6, ZF>())) k_magnus_persistent(PersistArgs a) {
+// STG: the fixed-point CSR instantiation whose rows read the matrix from shared memory, staged per
+// warp tile by the TMA bulk engine (csr_stage.cuh); one CTA of 8 warps per SM holds the slots.
+template <int FAM, bool HM6, int ZF, bool STG = false>
+__global__ void __launch_bounds__(kBlock, (STG ? 1 : min_blocks<FAM, HM6, ZF>())) k_magnus_persistent(PersistArgs a) {
+  static_assert(!STG || (FAM == FAM_CSR && ZF == 1 && !HM6), "staged rows: fixed-point CSR linear generators");
+  extern __shared__ __align__(128) unsigned char s_dyn[];
+  __shared__ __align__(8) uint64_t s_sbar[STG ? 2 * stage::kWarps : 1];
   __shared__ Term sT[kMaxTerms];
   __shared__ ExpRec sR;
   __shared__ double s_jb[kMaxSpins], s_j2[kMaxSpins];
@@ -179,6 +186,14 @@ __global__ void __launch_bounds__(kBlock, (min_blocks<FAM, HM6, ZF>())) k_magnus
   auto fail = [&](int status) {
     if (tid == 0) atomicCAS(&a.counters->status, 0, status);
   };
+  // staged rows: the warp's copy pipeline (its copies run across Leja iterations)
+  stage::Pipe P{};
+  if constexpr (STG) stage::init(P, s_dyn, s_sbar, warp, lane, lo, hi);
+  // leave the kernel: report the status and wait for the copies still in flight
+  auto bail = [&](int status) {
+    fail(status);
+    if constexpr (STG) stage::drain(P, a.spin_limit_ns);
+  };
 
   // ||psi|| and the largest component of every vector
   {
@@ -193,7 +208,7 @@ __global__ void __launch_bounds__(kBlock, (min_blocks<FAM, HM6, ZF>())) k_magnus
     // testing hook: CTA 0 leaves before its first barrier (a participant that never arrives), so
     // that every other CTA's bounded wait runs out
     if (a.skip_arrival && b == 0) return;
-    if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { fail(MAGNUS_ETIMEOUT); return; }
+    if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { bail(MAGNUS_ETIMEOUT); return; }
     if (warp == 0)
       for (int v = 0; v < nv; v++) {
         double t0, t1, m0;
@@ -220,7 +235,7 @@ __global__ void __launch_bounds__(kBlock, (min_blocks<FAM, HM6, ZF>())) k_magnus
     constexpr bool zf = ZF != 0 && FAM != FAM_GENERIC;
     // the host launches ZF = 1 for linear generators and ZF = 2 for M4 (whose records may be linear)
     if ((ZF == 1 && R.mode != MODE_LINEAR) || (ZF == 2 && R.mode != MODE_LINEAR && R.mode != MODE_M4)) {
-      fail(MAGNUS_EINVAL);
+      bail(MAGNUS_EINVAL);
       return;
     }
     // sum_k |bg_k| ||H_k||_inf (+ the M4 commutator's sum_{k<l} |kg| 2 ||H_k||_inf ||H_l||_inf): with
@@ -251,7 +266,7 @@ __global__ void __launch_bounds__(kBlock, (min_blocks<FAM, HM6, ZF>())) k_magnus
     if (!(R.gamma > 0.0)) {  // scalar generator: a phase
       const double2 ph = d[0];
       for (int64_t r = lo + tid; r < hi; r += blockDim.x) nxt[base + r] = cmul(ph, cur[base + r]);
-      if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { fail(MAGNUS_ETIMEOUT); return; }
+      if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { bail(MAGNUS_ETIMEOUT); return; }
       if (tid < nv) s_vm[tid] *= sqrt(cabs2(ph)) * (1.0 + 0x1p-40);
       double2 *tmp = cur; cur = nxt; nxt = tmp;
       if (b == 0 && tid == 0) a.counters->n_exp++;
@@ -269,7 +284,7 @@ __global__ void __launch_bounds__(kBlock, (min_blocks<FAM, HM6, ZF>())) k_magnus
       if (zf) {        // Z copy of the substep input
         zs_src = fix_scale(s_vm[vec], a.zhb);
         for (int64_t r = lo + tid; r < hi; r += blockDim.x) a.zc[base + r] = fix2(cur[base + r], zs_src);
-        if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { fail(MAGNUS_ETIMEOUT); return; }
+        if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { bail(MAGNUS_ETIMEOUT); return; }
       }
       bool done = false;
       int j;
@@ -284,7 +299,7 @@ __global__ void __launch_bounds__(kBlock, (min_blocks<FAM, HM6, ZF>())) k_magnus
           if (mine)
             for (int64_t r = lo + tid; r < hi; r += blockDim.x)
               for (int k = 0; k < nt; k++) a.u[((size_t)k * nv) * D + base + r] = Op<FAM>::term(cx, k, src + base, r);
-          if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { fail(MAGNUS_ETIMEOUT); return; }
+          if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { bail(MAGNUS_ETIMEOUT); return; }
         }
         // fixed-point M4, phase 1: u_k = H_k w from the copy of w, and the copy of u_k, scaled from
         // |u_k| <= ||H_k||_inf max|w| (x2 for complex terms)
@@ -302,7 +317,7 @@ __global__ void __launch_bounds__(kBlock, (min_blocks<FAM, HM6, ZF>())) k_magnus
                   a.u[((size_t)k * nv) * D + base + r] = hk;
                   a.zu[((size_t)k * nv) * D + base + r] = fix2(hk, zs_u[k]);
                 }
-            if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { fail(MAGNUS_ETIMEOUT); return; }
+            if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { bail(MAGNUS_ETIMEOUT); return; }
           }
         }
         // Method M6: K w = P w + R w / 12 + (i/240) (U (V w) - V (U w)) with
@@ -329,7 +344,7 @@ __global__ void __launch_bounds__(kBlock, (min_blocks<FAM, HM6, ZF>())) k_magnus
               V6(S_QW)[r] = lc(Q6);
               V6(S_RW)[r] = lc(R6);
             }
-          if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { fail(MAGNUS_ETIMEOUT); return; }
+          if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { bail(MAGNUS_ETIMEOUT); return; }
           if (mine)  // pass 2: P(Q w), Q(P w), R(P w), P(P w), P(R w)
             for (int64_t r = lo + tid; r < hi; r += blockDim.x) {
               terms_of(V6(S_QW), r);
@@ -341,7 +356,7 @@ __global__ void __launch_bounds__(kBlock, (min_blocks<FAM, HM6, ZF>())) k_magnus
               terms_of(V6(S_RW), r);
               V6(S_PRW)[r] = lc(P6);
             }
-          if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { fail(MAGNUS_ETIMEOUT); return; }
+          if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { bail(MAGNUS_ETIMEOUT); return; }
           if (mine)  // pass 3: u = U w, v = V w
             for (int64_t r = lo + tid; r < hi; r += blockDim.x) {
               terms_of(V6(S_PQW), r);
@@ -360,7 +375,7 @@ __global__ void __launch_bounds__(kBlock, (min_blocks<FAM, HM6, ZF>())) k_magnus
               V6(S_U)[r] = uw;
               V6(S_V)[r] = vw;
             }
-          if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { fail(MAGNUS_ETIMEOUT); return; }
+          if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { bail(MAGNUS_ETIMEOUT); return; }
           if (mine)  // pass 4: P u, Q u, R u, P v, Q v, R v
             for (int64_t r = lo + tid; r < hi; r += blockDim.x) {
               terms_of(V6(S_U), r);
@@ -372,7 +387,7 @@ __global__ void __launch_bounds__(kBlock, (min_blocks<FAM, HM6, ZF>())) k_magnus
               V6(S_QV)[r] = lc(Q6);
               V6(S_RV)[r] = lc(R6);
             }
-          if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { fail(MAGNUS_ETIMEOUT); return; }
+          if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { bail(MAGNUS_ETIMEOUT); return; }
           if (mine)  // pass 5: P(Q u), Q(P u), R(P u), P(P u), P(R u), P(Q v), Q(P v)
             for (int64_t r = lo + tid; r < hi; r += blockDim.x) {
               terms_of(V6(S_QU), r);
@@ -388,7 +403,7 @@ __global__ void __launch_bounds__(kBlock, (min_blocks<FAM, HM6, ZF>())) k_magnus
               terms_of(V6(S_PV), r);
               V6(S_QPV)[r] = lc(Q6);
             }
-          if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { fail(MAGNUS_ETIMEOUT); return; }
+          if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { bail(MAGNUS_ETIMEOUT); return; }
         }
         double sw = 0.0, sp = 0.0;
         unsigned mw = 0, mp = 0;
@@ -439,7 +454,123 @@ __global__ void __launch_bounds__(kBlock, (min_blocks<FAM, HM6, ZF>())) k_magnus
               mp = max(mp, abshi(pr));
             }
           };
-          if (j == 1) rows_z(std::true_type{}); else rows_z(std::false_type{});
+          // the same rows, tile by tile, with the matrix runs read from the warp's shared-memory
+          // slots (csr_stage.cuh); every term of this instantiation is a pattern or a product term
+          auto rows_staged = [&](auto first) {
+            using namespace stage;
+            if (!P.primed) {  // first pass: the row data of tile 0 and the copies of the first two tiles
+              P.primed = true;
+              if (P.ntiles > 0) {
+                int64_t ra, rb;
+                tile_rows(P, lo, hi, 0, ra, rb);
+                load_rowdata(P, sT, nt, ra + lane, rb);
+                if (lane == 0) {
+                  issue_tile(P, sT, nt, lo, hi, 0);
+                  issue_tile(P, sT, nt, lo, hi, 1);
+                }
+                P.issued = 2;
+                __syncwarp();
+              }
+            }
+            for (int jt = 0; jt < P.ntiles; jt++) {
+              const long long n = P.consumed;
+              int64_t ra, rb;
+              tile_rows(P, lo, hi, n, ra, rb);
+              const int64_t r = ra + lane;
+              const bool valid = r < rb;
+              int64_t e0[kMaxTerms], e1[kMaxTerms];
+              int fe[kMaxTerms];
+#pragma unroll
+              for (int k = 0; k < kMaxTerms; k++) {
+                e0[k] = P.ne0[k];
+                e1[k] = P.ne1[k];
+                fe[k] = P.nfe[k];
+              }
+              {  // row data of the next tile (the first tile of the next pass after the last)
+                int64_t na, nb;
+                tile_rows(P, lo, hi, n + 1, na, nb);
+                load_rowdata(P, sT, nt, na + lane, nb);
+              }
+              // lane 0: the runs of consumption n + 2, copied once this tile is done
+              int64_t q0[kMaxTerms], q1[kMaxTerms];
+              if (lane == 0) tile_spans(P, sT, nt, lo, hi, n + 2, q0, q1);
+              const double2 wr = valid ? ldv(src + base + r) : make_double2(0.0, 0.0);
+              double2 pold = make_double2(0.0, 0.0);
+              if constexpr (!decltype(first)::value) pold = valid ? nxt[base + r] : pold;
+              // the tile's runs: lane 0 holds the first row's start, the last row's lane the end
+              const int lastl = (int)(rb - ra) - 1;
+              int64_t t0[kMaxTerms], t1[kMaxTerms];
+#pragma unroll
+              for (int k = 0; k < kMaxTerms; k++) {
+                t0[k] = __shfl_sync(kFull, e0[k], 0);
+                t1[k] = __shfl_sync(kFull, e1[k], lastl);
+              }
+              Lay L;
+              layout(sT, nt, t0, t1, L);
+              const int sl = (int)(n & 1);
+              if (!wait_slot(P.bar + sl, (uint32_t)((n >> 1) & 1), a.spin_limit_ns)) {
+                // the copy did not arrive: report it; every block leaves at the next barrier
+                if (lane == 0) {
+                  atomicCAS(&a.counters->status, 0, MAGNUS_ETIMEOUT);
+                  atomicExch(&a.bar->error, 1);
+                }
+                break;
+              }
+              const unsigned char *slot = P.slot0 + (size_t)sl * kSlotBytes;
+              double2 y = make_double2(0.0, 0.0);
+              if (valid) {
+#pragma unroll
+                for (int k = 0; k < kMaxTerms; k++) {
+                  if (k >= nt) continue;
+                  const Term &t = sT[k];
+                  const int len = (int)(e1[k] - e0[k]);
+                  longlong2 acc;
+                  if (L.fits) {
+                    const int32_t *cs = reinterpret_cast<const int32_t *>(slot + L.off[2 * k] + (e0[k] * 4 - L.b0[2 * k]));
+                    if (t.pattern) {
+                      acc = zsum_smem(cs, len, zsrc, t.plen != 0 && (t.plen & 3) == 0);
+                    } else {
+                      const long long *vs = reinterpret_cast<const long long *>(
+                          slot + L.off[2 * k + 1] + (e0[k] * 8 - L.b0[2 * k + 1]));
+                      acc = zprod_smem(cs, vs, len, zsrc);
+                    }
+                  } else if (t.pattern) {
+                    acc = csr_row_zsum(t, zsrc, r);
+                  } else {
+                    int fe2;
+                    acc = csr_row_zprod_w(t, zsrc, r, fe2);
+                  }
+                  y = t.pattern ? rfma(s_wz[k], unfix2(acc, zs_src), y) : rfma(R.bg[k], unfix2(acc, zs_src - fe[k] - 2), y);
+                }
+                y = rfma(-shift, wr, y);
+              }
+              // the slot is free again: copy the runs of consumption n + 2 into it
+              P.consumed = n + 1;
+              __syncwarp();
+              if (lane == 0) {
+                fence_proxy_async();
+                issue_tile(P, sT, nt, n + 2, q0, q1);
+              }
+              P.issued = n + 3;
+              if (valid) {
+                dst[base + r] = y;
+                zdst[r] = fix2(y, zs_dst);
+                double2 pr;
+                if constexpr (decltype(first)::value) pr = cmul(d0, wr); else pr = pold;
+                pr = cfma(dj, y, pr);
+                nxt[base + r] = pr;
+                sw = fma(y.x, y.x, fma(y.y, y.y, sw));
+                sp = fma(pr.x, pr.x, fma(pr.y, pr.y, sp));
+                mw = max(mw, abshi(y));
+                mp = max(mp, abshi(pr));
+              }
+            }
+          };
+          if constexpr (STG) {
+            if (j == 1) rows_staged(std::true_type{}); else rows_staged(std::false_type{});
+          } else {
+            if (j == 1) rows_z(std::true_type{}); else rows_z(std::false_type{});
+          }
          }
         } else if (mine) {
           for (int64_t r = lo + tid; r < hi; r += blockDim.x) {
@@ -497,7 +628,10 @@ __global__ void __launch_bounds__(kBlock, (min_blocks<FAM, HM6, ZF>())) k_magnus
           }
         }
         block_reduce_store(sw, sp, mw, mp);
-        if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { fail(MAGNUS_ETIMEOUT); return; }
+        if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { bail(MAGNUS_ETIMEOUT); return; }
+        if constexpr (STG) {  // a staged copy that did not arrive (its block may have arrived last)
+          if (*(volatile int *)&a.bar->error) { bail(MAGNUS_ETIMEOUT); return; }
+        }
         zs_src = zs_dst;
         if (warp == 0) {
           int any = 0, bad = 0;
@@ -525,10 +659,10 @@ __global__ void __launch_bounds__(kBlock, (min_blocks<FAM, HM6, ZF>())) k_magnus
         }
         __syncthreads();
         it++;
-        if (s_flag == 2) { fail(MAGNUS_ENONFINITE); return; }
+        if (s_flag == 2) { bail(MAGNUS_ENONFINITE); return; }
         if (s_flag == 1) { done = true; break; }
       }
-      if (!done) { fail(MAGNUS_ENOCONV); return; }
+      if (!done) { bail(MAGNUS_ENOCONV); return; }
       if (tid < nv) {
         s_vn[tid] = s_pn[tid];
         s_vm[tid] = s_pm[tid];
@@ -550,11 +684,13 @@ __global__ void __launch_bounds__(kBlock, (min_blocks<FAM, HM6, ZF>())) k_magnus
     }
     if (b == 0 && tid == 0) a.counters->n_exp++;
   }
+  if constexpr (STG) stage::drain(P, a.spin_limit_ns);
   if (cur != a.psi)
     for (int64_t r = lo + tid; r < hi; r += blockDim.x) a.psi[base + r] = cur[base + r];
 }
 
-const void *kernel_for(int fam, bool m6, int zf) {
+const void *kernel_for(int fam, bool m6, int zf, bool stg = false) {
+  if (stg && !m6 && zf == 1 && fam == FAM_CSR) return (const void *)k_magnus_persistent<FAM_CSR, false, 1, true>;
   if (m6) {
     switch (fam) {
       case FAM_CSR: return (const void *)k_magnus_persistent<FAM_CSR, true, 0>;
@@ -578,16 +714,58 @@ const void *kernel_for(int fam, bool m6, int zf) {
 int persistent_block_size() { return kBlock; }
 
 // Resident CTAs per SM of the instantiation for this family (method M6, fixed-point linear
-// generators or the rest): the largest cooperative grid of that launch.
-cudaError_t persistent_max_blocks_per_sm(int fam, bool m6, int zf, int *n) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, kernel_for(fam, m6, zf), kBlock, 0);
+// generators, their staged-rows variant, or the rest): the largest cooperative grid of that launch.
+cudaError_t persistent_max_blocks_per_sm(int fam, bool m6, int zf, int *n, bool stg) {
+  const void *k = kernel_for(fam, m6, zf, stg);
+  const size_t dyn = (stg && !m6 && zf == 1 && fam == FAM_CSR) ? stage::kSmemBytes : 0;
+  if (dyn) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k, kBlock, dyn);
 }
 
 cudaError_t launch_persistent(const PersistArgs &a, int grid, int block, bool m6, cudaStream_t st) {
   PersistArgs copy = a;
   void *args[] = {&copy};
-  return cudaLaunchCooperativeKernel(kernel_for(a.fam, m6, persistent_fixed_kernel(a, m6)), dim3(grid), dim3(block),
-                                     args, 0, st);
+  const int zf = persistent_fixed_kernel(a, m6);
+  const bool stg = a.stg && !m6 && zf == 1 && a.fam == FAM_CSR;
+  return cudaLaunchCooperativeKernel(kernel_for(a.fam, m6, zf, stg), dim3(grid), dim3(block), args,
+                                     stg ? stage::kSmemBytes : 0, st);
+}
+
+size_t persistent_stage_smem_bytes() { return stage::kSmemBytes; }
+
+namespace {
+__global__ void k_stage_misfits(const Term *Tg, int nt, int64_t dim, unsigned long long *count) {
+  __shared__ Term sT[kMaxTerms];
+  for (int i = threadIdx.x; i < nt * (int)sizeof(Term) / 4; i += blockDim.x)
+    reinterpret_cast<int *>(sT)[i] = reinterpret_cast<const int *>(Tg)[i];
+  __syncthreads();
+  const int64_t ntile = (dim + stage::kTile - 1) / stage::kTile;
+  unsigned long long mine = 0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ntile; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t ra = t * stage::kTile, rb = min(dim, ra + stage::kTile);
+    int64_t e0[kMaxTerms], e1[kMaxTerms];
+#pragma unroll
+    for (int k = 0; k < kMaxTerms; k++) {
+      e0[k] = e1[k] = 0;
+      if (k < nt) stage::term_span(sT[k], ra, rb, e0[k], e1[k]);
+    }
+    stage::Lay L;
+    stage::layout(sT, nt, e0, e1, L);
+    mine += L.fits ? 0 : 1;
+  }
+  for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(kFull, mine, o);
+  if ((threadIdx.x & 31) == 0 && mine) atomicAdd(count, mine);
+}
+}  // namespace
+
+cudaError_t launch_stage_misfits(const Term *T, int nt, int64_t dim, unsigned long long *count, cudaStream_t st) {
+  const int64_t ntile = (dim + stage::kTile - 1) / stage::kTile;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(1024, (ntile + 255) / 256));
+  k_stage_misfits<<<grid, 256, 0, st>>>(T, nt, dim, count);
+  return cudaGetLastError();
 }
 
 }  // namespace mg

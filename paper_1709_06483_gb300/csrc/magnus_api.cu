@@ -22,6 +22,8 @@ struct magnus_plan_s {
   int max_blocks_m6 = 0;                 // its M6 instantiation
   int max_blocks_zf = 0;                 // its instantiation with fixed-point sums and products
   int max_blocks_zf4 = 0;                // and that of fixed-point M4
+  int max_blocks_stg = 0;                // and that of the staged-rows fixed-point CSR instantiation
+  bool staged = false;                   // fixed-point CSR linear generators read staged rows
   cudaStream_t stream = nullptr;
   int64_t dim = 0;
   int nterms = 0;
@@ -186,8 +188,10 @@ long long spin_limit(magnus_plan_t p) {
 }
 
 // grid: nvec * gv blocks, all co-resident (cooperative launch)
-void choose_grid(magnus_plan_t p, int *grid, int *gv, bool m6 = false, int zf = 0) {
-  const int per_sm = m6 ? p->max_blocks_m6 : (zf == 2 ? p->max_blocks_zf4 : (zf == 1 ? p->max_blocks_zf : p->max_blocks_per_sm));
+void choose_grid(magnus_plan_t p, int *grid, int *gv, bool m6 = false, int zf = 0, bool stg = false) {
+  const int per_sm = m6 ? p->max_blocks_m6
+                        : (zf == 2 ? p->max_blocks_zf4
+                                   : (zf == 1 ? (stg ? p->max_blocks_stg : p->max_blocks_zf) : p->max_blocks_per_sm));
   const int maxg = p->num_sms * std::max(1, per_sm);
   const int nv = p->opt.nvec;
   int per_vec = std::max(1, maxg / nv);
@@ -214,7 +218,7 @@ magnus_status run_persistent(magnus_plan_t p, void *psi, int64_t nexp, magnus_st
     gv = grid;
     need = (size_t)4 * grid * p->opt.nvec + (size_t)4 * p->opt.nvec;
   } else {
-    choose_grid(p, &grid, &gv, m6, (p->zc != nullptr && !m6) ? (m4 ? 2 : 1) : 0);
+    choose_grid(p, &grid, &gv, m6, (p->zc != nullptr && !m6) ? (m4 ? 2 : 1) : 0, p->staged && !m6 && !m4);
     need = (size_t)8 * grid;  // two slots x grid x (two sums, two maxima)
   }
   if ((int64_t)need > p->partials_cap) {
@@ -319,6 +323,7 @@ magnus_status run_persistent(magnus_plan_t p, void *psi, int64_t nexp, magnus_st
   a.zw1 = p->zw1;
   a.zhb = p->zhb;
   a.zreal = p->zreal;
+  a.stg = p->staged && a.zfix == 1 && p->fam == FAM_CSR;
   CUDA_TRY(p, cudaEventRecord(p->ev0, p->stream));
   if (p->fam == FAM_DENSE)
     CUDA_TRY(p, launch_dense_persistent(a, p->dense_real, grid, p->stream));
@@ -348,6 +353,7 @@ magnus_status run_persistent(magnus_plan_t p, void *psi, int64_t nexp, magnus_st
     stats->grid = grid;
     stats->block = p->fam == FAM_DENSE ? dense_block_size() : persistent_block_size();
     stats->fixed_sums = a.zfix != 0;
+    stats->staged = a.stg;
   }
   if (c.status != MAGNUS_OK) {
     const char *what = c.status == MAGNUS_ENOCONV      ? "Leja interpolation did not converge within m_max"
@@ -414,6 +420,8 @@ magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms
   if (!(o.tol_rel >= 0.0) || !(o.tol_abs >= 0.0) || !(o.tol_rel + o.tol_abs > 0.0))
     return set_err(nullptr, MAGNUS_EINVAL, "tolerances must be >= 0 and not both 0");
   if (o.fixed_sums != 0 && o.fixed_sums != 1) return set_err(nullptr, MAGNUS_EINVAL, "fixed_sums must be 0 or 1");
+  if (o.staged_rows < 0 || o.staged_rows > 2) return set_err(nullptr, MAGNUS_EINVAL, "staged_rows must be 0, 1 or 2");
+  if (o.plain_values != 0 && o.plain_values != 1) return set_err(nullptr, MAGNUS_EINVAL, "plain_values must be 0 or 1");
   if (!(o.rho_max > 0.0)) return set_err(nullptr, MAGNUS_EINVAL, "rho_max must be > 0");
   if (!(o.barrier_timeout_s >= 0.0) || o.barrier_timeout_s > 600.0)
     return set_err(nullptr, MAGNUS_EINVAL, "barrier_timeout_s must be in [0, 600]");
@@ -537,9 +545,11 @@ magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms
   PLAN_TRY(cudaMemcpyAsync(fh, flag, sizeof fh, cudaMemcpyDeviceToHost, p->stream));
   PLAN_TRY(cudaStreamSynchronize(p->stream));
   cudaFree(flag);
+  // (plain_values: complex-stored values stay complex, multiplied in place as complex128)
   for (int k = 0; k < nterms; k++)
     p->terms_host[k].real_valued =
-        (p->terms_host[k].kind == MAGNUS_TERM_CSR || p->terms_host[k].kind == MAGNUS_TERM_DENSE) && !fh[k];
+        (p->terms_host[k].kind == MAGNUS_TERM_CSR || p->terms_host[k].kind == MAGNUS_TERM_DENSE) && !fh[k] &&
+        !(o.plain_values && p->terms_host[k].rs == 2);
   for (int k = 0; k < nterms; k++)
     if (p->terms_host[k].kind == MAGNUS_TERM_DENSE && !p->terms_host[k].real_valued) p->dense_real = false;
   // real-valued CSR terms stored as complex128: a compact float64 copy of the real parts (the only
@@ -760,6 +770,30 @@ magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms
     }
   }
   PLAN_TRY(cudaMemcpyAsync(p->terms, p->terms_host, sizeof(Term) * nterms, cudaMemcpyHostToDevice, p->stream));
+  // staged rows: every term a pattern or a product term with 16-byte aligned arrays, and at most
+  // 1/64 of the 32-row tiles too large for a slot
+  constexpr int kStagedDefault = 2;  // staged_rows = 0: rows read from global memory
+  if (p->fam == FAM_CSR && p->zc && (o.staged_rows ? o.staged_rows : kStagedDefault) == 1) {
+    bool ok = true;
+    for (int k = 0; k < nterms; k++) {
+      const Term &T = p->terms_host[k];
+      ok &= (T.pattern || T.fval) && T.nnz > 0 && ((uintptr_t)T.col % 16) == 0 && ((uintptr_t)T.fval % 16) == 0;
+    }
+    if (ok) {
+      unsigned long long *cnt = nullptr, mis = 0;
+      PLAN_TRY(dalloc(&cnt, 1));
+      PLAN_TRY(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), p->stream));
+      PLAN_TRY(launch_stage_misfits(p->terms, nterms, dim, cnt, p->stream));
+      PLAN_TRY(cudaMemcpyAsync(&mis, cnt, sizeof mis, cudaMemcpyDeviceToHost, p->stream));
+      PLAN_TRY(cudaStreamSynchronize(p->stream));
+      cudaFree(cnt);
+      const unsigned long long ntile = (unsigned long long)((dim + 31) / 32);
+      if (mis * 64 <= ntile) {
+        PLAN_TRY(persistent_max_blocks_per_sm(FAM_CSR, false, 1, &p->max_blocks_stg, true));
+        p->staged = p->max_blocks_stg >= 1;
+      }
+    }
+  }
   PLAN_TRY(cudaStreamSynchronize(p->stream));
 #undef PLAN_TRY
   *out = p;

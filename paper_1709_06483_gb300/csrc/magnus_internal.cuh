@@ -221,6 +221,7 @@ struct PersistArgs {
   longlong2 *zc, *zw0, *zw1;
   longlong2 *zu;  // M4 in fixed point: copies of u_k, [nterms][nvec][dim]
   int zfix, zhb, zreal;  // zfix: 0 FP64, 1 fixed-point linear generators, 2 fixed-point M4
+  int stg;               // FAM_CSR, zfix 1: rows read from shared-memory slots the TMA fills per tile
 };
 enum { FAM_GENERIC = 0, FAM_CSR = 1, FAM_MF = 2, FAM_DENSE = 3 };
 // a.zfix selects the instantiation with fixed-point sums and products: 1 for linear generators
@@ -230,7 +231,12 @@ inline int persistent_fixed_kernel(const PersistArgs &a, bool m6) {
   return (!m6 && (a.fam == FAM_CSR || a.fam == FAM_MF)) ? a.zfix : 0;
 }
 int persistent_block_size();
-cudaError_t persistent_max_blocks_per_sm(int fam, bool m6, int zf, int *n);
+cudaError_t persistent_max_blocks_per_sm(int fam, bool m6, int zf, int *n, bool stg = false);
+// dynamic shared memory of the staged-rows instantiation (two slots per warp)
+size_t persistent_stage_smem_bytes();
+// count (device, zeroed by the caller) += the 32-row tiles (rows [32 t, 32 t + 32)) of the CSR terms
+// T[0..nt-1] whose runs do not fit one staging slot; such tiles are read from global memory
+cudaError_t launch_stage_misfits(const Term *T, int nt, int64_t dim, unsigned long long *count, cudaStream_t st);
 
 // Dense family (dense terms, optionally with a matrix-free field term): rows of all vectors per block.
 int dense_block_size();

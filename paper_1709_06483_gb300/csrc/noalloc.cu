@@ -7,8 +7,11 @@
 //
 // Host code must not use the name g_static_scratch as a device address (on the host it is only a
 // stand-in): the device address is fetched once per device with cudaGetSymbolAddress and passed to
-// the kernels.  The same kernels as the plan-based leja_expv run on that scratch, so both entry
-// points compute identical results.
+// the kernels.  The arithmetic is FP64 throughout: the terms go to the persistent kernel's generic
+// instantiation (k_magnus_persistent<FAM_GENERIC, no M6, FP64 sums>, at least 32 rows per CTA), not to the
+// matrix-free specialisation with diagonal tables and fixed-point sums that a plan chooses, so the
+// two entry points round differently and agree to the Leja tolerance (tested at 1e-10), not bit for
+// bit.
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -55,7 +58,7 @@ struct DeviceSetup {
   bool done = false;
   unsigned char *base = nullptr;  // device address of g_static_scratch on this device
   int num_sms = 0;
-  int blocks_per_sm = 0;
+  int blocks_per_sm = 0;          // co-resident CTAs per SM of the instantiation launched below
 };
 std::mutex g_setup_mutex;
 DeviceSetup g_setup[64];
@@ -105,7 +108,7 @@ extern "C" MAGNUS_API magnus_status magnus_expv_xxz_static(int32_t nspins, const
         return fail(MAGNUS_ECUDA, "magnus_expv_xxz_static: cudaGetSymbolAddress failed");
       unsigned char *base = (unsigned char *)ptr;
       if (cudaDeviceGetAttribute(&s.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-          persistent_max_blocks_per_sm(FAM_MF, false, 0, &s.blocks_per_sm) != cudaSuccess)
+          persistent_max_blocks_per_sm(FAM_GENERIC, false, 0, &s.blocks_per_sm) != cudaSuccess)
         return fail(MAGNUS_ECUDA, "magnus_expv_xxz_static: device query failed");
       if (launch_leja_points((double *)(base + kOffXi), kStaticMmax, (double *)(base + kOffCand),
                              (unsigned *)(base + kOffCounter), stream) != cudaSuccess ||
@@ -173,6 +176,7 @@ extern "C" MAGNUS_API magnus_status magnus_expv_xxz_static(int32_t nspins, const
     a.mlog = nullptr;
     a.mlog_cap = 0;
     a.spin_limit_ns = 4000000000LL;
+    a.fam = FAM_GENERIC;  // the instantiation whose occupancy sized the grid (zfix stays 0: FP64 sums)
     e = launch_persistent(a, grid, persistent_block_size(), false, stream);
   }
   Counters c{};

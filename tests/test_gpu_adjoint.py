@@ -107,3 +107,23 @@ def test_fidelity_autograd_function(mg):
         stepped = params + 0.05 * params.grad / params.grad.norm()
     F2 = mg.fidelity(plan, stepped, psi0, phit, 0.0, h, N, "CF4", kd=1, ckpt_every=5)
     assert F2.item() > F.item()
+
+
+def test_workload5_size_against_the_cpu_adjoint_every_entry(mg):
+    """16 spins (dim 65,536), the 32-mode sine drive of the control workload (T = 10), checkpoints
+    every 16 steps, but 48 Cf4 steps of 0.01 instead of 1000 so that the CPU adjoint finishes in
+    seconds: all 65 gradient entries (a0, 32 cosine, 32 sine amplitudes) and F against the FP64 CPU
+    adjoint, to 1e-8 relative to the largest entry.  GPU terms matrix-free (the control workload's),
+    the oracle's CSR."""
+    c = mi.workload5()
+    om, ck = c.drive_om, c.drive_as
+    n, N = c.nspins, 48
+    plan = mg.Plan(c.dim, [mg.XXZTerm(n, c.J, c.hz, c.delta), mg.FieldXTerm(n)],
+                   [mg.Drive.const(), mg.Drive(0.0, np.zeros(om.size), ck, om)], tol=1e-12)
+    F, grad, st = plan.adjoint_grad(cuda(c.psi0), cuda(c.phi), 0.0, c.h, N, "CF4", kd=1, ckpt_every=16)
+    P = oracle.Problem([oracle.xxz_csr(n, c.J, c.hz, c.delta), oracle.field_x_csr(n)],
+                       [oracle.Coeff.const(), oracle.Coeff(0.0, np.zeros(om.size), ck, om)], tol=1e-12)
+    Fr, gr = P.adjoint_grad(c.psi0, c.phi, 0.0, c.h, N, "CF4", kd=1)
+    assert grad.size == gr.size == 65
+    assert abs(F - Fr) <= 1e-10 * abs(Fr)
+    assert np.max(np.abs(grad - gr)) <= 1e-8 * np.max(np.abs(gr)), np.max(np.abs(grad - gr)) / np.max(np.abs(gr))

@@ -397,3 +397,105 @@ def test_apply_fixed_point_general_terms(mg):
         ref = sum(beta[k] * P.apply_term(k, x0[v]) for k in range(3))
         for fixed in (True, False):
             assert rel_scaled(ys[fixed][v], ref) < 1e-13, (fixed, v, rel_scaled(ys[fixed][v], ref))
+
+
+# ----------------------------------------------------------------- staged rows (shared-memory tiles)
+@pytest.mark.parametrize("nvec", [1, 3])
+def test_staged_rows_bit_identical_to_global_rows(mg, nvec):
+    """The staged rows (each warp's 32-row tiles copied into shared memory by the TMA bulk engine)
+    read the same entries as the rows read from global memory and sum them exactly in int64, so the
+    two plans agree bit for bit, and both match the oracle.  12-spin chain (dim 4096, 128 tiles),
+    CF4 and CF4:3."""
+    c = mi.xxz_chain(49, 12, 0.01, 12, nvec=nvec)
+    P = chain_problem(c)
+    for variant in ("CF4", "CF4_3"):
+        out = {}
+        for staged in (True, False):
+            plan = mg.Plan(c.dim, chain_terms(mg, c, "csr"), drives(mg, c), nvec=nvec, staged=staged)
+            psi = cuda(c.psi0)
+            st = plan.propagate(psi, 0.0, c.h, c.nsteps, variant, log_cap=1024)
+            assert st["staged"] == int(staged) and st["fixed_sums"] == 1
+            out[staged] = (psi.cpu().numpy(), st["m_log"])
+            plan.close()
+        assert np.array_equal(out[True][0], out[False][0])
+        assert np.array_equal(out[True][1], out[False][1])
+        psi0 = c.psi0.reshape(nvec, -1)
+        got = out[True][0].reshape(nvec, -1)
+        for v in range(nvec):
+            ref = P.propagate(psi0[v], 0.0, c.h, c.nsteps, variant)
+            assert rel(got[v], ref) < REL_TOL, (variant, v, rel(got[v], ref))
+
+
+def _banded_with_heavy_band(rng, D, band, w_heavy):
+    """Real symmetric banded matrix: half-bandwidth 2-6 per row, except rows [band, band + 32) with
+    half-bandwidth w_heavy (their tile and its neighbours' tiles hold hundreds of entries)."""
+    import scipy.sparse as sp
+    rr, cc = [], []
+    for r in range(D):
+        w = w_heavy if band <= r < band + 32 else int(rng.integers(2, 7))
+        c = np.arange(max(0, r - w), min(D, r + w + 1))
+        rr.append(np.full(c.size, r))
+        cc.append(c)
+    rr, cc = np.concatenate(rr), np.concatenate(cc)
+    A = sp.coo_matrix((rng.uniform(-1, 1, rr.size), (rr, cc)), shape=(D, D)).tocsr()
+    A = ((A + A.T) / 2).tocsr()
+    A.sort_indices()
+    return A.indptr.astype(np.int64), A.indices.astype(np.int32), A.data.astype(np.float64)
+
+
+def _tiles_too_large(rowptrs, slot=9472):
+    """32-row tiles whose runs (4 B per column, 8 B per mantissa of the first term, 16-byte blocks)
+    exceed one staging slot."""
+    D = rowptrs[0].size - 1
+    bad = 0
+    for t in range(0, D, 32):
+        tot = 0
+        for k, rp in enumerate(rowptrs):
+            e0, e1 = int(rp[t]), int(rp[min(D, t + 32)])
+            for es in ((4, 8) if k == 0 else (4,)):
+                tot += ((e1 * es + 15) // 16 * 16) - (e0 * es // 16 * 16)
+        bad += tot > slot
+    return bad
+
+
+def test_staged_rows_with_tiles_too_large_for_a_slot(mg):
+    """A real banded term with one band of 32 rows of 81 entries (its tile and the neighbouring tiles
+    do not fit a slot and are read from global memory inside the staged kernel) beside a pattern
+    term; dim 16384 (512 tiles, a few of them too large).  Bit-identical to the unstaged plan and
+    within 1e-10 of the oracle, with identical Leja degrees."""
+    rng = np.random.default_rng(50)
+    D = 16384
+    h1 = _banded_with_heavy_band(rng, D, 8000, 40)
+    # pattern term: the same banded structure at half-bandwidth 1-3, value 0.5, built sparsely
+    import scipy.sparse as sp
+    rr, cc = [], []
+    for r in range(D):
+        w = int(rng.integers(1, 4))
+        c = np.arange(max(0, r - w), min(D, r + w + 1))
+        rr.append(np.full(c.size, r))
+        cc.append(c)
+    rr, cc = np.concatenate(rr), np.concatenate(cc)
+    B = sp.coo_matrix((np.ones(rr.size), (rr, cc)), shape=(D, D)).tocsr()
+    B = (B + B.T).tocsr()
+    B.data[:] = 0.5
+    B.sort_indices()
+    h2 = (B.indptr.astype(np.int64), B.indices.astype(np.int32), B.data.astype(np.float64))
+    bad = _tiles_too_large([h1[0], h2[0]])
+    assert 1 <= bad <= D // 32 // 64, bad
+    psi0 = mi.random_state(rng, D)
+    f = oracle.Coeff(0.3, [1.0], [], [2.5])
+    Pr = oracle.Problem([oracle.CSR(r, c, v.astype(np.complex128)) for r, c, v in (h1, h2)], [oracle.Coeff.const(), f])
+    ost = oracle.Stats(256)
+    ref = Pr.propagate(psi0, 0.0, 0.02, 6, "CF4", ost)
+    out = {}
+    for staged in (True, False):
+        terms = [mg.CSRTerm(cuda(r), cuda(c), cuda(v)) for r, c, v in (h1, h2)]
+        plan = mg.Plan(D, terms, [mg.Drive.const(), mg.Drive(0.3, [1.0], [], [2.5])], staged=staged)
+        psi = cuda(psi0)
+        st = plan.propagate(psi, 0.0, 0.02, 6, "CF4", log_cap=256)
+        assert st["staged"] == int(staged)
+        assert np.array_equal(st["m_log"], ost.m_log)
+        out[staged] = psi.cpu().numpy()
+        plan.close()
+    assert np.array_equal(out[True], out[False])
+    assert rel(out[True], ref) < REL_TOL

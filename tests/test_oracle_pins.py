@@ -570,3 +570,20 @@ def test_lanczos_interval_propagation_agrees_and_needs_fewer_matvecs():
         mv[iv] = st.n_matvec
     assert np.linalg.norm(out["gershgorin"] - out["lanczos"]) < 1e-11
     assert mv["lanczos"] < 0.95 * mv["gershgorin"], mv
+
+
+def test_openmp_build_gives_the_checkers_bits():
+    """The OpenMP build of the oracle (used only to time the CPU baseline on all host cores) spreads
+    element-wise loops over threads; each entry keeps its operations and their order, so the
+    propagation is bit-identical to the single-threaded checker's (Cf4 and M4, 10 spins)."""
+    import os
+    c = mi.xxz_chain(71, 10, 0.02, 10)
+    out = {}
+    for threaded in (False, True):
+        P = oracle.Problem([oracle.xxz_csr(c.nspins, c.J, c.hz, c.delta), oracle.field_x_csr(c.nspins)],
+                           [oracle.Coeff.const(), oracle.Coeff(c.drive_a0, c.drive_ac, c.drive_as, c.drive_om)],
+                           threaded=threaded)
+        out[threaded] = [P.propagate(c.psi0, 0.0, c.h, c.nsteps, v) for v in ("CF4", "M4")]
+    for a, b in zip(out[False], out[True]):
+        assert np.array_equal(a, b)
+    assert os.path.exists(oracle._LIB_OMP)
