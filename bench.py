@@ -40,6 +40,7 @@ METRIC = "Magnus steps/s and Leja matvec GB/s vs plain FP64 GPU path at ≤1e-8 
 SUMS_FIXED = ("exact int64 fixed point: the sum_i sx_i row sums and the H_s (or bond) products; FP64: "
               "the conversions back, the Leja update and the norms")
 HBM_PEAK_FALLBACK = 6800.0
+ROW_LAYOUT_NAMES = {0: None, 1: "staged", 2: "csr", 3: "sliced"}
 SMS, FP64_FMA_PER_CLK, SM_MAX_MHZ = 152, 2, 2070.0
 FP64_PEAK_TFLOPS = SMS * FP64_FMA_PER_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12  # 1.259 TFLOP/s derived
 
@@ -269,7 +270,7 @@ def xxz_roofline(c, storage, variant, nnz_terms, st, kms, traffic_key=None):
     return roof
 
 
-def measure_xxz(mg, c, terms, storage, variant, steps, warmup, repeats, interval="lanczos", fixed=True, staged=None,
+def measure_xxz(mg, c, terms, storage, variant, steps, warmup, repeats, interval="lanczos", fixed=True, rows="auto",
                 plain=False, world=1, local=0, keep_state=False, traffic_key=None):
     """Steps/s of magnus_propagate on chain c: `warmup` untimed steps, then `repeats` timed regions of
     exactly `steps` steps from the same psi0 and t0, each bracketed by a barrier and a device
@@ -278,7 +279,7 @@ def measure_xxz(mg, c, terms, storage, variant, steps, warmup, repeats, interval
     import torch
     stream = torch.cuda.current_stream()
     nnz_terms = tuple(t.col.numel() for t in terms) if storage.startswith("csr") else (0, 0)
-    plan = mg.Plan(c.dim, terms, drives(mg, c), interval=interval, fixed_sums=fixed, staged=staged,
+    plan = mg.Plan(c.dim, terms, drives(mg, c), interval=interval, fixed_sums=fixed, rows=rows,
                    plain_values=plain)
     psi0 = torch.from_numpy(c.psi0).cuda()
     psi = psi0.clone()
@@ -311,7 +312,7 @@ def measure_xxz(mg, c, terms, storage, variant, steps, warmup, repeats, interval
            "min": round(rates[0], 3), "max": round(rates[-1], 3), "repeats": len(ms), "steps": steps,
            "ms_per_step": round(ms[mid] / steps, 4), "leja_iterations": st["n_matvec"], "max_degree": st["max_m"],
            "us_per_leja_iteration": round(st["kernel_ms"] * 1e3 / max(1, st["n_matvec"]), 2),
-           "fixed_sums": st["fixed_sums"], "staged": st["staged"], "grid": st["grid"],
+           "fixed_sums": st["fixed_sums"], "row_layout": ROW_LAYOUT_NAMES.get(st["row_layout"]), "grid": st["grid"],
            "roofline": xxz_roofline(c, rkey, variant, nnz_terms, st, st["kernel_ms"], traffic_key),
            "clocks": clk.summary()}
     if keep_state:
@@ -341,10 +342,10 @@ def run_ours(args):
     nnz_terms = tuple(t.col.numel() for t in terms) if storage.startswith("csr") else (0, 0)
     nnz_total = sum(nnz_terms) if storage.startswith("csr") else None
     fixed = bool(args.fixed_sums)
-    staged = {0: None, 1: True, 2: False}[args.staged]
     head = measure_xxz(mg, c, terms, storage, variant, args.steps, args.warmup, args.repeats, args.interval, fixed,
-                       staged, False, world, local, keep_state=True)
-    key = f"wl2_{storage}_{variant}" + ("_fixed" if head["fixed_sums"] else "") + ("_staged" if head["staged"] else "")
+                       args.rows, False, world, local, keep_state=True)
+    key = f"wl2_{storage}_{variant}" + ("_fixed" if head["fixed_sums"] else "") + (
+        f"_{head['row_layout']}" if head["row_layout"] else "")
     head["roofline"]["traffic"] = (None if profiled_traffic(key) is None
                                    else int(profiled_traffic(key) * head["roofline"]["leja_iterations"]))
     plan, psi_head = head.pop("_plan"), head.pop("_psi")
@@ -404,7 +405,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": f"xxz_chain_20spins_{storage}_{variant.lower()}", "spins": c.nspins, "dim": c.dim,
                    "nnz": nnz_total, "h": c.h, "t0": c.t0, "variant": variant, "storage": storage,
-                   "interval": args.interval, "staged_rows": bool(head["staged"]),
+                   "interval": args.interval, "row_layout": head["row_layout"],
                    "sums": SUMS_FIXED if head["fixed_sums"] else "FP64",
                    "leja_tol": 1e-10, "l2": "inputs larger than L2: the 640 MB CSR is streamed every iteration"
                    if storage.startswith("csr") else "matrix-free; 4 state vectors of 16 MB stay L2-resident",
@@ -427,13 +428,13 @@ def run_ours(args):
         # memory), and the state error of the headline path against it
         try:
             plain = measure_xxz(mg, c, workload_terms(mg, c, "csr"), "csr", variant, args.steps, 1,
-                                min(3, args.repeats), "gershgorin", False, False, True, world, local,
+                                min(3, args.repeats), "gershgorin", False, "csr", True, world, local,
                                 keep_state=True, traffic_key=f"wl2_csr_plain_{variant}")
             plain.pop("_plan").close()
             pp = plain.pop("_psi")
             err = float(torch.linalg.norm(psi_head - pp) / torch.linalg.norm(pp))
             rig = measure_xxz(mg, c, terms, storage, variant, args.steps, 1, 1, "gershgorin", fixed,
-                              staged, False, world, local)
+                              args.rows, False, world, local)
             line["vs_plain_fp64"] = {
                 "plain_fp64": {k: plain[k] for k in ("steps_per_s", "min", "max", "repeats", "leja_iterations",
                                                      "us_per_leja_iteration", "roofline")},
@@ -460,7 +461,7 @@ def run_ours(args):
 # --------------------------------------------------------------------------- every workload
 def wl_xxz(mg, mi, c, storage, variant, steps, repeats, interval, local, label):
     terms = workload_terms(mg, c, storage)
-    r = measure_xxz(mg, c, terms, storage, variant, steps, 3, repeats, interval, True, None, False, 1, local)
+    r = measure_xxz(mg, c, terms, storage, variant, steps, 3, repeats, interval, True, "auto", False, 1, local)
     r["workload"] = label
     return r
 
@@ -993,9 +994,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--fixed-sums", type=int, choices=[0, 1], default=1,
                     help="xxz20: pattern-term sums in fixed point (1) or FP64 (0)")
-    ap.add_argument("--staged", type=int, choices=[0, 1, 2], default=0,
-                    help="xxz20 CSR in fixed point: 1 = matrix runs staged in shared memory per warp tile, "
-                         "2 = rows read from global memory, 0 = the library's choice")
+    ap.add_argument("--rows", choices=["auto", "sliced", "csr", "staged"], default="auto",
+                    help="layout of the fixed-point CSR rows (options.row_layout)")
     ap.add_argument("--repeats", type=int, default=5,
                     help="timed regions of --steps steps each (the value is their median)")
     ap.add_argument("--headline-only", action="store_true",

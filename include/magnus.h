@@ -162,20 +162,29 @@ typedef enum {
  *                     a converted result below 2^-1022 flushes to zero (FP64 would keep a
  *                     subnormal).  0 = FP64 throughout.  Not part of the paper, which computes in
  *                     FP64 only.
- *   staged_rows [0]: how the CSR rows of fixed-point plans (every term CSR, fixed_sums, every term
- *                     a pattern or a product term) read the matrix.  1 = staged: each warp's
- *                     32-row tiles have their columns and mantissas copied into shared memory two
- *                     tiles ahead by the TMA bulk engine (one CTA of 8 warps per SM); tiles whose
- *                     runs do not fit a 9,472-byte slot are read from global memory, and a plan
- *                     stages only if at most 1/64 of its tiles are such.  2 = rows read from global
- *                     memory (4 CTAs per SM).  0 = the library's choice (currently 2).  The integer
- *                     sums make both ways bit-identical.
+ *   row_layout [MAGNUS_ROWS_AUTO]: how the rows of fixed-point CSR plans (every term CSR, fixed_sums)
+ *                     read the pattern and product terms (plan-owned copies, same bytes per entry):
+ *                     MAGNUS_ROWS_SLICED (the default) -- per 32-row slice the first w entries of
+ *                     every row column-major (w = the slice's shortest row), ordered so that rows
+ *                     sharing a column offset read it at the same position, the rest row-major;
+ *                     MAGNUS_ROWS_CSR -- the CSR arrays as given; MAGNUS_ROWS_STAGED -- each warp's
+ *                     32-row tiles of the CSR arrays copied into shared memory two tiles ahead by the
+ *                     TMA bulk engine (one CTA of 8 warps per SM; tiles larger than a 9,472-byte slot
+ *                     read from global memory; used only if at most 1/64 of the tiles are such).  The
+ *                     integer row sums make every layout give the same bits.
  *   plain_values [0]: 1 = multiply complex-stored CSR and dense values in place as complex128 numbers
  *                     even when every imaginary part is zero (no real-valued specialisation, no
  *                     float64 copy, no pattern or fixed-point rows): the plain FP64 path of the paper,
  *                     kept as the baseline the faster paths are measured against.  Real storage
  *                     (MAGNUS_TERM_*_REAL) is unaffected.  _reserved must be 0.
  */
+typedef enum {
+  MAGNUS_ROWS_AUTO = 0,   /* the library's choice (MAGNUS_ROWS_SLICED) */
+  MAGNUS_ROWS_STAGED = 1,
+  MAGNUS_ROWS_CSR = 2,
+  MAGNUS_ROWS_SLICED = 3
+} magnus_row_layout;
+
 typedef struct {
   double tol_rel;
   double tol_abs;
@@ -188,7 +197,7 @@ typedef struct {
   int32_t test_skip_arrival;
   int32_t interval;
   int32_t fixed_sums;
-  int32_t staged_rows;
+  int32_t row_layout;
   int32_t plain_values;
   int32_t _reserved;
 } magnus_options;
@@ -206,7 +215,7 @@ typedef struct {
   int32_t grid;         /* CTAs of that launch                                */
   int32_t block;        /* threads per CTA                                    */
   int32_t fixed_sums;   /* 1 if the call's matvecs ran in fixed point (options.fixed_sums)      */
-  int32_t staged;       /* 1 if its CSR rows were read from shared-memory slots (unstaged_rows) */
+  int32_t row_layout;   /* the fixed-point CSR rows' layout (magnus_row_layout; 0: not such a call) */
 } magnus_stats;
 
 typedef struct magnus_plan_s *magnus_plan_t;

@@ -77,6 +77,7 @@ struct magnus_plan_s {
   double *rcopy[kMaxTerms] = {nullptr, nullptr, nullptr, nullptr};  // real parts of complex-stored real CSR terms
   long long *fval[kMaxTerms] = {nullptr, nullptr, nullptr, nullptr};  // fixed-point values of real CSR terms
   int16_t *fexp[kMaxTerms] = {nullptr, nullptr, nullptr, nullptr};    // and their row exponents
+  SlicedRows sliced[kMaxTerms];                                         // sliced rows of those terms
   unsigned long long rowmax[kMaxTerms] = {0, 0, 0, 0};                // longest row of each real CSR term
   int zhb = 0;
   bool zreal = true;
@@ -125,6 +126,7 @@ void free_plan(magnus_plan_t p) {
                   p->fval[3], p->fexp[0], p->fexp[1], p->fexp[2], p->fexp[3]};
   for (void *b : bufs)
     if (b) cudaFree(b);
+  for (int k = 0; k < kMaxTerms; k++) free_sliced_rows(&p->sliced[k]);
   if (p->ev0) cudaEventDestroy(p->ev0);
   if (p->ev1) cudaEventDestroy(p->ev1);
   delete p;
@@ -151,6 +153,15 @@ magnus_status ensure_m4_sliced(magnus_plan_t p) {
   CUDA_TRY(p, dalloc(&p->ex_sets, (size_t)128 * (3 + p->nterms)));
   p->m4_sliced_ready = true;
   return MAGNUS_OK;
+}
+
+// the layout the fixed-point CSR rows of a launch read (0: not a fixed-point CSR launch)
+int row_layout_of_call(magnus_plan_t p, const PersistArgs &a) {
+  if (!a.zfix || p->fam != FAM_CSR) return 0;
+  if (a.stg) return MAGNUS_ROWS_STAGED;
+  for (int k = 0; k < p->nterms; k++)
+    if (p->terms_host[k].hbase) return MAGNUS_ROWS_SLICED;
+  return MAGNUS_ROWS_CSR;
 }
 
 bool is_pow2_dim(int64_t dim, int nspins) {
@@ -353,7 +364,7 @@ magnus_status run_persistent(magnus_plan_t p, void *psi, int64_t nexp, magnus_st
     stats->grid = grid;
     stats->block = p->fam == FAM_DENSE ? dense_block_size() : persistent_block_size();
     stats->fixed_sums = a.zfix != 0;
-    stats->staged = a.stg;
+    stats->row_layout = row_layout_of_call(p, a);
   }
   if (c.status != MAGNUS_OK) {
     const char *what = c.status == MAGNUS_ENOCONV      ? "Leja interpolation did not converge within m_max"
@@ -420,7 +431,8 @@ magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms
   if (!(o.tol_rel >= 0.0) || !(o.tol_abs >= 0.0) || !(o.tol_rel + o.tol_abs > 0.0))
     return set_err(nullptr, MAGNUS_EINVAL, "tolerances must be >= 0 and not both 0");
   if (o.fixed_sums != 0 && o.fixed_sums != 1) return set_err(nullptr, MAGNUS_EINVAL, "fixed_sums must be 0 or 1");
-  if (o.staged_rows < 0 || o.staged_rows > 2) return set_err(nullptr, MAGNUS_EINVAL, "staged_rows must be 0, 1 or 2");
+  if (o.row_layout < MAGNUS_ROWS_AUTO || o.row_layout > MAGNUS_ROWS_SLICED)
+    return set_err(nullptr, MAGNUS_EINVAL, "row_layout must be MAGNUS_ROWS_AUTO, _STAGED, _CSR or _SLICED");
   if (o.plain_values != 0 && o.plain_values != 1) return set_err(nullptr, MAGNUS_EINVAL, "plain_values must be 0 or 1");
   if (!(o.rho_max > 0.0)) return set_err(nullptr, MAGNUS_EINVAL, "rho_max must be > 0");
   if (!(o.barrier_timeout_s >= 0.0) || o.barrier_timeout_s > 600.0)
@@ -772,8 +784,27 @@ magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms
   PLAN_TRY(cudaMemcpyAsync(p->terms, p->terms_host, sizeof(Term) * nterms, cudaMemcpyHostToDevice, p->stream));
   // staged rows: every term a pattern or a product term with 16-byte aligned arrays, and at most
   // 1/64 of the 32-row tiles too large for a slot
-  constexpr int kStagedDefault = 2;  // staged_rows = 0: rows read from global memory
-  if (p->fam == FAM_CSR && p->zc && (o.staged_rows ? o.staged_rows : kStagedDefault) == 1) {
+  // row layout of the fixed-point CSR rows: sliced by default (MAGNUS_ROWS_AUTO)
+  const int layout = o.row_layout == MAGNUS_ROWS_AUTO ? MAGNUS_ROWS_SLICED : o.row_layout;
+  if (p->fam == FAM_CSR && p->zc && layout == MAGNUS_ROWS_SLICED && dim <= ((int64_t)1 << 28)) {
+    bool changed = false;
+    for (int k = 0; k < nterms; k++) {
+      Term &T = p->terms_host[k];
+      if (!(T.pattern || T.fval) || T.nnz <= 0) continue;
+      PLAN_TRY(build_sliced_rows(T.rowptr, T.col, T.fval, dim, &p->sliced[k], p->stream));
+      const SlicedRows &S = p->sliced[k];
+      T.hbase = S.hbase;
+      T.hcol = S.hcol;
+      T.hval = S.hval;
+      T.tptr = S.tptr;
+      T.tcol = S.tcol;
+      T.tval = S.tval;
+      changed = true;
+    }
+    if (changed)
+      PLAN_TRY(cudaMemcpyAsync(p->terms, p->terms_host, sizeof(Term) * nterms, cudaMemcpyHostToDevice, p->stream));
+  }
+  if (p->fam == FAM_CSR && p->zc && layout == MAGNUS_ROWS_STAGED) {
     bool ok = true;
     for (int k = 0; k < nterms; k++) {
       const Term &T = p->terms_host[k];

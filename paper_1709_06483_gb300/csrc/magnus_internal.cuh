@@ -40,6 +40,19 @@ struct Term {
   // of row r as fval[e] = round(a_e 2^(62 - fexp[r])), with max_e |a_e| < 2^fexp[r]
   const long long *fval;
   const int16_t *fexp;
+  // sliced rows (pattern and product terms of fixed-point CSR plans; null: CSR rows): per 32-row
+  // slice s the first w_s entries of every row (w_s = the slice's shortest row) column-major,
+  // entry k of row 32 s + l at hbase[s] + 32 k + l of hcol (and hval, the mantissas), w_s =
+  // (hbase[s+1] - hbase[s]) / 32; the rest of each row (its tail) row-major at [tptr[r], tptr[r+1])
+  // of tcol / tval (tptr null: no row has a tail).  Within a row the entries are ordered by how
+  // many rows of the slice share their column offset col - r, so that entry k of the 32 rows
+  // gathers from one run of the vector where the matrix allows.
+  const int64_t *hbase;
+  const int32_t *hcol;
+  const long long *hval;
+  const int64_t *tptr;
+  const int32_t *tcol;
+  const long long *tval;
 };
 
 // Public term (magnus_term) -> storage fields of the internal Term: real-storage kinds become CSR /
@@ -234,6 +247,22 @@ int persistent_block_size();
 cudaError_t persistent_max_blocks_per_sm(int fam, bool m6, int zf, int *n, bool stg = false);
 // dynamic shared memory of the staged-rows instantiation (two slots per warp)
 size_t persistent_stage_smem_bytes();
+// Sliced rows of a CSR term (rowptr, col, and for a product term its mantissas fval; fval null for a
+// pattern term), dim rows: fills hbase [ceil(dim/32)+1], hcol/hval [32 sum_s w_s] and, if some row
+// has a tail, tptr [dim+1], tcol/tval (allocated here with cudaMalloc; *ntail = tail entries).
+// Rows of a slice longer than 24 entries keep their CSR order.
+struct SlicedRows {
+  int64_t *hbase = nullptr;
+  int32_t *hcol = nullptr;
+  long long *hval = nullptr;
+  int64_t *tptr = nullptr;
+  int32_t *tcol = nullptr;
+  long long *tval = nullptr;
+  int64_t nhead = 0, ntail = 0;
+};
+cudaError_t build_sliced_rows(const int64_t *rowptr, const int32_t *col, const long long *fval, int64_t dim,
+                              SlicedRows *out, cudaStream_t st);
+void free_sliced_rows(SlicedRows *s);
 // count (device, zeroed by the caller) += the 32-row tiles (rows [32 t, 32 t + 32)) of the CSR terms
 // T[0..nt-1] whose runs do not fit one staging slot; such tiles are read from global memory
 cudaError_t launch_stage_misfits(const Term *T, int nt, int64_t dim, unsigned long long *count, cudaStream_t st);

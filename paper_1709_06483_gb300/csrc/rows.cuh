@@ -242,9 +242,111 @@ static __device__ __forceinline__ void zadd(longlong2 &acc, longlong2 v) {
   acc.y += v.y;
 }
 
+// ------------------------------------------------ sliced rows (Term::hbase, slices.cu)
+// Head of row r: its slice's first w entries, column-major (entry k at hbase[s] + 32 k + (r & 31)):
+// one coalesced load of entry k for the warp's 32 rows, no row pointer.  Tail: the rest, row-major
+// behind tptr.  Both sums exact in int64, so the order of the entries does not matter.
+static __device__ __forceinline__ void sl_head(const Term &t, int64_t r, int64_t &hb, int &w) {
+  const int64_t s = r >> 5;
+  hb = __ldg(t.hbase + s);
+  w = (int)((__ldg(t.hbase + s + 1) - hb) >> 5);
+  hb += r & 31;
+}
+
+// sum_e Z[col_e] over the sliced row r of a pattern term
+static __device__ __forceinline__ longlong2 sl_row_zsum(const Term &t, const longlong2 *z, int64_t r) {
+  int64_t hb;
+  int w;
+  sl_head(t, r, hb, w);
+  const int32_t *hc = t.hcol + hb;
+  longlong2 acc = make_longlong2(0, 0);
+  int k = 0;
+  for (; k + kRound <= w; k += kRound) {
+    int c[kRound];
+    longlong2 v[kRound];
+#pragma unroll
+    for (int q = 0; q < kRound; q++) c[q] = __ldg(hc + 32 * (k + q));
+#pragma unroll
+    for (int q = 0; q < kRound; q++) v[q] = ldz(z + c[q]);
+#pragma unroll
+    for (int q = 0; q < kRound; q++) zadd(acc, v[q]);
+  }
+  if (kRound == 8 && k + 4 <= w) {
+    int c[4];
+    longlong2 v[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) c[q] = __ldg(hc + 32 * (k + q));
+#pragma unroll
+    for (int q = 0; q < 4; q++) v[q] = ldz(z + c[q]);
+#pragma unroll
+    for (int q = 0; q < 4; q++) zadd(acc, v[q]);
+    k += 4;
+  }
+  for (; k < w; k++) zadd(acc, ldz(z + __ldg(hc + 32 * k)));
+  if (t.tptr)
+    for (int64_t e = __ldg(t.tptr + r), e1 = __ldg(t.tptr + r + 1); e < e1; e++) zadd(acc, ldz(z + __ldg(t.tcol + e)));
+  return acc;
+}
+
+// sum_e hi64(fval_e Z[col_e]) over the sliced row r of a product term (the tail with the warp's
+// longest tail as the trip count: call with the warp converged)
+static __device__ __forceinline__ longlong2 sl_row_zprod(const Term &t, const longlong2 *z, int64_t r) {
+  int64_t hb;
+  int w;
+  sl_head(t, r, hb, w);
+  const int32_t *hc = t.hcol + hb;
+  const long long *hv = t.hval + hb;
+  longlong2 acc = make_longlong2(0, 0);
+  int k = 0;
+  for (; k + kRound <= w; k += kRound) {
+    int c[kRound];
+    long long a[kRound];
+    longlong2 v[kRound];
+#pragma unroll
+    for (int q = 0; q < kRound; q++) c[q] = __ldg(hc + 32 * (k + q));
+#pragma unroll
+    for (int q = 0; q < kRound; q++) a[q] = __ldg(hv + 32 * (k + q));
+#pragma unroll
+    for (int q = 0; q < kRound; q++) v[q] = ldz(z + c[q]);
+#pragma unroll
+    for (int q = 0; q < kRound; q++) {
+      acc.x += __mul64hi(a[q], v[q].x);
+      acc.y += __mul64hi(a[q], v[q].y);
+    }
+  }
+  for (; k < w; k++) {
+    const long long a = __ldg(hv + 32 * k);
+    const longlong2 v = ldz(z + __ldg(hc + 32 * k));
+    acc.x += __mul64hi(a, v.x);
+    acc.y += __mul64hi(a, v.y);
+  }
+  if (t.tptr) {
+    const int64_t e0 = __ldg(t.tptr + r);
+    const int len = (int)(__ldg(t.tptr + r + 1) - e0);
+    const int lmax = __reduce_max_sync(__activemask(), len);
+    for (int j = 0; j < lmax; j += 4) {
+      long long a[4];
+      longlong2 v[4];
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        const bool in = j + q < len;
+        a[q] = in ? __ldg(t.tval + e0 + j + q) : 0ll;
+        v[q] = in ? ldz(z + __ldg(t.tcol + e0 + j + q)) : make_longlong2(0, 0);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        acc.x += __mul64hi(a[q], v[q].x);
+        acc.y += __mul64hi(a[q], v[q].y);
+      }
+    }
+  }
+  return acc;
+}
+
 // sum_e Z[col_e] over a CSR row, rounds of kRound entries (rows of one length plen start at r plen:
 // no row-pointer load before the column loads)
 static __device__ __forceinline__ longlong2 csr_row_zsum(const Term &t, const longlong2 *z, int64_t r) {
+  if (t.hbase) return sl_row_zsum(t, z, r);
   int64_t e = t.plen ? r * t.plen : __ldg(t.rowptr + r);
   const int64_t e1 = t.plen ? e + t.plen : __ldg(t.rowptr + r + 1);
   longlong2 acc = make_longlong2(0, 0);
@@ -278,6 +380,10 @@ static __device__ __forceinline__ longlong2 csr_row_zsum(const Term &t, const lo
 // warp-uniform trip count; returns the sum and, in fe, the row's exponent.  The row's value is
 // sum 2^(fe + 2 - zs) with zs the scale of Z.  Call with the warp converged.
 static __device__ __forceinline__ longlong2 csr_row_zprod_w(const Term &t, const longlong2 *z, int64_t r, int &fe) {
+  if (t.hbase) {
+    fe = __ldg(t.fexp + r);
+    return sl_row_zprod(t, z, r);
+  }
   const int64_t e0 = __ldg(t.rowptr + r);
   const int len = (int)(__ldg(t.rowptr + r + 1) - e0);
   const int lmax = __reduce_max_sync(__activemask(), len);

@@ -399,31 +399,54 @@ def test_apply_fixed_point_general_terms(mg):
             assert rel_scaled(ys[fixed][v], ref) < 1e-13, (fixed, v, rel_scaled(ys[fixed][v], ref))
 
 
-# ----------------------------------------------------------------- staged rows (shared-memory tiles)
+# ----------------------------------------------------------------- row layouts of the fixed-point CSR rows
+LAYOUTS = {"csr": 2, "staged": 1, "sliced": 3}
+
+
 @pytest.mark.parametrize("nvec", [1, 3])
-def test_staged_rows_bit_identical_to_global_rows(mg, nvec):
-    """The staged rows (each warp's 32-row tiles copied into shared memory by the TMA bulk engine)
-    read the same entries as the rows read from global memory and sum them exactly in int64, so the
-    two plans agree bit for bit, and both match the oracle.  12-spin chain (dim 4096, 128 tiles),
-    CF4 and CF4:3."""
+def test_row_layouts_bit_identical(mg, nvec):
+    """The three layouts of the fixed-point CSR rows -- the CSR arrays as given, each warp's 32-row
+    tiles staged in shared memory by the TMA bulk engine, and the sliced rows (column-major heads of
+    32-row slices, entries reordered so that shared column offsets line up) -- read the same entries
+    and sum them exactly in int64, so the three plans agree bit for bit, and match the oracle.
+    12-spin chain (dim 4096, 128 slices), CF4 and CF4:3."""
     c = mi.xxz_chain(49, 12, 0.01, 12, nvec=nvec)
     P = chain_problem(c)
     for variant in ("CF4", "CF4_3"):
         out = {}
-        for staged in (True, False):
-            plan = mg.Plan(c.dim, chain_terms(mg, c, "csr"), drives(mg, c), nvec=nvec, staged=staged)
+        for rows, code in LAYOUTS.items():
+            plan = mg.Plan(c.dim, chain_terms(mg, c, "csr"), drives(mg, c), nvec=nvec, rows=rows)
             psi = cuda(c.psi0)
             st = plan.propagate(psi, 0.0, c.h, c.nsteps, variant, log_cap=1024)
-            assert st["staged"] == int(staged) and st["fixed_sums"] == 1
-            out[staged] = (psi.cpu().numpy(), st["m_log"])
+            assert st["row_layout"] == code and st["fixed_sums"] == 1
+            out[rows] = (psi.cpu().numpy(), st["m_log"])
             plan.close()
-        assert np.array_equal(out[True][0], out[False][0])
-        assert np.array_equal(out[True][1], out[False][1])
+        for rows in ("staged", "sliced"):
+            assert np.array_equal(out[rows][0], out["csr"][0]), rows
+            assert np.array_equal(out[rows][1], out["csr"][1]), rows
         psi0 = c.psi0.reshape(nvec, -1)
-        got = out[True][0].reshape(nvec, -1)
+        got = out["sliced"][0].reshape(nvec, -1)
         for v in range(nvec):
             ref = P.propagate(psi0[v], 0.0, c.h, c.nsteps, variant)
             assert rel(got[v], ref) < REL_TOL, (variant, v, rel(got[v], ref))
+
+
+def test_sliced_rows_m4_and_apply(mg):
+    """M4 (both phases on the sliced rows) and the generator matvec alone (magnus_apply) give the
+    bits of the CSR layout; 11 spins, odd number of slices per block."""
+    c = mi.xxz_chain(52, 11, 0.01, 10)
+    res = {}
+    for rows in ("csr", "sliced"):
+        plan = mg.Plan(c.dim, chain_terms(mg, c, "csr"), drives(mg, c), rows=rows)
+        psi = cuda(c.psi0)
+        plan.propagate(psi, 0.0, c.h, c.nsteps, "M4")
+        y = plan.apply(np.array([0.7, -1.3]), cuda(c.psi0))
+        res[rows] = (psi.cpu().numpy(), y.cpu().numpy())
+        plan.close()
+    assert np.array_equal(res["csr"][0], res["sliced"][0])
+    assert np.array_equal(res["csr"][1], res["sliced"][1])
+    ref = chain_problem(c).propagate(c.psi0, 0.0, c.h, c.nsteps, "M4")
+    assert rel(res["sliced"][0], ref) < REL_TOL
 
 
 def _banded_with_heavy_band(rng, D, band, w_heavy):
@@ -458,10 +481,11 @@ def _tiles_too_large(rowptrs, slot=9472):
     return bad
 
 
-def test_staged_rows_with_tiles_too_large_for_a_slot(mg):
-    """A real banded term with one band of 32 rows of 81 entries (its tile and the neighbouring tiles
-    do not fit a slot and are read from global memory inside the staged kernel) beside a pattern
-    term; dim 16384 (512 tiles, a few of them too large).  Bit-identical to the unstaged plan and
+def test_row_layouts_with_long_rows(mg):
+    """A real banded term with one band of 32 rows of 81 entries beside a pattern term; dim 16384
+    (512 tiles).  Staged: a few tiles do not fit a slot and are read from global memory inside the
+    staged kernel.  Sliced: the rows of those slices are longer than the reordering handles (CSR
+    order kept) and most of their entries sit in the tails.  Bit-identical to the CSR layout and
     within 1e-10 of the oracle, with identical Leja degrees."""
     rng = np.random.default_rng(50)
     D = 16384
@@ -488,14 +512,15 @@ def test_staged_rows_with_tiles_too_large_for_a_slot(mg):
     ost = oracle.Stats(256)
     ref = Pr.propagate(psi0, 0.0, 0.02, 6, "CF4", ost)
     out = {}
-    for staged in (True, False):
+    for rows, code in LAYOUTS.items():
         terms = [mg.CSRTerm(cuda(r), cuda(c), cuda(v)) for r, c, v in (h1, h2)]
-        plan = mg.Plan(D, terms, [mg.Drive.const(), mg.Drive(0.3, [1.0], [], [2.5])], staged=staged)
+        plan = mg.Plan(D, terms, [mg.Drive.const(), mg.Drive(0.3, [1.0], [], [2.5])], rows=rows)
         psi = cuda(psi0)
         st = plan.propagate(psi, 0.0, 0.02, 6, "CF4", log_cap=256)
-        assert st["staged"] == int(staged)
+        assert st["row_layout"] == code, rows
         assert np.array_equal(st["m_log"], ost.m_log)
-        out[staged] = psi.cpu().numpy()
+        out[rows] = psi.cpu().numpy()
         plan.close()
-    assert np.array_equal(out[True], out[False])
-    assert rel(out[True], ref) < REL_TOL
+    assert np.array_equal(out["staged"], out["csr"])
+    assert np.array_equal(out["sliced"], out["csr"])
+    assert rel(out["sliced"], ref) < REL_TOL
