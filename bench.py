@@ -335,7 +335,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     mg.load()
-    c = mi.workload2()
+    c = mi.workload1() if args.workload == "xxz10" else mi.workload2()
     variant, storage = args.variant, args.storage
     stream = torch.cuda.current_stream()
     terms = workload_terms(mg, c, storage)
@@ -403,7 +403,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64+i64" if head["fixed_sums"] else "f64",
         "data": "synthetic",
-        "config": {"workload": f"xxz_chain_20spins_{storage}_{variant.lower()}", "spins": c.nspins, "dim": c.dim,
+        "config": {"workload": f"xxz_chain_{c.nspins}spins_{storage}_{variant.lower()}", "spins": c.nspins, "dim": c.dim,
                    "nnz": nnz_total, "h": c.h, "t0": c.t0, "variant": variant, "storage": storage,
                    "interval": args.interval, "row_layout": head["row_layout"],
                    "sums": SUMS_FIXED if head["fixed_sums"] else "FP64",
@@ -1005,8 +1005,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--spins", type=int, default=13, help="dense13 only: chain length (profiling smaller cases)")
     ap.add_argument("--states", type=int, default=64, help="dense13 only: states sharing H")
-    ap.add_argument("--workload", choices=["xxz20", "dense13", "batch512", "adjoint16", "spmv20"], default="xxz20",
-                    help="xxz20: the headline 20-spin chain; dense13: 13-spin dense chain, 64 states, FP64 vs split")
+    ap.add_argument("--workload", choices=["xxz20", "xxz10", "dense13", "batch512", "adjoint16", "spmv20"],
+                    default="xxz20", help="xxz20: the headline 20-spin chain (xxz10: the 10-spin chain in its "
+                    "place); dense13: 13-spin dense chain, 64 states, FP64 vs split")
     args = ap.parse_args()
     if args.workload == "dense13" and args.impl == "ours":
         run_dense13(args)

@@ -163,15 +163,16 @@ typedef enum {
  *                     subnormal).  0 = FP64 throughout.  Not part of the paper, which computes in
  *                     FP64 only.
  *   row_layout [MAGNUS_ROWS_AUTO]: how the rows of fixed-point CSR plans (every term CSR, fixed_sums)
- *                     read the pattern and product terms (plan-owned copies, same bytes per entry):
- *                     MAGNUS_ROWS_SLICED (the default) -- per 32-row slice the first w entries of
- *                     every row column-major (w = the slice's shortest row), ordered so that rows
- *                     sharing a column offset read it at the same position, the rest row-major;
- *                     MAGNUS_ROWS_CSR -- the CSR arrays as given; MAGNUS_ROWS_STAGED -- each warp's
- *                     32-row tiles of the CSR arrays copied into shared memory two tiles ahead by the
- *                     TMA bulk engine (one CTA of 8 warps per SM; tiles larger than a 9,472-byte slot
- *                     read from global memory; used only if at most 1/64 of the tiles are such).  The
- *                     integer row sums make every layout give the same bits.
+ *                     read the pattern and product terms; the integer row sums make every layout give
+ *                     the same bits.  MAGNUS_ROWS_CSR (the default) -- the CSR arrays as given, a
+ *                     row per thread; MAGNUS_ROWS_SLICED -- plan-owned copies cut into 32-row slices:
+ *                     the first w entries of every row column-major (w = the slice's shortest row),
+ *                     ordered so that rows sharing a column offset read it at the same position, the
+ *                     rest row-major (same bytes per entry); MAGNUS_ROWS_STAGED -- those slices
+ *                     copied into shared memory two tiles ahead by the TMA bulk engine (two CTAs of 8
+ *                     warps per SM; plans of at most two terms; a tile larger than a 6,400-byte slot
+ *                     is read from global memory, and a plan stages only if at most 1/64 of its
+ *                     tiles are such).
  *   plain_values [0]: 1 = multiply complex-stored CSR and dense values in place as complex128 numbers
  *                     even when every imaginary part is zero (no real-valued specialisation, no
  *                     float64 copy, no pattern or fixed-point rows): the plain FP64 path of the paper,
@@ -179,7 +180,7 @@ typedef enum {
  *                     (MAGNUS_TERM_*_REAL) is unaffected.  _reserved must be 0.
  */
 typedef enum {
-  MAGNUS_ROWS_AUTO = 0,   /* the library's choice (MAGNUS_ROWS_SLICED) */
+  MAGNUS_ROWS_AUTO = 0,   /* the library's choice (MAGNUS_ROWS_CSR) */
   MAGNUS_ROWS_STAGED = 1,
   MAGNUS_ROWS_CSR = 2,
   MAGNUS_ROWS_SLICED = 3

@@ -807,6 +807,7 @@ MAGNUS_API magnus_status magnus_batch_destroy(magnus_batch_t b) {
 
 MAGNUS_API magnus_status magnus_batch_propagate(magnus_batch_t b, void *const *psi, double t0, double h,
                                                 int64_t nsteps, int32_t variant, magnus_batch_stats *stats) {
+  NvtxRange nvtx_range("magnus_batch_propagate");
   if (!b) return berr(nullptr, MAGNUS_EINVAL, "batch is null");
   b->err.clear();
   if (!psi) return berr(b, MAGNUS_EINVAL, "psi array is null");

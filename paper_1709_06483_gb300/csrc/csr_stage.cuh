@@ -1,17 +1,22 @@
-// Staged CSR rows for the fixed-point Leja pass (FAM_CSR, linear generators): each warp takes the
-// block's rows in tiles of 32 (one row per lane) and reads the matrix of a tile from shared memory.
-// A tile's rows own one contiguous run of every term's arrays -- columns, and for product terms
-// the 62-bit value mantissas -- so one lane copies those runs into a slot of the warp's shared
-// memory with cp.async.bulk (the TMA bulk engine) two tiles ahead of the one the warp computes,
-// completion counted on the slot's mbarrier.  The lanes then walk their rows in shared memory and
-// only the gathers of the fixed-point vector go to global memory.  The matrix is the same in every
-// Leja iteration, so the pipeline runs on across iterations: the copies issued at the end of a pass
-// are the first tiles of the next one.
+// Staged rows for the fixed-point Leja pass (FAM_CSR, linear generators, row_layout STAGED): each
+// warp takes the block's rows in tiles of 32 (one row per lane; a tile is one slice of the sliced
+// rows, slices.cu) and reads the matrix of its sliced terms from shared memory.  The slice's head
+// (w entries per row, column-major) and the tile's tail entries (row-major) are contiguous runs of
+// the sliced arrays, so one lane copies them into a slot of the warp's shared memory with
+// cp.async.bulk (the TMA bulk engine) two tiles ahead of the tile the warp computes, completion
+// counted on the slot's mbarrier, and writes a small descriptor of the slot beside it.  The lanes
+// then read entry k of their 32 rows from consecutive words (no bank conflicts) and only gather the
+// fixed-point vector from global memory.  Rows of one length of a pattern term (plen, the
+// transverse field) need no row pointer: their columns are read from global memory with 16-byte
+// loads issued at the start of the tile.  The matrix is the same in every Leja iteration, so the
+// pipeline runs on across iterations: the copies issued at the end of a pass are the first tiles
+// of the next one.
 //
 // Sums and products are exact 64-bit integers (rows.cuh), so the order in which a row's entries are
-// read does not change the result: a staged row gives the bits the unstaged row gives.  A tile
-// whose runs do not fit a slot, or would reach past the last 16-byte block of an array, is read
-// from global memory by the unstaged rows (its copy is an empty arrival).
+// read does not change the result: a staged row gives the bits of the sliced and CSR rows.  A tile
+// whose runs do not fit a slot is read from global memory by the sliced rows (its copy is an empty
+// arrival).  The sliced tail arrays carry 16 bytes of padding, so a run rounded out to whole
+// 16-byte blocks stays inside them.
 #pragma once
 
 #include "rows.cuh"
@@ -20,74 +25,87 @@
 namespace mg {
 namespace stage {
 
-constexpr int kWarps = 8;            // warps per CTA (256 threads)
-constexpr int kTile = 32;            // rows per tile, one per lane
-constexpr int kSlotBytes = 9472;     // one slot; 74 x 128 B (the 20-spin chain's largest tile needs 9328)
-constexpr size_t kSmemBytes = (size_t)kWarps * 2 * kSlotBytes;  // 151,552 B of dynamic shared memory
-constexpr int kRound = 16;           // gathers in flight per lane
+constexpr int kWarps = 8;            // warps per CTA (256 threads), two CTAs per SM
+constexpr int kTile = 32;            // rows per tile (one slice), one per lane
+constexpr int kSlotBytes = 6400;     // 50 x 128 B: the 20-spin chain's H_s tiles need up to 6,752
+constexpr int kDescBytes = 128;      // two descriptors of a warp's slots, then its next span
+constexpr int kTerms = 2;            // terms of a staged plan (the register arrays are this long)
+constexpr size_t kSmemBytes = (size_t)kWarps * (2 * kSlotBytes + 3 * kDescBytes);  // 105,472 B per CTA
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// Byte runs of one tile inside a slot: run 2k holds term k's columns, run 2k+1 its mantissas.
-struct Lay {
-  uint32_t off[2 * kMaxTerms];  // offset of the run in the slot
-  int64_t b0[2 * kMaxTerms];    // first byte of the run in the global array (16-byte aligned)
-  uint32_t len[2 * kMaxTerms];  // bytes (a multiple of 16, possibly 0)
-  uint32_t total;
-  bool fits;
+// a term read from the slots: sliced, and not a pattern whose rows are all one length
+__device__ __forceinline__ bool staged_term(const Term &t) { return t.hbase && !(t.pattern && t.plen); }
+
+// Slot descriptor (written by lane 0 at issue time, read by the lanes after the slot's phase).
+struct Desc {
+  int fits;
+  int w[kTerms];             // head width of each staged term in this slice
+  uint32_t hc[kTerms];       // slot offsets: head columns, head mantissas,
+  uint32_t hv[kTerms];
+  uint32_t tc[kTerms];       // the tail runs (their first 16-byte block)
+  uint32_t tv[kTerms];
+  long long t0[kTerms];      // first tail entry of the tile
 };
+static_assert(sizeof(Desc) <= kDescBytes, "descriptor size");
 
-// entry range [e0, e1) of term t over rows [ra, rb): row pointers, or r * plen for rows of one length
-__device__ __forceinline__ void term_span(const Term &t, int64_t ra, int64_t rb, int64_t &e0, int64_t &e1) {
-  if (t.plen) {
-    e0 = ra * t.plen;
-    e1 = rb * t.plen;
-  } else {
-    e0 = __ldg(t.rowptr + ra);
-    e1 = __ldg(t.rowptr + rb);
-  }
-}
+// Runs of one tile: slice s = ra / 32; per staged term the head [hbase[s], hbase[s+1]) and the tail
+// entries [tptr[ra], tptr[rb]).
+struct Span {
+  long long h0[kTerms], h1[kTerms], t0[kTerms], t1[kTerms];
+};
+static_assert(sizeof(Span) <= kDescBytes, "span size");
 
-__device__ __forceinline__ void layout(const Term *T, int nt, const int64_t (&e0)[kMaxTerms],
-                                       const int64_t (&e1)[kMaxTerms], Lay &L) {
-  uint32_t off = 0;
-  bool fits = true;
+__device__ __forceinline__ void load_span(const Term *T, int nt, int64_t ra, int64_t rb, Span &S) {
 #pragma unroll
-  for (int k = 0; k < kMaxTerms; k++) {
-#pragma unroll
-    for (int v = 0; v < 2; v++) {
-      const int q = 2 * k + v;
-      L.off[q] = off;
-      L.b0[q] = 0;
-      L.len[q] = 0;
-      if (k >= nt || (v == 1 && T[k].pattern)) continue;
-      const int es = v ? 8 : 4;  // bytes per entry
-      const int64_t b0 = (e0[k] * es) & ~(int64_t)15;
-      const int64_t b1 = (e1[k] * es + 15) & ~(int64_t)15;
-      const int64_t end = (T[k].nnz * es) & ~(int64_t)15;  // last whole 16-byte block of the array
-      const int64_t nb = b1 - b0;
-      if (b1 > end || nb < 0 || nb > (int64_t)kSlotBytes) fits = false;  // (nb < 0: rows out of order)
-      L.b0[q] = b0;
-      L.len[q] = (nb >= 0 && nb <= (int64_t)kSlotBytes) ? (uint32_t)nb : 0u;
-      off += L.len[q];
+  for (int k = 0; k < kTerms; k++) {
+    S.h0[k] = S.h1[k] = S.t0[k] = S.t1[k] = 0;
+    if (k >= nt || !staged_term(T[k])) continue;
+    S.h0[k] = __ldg(T[k].hbase + (ra >> 5));
+    S.h1[k] = __ldg(T[k].hbase + (ra >> 5) + 1);
+    if (T[k].tptr) {
+      S.t0[k] = __ldg(T[k].tptr + ra);
+      S.t1[k] = __ldg(T[k].tptr + rb);
     }
   }
-  L.total = off;
-  L.fits = fits && off <= (uint32_t)kSlotBytes;
 }
 
-// One lane: arrive on the slot's barrier expecting the tile's bytes and start the copies (an empty
-// arrival for a tile read from global memory).
-__device__ __forceinline__ void issue(const Term *T, int nt, const Lay &L, unsigned char *slot, uint64_t *bar) {
-  tc::mbar_expect_tx(bar, L.fits ? L.total : 0u);
-  if (!L.fits) return;
+// tail run of entries [t0, t1) of `es`-byte entries, rounded out to whole 16-byte blocks
+__device__ __forceinline__ long long run_lo(long long t0, int es) { return (t0 * es) & ~15ll; }
+__device__ __forceinline__ long long run_hi(long long t1, int es) { return (t1 * es + 15) & ~15ll; }
+
+// Slot layout of a tile; returns its bytes (D.fits: they fit one slot).
+__device__ __forceinline__ uint32_t layout(const Term *T, int nt, const Span &S, Desc &D) {
+  long long off = 0;
+  bool ok = true;
 #pragma unroll
-  for (int k = 0; k < kMaxTerms; k++) {
-    if (k >= nt) continue;
-    if (L.len[2 * k]) tc::bulk_load(slot + L.off[2 * k], (const char *)T[k].col + L.b0[2 * k], L.len[2 * k], bar);
-    if (L.len[2 * k + 1])
-      tc::bulk_load(slot + L.off[2 * k + 1], (const char *)T[k].fval + L.b0[2 * k + 1], L.len[2 * k + 1], bar);
+  for (int k = 0; k < kTerms; k++) {
+    D.w[k] = 0;
+    D.hc[k] = D.hv[k] = D.tc[k] = D.tv[k] = 0;
+    D.t0[k] = 0;
+    if (k >= nt || !staged_term(T[k])) continue;
+    const long long nh = S.h1[k] - S.h0[k];  // 32 w entries
+    const long long nl = S.t1[k] - S.t0[k];
+    if (nh < 0 || nh > kSlotBytes || nl < 0 || nl > kSlotBytes) { ok = false; continue; }  // (malformed)
+    D.w[k] = (int)(nh >> 5);
+    D.t0[k] = S.t0[k];
+    D.hc[k] = (uint32_t)off;
+    off += 4 * nh;
+    if (!T[k].pattern) {
+      D.hv[k] = (uint32_t)off;
+      off += 8 * nh;
+    }
+    if (T[k].tptr && nl > 0) {
+      D.tc[k] = (uint32_t)off;
+      off += run_hi(S.t1[k], 4) - run_lo(S.t0[k], 4);
+      if (!T[k].pattern) {
+        D.tv[k] = (uint32_t)off;
+        off += run_hi(S.t1[k], 8) - run_lo(S.t0[k], 8);
+      }
+    }
   }
+  D.fits = ok && off <= kSlotBytes;
+  return (uint32_t)(D.fits ? off : 0);
 }
 
 // bounded wait on an mbarrier phase (global timer), false if it runs out
@@ -104,69 +122,94 @@ __device__ __forceinline__ bool wait_slot(uint64_t *bar, uint32_t parity, long l
 // slot n & 1 (phase parity (n >> 1) & 1) and holds the warp's tile n mod ntiles; after consuming n
 // the warp issues n + 2.
 struct Pipe {
-  unsigned char *slot0;
+  unsigned char *slot0;     // two slots, then two descriptors
   uint64_t *bar;            // two mbarriers in shared memory
   long long issued, consumed;
   int ntiles;               // tiles of this warp per pass (0: the warp has no rows)
   int w;                    // warp index in the CTA
+  int tc;                   // consumed mod ntiles (the tile of the next consumption)
   bool primed;
-  // row data of the next tile to consume, loaded one tile ahead: per term the row's entry range
-  // and (product terms) its exponent
-  int64_t ne0[kMaxTerms], ne1[kMaxTerms];
-  int nfe[kMaxTerms];
+  // row data of the next tile to consume, loaded one tile ahead: per staged term the row's tail
+  // range, per product term its exponent
+  long long nt0[kTerms], nt1[kTerms];
+  int nfe[kTerms];
 };
 
-__device__ __forceinline__ void tile_rows(const Pipe &P, int64_t lo, int64_t hi, long long n, int64_t &ra,
-                                          int64_t &rb) {
-  const int64_t t = P.w + (int64_t)kWarps * (n % P.ntiles);
-  ra = lo + kTile * t;
+__device__ __forceinline__ unsigned char *slot_ptr(const Pipe &P, long long n) {
+  return P.slot0 + (size_t)(n & 1) * kSlotBytes;
+}
+__device__ __forceinline__ Desc *desc_ptr(const Pipe &P, long long n) {
+  return reinterpret_cast<Desc *>(P.slot0 + 2 * (size_t)kSlotBytes + (size_t)(n & 1) * kDescBytes);
+}
+// lane 0's record of the runs of the tile it copies next (shared memory, not registers)
+__device__ __forceinline__ Span *span_ptr(const Pipe &P) {
+  return reinterpret_cast<Span *>(P.slot0 + 2 * (size_t)kSlotBytes + 2 * (size_t)kDescBytes);
+}
+
+// rows of the warp's tile `i` (0 <= i < ntiles)
+__device__ __forceinline__ void tile_rows(const Pipe &P, int64_t lo, int64_t hi, int i, int64_t &ra, int64_t &rb) {
+  ra = lo + (int64_t)kTile * (P.w + kWarps * i);
   rb = min(hi, ra + kTile);
 }
+// tile index d consumptions after the next one (d small): no division
+__device__ __forceinline__ int tile_ahead(const Pipe &P, int d) {
+  int i = P.tc + d;
+  while (i >= P.ntiles) i -= P.ntiles;
+  return i;
+}
 
-// entry ranges and exponents of this lane's row r of tile consumption n (zero-length if r >= rb)
+// tail range and exponent of this lane's row r (zero-length if r >= rb)
 __device__ __forceinline__ void load_rowdata(Pipe &P, const Term *T, int nt, int64_t r, int64_t rb) {
 #pragma unroll
-  for (int k = 0; k < kMaxTerms; k++) {
-    P.ne0[k] = P.ne1[k] = 0;
+  for (int k = 0; k < kTerms; k++) {
+    P.nt0[k] = P.nt1[k] = 0;
     P.nfe[k] = 0;
     if (k >= nt || r >= rb) continue;
-    term_span(T[k], r, r + 1, P.ne0[k], P.ne1[k]);
     if (!T[k].pattern) P.nfe[k] = __ldg(T[k].fexp + r);
+    if (staged_term(T[k]) && T[k].tptr) {
+      P.nt0[k] = __ldg(T[k].tptr + r);
+      P.nt1[k] = __ldg(T[k].tptr + r + 1);
+    }
   }
 }
 
-// the runs' entry ranges of consumption n (row pointers loaded here)
-__device__ __forceinline__ void tile_spans(const Pipe &P, const Term *T, int nt, int64_t lo, int64_t hi, long long n,
-                                           int64_t (&e0)[kMaxTerms], int64_t (&e1)[kMaxTerms]) {
-  int64_t ra, rb;
-  tile_rows(P, lo, hi, n, ra, rb);
+// lane 0: write the descriptor of consumption n and start its copies (an empty arrival if the tile
+// does not fit)
+__device__ __forceinline__ void issue(Pipe &P, const Term *T, int nt, long long n, const Span &S) {
+  Desc L;
+  const uint32_t total = layout(T, nt, S, L);
+  *desc_ptr(P, n) = L;
+  unsigned char *slot = slot_ptr(P, n);
+  uint64_t *bar = P.bar + (n & 1);
+  tc::mbar_expect_tx(bar, total);
+  if (!L.fits) return;
 #pragma unroll
-  for (int k = 0; k < kMaxTerms; k++) {
-    e0[k] = e1[k] = 0;
-    if (k < nt) term_span(T[k], ra, rb, e0[k], e1[k]);
+  for (int k = 0; k < kTerms; k++) {
+    if (k >= nt || !staged_term(T[k])) continue;
+    const uint32_t nh = (uint32_t)(S.h1[k] - S.h0[k]);
+    if (nh) {
+      tc::bulk_load(slot + L.hc[k], T[k].hcol + S.h0[k], 4 * nh, bar);
+      if (!T[k].pattern) tc::bulk_load(slot + L.hv[k], T[k].hval + S.h0[k], 8 * nh, bar);
+    }
+    if (T[k].tptr && S.t1[k] > S.t0[k]) {
+      const long long b0 = run_lo(S.t0[k], 4), b1 = run_hi(S.t1[k], 4);
+      tc::bulk_load(slot + L.tc[k], (const char *)T[k].tcol + b0, (uint32_t)(b1 - b0), bar);
+      if (!T[k].pattern) {
+        const long long v0 = run_lo(S.t0[k], 8), v1 = run_hi(S.t1[k], 8);
+        tc::bulk_load(slot + L.tv[k], (const char *)T[k].tval + v0, (uint32_t)(v1 - v0), bar);
+      }
+    }
   }
-}
-
-// lane 0 of the warp: copy the runs of consumption n (entry ranges e0, e1) into its slot
-__device__ __forceinline__ void issue_tile(Pipe &P, const Term *T, int nt, long long n, const int64_t (&e0)[kMaxTerms],
-                                           const int64_t (&e1)[kMaxTerms]) {
-  Lay L;
-  layout(T, nt, e0, e1, L);
-  issue(T, nt, L, P.slot0 + (size_t)(n & 1) * kSlotBytes, P.bar + (n & 1));
-}
-__device__ __forceinline__ void issue_tile(Pipe &P, const Term *T, int nt, int64_t lo, int64_t hi, long long n) {
-  int64_t e0[kMaxTerms], e1[kMaxTerms];
-  tile_spans(P, T, nt, lo, hi, n, e0, e1);
-  issue_tile(P, T, nt, n, e0, e1);
 }
 
 // Set up the warp's two mbarriers (once per kernel).
 __device__ __forceinline__ void init(Pipe &P, unsigned char *smem, uint64_t *bars, int w, int lane, int64_t lo,
                                      int64_t hi) {
   P.w = w;
-  P.slot0 = smem + (size_t)w * 2 * kSlotBytes;
+  P.slot0 = smem + (size_t)w * (2 * kSlotBytes + 3 * kDescBytes);
   P.bar = bars + 2 * w;
   P.issued = P.consumed = 0;
+  P.tc = 0;
   P.primed = false;
   const int64_t T = (hi - lo + kTile - 1) / kTile;
   P.ntiles = (int)(w < T ? (T - w + kWarps - 1) / kWarps : 0);
@@ -184,58 +227,61 @@ __device__ __forceinline__ void drain(Pipe &P, long long limit_ns) {
   P.consumed = P.issued;
 }
 
-// sum over the lane's row of Z[col] (pattern term), columns in shared memory at cs
-__device__ __forceinline__ longlong2 zsum_smem(const int32_t *cs, int len, const longlong2 *z, bool vec4) {
+// sum over the lane's staged row of Z[col] (pattern term): head entry k at hc[32 k], tail at tc
+__device__ __forceinline__ longlong2 zsum_staged(const int32_t *hc, int w, const int32_t *tc, int tlen,
+                                                 const longlong2 *z) {
   longlong2 acc = make_longlong2(0, 0);
   int k = 0;
-  if (vec4) {  // 16-byte aligned rows whose length is a multiple of 4 (rows of one length)
-    for (; k + kRound <= len; k += kRound) {
-      int c[kRound];
-#pragma unroll
-      for (int q = 0; q < kRound; q += 4) {
-        const int4 v = *reinterpret_cast<const int4 *>(cs + k + q);
-        c[q] = v.x; c[q + 1] = v.y; c[q + 2] = v.z; c[q + 3] = v.w;
-      }
-      longlong2 g[kRound];
-#pragma unroll
-      for (int q = 0; q < kRound; q++) g[q] = rows::ldz(z + c[q]);
-#pragma unroll
-      for (int q = 0; q < kRound; q++) rows::zadd(acc, g[q]);
-    }
-    for (; k + 4 <= len; k += 4) {
-      const int4 v = *reinterpret_cast<const int4 *>(cs + k);
-      const longlong2 g0 = rows::ldz(z + v.x), g1 = rows::ldz(z + v.y), g2 = rows::ldz(z + v.z), g3 = rows::ldz(z + v.w);
-      rows::zadd(acc, g0); rows::zadd(acc, g1); rows::zadd(acc, g2); rows::zadd(acc, g3);
-    }
-  }
-  // warp-uniform trip count: lanes past their row's end add zeros
-  const int lmax = __reduce_max_sync(__activemask(), len);
-  for (; k < lmax; k += 8) {
+  for (; k + 8 <= w; k += 8) {
     longlong2 g[8];
 #pragma unroll
-    for (int q = 0; q < 8; q++) g[q] = (k + q < len) ? rows::ldz(z + cs[k + q]) : make_longlong2(0, 0);
+    for (int q = 0; q < 8; q++) g[q] = rows::ldz(z + hc[32 * (k + q)]);
 #pragma unroll
     for (int q = 0; q < 8; q++) rows::zadd(acc, g[q]);
   }
+  for (; k < w; k++) rows::zadd(acc, rows::ldz(z + hc[32 * k]));
+  for (int j = 0; j < tlen; j++) rows::zadd(acc, rows::ldz(z + tc[j]));
   return acc;
 }
 
-// sum over the lane's row of hi64(fval[e] Z[col[e]]) (product term), columns at cs and mantissas at
-// vs in shared memory, with the warp's longest row as the trip count
-__device__ __forceinline__ longlong2 zprod_smem(const int32_t *cs, const long long *vs, int len, const longlong2 *z) {
-  const int lmax = __reduce_max_sync(__activemask(), len);
+// sum over the lane's staged row of hi64(a Z[col]) (product term): head mantissa k at hv[32 k], the
+// tail's at tv; the tail with the warp's longest tail as the trip count (call with the warp converged)
+__device__ __forceinline__ longlong2 zprod_staged(const int32_t *hc, const long long *hv, int w, const int32_t *tc,
+                                                  const long long *tv, int tlen, const longlong2 *z) {
   longlong2 acc = make_longlong2(0, 0);
-  for (int k = 0; k < lmax; k += kRound) {
-    longlong2 g[kRound];
-    long long a[kRound];
+  int k = 0;
+  for (; k + 8 <= w; k += 8) {
+    long long a[8];
+    longlong2 g[8];
 #pragma unroll
-    for (int q = 0; q < kRound; q++) {
-      const bool in = k + q < len;
-      a[q] = in ? vs[k + q] : 0ll;
-      g[q] = in ? rows::ldz(z + cs[k + q]) : make_longlong2(0, 0);
+    for (int q = 0; q < 8; q++) {
+      a[q] = hv[32 * (k + q)];
+      g[q] = rows::ldz(z + hc[32 * (k + q)]);
     }
 #pragma unroll
-    for (int q = 0; q < kRound; q++) {
+    for (int q = 0; q < 8; q++) {
+      acc.x += __mul64hi(a[q], g[q].x);
+      acc.y += __mul64hi(a[q], g[q].y);
+    }
+  }
+  for (; k < w; k++) {
+    const long long a = hv[32 * k];
+    const longlong2 g = rows::ldz(z + hc[32 * k]);
+    acc.x += __mul64hi(a, g.x);
+    acc.y += __mul64hi(a, g.y);
+  }
+  const int lmax = __reduce_max_sync(__activemask(), tlen);
+  for (int j = 0; j < lmax; j += 4) {
+    long long a[4];
+    longlong2 g[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const bool in = j + q < tlen;
+      a[q] = in ? tv[j + q] : 0ll;
+      g[q] = in ? rows::ldz(z + tc[j + q]) : make_longlong2(0, 0);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
       acc.x += __mul64hi(a[q], g[q].x);
       acc.y += __mul64hi(a[q], g[q].y);
     }

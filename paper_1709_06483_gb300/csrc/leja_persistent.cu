@@ -70,10 +70,11 @@ __device__ __forceinline__ double2 scal2(double s, double2 a) { return make_doub
 // extra code does not weigh on the register budget of the other methods).  ZF: the instantiations
 // with fixed-point sums and products (options.fixed_sums): 1 for linear generators (M2, Cf4, Cf4:3),
 // which carries only that path, 2 for M4 (its two phases on fixed-point copies of w and of u_k).
-// STG: the fixed-point CSR instantiation whose rows read the matrix from shared memory, staged per
-// warp tile by the TMA bulk engine (csr_stage.cuh); one CTA of 8 warps per SM holds the slots.
+// STG: the fixed-point CSR instantiation whose rows read the sliced matrix from shared memory,
+// staged per warp tile by the TMA bulk engine (csr_stage.cuh); two CTAs of 8 warps per SM hold the
+// slots.
 template <int FAM, bool HM6, int ZF, bool STG = false>
-__global__ void __launch_bounds__(kBlock, (STG ? 1 : min_blocks<FAM, HM6, ZF>())) k_magnus_persistent(PersistArgs a) {
+__global__ void __launch_bounds__(kBlock, (STG ? 2 : min_blocks<FAM, HM6, ZF>())) k_magnus_persistent(PersistArgs a) {
   static_assert(!STG || (FAM == FAM_CSR && ZF == 1 && !HM6), "staged rows: fixed-point CSR linear generators");
   extern __shared__ __align__(128) unsigned char s_dyn[];
   __shared__ __align__(8) uint64_t s_sbar[STG ? 2 * stage::kWarps : 1];
@@ -92,6 +93,7 @@ __global__ void __launch_bounds__(kBlock, (STG ? 1 : min_blocks<FAM, HM6, ZF>())
   __shared__ double s_red[2][kBlock / 32];
   __shared__ unsigned s_rmx[2][kBlock / 32];
   __shared__ int s_flag;
+  __shared__ int s_kp;  // staged rows: the pattern term whose rows of one length are read as 16-byte loads
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned G = gridDim.x;
@@ -106,6 +108,11 @@ __global__ void __launch_bounds__(kBlock, (STG ? 1 : min_blocks<FAM, HM6, ZF>())
 
   for (int i = tid; i < nt * (int)sizeof(Term) / 4; i += blockDim.x)
     reinterpret_cast<int *>(sT)[i] = reinterpret_cast<const int *>(a.terms)[i];
+  if (tid == 0) {
+    s_kp = -1;
+    for (int k = 0; k < nt; k++)
+      if (s_kp < 0 && sT[k].pattern && sT[k].plen > 0 && sT[k].plen <= 20 && (sT[k].plen & 3) == 0) s_kp = k;
+  }
   __syncthreads();
   Ctx cx{};
   cx.T = sT;
@@ -421,6 +428,8 @@ __global__ void __launch_bounds__(kBlock, (STG ? 1 : min_blocks<FAM, HM6, ZF>())
             for (int64_t r = lo + tid; r < hi; r += blockDim.x) {
               double2 wr;
               double2 y;
+              double2 pold = make_double2(0.0, 0.0);
+              if constexpr (!decltype(first)::value) pold = nxt[base + r];  // issued before the row's gathers
               if (ZF == 2 && R.mode == MODE_M4) {
                 // phase 2: sum_k bg_k u_k + sum_{k<l} kg (H_k u_l - H_l u_k) (times -i) - shift w
                 y = make_double2(0.0, 0.0);
@@ -445,7 +454,7 @@ __global__ void __launch_bounds__(kBlock, (STG ? 1 : min_blocks<FAM, HM6, ZF>())
               dst[base + r] = y;
               zdst[r] = fix2(y, zs_dst);
               double2 pr;
-              if constexpr (decltype(first)::value) pr = cmul(d0, wr); else pr = nxt[base + r];
+              if constexpr (decltype(first)::value) pr = cmul(d0, wr); else pr = pold;
               pr = cfma(dj, y, pr);
               nxt[base + r] = pr;
               sw = fma(y.x, y.x, fma(y.y, y.y, sw));
@@ -454,59 +463,66 @@ __global__ void __launch_bounds__(kBlock, (STG ? 1 : min_blocks<FAM, HM6, ZF>())
               mp = max(mp, abshi(pr));
             }
           };
-          // the same rows, tile by tile, with the matrix runs read from the warp's shared-memory
-          // slots (csr_stage.cuh); every term of this instantiation is a pattern or a product term
+          // the same rows, tile by tile: the sliced terms' heads and tails from the warp's
+          // shared-memory slots (csr_stage.cuh), the rows of one length of pattern terms from global
+          // memory; every term of this instantiation is a pattern or a product term
           auto rows_staged = [&](auto first) {
             using namespace stage;
+            if (P.ntiles == 0) return;
             if (!P.primed) {  // first pass: the row data of tile 0 and the copies of the first two tiles
               P.primed = true;
-              if (P.ntiles > 0) {
-                int64_t ra, rb;
-                tile_rows(P, lo, hi, 0, ra, rb);
-                load_rowdata(P, sT, nt, ra + lane, rb);
-                if (lane == 0) {
-                  issue_tile(P, sT, nt, lo, hi, 0);
-                  issue_tile(P, sT, nt, lo, hi, 1);
+              int64_t ra, rb;
+              tile_rows(P, lo, hi, 0, ra, rb);
+              load_rowdata(P, sT, nt, ra + lane, rb);
+              if (lane == 0)
+                for (long long n = 0; n < 2; n++) {
+                  tile_rows(P, lo, hi, tile_ahead(P, (int)n), ra, rb);
+                  Span S;
+                  load_span(sT, nt, ra, rb, S);
+                  issue(P, sT, nt, n, S);
                 }
-                P.issued = 2;
-                __syncwarp();
-              }
+              P.issued = 2;
+              __syncwarp();
             }
             for (int jt = 0; jt < P.ntiles; jt++) {
               const long long n = P.consumed;
               int64_t ra, rb;
-              tile_rows(P, lo, hi, n, ra, rb);
+              tile_rows(P, lo, hi, P.tc, ra, rb);
               const int64_t r = ra + lane;
               const bool valid = r < rb;
-              int64_t e0[kMaxTerms], e1[kMaxTerms];
-              int fe[kMaxTerms];
+              long long t0[kTerms], t1[kTerms];
+              int fe[kTerms];
 #pragma unroll
-              for (int k = 0; k < kMaxTerms; k++) {
-                e0[k] = P.ne0[k];
-                e1[k] = P.ne1[k];
+              for (int k = 0; k < kTerms; k++) {
+                t0[k] = P.nt0[k];
+                t1[k] = P.nt1[k];
                 fe[k] = P.nfe[k];
+              }
+              // columns of the rows of one length of a pattern term (no row pointer needed, at most
+              // 20 entries, 16-byte aligned): issued first, as 16-byte loads
+              int4 pc[5];
+              const int kp = s_kp;
+              const int p4 = kp >= 0 ? sT[kp].plen / 4 : 0;
+              if (kp >= 0 && valid) {
+                const int4 *c4 = reinterpret_cast<const int4 *>(sT[kp].col + r * sT[kp].plen);
+#pragma unroll
+                for (int q = 0; q < 5; q++)
+                  if (q < p4) pc[q] = __ldg(c4 + q);
               }
               {  // row data of the next tile (the first tile of the next pass after the last)
                 int64_t na, nb;
-                tile_rows(P, lo, hi, n + 1, na, nb);
+                tile_rows(P, lo, hi, tile_ahead(P, 1), na, nb);
                 load_rowdata(P, sT, nt, na + lane, nb);
               }
               // lane 0: the runs of consumption n + 2, copied once this tile is done
-              int64_t q0[kMaxTerms], q1[kMaxTerms];
-              if (lane == 0) tile_spans(P, sT, nt, lo, hi, n + 2, q0, q1);
+              if (lane == 0) {
+                int64_t qa, qb;
+                tile_rows(P, lo, hi, tile_ahead(P, 2), qa, qb);
+                load_span(sT, nt, qa, qb, *span_ptr(P));
+              }
               const double2 wr = valid ? ldv(src + base + r) : make_double2(0.0, 0.0);
               double2 pold = make_double2(0.0, 0.0);
               if constexpr (!decltype(first)::value) pold = valid ? nxt[base + r] : pold;
-              // the tile's runs: lane 0 holds the first row's start, the last row's lane the end
-              const int lastl = (int)(rb - ra) - 1;
-              int64_t t0[kMaxTerms], t1[kMaxTerms];
-#pragma unroll
-              for (int k = 0; k < kMaxTerms; k++) {
-                t0[k] = __shfl_sync(kFull, e0[k], 0);
-                t1[k] = __shfl_sync(kFull, e1[k], lastl);
-              }
-              Lay L;
-              layout(sT, nt, t0, t1, L);
               const int sl = (int)(n & 1);
               if (!wait_slot(P.bar + sl, (uint32_t)((n >> 1) & 1), a.spin_limit_ns)) {
                 // the copy did not arrive: report it; every block leaves at the next barrier
@@ -516,40 +532,66 @@ __global__ void __launch_bounds__(kBlock, (STG ? 1 : min_blocks<FAM, HM6, ZF>())
                 }
                 break;
               }
-              const unsigned char *slot = P.slot0 + (size_t)sl * kSlotBytes;
+              __syncwarp();
+              const Desc &Dd = *desc_ptr(P, n);
+              const unsigned char *slot = slot_ptr(P, n);
+              const bool fits = Dd.fits != 0;
               double2 y = make_double2(0.0, 0.0);
               if (valid) {
+                longlong2 acc[kTerms];
 #pragma unroll
-                for (int k = 0; k < kMaxTerms; k++) {
+                for (int k = 0; k < kTerms; k++) {
+                  acc[k] = make_longlong2(0, 0);
                   if (k >= nt) continue;
                   const Term &t = sT[k];
-                  const int len = (int)(e1[k] - e0[k]);
-                  longlong2 acc;
-                  if (L.fits) {
-                    const int32_t *cs = reinterpret_cast<const int32_t *>(slot + L.off[2 * k] + (e0[k] * 4 - L.b0[2 * k]));
-                    if (t.pattern) {
-                      acc = zsum_smem(cs, len, zsrc, t.plen != 0 && (t.plen & 3) == 0);
-                    } else {
-                      const long long *vs = reinterpret_cast<const long long *>(
-                          slot + L.off[2 * k + 1] + (e0[k] * 8 - L.b0[2 * k + 1]));
-                      acc = zprod_smem(cs, vs, len, zsrc);
+                  if (k == kp) {
+#pragma unroll
+                    for (int h = 0; h < 3; h++) {
+                      if (2 * h >= p4) break;
+                      longlong2 g[8];
+#pragma unroll
+                      for (int i = 0; i < 8; i++) {
+                        const int4 v = pc[min(2 * h + i / 4, 4)];
+                        const int cq = (i & 3) == 0 ? v.x : (i & 3) == 1 ? v.y : (i & 3) == 2 ? v.z : v.w;
+                        g[i] = (2 * h + i / 4 < p4) ? ldz(zsrc + cq) : make_longlong2(0, 0);
+                      }
+#pragma unroll
+                      for (int i = 0; i < 8; i++) zadd(acc[k], g[i]);
                     }
-                  } else if (t.pattern) {
-                    acc = csr_row_zsum(t, zsrc, r);
+                  } else if (t.pattern && t.plen) {
+                    acc[k] = csr_row_zsum(t, zsrc, r);
+                  } else if (fits) {
+                    const int32_t *hc = reinterpret_cast<const int32_t *>(slot + Dd.hc[k]) + lane;
+                    const int tl = (int)(t1[k] - t0[k]);
+                    const int32_t *tcp = reinterpret_cast<const int32_t *>(slot + Dd.tc[k]) +
+                                         (t0[k] - (run_lo(Dd.t0[k], 4) >> 2));
+                    if (t.pattern) {
+                      acc[k] = zsum_staged(hc, Dd.w[k], tcp, tl, zsrc);
+                    } else {
+                      const long long *hv = reinterpret_cast<const long long *>(slot + Dd.hv[k]) + lane;
+                      const long long *tvp = reinterpret_cast<const long long *>(slot + Dd.tv[k]) +
+                                             (t0[k] - (run_lo(Dd.t0[k], 8) >> 3));
+                      acc[k] = zprod_staged(hc, hv, Dd.w[k], tcp, tvp, tl, zsrc);
+                    }
                   } else {
-                    int fe2;
-                    acc = csr_row_zprod_w(t, zsrc, r, fe2);
+                    acc[k] = t.pattern ? sl_row_zsum(t, zsrc, r) : sl_row_zprod(t, zsrc, r);
                   }
-                  y = t.pattern ? rfma(s_wz[k], unfix2(acc, zs_src), y) : rfma(R.bg[k], unfix2(acc, zs_src - fe[k] - 2), y);
+                }
+#pragma unroll
+                for (int k = 0; k < kTerms; k++) {
+                  if (k >= nt) continue;
+                  y = sT[k].pattern ? rfma(s_wz[k], unfix2(acc[k], zs_src), y)
+                                    : rfma(R.bg[k], unfix2(acc[k], zs_src - fe[k] - 2), y);
                 }
                 y = rfma(-shift, wr, y);
               }
               // the slot is free again: copy the runs of consumption n + 2 into it
               P.consumed = n + 1;
+              P.tc = tile_ahead(P, 1);
               __syncwarp();
               if (lane == 0) {
                 fence_proxy_async();
-                issue_tile(P, sT, nt, n + 2, q0, q1);
+                issue(P, sT, nt, n + 2, *span_ptr(P));
               }
               P.issued = n + 3;
               if (valid) {
@@ -746,14 +788,10 @@ __global__ void k_stage_misfits(const Term *Tg, int nt, int64_t dim, unsigned lo
   unsigned long long mine = 0;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ntile; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t ra = t * stage::kTile, rb = min(dim, ra + stage::kTile);
-    int64_t e0[kMaxTerms], e1[kMaxTerms];
-#pragma unroll
-    for (int k = 0; k < kMaxTerms; k++) {
-      e0[k] = e1[k] = 0;
-      if (k < nt) stage::term_span(sT[k], ra, rb, e0[k], e1[k]);
-    }
-    stage::Lay L;
-    stage::layout(sT, nt, e0, e1, L);
+    stage::Span S;
+    stage::load_span(sT, nt, ra, rb, S);
+    stage::Desc L;
+    stage::layout(sT, nt, S, L);
     mine += L.fits ? 0 : 1;
   }
   for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(kFull, mine, o);

@@ -4,11 +4,21 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "magnus.h"
 
 namespace mg {
+
+// NVTX range for the extent of a scope (a profiler shows the API calls and the launches inside
+// them; header-only, inert when no tool is attached)
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 constexpr int kMaxTerms = 4;
 constexpr int kMaxPairs = kMaxTerms * (kMaxTerms - 1) / 2;

@@ -196,8 +196,10 @@ cudaError_t build_sliced_rows(const int64_t *rowptr, const int32_t *col, const l
   if (out->ntail > 0) {
     if ((e = cudaMalloc(&tl, sizeof(int64_t) * dim)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&out->tptr, sizeof(int64_t) * (dim + 1))) != cudaSuccess) return fail(e);
-    if ((e = cudaMalloc(&out->tcol, sizeof(int32_t) * out->ntail)) != cudaSuccess) return fail(e);
-    if (fval && (e = cudaMalloc(&out->tval, sizeof(long long) * out->ntail)) != cudaSuccess) return fail(e);
+    // 4 entries of padding: a run rounded out to whole 16-byte blocks (the staged rows' copies)
+    // stays inside the allocation
+    if ((e = cudaMalloc(&out->tcol, sizeof(int32_t) * (out->ntail + 4))) != cudaSuccess) return fail(e);
+    if (fval && (e = cudaMalloc(&out->tval, sizeof(long long) * (out->ntail + 4))) != cudaSuccess) return fail(e);
     const int g2 = (int)std::max<int64_t>(1, std::min<int64_t>(4096, (dim + 255) / 256));
     k_tail_len<<<g2, 256, 0, st>>>(rowptr, dim, w, tl);
     k_scan<<<1, 1024, 0, st>>>(tl, dim, out->tptr);

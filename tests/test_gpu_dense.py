@@ -239,3 +239,26 @@ def test_dense13_full_size_tensor_sampled(mg, dense13):
     for v in (0, 63):
         ref = P.propagate(c.psi0[v], 0.0, c.h, 1, "CF4")
         assert rel(out[v], ref) < 1e-9, (v, rel(out[v], ref))
+
+
+@pytest.mark.parametrize("precision,tol", [("tensor_sliced", 1e-8), ("fp32_split", 1e-10)])
+def test_reduced_precision_over_a_whole_propagation(mg, precision, tol):
+    """The reduced-precision dense paths over the whole propagation t in [0, 1] (100 Cf4 steps of
+    0.01), 12 spins (dim 4096), 64 states in the bench's launch configuration: states 0 and 63
+    against the FP64 oracle.  Bound: the 1e-8 state error the tensor-core path is held to (its
+    neglected digit products accumulate over the steps), 1e-10 for the FP32 split (error-free
+    products).  The oracle runs its OpenMP build (the checker's bits on all host cores)."""
+    c = mi.workload3(nvec=64, nspins=12, h=0.01, nsteps=100)
+    Hs = mg.build_longrange_dense(c.nspins, c.hz, 1.5, c.delta)
+    Hd = mg.build_field_x_dense(c.nspins)
+    prec = {"tensor_sliced": mg.TENSOR_SLICED, "fp32_split": mg.FP32_SPLIT}[precision]
+    plan = mg.Plan(c.dim, [mg.DenseTerm(Hs), mg.DenseTerm(Hd)], drive_pair(mg, c), nvec=64, precision=prec)
+    psi = cuda(c.psi0)
+    plan.propagate(psi, 0.0, c.h, c.nsteps, "CF4")
+    out = psi.cpu().numpy()
+    f = oracle.Coeff(c.drive_a0, c.drive_ac, c.drive_as, c.drive_om)
+    P = oracle.Problem([oracle.longrange_dense(c.nspins, c.hz, 1.5, c.delta), oracle.field_x_dense(c.nspins)],
+                       [oracle.Coeff.const(), f], threaded=True)
+    for v in (0, 63):
+        ref = P.propagate(c.psi0[v], 0.0, c.h, c.nsteps, "CF4")
+        assert rel(out[v], ref) < tol, (precision, v, rel(out[v], ref))
