@@ -137,11 +137,15 @@ typedef enum {
  *                     MAGNUS_TENSOR_SLICED need real-valued dense terms (the drive may add
  *                     MAGNUS_TERM_FIELD_X terms); MAGNUS_TENSOR_SLICED also needs dim a multiple of
  *                     128.  MAGNUS_TENSOR_SLICED cuts every dense row (row scale 2^e_r) and every
- *                     state component column (scale 2^e_c) into 5 signed 7-bit digits, forms the 15
- *                     digit products of weight >= 2^-42 on the bf16 tensor cores (exact in FP32 over
- *                     128 columns) and carries their sums in int64; the neglected part of one output
- *                     entry is below dim * 2^-32 * max_j |H_rj| * max_j |w_j| (not part of the
- *                     paper, which computes in FP64 only).
+ *                     state component column (scale 2^e_c) into signed digits and forms their
+ *                     products exactly on the bf16 tensor cores, summing them in FP32 (exact within
+ *                     a chunk of K) and int64.  Linear generators (M2, CF4, CF4:3; tcgen05): values
+ *                     scaled to 31 bits, 4 digits of at most 128 in magnitude, the 10 digit pairs of
+ *                     level <= 3, chunks of 512 K; neglected part of one output entry below
+ *                     dim * 2^-29 * max_j |H_rj| * max_j |w_j|.  M4 (mma.sync): 5 signed 7-bit
+ *                     digits, the 15 pairs of weight >= 2^-42, chunks of 128; below
+ *                     dim * 2^-32 * max_j |H_rj| * max_j |w_j|.  (Not part of the paper, which
+ *                     computes in FP64 only.)
  *   barrier_timeout_s [0 = 4 s]: limit of every device-side wait at a grid barrier; a wait that runs
  *                     out makes the call return MAGNUS_ETIMEOUT and leaves the context usable
  *   test_skip_arrival [0]: testing only -- if nonzero, CTA 0 of the sparse/matrix-free propagation

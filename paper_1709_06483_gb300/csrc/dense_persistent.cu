@@ -367,6 +367,9 @@ __device__ __forceinline__ int cover_exponent(double m) {
 // ------------------------------------------------------------------ kernel
 // PREC: 0 FP64, 1 FP32 split, 2 sliced digits on mma.sync (5 x 7 bits), 3 sliced digits on tcgen05
 // (4 x 8 bits, linear generators; the product phase of dense_tc.cuh).
+constexpr int kEpiTiles = 4;   // 128-row tiles a block's rows can touch (at most 256 rows per block)
+constexpr int kEpiOwners = 8;  // CTAs whose partial tiles a tile is summed from
+
 template <bool REAL, bool TILED, int PREC>
 __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) {
   constexpr bool SPLIT = PREC == 1;
@@ -385,6 +388,10 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
   __shared__ unsigned long long s_cmax[kTcCols];
   __shared__ int s_cexp[kTcCols];
   __shared__ tcg::Bars tc_bars;
+  // tcgen05 epilogue: per (dense term, row tile of this block) the offsets of its partial tiles
+  __shared__ long long s_own[kMaxTerms][kEpiTiles][kEpiOwners];
+  __shared__ int s_nown[kMaxTerms][kEpiTiles];
+  __shared__ int s_epi_ok;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ty = tid >> 4, tx = tid & 15;
@@ -406,7 +413,7 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
   if (TC) {
     tc_geom.ndense = a.tc_ndense;
     tc_geom.T = a.tc_T;
-    tc_geom.chunk = (D % tcg::kChunkMax == 0) ? tcg::kChunkMax : tcg::kM;
+    tc_geom.chunk = tcg::chunk_for(D);
     tc_geom.C = (int)(D / tc_geom.chunk);
     tc_geom.N = a.tc_N;
     tc_geom.slots = a.tc_slots;
@@ -429,9 +436,17 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
 
   // Reduce per-thread per-vector sums (tiled: vectors tx + 16 q; warp-per-row: the lane's own
   // vector 0) to this block's partials, barrier, every block sums the partials (into s_tot).
-  auto reduce_and_share = [&](double (&sw)[4], double (&sp)[4]) -> bool {
+  auto reduce_and_share = [&](double (&sw)[4], double (&sp)[4], bool parts_written = false) -> bool {
     double *slot = partials + (size_t)(it & 1u) * G * nv * 2;
-    if (TILED) {
+    if (parts_written) {  // s_part[warp][v] already holds every warp's share (the tensor-core epilogue)
+      __syncthreads();
+      for (int v = tid; v < nv; v += blockDim.x) {
+        double y0 = 0.0, y1 = 0.0;
+        for (int w = 0; w < kDBlock / 32; w++) { y0 += s_part[w][v][0]; y1 += s_part[w][v][1]; }
+        slot[((size_t)b * nv + v) * 2] = y0;
+        slot[((size_t)b * nv + v) * 2 + 1] = y1;
+      }
+    } else if (TILED) {
 #pragma unroll
       for (int q = 0; q < 4; q++) {
         sw[q] += __shfl_xor_sync(kFull, sw[q], 16);
@@ -461,19 +476,34 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
       }
     }
     if (!grid_barrier(a.bar, G, a.spin_limit_ns)) return false;
-    // every block sums every vector's partials itself, in the same fixed order (one warp per
-    // vector): the totals are identical in all blocks and no second barrier is needed
-    for (int v = warp; v < nv; v += kDBlock / 32) {
-      double y0 = 0.0, y1 = 0.0;
-      for (int q = lane; q < (int)G; q += 32) {
-        y0 += slot[((size_t)q * nv + v) * 2];
-        y1 += slot[((size_t)q * nv + v) * 2 + 1];
+    // every block sums every vector's partials itself, in the same fixed order (warp w takes the
+    // vectors w, w + 8, ..., lane l the blocks l, l + 32, ...; the loads of all the warp's vectors go
+    // out together): the totals are identical in all blocks and no second barrier is needed
+    constexpr int kVpw = kVecMax / (kDBlock / 32);
+    double y0[kVpw], y1[kVpw];
+#pragma unroll
+    for (int i = 0; i < kVpw; i++) y0[i] = y1[i] = 0.0;
+    for (int q = lane; q < (int)G; q += 32) {
+      double p0[kVpw], p1[kVpw];
+#pragma unroll
+      for (int i = 0; i < kVpw; i++) {
+        const int v = warp + (kDBlock / 32) * i;
+        p0[i] = v < nv ? slot[((size_t)q * nv + v) * 2] : 0.0;
+        p1[i] = v < nv ? slot[((size_t)q * nv + v) * 2 + 1] : 0.0;
       }
-      y0 = warp_sum(y0);
-      y1 = warp_sum(y1);
-      if (lane == 0) {
-        s_tot[v][0] = y0;
-        s_tot[v][1] = y1;
+#pragma unroll
+      for (int i = 0; i < kVpw; i++) {
+        y0[i] += p0[i];
+        y1[i] += p1[i];
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < kVpw; i++) {
+      const int v = warp + (kDBlock / 32) * i;
+      const double t0 = warp_sum(y0[i]), t1 = warp_sum(y1[i]);
+      if (lane == 0 && v < nv) {
+        s_tot[v][0] = t0;
+        s_tot[v][1] = t1;
       }
     }
     __syncthreads();
@@ -824,7 +854,117 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
                 }
             }
         };
-        if (TILED) {
+        bool tc_epi = false;
+        const int64_t t_first = lo / tcg::kM;  // first 128-row tile of this block's rows
+        if (TC && R.mode == MODE_LINEAR) {
+          // epilogue of the tensor-core products: warp w takes the vectors w, w + 8, ..., its lanes
+          // the block's rows, so that the partial tiles (row-contiguous per column) and the vectors
+          // are read and written in consecutive runs.  y sums the terms in term order and each
+          // tile's owners in CTA order, as tc_term does.
+          // the CTAs holding each (dense term, 128-row tile) of this block's rows and the offsets of
+          // their partial tiles, in CTA order: a small table made once per iteration (the general
+          // path below serves blocks whose rows or tiles do not fit it)
+          if (tid == 0) s_epi_ok = (hi <= lo) || ((hi - 1) / tcg::kM - t_first < kEpiTiles);
+          __syncthreads();
+          if (tid < kMaxTerms * kEpiTiles && s_epi_ok) {
+            const int k = tid / kEpiTiles, ti = tid % kEpiTiles;
+            int n_own = 0;
+            const int64_t rt = t_first + ti;
+            if (k < nt && sT[k].kind == MAGNUS_TERM_DENSE && lo < hi && rt * tcg::kM < hi) {
+              const long long tile = (long long)a.tc_dslot[k] * tc_geom.T + rt;
+              int bf, bl;
+              tcg::tile_owners(tile, tc_geom, (int)G, &bf, &bl);
+              for (int bb = bf; bb <= bl; bb++) {
+                const long long b_lo = tcg::range_lo(bb, (int)G, tc_geom.N);
+                if (b_lo == tcg::range_lo(bb + 1, (int)G, tc_geom.N)) continue;
+                if (n_own == kEpiOwners) {
+                  s_epi_ok = 0;  // more owners than the table holds (benign race: every writer stores 0)
+                  break;
+                }
+                s_own[k][ti][n_own++] = ((long long)bb * tc_geom.slots + (tile - b_lo / tc_geom.C)) *
+                                        (long long)(tcg::kN * tcg::kM);
+              }
+            }
+            s_nown[k][ti] = n_own;
+          }
+          for (int v = lane; v < kVecMax; v += 32) {
+            s_part[warp][v][0] = 0.0;
+            s_part[warp][v][1] = 0.0;
+          }
+          __syncthreads();
+          tc_epi = s_epi_ok != 0;
+        }
+        if (tc_epi) {
+          // y[r][v] = sum_k coef_k (H_k W)[r][v] (+ field terms), terms in order, owners in CTA order
+          auto epi_y = [&](int64_t r, int v) {
+            double2 y = make_double2(0.0, 0.0);
+            const int ti = (int)(r / tcg::kM - t_first), rr = (int)(r % tcg::kM);
+            for (int k = 0; k < nt; k++) {
+              const double coef = R.bg[k];
+              if (coef == 0.0) continue;
+              if (sT[k].kind == MAGNUS_TERM_DENSE) {
+                double sx = 0.0, sy = 0.0;
+                const int no = s_nown[k][ti];
+                for (int o = 0; o < no; o++) {
+                  const double *Pt = a.tc_P + s_own[k][ti][o] + rr;
+                  sx += Pt[(size_t)(2 * v) * tcg::kM];
+                  sy += Pt[(size_t)(2 * v + 1) * tcg::kM];
+                }
+                y.x = fma(coef, sx, y.x);
+                y.y = fma(coef, sy, y.y);
+              } else if (sT[k].kind == MAGNUS_TERM_FIELD_X) {
+                y = rfma(coef, fieldx_at(sT[k].nspins, src + (int64_t)v * D, r), y);
+              }
+            }
+            return y;
+          };
+          for (int v = warp; v < nv; v += kDBlock / 32) {
+            double pw = 0.0, pp = 0.0;
+            unsigned long long mx = 0ull, my = 0ull;
+            if (s_act[v])
+              for (int64_t r0 = lo; r0 < hi; r0 += 64) {  // two rows per lane, their loads together
+                const int64_t ra = r0 + lane, rb = r0 + 32 + lane;
+                const bool ia = ra < hi, ib = rb < hi;
+                double2 ya = make_double2(0.0, 0.0), yb = ya, wa = ya, wb = ya, pa = ya, pb = ya;
+                const int64_t xa = (int64_t)v * D + ra, xb = (int64_t)v * D + rb;
+                if (ia) { ya = epi_y(ra, v); wa = ldv(src + xa); if (j > 1) pa = nxt[xa]; }
+                if (ib) { yb = epi_y(rb, v); wb = ldv(src + xb); if (j > 1) pb = nxt[xb]; }
+                if (ia) {
+                  ya = rfma(-shift, wa, ya);
+                  dst[xa] = ya;
+                  mx = max(mx, (unsigned long long)__double_as_longlong(fabs(ya.x)));
+                  my = max(my, (unsigned long long)__double_as_longlong(fabs(ya.y)));
+                  pa = cfma(dj, ya, (j == 1) ? cmul(d0, wa) : pa);
+                  nxt[xa] = pa;
+                  pw += cabs2(ya);
+                  pp += cabs2(pa);
+                }
+                if (ib) {
+                  yb = rfma(-shift, wb, yb);
+                  dst[xb] = yb;
+                  mx = max(mx, (unsigned long long)__double_as_longlong(fabs(yb.x)));
+                  my = max(my, (unsigned long long)__double_as_longlong(fabs(yb.y)));
+                  pb = cfma(dj, yb, (j == 1) ? cmul(d0, wb) : pb);
+                  nxt[xb] = pb;
+                  pw += cabs2(yb);
+                  pp += cabs2(pb);
+                }
+              }
+            pw = warp_sum(pw);
+            pp = warp_sum(pp);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+              mx = max(mx, __shfl_xor_sync(kFull, mx, o));
+              my = max(my, __shfl_xor_sync(kFull, my, o));
+            }
+            if (lane == 0) {
+              s_part[warp][v][0] = pw;
+              s_part[warp][v][1] = pp;
+              s_cmax[2 * v] = mx;
+              s_cmax[2 * v + 1] = my;
+            }
+          }
+        } else if (TILED) {
           for (int64_t r0 = lo; r0 < hi; r0 += kTM) {
             double2 y[2][4];
             if (R.mode == MODE_M4) {
@@ -866,7 +1006,11 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
           }
         }
         if (!TILED) sw[0] = warp_sum(sw[0]), sp[0] = warp_sum(sp[0]);
-        if (TC && j < a.m_max) {  // this block's column maxima -> the epilogue slot (published by the next barrier)
+        if (tc_epi && j < a.m_max) {  // this block's column maxima (written above) -> the epilogue slot
+          __syncthreads();
+          for (int c = tid; c < 2 * nv; c += blockDim.x)
+            if (s_cmax[c]) atomicMax(&a.colmax[3 * kTcCols + c], s_cmax[c]);
+        } else if (TC && j < a.m_max) {  // this block's column maxima -> the epilogue slot (published by the next barrier)
           for (int c = tid; c < kTcCols; c += blockDim.x) s_cmax[c] = 0ull;
           __syncthreads();
 #pragma unroll
@@ -887,25 +1031,26 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
           for (int c = tid; c < 2 * nv; c += blockDim.x)
             if (s_cmax[c]) atomicMax(&a.colmax[3 * kTcCols + c], s_cmax[c]);
         }
-        if (!reduce_and_share(sw, sp)) { fail(MAGNUS_ETIMEOUT); return; }
-        if (warp == 0) {
+        if (!reduce_and_share(sw, sp, tc_epi)) { fail(MAGNUS_ETIMEOUT); return; }
+        if (warp == 0) {  // every vector's stop test, one lane per vector (they are independent)
           int any = 0, bad = 0;
           const double adj = sqrt(cabs2(dj));
-          if (lane == 0)
-            for (int v = 0; v < nv; v++) {
-              if (!s_act[v]) continue;
-              const double tw = s_tot[v][0], tp = s_tot[v][1];
-              const double ej = adj * sqrt(tw), pn = sqrt(tp);
-              if (!isfinite(ej) || !isfinite(pn)) bad = 1;
-              if (ej + s_ep[v] <= a.tol_abs + a.tol_rel * pn) {
-                s_act[v] = 0;
-                s_m[v] = j;
-                s_pn[v] = pn;
-              } else {
-                s_ep[v] = ej;
-                any = 1;
-              }
+          for (int v = lane; v < nv; v += 32) {
+            if (!s_act[v]) continue;
+            const double tw = s_tot[v][0], tp = s_tot[v][1];
+            const double ej = adj * sqrt(tw), pn = sqrt(tp);
+            if (!isfinite(ej) || !isfinite(pn)) bad = 1;
+            if (ej + s_ep[v] <= a.tol_abs + a.tol_rel * pn) {
+              s_act[v] = 0;
+              s_m[v] = j;
+              s_pn[v] = pn;
+            } else {
+              s_ep[v] = ej;
+              any = 1;
             }
+          }
+          any = __any_sync(kFull, any);
+          bad = __any_sync(kFull, bad);
           if (lane == 0) s_flag = bad ? 2 : (any ? 0 : 1);
         }
         __syncthreads();
@@ -1065,8 +1210,10 @@ cudaError_t launch_slice_dense_tc(const double *Hr, int rs, int64_t D, void *dig
 
 size_t dense_tc_smem_bytes() { return tcg::kSmemBytes; }
 
+int dense_tc_chunk(int64_t D) { return tcg::chunk_for(D); }
+
 int dense_tc_slots(int ndense, int64_t D, int grid) {
-  const long long T = D / tcg::kM, C = D / ((D % tcg::kChunkMax == 0) ? tcg::kChunkMax : tcg::kM);
+  const long long T = D / tcg::kM, C = D / tcg::chunk_for(D);
   const long long N = (long long)ndense * T * C;
   int slots = 1;
   for (int b = 0; b < grid; b++) {

@@ -1,18 +1,19 @@
 // Exact-digit dense products on the 5th-generation tensor cores (MAGNUS_TENSOR_SLICED, linear
 // generators).  Y_k = H_k W for every dense term k and one set W of up to 128 real columns (the real
 // and imaginary parts of up to 64 states), with H_k and W given as 4 signed 8-bit digits per value:
-//     H[r][j] = 2^{e_r} sum_t h_t[r][j] 2^{-8(t+1)},   W[c][j] = 2^{e_c} sum_u w_u[c][j] 2^{-8(u+1)},
-// |h_0|, |w_0| <= 256, the other digits <= 128, all exact in bf16.  The digit products of level
-// g = t + u <= 3 (10 of the 16 pairs) are summed by tcgen05.mma (kind::f16) into four FP32
-// accumulators in tensor memory, one 128 x 128 tile each (all 512 TMEM columns):
-//   * levels 0 and 1 restart every chunk of 256 K values (128 if D is not a multiple of 256); per K
-//     index |h_0 w_0| <= 2^16 and |h_0 w_1 + h_1 w_0| <= 2^16, so every partial sum is an integer
-//     of magnitude at most 2^24, which FP32 holds exactly; the chunk sums are moved to int64
-//     (S = 2^8 L_0 + L_1) after each chunk;
+//     H[r][j] = 2^{e_r} sum_t h_t[r][j] 2^{-8(t+1) + 1},   W[c][j] = 2^{e_c} sum_u w_u[c][j] 2^{-8(u+1) + 1},
+// (a value scaled to 31 bits, N = round(x 2^{31-e}), cut into balanced base-256 digits) with every
+// |h_t|, |w_u| <= 128, all exact in bf16.  The digit products of level g = t + u <= 3 (10 of the 16
+// pairs) are summed by tcgen05.mma (kind::f16) into four FP32 accumulators in tensor memory, one
+// 128 x 128 tile each (all 512 TMEM columns):
+//   * levels 0 and 1 restart every chunk of 512 K values (the largest of 512, 256, 128 dividing D);
+//     per K index |h_0 w_0| <= 2^14 and |h_0 w_1 + h_1 w_0| <= 2^15, so every partial sum is an
+//     integer of magnitude at most 2^24, which FP32 holds exactly; the chunk sums are moved to
+//     int64 (S = 2^8 L_0 + L_1) after each chunk;
 //   * levels 2 and 3 (weights 2^-16 and 2^-24 of level 0) accumulate in FP32 over the whole range;
 //     their rounding is below 2^-40 of the product scale.
-// The value is Y[r][c] = 2^{e_r + e_c - 24} (S + (L_2 + L_3 2^-8) 2^-8).  The truncation after four
-// digits and the omitted levels 4..6 leave below D * 2^-30 * max_j |H_rj| * max_j |W_cj| per entry.
+// The value is Y[r][c] = 2^{e_r + e_c - 22} (S + (L_2 + L_3 2^-8) 2^-8).  The truncation after four
+// digits and the omitted levels 4..6 leave below D * 2^-29 * max_j |H_rj| * max_j |W_cj| per entry.
 //
 // Work split: the items (dense term, 128-row tile, K chunk) in that order are cut into G contiguous
 // ranges, one per CTA; a CTA accumulates consecutive chunks of the same tile and writes one FP64
@@ -40,7 +41,8 @@ constexpr int kSl = 4;                          // digits per value
 constexpr int kM = 128;                         // rows per tile (MMA M)
 constexpr int kN = 128;                         // columns (MMA N)
 constexpr int kKS = 32;                         // K per pipeline stage
-constexpr int kChunkMax = 256;                  // K per exact chunk (256, or 128 when D is not a multiple of 256)
+constexpr int kChunkMax = 512;                  // K per exact chunk (512, or the largest of 256, 128 dividing D)
+constexpr int kNBits = 31;                      // values scaled to kNBits bits before cutting into digits
 constexpr int kNS = 3;                          // ring depth
 constexpr uint32_t kBox = 8 * kM * kSl * 2;     // 8 KB: one TMA box (8 K x 128 rows x 4 digits)
 constexpr uint32_t kStageA = 4 * kBox;          // 32 KB: the 4 K-cores of a stage
@@ -85,19 +87,22 @@ __host__ __device__ inline size_t tiled_offset(int64_t D, int64_t r, int64_t j, 
   return ((((size_t)(r / kM) * (size_t)(D / 8) + (size_t)(j / 8)) * kSl + t) * kM + (size_t)(r % kM)) * 8 + (size_t)(j % 8);
 }
 
-// x (finite, |x| < 2^e) -> N = round(x 2^{32 - e}), |N| <= 2^32, from the bits of x (integer pipe
+// K per exact chunk for dimension D (a multiple of 128)
+__host__ __device__ inline int chunk_for(int64_t D) { return D % 512 == 0 ? 512 : (D % 256 == 0 ? 256 : 128); }
+
+// x (finite, |x| < 2^e) -> N = round(x 2^{31 - e}), |N| <= 2^31, from the bits of x (integer pipe
 // only: on this part the FP64 pipe is the scarce one)
 __device__ __forceinline__ long long fixed32(double x, int e) {
   const long long bits = __double_as_longlong(x);
   const int ex = (int)((bits >> 52) & 0x7FF);
-  if (ex == 0) return 0;                            // zero (or subnormal: below 2^-1022 <= 2^{e-32} here)
+  if (ex == 0) return 0;                            // zero (or subnormal: below 2^-1022 <= 2^{e-31} here)
   const long long mant = (bits & 0xFFFFFFFFFFFFFll) | 0x10000000000000ll;
-  const int sh = e + 1043 - ex;                     // x 2^{32-e} = mant 2^{-sh}; sh >= 21 as |x| < 2^e
+  const int sh = e + 1075 - kNBits - ex;            // x 2^{31-e} = mant 2^{-sh}; sh >= 22 as |x| < 2^e
   long long n = sh >= 63 ? 0 : ((mant >> (sh - 1)) + 1) >> 1;  // round half up in magnitude
   return bits < 0 ? -n : n;
 }
 
-// N -> 4 balanced base-256 digits d_t (N = sum_t d_t 2^{8(3-t)}, |d_0| <= 256, |d_t| <= 128)
+// N -> 4 balanced base-256 digits d_t (N = sum_t d_t 2^{8(3-t)}, every |d_t| <= 128 for |N| <= 2^31)
 __device__ __forceinline__ void digits4(long long n, int (&d)[kSl]) {
   d[0] = (int)((n + (1ll << 23)) >> 24);
   n -= (long long)d[0] << 24;
@@ -289,8 +294,8 @@ __device__ bool gemm_phase(const __nv_bfloat16 *hd, const __nv_bfloat16 *wd, con
         for (int q = 0; q < 16; q++) {
           const int cc = (int)col + q;
           const double lo = ((double)__uint_as_float(v2[q]) + (double)__uint_as_float(v3[q]) * 0x1.0p-8) * 0x1.0p-8;
-          // 2^{e_r + e_c - 24} from its exponent bits when it is a normal number
-          const int bx = er + ec[cc] - 24 + 1023;
+          // 2^{e_r + e_c - 2 kNBits + 40} (= 2^{e_r + e_c - 22}) from its exponent bits when it is normal
+          const int bx = er + ec[cc] - 2 * kNBits + 40 + 1023;
           const double sc = (bx > 0 && bx < 2047) ? __longlong_as_double((long long)bx << 52) : ldexp(1.0, bx - 1023);
           out[(size_t)cc * kM + row] = fma((double)S[c16 * 16 + q], sc, lo * sc);
         }

@@ -301,7 +301,7 @@ magnus_status run_persistent(magnus_plan_t p, void *psi, int64_t nexp, magnus_st
     a.tc_ndense = p->tc_ndense;
     a.tc_slots = p->tc_slots;
     a.tc_T = (int)(p->dim / 128);
-    a.tc_N = (long long)p->tc_ndense * a.tc_T * (p->dim / ((p->dim % 256 == 0) ? 256 : 128));
+    a.tc_N = (long long)p->tc_ndense * a.tc_T * (p->dim / dense_tc_chunk(p->dim));
     a.tc_spins = 1ll << 26;
     for (int k = 0; k < kMaxTerms; k++) a.tc_dslot[k] = p->tc_dslot[k];
     a.tc_hd = p->tc_hd;

@@ -287,6 +287,7 @@ cudaError_t launch_dense_persistent(const PersistArgs &a, bool real_valued, int 
 // exponents at rexp.
 cudaError_t launch_slice_dense_tc(const double *Hr, int rs, int64_t D, void *digits, int *rexp, cudaStream_t st);
 size_t dense_tc_smem_bytes();
+int dense_tc_chunk(int64_t D);  // K per exact chunk of the tcgen05 digit products
 int dense_tc_slots(int ndense, int64_t D, int grid);
 
 // Dense term (complex128, real parts used) -> bf16 digits [5][D][D] and row exponents [D].

@@ -542,160 +542,6 @@ static __device__ __forceinline__ double2 mf_xxz_row_z(const Ctx &c, const long 
   return make_double2(fma(cr, xr.x, bonds.x), fma(cr, xr.y, bonds.y));
 }
 
-// ------------------------------------------------ fixed-point CSR rows, loads issued early
-// The same row sums as csr_row_zsum / csr_row_zprod_w from entry ranges already loaded, so that a
-// caller can issue every load that needs no earlier one (row pointers, exponents, the vector entry
-// x_r) before the first gathers.
-static __device__ __forceinline__ longlong2 zsum_range(const int32_t *col, int len, const longlong2 *z) {
-  longlong2 acc = make_longlong2(0, 0);
-  int k = 0;
-  for (; k + kRound <= len; k += kRound) {
-    int c[kRound];
-    longlong2 v[kRound];
-#pragma unroll
-    for (int q = 0; q < kRound; q++) c[q] = __ldg(col + k + q);
-#pragma unroll
-    for (int q = 0; q < kRound; q++) v[q] = ldz(z + c[q]);
-#pragma unroll
-    for (int q = 0; q < kRound; q++) zadd(acc, v[q]);
-  }
-  for (; k < len; k++) zadd(acc, ldz(z + __ldg(col + k)));
-  return acc;
-}
-
-// rows of one length P, 16-byte aligned (P a multiple of 4): the columns as 16-byte loads
-static __device__ __forceinline__ longlong2 zsum_vec4(const int32_t *col, int P, const longlong2 *z) {
-  longlong2 acc = make_longlong2(0, 0);
-  const int4 *c4 = reinterpret_cast<const int4 *>(col);
-  int k = 0;
-  for (; k + 8 <= P; k += 8) {
-    const int4 a = __ldg(c4 + k / 4), b = __ldg(c4 + k / 4 + 1);
-    longlong2 v[8];
-    v[0] = ldz(z + a.x); v[1] = ldz(z + a.y); v[2] = ldz(z + a.z); v[3] = ldz(z + a.w);
-    v[4] = ldz(z + b.x); v[5] = ldz(z + b.y); v[6] = ldz(z + b.z); v[7] = ldz(z + b.w);
-#pragma unroll
-    for (int q = 0; q < 8; q++) zadd(acc, v[q]);
-  }
-  for (; k < P; k += 4) {
-    const int4 a = __ldg(c4 + k / 4);
-    const longlong2 v0 = ldz(z + a.x), v1 = ldz(z + a.y), v2 = ldz(z + a.z), v3 = ldz(z + a.w);
-    zadd(acc, v0); zadd(acc, v1); zadd(acc, v2); zadd(acc, v3);
-  }
-  return acc;
-}
-
-// product row with the warp's longest row as the trip count (call with the warp converged)
-static __device__ __forceinline__ longlong2 zprod_range_w(const int32_t *col, const long long *fv, int len,
-                                                          const longlong2 *z) {
-  const int lmax = __reduce_max_sync(__activemask(), len);
-  longlong2 acc = make_longlong2(0, 0);
-  int k = 0;
-  for (; k + kRound <= lmax; k += kRound) {
-    int c[kRound];
-    long long a[kRound];
-    longlong2 v[kRound];
-#pragma unroll
-    for (int q = 0; q < kRound; q++) c[q] = (k + q < len) ? __ldg(col + k + q) : -1;
-#pragma unroll
-    for (int q = 0; q < kRound; q++) a[q] = (k + q < len) ? __ldg(fv + k + q) : 0ll;
-#pragma unroll
-    for (int q = 0; q < kRound; q++) v[q] = (c[q] >= 0) ? ldz(z + c[q]) : make_longlong2(0, 0);
-#pragma unroll
-    for (int q = 0; q < kRound; q++) {
-      acc.x += __mul64hi(a[q], v[q].x);
-      acc.y += __mul64hi(a[q], v[q].y);
-    }
-  }
-  for (; k < lmax; k++) {
-    const bool in = k < len;
-    const long long a = in ? __ldg(fv + k) : 0ll;
-    const longlong2 v = in ? ldz(z + __ldg(col + k)) : make_longlong2(0, 0);
-    acc.x += __mul64hi(a, v.x);
-    acc.y += __mul64hi(a, v.y);
-  }
-  return acc;
-}
-
-#ifndef MG_EARLY_ROWS
-#define MG_EARLY_ROWS 0
-#endif
-#ifndef MG_EARLY_VEC4
-#define MG_EARLY_VEC4 1
-#endif
-#ifndef MG_EARLY_ORDER
-#define MG_EARLY_ORDER 1
-#endif
-#ifndef MG_EARLY_XR
-#define MG_EARLY_XR 1
-#endif
-#ifndef MG_EARLY_NT4
-#define MG_EARLY_NT4 0
-#endif
-
-// sum_k w_k (H_k x)[r] - shift x[r] for CSR terms that are all pattern or product terms: the row
-// pointers, the exponents and x_r are loaded first, the rows of one length (their columns need no
-// row pointer) are summed before the others, and the weighted sums combine in term order -- the
-// FP64 operations and their order are those of the general path, so the result is the same.
-// NT: at least the plan's number of terms (2 for the common chain + drive, else kMaxTerms), so
-// that the per-term registers exist only for terms that can be there
-template <int NT>
-static __device__ __forceinline__ double2 combo_z_early(const Ctx &c, const ExpRec &R, const double *wz, double shift,
-                                                       const double2 *x, const longlong2 *z, int zs, int64_t r,
-                                                       double2 &xr) {
-  int64_t e0[NT], e1[NT];
-  int fe[NT];
-#pragma unroll
-  for (int k = 0; k < NT; k++) {
-    e0[k] = e1[k] = 0;
-    fe[k] = 0;
-    if (k >= c.nt) continue;
-    const Term &t = c.T[k];
-    if (!t.pattern) fe[k] = __ldg(t.fexp + r);
-    if (t.hbase) continue;  // sliced rows: their head needs no row pointer
-    if (t.plen) {
-      e0[k] = r * t.plen;
-      e1[k] = e0[k] + t.plen;
-    } else {
-      e0[k] = __ldg(t.rowptr + r);
-      e1[k] = __ldg(t.rowptr + r + 1);
-    }
-  }
-  if (MG_EARLY_XR) xr = ldv(x + r);
-  longlong2 acc[NT];
-#pragma unroll
-  for (int k = 0; k < NT; k++) {  // rows of one length first
-    acc[k] = make_longlong2(0, 0);
-    if (k >= c.nt || !MG_EARLY_ORDER) continue;
-    const Term &t = c.T[k];
-    if (!(t.pattern && t.plen && !t.hbase)) continue;
-    acc[k] = (MG_EARLY_VEC4 && (t.plen & 3) == 0) ? zsum_vec4(t.col + e0[k], t.plen, z)
-                                                   : zsum_range(t.col + e0[k], t.plen, z);
-  }
-#pragma unroll
-  for (int k = 0; k < NT; k++) {
-    if (k >= c.nt) continue;
-    const Term &t = c.T[k];
-    if (MG_EARLY_ORDER && t.pattern && t.plen && !t.hbase) continue;
-    if (!MG_EARLY_ORDER && t.pattern && t.plen && !t.hbase && MG_EARLY_VEC4 && (t.plen & 3) == 0)
-      acc[k] = zsum_vec4(t.col + e0[k], t.plen, z);
-    else if (t.hbase)
-      acc[k] = t.pattern ? sl_row_zsum(t, z, r) : sl_row_zprod(t, z, r);
-    else if (t.pattern)
-      acc[k] = zsum_range(t.col + e0[k], (int)(e1[k] - e0[k]), z);
-    else
-      acc[k] = zprod_range_w(t.col + e0[k], t.fval + e0[k], (int)(e1[k] - e0[k]), z);
-  }
-  double2 y = make_double2(0.0, 0.0);
-#pragma unroll
-  for (int k = 0; k < NT; k++) {
-    if (k >= c.nt) continue;
-    const Term &t = c.T[k];
-    y = t.pattern ? rfma(wz[k], unfix2(acc[k], zs), y) : rfma(R.bg[k], unfix2(acc[k], zs - fe[k] - 2), y);
-  }
-  if (!MG_EARLY_XR) xr = ldv(x + r);
-  return rfma(-shift, xr, y);
-}
-
 template <int FAM>
 struct Op {
   // (H_k x)[r]
@@ -757,12 +603,6 @@ struct Op {
                        : mf_xxz_row(c, c.jb, R.bg[0], shift, x, r, xr);
       return rfma(wz[1], unfix2(fieldx_row_zsum(c.n, z, r), zs), y);
     } else {
-#if MG_EARLY_ROWS
-      bool allz = true;
-      for (int k = 0; k < c.nt; k++) allz &= (c.T[k].pattern || c.T[k].fval) != 0;
-      if (allz && c.nt <= 2) return combo_z_early<2>(c, R, wz, shift, x, z, zs, r, xr);
-      if (MG_EARLY_NT4 && allz) return combo_z_early<kMaxTerms>(c, R, wz, shift, x, z, zs, r, xr);
-#endif
       double2 y = make_double2(0.0, 0.0);
       for (int k = 0; k < c.nt; k++) {
         const Term &t = c.T[k];
