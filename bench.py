@@ -483,6 +483,9 @@ def run_all_workloads(args, mg, mi, local):
                                                  local, "20-spin XXZ chain, matrix-free, CF4, h = 0.005, 100 steps")),
         ("cfg3_dense13", lambda: dense_workload(mg, mi, local, nvec=64, nspins=13, rate_steps=(2, 4, 100),
                                                 err_states=4, err_steps=100)),
+        ("cfg3_dense13_m4_tensor", lambda: dense_workload(mg, mi, local, nvec=64, nspins=13, rate_steps=(2, 0, 50),
+                                                          err_states=4, err_steps=50, variant="M4",
+                                                          modes=("fp64", "tensor_sliced"))),
         ("cfg4_batch512", lambda: batch_workload(mg, mi, local, steps=100, storage="csr", fixed=True)),
         ("cfg5_adjoint16", lambda: adjoint_workload(mg, mi, local, nsteps=1000)),
     ]
@@ -541,8 +544,12 @@ def dense_workload(mg, mi, local, nvec=64, nspins=13, rate_steps=(2, 4, 100), er
              "matvec_gbs": round(bytes_it * nmv / (kms / 1e3) / 1e9, 2),
              "fp64_equiv_tflops": round(2 * fma_it * nmv / (kms / 1e3) / 1e12, 4), "clocks": clk.summary()}
         if prec == "tensor_sliced":
-            # issued bf16 MMA work (tcgen05, Cf4): 10 digit pairs x 2 flops x D^2 x 128 columns per dense term
-            r["bf16_tflops_issued"] = round(10 * 2 * D * D * 128 * 2 * nmv / (kms / 1e3) / 1e12, 2)
+            # issued bf16 MMA work (tcgen05): 10 digit pairs x 2 flops x D^2 x 128 columns per dense term
+            # and product phase; phases per Leja iteration: 1 (linear generators), 2 for M4 (u_k = H_k w,
+            # then the one commutator pair of the two dense terms)
+            phases = 2 if variant == "M4" else 1
+            r["product_phases_per_iteration"] = phases
+            r["bf16_tflops_issued"] = round(phases * 10 * 2 * D * D * 128 * 2 * nmv / (kms / 1e3) / 1e12, 2)
         if prec == "fp64":
             r["roofline"] = {"bound": "alu", "achieved": r["fp64_equiv_tflops"], "peak": round(FP64_PEAK_TFLOPS, 4),
                              "unit": "TFLOP/s", "frac": round(r["fp64_equiv_tflops"] / FP64_PEAK_TFLOPS, 4)}
@@ -584,7 +591,7 @@ def dense_workload(mg, mi, local, nvec=64, nspins=13, rate_steps=(2, 4, 100), er
                                           if "bf16_tflops" in peaks else
                                           "1900 TFLOP/s bf16 burst, of fallback (no MEASURED_PEAKS.json)"),
                           "work": "10 bf16 digit-pair products x 2 flops x dim^2 x 128 columns per dense term per "
-                                  "Leja iteration"}
+                                  "product phase (1 per Leja iteration, 2 for M4)"}
     f64 = res.get("fp64")
     return {"workload": f"long-range chain, {nspins} spins, dense H_s and sum sx (2 x {16 * D * D / 1e9:.2f} GB "
                         f"complex128), {nvec} states, {variant}, h = 0.01",

@@ -44,7 +44,9 @@ typedef enum {
   MAGNUS_ECUDA = 3,      /* a CUDA call failed (see magnus_last_error)                   */
   MAGNUS_ENOCONV = 4,    /* a Leja polynomial reached m_max without meeting the tolerance */
   MAGNUS_ENONFINITE = 5, /* a norm became NaN or Inf                                     */
-  MAGNUS_ETIMEOUT = 6    /* a device-side wait gave up (bounded spin)                     */
+  MAGNUS_ETIMEOUT = 6,   /* a device-side wait gave up (bounded spin)                     */
+  MAGNUS_EDRIFT = 7      /* a substep changed the state's norm by more than options.norm_check
+                            allows (exp(-i tau K) of a Hermitian K keeps the norm)         */
 } magnus_status;
 
 typedef enum {
@@ -139,12 +141,12 @@ typedef enum {
  *                     128.  MAGNUS_TENSOR_SLICED cuts every dense row (row scale 2^e_r) and every
  *                     state component column (scale 2^e_c) into signed digits and forms their
  *                     products exactly on the bf16 tensor cores, summing them in FP32 (exact within
- *                     a chunk of K) and int64.  Linear generators (M2, CF4, CF4:3; tcgen05): values
- *                     scaled to 31 bits, 4 digits of at most 128 in magnitude, the 10 digit pairs of
- *                     level <= 3, chunks of 512 K; neglected part of one output entry below
- *                     dim * 2^-29 * max_j |H_rj| * max_j |w_j|.  M4 (mma.sync): 5 signed 7-bit
- *                     digits, the 15 pairs of weight >= 2^-42, chunks of 128; below
- *                     dim * 2^-32 * max_j |H_rj| * max_j |w_j|.  (Not part of the paper, which
+ *                     a chunk of K) and int64, on tcgen05: values scaled to 31 bits, 4 digits of at
+ *                     most 128 in magnitude, the 10 digit pairs of level <= 3, chunks of 512 K;
+ *                     neglected part of one output entry below dim * 2^-29 * max_j |H_rj| *
+ *                     max_j |w_j|.  Every generator: M2, CF4, CF4:3 one product phase per Leja
+ *                     iteration; M4 one for u_k = H_k w and one per commutator pair (H_k u_l and
+ *                     H_l u_k from the digits of u_l and u_k).  (Not part of the paper, which
  *                     computes in FP64 only.)
  *   barrier_timeout_s [0 = 4 s]: limit of every device-side wait at a grid barrier; a wait that runs
  *                     out makes the call return MAGNUS_ETIMEOUT and leaves the context usable
@@ -182,6 +184,13 @@ typedef enum {
  *                     float64 copy, no pattern or fixed-point rows): the plain FP64 path of the paper,
  *                     kept as the baseline the faster paths are measured against.  Real storage
  *                     (MAGNUS_TERM_*_REAL) is unaffected.  _reserved must be 0.
+ *   norm_check [0 = off]: a posteriori check of every substep (plans; batches do not check).  The
+ *                     Leja parameters come from a spectral interval; Gershgorin encloses the
+ *                     spectrum, the Lanczos interval (MAGNUS_INTERVAL_LANCZOS) does not prove it.
+ *                     Every exponential of a Hermitian generator keeps the norm, so a substep whose
+ *                     | ||p|| - ||v|| | exceeds norm_check * (tol_abs + tol_rel ||v||) + 1e-13 ||v||
+ *                     ends the call with MAGNUS_EDRIFT (p the substep's result, v its input).  The
+ *                     largest relative drift is reported in magnus_stats.norm_drift either way.
  */
 typedef enum {
   MAGNUS_ROWS_AUTO = 0,   /* the library's choice (MAGNUS_ROWS_CSR) */
@@ -205,6 +214,7 @@ typedef struct {
   int32_t row_layout;
   int32_t plain_values;
   int32_t _reserved;
+  double norm_check;
 } magnus_options;
 
 typedef struct {
@@ -221,6 +231,8 @@ typedef struct {
   int32_t block;        /* threads per CTA                                    */
   int32_t fixed_sums;   /* 1 if the call's matvecs ran in fixed point (options.fixed_sums)      */
   int32_t row_layout;   /* the fixed-point CSR rows' layout (magnus_row_layout; 0: not such a call) */
+  double norm_drift;    /* largest | ||p|| - ||v|| | / ||v|| over the call's substeps and states (p the
+                           substep's result, v its input): 0 up to rounding and the Leja tolerance */
 } magnus_stats;
 
 typedef struct magnus_plan_s *magnus_plan_t;

@@ -17,7 +17,7 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libmagnus_gb300.so")
 
-OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ENONFINITE, ETIMEOUT = range(7)
+OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ENONFINITE, ETIMEOUT, EDRIFT = range(8)
 M4, CF4, CF4_3, M2, M6 = 1, 2, 3, 4, 5
 VARIANTS = {"M4": M4, "CF4": CF4, "CF4_3": CF4_3, "M2": M2, "M6": M6}
 TERM_CSR, TERM_DENSE, TERM_XXZ, TERM_FIELD_X, TERM_CSR_REAL, TERM_DENSE_REAL = 0, 1, 2, 3, 4, 5
@@ -58,14 +58,16 @@ class Options(C.Structure):
     _fields_ = [("tol_rel", C.c_double), ("tol_abs", C.c_double), ("rho_max", C.c_double), ("m_max", C.c_int32),
                 ("nvec", C.c_int32), ("ctas", C.c_int32), ("precision", C.c_int32), ("barrier_timeout_s", C.c_double),
                 ("test_skip_arrival", C.c_int32), ("interval", C.c_int32), ("fixed_sums", C.c_int32),
-                ("row_layout", C.c_int32), ("plain_values", C.c_int32), ("_reserved", C.c_int32)]
+                ("row_layout", C.c_int32), ("plain_values", C.c_int32), ("_reserved", C.c_int32),
+                ("norm_check", C.c_double)]
 
 
 class Stats(C.Structure):
     _fields_ = [("n_exp", C.c_int64), ("n_substeps", C.c_int64), ("n_matvec", C.c_int64),
                 ("n_termapply", C.c_int64), ("max_m", C.c_int32), ("status", C.c_int32),
                 ("m_log", C.POINTER(C.c_int32)), ("m_log_cap", C.c_int64), ("kernel_ms", C.c_double),
-                ("grid", C.c_int32), ("block", C.c_int32), ("fixed_sums", C.c_int32), ("row_layout", C.c_int32)]
+                ("grid", C.c_int32), ("block", C.c_int32), ("fixed_sums", C.c_int32), ("row_layout", C.c_int32),
+                ("norm_drift", C.c_double)]
 
 
 class BatchItem(C.Structure):
@@ -272,7 +274,7 @@ class Plan:
 
     def __init__(self, dim, terms, drives, tol=1e-10, tol_abs=None, rho_max=4.0, m_max=100, nvec=1, ctas=0,
                  precision=FP64, stream=None, barrier_timeout_s=0.0, test_skip_arrival=0, interval="gershgorin",
-                 fixed_sums=True, rows="auto", plain_values=False):
+                 fixed_sums=True, rows="auto", plain_values=False, norm_check=0.0):
         import torch
         L = load()
         if len(terms) != len(drives):
@@ -284,7 +286,8 @@ class Plan:
         carr = (Coeff * len(drives))(*[d.ctype() for d in drives])
         opt = Options(float(tol), float(tol if tol_abs is None else tol_abs), float(rho_max), int(m_max), int(nvec),
                       int(ctas), int(precision), float(barrier_timeout_s), int(test_skip_arrival),
-                      INTERVALS[interval], int(bool(fixed_sums)), ROW_LAYOUTS[rows], int(bool(plain_values)), 0)
+                      INTERVALS[interval], int(bool(fixed_sums)), ROW_LAYOUTS[rows], int(bool(plain_values)), 0,
+                      float(norm_check))
         h = C.c_void_p()
         _check(L.magnus_plan_create(C.byref(h), self.dim, len(terms), tarr, carr, C.byref(opt),
                                     _stream_ptr(self.stream)))
@@ -389,7 +392,7 @@ class Plan:
 
 def _as_dict(st: Stats, log):
     out = {k: getattr(st, k) for k in ("n_exp", "n_substeps", "n_matvec", "n_termapply", "max_m", "status",
-                                       "kernel_ms", "grid", "block", "fixed_sums", "row_layout")}
+                                       "kernel_ms", "grid", "block", "fixed_sums", "row_layout", "norm_drift")}
     if log is not None:
         out["m_log"] = log[: min(st.n_substeps, log.size)].copy()
     return out

@@ -14,8 +14,8 @@
 // block sums each vector's partials over all blocks in the same fixed order, so all blocks hold the
 // same totals and take the same decisions.
 //
-// MAGNUS_TENSOR_SLICED: exact digit products on the tensor cores (dense_tc.cuh on tcgen05 for the
-// linear generators, a warp-level mma.sync digit kernel for M4).
+// MAGNUS_TENSOR_SLICED: exact digit products on the tcgen05 tensor cores (dense_tc.cuh), for the
+// linear generators and for both product phases of M4 (u_k = H_k w, then the commutators).
 #include <math.h>
 
 #include <algorithm>
@@ -210,152 +210,7 @@ __device__ __forceinline__ double2 fieldx_at(int n, const double2 *x, int64_t r)
   return acc;
 }
 
-// ----------------------------------------------------------------- sliced tensor-core GEMM
-// Exact-slice products on the bf16 tensor cores (MAGNUS_TENSOR_SLICED).  Every row of H and every
-// column of the vectors is scaled by a power of two into (-1, 1) and cut into kSl signed 7-bit
-// integer digits (|digit| <= 128, exact in bf16):  x = 2^e sum_t D_t 2^{-7t} + O(2^{e-7 kSl}).
-// The products of digit pairs with t + u <= kSl + 1 are summed on the tensor cores in FP32; within
-// a K-chunk of kChunk columns every partial sum is an integer below 2^24, so FP32 holds it exactly.
-// Chunk sums are carried in int64 (shifted to a common scale), and converted to FP64 once per tile.
-constexpr int kSl = 5;          // digits per value (35 bits)
-constexpr int kChunk = 128;     // exact FP32 accumulation length: 5 pairs x 128 x 2^14 < 2^24
-constexpr int kKS = 32;         // columns per shared-memory stage
-constexpr int kRowPad = 40;     // bf16 per staged row (32 + 8: conflict-free ldmatrix)
-constexpr int kTcCols = 2 * kVecMax;  // real columns: (re, im) of every vector
-struct TcSmem {
-  __nv_bfloat16 a[kSl][kTM][kRowPad];
-  __nv_bfloat16 b[kSl][kTcCols][kRowPad];
-};
-constexpr size_t kTcSmemBytes = sizeof(TcSmem) > sizeof(double) * kTM * kTcCols ? sizeof(TcSmem)
-                                                                                : sizeof(double) * kTM * kTcCols;
-
-__device__ __forceinline__ void ldsm_x4(unsigned (&r)[4], const void *p) {
-  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a));
-}
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
-  asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-               "{%0,%1,%2,%3};"
-               : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-               : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
-// y[i][q] += coef * sum_j H[r0 + 2 ty + i][j] W[v = tx + 16 q][j] for the (ty, tx) output layout.
-// hs: digits of H [kSl][D][D], eh: row exponents; ws: digits of the vectors [kSl][2 nv][D] (column
-// c = 2 v + {0: re, 1: im}), ew: column exponents.  Tile 32 rows x 128 columns, 8 warps of 16 x 32.
-__device__ void gemm_tile_sliced(unsigned char *smem, const __nv_bfloat16 *hs, const int *eh, const __nv_bfloat16 *ws,
-                                 const int *ew, double coef, int64_t D, int nv, int64_t r0, double2 (&y)[2][4]) {
-  TcSmem &S = *reinterpret_cast<TcSmem *>(smem);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wr = warp >> 2, wc = warp & 3;  // warp rows wr*16, columns wc*32
-  const int ncols = 2 * nv;
-  long long sum64[4][4];
-#pragma unroll
-  for (int nt = 0; nt < 4; nt++)
-#pragma unroll
-    for (int i = 0; i < 4; i++) sum64[nt][i] = 0;
-  const size_t sl_h = (size_t)D * D, sl_w = (size_t)ncols * D;
-  for (int64_t c0 = 0; c0 < D; c0 += kChunk) {
-    float acc[kSl][4][4];
-#pragma unroll
-    for (int g = 0; g < kSl; g++)
-#pragma unroll
-      for (int nt = 0; nt < 4; nt++)
-#pragma unroll
-        for (int i = 0; i < 4; i++) acc[g][nt][i] = 0.f;
-    for (int64_t k0 = c0; k0 < c0 + kChunk; k0 += kKS) {
-      __syncthreads();
-      // stage digits: A rows r0..r0+31, B columns 0..127, columns k0..k0+31 (16-byte pieces)
-      for (int i = tid; i < kSl * kTM * 4; i += kDBlock) {
-        const int t = i / (kTM * 4), rr = (i / 4) % kTM, piece = i % 4;
-        cp_async16(&S.a[t][rr][piece * 8], hs + t * sl_h + (size_t)(r0 + rr) * D + k0 + piece * 8);
-      }
-      for (int i = tid; i < kSl * kTcCols * 4; i += kDBlock) {
-        const int u = i / (kTcCols * 4), cc = (i / 4) % kTcCols, piece = i % 4;
-        if (cc < ncols) cp_async16(&S.b[u][cc][piece * 8], ws + u * sl_w + (size_t)cc * D + k0 + piece * 8);
-        else *reinterpret_cast<uint4 *>(&S.b[u][cc][piece * 8]) = make_uint4(0, 0, 0, 0);
-      }
-      cp_async_wait_all();
-      __syncthreads();
-#pragma unroll
-      for (int ks = 0; ks < kKS; ks += 16) {
-        unsigned af[kSl][4];
-#pragma unroll
-        for (int t = 0; t < kSl; t++)
-          ldsm_x4(af[t], &S.a[t][wr * 16 + (lane & 15)][ks + (lane >> 4) * 8]);
-#pragma unroll
-        for (int np = 0; np < 2; np++) {  // n-tile pairs (2 np, 2 np + 1)
-          unsigned bf[kSl][4];
-#pragma unroll
-          for (int u = 0; u < kSl; u++)
-            ldsm_x4(bf[u], &S.b[u][wc * 32 + np * 16 + (lane & 7) + ((lane >> 4) << 3)][ks + ((lane >> 3) & 1) * 8]);
-#pragma unroll
-          for (int t = 0; t < kSl; t++)
-#pragma unroll
-            for (int u = 0; u < kSl; u++) {
-              if (t + u > kSl - 1) continue;  // keep digit pairs with (t+1)+(u+1) <= kSl + 1
-              mma_bf16(acc[t + u][2 * np], af[t], bf[u][0], bf[u][1]);
-              mma_bf16(acc[t + u][2 * np + 1], af[t], bf[u][2], bf[u][3]);
-            }
-        }
-      }
-    }
-    // exact integer chunk sums -> int64 at the common scale 2^{-7 (kSl + 1)}
-#pragma unroll
-    for (int g = 0; g < kSl; g++)
-#pragma unroll
-      for (int nt = 0; nt < 4; nt++)
-#pragma unroll
-        for (int i = 0; i < 4; i++)
-          sum64[nt][i] += (long long)__float2int_rn(acc[g][nt][i]) << (7 * (kSl - 1 - g));
-  }
-  // scale back: value = sum64 * 2^{e_row + e_col - 7 (kSl + 1)}; stage through shared memory into
-  // the (ty, tx) layout of the FP64 epilogue
-  __syncthreads();
-  double *Y = reinterpret_cast<double *>(smem);  // [kTM][kTcCols]
-#pragma unroll
-  for (int nt = 0; nt < 4; nt++)
-#pragma unroll
-    for (int i = 0; i < 4; i++) {
-      const int row = wr * 16 + (lane >> 2) + (i >= 2 ? 8 : 0);
-      const int col = wc * 32 + nt * 8 + (lane & 3) * 2 + (i & 1);
-      double v = 0.0;
-      if (col < ncols) v = ldexp((double)sum64[nt][i], eh[r0 + row] + ew[col] - 7 * (kSl + 1));
-      Y[row * kTcCols + col] = v;
-    }
-  __syncthreads();
-  const int ty = tid >> 4, tx = tid & 15;
-#pragma unroll
-  for (int i = 0; i < 2; i++)
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-      const int v = tx + 16 * q;
-      if (v < nv) {
-        const int row = 2 * ty + i;
-        y[i][q].x = fma(coef, Y[row * kTcCols + 2 * v], y[i][q].x);
-        y[i][q].y = fma(coef, Y[row * kTcCols + 2 * v + 1], y[i][q].y);
-      }
-    }
-  __syncthreads();
-}
-
-// Digits of one value with exponent e: x = 2^e sum_t d_t 2^{-7t} + rest (exact FP64 steps).
-__device__ __forceinline__ void slice_value(double x, int e, __nv_bfloat16 *out, size_t stride) {
-  double a = ldexp(x, -e);
-#pragma unroll
-  for (int t = 1; t <= kSl; t++) {
-    const double sc = ldexp(1.0, 7 * t);
-    const double q = rint(a * sc);
-    out[(t - 1) * stride] = __float2bfloat16_rn((float)q);
-    a = fma(-q, 1.0 / sc, a);
-  }
-}
+constexpr int kTcCols = 2 * kVecMax;  // real columns of a vector set: (re, im) of every vector
 
 // exponent e with |x| < 2^e for all |x| <= m (0 for m == 0)
 __device__ __forceinline__ int cover_exponent(double m) {
@@ -365,16 +220,17 @@ __device__ __forceinline__ int cover_exponent(double m) {
 }
 
 // ------------------------------------------------------------------ kernel
-// PREC: 0 FP64, 1 FP32 split, 2 sliced digits on mma.sync (5 x 7 bits), 3 sliced digits on tcgen05
-// (4 x 8 bits, linear generators; the product phase of dense_tc.cuh).
+// PREC: 0 FP64, 1 FP32 split, 3 digit products on tcgen05 (4 x 8 bits; the product phase of
+// dense_tc.cuh, linear generators), 4 the same with M4 (the product phases of u_k = H_k w and of the
+// commutators).
 constexpr int kEpiTiles = 4;   // 128-row tiles a block's rows can touch (at most 256 rows per block)
 constexpr int kEpiOwners = 8;  // CTAs whose partial tiles a tile is summed from
 
 template <bool REAL, bool TILED, int PREC>
 __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) {
   constexpr bool SPLIT = PREC == 1;
-  constexpr bool SLICED = PREC == 2;
-  constexpr bool TC = PREC == 3;
+  constexpr bool TC = PREC == 3 || PREC == 4;
+  constexpr bool TCM4 = PREC == 4;  // tcgen05 with the M4 generator's two product phases
   __shared__ Term sT[kMaxTerms];
   __shared__ ExpRec sR;
   __shared__ double s_vn[kVecMax], s_ep[kVecMax], s_pn[kVecMax];
@@ -382,6 +238,7 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
   __shared__ double s_part[kDBlock / 32][kVecMax][2];
   __shared__ double s_tot[kVecMax][2];  // per-vector totals of the last reduction
   __shared__ int s_flag;
+  __shared__ int s_drift;  // the norm check of the last substep failed
   __shared__ TileSmem TS;
   DenseSmem &S = TS.d;
   extern __shared__ __align__(16) unsigned char dsm[];
@@ -552,33 +409,23 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
       for (int c = tid; c < kTcCols; c += blockDim.x) a.colmax[(size_t)((slice_ev + 2) % 3u) * kTcCols + c] = 0ull;
     __syncthreads();
     __nv_bfloat16 *dg = (__nv_bfloat16 *)digits;
-    if (TC) {
-      // one work item = one column and 8 consecutive rows (this block's rows come in whole
-      // 32-row tiles): the digits of the 8 values go out as four 16-byte stores
-      const int ncol = 2 * nv;
-      const int64_t ngroups = (hi - lo) / 8;
-      for (int64_t w = tid; w < ngroups * ncol; w += blockDim.x) {
-        const int c = (int)(w % ncol), v = c >> 1;
-        const int64_t r0 = lo + 8 * (w / ncol);
-        double xv[8];
+    // one work item = one column and 8 consecutive rows (this block's rows come in whole 32-row
+    // tiles): the digits of the 8 values go out as four 16-byte stores
+    const int ncol = 2 * nv;
+    const int64_t ngroups = (hi - lo) / 8;
+    for (int64_t w = tid; w < ngroups * ncol; w += blockDim.x) {
+      const int c = (int)(w % ncol), v = c >> 1;
+      const int64_t r0 = lo + 8 * (w / ncol);
+      double xv[8];
 #pragma unroll
-        for (int i = 0; i < 8; i++) {
-          const double2 x = X[(int64_t)v * D + r0 + i];
-          xv[i] = (c & 1) ? x.y : x.x;
-        }
-        tcg::slice8_tiled(xv, s_cexp[c], dg, D, c, r0);
+      for (int i = 0; i < 8; i++) {
+        const double2 x = X[(int64_t)v * D + r0 + i];
+        xv[i] = (c & 1) ? x.y : x.x;
       }
-    } else {
-      const size_t stride = (size_t)2 * nv * D;
-      for (int v = 0; v < nv; v++)
-        for (int64_t r = lo + tid; r < hi; r += blockDim.x) {
-          const double2 x = X[(int64_t)v * D + r];
-          slice_value(x.x, s_cexp[2 * v], dg + (size_t)(2 * v) * D + r, stride);
-          slice_value(x.y, s_cexp[2 * v + 1], dg + (size_t)(2 * v + 1) * D + r, stride);
-        }
+      tcg::slice8_tiled(xv, s_cexp[c], dg, D, c, r0);
     }
     // the digits are read next by TMA (async proxy) in other CTAs
-    if (TC) asm volatile("fence.proxy.async.global;" ::: "memory");
+    asm volatile("fence.proxy.async.global;" ::: "memory");
     slice_ev++;
     return grid_barrier(a.bar, G, a.spin_limit_ns);
   };
@@ -619,8 +466,23 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
     }
   };
 
-  const void *sl_src[kMaxTerms] = {nullptr, nullptr, nullptr, nullptr};  // digits of the vectors being read
-  const int *ex_src[kMaxTerms] = {nullptr, nullptr, nullptr, nullptr};
+  // the sets of one product phase: every dense term multiplies set `set`
+  auto tc_all = [&](int set) {
+    tcg::Sets W;
+    for (int q = 0; q < tcg::kMaxSets; q++) {
+      W.wd[q] = (const __nv_bfloat16 *)tc_set_digits(set);
+      W.ec[q] = tc_set_exps(set);
+    }
+    return W;
+  };
+  // one product phase on the tensor cores (this CTA's items), then a barrier
+  auto tc_products = [&](const tcg::Sets &W) -> bool {
+    if (!tcg::gemm_phase((const __nv_bfloat16 *)a.tc_hd, W, tc_geom, a.tc_eh, a.tc_P, dsm, tc_bars, tc_pipe,
+                         a.tc_spins))
+      return false;
+    return grid_barrier(a.bar, G, a.spin_limit_ns);
+  };
+
   auto apply_terms = [&](const double *coef, const double2 *const *srcs, const float4 *const *shs, int64_t r0,
                          double2 (&y)[2][4]) {
     if (TILED) {
@@ -633,9 +495,6 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
         if (sT[k].kind == MAGNUS_TERM_DENSE) {
           if (TC)
             tc_term(k, coef[k], r0, y);
-          else if (SLICED)
-            gemm_tile_sliced(dsm, (const __nv_bfloat16 *)a.hslice[k], a.hexp[k], (const __nv_bfloat16 *)sl_src[k],
-                             ex_src[k], coef[k], D, nv, r0, y);
           else if (SPLIT)
             gemm_tile_split(TS.f, a.hsplit[k], coef[k], shs[k], D, nv, r0, hi, y);
           else
@@ -723,9 +582,6 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
             a.sh_cur[(int64_t)v * D + r] = split4(cur[(int64_t)v * D + r]);
         if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { fail(MAGNUS_ETIMEOUT); return; }
       }
-      if (SLICED) {
-        if (!slice_set(cur, a.sl_cur, a.ex_cur)) { fail(MAGNUS_ETIMEOUT); return; }
-      }
       if (TC) {
         if (!slice_set(cur, tc_set_digits(0), tc_set_exps(0))) { fail(MAGNUS_ETIMEOUT); return; }
       }
@@ -741,21 +597,11 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
         const double2 *srcs[kMaxTerms] = {src, src, src, src};
         const float4 *shs[kMaxTerms] = {src_sh, src_sh, src_sh, src_sh};
         if (TC) {  // all dense products of this iteration on the tensor cores, then a barrier
-          if (R.mode != MODE_LINEAR) { fail(MAGNUS_EINVAL); return; }
+          if (!TCM4 && R.mode != MODE_LINEAR) { fail(MAGNUS_EINVAL); return; }
           const int set = (j == 1) ? 0 : (((j - 2) & 1) ? 2 : 1);
-          if (!tcg::gemm_phase((const __nv_bfloat16 *)a.tc_hd, (const __nv_bfloat16 *)tc_set_digits(set), tc_geom,
-                               a.tc_eh, tc_set_exps(set), a.tc_P, dsm, tc_bars, tc_pipe, a.tc_spins)) {
-            fail(MAGNUS_ETIMEOUT);
-            return;
-          }
-          if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { fail(MAGNUS_ETIMEOUT); return; }
+          if (!tc_products(tc_all(set))) { fail(MAGNUS_ETIMEOUT); return; }
         }
-        if (SLICED) {
-          const void *d_src = (j == 1) ? a.sl_cur : (((j - 2) & 1) ? a.sl_w1 : a.sl_w0);
-          const int *e_src = (j == 1) ? a.ex_cur : (((j - 2) & 1) ? a.ex_w1 : a.ex_w0);
-          for (int k = 0; k < kMaxTerms; k++) { sl_src[k] = d_src; ex_src[k] = e_src; }
-        }
-        if (R.mode == MODE_M4) {
+        if ((!TC || TCM4) && R.mode == MODE_M4) {
           // phase 1: u_k = H_k src for every vector, this block's rows
           double one[kMaxTerms];
           for (int k = 0; k < nt; k++) {
@@ -786,14 +632,12 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
             }
           }
           if (!grid_barrier(a.bar, G, a.spin_limit_ns)) { fail(MAGNUS_ETIMEOUT); return; }
-          if (SLICED)
-            for (int k = 0; k < nt; k++) {
-              const size_t set = (size_t)kSl * 2 * nv * D;
-              if (!slice_set(a.u + (size_t)k * nv * D, (__nv_bfloat16 *)a.sl_u + k * set, a.ex_u + k * kTcCols)) {
+          if (TCM4)  // digits of every u_k: set 3 + k
+            for (int k = 0; k < nt; k++)
+              if (!slice_set(a.u + (size_t)k * nv * D, tc_set_digits(3 + k), tc_set_exps(3 + k))) {
                 fail(MAGNUS_ETIMEOUT);
                 return;
               }
-            }
         }
         double sw[4] = {0, 0, 0, 0}, sp[4] = {0, 0, 0, 0};
         // epilogue for one output (row r, vector v) with y = the combined matvec
@@ -815,45 +659,80 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
           sw[q] += cabs2(y);
           sp[q] += cabs2(pr);
         };
+        // y += -i kg (H_k u_l - H_l u_k) for one pair k < l, this thread's outputs of the tile at r0
+        auto comm_pair = [&](int k, int l, double kg, int64_t r0, double2 (&y)[2][4]) {
+          double ck[kMaxTerms] = {0, 0, 0, 0}, cl[kMaxTerms] = {0, 0, 0, 0};
+          ck[k] = kg;
+          cl[l] = -kg;
+          const double2 *sk[kMaxTerms], *sl[kMaxTerms];
+          const float4 *hk[kMaxTerms], *hl[kMaxTerms];
+          for (int q = 0; q < kMaxTerms; q++) {
+            sk[q] = a.u + (size_t)l * nv * D;  // H_k applied to u_l
+            sl[q] = a.u + (size_t)k * nv * D;  // H_l applied to u_k
+            hk[q] = a.sh_u + (size_t)l * nv * D;
+            hl[q] = a.sh_u + (size_t)k * nv * D;
+          }
+          double2 z1[2][4], z2[2][4];
+          apply_terms(ck, sk, hk, r0, z1);
+          apply_terms(cl, sl, hl, r0, z2);
+          for (int i = 0; i < 2; i++)
+            for (int q = 0; q < 4; q++) {
+              const double zx = z1[i][q].x + z2[i][q].x, zy = z1[i][q].y + z2[i][q].y;
+              y[i][q].x += zy;  // -i z
+              y[i][q].y -= zx;
+            }
+        };
         auto commutator = [&](int64_t r0, double2 (&y)[2][4]) {
-          // y += sum_k bg_k u_k - i sum_{k<l} kg_kl (H_k u_l - H_l u_k)
+          // y += -i sum_{k<l} kg_kl (H_k u_l - H_l u_k)
           int pi = 0;
+          for (int k = 0; k < nt; k++)
+            for (int l = k + 1; l < nt; l++, pi++)
+              if (R.kg[pi] != 0.0) comm_pair(k, l, R.kg[pi], r0, y);
+        };
+        if (TCM4 && R.mode == MODE_M4) {
+          // the commutators on the tensor cores: per pair k < l one product phase in which dense term
+          // k multiplies the digits of u_l and dense term l those of u_k; -i kg (H_k u_l - H_l u_k) of
+          // the pairs, in pair order, summed into tc_cacc for this block's rows (the order of the
+          // commutator above, so the same sums)
+          int pi = 0;
+          bool first = true;
           for (int k = 0; k < nt; k++)
             for (int l = k + 1; l < nt; l++, pi++) {
               if (R.kg[pi] == 0.0) continue;
-              double ck[kMaxTerms] = {0, 0, 0, 0}, cl[kMaxTerms] = {0, 0, 0, 0};
-              ck[k] = R.kg[pi];
-              cl[l] = -R.kg[pi];
-              const double2 *sk[kMaxTerms], *sl[kMaxTerms];
-              const float4 *hk[kMaxTerms], *hl[kMaxTerms];
-              for (int q = 0; q < kMaxTerms; q++) {
-                sk[q] = a.u + (size_t)l * nv * D;  // H_k applied to u_l
-                sl[q] = a.u + (size_t)k * nv * D;  // H_l applied to u_k
-                hk[q] = a.sh_u + (size_t)l * nv * D;
-                hl[q] = a.sh_u + (size_t)k * nv * D;
+              const bool dk = sT[k].kind == MAGNUS_TERM_DENSE, dl = sT[l].kind == MAGNUS_TERM_DENSE;
+              if (dk || dl) {
+                // every block has summed the previous phase's partial tiles before they are rewritten
+                if (!first && !grid_barrier(a.bar, G, a.spin_limit_ns)) { fail(MAGNUS_ETIMEOUT); return; }
+                tcg::Sets W = tc_all(3 + l);
+                if (dl) {
+                  W.wd[a.tc_dslot[l]] = (const __nv_bfloat16 *)tc_set_digits(3 + k);
+                  W.ec[a.tc_dslot[l]] = tc_set_exps(3 + k);
+                }
+                if (!tc_products(W)) { fail(MAGNUS_ETIMEOUT); return; }
               }
-              double2 z1[2][4], z2[2][4];
-              const size_t set = (size_t)kSl * 2 * nv * D;
-              if (SLICED)
-                for (int q = 0; q < kMaxTerms; q++) {
-                  sl_src[q] = (const __nv_bfloat16 *)a.sl_u + l * set;
-                  ex_src[q] = a.ex_u + l * kTcCols;
-                }
-              apply_terms(ck, sk, hk, r0, z1);
-              if (SLICED)
-                for (int q = 0; q < kMaxTerms; q++) {
-                  sl_src[q] = (const __nv_bfloat16 *)a.sl_u + k * set;
-                  ex_src[q] = a.ex_u + k * kTcCols;
-                }
-              apply_terms(cl, sl, hl, r0, z2);
-              for (int i = 0; i < 2; i++)
-                for (int q = 0; q < 4; q++) {
-                  const double zx = z1[i][q].x + z2[i][q].x, zy = z1[i][q].y + z2[i][q].y;
-                  y[i][q].x += zy;  // -i z
-                  y[i][q].y -= zx;
-                }
+              for (int64_t r0 = lo; r0 < hi; r0 += kTM) {
+                double2 z[2][4];
+                for (int i = 0; i < 2; i++)
+                  for (int q = 0; q < 4; q++) {
+                    const int64_t r = r0 + 2 * ty + i;
+                    const int v = tx + 16 * q;
+                    z[i][q] = (first || r >= hi || v >= nv) ? make_double2(0.0, 0.0) : a.tc_cacc[(int64_t)v * D + r];
+                  }
+                comm_pair(k, l, R.kg[pi], r0, z);
+                for (int i = 0; i < 2; i++)
+                  for (int q = 0; q < 4; q++) {
+                    const int64_t r = r0 + 2 * ty + i;
+                    const int v = tx + 16 * q;
+                    if (r < hi && v < nv) a.tc_cacc[(int64_t)v * D + r] = z[i][q];
+                  }
+              }
+              first = false;
             }
-        };
+          if (first)  // no commutator
+            for (int v = 0; v < nv; v++)
+              for (int64_t r = lo + tid; r < hi; r += blockDim.x) a.tc_cacc[(int64_t)v * D + r] = make_double2(0.0, 0.0);
+          __syncthreads();
+        }
         bool tc_epi = false;
         const int64_t t_first = lo / tcg::kM;  // first 128-row tile of this block's rows
         if (TC && R.mode == MODE_LINEAR) {
@@ -969,8 +848,12 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
             double2 y[2][4];
             if (R.mode == MODE_M4) {
               for (int i = 0; i < 2; i++)
-                for (int q = 0; q < 4; q++) y[i][q] = make_double2(0.0, 0.0);
-              commutator(r0, y);
+                for (int q = 0; q < 4; q++) {
+                  const int64_t r = r0 + 2 * ty + i;
+                  const int v = tx + 16 * q;
+                  y[i][q] = (TCM4 && r < hi && v < nv) ? a.tc_cacc[(int64_t)v * D + r] : make_double2(0.0, 0.0);
+                }
+              if (!TC) commutator(r0, y);
               for (int i = 0; i < 2; i++) {
                 const int64_t r = r0 + 2 * ty + i;
                 if (r >= hi) continue;
@@ -1063,12 +946,6 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
           done = true;
           break;
         }
-        if (SLICED && j < a.m_max) {  // digits of w_j for the next iteration's tensor-core products
-          if (!slice_set(dst, ((j - 1) & 1) ? a.sl_w1 : a.sl_w0, ((j - 1) & 1) ? a.ex_w1 : a.ex_w0)) {
-            fail(MAGNUS_ETIMEOUT);
-            return;
-          }
-        }
         if (TC && j < a.m_max) {  // digits of w_j from the maxima gathered in the epilogue
           const int set = ((j - 1) & 1) ? 2 : 1;
           const unsigned long long *cm = a.colmax + 3 * kTcCols;
@@ -1101,6 +978,14 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
         }
       }
       if (!done) { fail(MAGNUS_ENOCONV); return; }
+      if (tid == 0) {  // a posteriori norm check of the substep (every block decides alike)
+        int bad = 0;
+        for (int v = 0; v < nv; v++)
+          bad |= drift_fails(s_pn[v], s_vn[v], a.tol_abs, a.tol_rel, a.norm_check, a.counters, b == 0) ? 1 : 0;
+        s_drift = bad;
+      }
+      __syncthreads();
+      if (s_drift) { fail(MAGNUS_EDRIFT); return; }
       if (tid < nv) s_vn[tid] = s_pn[tid];
       if (b == 0 && tid == 0) {
         Counters *c = a.counters;
@@ -1126,26 +1011,26 @@ __global__ void __launch_bounds__(kDBlock, 1) k_dense_persistent(PersistArgs a) 
 
 const void *dense_kernel(bool real, bool tiled, int prec) {
   if (prec == 1) return (const void *)k_dense_persistent<true, true, 1>;
-  if (prec == 2) return (const void *)k_dense_persistent<true, true, 2>;
   if (prec == 3) return (const void *)k_dense_persistent<true, true, 3>;
+  if (prec == 4) return (const void *)k_dense_persistent<true, true, 4>;
   if (real)
     return tiled ? (const void *)k_dense_persistent<true, true, 0> : (const void *)k_dense_persistent<true, false, 0>;
   return tiled ? (const void *)k_dense_persistent<false, true, 0> : (const void *)k_dense_persistent<false, false, 0>;
 }
 
-cudaError_t sliced_attr() {
+cudaError_t tc_smem_attr() {
   static bool done = false;
   if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(dense_kernel(true, true, 2), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kTcSmemBytes);
+  cudaError_t e = cudaFuncSetAttribute(dense_kernel(true, true, 3), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)tcg::kSmemBytes);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(dense_kernel(true, true, 3), cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(dense_kernel(true, true, 4), cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)tcg::kSmemBytes);
   if (e == cudaSuccess) done = true;
   return e;
 }
 
-size_t dyn_smem(int prec) { return prec == 2 ? kTcSmemBytes : (prec == 3 ? tcg::kSmemBytes : 0); }
+size_t dyn_smem(int prec) { return prec >= 3 ? tcg::kSmemBytes : 0; }
 
 }  // namespace
 
@@ -1162,29 +1047,6 @@ __global__ void k_split_dense(const double *Hr, int rs, float2 *out, int64_t n) 
 }
 }  // namespace
 
-namespace {
-// one warp per row: row maximum -> exponent, then the row's digits
-__global__ void k_slice_dense(const double *Hr, int rs, int64_t D, __nv_bfloat16 *digits, int *rexp) {
-  const int lane = threadIdx.x & 31;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < D; r += nw) {
-    double m = 0.0;
-    for (int64_t c = lane; c < D; c += 32) m = fmax(m, fabs(Hr[(r * D + c) * rs]));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(kFull, m, o));
-    const int e = cover_exponent(m);
-    if (lane == 0) rexp[r] = e;
-    for (int64_t c = lane; c < D; c += 32) slice_value(Hr[(r * D + c) * rs], e, digits + r * D + c, (size_t)D * D);
-  }
-}
-}  // namespace
-
-cudaError_t launch_slice_dense(const double *Hr, int rs, int64_t D, void *digits, int *rexp, cudaStream_t st) {
-  k_slice_dense<<<152 * 8, 256, 0, st>>>(Hr, rs, D, (__nv_bfloat16 *)digits, rexp);
-  return cudaGetLastError();
-}
-
-size_t dense_sliced_smem_bytes() { return kTcSmemBytes; }
 
 namespace {
 // one warp per row: row maximum -> exponent, then the row's 4 digits of 8 bits
@@ -1230,12 +1092,12 @@ cudaError_t launch_split_dense(const double *Hr, int rs, float2 *out, int64_t n,
 
 cudaError_t dense_max_blocks_per_sm(int *n) {
   int best = 1 << 30;
-  cudaError_t e0 = sliced_attr();
+  cudaError_t e0 = tc_smem_attr();
   if (e0 != cudaSuccess) return e0;
   for (int r = 0; r < 2; r++)
     for (int t = 0; t < 5; t++) {
       int k = 0;
-      const int prec = t >= 2 ? t - 1 : 0;
+      const int prec = t < 2 ? 0 : (t == 2 ? 1 : t);  // FP64 warp rows, FP64 tiles, split, tcgen05, tcgen05 M4
       cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, dense_kernel(r, t > 0, prec), kDBlock,
                                                                     dyn_smem(prec));
       if (e != cudaSuccess) return e;
@@ -1248,9 +1110,9 @@ cudaError_t dense_max_blocks_per_sm(int *n) {
 cudaError_t launch_dense_persistent(const PersistArgs &a, bool real_valued, int grid, cudaStream_t st) {
   PersistArgs copy = a;
   void *args[] = {&copy};
-  const int prec = a.tc ? 3 : (a.sliced ? 2 : (a.split ? 1 : 0));
-  if (prec >= 2) {
-    cudaError_t e = sliced_attr();
+  const int prec = a.tc ? 2 + a.tc : (a.split ? 1 : 0);
+  if (prec >= 3) {
+    cudaError_t e = tc_smem_attr();
     if (e != cudaSuccess) return e;
   }
   return cudaLaunchCooperativeKernel(dense_kernel(real_valued, a.nvec > 1 || prec > 0, prec), dim3(grid),

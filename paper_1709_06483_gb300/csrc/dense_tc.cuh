@@ -1,6 +1,7 @@
-// Exact-digit dense products on the 5th-generation tensor cores (MAGNUS_TENSOR_SLICED, linear
-// generators).  Y_k = H_k W for every dense term k and one set W of up to 128 real columns (the real
-// and imaginary parts of up to 64 states), with H_k and W given as 4 signed 8-bit digits per value:
+// Exact-digit dense products on the 5th-generation tensor cores (MAGNUS_TENSOR_SLICED).
+// Y_k = H_k W_k for every dense term k and a set W_k of up to 128 real columns (the real and
+// imaginary parts of up to 64 states; one set for all terms in the linear generators, the set of
+// u_l for term k in the commutators of M4), with H_k and W_k given as 4 signed 8-bit digits per value:
 //     H[r][j] = 2^{e_r} sum_t h_t[r][j] 2^{-8(t+1) + 1},   W[c][j] = 2^{e_c} sum_u w_u[c][j] 2^{-8(u+1) + 1},
 // (a value scaled to 31 bits, N = round(x 2^{31-e}), cut into balanced base-256 digits) with every
 // |h_t|, |w_u| <= 128, all exact in bf16.  The digit products of level g = t + u <= 3 (10 of the 16
@@ -65,6 +66,15 @@ struct Bars {
 struct Pipe {
   uint32_t stage;  // stages issued so far
   uint32_t chunk;  // chunks completed so far
+};
+
+// the vector set each dense term multiplies in one product phase (its digits and column exponents):
+// the same set for every term in the linear generators; in the commutator phases of M4, term k
+// multiplies the set of u_l
+constexpr int kMaxSets = 4;
+struct Sets {
+  const __nv_bfloat16 *wd[kMaxSets];
+  const int *ec[kMaxSets];
 };
 
 struct Geometry {
@@ -150,13 +160,13 @@ __device__ __forceinline__ int cover_exponent(double m) {
   return e;
 }
 
-// Y_k = H_k W for the vector digits wd (tiled, one set), this CTA's range.  hd: tiled digits of all
-// dense terms; P: partial tiles [G][slots][kN cols][kM rows] (FP64, column-major in the tile); eh:
-// row exponents [ndense][D]; ec: column exponents of the set [kN].  smem: kSmemBytes of dynamic
-// shared memory.  Returns false if a bounded wait ran out (the caller reports MAGNUS_ETIMEOUT).
-__device__ bool gemm_phase(const __nv_bfloat16 *hd, const __nv_bfloat16 *wd, const Geometry &g, const int *eh,
-                           const int *ec, double *P, unsigned char *smem_raw, Bars &bars, Pipe &pipe,
-                           long long max_spins) {
+// Y_k = H_k W_k for every dense term k, W_k given by W.wd[k] (tiled digits) and W.ec[k] (its column
+// exponents [kN]), this CTA's range.  hd: tiled digits of all dense terms; P: partial tiles
+// [G][slots][kN cols][kM rows] (FP64, column-major in the tile); eh: row exponents [ndense][D].
+// smem: kSmemBytes of dynamic shared memory.  Returns false if a bounded wait ran out (the caller
+// reports MAGNUS_ETIMEOUT).
+__device__ bool gemm_phase(const __nv_bfloat16 *hd, const Sets &W, const Geometry &g, const int *eh, double *P,
+                           unsigned char *smem_raw, Bars &bars, Pipe &pipe, long long max_spins) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int b = blockIdx.x, G = gridDim.x;
   unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -188,7 +198,7 @@ __device__ bool gemm_phase(const __nv_bfloat16 *hd, const __nv_bfloat16 *wd, con
     unsigned char *sa = smem + (size_t)buf * kStageBytes, *sb = sa + kStageA;
     // tile = term * T + row tile: its K-blocks start at tile * (D / 8) blocks of kBox bytes
     const unsigned char *ga = (const unsigned char *)hd + ((size_t)tile * (size_t)(D / 8) + (size_t)(k0 / 8)) * kBox;
-    const unsigned char *gb = (const unsigned char *)wd + (size_t)(k0 / 8) * kBox;
+    const unsigned char *gb = (const unsigned char *)W.wd[(int)(tile / g.T)] + (size_t)(k0 / 8) * kBox;
     tc::mbar_expect_tx(&bars.full[buf], kStageBytes);
     tc::bulk_load(sa, ga, kStageA, &bars.full[buf]);
     tc::bulk_load(sb, gb, kStageA, &bars.full[buf]);
@@ -282,6 +292,7 @@ __device__ bool gemm_phase(const __nv_bfloat16 *hd, const __nv_bfloat16 *wd, con
       // FP64 partial tile: levels 0/1 exact, 2/3 from tensor memory
       const int term = (int)(tile / g.T), r0 = (int)(tile % g.T) * kM;
       const int er = eh[(long long)term * D + r0 + row];
+      const int *ec = W.ec[term];
       double *out = P + ((size_t)b * g.slots + slot) * (size_t)(kN * kM);
 #pragma unroll
       for (int c16 = 0; c16 < 4; c16++) {

@@ -93,6 +93,7 @@ __global__ void __launch_bounds__(kBlock, (STG ? 2 : min_blocks<FAM, HM6, ZF>())
   __shared__ double s_red[2][kBlock / 32];
   __shared__ unsigned s_rmx[2][kBlock / 32];
   __shared__ int s_flag;
+  __shared__ int s_drift;  // the norm check of the last substep failed
   __shared__ int s_kp;  // staged rows: the pattern term whose rows of one length are read as 16-byte loads
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -705,6 +706,14 @@ __global__ void __launch_bounds__(kBlock, (STG ? 2 : min_blocks<FAM, HM6, ZF>())
         if (s_flag == 1) { done = true; break; }
       }
       if (!done) { bail(MAGNUS_ENOCONV); return; }
+      if (tid == 0) {  // a posteriori norm check of the substep (every block decides alike)
+        int bad = 0;
+        for (int v = 0; v < nv; v++)
+          bad |= drift_fails(s_pn[v], s_vn[v], a.tol_abs, a.tol_rel, a.norm_check, a.counters, b == 0) ? 1 : 0;
+        s_drift = bad;
+      }
+      __syncthreads();
+      if (s_drift) { bail(MAGNUS_EDRIFT); return; }
       if (tid < nv) {
         s_vn[tid] = s_pn[tid];
         s_vm[tid] = s_pm[tid];

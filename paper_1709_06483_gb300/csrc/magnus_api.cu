@@ -52,21 +52,17 @@ struct magnus_plan_s {
   bool dense_real = true;
   float2 *hsplit[kMaxTerms] = {nullptr, nullptr, nullptr, nullptr};
   float4 *sh_cur = nullptr, *sh_w0 = nullptr, *sh_w1 = nullptr, *sh_u = nullptr;
-  uint16_t *hslice[kMaxTerms] = {nullptr, nullptr, nullptr, nullptr};
-  int *hexp[kMaxTerms] = {nullptr, nullptr, nullptr, nullptr};
-  uint16_t *sl_cur = nullptr, *sl_w0 = nullptr, *sl_w1 = nullptr, *sl_u = nullptr;
-  int *ex_sets = nullptr;                // [3 + nterms][128] column exponents
   unsigned long long *colmax = nullptr;  // [4][128]: 3 rotating slicing slots + the epilogue's
   double2 *m6 = nullptr;                 // M6 intermediate vectors [kM6Slots][nvec][dim], on first use
   // MAGNUS_TENSOR_SLICED on tcgen05 (linear generators)
   uint16_t *tc_hd = nullptr;             // dense-term digits, tiled [ndense][dim/128][dim/8][4][128][8]
   int *tc_eh = nullptr;                  // their row exponents [ndense][dim]
-  uint16_t *tc_wd = nullptr;             // vector-set digits, tiled [3][dim/8][4][128][8]
-  int *tc_ex = nullptr;                  // column exponents [3][128]
+  uint16_t *tc_wd = nullptr;             // vector-set digits, tiled [3 + nterms][dim/8][4][128][8]
+  int *tc_ex = nullptr;                  // column exponents [3 + nterms][128]
+  double2 *tc_cacc = nullptr;            // M4 commutator sums [nvec][dim]
   double *tc_P = nullptr;                // partial tiles [grid][slots][128][128]
   int tc_grid = 0, tc_slots = 0, tc_ndense = 0;
   int tc_dslot[kMaxTerms] = {0, 0, 0, 0};
-  bool m4_sliced_ready = false;          // the 5 x 7-bit tables of the M4 path exist
   Coeff coeff_host[kMaxTerms];           // staging of magnus_set_coeff
   int lbits = 0;
   double *dlo = nullptr, *dhi = nullptr;
@@ -119,9 +115,8 @@ void free_plan(magnus_plan_t p) {
   void *bufs[] = {p->terms, p->coeffs, p->term_ab, p->xi, p->cand, p->counter, p->bar, p->counters, p->partials,
                   p->alt, p->w0, p->w1, p->u, p->recs, p->dd, p->mlog, p->dlo, p->dhi,
                   p->hsplit[0], p->hsplit[1], p->hsplit[2], p->hsplit[3], p->sh_cur, p->sh_w0, p->sh_w1, p->sh_u,
-                  p->hslice[0], p->hslice[1], p->hslice[2], p->hslice[3], p->hexp[0], p->hexp[1], p->hexp[2],
-                  p->hexp[3], p->sl_cur, p->sl_w0, p->sl_w1, p->sl_u, p->ex_sets, p->colmax, p->m6,
-                  p->tc_hd, p->tc_eh, p->tc_wd, p->tc_ex, p->tc_P, p->zc, p->zw0, p->zw1, p->zu, p->zmax,
+                  p->colmax, p->m6,
+                  p->tc_hd, p->tc_eh, p->tc_wd, p->tc_ex, p->tc_P, p->tc_cacc, p->zc, p->zw0, p->zw1, p->zu, p->zmax,
                   p->rcopy[0], p->rcopy[1], p->rcopy[2], p->rcopy[3], p->fval[0], p->fval[1], p->fval[2],
                   p->fval[3], p->fexp[0], p->fexp[1], p->fexp[2], p->fexp[3]};
   for (void *b : bufs)
@@ -130,29 +125,6 @@ void free_plan(magnus_plan_t p) {
   if (p->ev0) cudaEventDestroy(p->ev0);
   if (p->ev1) cudaEventDestroy(p->ev1);
   delete p;
-}
-
-// the 5 x 7-bit digit tables of the mma.sync path (M4 generators in MAGNUS_TENSOR_SLICED), made on
-// first use
-magnus_status ensure_m4_sliced(magnus_plan_t p) {
-  if (p->m4_sliced_ready) return MAGNUS_OK;
-  const size_t kDigits = 5;
-  const int64_t dim = p->dim;
-  const size_t nd = (size_t)dim * p->opt.nvec;
-  for (int k = 0; k < p->nterms; k++)
-    if (p->terms_host[k].kind == MAGNUS_TERM_DENSE) {
-      CUDA_TRY(p, dalloc(&p->hslice[k], kDigits * (size_t)dim * dim));
-      CUDA_TRY(p, dalloc(&p->hexp[k], (size_t)dim));
-      CUDA_TRY(p, launch_slice_dense(p->terms_host[k].rv, p->terms_host[k].rs, dim, p->hslice[k], p->hexp[k], p->stream));
-    }
-  const size_t set = kDigits * 2 * nd;
-  CUDA_TRY(p, dalloc(&p->sl_cur, set));
-  CUDA_TRY(p, dalloc(&p->sl_w0, set));
-  CUDA_TRY(p, dalloc(&p->sl_w1, set));
-  CUDA_TRY(p, dalloc(&p->sl_u, set * p->nterms));
-  CUDA_TRY(p, dalloc(&p->ex_sets, (size_t)128 * (3 + p->nterms)));
-  p->m4_sliced_ready = true;
-  return MAGNUS_OK;
 }
 
 // the layout the fixed-point CSR rows of a launch read (0: not a fixed-point CSR launch)
@@ -256,6 +228,7 @@ magnus_status run_persistent(magnus_plan_t p, void *psi, int64_t nexp, magnus_st
   a.nexp = nexp;
   a.tol_rel = p->opt.tol_rel;
   a.tol_abs = p->opt.tol_abs;
+  a.norm_check = p->opt.norm_check;
   a.terms = p->terms;
   a.recs = p->recs;
   a.dd = p->dd;
@@ -283,12 +256,7 @@ magnus_status run_persistent(magnus_plan_t p, void *psi, int64_t nexp, magnus_st
   a.sh_w1 = p->sh_w1;
   a.sh_u = p->sh_u;
   const bool tensor = p->opt.precision == MAGNUS_TENSOR_SLICED;
-  a.sliced = tensor && m4;
-  a.tc = tensor && !m4;
-  if (a.sliced) {
-    magnus_status ms = ensure_m4_sliced(p);
-    if (ms != MAGNUS_OK) return ms;
-  }
+  a.tc = tensor ? (m4 ? 2 : 1) : 0;
   if (a.tc) {
     if (p->tc_grid != grid) {  // partial tiles for this grid
       if (p->tc_P) cudaFree(p->tc_P);
@@ -309,20 +277,7 @@ magnus_status run_persistent(magnus_plan_t p, void *psi, int64_t nexp, magnus_st
     a.tc_wd = p->tc_wd;
     a.tc_ex = p->tc_ex;
     a.tc_P = p->tc_P;
-  }
-  for (int k = 0; k < kMaxTerms; k++) {
-    a.hslice[k] = p->hslice[k];
-    a.hexp[k] = p->hexp[k];
-  }
-  a.sl_cur = p->sl_cur;
-  a.sl_w0 = p->sl_w0;
-  a.sl_w1 = p->sl_w1;
-  a.sl_u = p->sl_u;
-  if (p->ex_sets) {
-    a.ex_cur = p->ex_sets;
-    a.ex_w0 = p->ex_sets + 128;
-    a.ex_w1 = p->ex_sets + 256;
-    a.ex_u = p->ex_sets + 384;
+    a.tc_cacc = p->tc_cacc;
   }
   a.colmax = p->colmax;
   a.m6 = p->m6;
@@ -368,11 +323,15 @@ magnus_status run_persistent(magnus_plan_t p, void *psi, int64_t nexp, magnus_st
     stats->block = p->fam == FAM_DENSE ? dense_block_size() : persistent_block_size();
     stats->fixed_sums = a.zfix != 0;
     stats->row_layout = row_layout_of_call(p, a);
+    double drift;
+    memcpy(&drift, &c.max_drift, sizeof drift);
+    stats->norm_drift = drift;
   }
   if (c.status != MAGNUS_OK) {
     const char *what = c.status == MAGNUS_ENOCONV      ? "Leja interpolation did not converge within m_max"
                        : c.status == MAGNUS_ENONFINITE ? "non-finite norm in the Leja iteration"
                        : c.status == MAGNUS_ETIMEOUT   ? "grid barrier wait timed out"
+                       : c.status == MAGNUS_EDRIFT     ? "a substep changed the state's norm beyond options.norm_check"
                                                        : "device error";
     return set_err(p, (magnus_status)c.status, "%s", what);
   }
@@ -415,6 +374,7 @@ const char *magnus_status_string(magnus_status s) {
     case MAGNUS_ENOCONV: return "MAGNUS_ENOCONV";
     case MAGNUS_ENONFINITE: return "MAGNUS_ENONFINITE";
     case MAGNUS_ETIMEOUT: return "MAGNUS_ETIMEOUT";
+    case MAGNUS_EDRIFT: return "MAGNUS_EDRIFT";
   }
   return "MAGNUS_UNKNOWN";
 }
@@ -437,6 +397,8 @@ magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms
   if (o.row_layout < MAGNUS_ROWS_AUTO || o.row_layout > MAGNUS_ROWS_SLICED)
     return set_err(nullptr, MAGNUS_EINVAL, "row_layout must be MAGNUS_ROWS_AUTO, _STAGED, _CSR or _SLICED");
   if (o.plain_values != 0 && o.plain_values != 1) return set_err(nullptr, MAGNUS_EINVAL, "plain_values must be 0 or 1");
+  if (!(o.norm_check >= 0.0) || !std::isfinite(o.norm_check))
+    return set_err(nullptr, MAGNUS_EINVAL, "norm_check must be finite and >= 0 (0 = off)");
   if (!(o.rho_max > 0.0)) return set_err(nullptr, MAGNUS_EINVAL, "rho_max must be > 0");
   if (!(o.barrier_timeout_s >= 0.0) || o.barrier_timeout_s > 600.0)
     return set_err(nullptr, MAGNUS_EINVAL, "barrier_timeout_s must be in [0, 600]");
@@ -657,8 +619,9 @@ magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms
         set_err(p, MAGNUS_EINVAL, "MAGNUS_TENSOR_SLICED needs real-valued dense terms and dim a multiple of 128");
         return fail(MAGNUS_EINVAL);
       }
-      // tcgen05 path (linear generators): 4 x 8-bit digits of every dense term and of the three
-      // vector sets, tiled in the order the tensor cores read them (columns beyond 2 nvec stay zero)
+      // tcgen05 path: 4 x 8-bit digits of every dense term and of the vector sets (substep input,
+      // w0, w1 and, for M4, one u_k per term), tiled in the order the tensor cores read them
+      // (columns beyond 2 nvec stay zero)
       int nden = 0;
       for (int k = 0; k < nterms; k++)
         if (p->terms_host[k].kind == MAGNUS_TERM_DENSE) p->tc_dslot[k] = nden++;
@@ -671,10 +634,12 @@ magnus_status magnus_plan_create(magnus_plan_t *out, int64_t dim, int32_t nterms
           PLAN_TRY(launch_slice_dense_tc(p->terms_host[k].rv, p->terms_host[k].rs, dim, p->tc_hd + (size_t)p->tc_dslot[k] * 4 * dd,
                                          p->tc_eh + (size_t)p->tc_dslot[k] * dim, p->stream));
       const size_t wset = (size_t)4 * 128 * dim;
-      PLAN_TRY(dalloc(&p->tc_wd, 3 * wset));
-      PLAN_TRY(dalloc(&p->tc_ex, (size_t)3 * 128));
-      PLAN_TRY(cudaMemsetAsync(p->tc_wd, 0, sizeof(uint16_t) * 3 * wset, p->stream));
-      PLAN_TRY(cudaMemsetAsync(p->tc_ex, 0, sizeof(int) * 3 * 128, p->stream));
+      const size_t nsets = 3 + (size_t)nterms;
+      PLAN_TRY(dalloc(&p->tc_wd, nsets * wset));
+      PLAN_TRY(dalloc(&p->tc_ex, nsets * 128));
+      PLAN_TRY(cudaMemsetAsync(p->tc_wd, 0, sizeof(uint16_t) * nsets * wset, p->stream));
+      PLAN_TRY(cudaMemsetAsync(p->tc_ex, 0, sizeof(int) * nsets * 128, p->stream));
+      PLAN_TRY(dalloc(&p->tc_cacc, nd));
       PLAN_TRY(dalloc(&p->colmax, (size_t)4 * 128));
     }
     if (mf) {

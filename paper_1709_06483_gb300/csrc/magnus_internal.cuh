@@ -116,7 +116,17 @@ struct Counters {
   long long n_exp, n_substeps, n_matvec, n_termapply;
   int max_m;
   int status;
+  unsigned long long max_drift;  // bits of the largest | ||p|| - ||v|| | / ||v|| (non-negative doubles order like their bits)
 };
+
+// After a substep: record | ||p|| - ||v|| | / ||v|| (block 0) and say whether it breaks the norm check
+// (every block takes the same decision: pn and vn are the shared totals).
+__device__ __forceinline__ bool drift_fails(double pn, double vn, double tol_abs, double tol_rel, double check,
+                                            Counters *c, bool record) {
+  const double d = fabs(pn - vn);
+  if (record && vn > 0.0) atomicMax(&c->max_drift, (unsigned long long)__double_as_longlong(d / vn));
+  return check > 0.0 && d > check * (tol_abs + tol_rel * vn) + 1e-13 * vn;
+}
 
 // ---------------------------------------------------------------- complex helpers
 __host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
@@ -190,6 +200,7 @@ struct PersistArgs {
   int m_max;
   int64_t nexp;
   double tol_rel, tol_abs;
+  double norm_check;       // > 0: a substep whose norm drift exceeds norm_check (tol_abs + tol_rel ||v||) + 1e-13 ||v|| fails with MAGNUS_EDRIFT
   const Term *terms;       // device [nterms]
   const ExpRec *recs;      // device [nexp]
   const double2 *dd;       // device [nexp][m_max+1]
@@ -219,22 +230,18 @@ struct PersistArgs {
   // column-maximum slots of the slicing passes ([4][128], zero at launch: three rotate, the fourth
   // collects the maxima the tcgen05 path gathers in its epilogue)
   double2 *m6;  // M6 intermediate vectors, kM6Slots x [nvec][dim]
-  // FAM_DENSE with MAGNUS_TENSOR_SLICED on tcgen05 (linear generators): 4 x 8-bit digits
-  int tc;
+  // FAM_DENSE with MAGNUS_TENSOR_SLICED on tcgen05 (linear generators and M4): 4 x 8-bit digits
+  int tc;                         // tcgen05 digit products: 1 linear generators, 2 M4
   int tc_ndense, tc_slots, tc_T;
   long long tc_N;
   long long tc_spins;             // spin budget of every mbarrier wait
   int tc_dslot[kMaxTerms];        // dense term k -> its index among the dense terms
   const void *tc_hd;              // dense-term digits, tiled [ndense][dim/128][dim/8][4][128][8]
   const int *tc_eh;               // row exponents [ndense][dim]
-  void *tc_wd;                    // vector-set digits, tiled [3][dim/8][4][128][8] (sets: substep input, w0, w1)
-  int *tc_ex;                     // their column exponents [3][128]
+  void *tc_wd;                    // vector-set digits, tiled [3 + nterms][dim/8][4][128][8] (sets: substep input, w0, w1, u_k)
+  int *tc_ex;                     // their column exponents [3 + nterms][128]
+  double2 *tc_cacc;               // M4: the commutator sum of the current Leja iteration [nvec][dim]
   double *tc_P;                   // partial product tiles [grid][slots][128][128]
-  int sliced;
-  const void *hslice[kMaxTerms];
-  const int *hexp[kMaxTerms];
-  void *sl_cur, *sl_w0, *sl_w1, *sl_u;
-  int *ex_cur, *ex_w0, *ex_w1, *ex_u;
   // column-maximum slots of the slicing passes ([4][128], zero at launch): three rotate, the fourth
   // collects the maxima the tcgen05 path gathers in its epilogue
   unsigned long long *colmax;
@@ -291,8 +298,6 @@ int dense_tc_chunk(int64_t D);  // K per exact chunk of the tcgen05 digit produc
 int dense_tc_slots(int ndense, int64_t D, int grid);
 
 // Dense term (complex128, real parts used) -> bf16 digits [5][D][D] and row exponents [D].
-cudaError_t launch_slice_dense(const double *Hr, int rs, int64_t D, void *digits, int *rexp, cudaStream_t st);
-size_t dense_sliced_smem_bytes();
 
 // H (real parts Hr[e * rs]) -> FP32 (hi, lo) pairs, n entries.
 cudaError_t launch_split_dense(const double *Hr, int rs, float2 *out, int64_t n, cudaStream_t st);

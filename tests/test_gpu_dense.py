@@ -141,11 +141,10 @@ def test_fp32_split_rejects_complex_terms(mg):
 @pytest.mark.parametrize("field", ["dense", "mfree"])
 @pytest.mark.parametrize("nspins,nvec", [(8, 6), (7, 1), (9, 64)])
 def test_tensor_sliced_precision(mg, variant, field, nspins, nvec):
-    """MAGNUS_TENSOR_SLICED: dense matvecs as exact bf16 digit products on the tensor cores.
+    """MAGNUS_TENSOR_SLICED: dense matvecs as exact bf16 digit products on the tcgen05 tensor cores
+    (Cf4: one product phase per Leja iteration; M4: u_k = H_k w, then the commutator phase).
     Stated accuracy: state error <= 1e-9 relative to the FP64 oracle; the Leja degrees may differ
     by rounding, so they are not compared."""
-    if variant == "M4" and nvec == 64:
-        pytest.skip("covered by the smaller M4 cases")
     c = mi.workload3(nvec=nvec, nspins=nspins, h=0.02, nsteps=6)
     Hs = mg.build_longrange_dense(c.nspins, c.hz, 1.5, c.delta)
     Hd = mg.build_field_x_dense(c.nspins) if field == "dense" else mg.FieldXTerm(c.nspins)
@@ -158,6 +157,31 @@ def test_tensor_sliced_precision(mg, variant, field, nspins, nvec):
     psi0 = c.psi0.reshape(nvec, -1)
     check = range(nvec) if nvec <= 8 else [0, 1, 31, 62, 63]
     errs = [rel(out[v], P.propagate(psi0[v], 0.0, c.h, c.nsteps, variant)) for v in check]
+    assert max(errs) < 1e-9, errs
+
+
+@pytest.mark.parametrize("nterms", [1, 3])
+def test_tensor_sliced_m4_commutator_pairs(mg, nterms):
+    """M4 on the tensor cores with one term (no commutator: the commutator sum stays zero) and with
+    three terms (two dense terms and a matrix-free field: three commutator pairs, each its own
+    product phase, summed in pair order), against the FP64 oracle with the same terms."""
+    c = mi.workload3(nvec=5, nspins=8, h=0.02, nsteps=6)
+    Hs = mg.build_longrange_dense(c.nspins, c.hz, 1.5, c.delta)
+    Hd = mg.build_field_x_dense(c.nspins)
+    f = (c.drive_a0, c.drive_ac, c.drive_as, c.drive_om)
+    g = (0.2, [-0.15], [0.1], [1.3])  # the third term's drive
+    terms = [mg.DenseTerm(Hs), mg.DenseTerm(Hd), mg.FieldXTerm(c.nspins)][:nterms]
+    drives = [mg.Drive.const(), mg.Drive(*f), mg.Drive(*g)][:nterms]
+    plan = mg.Plan(c.dim, terms, drives, nvec=5, precision=mg.TENSOR_SLICED)
+    psi = cuda(c.psi0)
+    plan.propagate(psi, 0.0, c.h, c.nsteps, "M4")
+    H_or = [oracle.longrange_dense(c.nspins, c.hz, 1.5, c.delta), oracle.field_x_dense(c.nspins),
+            oracle.field_x_dense(c.nspins)][:nterms]
+    C_or = [oracle.Coeff.const(), oracle.Coeff(*f), oracle.Coeff(*g)][:nterms]
+    P = oracle.Problem(H_or, C_or, tol=1e-10)
+    out = psi.cpu().numpy().reshape(5, -1)
+    psi0 = c.psi0.reshape(5, -1)
+    errs = [rel(out[v], P.propagate(psi0[v], 0.0, c.h, c.nsteps, "M4")) for v in range(5)]
     assert max(errs) < 1e-9, errs
 
 
@@ -241,24 +265,26 @@ def test_dense13_full_size_tensor_sampled(mg, dense13):
         assert rel(out[v], ref) < 1e-9, (v, rel(out[v], ref))
 
 
-@pytest.mark.parametrize("precision,tol", [("tensor_sliced", 1e-8), ("fp32_split", 1e-10)])
-def test_reduced_precision_over_a_whole_propagation(mg, precision, tol):
-    """The reduced-precision dense paths over the whole propagation t in [0, 1] (100 Cf4 steps of
-    0.01), 12 spins (dim 4096), 64 states in the bench's launch configuration: states 0 and 63
-    against the FP64 oracle.  Bound: the 1e-8 state error the tensor-core path is held to (its
-    neglected digit products accumulate over the steps), 1e-10 for the FP32 split (error-free
-    products).  The oracle runs its OpenMP build (the checker's bits on all host cores)."""
+@pytest.mark.parametrize("precision,tol,variant", [("tensor_sliced", 1e-8, "CF4"), ("fp32_split", 1e-10, "CF4"),
+                                                   ("tensor_sliced", 1e-8, "M4")])
+def test_reduced_precision_over_a_whole_propagation(mg, precision, tol, variant):
+    """The reduced-precision dense paths over the whole propagation t in [0, 1] (100 steps of 0.01,
+    Cf4, and M4 on the tensor cores), 12 spins (dim 4096), 64 states in the bench's launch
+    configuration: states 0 and 63 against the FP64 oracle.  Bound: the 1e-8 state error the
+    tensor-core path is held to (its neglected digit products accumulate over the steps), 1e-10 for
+    the FP32 split (error-free products).  The oracle runs its OpenMP build (the checker's bits on
+    all host cores)."""
     c = mi.workload3(nvec=64, nspins=12, h=0.01, nsteps=100)
     Hs = mg.build_longrange_dense(c.nspins, c.hz, 1.5, c.delta)
     Hd = mg.build_field_x_dense(c.nspins)
     prec = {"tensor_sliced": mg.TENSOR_SLICED, "fp32_split": mg.FP32_SPLIT}[precision]
     plan = mg.Plan(c.dim, [mg.DenseTerm(Hs), mg.DenseTerm(Hd)], drive_pair(mg, c), nvec=64, precision=prec)
     psi = cuda(c.psi0)
-    plan.propagate(psi, 0.0, c.h, c.nsteps, "CF4")
+    plan.propagate(psi, 0.0, c.h, c.nsteps, variant)
     out = psi.cpu().numpy()
     f = oracle.Coeff(c.drive_a0, c.drive_ac, c.drive_as, c.drive_om)
     P = oracle.Problem([oracle.longrange_dense(c.nspins, c.hz, 1.5, c.delta), oracle.field_x_dense(c.nspins)],
                        [oracle.Coeff.const(), f], threaded=True)
     for v in (0, 63):
-        ref = P.propagate(c.psi0[v], 0.0, c.h, c.nsteps, "CF4")
-        assert rel(out[v], ref) < tol, (precision, v, rel(out[v], ref))
+        ref = P.propagate(c.psi0[v], 0.0, c.h, c.nsteps, variant)
+        assert rel(out[v], ref) < tol, (precision, variant, v, rel(out[v], ref))

@@ -38,6 +38,7 @@ def test_status_strings_without_gpu():
     mg.build_lib = None
     lib = mg.load()
     assert lib.magnus_status_string(mg.ENOCONV) == b"MAGNUS_ENOCONV"
+    assert lib.magnus_status_string(mg.EDRIFT) == b"MAGNUS_EDRIFT"
     assert lib.magnus_xxz_nnz(20) == 31981568 - 20 * (1 << 20)  # 2^20 + 19 * 2^19
 
 
@@ -46,9 +47,11 @@ _STRUCTS = {
     "magnus_term": ("Term", ["kind", "nspins", "nnz", "rowptr", "col", "val", "J", "hz", "delta"]),
     "magnus_coeff": ("Coeff", ["a0", "nmodes", "_pad", "ac", "as", "om"]),
     "magnus_options": ("Options", ["tol_rel", "tol_abs", "rho_max", "m_max", "nvec", "ctas", "precision",
-                                   "barrier_timeout_s", "test_skip_arrival", "interval", "fixed_sums", "row_layout", "plain_values", "_reserved"]),
+                                   "barrier_timeout_s", "test_skip_arrival", "interval", "fixed_sums", "row_layout", "plain_values", "_reserved",
+                                   "norm_check"]),
     "magnus_stats": ("Stats", ["n_exp", "n_substeps", "n_matvec", "n_termapply", "max_m", "status", "m_log",
-                               "m_log_cap", "kernel_ms", "grid", "block", "fixed_sums", "row_layout"]),
+                               "m_log_cap", "kernel_ms", "grid", "block", "fixed_sums", "row_layout",
+                               "norm_drift"]),
     "magnus_batch_item": ("BatchItem", ["dim", "nterms", "_pad", "terms", "coeffs"]),
     "magnus_batch_stats": ("BatchStats", ["n_exp", "n_substeps", "n_matvec", "n_termapply", "max_m", "status",
                                           "m_log", "m_log_cap_per_item", "graph_ms", "block", "cluster",

@@ -516,6 +516,31 @@ def test_lanczos_interval_dense_complex_and_small_dim():
     assert abs(a - (ev[0] - 0.01 * W)) < 1e-9 * W and abs(b - (ev[-1] + 0.01 * W)) < 1e-9 * W
 
 
+@pytest.mark.parametrize("lam_top", [1.1, 1.2])
+def test_lanczos_heuristic_missing_an_eigenvalue_is_not_silent(lam_top):
+    """The Lanczos enclosure is no proof: for an eigenvector orthogonal to its start vector with an
+    eigenvalue just above the rest of the spectrum (tests/hidden_eigen.py), the interval ends below
+    that eigenvalue.  The propagation on it still matches the exact exp(-i T H) psi (scipy's expm)
+    to the Leja tolerance: the error estimate |d_j| ||w_j|| is taken on the vector itself, whose
+    component along the missed eigenvector is resolved however the points were placed, and the
+    norm of the result (the a posteriori check's quantity) stays 1 to the same level.  Steps from
+    0.2 to 20 (one substep to many)."""
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    import hidden_eigen
+    H, Q = hidden_eigen.hidden_top(256, lam_top)
+    P = oracle.Problem([H], [oracle.Coeff.const()], interval="lanczos")
+    a, b = P.interval(0)
+    assert b < lam_top - 0.05, (a, b)  # the enclosure misses the top eigenvalue
+    assert b > 1.0  # and holds the rest
+    psi = Q[:, 0] + 0.1 * Q[:, 5]
+    psi /= np.linalg.norm(psi)
+    for h, ns in ((0.2, 5), (1.0, 1), (4.0, 1), (20.0, 1)):
+        out = P.propagate(psi, 0.0, h, ns, "CF4")
+        ref = scipy_linalg.expm(-1j * (h * ns) * H) @ psi
+        assert np.linalg.norm(out - ref) < 1e-9, (h, np.linalg.norm(out - ref))
+        assert abs(np.linalg.norm(out) - 1.0) < 1e-9
+
+
 def test_lanczos_residuals_on_three_eigenvalues():
     """Unconverged Ritz values, where the residual term of the enclosure matters.  H has the
     eigenvalues -1, 0, 1 (16 copies each, rotated so that Gershgorin is much wider).  Lanczos on H
