@@ -313,6 +313,7 @@ def measure_xxz(mg, c, terms, storage, variant, steps, warmup, repeats, interval
            "ms_per_step": round(ms[mid] / steps, 4), "leja_iterations": st["n_matvec"], "max_degree": st["max_m"],
            "us_per_leja_iteration": round(st["kernel_ms"] * 1e3 / max(1, st["n_matvec"]), 2),
            "fixed_sums": st["fixed_sums"], "row_layout": ROW_LAYOUT_NAMES.get(st["row_layout"]), "grid": st["grid"],
+           "norm_drift": st["norm_drift"],
            "roofline": xxz_roofline(c, rkey, variant, nnz_terms, st, st["kernel_ms"], traffic_key),
            "clocks": clk.summary()}
     if keep_state:
@@ -414,7 +415,10 @@ def run_ours(args):
                    "min": head["min"], "max": head["max"]},
         "matvec_gbs": head["roofline"]["hbm_gbs"],
         "leja": {"iterations": head["leja_iterations"], "max_degree": head["max_degree"],
-                 "us_per_iteration": head["us_per_leja_iteration"]},
+                 "us_per_iteration": head["us_per_leja_iteration"],
+                 "norm_drift": head["norm_drift"],
+                 "norm_drift_how": "largest | ||p|| - ||v|| | / ||v|| over the substeps (the a posteriori check's "
+                                   "quantity; 0 up to rounding and the Leja tolerance)"},
         "roofline": head["roofline"],
         "e2e": e2e,
         "gpu_launches": 2 * head["repeats"],
@@ -452,6 +456,10 @@ def run_ours(args):
         line["workloads"] = run_all_workloads(args, mg, mi, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(variant, args.cpu_steps, args.interval)
+        if "workloads" in line:
+            for name, rec in workload_cpu_baselines().items():
+                if name in line["workloads"]:
+                    line["workloads"][name]["cpu_oracle"] = rec
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -926,13 +934,13 @@ def oracle_problem(c, interval="gershgorin"):
     return oracle.Problem([Hs, Hd], [oracle.Coeff.const(), f], interval=interval)
 
 
-def _oracle_timing(steps, variant, interval, threaded):
+def _oracle_timing(steps, variant, interval, threaded, workload="xxz20", count=1):
     """Run oracle/cpu_timing.py in a process of its own (no CUDA context) and return its record."""
     env = dict(os.environ)
     if threaded:
         env["OMP_NUM_THREADS"] = str(os.cpu_count() or 1)
     cmd = [sys.executable, "-m", "oracle.cpu_timing", "--steps", str(steps), "--variant", variant,
-           "--interval", interval] + (["--threaded"] if threaded else [])
+           "--interval", interval, "--workload", workload, "--count", str(count)] + (["--threaded"] if threaded else [])
     out = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
     if out.returncode != 0:
         raise RuntimeError(out.stderr[-500:])
@@ -957,6 +965,43 @@ def cpu_baseline(variant, nsteps, interval="gershgorin"):
     except Exception as exc:  # noqa: BLE001 - e.g. no OpenMP runtime on the host
         rec["all_cores"] = {"unavailable": repr(exc)[:200]}
     return rec
+
+
+def workload_cpu_baselines():
+    """The FP64 CPU oracle on a bounded sample of each of the other workloads (a few seconds each),
+    single-threaded and on every core, in the unit of the workload's GPU rate: the 10-spin chain
+    whole (100 Cf4 steps); the dense chain one state for one step (scaled to 64 states); the batch
+    the first 32 chains for 10 steps (scaled by rows to all 512); the adjoint the first 20 of its
+    1000 steps (forward and gradient)."""
+    specs = {
+        "cfg1_xxz10_csr_cf4": ("xxz10", 100, 1, "steps/s",
+                               lambda r: r["steps"] / r["seconds"], "all 100 CF4 steps of the 10-spin chain"),
+        "cfg3_dense13": ("dense13", 1, 1, "steps/s (64 states)",
+                         lambda r: r["steps"] / (r["seconds"] * 64 / r["states"]),
+                         "1 CF4 step of 1 of the 64 states, scaled to 64 states"),
+        "cfg4_batch512": ("batch512", 10, 32, "steps/s (all 512 chains per step)",
+                          lambda r: r["steps"] / (r["seconds"] * r["rows_all"] / r["rows"]),
+                          "10 CF4 steps of the first 32 chains, scaled by rows to all 512"),
+        "cfg5_adjoint16": ("adjoint16", 20, 1, "adjoint steps/s (forward + gradient)",
+                           lambda r: r["steps"] / r["seconds"], "the first 20 of the 1000 CF4 steps, forward and gradient"),
+    }
+    out = {}
+    for name, (wl, steps, count, unit, rate, sample) in specs.items():
+        try:
+            one = _oracle_timing(steps, "CF4", "gershgorin", False, wl, count)
+            rec = {"value": round(rate(one), 6), "unit": unit, "cores": 1, "kind": "oracle", "sample": sample,
+                   "seconds": round(one["seconds"], 3)}
+            try:
+                allc = _oracle_timing(steps, "CF4", "gershgorin", True, wl, count)
+                rec["all_cores"] = {"value": round(rate(allc), 6), "unit": unit, "cores": allc["threads"],
+                                    "kind": "oracle (OpenMP build of the same source)",
+                                    "seconds": round(allc["seconds"], 3)}
+            except Exception as exc:  # noqa: BLE001
+                rec["all_cores"] = {"unavailable": repr(exc)[:200]}
+            out[name] = rec
+        except Exception as exc:  # noqa: BLE001 - the rest still runs
+            out[name] = {"error": repr(exc)[:200]}
+    return out
 
 
 def run_reference(args):
