@@ -52,7 +52,8 @@ struct BatchArgs {
   const double *xi;
   const BatchItem *items;
   const int *order;       // processing order (largest first)
-  unsigned *next;         // queue head, zero before the launch
+  unsigned *next;         // queue heads, zero before the launch: [0] items shared by a cluster, [1] the rest
+  int nbig;               // the first nbig items (in processing order) are shared by the CTAs of a cluster
   Counters *counters;
 };
 
@@ -62,8 +63,10 @@ using namespace rows;
 
 // One problem per thread-block cluster: the cluster's CTAs split the problem's rows, exchange their
 // partial norms through distributed shared memory and synchronise with the hardware cluster
-// barrier (release/acquire at cluster scope), so a large chain runs on several SMs at once.
-// Cluster size 1 is the plain CTA-per-problem case.  ZF: the instantiation for linear generators
+// barrier (release/acquire at cluster scope), so a large chain runs on several SMs at once.  Only
+// the problems larger than one CTA's fair share of all rows are shared so (the first A.nbig in
+// the largest-first order); after them every CTA takes the remaining problems alone from a second
+// queue.  Cluster size 1 is the plain CTA-per-problem case.  ZF: the instantiation for linear generators
 // whose pattern terms are summed in fixed point (as in the single-problem kernel); it also
 // tracks the largest component of every vector, from which the fixed-point scales follow.
 template <int FAM, int BS, bool ZF>
@@ -84,6 +87,12 @@ __global__ void __launch_bounds__(BS) k_batched(BatchArgs A) {
 
   cg::cluster_group cl = cg::this_cluster();
   const unsigned crank = cl.block_rank(), csize = cl.num_blocks();
+  // solo: after the shared items, every CTA takes the remaining (small) items alone, from a queue
+  // of their own, with CTA-local synchronisation only
+  bool solo = false;
+  auto csync = [&]() {
+    if (solo) __syncthreads(); else cl.sync();
+  };
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   unsigned slot = 0;
   // sums of two values over all threads of the cluster, identical in every thread afterwards
@@ -116,12 +125,12 @@ __global__ void __launch_bounds__(BS) k_batched(BatchArgs A) {
       s_part[slot][2] = __hiloint2double((int)n0, 0);
       s_part[slot][3] = __hiloint2double((int)n1, 0);
     }
-    cl.sync();
+    csync();
     if (tid == 0) {
       double y0 = 0.0, y1 = 0.0;
       unsigned n0 = 0, n1 = 0;
-      for (unsigned q = 0; q < csize; q++) {
-        const double *rp = cl.map_shared_rank(&s_part[slot][0], q);
+      for (unsigned q = 0; q < (solo ? 1u : csize); q++) {
+        const double *rp = solo ? &s_part[slot][0] : cl.map_shared_rank(&s_part[slot][0], q);
         y0 += rp[0];
         y1 += rp[1];
         if (ZF) { n0 = max(n0, (unsigned)__double2hiint(rp[2])); n1 = max(n1, (unsigned)__double2hiint(rp[3])); }
@@ -136,20 +145,31 @@ __global__ void __launch_bounds__(BS) k_batched(BatchArgs A) {
   };
 
   for (;;) {
-    cl.sync();
-    if (crank == 0 && tid == 0) s_next = (int)atomicAdd(A.next, 1u);
-    cl.sync();
-    if (tid == 0) s_item = *cl.map_shared_rank(&s_next, 0);
-    cl.sync();  // every CTA has read rank 0's index before any CTA may leave the kernel
-    const int q = s_item;
+    int q = A.count;
+    if (!solo) {
+      cl.sync();
+      if (crank == 0 && tid == 0) s_next = (int)atomicAdd(A.next, 1u);
+      cl.sync();
+      if (tid == 0) s_item = *cl.map_shared_rank(&s_next, 0);
+      cl.sync();  // every CTA has read rank 0's index before any CTA may leave or go solo
+      q = s_item;
+      if (q >= A.nbig) solo = true;  // the same decision in every CTA of the cluster
+    }
+    if (solo) {
+      __syncthreads();
+      if (tid == 0) s_item = A.nbig + (int)atomicAdd(A.next + 1, 1u);
+      __syncthreads();
+      q = s_item;
+    }
     if (q >= A.count) break;
+    const unsigned cr = solo ? 0u : crank, cn = solo ? 1u : csize;  // this CTA's share of the item
     if (tid == 0) sI = A.items[A.order[q]];
     __syncthreads();
     const int64_t D = sI.dim;
     const int nt = sI.nterms;
     // this CTA's rows: whole warps of consecutive rows
-    const int64_t rows_per = (((D + csize - 1) / csize) + 31) & ~(int64_t)31;
-    const int64_t lo = min(D, (int64_t)crank * rows_per), hi = min(D, lo + rows_per);
+    const int64_t rows_per = (((D + cn - 1) / cn) + 31) & ~(int64_t)31;
+    const int64_t lo = min(D, (int64_t)cr * rows_per), hi = min(D, lo + rows_per);
     for (int i = tid; i < nt * (int)sizeof(Term) / 4; i += BS)
       reinterpret_cast<int *>(sT)[i] = reinterpret_cast<const int *>(sI.terms)[i];
     __syncthreads();
@@ -211,7 +231,7 @@ __global__ void __launch_bounds__(BS) k_batched(BatchArgs A) {
       if (!(R.gamma > 0.0)) {
         const double2 ph = d[0];
         for (int64_t r = lo + tid; r < hi; r += BS) nxt[r] = cmul(ph, cur[r]);
-        cl.sync();
+        csync();
         vm *= sqrt(cabs2(ph)) * (1.0 + 0x1p-40);
         double2 *tmp = cur; cur = nxt; nxt = tmp;
         continue;
@@ -224,7 +244,7 @@ __global__ void __launch_bounds__(BS) k_batched(BatchArgs A) {
         if (ZF) {  // fixed-point copy of the substep input
           zs_src = fix_scale(vm, sI.zhb);
           for (int64_t r = lo + tid; r < hi; r += BS) sI.zc[r] = fix2(cur[r], zs_src);
-          cl.sync();
+          csync();
         }
         for (int j = 1; j <= A.m_max; j++) {
           const double2 *src = (j == 1) ? cur : (((j - 2) & 1) ? sI.w1 : sI.w0);
@@ -265,7 +285,7 @@ __global__ void __launch_bounds__(BS) k_batched(BatchArgs A) {
           if (R.mode == MODE_M4) {
             for (int64_t r = lo + tid; r < hi; r += BS)
               for (int k = 0; k < nt; k++) sI.u[(size_t)k * D + r] = Op<FAM>::term(cx, k, src, r);
-            cl.sync();
+            csync();
           }
           double sw = 0.0, sp = 0.0;
           for (int64_t r = lo + tid; r < hi; r += BS) {
@@ -304,7 +324,7 @@ __global__ void __launch_bounds__(BS) k_batched(BatchArgs A) {
           ep = ej;
         }
         if (status == MAGNUS_OK && m == 0) { status = MAGNUS_ENOCONV; m = A.m_max; }
-        if (crank == 0 && tid == 0) {
+        if (cr == 0 && tid == 0) {
           atomicAdd((unsigned long long *)&A.counters->n_matvec, (unsigned long long)m);
           atomicAdd((unsigned long long *)&A.counters->n_termapply,
                     (unsigned long long)m * nt * (R.mode == MODE_M4 ? 2 : 1));
@@ -317,10 +337,10 @@ __global__ void __launch_bounds__(BS) k_batched(BatchArgs A) {
         vm = pm;
         double2 *tmp = cur; cur = nxt; nxt = tmp;
       }
-      if (crank == 0 && tid == 0) atomicAdd((unsigned long long *)&A.counters->n_exp, 1ULL);
+      if (cr == 0 && tid == 0) atomicAdd((unsigned long long *)&A.counters->n_exp, 1ULL);
     }
     if (status != MAGNUS_OK) {
-      if (crank == 0 && tid == 0) atomicCAS(&A.counters->status, 0, status);
+      if (cr == 0 && tid == 0) atomicCAS(&A.counters->status, 0, status);
     } else if (cur != sI.psi) {
       for (int64_t r = lo + tid; r < hi; r += BS) sI.psi[r] = cur[r];
     }
@@ -380,6 +400,7 @@ struct magnus_batch_s {
   std::vector<size_t> zoff;
   std::vector<int> zhb, zreal;
   int *order = nullptr;
+  std::vector<int> order_host;    // the processing order (largest first)
   BatchItem *items_dev = nullptr;
   std::vector<BatchItem> items_host;
   ExpRec *recs = nullptr;
@@ -445,7 +466,7 @@ magnus_status enqueue_run(magnus_batch_t b, int variant, double t0, double h, in
   const bool zf = b->zf && variant != MAGNUS_M4;
   BTRY(b, launch_exp_setup_batch(variant, t0, h, nsteps, b->count, b->nterms_dev, b->coeffs, b->term_ab, b->xi,
                                  b->opt.m_max, b->opt.rho_max, b->recs, b->dd, b->recs_cap, b->stream));
-  BTRY(b, cudaMemsetAsync(b->next, 0, sizeof(unsigned), b->stream));
+  BTRY(b, cudaMemsetAsync(b->next, 0, 2 * sizeof(unsigned), b->stream));
   BTRY(b, cudaMemsetAsync(b->counters, 0, sizeof(Counters), b->stream));
   BatchArgs A{};
   A.count = b->count;
@@ -458,12 +479,23 @@ magnus_status enqueue_run(magnus_batch_t b, int variant, double t0, double h, in
   A.order = b->order;
   A.next = b->next;
   A.counters = b->counters;
+  A.nbig = b->count;
   int per_sm = 0;
   BTRY(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel_for(b->fam, bs, zf), bs, 0));
   int grid = b->num_sms * std::max(1, per_sm);
   if (b->opt.ctas > 0) grid = std::min(grid, b->opt.ctas);
   grid = std::min(grid, b->count * cs);
   grid = std::max(cs, grid - grid % cs);
+  if (cs > 1) {
+    // a cluster shares only the items larger than one CTA's fair share of all rows; after them its
+    // CTAs take the rest alone (splitting small items only adds cluster barriers)
+    int64_t total = 0;
+    for (int i = 0; i < b->count; i++) total += b->dims[i];
+    const int64_t fair = total / grid;
+    int nbig = 0;
+    while (nbig < b->count && b->dims[b->order_host[nbig]] > fair) nbig++;
+    A.nbig = nbig;
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(bs);
@@ -596,7 +628,7 @@ MAGNUS_API magnus_status magnus_batch_create(magnus_batch_t *out, int32_t count,
   BCREATE(balloc(b, &b->xi, o.m_max + 1));
   BCREATE(balloc(b, &b->cand, 2 * (o.m_max + 1)));
   BCREATE(balloc(b, &b->counter, 1));
-  BCREATE(balloc(b, &b->next, 1));
+  BCREATE(balloc(b, &b->next, 2));
   BCREATE(balloc(b, &b->counters, 1));
   BCREATE(balloc(b, &b->order, count));
   BCREATE(balloc(b, &b->nterms_dev, count));
@@ -683,6 +715,7 @@ MAGNUS_API magnus_status magnus_batch_create(magnus_batch_t *out, int32_t count,
   std::iota(ord.begin(), ord.end(), 0);
   std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return b->dims[x] > b->dims[y]; });
   BCREATE(cudaMemcpyAsync(b->order, ord.data(), sizeof(int) * count, cudaMemcpyHostToDevice, b->stream));
+  b->order_host = ord;
   BCREATE(cudaMemcpyAsync(b->nterms_dev, b->nterms.data(), sizeof(int) * count, cudaMemcpyHostToDevice, b->stream));
   std::vector<double> ab((size_t)count * 2 * kMaxTerms);
   BCREATE(cudaMemcpyAsync(ab.data(), b->term_ab, sizeof(double) * ab.size(), cudaMemcpyDeviceToHost, b->stream));

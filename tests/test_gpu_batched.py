@@ -81,6 +81,25 @@ def test_every_cta_and_cluster_size(mg, small_chains, bs, cs):
         assert rel(psis[i].cpu().numpy(), ref) < REL_TOL
 
 
+@pytest.mark.parametrize("cs", [2, 4])
+def test_shared_large_item_then_small_items_alone(mg, cs):
+    """One chain far above a CTA's fair share of the rows (shared by the CTAs of a cluster) and ten
+    small ones (taken by single CTAs from the second queue once the shared items are handed out),
+    Cf4 with fixed-point sums and M4 in FP64, against the oracle."""
+    big = mi.xxz_chain(60, 12, 0.01, 6)
+    small = [mi.xxz_chain(61 + i, 5, 0.01, 6) for i in range(10)]
+    chains = [small[0], big] + small[1:]  # the large one is not first in the list
+    for variant in ("CF4", "M4"):
+        B = mg.Batch(problems(mg, chains, "csr"), ctas=-(256 + 65536 * cs))
+        psis = [torch.from_numpy(c.psi0.copy()).cuda() for c in chains]
+        st = B.propagate(psis, 0.0, 0.01, 6, variant)
+        assert st["cluster"] == cs
+        for i, c in enumerate(chains):
+            ref, _ = oracle_run(c, 0.0, 0.01, 6, variant)
+            assert rel(psis[i].cpu().numpy(), ref) < REL_TOL, (variant, i)
+        B.close()
+
+
 def test_graph_replay_and_continuation(mg, small_chains):
     """Two calls of 6 steps (the second replays a new graph from t0 = 6h) equal one run of 12 steps;
     a third identical call replays the cached graph."""
