@@ -216,6 +216,7 @@ class ClockSampler:
 # plan set-up that chooses the matrices' layout and the kernel instantiation)
 PERSISTENT_SOURCES = ("leja_persistent.cu", "rows.cuh", "csr_stage.cuh", "tcgen05.cuh", "persist_common.cuh",
                       "magnus_internal.cuh", "magnus_api.cu")
+BATCH_SOURCES = ("batched.cu", "rows.cuh", "persist_common.cuh", "magnus_internal.cuh")
 DENSE_TC_SOURCES = ("dense_persistent.cu", "dense_tc.cuh", "tcgen05.cuh", "persist_common.cuh", "magnus_internal.cuh")
 
 
@@ -643,7 +644,8 @@ def run_dense13(args):
 
 
 # --------------------------------------------------------------------------- batched workload
-def batch_workload(mg, mi, local, steps=100, storage="csr", fixed=True, variant="CF4", warmup=1, sample_every=32):
+def batch_workload(mg, mi, local, steps=100, storage="csr", fixed=True, variant="CF4", warmup=1, sample_every=32,
+                   config=None):
     """512 independent XXZ chains of 8-14 spins (dims 256..16384), per-chain drive A cos(w t), Cf4,
     h = 0.01, one persistent launch under a replayed CUDA graph.  A step advances every chain by one
     Magnus step.  Compared with one plan and launch per chain on every sample_every-th chain."""
@@ -658,7 +660,8 @@ def batch_workload(mg, mi, local, steps=100, storage="csr", fixed=True, variant=
             nnz_c += terms[1].col.numel()
         probs.append((c.dim, terms, drives(mg, c)))
     nnz = nnz_s + nnz_c
-    B = mg.Batch(probs, fixed_sums=fixed)
+    # config (CTA size, cluster size) fixes the launch shape; None lets the batch's autotuner choose
+    B = mg.Batch(probs, fixed_sums=fixed, **({"ctas": -(config[0] + 65536 * config[1])} if config else {}))
     psi0 = [torch.from_numpy(c.psi0).cuda() for c in chains]
     psis = [p.clone() for p in psi0]
     B.propagate(psis, 0.0, 0.01, warmup or 1, variant)  # autotune + warm-up
@@ -714,6 +717,9 @@ def batch_workload(mg, mi, local, steps=100, storage="csr", fixed=True, variant=
     share = len(sample) / len(chains)
     seq_rate = seq_steps / (seq_ms / share / 1e3)
     batch_rate = steps / (gms / 1e3)
+    # DRAM bytes per step from the committed capture of this launch shape, if it matches the sources
+    tkey = f"batch512_{storage}_{variant}_{st['block']}x{st['cluster']}" + ("_fixed" if fixed else "")
+    t_step = profiled_traffic(tkey, BATCH_SOURCES)
     B.close()
     return {
         "workload": f"512 XXZ chains of 8-14 spins, {storage}, {variant}, h = 0.01, {steps} steps per graph replay",
@@ -733,7 +739,8 @@ def batch_workload(mg, mi, local, steps=100, storage="csr", fixed=True, variant=
                            "unit": "TFLOP/s", "frac": round(tflops / FP64_PEAK_TFLOPS, 4)}),
                          kernel="k_batched", hbm_gbs=round(gbs, 1), hbm_frac=round(gbs / hbm_peak, 4),
                          fp64_tflops=round(tflops, 4), fp64_frac=round(tflops / FP64_PEAK_TFLOPS, 4),
-                         traffic=None, note="graph time includes the batch's setup launch"),
+                         traffic=None if t_step is None else int(t_step * steps),
+                         traffic_key=tkey, note="graph time includes the batch's setup launch"),
         "wall_ms": round(wall * 1e3, 2), "clocks": clk.summary(),
         "gpu_launches_detail": "graph: k_exp_setup_batch + k_batched (plus two memsets)"}
 
@@ -747,8 +754,9 @@ def run_batch512(args):
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     mg.load()
+    cfg = tuple(int(x) for x in args.batch_config.split("x")) if args.batch_config else None
     r = batch_workload(mg, mi, local, steps=args.steps, storage=args.storage, fixed=bool(args.fixed_sums),
-                       variant=args.variant, warmup=args.warmup, sample_every=16)
+                       variant=args.variant, warmup=args.warmup, sample_every=16, config=cfg)
     line = {
         "metric": METRIC, "value": r["steps_per_s"], "unit": r["unit"], "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
@@ -1055,6 +1063,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=16,
                     help="steps of the CPU oracle sample (about 12 s on one Grace core)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-config", default="", help="batch512 only: CTAxCLUSTER (e.g. 1024x1) instead of the "
+                    "autotuner's choice")
     ap.add_argument("--spins", type=int, default=13, help="dense13 only: chain length (profiling smaller cases)")
     ap.add_argument("--states", type=int, default=64, help="dense13 only: states sharing H")
     ap.add_argument("--workload", choices=["xxz20", "xxz10", "dense13", "batch512", "adjoint16", "spmv20"],
