@@ -346,10 +346,7 @@ def run_ours(args):
     fixed = bool(args.fixed_sums)
     head = measure_xxz(mg, c, terms, storage, variant, args.steps, args.warmup, args.repeats, args.interval, fixed,
                        args.rows, False, world, local, keep_state=True)
-    key = f"wl2_{storage}_{variant}" + ("_fixed" if head["fixed_sums"] else "") + (
-        f"_{head['row_layout']}" if head["row_layout"] else "")
-    head["roofline"]["traffic"] = (None if profiled_traffic(key) is None
-                                   else int(profiled_traffic(key) * head["roofline"]["leja_iterations"]))
+    attach_traffic(head, c, storage, variant)
     plan, psi_head = head.pop("_plan"), head.pop("_psi")
     value = head["steps_per_s"]
     psi = torch.empty_like(psi_head)
@@ -468,9 +465,23 @@ def run_ours(args):
 
 
 # --------------------------------------------------------------------------- every workload
+def attach_traffic(rec, c, storage, variant):
+    """The roofline's `traffic` of a 20-spin run: DRAM bytes per Leja iteration from the committed ncu
+    capture of the same workload, storage, method and row layout (profiles/traffic.json, valid only
+    for the sources it was taken on) times the run's Leja iterations; None without such a capture."""
+    if c.nspins != 20:
+        return
+    key = f"wl2_{storage}_{variant}" + ("_fixed" if rec["fixed_sums"] else "") + (
+        f"_{rec['row_layout']}" if rec["row_layout"] else "")
+    t = profiled_traffic(key)
+    rec["roofline"]["traffic"] = None if t is None else int(t * rec["roofline"]["leja_iterations"])
+    rec["roofline"]["traffic_key"] = key
+
+
 def wl_xxz(mg, mi, c, storage, variant, steps, repeats, interval, local, label):
     terms = workload_terms(mg, c, storage)
     r = measure_xxz(mg, c, terms, storage, variant, steps, 3, repeats, interval, True, "auto", False, 1, local)
+    attach_traffic(r, c, storage, variant)
     r["workload"] = label
     return r
 
