@@ -104,3 +104,35 @@ def test_clock_summary_of_sampled_records():
     assert got["reasons"] == ["hw_slowdown", "sw_power_cap"]
     s.out = ""
     assert s.summary()["reasons"] == ["unavailable"]
+
+
+def test_traffic_attaches_only_to_a_matching_capture(tmp_path, monkeypatch):
+    """A 20-spin run's roofline takes its DRAM traffic from profiles/traffic.json only under the key
+    of its storage, method, arithmetic and row layout, and only while the kernel sources hash to the
+    capture's; the 10-spin chain never gets one."""
+    class C:
+        def __init__(self, n):
+            self.nspins = n
+
+    def rec(layout):
+        return {"fixed_sums": 1, "row_layout": layout, "roofline": {"leja_iterations": 10, "traffic": None}}
+
+    sha = bench.kernel_source_hash(bench.PERSISTENT_SOURCES)
+    table = {"wl2_csr_M4_fixed_csr": {"kernel_sha": sha, "dram_bytes_per_iteration": 5},
+             "wl2_mfree_CF4_fixed": {"kernel_sha": "0" * 16, "dram_bytes_per_iteration": 7}}
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(table))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda files=bench.PERSISTENT_SOURCES: sha)
+    r = rec("csr")
+    bench.attach_traffic(r, C(20), "csr", "M4")
+    assert r["roofline"]["traffic"] == 50 and r["roofline"]["traffic_key"] == "wl2_csr_M4_fixed_csr"
+    r = rec(None)
+    bench.attach_traffic(r, C(20), "mfree", "CF4")  # captured on other sources: no traffic
+    assert r["roofline"]["traffic"] is None and r["roofline"]["traffic_key"] == "wl2_mfree_CF4_fixed"
+    r = rec("csr")
+    bench.attach_traffic(r, C(20), "csr", "CF4")  # no capture under this key
+    assert r["roofline"]["traffic"] is None
+    r = rec("csr")
+    bench.attach_traffic(r, C(10), "csr", "M4")
+    assert r["roofline"]["traffic"] is None and "traffic_key" not in r["roofline"]
