@@ -599,9 +599,10 @@ def dense_workload(mg, mi, local, nvec=64, nspins=13, rate_steps=(2, 4, 100), er
     bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
     if "tensor_sliced" in res:
         ts = res["tensor_sliced"]
-        # DRAM bytes per Leja iteration from the 12-spin capture (dim 4096), scaled by (dim / 4096)^2:
-        # the traffic is the digits of the dense terms, read once per iteration
-        t12 = profiled_traffic("dense_tc_12spins_64states", DENSE_TC_SOURCES)
+        # DRAM bytes per Leja iteration from the 12-spin capture (dim 4096) of the same method, scaled
+        # by (dim / 4096)^2: the traffic is the digits of the dense terms, read once per product phase
+        # (one per Leja iteration for linear generators, two for M4)
+        t12 = profiled_traffic("dense_tc_12spins_64states" + ("_m4" if variant == "M4" else ""), DENSE_TC_SOURCES)
         ts["roofline"] = {"bound": "tensor", "kernel": "k_dense_persistent (tcgen05 digit products)",
                           "achieved": ts["bf16_tflops_issued"], "peak": bf16_peak, "unit": "TFLOP/s",
                           "frac": round(ts["bf16_tflops_issued"] / bf16_peak, 4),
