@@ -241,6 +241,20 @@ def test_expv_degenerate_cases():
     assert np.max(np.abs(out - np.exp(-0.7j) * c.psi0)) < 1e-15
 
 
+@pytest.mark.parametrize("variant", ["M2", "M4", "CF4", "CF4_3", "M6"])
+def test_zero_state_and_zero_steps(variant):
+    """Every method is linear in the state and a propagation of no steps is the identity: the zero
+    state stays exactly zero (its stop test holds at the first Leja iteration), and zero steps return
+    the input unchanged."""
+    c, P, Hs, Hd = _chain_problem(6)
+    zero = np.zeros_like(c.psi0)
+    st = oracle.Stats(64)
+    out = P.propagate(zero, 0.0, 0.01, 3, variant, st)
+    assert np.array_equal(out, zero)
+    assert all(m <= 1 for m in st.m_log)
+    assert np.array_equal(P.propagate(c.psi0, 0.3, 0.01, 0, variant), c.psi0)
+
+
 def test_expv_reports_no_convergence():
     c, P, Hs, Hd = _chain_problem(6, m_max=3)
     with pytest.raises(oracle.OracleError) as e:
